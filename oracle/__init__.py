@@ -1,0 +1,203 @@
+"""TEST INFRASTRUCTURE ONLY: Python access to the plain FP64 C oracle.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It loads ``oracle/_build/libucp_oracle.so``
+(compiled by :func:`build`) through ctypes and exposes the oracle's functions
+on numpy arrays.  Nothing here shares code with the CUDA library.
+
+The oracle follows the paper's Section V-A problem statement (Witsenhausen's
+counterexample), Corollary 1 (pointwise minimisation of the marginal cost),
+eq. (2) (partial exhaustion over neighbouring samples), Section IV-A (Jacobi
+parallelism over the grid) and the closed-form u1 = E[x1 | y1] of Section IV-C.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ucp_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libucp_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc: FP64, no fused multiply-add, OpenMP."""
+    if (not force and os.path.exists(_OUT)
+            and os.path.getmtime(_OUT) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(_SRC[:-1] + "h"))):
+        return _OUT
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    tmp = _OUT + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("delta", ctypes.c_double), ("x_half", ctypes.c_double),
+                ("w_half", ctypes.c_double), ("y_half", ctypes.c_double),
+                ("cand_half", ctypes.c_double), ("n_coarse", ctypes.c_int32),
+                ("n_refine", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("n_nbr", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(_Params)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        L.orc_sizes.argtypes = [P, i64p, i64p, i64p, i64p, i32p]
+        L.orc_grids.argtypes = [P, dp, dp, dp, dp, dp]
+        L.orc_value.argtypes = [P, ctypes.c_int64]
+        L.orc_value.restype = ctypes.c_double
+        L.orc_init.argtypes = [P, ctypes.c_int, dp, i64p]
+        L.orc_S.argtypes = [P, dp, ctypes.c_int64]
+        L.orc_S.restype = ctypes.c_double
+        L.orc_cost.argtypes = [P, dp, ctypes.c_int64, ctypes.c_int64]
+        L.orc_cost.restype = ctypes.c_double
+        L.orc_search.argtypes = [P, i64p, dp, i64p, i32p, ctypes.c_int64,
+                                 ctypes.c_int64]
+        L.orc_candidates.argtypes = [P, i64p, dp, ctypes.c_int64, i64p, dp]
+        L.orc_mmse.argtypes = [P, i64p, dp, ctypes.c_int64, ctypes.c_int64]
+        L.orc_J.argtypes = [P, i64p, dp]
+        L.orc_J.restype = ctypes.c_double
+        L.orc_solve.argtypes = [P, ctypes.c_int, dp, ctypes.c_int, i64p, dp,
+                                dp, i32p]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_get_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+class Oracle:
+    """One Witsenhausen instance on the oracle.
+
+    ``params`` is a mapping with keys k, sigma, delta, x_half, w_half, y_half,
+    cand_half, n_coarse, n_refine, n_levels, n_nbr (extra keys are ignored).
+    Controllers f are int64 lattice indices nu; ``value(nu)`` converts.
+    """
+
+    def __init__(self, params):
+        self.params = dict(params)
+        self._p = _Params(*(float(params[k]) for k in
+                            ("k", "sigma", "delta", "x_half", "w_half",
+                             "y_half", "cand_half")),
+                          *(int(params[k]) for k in
+                            ("n_coarse", "n_refine", "n_levels", "n_nbr")))
+        n = [ctypes.c_int64() for _ in range(4)]
+        sh = ctypes.c_int32()
+        if lib().orc_sizes(ctypes.byref(self._p), *(ctypes.byref(v) for v in n),
+                           ctypes.byref(sh)) != 0:
+            raise ValueError(f"invalid oracle parameters: {params}")
+        self.n_x, self.n_w, self.n_y, self.n_cand = (v.value for v in n)
+        self.shift = sh.value
+
+    # -- grids ----------------------------------------------------------
+    def grids(self):
+        x = np.empty(self.n_x); px = np.empty(self.n_x)
+        w = np.empty(self.n_w); phi = np.empty(self.n_w)
+        y = np.empty(self.n_y)
+        lib().orc_grids(ctypes.byref(self._p), _dp(x), _dp(px), _dp(w),
+                        _dp(phi), _dp(y))
+        return dict(x=x, px=px, w=w, phi=phi, y=y)
+
+    def value(self, nu):
+        nu = np.asarray(nu, dtype=np.int64)
+        return np.ldexp(nu.astype(np.float64) * self.params["delta"], -self.shift)
+
+    def init(self, kind: int, table=None):
+        nu = np.empty(self.n_x, dtype=np.int64)
+        tab = None if table is None else np.ascontiguousarray(table, np.float64)
+        rc = lib().orc_init(ctypes.byref(self._p), int(kind),
+                            _dp(tab) if tab is not None else None, _i64p(nu))
+        if rc != 0:
+            raise ValueError("oracle init failed")
+        return nu
+
+    # -- pieces of the sweep ------------------------------------------------
+    def S(self, U, nu) -> float:
+        U = np.ascontiguousarray(U, np.float64)
+        return float(lib().orc_S(ctypes.byref(self._p), _dp(U), int(nu)))
+
+    def cost(self, U, i, nu) -> float:
+        U = np.ascontiguousarray(U, np.float64)
+        return float(lib().orc_cost(ctypes.byref(self._p), _dp(U), int(i),
+                                    int(nu)))
+
+    def search(self, nu_pre, U, i0=0, i1=None):
+        i1 = self.n_x if i1 is None else i1
+        nu_pre = np.ascontiguousarray(nu_pre, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        out = nu_pre.copy()
+        idx = np.full(self.n_x, -1, dtype=np.int32)
+        lib().orc_search(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
+                         _i64p(out), _i32p(idx), int(i0), int(i1))
+        return out, idx
+
+    def candidates(self, nu_pre, U, i):
+        nu_pre = np.ascontiguousarray(nu_pre, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        nus = np.empty(self.n_cand, dtype=np.int64)
+        gs = np.empty(self.n_cand)
+        idx = lib().orc_candidates(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
+                                   int(i), _i64p(nus), _dp(gs))
+        return nus, gs, int(idx)
+
+    def mmse(self, nu, j0=0, j1=None):
+        j1 = self.n_y if j1 is None else j1
+        nu = np.ascontiguousarray(nu, np.int64)
+        U = np.full(self.n_y, np.nan)
+        lib().orc_mmse(ctypes.byref(self._p), _i64p(nu), _dp(U), int(j0), int(j1))
+        return U
+
+    def J(self, nu, U) -> float:
+        nu = np.ascontiguousarray(nu, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        return float(lib().orc_J(ctypes.byref(self._p), _i64p(nu), _dp(U)))
+
+    def solve(self, init_kind: int, n_sweeps: int, table=None, want_idx=False):
+        nu = np.empty(self.n_x, dtype=np.int64)
+        U = np.empty(self.n_y)
+        Jh = np.empty(n_sweeps + 1)
+        idx = np.empty((n_sweeps, self.n_x), dtype=np.int32) if want_idx else None
+        tab = None if table is None else np.ascontiguousarray(table, np.float64)
+        rc = lib().orc_solve(ctypes.byref(self._p), int(init_kind),
+                             _dp(tab) if tab is not None else None, int(n_sweeps),
+                             _i64p(nu), _dp(U), _dp(Jh),
+                             _i32p(idx) if idx is not None else None)
+        if rc != 0:
+            raise ValueError("oracle solve failed")
+        return dict(nu=nu, U=U, J=Jh, idx=idx)

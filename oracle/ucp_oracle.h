@@ -1,0 +1,94 @@
+/*
+ * ucp_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Declarations of the plain, slow FP64 CPU oracle for the coordinate-descent
+ * sweep of the generic UCP solver (Tseng, "A Generic Solver for Unconstrained
+ * Control Problems with Integral Functional Objectives", ACC 2020) on
+ * Witsenhausen's counterexample (Section V-A).  Only tests/, the smoke check
+ * and the CPU-baseline leg of bench.py may load this library.  It shares no
+ * code, header or table with the CUDA library.
+ *
+ * Notation (Section V-A): x1 = x0 + u0(x0), y1 = x1 + w, x2 = x1 - u1(y1),
+ * J = E[k^2 u0^2 + x2^2], x0 ~ N(0, sigma^2), w ~ N(0, 1).  The first
+ * controller is carried as f(x0) = x1 = x0 + u0(x0).
+ *
+ * Controller values live on the lattice  delta * 2^-shift * Z  with
+ * shift = L * log2(n_refine / 2); they are passed as int64 lattice indices nu
+ * (value = nu * delta * 2^-shift).  Every candidate the search generates lies
+ * on this lattice, so positions on the y grid are exact.
+ */
+#ifndef UCP_ORACLE_H
+#define UCP_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double k;          /* control-cost weight, k > 0                           */
+    double sigma;      /* prior std of x0, sigma > 0                           */
+    double delta;      /* common spacing of the x0, w and y grids              */
+    double x_half;     /* x0 grid is [-x_half, x_half]                         */
+    double w_half;     /* w quadrature grid is [-w_half, w_half]               */
+    double y_half;     /* u1 table grid is [-y_half, y_half]                   */
+    double cand_half;  /* coarse candidates cover [-cand_half, cand_half]      */
+    int32_t n_coarse;  /* number of coarse candidates (64)                     */
+    int32_t n_refine;  /* candidates per refinement level (16)                 */
+    int32_t n_levels;  /* refinement levels L                                  */
+    int32_t n_nbr;     /* neighbours per side in the partial exhaustion (2)    */
+} orc_params;
+
+/* Sizes; returns 0 on success, -1 on invalid parameters. */
+int orc_sizes(const orc_params* p, int64_t* n_x, int64_t* n_w, int64_t* n_y,
+              int64_t* n_cand, int32_t* shift);
+
+/* Grids and normalised rectangle-rule weights. */
+int orc_grids(const orc_params* p, double* x, double* px, double* w,
+              double* phi, double* y);
+
+/* Value of lattice index nu. */
+double orc_value(const orc_params* p, int64_t nu);
+
+/* Initial controller f: kind 0 identity, 1 odd staircase, 2 table. */
+int orc_init(const orc_params* p, int kind, const double* table,
+             int64_t* nu_out);
+
+/* S(u) = sum_l phi_l (u - U^(u + w_l))^2 at u = value(nu). */
+double orc_S(const orc_params* p, const double* U, int64_t nu);
+
+/* g(u; x_i) = k^2 (u - x_i)^2 + S(u). */
+double orc_cost(const orc_params* p, const double* U, int64_t i, int64_t nu);
+
+/* Candidate search for x_i, i in [i0, i1): Jacobi, reads nu_pre, writes
+ * nu_out[i] and idx_out[i] (list position of the winner). */
+void orc_search(const orc_params* p, const int64_t* nu_pre, const double* U,
+                int64_t* nu_out, int32_t* idx_out, int64_t i0, int64_t i1);
+
+/* Full candidate list for x_i with every cost, in list order (for tests). */
+int orc_candidates(const orc_params* p, const int64_t* nu_pre, const double* U,
+                   int64_t i, int64_t* nu_list, double* g_list);
+
+/* u1 update U_j = E[x1 | y1 = y_j] for j in [j0, j1). */
+void orc_mmse(const orc_params* p, const int64_t* nu, double* U, int64_t j0,
+              int64_t j1);
+
+/* J = sum_i px_i (k^2 (f_i - x_i)^2 + S(f_i)). */
+double orc_J(const orc_params* p, const int64_t* nu, const double* U);
+
+/* init -> U = mmse(f) -> n_sweeps x {search, mmse, J}.  J_hist[0] is J of
+ * the initial state, J_hist[s] after sweep s.  idx_hist may be NULL. */
+int orc_solve(const orc_params* p, int init_kind, const double* table,
+              int n_sweeps, int64_t* nu_out, double* U_out, double* J_hist,
+              int32_t* idx_hist);
+
+/* Threads used by orc_search / orc_mmse / orc_solve (OpenMP; 1 = serial).
+ * Results do not depend on the thread count. */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
