@@ -1,0 +1,169 @@
+/*
+ * ucp.h -- C ABI of libucp.so: the coordinate-descent sweep of the generic
+ * UCP solver (Tseng, "A Generic Solver for Unconstrained Control Problems
+ * with Integral Functional Objectives", ACC 2020) on Witsenhausen's
+ * counterexample, computed by CUDA kernels for sm_103a (GB300).
+ *
+ * Problem (Section V-A): x1 = x0 + u0(x0), y1 = x1 + w, x2 = x1 - u1(y1),
+ * J = E[k^2 u0^2 + x2^2], x0 ~ N(0, sigma^2), w ~ N(0, 1).  The library
+ * carries the first controller as f(x0) = x1 = x0 + u0(x0) on the x0 grid and
+ * u1 as a table U on the y grid, linearly interpolated and held constant
+ * beyond its ends.  Controllers are step/linear tables on linearly spaced
+ * samples as in Section III-D ("Initialization").
+ *
+ * One sweep (Algorithm 1's partial-exhaustion phase for m = 0, then the u1
+ * update, then J):
+ *   1. u0 step (Corollary 1, eq. (2), Section IV-A): for every x_i in
+ *      parallel, f_i <- the first minimiser of
+ *          g(u; x_i) = k^2 (u - x_i)^2 + sum_l phi_l (u - U^(u + w_l))^2
+ *      over the candidate list [f_i; f_{i-r..i-1}, f_{i+1..i+r};
+ *      n_coarse values symmetric about 0; n_levels levels of n_refine values
+ *      around the best so far, each level n_refine/2 times finer].  Every
+ *      x_i reads the pre-sweep f (Jacobi).
+ *   2. u1 step: U_j <- E[x1 | y1 = y_j], the minimiser of the quadratic
+ *      marginal cost C_1 (one Newton step of Section III-D; the closed form
+ *      of Section IV-C).
+ *   3. J <- sum_i p_i g(f_i; x_i) in FP64.
+ *
+ * Conventions for every call:
+ *   - Return value: a ucp_status.  No call aborts, traps or exits.  After
+ *     UCP_E_CUDA or UCP_E_TIMEOUT the object is poisoned and later calls on
+ *     it return UCP_E_STATE; ucp_last_error() gives a one-line reason.
+ *   - Pointers named host_* or documented as host are host memory owned by
+ *     the caller; the library copies from/to them before returning.  The
+ *     library owns all device memory it allocates (through the context's
+ *     allocator, or cudaMalloc if none was given) and frees it on destroy.
+ *   - Objects are not thread-safe, except ucp_submit / ucp_poll, which may be
+ *     called from any thread.
+ *   - Device work is issued on the stream given at creation (cudaStream_t
+ *     passed as void*; NULL makes the library create its own stream).
+ */
+#ifndef UCP_H
+#define UCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define UCP_API __attribute__((visibility("default")))
+#else
+#define UCP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UCP_OK = 0,
+    UCP_PENDING = 1,      /* ucp_poll: the request has not finished        */
+    UCP_E_ARG = -1,       /* invalid argument; nothing was changed          */
+    UCP_E_NOMEM = -2,     /* device allocation failed                       */
+    UCP_E_BUDGET = -3,    /* one request alone exceeds the server budget    */
+    UCP_E_CUDA = -4,      /* a CUDA call failed; the object is poisoned     */
+    UCP_E_TIMEOUT = -5,   /* a bounded device wait gave up                  */
+    UCP_E_STATE = -6,     /* object poisoned, destroyed or busy             */
+    UCP_E_NOTFOUND = -7   /* unknown ticket                                 */
+} ucp_status;
+
+/* Problem and solver parameters (Section V-A problem; grids of Section
+ * III-D).  All half widths must be multiples of delta (relative tolerance
+ * 1e-9).  Grids: x_i = (i - X/delta) delta, i < 2X/delta + 1; likewise w and
+ * y.  Prior weights p_i ~ exp(-x_i^2 / 2 sigma^2) and quadrature weights
+ * phi_l ~ exp(-w_l^2 / 2) are normalised to sum 1 (rectangle rule). */
+typedef struct {
+    double k;           /* > 0                                              */
+    double sigma;       /* > 0                                              */
+    double delta;       /* > 0, common spacing of the x0, w and y grids     */
+    double x_half;      /* x0 grid [-x_half, x_half]                        */
+    double w_half;      /* w grid [-w_half, w_half]                         */
+    double y_half;      /* u1 table grid [-y_half, y_half]                  */
+    double cand_half;   /* coarse candidates cover [-cand_half, cand_half]  */
+    int32_t n_coarse;   /* >= 2 (64)                                        */
+    int32_t n_refine;   /* 2, 4, 8, 16 or 32 (16)                           */
+    int32_t n_levels;   /* 0..8 (4)                                          */
+    int32_t n_nbr;      /* neighbours per side, 0..8 (2: "2 points per
+                           direction", Section III-D)                        */
+    int32_t init_kind;  /* 0 identity f(x) = x (Section III-D);
+                           1 odd staircase 3.5 sgn(x) (2 min(floor(|x|/7),2)+1);
+                           2 table (init_table)                              */
+    int32_t precision;  /* 0: plain FP64 path (every cost a sequential FP64
+                           quadrature); 1: fast path (correlation tables
+                           screen the candidates, near-ties re-decided by the
+                           FP64 quadrature).  Both make the same decisions.  */
+    const double* init_table; /* host, n_x values of f, init_kind 2 only     */
+    uint64_t init_len;        /* must equal n_x for init_kind 2              */
+    uint64_t flags;           /* reserved, must be 0                         */
+} ucp_params;
+
+/* Device allocator hooks (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer aligned to 256 bytes or NULL. */
+typedef void* (*ucp_alloc_fn)(size_t bytes, void* user);
+typedef void (*ucp_free_fn)(void* ptr, void* user);
+
+typedef struct ucp_ctx ucp_ctx;
+typedef struct ucp_inst ucp_inst;
+typedef struct ucp_batch ucp_batch;
+typedef struct ucp_srv ucp_srv;
+
+UCP_API const char* ucp_status_str(ucp_status s);
+/* Reason for the last failing call on this thread (static storage). */
+UCP_API const char* ucp_last_error(void);
+/* Library version, build architecture string (e.g. "sm_103a"). */
+UCP_API const char* ucp_version(void);
+
+/* Validate params on the host without touching the GPU; returns the grid
+ * sizes, the candidate-list length and the device bytes one instance will
+ * hold (any output may be NULL).  UCP_E_ARG with ucp_last_error() naming
+ * the offending field when invalid. */
+UCP_API ucp_status ucp_plan(const ucp_params* params, uint64_t* n_x, uint64_t* n_w,
+                            uint64_t* n_y, uint64_t* n_cand,
+                            uint64_t* device_bytes);
+
+/* Context: device ordinal, optional allocator (both NULL = cudaMalloc). */
+UCP_API ucp_status ucp_ctx_create(int32_t device, ucp_alloc_fn alloc, ucp_free_fn free_fn,
+                          void* user, ucp_ctx** out);
+UCP_API ucp_status ucp_ctx_destroy(ucp_ctx* ctx);
+
+/* ---- one instance ---------------------------------------------------- */
+
+/* Validate params, build the grids and weights on the device, set f from
+ * the init, then U <- E[x1 | y1] and J.  Work is enqueued on `stream`. */
+UCP_API ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params, void* stream,
+                      ucp_inst** out);
+/* Grid sizes, candidate-list length and device bytes held. */
+UCP_API ucp_status ucp_sizes(const ucp_inst* inst, uint64_t* n_x, uint64_t* n_w,
+                     uint64_t* n_y, uint64_t* n_cand, uint64_t* device_bytes);
+/* Enqueue n_sweeps sweeps (asynchronous; J after each is recorded). */
+UCP_API ucp_status ucp_sweep(ucp_inst* inst, int32_t n_sweeps);
+/* Synchronise and return J of the current controllers. */
+UCP_API ucp_status ucp_eval_J(ucp_inst* inst, double* J_out);
+/* Synchronise and return J after each sweep: host out[0..n), out[0] is the
+ * initial J; n is clamped to the sweeps done + 1, *n_written set. */
+UCP_API ucp_status ucp_J_history(ucp_inst* inst, double* out, uint64_t n,
+                         uint64_t* n_written);
+/* Synchronise and copy the controllers to host buffers (any may be NULL):
+ * f (n_x; u0 = f - x0 if as_paper_u0), U (n_y), idx = list position of the
+ * winner of every x_i in the last sweep (n_x, -1 before the first sweep). */
+UCP_API ucp_status ucp_get_controllers(ucp_inst* inst, double* f, uint64_t n_x,
+                               double* u1, uint64_t n_y, int32_t as_paper_u0,
+                               int32_t* idx);
+/* Replace the state from host buffers: f (n_x values, rounded to the lattice
+ * delta 2^-(n_levels log2(n_refine/2)) that all candidates lie on); U (n_y)
+ * or NULL to recompute U <- E[x1 | y1].  J is recomputed.  Resume from a
+ * checkpoint = ucp_get_controllers + ucp_set_controllers. */
+UCP_API ucp_status ucp_set_controllers(ucp_inst* inst, const double* f, uint64_t n_x,
+                               const double* u1, uint64_t n_y);
+UCP_API ucp_status ucp_destroy(ucp_inst* inst);
+
+/* Per-kernel CUDA-event timing on the instance stream (off by default).
+ * ucp_kernel_times fills up to cap entries: name (static), launches and
+ * total milliseconds since the last reset; returns the entry count. */
+UCP_API ucp_status ucp_profile(ucp_inst* inst, int32_t enable);
+UCP_API int32_t ucp_kernel_times(ucp_inst* inst, const char** names,
+                         int64_t* launches, double* total_ms, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,261 @@
+"""Thin Python binding of libucp.so (C ABI in include/ucp.h).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  PyTorch supplies the CUDA stream and, through the allocator hooks,
+the device memory (its caching allocator).  The library must have been built
+(``__graft_entry__.build()`` or ``python -m paper_1908_04489_gb300.build``);
+if it is missing, loading raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+UCP_OK, UCP_PENDING = 0, 1
+STATUS = {0: "UCP_OK", 1: "UCP_PENDING", -1: "UCP_E_ARG", -2: "UCP_E_NOMEM",
+          -3: "UCP_E_BUDGET", -4: "UCP_E_CUDA", -5: "UCP_E_TIMEOUT",
+          -6: "UCP_E_STATE", -7: "UCP_E_NOTFOUND"}
+
+
+class UcpError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} {detail}".strip())
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``ucp_params``."""
+    _fields_ = [("k", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("delta", ctypes.c_double), ("x_half", ctypes.c_double),
+                ("w_half", ctypes.c_double), ("y_half", ctypes.c_double),
+                ("cand_half", ctypes.c_double), ("n_coarse", ctypes.c_int32),
+                ("n_refine", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("n_nbr", ctypes.c_int32), ("init_kind", ctypes.c_int32),
+                ("precision", ctypes.c_int32),
+                ("init_table", ctypes.POINTER(ctypes.c_double)),
+                ("init_len", ctypes.c_uint64), ("flags", ctypes.c_uint64)]
+
+    @classmethod
+    def from_dict(cls, p, table=None):
+        obj = cls(float(p["k"]), float(p["sigma"]), float(p["delta"]),
+                  float(p["x_half"]), float(p["w_half"]), float(p["y_half"]),
+                  float(p["cand_half"]), int(p["n_coarse"]), int(p["n_refine"]),
+                  int(p["n_levels"]), int(p["n_nbr"]), int(p.get("init_kind", 0)),
+                  int(p.get("precision", 0)), None, 0, int(p.get("flags", 0)))
+        if table is not None:
+            obj._table = np.ascontiguousarray(table, dtype=np.float64)
+            obj.init_table = obj._table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            obj.init_len = obj._table.size
+        return obj
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libucp.so; raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libucp.so is not built ({path}); run "
+                           "__graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER(Params)
+    L.ucp_status_str.argtypes = [ctypes.c_int]
+    L.ucp_status_str.restype = ctypes.c_char_p
+    L.ucp_last_error.restype = ctypes.c_char_p
+    L.ucp_version.restype = ctypes.c_char_p
+    L.ucp_plan.argtypes = [P, _u64p, _u64p, _u64p, _u64p, _u64p]
+    L.ucp_ctx_create.argtypes = [ctypes.c_int32, ALLOC_FN, FREE_FN, _vp,
+                                 ctypes.POINTER(_vp)]
+    L.ucp_ctx_destroy.argtypes = [_vp]
+    L.ucp_create.argtypes = [_vp, P, _vp, ctypes.POINTER(_vp)]
+    L.ucp_sizes.argtypes = [_vp, _u64p, _u64p, _u64p, _u64p, _u64p]
+    L.ucp_sweep.argtypes = [_vp, ctypes.c_int32]
+    L.ucp_eval_J.argtypes = [_vp, _dp]
+    L.ucp_J_history.argtypes = [_vp, _dp, _u64, _u64p]
+    L.ucp_get_controllers.argtypes = [_vp, _dp, _u64, _dp, _u64, ctypes.c_int32,
+                                      _i32p]
+    L.ucp_set_controllers.argtypes = [_vp, _dp, _u64, _dp, _u64]
+    L.ucp_destroy.argtypes = [_vp]
+    L.ucp_profile.argtypes = [_vp, ctypes.c_int32]
+    L.ucp_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_char_p),
+                                   ctypes.POINTER(ctypes.c_int64), _dp,
+                                   ctypes.c_int32]
+    L.ucp_kernel_times.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(st, where):
+    if st != UCP_OK:
+        detail = load().ucp_last_error().decode(errors="replace")
+        raise UcpError(st, where, detail)
+
+
+def _ptr(a, typ):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(typ))
+
+
+def plan(params) -> dict:
+    """Validate parameters on the host (no GPU needed): sizes and bytes."""
+    L = load()
+    v = [ctypes.c_uint64() for _ in range(5)]
+    _check(L.ucp_plan(ctypes.byref(Params.from_dict(params)),
+                      *(ctypes.byref(x) for x in v)), "ucp_plan")
+    return dict(zip(("n_x", "n_w", "n_y", "n_cand", "device_bytes"),
+                    (x.value for x in v)))
+
+
+class Context:
+    """ucp_ctx bound to a CUDA device, with PyTorch's caching allocator."""
+
+    def __init__(self, device: int | None = None, use_torch_allocator=True):
+        import torch
+        L = load()
+        self.device = torch.cuda.current_device() if device is None else device
+        self._alloc = self._free = None
+        if use_torch_allocator:
+            dev = self.device
+
+            def _a(n, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(
+                        int(n), dev, torch.cuda.current_stream(dev))
+                except RuntimeError:
+                    return None
+
+            def _f(p, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            self._alloc, self._free = ALLOC_FN(_a), FREE_FN(_f)
+        else:
+            self._alloc = ctypes.cast(None, ALLOC_FN)
+            self._free = ctypes.cast(None, FREE_FN)
+        h = _vp()
+        _check(L.ucp_ctx_create(self.device, self._alloc, self._free, None,
+                                ctypes.byref(h)), "ucp_ctx_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().ucp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = None
+
+
+def default_context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context()
+    return _default_ctx
+
+
+class Instance:
+    """One Witsenhausen instance (``ucp_create`` ... ``ucp_destroy``)."""
+
+    def __init__(self, params, table=None, stream=None, ctx: Context | None = None):
+        import torch
+        L = load()
+        self.ctx = ctx or default_context()
+        self.params = dict(params)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.ctx.device)
+        self.stream = stream
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        h = _vp()
+        self._p = Params.from_dict(params, table)
+        _check(L.ucp_create(self.ctx.h, ctypes.byref(self._p), _vp(sp),
+                            ctypes.byref(h)), "ucp_create")
+        self.h = h
+        v = [ctypes.c_uint64() for _ in range(5)]
+        _check(L.ucp_sizes(h, *(ctypes.byref(x) for x in v)), "ucp_sizes")
+        self.n_x, self.n_w, self.n_y, self.n_cand, self.device_bytes = \
+            (x.value for x in v)
+
+    def sweep(self, n: int = 1):
+        _check(load().ucp_sweep(self.h, int(n)), "ucp_sweep")
+
+    def eval_J(self) -> float:
+        J = ctypes.c_double()
+        _check(load().ucp_eval_J(self.h, ctypes.byref(J)), "ucp_eval_J")
+        return J.value
+
+    def J_history(self, n: int = 1 << 20) -> np.ndarray:
+        out = np.empty(n)
+        m = ctypes.c_uint64()
+        _check(load().ucp_J_history(self.h, _ptr(out, ctypes.c_double), n,
+                                    ctypes.byref(m)), "ucp_J_history")
+        return out[:m.value]
+
+    def get_controllers(self, as_paper_u0=False, want=("f", "U", "idx")):
+        f = np.empty(self.n_x) if "f" in want else None
+        U = np.empty(self.n_y) if "U" in want else None
+        idx = np.empty(self.n_x, dtype=np.int32) if "idx" in want else None
+        _check(load().ucp_get_controllers(
+            self.h, _ptr(f, ctypes.c_double), self.n_x,
+            _ptr(U, ctypes.c_double), self.n_y, int(bool(as_paper_u0)),
+            _ptr(idx, ctypes.c_int32)), "ucp_get_controllers")
+        return dict(f=f, U=U, idx=idx)
+
+    def set_controllers(self, f, U=None):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        U = None if U is None else np.ascontiguousarray(U, dtype=np.float64)
+        _check(load().ucp_set_controllers(
+            self.h, _ptr(f, ctypes.c_double), f.size, _ptr(U, ctypes.c_double),
+            0 if U is None else U.size), "ucp_set_controllers")
+
+    def profile(self, on=True):
+        _check(load().ucp_profile(self.h, int(bool(on))), "ucp_profile")
+
+    def kernel_times(self) -> dict:
+        L = load()
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = L.ucp_kernel_times(self.h, names, launches, ms, cap)
+        return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(load().ucp_destroy(self.h), "ucp_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

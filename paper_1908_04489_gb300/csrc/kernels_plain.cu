@@ -1,0 +1,368 @@
+// kernels_plain.cu -- the plain FP64 path of the sweep.
+//
+// Every marginal cost is the direct w quadrature of Section V-A's objective,
+//   g(u; x_i) = k^2 (u - x_i)^2 + sum_l phi_l (u - U^(u + w_l))^2,
+// summed over l in index order with one rounding per operation (no fused
+// multiply-add): the same value, bit for bit, as a straightforward serial
+// FP64 evaluation of the definition.  The fast path uses these kernels'
+// device functions to re-decide near-ties, so both paths make the same
+// decisions.  Parallelism follows Section IV-A: all x_i (and all y_j) are
+// independent within one controller update.
+#include <float.h>
+#include <limits.h>
+
+#include "ucp_internal.cuh"
+
+namespace ucp {
+
+namespace {
+
+__device__ __forceinline__ double inv_one(const Geom& g) {
+    return __longlong_as_double((int64_t)(1023 - g.shift) << 52);  // 2^-shift
+}
+
+__device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
+    return __dmul_rn(__dmul_rn((double)nu, g.delta), inv_one(g));
+}
+
+__device__ __forceinline__ double x_of(const Geom& g, int64_t i) {
+    return __dmul_rn((double)(i - g.hx), g.delta);
+}
+
+// S(u) at u = value(nu): positions of u + w_l on the y grid are jb + l + t
+// with exact integer jb and dyadic t; U^ is linear between samples and
+// constant beyond the ends (Ud = 0 there).
+__device__ double S_plain(const Geom& g, const double* __restrict__ phi,
+                          const double* __restrict__ U,
+                          const double* __restrict__ Ud, int64_t nu) {
+    const int64_t cell = nu >> g.shift;  // floor division by 2^shift
+    const double t = __dmul_rn((double)(nu - (cell << g.shift)), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy;
+    const double u = value_of(g, nu);
+    const int64_t ny1 = g.n_y - 1;
+    double acc = 0.0;
+    int64_t l = 0;
+    // left clamp: j = jb + l < 0 -> U^ = U_0
+    const double u0 = U[0];
+    const double eL = __dsub_rn(u, __dadd_rn(u0, __dmul_rn(t, 0.0)));
+    const double eL2 = __dmul_rn(eL, eL);
+    for (; l < g.n_w && jb + l < 0; ++l)
+        acc = __dadd_rn(acc, __dmul_rn(phi[l], eL2));
+    // interior: 0 <= j < n_y - 1
+    for (; l < g.n_w && jb + l < ny1; ++l) {
+        const int64_t j = jb + l;
+        const double uh = __dadd_rn(U[j], __dmul_rn(t, Ud[j]));
+        const double e = __dsub_rn(u, uh);
+        acc = __dadd_rn(acc, __dmul_rn(phi[l], __dmul_rn(e, e)));
+    }
+    // right clamp: j >= n_y - 1 -> U^ = U_{n_y - 1}
+    const double uN = U[ny1];
+    const double eR = __dsub_rn(u, __dadd_rn(uN, __dmul_rn(t, 0.0)));
+    const double eR2 = __dmul_rn(eR, eR);
+    for (; l < g.n_w; ++l) acc = __dadd_rn(acc, __dmul_rn(phi[l], eR2));
+    return acc;
+}
+
+__device__ __forceinline__ double cost_from_S(const Geom& g, int64_t i,
+                                              int64_t nu, double S) {
+    const double a = __dsub_rn(value_of(g, nu), x_of(g, i));
+    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), S);
+}
+
+// (g, pos) lexicographic order == "first strict minimum in list order".
+__device__ __forceinline__ bool before(double ga, int32_t pa, double gb,
+                                       int32_t pb) {
+    return ga < gb || (ga == gb && pa < pb);
+}
+
+template <int G>
+__device__ __forceinline__ void group_argmin(double& gv, int32_t& pos,
+                                             int64_t& nu) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const double go = __shfl_xor_sync(0xffffffffu, gv, off, G);
+        const int32_t po = __shfl_xor_sync(0xffffffffu, pos, off, G);
+        const int64_t no = __shfl_xor_sync(0xffffffffu, nu, off, G);
+        if (before(go, po, gv, pos)) { gv = go; pos = po; nu = no; }
+    }
+}
+
+// ---- setup ------------------------------------------------------------
+
+__global__ void k_weights(Geom g, double* px, double* phi) {
+    __shared__ double total;
+    for (int64_t i = threadIdx.x; i < g.n_x; i += blockDim.x) {
+        const double xi = x_of(g, i);
+        px[i] = exp(-__ddiv_rn(__dmul_rn(xi, xi), g.two_s2));
+    }
+    for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x) {
+        const double wl = __dmul_rn((double)(l - g.hw), g.delta);
+        phi[l] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int64_t i = 0; i < g.n_x; ++i) s = __dadd_rn(s, px[i]);
+        total = s;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < g.n_x; i += blockDim.x)
+        px[i] = __ddiv_rn(px[i], total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int64_t l = 0; l < g.n_w; ++l) s = __dadd_rn(s, phi[l]);
+        total = s;
+    }
+    __syncthreads();
+    for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x)
+        phi[l] = __ddiv_rn(phi[l], total);
+}
+
+// kind 0: identity f(x) = x; kind 1: odd staircase with step n7 (units of
+// delta) and level lattice indices lv[0..2].
+__global__ void k_init(Geom g, int kind, int64_t n7, int64_t lv0, int64_t lv1,
+                       int64_t lv2, int64_t* nu) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_x) return;
+    const int64_t a = i - g.hx;
+    if (kind == 0) {
+        nu[i] = a * g.one;
+    } else {
+        if (a == 0) { nu[i] = 0; return; }
+        int64_t m = (a < 0 ? -a : a) / n7;
+        const int64_t v = m == 0 ? lv0 : (m == 1 ? lv1 : lv2);
+        nu[i] = a < 0 ? -v : v;
+    }
+}
+
+__global__ void k_table_to_lattice(Geom g, const double* table, int64_t* nu) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_x) return;
+    const double v = __dmul_rn(__ddiv_rn(table[i], g.delta), (double)g.one);
+    nu[i] = llround(v);
+}
+
+__global__ void k_coarse(Geom g, int64_t* coarse) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_coarse) return;
+    coarse[j] = (int64_t)(2 * j - (g.n_coarse - 1)) * (g.q / 2) * g.one;
+}
+
+__global__ void k_f_values(Geom g, const int64_t* nu, double* out, int as_u0) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_x) return;
+    const double f = value_of(g, nu[i]);
+    out[i] = as_u0 ? __dsub_rn(f, x_of(g, i)) : f;
+}
+
+// ---- u1 step: U_j = E[x1 | y1 = y_j] -----------------------------------
+// One thread per y_j sums over all x_i in index order (same order as a
+// serial evaluation), after subtracting min_i E_ij from the exponents
+// E_ij = x_i^2 / (2 sigma^2) + (y_j - f_i)^2 / 2.
+constexpr int kMmseChunk = 1024;
+
+__global__ void __launch_bounds__(128) k_mmse_plain(Geom g, const int64_t* nu,
+                                                    double* U) {
+    __shared__ double s_pri[kMmseChunk];
+    __shared__ double s_f[kMmseChunk];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double yj = __dmul_rn((double)((j < g.n_y ? j : g.n_y - 1) - g.hy),
+                                g.delta);
+    double emin = DBL_MAX;
+    for (int pass = 0; pass < 2; ++pass) {
+        double num = 0.0, den = 0.0;
+        for (int64_t base = 0; base < g.n_x; base += kMmseChunk) {
+            const int cnt = (int)min((int64_t)kMmseChunk, g.n_x - base);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                const double xi = x_of(g, base + t);
+                s_pri[t] = __ddiv_rn(__dmul_rn(xi, xi), g.two_s2);
+                s_f[t] = value_of(g, nu[base + t]);
+            }
+            __syncthreads();
+            if (pass == 0) {
+                for (int t = 0; t < cnt; ++t) {
+                    const double d = __dsub_rn(yj, s_f[t]);
+                    const double e = __dadd_rn(s_pri[t],
+                                               __ddiv_rn(__dmul_rn(d, d), 2.0));
+                    emin = e < emin ? e : emin;
+                }
+            } else {
+                for (int t = 0; t < cnt; ++t) {
+                    const double d = __dsub_rn(yj, s_f[t]);
+                    const double e = __dadd_rn(s_pri[t],
+                                               __ddiv_rn(__dmul_rn(d, d), 2.0));
+                    const double wgt = exp(-__dsub_rn(e, emin));
+                    num = __dadd_rn(num, __dmul_rn(wgt, s_f[t]));
+                    den = __dadd_rn(den, wgt);
+                }
+            }
+        }
+        if (pass == 1 && j < g.n_y) U[j] = __ddiv_rn(num, den);
+    }
+}
+
+__global__ void k_udiff(Geom g, const double* U, double* Ud) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_y) return;
+    Ud[j] = j + 1 < g.n_y ? __dsub_rn(U[j + 1], U[j]) : 0.0;
+}
+
+__global__ void k_S_list(Geom g, const double* __restrict__ phi,
+                         const double* __restrict__ U,
+                         const double* __restrict__ Ud,
+                         const int64_t* __restrict__ nus, int64_t n,
+                         double* out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    out[k] = S_plain(g, phi, U, Ud, nus[k]);
+}
+
+// ---- u0 step: candidate search, one group of n_refine lanes per x_i ----
+template <int G>
+__global__ void __launch_bounds__(256) k_search_plain(
+    Geom g, const double* __restrict__ phi, const double* __restrict__ U,
+    const double* __restrict__ Ud, const int64_t* __restrict__ nu_pre,
+    const double* __restrict__ Sf, const double* __restrict__ Sc,
+    const int64_t* __restrict__ coarse, int64_t* __restrict__ nu_out,
+    int32_t* __restrict__ idx_out) {
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool active = i < g.n_x;
+    const int64_t ic = active ? i : g.n_x - 1;
+
+    double best_g = DBL_MAX;
+    int32_t best_p = INT_MAX;
+    int64_t best_nu = 0;
+    // stage 0: incumbent, neighbours, coarse (their S is precomputed)
+    const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
+    for (int p = lane; p < n0; p += G) {
+        int64_t nu;
+        double S;
+        if (p == 0) {
+            nu = nu_pre[ic];
+            S = Sf[ic];
+        } else if (p <= 2 * g.n_nbr) {
+            const int d = p <= g.n_nbr ? p - g.n_nbr - 1 : p - g.n_nbr;
+            int64_t ii = ic + d;
+            if (ii < 0 || ii >= g.n_x) ii = ic;
+            nu = nu_pre[ii];
+            S = Sf[ii];
+        } else {
+            const int c = p - 1 - 2 * g.n_nbr;
+            nu = coarse[c];
+            S = Sc[c];
+        }
+        const double gv = cost_from_S(g, ic, nu, S);
+        if (before(gv, p, best_g, best_p)) { best_g = gv; best_p = p; best_nu = nu; }
+    }
+    group_argmin<G>(best_g, best_p, best_nu);
+
+    // refinement levels around the best so far
+    const int half = G / 2;
+    const int64_t m = lane < half ? lane - half : lane - half + 1;
+    int pos = n0;
+    for (int lv = 1; lv <= g.n_levels; ++lv) {
+        const int64_t h = g.q << (g.bits * (g.n_levels - lv));
+        const int64_t nu = best_nu + m * h;
+        const double gv = cost_from_S(g, ic, nu, S_plain(g, phi, U, Ud, nu));
+        double cg = best_g;
+        int32_t cp = best_p;
+        int64_t cn = best_nu;
+        if (before(gv, pos + lane, cg, cp)) { cg = gv; cp = pos + lane; cn = nu; }
+        group_argmin<G>(cg, cp, cn);
+        best_g = cg; best_p = cp; best_nu = cn;
+        pos += G;
+    }
+    if (active && lane == 0) {
+        nu_out[i] = best_nu;
+        idx_out[i] = best_p;
+    }
+}
+
+// ---- J = sum_i p_i (k^2 (f_i - x_i)^2 + S(f_i)), serial order ------------
+__global__ void k_J_plain(Geom g, const double* px, const int64_t* nu,
+                          const double* Sf, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double J = 0.0;
+    for (int64_t i = 0; i < g.n_x; ++i)
+        J = __dadd_rn(J, __dmul_rn(px[i], cost_from_S(g, i, nu[i], Sf[i])));
+    *out = J;
+}
+
+inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ---- launch wrappers ----------------------------------------------------
+
+void launch_weights(const Geom& g, DevState& d, cudaStream_t s) {
+    k_weights<<<1, 1024, 0, s>>>(g, d.px, d.phi);
+}
+
+void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s) {
+    int64_t n7 = 1, lv[3] = {0, 0, 0};
+    if (kind == 1) {
+        n7 = llround(7.0 / g.delta);
+        for (int m = 0; m < 3; ++m)
+            lv[m] = llround(3.5 * (double)(2 * m + 1) / g.delta * (double)g.one);
+    }
+    k_init<<<blocks(g.n_x, 256), 256, 0, s>>>(g, kind, n7, lv[0], lv[1], lv[2],
+                                              d.nu[buf]);
+}
+
+void launch_table_to_lattice(const Geom& g, const double* table, int64_t* nu,
+                             cudaStream_t s) {
+    k_table_to_lattice<<<blocks(g.n_x, 256), 256, 0, s>>>(g, table, nu);
+}
+
+void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s) {
+    k_coarse<<<blocks(g.n_coarse, 128), 128, 0, s>>>(g, d.coarse);
+}
+
+void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s) {
+    k_mmse_plain<<<blocks(g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+}
+
+void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {
+    k_udiff<<<blocks(g.n_y, 256), 256, 0, s>>>(g, d.U, d.Ud);
+}
+
+void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
+                   double* out, cudaStream_t s) {
+    if (n <= 0) return;
+    k_S_list<<<blocks(n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out);
+}
+
+void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s) {
+    const int64_t threads = g.n_x * (int64_t)g.n_refine;
+    const int bs = 256;
+#define UCP_SEARCH_CASE(G)                                                    \
+    case G:                                                                   \
+        k_search_plain<G><<<blocks(threads, bs), bs, 0, s>>>(                 \
+            g, d.phi, d.U, d.Ud, d.nu[buf_in], d.Sf, d.Sc, d.coarse,          \
+            d.nu[buf_in ^ 1], d.idx);                                         \
+        break;
+    switch (g.n_refine) {
+        UCP_SEARCH_CASE(2)
+        UCP_SEARCH_CASE(4)
+        UCP_SEARCH_CASE(8)
+        UCP_SEARCH_CASE(16)
+        UCP_SEARCH_CASE(32)
+        default: break;
+    }
+#undef UCP_SEARCH_CASE
+}
+
+void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
+                    cudaStream_t s) {
+    k_J_plain<<<1, 32, 0, s>>>(g, d.px, d.nu[buf], d.Sf, d.J + slot);
+}
+
+void launch_f_values(const Geom& g, const int64_t* nu, const double*,
+                     double* out, int as_u0, cudaStream_t s) {
+    k_f_values<<<blocks(g.n_x, 256), 256, 0, s>>>(g, nu, out, as_u0);
+}
+
+}  // namespace ucp

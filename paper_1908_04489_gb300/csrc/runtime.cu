@@ -1,0 +1,305 @@
+// runtime.cu -- instance lifecycle and the sweep driver (host side).
+//
+// Sweep order (Algorithm 1's partial-exhaustion phase for u0, then the
+// closed-form u1 update, then J; Section IV-A's Jacobi parallelism):
+//   search(f_pre, U) -> f ; U <- E[x1 | y1] ; S at the coarse list and at f
+//   under the new U ; J.
+#include <string.h>
+
+#include "ucp_runtime.h"
+
+namespace ucp {
+
+// ---- event timers -------------------------------------------------------
+
+int Prof::begin(const char* name, cudaEvent_t* a) {
+    if (!on) return -1;
+    int k = -1;
+    for (size_t s = 0; s < stats.size(); ++s)
+        if (strcmp(stats[s].name, name) == 0) { k = (int)s; break; }
+    if (k < 0) {
+        stats.push_back({name, 0, 0.0});
+        k = (int)stats.size() - 1;
+    }
+    if (pending.size() >= 4096) drain();
+    if (pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        pool.push_back(e);
+    }
+    *a = pool.back();
+    pool.pop_back();
+    cudaEventRecord(*a, stream);
+    return k;
+}
+
+void Prof::end(int stat, cudaEvent_t a) {
+    if (stat < 0) return;
+    cudaEvent_t b;
+    if (pool.empty()) {
+        if (cudaEventCreate(&b) != cudaSuccess) { pool.push_back(a); return; }
+    } else {
+        b = pool.back();
+        pool.pop_back();
+    }
+    cudaEventRecord(b, stream);
+    pending.push_back({stat, a, b});
+}
+
+void Prof::drain() {
+    if (pending.empty()) return;
+    cudaStreamSynchronize(stream);
+    for (auto& p : pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            stats[p.stat].launches += 1;
+            stats[p.stat].ms += ms;
+        }
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    pending.clear();
+}
+
+Prof::~Prof() {
+    for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
+ucp_status prof_enable(Prof* p, cudaStream_t s, bool on) {
+    p->drain();
+    p->stream = s;
+    p->on = on;
+    p->stats.clear();
+    return UCP_OK;
+}
+
+int prof_collect(Prof* p, const char** names, int64_t* launches, double* ms,
+                 int cap) {
+    p->drain();
+    int n = (int)p->stats.size();
+    for (int k = 0; k < n && k < cap; ++k) {
+        if (names) names[k] = p->stats[k].name;
+        if (launches) launches[k] = p->stats[k].launches;
+        if (ms) ms[k] = p->stats[k].ms;
+    }
+    return n;
+}
+
+#define UCP_LAUNCH(in, NAME, CALL)                                  \
+    do {                                                            \
+        cudaEvent_t ucp_ev_a_;                                      \
+        const int ucp_k_ = (in)->prof.begin(NAME, &ucp_ev_a_);      \
+        CALL;                                                       \
+        (in)->prof.end(ucp_k_, ucp_ev_a_);                          \
+    } while (0)
+
+// ---- device memory --------------------------------------------------------
+
+void* Arena::get(size_t n) {
+    n = (n + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (ctx && ctx->alloc) {
+        p = ctx->alloc(n, ctx->user);
+    } else if (cudaMalloc(&p, n) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) { ptrs.push_back(p); bytes += n; }
+    return p;
+}
+
+void Arena::put(void* p) {
+    for (size_t k = 0; k < ptrs.size(); ++k)
+        if (ptrs[k] == p) {
+            if (ctx && ctx->free_fn) ctx->free_fn(p, ctx->user);
+            else cudaFree(p);
+            ptrs.erase(ptrs.begin() + k);
+            return;
+        }
+}
+
+void Arena::release_all() {
+    for (void* p : ptrs) {
+        if (ctx && ctx->free_fn) ctx->free_fn(p, ctx->user);
+        else cudaFree(p);
+    }
+    ptrs.clear();
+    bytes = 0;
+}
+
+// ---- instance -------------------------------------------------------------
+
+static ucp_status check(ucp_inst* in, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        in->poisoned = true;
+        set_error("%s: %s", where, cudaGetErrorString(e));
+        return UCP_E_CUDA;
+    }
+    return UCP_OK;
+}
+
+static ucp_status refresh_costs(ucp_inst* in, int slot) {
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    UCP_LAUNCH(in, "udiff", launch_udiff(g, d, in->stream));
+    UCP_LAUNCH(in, "S_coarse", launch_S_list(g, d, d.coarse, g.n_coarse, d.Sc, in->stream));
+    UCP_LAUNCH(in, "S_f", launch_S_list(g, d, d.nu[in->cur], g.n_x, d.Sf, in->stream));
+    UCP_LAUNCH(in, "J", launch_J_plain(g, d, in->cur, slot, in->stream));
+    return check(in, "refresh");
+}
+
+static ucp_status grow_history(ucp_inst* in, long long need) {
+    if (need <= in->hist_cap) return UCP_OK;
+    long long cap = in->hist_cap;
+    while (cap < need) cap *= 2;
+    double* nh = (double*)in->arena.get(sizeof(double) * (size_t)cap);
+    if (!nh) {
+        set_error("%s%s", "J history: out of device memory", "");
+        return UCP_E_NOMEM;
+    }
+    cudaMemcpyAsync(nh, in->d.J, sizeof(double) * (size_t)(in->sweeps_done + 1),
+                    cudaMemcpyDeviceToDevice, in->stream);
+    if (cudaStreamSynchronize(in->stream) != cudaSuccess) return check(in, "history");
+    in->arena.put(in->d.J);
+    in->d.J = nh;
+    in->hist_cap = cap;
+    in->bytes = in->arena.bytes;
+    return UCP_OK;
+}
+
+static size_t rnd(size_t n) { return (n + 255) & ~(size_t)255; }
+
+size_t inst_bytes(const Geom& g, int) {
+    const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
+    const size_t nc = (size_t)g.n_coarse;
+    return 6 * rnd(8 * nx) + rnd(4 * nx) + 2 * rnd(8 * ny) + rnd(8 * nw) +
+           2 * rnd(8 * nc) + rnd(8 * 64) + rnd(8 * 4096);
+}
+
+ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
+                     const Geom& g, cudaStream_t stream) {
+    in->ctx = ctx;
+    in->params = p;
+    in->params.init_table = nullptr;
+    in->g = g;
+    in->arena.ctx = ctx;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return check(in, "set device");
+    if (stream) {
+        in->stream = stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&in->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return check(in, "stream");
+        in->own_stream = true;
+    }
+    in->prof.stream = in->stream;
+    in->hist_cap = 64;
+    DevState& d = in->d;
+    Arena& A = in->arena;
+    const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
+    d.px = (double*)A.get(8 * nx);
+    d.phi = (double*)A.get(8 * nw);
+    d.U = (double*)A.get(8 * ny);
+    d.Ud = (double*)A.get(8 * ny);
+    d.nu[0] = (int64_t*)A.get(8 * nx);
+    d.nu[1] = (int64_t*)A.get(8 * nx);
+    d.coarse = (int64_t*)A.get(8 * (size_t)g.n_coarse);
+    d.Sf = (double*)A.get(8 * nx);
+    d.Sc = (double*)A.get(8 * (size_t)g.n_coarse);
+    d.idx = (int32_t*)A.get(4 * nx);
+    d.J = (double*)A.get(8 * (size_t)in->hist_cap);
+    d.scratch = (double*)A.get(8 * 4096);
+    d.table = (double*)A.get(8 * nx);
+    if (!d.px || !d.phi || !d.U || !d.Ud || !d.nu[0] || !d.nu[1] || !d.coarse ||
+        !d.Sf || !d.Sc || !d.idx || !d.J || !d.scratch || !d.table) {
+        set_error("%s%s", "ucp_create: out of device memory", "");
+        return UCP_E_NOMEM;
+    }
+    in->bytes = A.bytes;
+    cudaStream_t s = in->stream;
+    UCP_LAUNCH(in, "weights", launch_weights(g, d, s));
+    UCP_LAUNCH(in, "coarse", launch_coarse_list(g, d, s));
+    if (p.init_kind == 2) {
+        cudaMemcpyAsync(d.table, p.init_table, 8 * nx, cudaMemcpyHostToDevice, s);
+        UCP_LAUNCH(in, "init", launch_table_to_lattice(g, d.table, d.nu[0], s));
+        // the caller's host buffer must not be read after we return
+        if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "init copy");
+    } else {
+        UCP_LAUNCH(in, "init", launch_init(g, d, p.init_kind, 0, s));
+    }
+    cudaMemsetAsync(d.idx, 0xff, 4 * nx, s);
+    in->cur = 0;
+    in->sweeps_done = 0;
+    UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, 0, s));
+    return refresh_costs(in, 0);
+}
+
+ucp_status inst_sweep(ucp_inst* in, int n) {
+    if (n == 0) return UCP_OK;
+    ucp_status st = grow_history(in, in->sweeps_done + 1 + n);
+    if (st != UCP_OK) return st;
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    cudaStream_t s = in->stream;
+    for (int k = 0; k < n; ++k) {
+        UCP_LAUNCH(in, "search", launch_search_plain(g, d, in->cur, s));
+        in->cur ^= 1;
+        UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, in->cur, s));
+        in->sweeps_done += 1;
+        st = refresh_costs(in, (int)in->sweeps_done);
+        if (st != UCP_OK) return st;
+    }
+    return UCP_OK;
+}
+
+ucp_status inst_sync(ucp_inst* in) {
+    if (cudaStreamSynchronize(in->stream) != cudaSuccess) return check(in, "sync");
+    return check(in, "sync");
+}
+
+ucp_status inst_read(ucp_inst* in, const void* dev, void* host, size_t bytes) {
+    cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, in->stream);
+    return inst_sync(in);
+}
+
+ucp_status inst_get(ucp_inst* in, double* f, double* u1, int as_u0, int32_t* idx) {
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    cudaStream_t s = in->stream;
+    if (f) {
+        UCP_LAUNCH(in, "f_values", launch_f_values(g, d.nu[in->cur], nullptr, d.table, as_u0, s));
+        cudaMemcpyAsync(f, d.table, 8 * (size_t)g.n_x, cudaMemcpyDeviceToHost, s);
+    }
+    if (u1) cudaMemcpyAsync(u1, d.U, 8 * (size_t)g.n_y, cudaMemcpyDeviceToHost, s);
+    if (idx) cudaMemcpyAsync(idx, d.idx, 4 * (size_t)g.n_x, cudaMemcpyDeviceToHost, s);
+    return inst_sync(in);
+}
+
+ucp_status inst_set(ucp_inst* in, const double* f, const double* u1) {
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    cudaStream_t s = in->stream;
+    cudaMemcpyAsync(d.table, f, 8 * (size_t)g.n_x, cudaMemcpyHostToDevice, s);
+    UCP_LAUNCH(in, "init", launch_table_to_lattice(g, d.table, d.nu[in->cur], s));
+    if (u1) {
+        cudaMemcpyAsync(d.U, u1, 8 * (size_t)g.n_y, cudaMemcpyHostToDevice, s);
+    } else {
+        UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, in->cur, s));
+    }
+    cudaMemsetAsync(d.idx, 0xff, 4 * (size_t)g.n_x, s);
+    in->sweeps_done = 0;
+    ucp_status st = refresh_costs(in, 0);
+    if (st != UCP_OK) return st;
+    return inst_sync(in);  // host buffers are not read after return
+}
+
+void inst_release(ucp_inst* in) {
+    if (in->stream) cudaStreamSynchronize(in->stream);
+    in->prof.drain();
+    in->arena.release_all();
+    if (in->own_stream && in->stream) cudaStreamDestroy(in->stream);
+    in->stream = nullptr;
+}
+
+}  // namespace ucp

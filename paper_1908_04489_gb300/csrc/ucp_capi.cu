@@ -1,0 +1,291 @@
+// ucp_capi.cu -- the C ABI of libucp.so (declared in include/ucp.h):
+// argument validation, device memory, the per-instance sweep driver and the
+// per-kernel CUDA-event timers.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ucp_internal.cuh"
+#include "ucp_runtime.h"
+
+namespace ucp {
+
+static thread_local char g_last_error[512] = "";
+
+void set_error(const char* fmt, const char* a, const char* b) {
+    snprintf(g_last_error, sizeof(g_last_error), fmt, a ? a : "", b ? b : "");
+}
+
+static int half_steps(double half, double delta, int64_t* out) {
+    const double r = half / delta;
+    const double n = floor(r + 0.5);
+    if (!(n >= 0.0) || fabs(r - n) > 1e-9 * (n > 1.0 ? n : 1.0)) return -1;
+    *out = (int64_t)n;
+    return 0;
+}
+
+const char* make_geom(const ucp_params& p, Geom* g) {
+    memset(g, 0, sizeof(*g));
+    if (!(p.k > 0.0) || !isfinite(p.k)) return "k must be a positive number";
+    if (!(p.sigma > 0.0) || !isfinite(p.sigma)) return "sigma must be positive";
+    if (!(p.delta > 0.0) || !isfinite(p.delta)) return "delta must be positive";
+    if (half_steps(p.x_half, p.delta, &g->hx) || g->hx < 1)
+        return "x_half must be a positive multiple of delta";
+    if (half_steps(p.w_half, p.delta, &g->hw) || g->hw < 1)
+        return "w_half must be a positive multiple of delta";
+    if (half_steps(p.y_half, p.delta, &g->hy) || g->hy < 1)
+        return "y_half must be a positive multiple of delta";
+    if (half_steps(p.cand_half, p.delta, &g->hr))
+        return "cand_half must be a multiple of delta";
+    if (p.n_coarse < 2 || p.n_coarse > 4096) return "n_coarse must be in [2, 4096]";
+    if (p.n_refine != 2 && p.n_refine != 4 && p.n_refine != 8 &&
+        p.n_refine != 16 && p.n_refine != 32)
+        return "n_refine must be 2, 4, 8, 16 or 32";
+    if (p.n_levels < 0 || p.n_levels > 8) return "n_levels must be in [0, 8]";
+    if (p.n_nbr < 0 || p.n_nbr > 8) return "n_nbr must be in [0, 8]";
+    if (p.flags != 0) return "flags must be 0";
+    if (p.precision != 0 && p.precision != 1) return "precision must be 0 or 1";
+    if (p.init_kind < 0 || p.init_kind > 2) return "init_kind must be 0, 1 or 2";
+    int bits = 0;
+    while ((1 << bits) < p.n_refine / 2) ++bits;
+    g->bits = bits;
+    g->shift = bits * p.n_levels;
+    if (g->shift > 30) return "n_levels * log2(n_refine/2) must be <= 30";
+    g->one = (int64_t)1 << g->shift;
+    g->n_x = 2 * g->hx + 1;
+    g->n_w = 2 * g->hw + 1;
+    g->n_y = 2 * g->hy + 1;
+    if (g->n_x > (1 << 26) || g->n_w > (1 << 24) || g->n_y > (1 << 26))
+        return "grid too large";
+    const int64_t nc1 = p.n_coarse - 1;
+    int64_t c = (g->hr + nc1 - 1) / nc1;
+    if (c < 1) c = 1;
+    g->q = 2 * c;
+    // lattice indices of every reachable value must stay far inside int64
+    const double reach = (double)(g->hr + g->hx + g->hy + 2 * g->q) * (double)g->one;
+    if (reach > 4.0e15) return "grid extent too large for the candidate lattice";
+    g->k = p.k;
+    g->kk = p.k * p.k;
+    g->sigma = p.sigma;
+    g->delta = p.delta;
+    g->two_s2 = 2.0 * p.sigma * p.sigma;
+    g->n_coarse = p.n_coarse;
+    g->n_refine = p.n_refine;
+    g->n_levels = p.n_levels;
+    g->n_nbr = p.n_nbr;
+    g->n_cand = 1 + 2 * p.n_nbr + p.n_coarse + p.n_levels * p.n_refine;
+    if (p.init_kind == 1) {
+        int64_t n7;
+        if (half_steps(7.0, p.delta, &n7) || n7 < 1)
+            return "staircase init needs 7 to be a multiple of delta";
+    }
+    if (p.init_kind == 2) {
+        if (!p.init_table) return "init_kind 2 needs init_table";
+        if (p.init_len != (uint64_t)g->n_x) return "init_len must equal n_x";
+    }
+    return nullptr;
+}
+
+}  // namespace ucp
+
+using namespace ucp;
+
+// ---- status / version ---------------------------------------------------
+
+extern "C" const char* ucp_status_str(ucp_status s) {
+    switch (s) {
+        case UCP_OK: return "ok";
+        case UCP_PENDING: return "pending";
+        case UCP_E_ARG: return "invalid argument";
+        case UCP_E_NOMEM: return "out of device memory";
+        case UCP_E_BUDGET: return "request exceeds the server budget";
+        case UCP_E_CUDA: return "CUDA error";
+        case UCP_E_TIMEOUT: return "device wait timed out";
+        case UCP_E_STATE: return "object poisoned, destroyed or busy";
+        case UCP_E_NOTFOUND: return "unknown ticket";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* ucp_last_error(void) { return g_last_error; }
+
+extern "C" const char* ucp_version(void) { return "ucp 0.1 sm_103a"; }
+
+extern "C" ucp_status ucp_plan(const ucp_params* params, uint64_t* n_x,
+                               uint64_t* n_w, uint64_t* n_y, uint64_t* n_cand,
+                               uint64_t* device_bytes) {
+    if (!params) {
+        set_error("ucp_plan: %s%s", "NULL params", "");
+        return UCP_E_ARG;
+    }
+    Geom g;
+    if (const char* why = make_geom(*params, &g)) {
+        set_error("ucp_plan: %s%s", why, "");
+        return UCP_E_ARG;
+    }
+    if (n_x) *n_x = (uint64_t)g.n_x;
+    if (n_w) *n_w = (uint64_t)g.n_w;
+    if (n_y) *n_y = (uint64_t)g.n_y;
+    if (n_cand) *n_cand = (uint64_t)g.n_cand;
+    if (device_bytes) *device_bytes = (uint64_t)inst_bytes(g, params->precision);
+    return UCP_OK;
+}
+
+// ---- context ----------------------------------------------------------
+
+extern "C" ucp_status ucp_ctx_create(int32_t device, ucp_alloc_fn alloc,
+                                     ucp_free_fn free_fn, void* user,
+                                     ucp_ctx** out) {
+    if (!out || ((alloc == nullptr) != (free_fn == nullptr))) {
+        set_error("ucp_ctx_create: %s%s", "out must be non-NULL and alloc/free ",
+                  "given together");
+        return UCP_E_ARG;
+    }
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device < 0 || device >= n) {
+        set_error("ucp_ctx_create: no such CUDA device (%s)%s",
+                  cudaGetErrorString(e), "");
+        return e != cudaSuccess ? UCP_E_CUDA : UCP_E_ARG;
+    }
+    ucp_ctx* c = new ucp_ctx();
+    c->device = device;
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = user;
+    *out = c;
+    return UCP_OK;
+}
+
+extern "C" ucp_status ucp_ctx_destroy(ucp_ctx* ctx) {
+    if (!ctx) return UCP_E_ARG;
+    delete ctx;
+    return UCP_OK;
+}
+
+// ---- instance ---------------------------------------------------------
+
+extern "C" ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params,
+                                 void* stream, ucp_inst** out) {
+    if (!params || !out) {
+        set_error("ucp_create: %s%s", "NULL argument", "");
+        return UCP_E_ARG;
+    }
+    *out = nullptr;
+    Geom g;
+    if (const char* why = make_geom(*params, &g)) {
+        set_error("ucp_create: %s%s", why, "");
+        return UCP_E_ARG;
+    }
+    if (!ctx) {
+        set_error("ucp_create: %s%s", "NULL context", "");
+        return UCP_E_ARG;
+    }
+    ucp_inst* in = new ucp_inst();
+    ucp_status st = inst_init(in, ctx, *params, g, (cudaStream_t)stream);
+    if (st != UCP_OK) {
+        inst_release(in);
+        delete in;
+        return st;
+    }
+    *out = in;
+    return UCP_OK;
+}
+
+extern "C" ucp_status ucp_sizes(const ucp_inst* in, uint64_t* n_x, uint64_t* n_w,
+                                uint64_t* n_y, uint64_t* n_cand,
+                                uint64_t* device_bytes) {
+    if (!in) return UCP_E_ARG;
+    if (n_x) *n_x = (uint64_t)in->g.n_x;
+    if (n_w) *n_w = (uint64_t)in->g.n_w;
+    if (n_y) *n_y = (uint64_t)in->g.n_y;
+    if (n_cand) *n_cand = (uint64_t)in->g.n_cand;
+    if (device_bytes) *device_bytes = (uint64_t)in->bytes;
+    return UCP_OK;
+}
+
+extern "C" ucp_status ucp_sweep(ucp_inst* in, int32_t n_sweeps) {
+    if (!in || n_sweeps < 0) {
+        set_error("ucp_sweep: %s%s", "NULL instance or negative count", "");
+        return UCP_E_ARG;
+    }
+    if (in->poisoned) return UCP_E_STATE;
+    return inst_sweep(in, n_sweeps);
+}
+
+extern "C" ucp_status ucp_eval_J(ucp_inst* in, double* J_out) {
+    if (!in || !J_out) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    double J = 0.0;
+    ucp_status st = inst_read(in, in->d.J + in->sweeps_done, &J, sizeof(double));
+    if (st == UCP_OK) *J_out = J;
+    return st;
+}
+
+extern "C" ucp_status ucp_J_history(ucp_inst* in, double* out, uint64_t n,
+                                    uint64_t* n_written) {
+    if (!in || (!out && n)) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    uint64_t m = (uint64_t)in->sweeps_done + 1;
+    if (n < m) m = n;
+    ucp_status st = m ? inst_read(in, in->d.J, out, m * sizeof(double)) : inst_sync(in);
+    if (st == UCP_OK && n_written) *n_written = m;
+    return st;
+}
+
+extern "C" ucp_status ucp_get_controllers(ucp_inst* in, double* f, uint64_t n_x,
+                                          double* u1, uint64_t n_y,
+                                          int32_t as_paper_u0, int32_t* idx) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    if ((f || idx) && n_x != (uint64_t)in->g.n_x) {
+        set_error("ucp_get_controllers: %s%s", "n_x does not match", "");
+        return UCP_E_ARG;
+    }
+    if (u1 && n_y != (uint64_t)in->g.n_y) {
+        set_error("ucp_get_controllers: %s%s", "n_y does not match", "");
+        return UCP_E_ARG;
+    }
+    return inst_get(in, f, u1, as_paper_u0, idx);
+}
+
+extern "C" ucp_status ucp_set_controllers(ucp_inst* in, const double* f,
+                                          uint64_t n_x, const double* u1,
+                                          uint64_t n_y) {
+    if (!in || !f || n_x != (uint64_t)in->g.n_x ||
+        (u1 && n_y != (uint64_t)in->g.n_y)) {
+        set_error("ucp_set_controllers: %s%s", "bad buffer or size", "");
+        return UCP_E_ARG;
+    }
+    if (in->poisoned) return UCP_E_STATE;
+    for (uint64_t i = 0; i < n_x; ++i)
+        if (!(fabs(f[i] / in->g.delta) * (double)in->g.one < 4.0e15)) {
+            set_error("ucp_set_controllers: %s%s", "f value out of range", "");
+            return UCP_E_ARG;
+        }
+    return inst_set(in, f, u1);
+}
+
+extern "C" ucp_status ucp_destroy(ucp_inst* in) {
+    if (!in) return UCP_E_ARG;
+    cudaStreamSynchronize(in->stream);
+    inst_release(in);
+    delete in;
+    return UCP_OK;
+}
+
+extern "C" ucp_status ucp_profile(ucp_inst* in, int32_t enable) {
+    if (!in) return UCP_E_ARG;
+    return prof_enable(&in->prof, in->stream, enable != 0);
+}
+
+extern "C" int32_t ucp_kernel_times(ucp_inst* in, const char** names,
+                                    int64_t* launches, double* total_ms,
+                                    int32_t cap) {
+    if (!in) return -1;
+    return prof_collect(&in->prof, names, launches, total_ms, cap);
+}

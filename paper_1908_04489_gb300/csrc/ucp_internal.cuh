@@ -1,0 +1,69 @@
+// ucp_internal.cuh -- shared declarations of the CUDA library (not part of
+// the public ABI).  Geometry of one Witsenhausen instance (Section V-A) on
+// the grids of Section III-D, and the launch wrappers of every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ucp.h"
+
+namespace ucp {
+
+// Integer geometry of one instance.  Controller values are carried as int64
+// lattice indices nu with value nu * delta * 2^-shift; the position of
+// u + w_l on the y grid is then cell(nu) - hw + hy + l + frac(nu), exact.
+struct Geom {
+    double k, kk, sigma, delta, two_s2;
+    int64_t hx, hw, hy, hr;     // half widths in units of delta
+    int64_t n_x, n_w, n_y;
+    int32_t shift;              // L * bits
+    int32_t bits;               // log2(n_refine / 2)
+    int64_t one;                // 2^shift
+    int64_t q;                  // coarse spacing in units of delta (even)
+    int32_t n_coarse, n_refine, n_levels, n_nbr;
+    int32_t n_cand;             // 1 + 2 n_nbr + n_coarse + L n_refine
+};
+
+// Fills g from params; returns nullptr or a static reason string.
+const char* make_geom(const ucp_params& p, Geom* g);
+
+__host__ __device__ inline int64_t floor_div(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b) != 0 && ((a < 0) != (b < 0))) q -= 1;
+    return q;
+}
+
+// Device buffers of one instance (all owned by the instance).
+struct DevState {
+    double* px;       // [n_x] normalised prior weights p_i
+    double* phi;      // [n_w] normalised quadrature weights phi_l
+    double* U;        // [n_y] u1 table
+    double* Ud;       // [n_y] U_{j+1} - U_j, 0 at the last entry
+    int64_t* nu[2];   // [n_x] controller f, double buffered (Jacobi)
+    int64_t* coarse;  // [n_coarse] coarse candidates (lattice indices)
+    double* Sf;       // [n_x] S(f_i) under the current U
+    double* Sc;       // [n_coarse] S at the coarse candidates
+    int32_t* idx;     // [n_x] winner list position of the last sweep
+    double* J;        // [1 + max_hist] J history
+    double* scratch;  // reduction partials
+    double* table;    // [n_x] staging for table inits / set_controllers
+};
+
+// ---- plain FP64 path (kernels_plain.cu) --------------------------------
+void launch_weights(const Geom& g, DevState& d, cudaStream_t s);
+void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s);
+void launch_table_to_lattice(const Geom& g, const double* table, int64_t* nu,
+                             cudaStream_t s);
+void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s);
+void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s);
+void launch_udiff(const Geom& g, DevState& d, cudaStream_t s);
+void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
+                   double* out, cudaStream_t s);
+void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s);
+void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
+                    cudaStream_t s);
+void launch_f_values(const Geom& g, const int64_t* nu, const double* x_or_null,
+                     double* out, int as_u0, cudaStream_t s);
+
+}  // namespace ucp

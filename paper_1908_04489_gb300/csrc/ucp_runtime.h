@@ -1,0 +1,89 @@
+// ucp_runtime.h -- host-side runtime objects behind the C ABI: context,
+// instance (device state + sweep driver), per-kernel event timers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "ucp_internal.cuh"
+
+struct ucp_ctx {
+    int device = 0;
+    ucp_alloc_fn alloc = nullptr;
+    ucp_free_fn free_fn = nullptr;
+    void* user = nullptr;
+};
+
+namespace ucp {
+
+void set_error(const char* fmt, const char* a, const char* b);
+
+// CUDA-event timers around every kernel launch of one stream.
+struct Prof {
+    struct Stat {
+        const char* name;
+        long long launches;
+        double ms;
+    };
+    struct Pending {
+        int stat;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    cudaStream_t stream = nullptr;
+    std::vector<Stat> stats;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    int begin(const char* name, cudaEvent_t* a);  // -1 when off
+    void end(int stat, cudaEvent_t a);
+    void drain();
+    ~Prof();
+};
+
+ucp_status prof_enable(Prof* p, cudaStream_t s, bool on);
+int prof_collect(Prof* p, const char** names, int64_t* launches, double* ms,
+                 int cap);
+
+// Owner of device allocations made through a context.
+struct Arena {
+    ucp_ctx* ctx = nullptr;
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    void* get(size_t n);   // nullptr on failure
+    void put(void* p);
+    void release_all();
+};
+
+}  // namespace ucp
+
+struct ucp_inst {
+    ucp_ctx* ctx = nullptr;
+    ucp_params params{};
+    ucp::Geom g{};
+    ucp::DevState d{};
+    ucp::Arena arena;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool poisoned = false;
+    int cur = 0;                 // which nu buffer holds f
+    long long sweeps_done = 0;   // J history slots used: sweeps_done + 1
+    long long hist_cap = 0;
+    size_t bytes = 0;
+    ucp::Prof prof;
+};
+
+namespace ucp {
+
+// Device bytes one instance allocates (matches inst_init).
+size_t inst_bytes(const Geom& g, int precision);
+ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
+                     const Geom& g, cudaStream_t stream);
+ucp_status inst_sweep(ucp_inst* in, int n);
+ucp_status inst_sync(ucp_inst* in);
+ucp_status inst_read(ucp_inst* in, const void* dev, void* host, size_t bytes);
+ucp_status inst_get(ucp_inst* in, double* f, double* u1, int as_u0, int32_t* idx);
+ucp_status inst_set(ucp_inst* in, const double* f, const double* u1);
+void inst_release(ucp_inst* in);
+
+}  // namespace ucp

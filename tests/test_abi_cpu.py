@@ -1,0 +1,81 @@
+"""The C-ABI library loads and exports every symbol include/ucp.h declares;
+host-side validation works without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_04489_gb300 import binding, build
+    build.build()
+    return binding.load()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"UCP_API\s+[\w\s\*]+?\b(ucp_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "ucp_create" in names and "ucp_sweep" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_version_and_status_strings(lib):
+    assert b"sm_103a" in lib.ucp_version()
+    assert lib.ucp_status_str(0) == b"ok"
+    assert lib.ucp_status_str(-7) == b"unknown ticket"
+
+
+def test_plan_sizes_match_the_configs(lib):
+    from paper_1908_04489_gb300 import binding, workloads
+    s = binding.plan(workloads.c1())
+    assert (s["n_x"], s["n_w"], s["n_y"], s["n_cand"]) == (1001, 241, 1401, 133)
+    s = binding.plan(workloads.c2())
+    assert (s["n_x"], s["n_w"], s["n_y"]) == (10001, 2401, 14001)
+    s = binding.plan(workloads.c5())
+    assert (s["n_x"], s["n_w"], s["n_y"], s["n_cand"]) == (100001, 14001, 120001,
+                                                           1 + 4 + 64 + 96)
+    assert 0 < s["device_bytes"] < 64 << 20
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("k", 0.0, "k must"), ("sigma", -1.0, "sigma"), ("delta", 0.0, "delta"),
+    ("x_half", 25.02, "x_half"), ("w_half", 0.0, "w_half"),
+    ("n_refine", 12, "n_refine"), ("n_levels", 9, "n_levels"),
+    ("n_coarse", 1, "n_coarse"), ("n_nbr", -1, "n_nbr"),
+    ("precision", 2, "precision"), ("init_kind", 5, "init_kind"),
+    ("flags", 1, "flags"),
+])
+def test_plan_rejects_invalid_fields(lib, field, value, msg):
+    from paper_1908_04489_gb300 import binding, workloads
+    p = workloads.c1()
+    p[field] = value
+    with pytest.raises(binding.UcpError) as e:
+        binding.plan(p)
+    assert e.value.status == -1 and msg in str(e.value)
+
+
+def test_create_validates_before_touching_the_device(lib):
+    from paper_1908_04489_gb300 import binding, workloads
+    p = binding.Params.from_dict(dict(workloads.c1(), k=-1.0))
+    h = ctypes.c_void_p()
+    assert lib.ucp_create(None, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert b"k must" in lib.ucp_last_error()
+    p = binding.Params.from_dict(workloads.c1())
+    assert lib.ucp_create(None, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert b"context" in lib.ucp_last_error()
+    p = binding.Params.from_dict(dict(workloads.c1(), init_kind=2))
+    assert lib.ucp_create(None, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert b"init_table" in lib.ucp_last_error()
