@@ -80,6 +80,8 @@ def kernel_work(p, sizes):
     return {
         "search": nx * L * R * nw * 6.0,
         "mmse": nx * ny * 8.0,
+        "mmse_main": nx * ny * 8.0,
+        "tables": sizes.get("n_pos", 0) * nw * 6.0,
         "S_f": nx * nw * 6.0,
         "S_coarse": p["n_coarse"] * nw * 6.0,
         "J": nx * 5.0,
@@ -208,7 +210,8 @@ def run_gpu(args):
 
     p, desc = workload(args.workload, args.precision)
     sizes = binding.plan(p)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     def solve(profile=False):
@@ -254,6 +257,7 @@ def run_gpu(args):
             a[0] += n
             a[1] += ms
         Js.append(inst.eval_J())
+        recosts = inst.tie_recosts()
         last = inst
     torch.cuda.synchronize()
     if world > 1:
@@ -329,6 +333,7 @@ def run_gpu(args):
         "gpu_launches": int(sum(v[0] for v in kern.values())),
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kern.items()},
         "roofline": roofline, "e2e": e2e, "clocks": clk, "parity": parity,
+        "tie_recosts_per_solve": recosts,
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu

@@ -36,7 +36,7 @@
  *   - Objects are not thread-safe, except ucp_submit / ucp_poll, which may be
  *     called from any thread.
  *   - Device work is issued on the stream given at creation (cudaStream_t
- *     passed as void*; NULL makes the library create its own stream).
+ *     passed as void*; NULL is the CUDA default stream).
  */
 #ifndef UCP_H
 #define UCP_H
@@ -155,6 +155,11 @@ UCP_API ucp_status ucp_get_controllers(ucp_inst* inst, double* f, uint64_t n_x,
 UCP_API ucp_status ucp_set_controllers(ucp_inst* inst, const double* f, uint64_t n_x,
                                const double* u1, uint64_t n_y);
 UCP_API ucp_status ucp_destroy(ucp_inst* inst);
+
+/* Fast path: number of candidate costs re-computed by the serial FP64
+ * quadrature because screened table costs left a near-tie open (since
+ * creation; 0 on the plain path).  Synchronises. */
+UCP_API ucp_status ucp_tie_recosts(ucp_inst* inst, int64_t* out);
 
 /* Per-kernel CUDA-event timing on the instance stream (off by default).
  * ucp_kernel_times fills up to cap entries: name (static), launches and

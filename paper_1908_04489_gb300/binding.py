@@ -101,6 +101,7 @@ def load():
                                    ctypes.POINTER(ctypes.c_int64), _dp,
                                    ctypes.c_int32]
     L.ucp_kernel_times.restype = ctypes.c_int32
+    L.ucp_tie_recosts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     _lib = L
     return L
 
@@ -242,6 +243,11 @@ class Instance:
         ms = (ctypes.c_double * cap)()
         n = L.ucp_kernel_times(self.h, names, launches, ms, cap)
         return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+    def tie_recosts(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().ucp_tie_recosts(self.h, ctypes.byref(v)), "ucp_tie_recosts")
+        return v.value
 
     def close(self):
         if getattr(self, "h", None):

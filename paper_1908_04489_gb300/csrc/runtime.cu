@@ -6,6 +6,7 @@
 //   under the new U ; J.
 #include <string.h>
 
+#include "ucp_fast.cuh"
 #include "ucp_runtime.h"
 
 namespace ucp {
@@ -171,11 +172,70 @@ static ucp_status grow_history(ucp_inst* in, long long need) {
 
 static size_t rnd(size_t n) { return (n + 255) & ~(size_t)255; }
 
-size_t inst_bytes(const Geom& g, int) {
+size_t inst_bytes(const Geom& g, int precision) {
     const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
     const size_t nc = (size_t)g.n_coarse;
-    return 6 * rnd(8 * nx) + rnd(4 * nx) + 2 * rnd(8 * ny) + rnd(8 * nw) +
-           2 * rnd(8 * nc) + rnd(8 * 64) + rnd(8 * 4096);
+    size_t b = 6 * rnd(8 * nx) + rnd(4 * nx) + 2 * rnd(8 * ny) + rnd(8 * nw) +
+               2 * rnd(8 * nc) + rnd(8 * 64) + rnd(8 * 4096);
+    if (precision == 1) {
+        FastPlan fp;
+        fast_plan(g, &fp);
+        b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
+             rnd(8 * nw) + 3 * rnd(8 * nx) + rnd(8 * ny) + rnd(4 * ny) +
+             2 * rnd(8 * (size_t)fp.n_chunks * ny) + rnd(8 * (size_t)fp.J_blocks) +
+             rnd(8) + rnd(4);
+    }
+    return b;
+}
+
+static ucp_status fast_alloc(ucp_inst* in) {
+    const Geom& g = in->g;
+    FastView& f = in->fv;
+    DevState& d = in->d;
+    Arena& A = in->arena;
+    fast_plan(g, &f);
+    f.phi = d.phi;
+    f.U = d.U;
+    f.Ud = d.Ud;
+    f.coarse = d.coarse;
+    const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
+    f.P = (double*)A.get(8 * (size_t)f.n_pos);
+    f.Q = (double*)A.get(8 * (size_t)f.n_pos);
+    f.R = (double*)A.get(8 * (size_t)f.n_pos);
+    f.E = (double*)A.get(8 * (size_t)f.n_e);
+    f.E2 = (double*)A.get(8 * (size_t)f.n_e);
+    f.EE = (double*)A.get(8 * (size_t)f.n_e);
+    f.a = (double*)A.get(8 * nw);
+    f.prior = (double*)A.get(8 * nx);
+    f.src_f = (double*)A.get(8 * nx);
+    f.src_F = (double*)A.get(8 * nx);
+    f.Yfac = (double*)A.get(8 * ny);
+    f.mshift = (float*)A.get(4 * ny);
+    f.partN = (double*)A.get(8 * (size_t)f.n_chunks * ny);
+    f.partD = (double*)A.get(8 * (size_t)f.n_chunks * ny);
+    f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
+    f.W2_dev = (double*)A.get(8);
+    f.n_exact = (int32_t*)A.get(4);
+    if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.prior ||
+        !f.src_f || !f.src_F || !f.Yfac || !f.mshift || !f.partN || !f.partD ||
+        !f.Jpart || !f.W2_dev || !f.n_exact) {
+        set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
+        return UCP_E_NOMEM;
+    }
+    // bounds on |table cost - serial FP64 cost| (see kernels_fast.cu)
+    f.beta_rel = (double)(g.n_w + 48) * 0x1p-52;
+    const double A_ = 8.0 * ((double)(g.hw + g.hy + g.hr + 2 * g.q) * g.delta) + 16.0;
+    f.beta_abs = A_ * 0x1p-50;
+    f.cstep = exp(-g.delta * g.delta);
+    return UCP_OK;
+}
+
+static ucp_status fast_refresh(ucp_inst* in, int slot) {
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    launch_tables(g, in->fv, d.U, d.Ud, in->stream, &in->prof);
+    launch_J_fast(g, in->fv, d.px, d.nu[in->cur], d.J + slot, in->stream, &in->prof);
+    return check(in, "refresh");
 }
 
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
@@ -186,13 +246,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     in->g = g;
     in->arena.ctx = ctx;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return check(in, "set device");
-    if (stream) {
-        in->stream = stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&in->stream, cudaStreamNonBlocking) != cudaSuccess)
-            return check(in, "stream");
-        in->own_stream = true;
-    }
+    in->stream = stream;  // NULL: the default stream
     in->prof.stream = in->stream;
     in->hist_cap = 64;
     DevState& d = in->d;
@@ -216,10 +270,21 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
         set_error("%s%s", "ucp_create: out of device memory", "");
         return UCP_E_NOMEM;
     }
+    in->fast = p.precision == 1;
+    if (in->fast) {
+        ucp_status st = fast_alloc(in);
+        if (st != UCP_OK) return st;
+    }
     in->bytes = A.bytes;
     cudaStream_t s = in->stream;
     UCP_LAUNCH(in, "weights", launch_weights(g, d, s));
     UCP_LAUNCH(in, "coarse", launch_coarse_list(g, d, s));
+    if (in->fast) {
+        UCP_LAUNCH(in, "fast_setup", launch_fast_setup(g, in->fv, s));
+        cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
+        cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
+    }
     if (p.init_kind == 2) {
         cudaMemcpyAsync(d.table, p.init_table, 8 * nx, cudaMemcpyHostToDevice, s);
         UCP_LAUNCH(in, "init", launch_table_to_lattice(g, d.table, d.nu[0], s));
@@ -231,6 +296,10 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     cudaMemsetAsync(d.idx, 0xff, 4 * nx, s);
     in->cur = 0;
     in->sweeps_done = 0;
+    if (in->fast) {
+        launch_mmse_fast(g, in->fv, d.nu[0], d.U, s, &in->prof);
+        return fast_refresh(in, 0);
+    }
     UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, 0, s));
     return refresh_costs(in, 0);
 }
@@ -242,6 +311,18 @@ ucp_status inst_sweep(ucp_inst* in, int n) {
     const Geom& g = in->g;
     DevState& d = in->d;
     cudaStream_t s = in->stream;
+    if (in->fast) {
+        for (int k = 0; k < n; ++k) {
+            UCP_LAUNCH(in, "search", launch_search_fast(g, in->fv, d.nu[in->cur],
+                                                        d.nu[in->cur ^ 1], d.idx, s));
+            in->cur ^= 1;
+            launch_mmse_fast(g, in->fv, d.nu[in->cur], d.U, s, &in->prof);
+            in->sweeps_done += 1;
+            st = fast_refresh(in, (int)in->sweeps_done);
+            if (st != UCP_OK) return st;
+        }
+        return UCP_OK;
+    }
     for (int k = 0; k < n; ++k) {
         UCP_LAUNCH(in, "search", launch_search_plain(g, d, in->cur, s));
         in->cur ^= 1;
@@ -284,12 +365,14 @@ ucp_status inst_set(ucp_inst* in, const double* f, const double* u1) {
     UCP_LAUNCH(in, "init", launch_table_to_lattice(g, d.table, d.nu[in->cur], s));
     if (u1) {
         cudaMemcpyAsync(d.U, u1, 8 * (size_t)g.n_y, cudaMemcpyHostToDevice, s);
+    } else if (in->fast) {
+        launch_mmse_fast(g, in->fv, d.nu[in->cur], d.U, s, &in->prof);
     } else {
         UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, in->cur, s));
     }
     cudaMemsetAsync(d.idx, 0xff, 4 * (size_t)g.n_x, s);
     in->sweeps_done = 0;
-    ucp_status st = refresh_costs(in, 0);
+    ucp_status st = in->fast ? fast_refresh(in, 0) : refresh_costs(in, 0);
     if (st != UCP_OK) return st;
     return inst_sync(in);  // host buffers are not read after return
 }

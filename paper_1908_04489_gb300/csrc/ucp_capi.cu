@@ -49,6 +49,8 @@ const char* make_geom(const ucp_params& p, Geom* g) {
     if (p.n_nbr < 0 || p.n_nbr > 8) return "n_nbr must be in [0, 8]";
     if (p.flags != 0) return "flags must be 0";
     if (p.precision != 0 && p.precision != 1) return "precision must be 0 or 1";
+    if (p.delta * (p.x_half + p.y_half + p.cand_half) > 200.0)
+        return "delta * (x_half + y_half + cand_half) must be <= 200";
     if (p.init_kind < 0 || p.init_kind > 2) return "init_kind must be 0, 1 or 2";
     int bits = 0;
     while ((1 << bits) < p.n_refine / 2) ++bits;
@@ -288,4 +290,14 @@ extern "C" int32_t ucp_kernel_times(ucp_inst* in, const char** names,
                                     int32_t cap) {
     if (!in) return -1;
     return prof_collect(&in->prof, names, launches, total_ms, cap);
+}
+
+extern "C" ucp_status ucp_tie_recosts(ucp_inst* in, int64_t* out) {
+    if (!in || !out) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    if (!in->fast) { *out = 0; return UCP_OK; }
+    int32_t v = 0;
+    ucp_status st = inst_read(in, in->fv.n_exact, &v, sizeof(v));
+    if (st == UCP_OK) *out = v;
+    return st;
 }

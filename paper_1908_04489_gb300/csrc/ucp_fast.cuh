@@ -1,0 +1,20 @@
+// ucp_fast.cuh -- state and launches of the fast path (kernels_fast.cu).
+#pragma once
+
+#include "ucp_internal.cuh"
+#include "ucp_runtime.h"
+
+namespace ucp {
+
+void fast_plan(const Geom& g, FastPlan* fp);
+void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s);
+void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
+                      double* U, cudaStream_t s, Prof* prof);
+void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
+                   cudaStream_t s, Prof* prof);
+void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
+                        int64_t* nu_out, int32_t* idx, cudaStream_t s);
+void launch_J_fast(const Geom& g, const FastView& f, const double* px,
+                   const int64_t* nu, double* out, cudaStream_t s, Prof* prof);
+
+}  // namespace ucp

@@ -50,6 +50,47 @@ struct DevState {
     double* table;    // [n_x] staging for table inits / set_controllers
 };
 
+// Sizes of the fast path's buffers for one instance.
+struct FastPlan {
+    int64_t c_lo;      // lowest lattice cell covered by the tables
+    int64_t n_pos;     // table positions (cells c_lo .. c_lo + n_pos - 1)
+    int64_t jlo;       // y-index of table E-index 0
+    int64_t n_e;       // length of E, E^2, E E_+ (n_pos + n_w + 1)
+    int64_t chunk;     // sources per block column of the u1 kernel
+    int n_chunks;      // block columns of the u1 kernel
+    int64_t j_blocks;  // block rows of the u1 kernel
+    int64_t J_blocks;  // blocks of the J reduction
+};
+
+// Everything the fast kernels read or write (device pointers + scalars).
+struct FastView : FastPlan {
+    const double* phi;   // [n_w] quadrature weights
+    const double* U;     // [n_y] u1 table
+    const double* Ud;    // [n_y] U_{j+1} - U_j
+    const int64_t* coarse;
+    double* P;           // [n_pos] correlation tables
+    double* Q;
+    double* R;
+    double* E;           // [n_e] U^(y) - y on the extended grid
+    double* E2;          // [n_e] E^2
+    double* EE;          // [n_e] E_m E_{m+1}
+    double* a;           // [n_w] phi_l w_l
+    double* prior;       // [n_x] x_i^2 / (2 sigma^2)
+    double* Yfac;        // [n_y] exp(-delta y_j - delta^2 / 2)
+    double* src_f;       // [n_x] f_i of the current sweep
+    double* src_F;       // [n_x] exp(delta f_i)
+    float* mshift;       // [n_y] approximate min_i of the u1 exponents
+    double* partN;       // [n_chunks * n_y] numerator partials
+    double* partD;       // [n_chunks * n_y] denominator partials
+    double* Jpart;       // [J_blocks]
+    double* W2_dev;      // sum phi_l w_l^2 (device copy)
+    int32_t* n_exact;    // count of serial re-costings (near ties)
+    double W2;           // host copy of *W2_dev
+    double beta_rel;     // table-value error bound: beta_rel * M + ...
+    double beta_abs;     //   ... + beta_abs * (2 sqrt(M) + 1)
+    double cstep;        // exp(-delta^2)
+};
+
 // ---- plain FP64 path (kernels_plain.cu) --------------------------------
 void launch_weights(const Geom& g, DevState& d, cudaStream_t s);
 void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s);

@@ -71,6 +71,8 @@ struct ucp_inst {
     long long hist_cap = 0;
     size_t bytes = 0;
     ucp::Prof prof;
+    bool fast = false;           // precision 1
+    ucp::FastView fv{};
 };
 
 namespace ucp {
