@@ -168,6 +168,31 @@ UCP_API ucp_status ucp_profile(ucp_inst* inst, int32_t enable);
 UCP_API int32_t ucp_kernel_times(ucp_inst* inst, const char** names,
                          int64_t* launches, double* total_ms, int32_t cap);
 
+/* ---- allocation-free u1 step ------------------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory (a process whose device memory is owned by
+ * another framework, a real-time control loop that must not enter the
+ * allocator, a plug-in handed only its input and output buffers).
+ *
+ * Computes the u1 table U_j = E[x1 | y1 = y_j] (the same u1 step as
+ * ucp_sweep / ucp_set_controllers on the fast path) for the controller f:
+ *   params  host; validated as by ucp_plan (precision is ignored).
+ *   f_dev   device, n_x doubles: f(x_i) on the x0 grid, rounded to the
+ *           candidate lattice as ucp_set_controllers does.
+ *   u1_dev  device, n_y doubles, written.
+ *   stream  cudaStream_t as void* (NULL: default stream); the call is
+ *           asynchronous on it.
+ * It allocates nothing: its intermediate buffers live in one fixed device
+ * array of 5.5 MiB that every GPU loading the library holds until exit.
+ * Limits: n_x <= 32768 and n_y <= 32768, else UCP_E_ARG.  The first call on
+ * a device looks up that array's address with the device current; make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race, so serialise them.  UCP_E_CUDA on a launch failure. */
+UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
+                                         const double* f_dev, double* u1_dev,
+                                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif
