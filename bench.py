@@ -342,6 +342,20 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile(args):
+    """One instance of the workload, then --profile-sweeps sweeps: the launch
+    sequence the ncu summaries under profiles/ were captured from."""
+    import torch
+    from paper_1908_04489_gb300 import binding, build
+    build.build()
+    p, _ = workload(args.workload, args.precision)
+    with binding.Instance(p) as inst:
+        inst.sweep(args.profile_sweeps)
+        print(json.dumps({"workload": args.workload, "J": inst.eval_J(),
+                          "sweeps": args.profile_sweeps}))
+    torch.cuda.synchronize()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -378,9 +392,14 @@ def main():
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="only build one instance and run this many sweeps "
+                         "(a short, fixed launch sequence for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_sweeps:
+        run_profile(args)
     else:
         run_gpu(args)
 

@@ -168,6 +168,14 @@ UCP_API ucp_status ucp_profile(ucp_inst* inst, int32_t enable);
 UCP_API int32_t ucp_kernel_times(ucp_inst* inst, const char** names,
                          int64_t* launches, double* total_ms, int32_t cap);
 
+/* Measured ALU throughput of the current device (no paper counterpart: the
+ * denominators of the roofline fractions of the ALU-bound kernels): FP64
+ * FMA and FP32 FMA in TFLOP/s (2 flops per FMA) and FP32 ex2 (SFU) in
+ * Gop/s, from dependent-chain kernels that fill every SM.  Allocates and
+ * frees a small device buffer; synchronises. */
+UCP_API ucp_status ucp_probe_alu(double* fp64_tflops, double* fp32_tflops,
+                                 double* ex2_gops, void* stream);
+
 /* ---- allocation-free u1 step ------------------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that may
@@ -184,7 +192,7 @@ UCP_API int32_t ucp_kernel_times(ucp_inst* inst, const char** names,
  *   stream  cudaStream_t as void* (NULL: default stream); the call is
  *           asynchronous on it.
  * It allocates nothing: its intermediate buffers live in one fixed device
- * array of 5.5 MiB that every GPU loading the library holds until exit.
+ * array of 5.75 MiB that every GPU loading the library holds until exit.
  * Limits: n_x <= 32768 and n_y <= 32768, else UCP_E_ARG.  The first call on
  * a device looks up that array's address with the device current; make it
  * before any stream capture.  All calls share the array: calls that overlap

@@ -102,6 +102,7 @@ def load():
                                    ctypes.c_int32]
     L.ucp_kernel_times.restype = ctypes.c_int32
     L.ucp_tie_recosts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.ucp_probe_alu.argtypes = [_dp, _dp, _dp, _vp]
     _lib = L
     return L
 
@@ -123,6 +124,16 @@ def plan(params) -> dict:
     _check(L.ucp_plan(ctypes.byref(Params.from_dict(params)),
                       *(ctypes.byref(x) for x in v)), "ucp_plan")
     return dict(zip(("n_x", "n_w", "n_y", "n_cand", "device_bytes"),
+                    (x.value for x in v)))
+
+
+def probe_alu(stream=None) -> dict:
+    """Measured FP64 / FP32 FMA TFLOP/s and FP32 ex2 Gop/s of this GPU."""
+    v = [ctypes.c_double() for _ in range(3)]
+    sp = getattr(stream, "cuda_stream", stream)
+    _check(load().ucp_probe_alu(*(ctypes.byref(x) for x in v), _vp(sp)),
+           "ucp_probe_alu")
+    return dict(zip(("fp64_tflops", "fp32_tflops", "ex2_gops"),
                     (x.value for x in v)))
 
 

@@ -8,31 +8,37 @@
 //   S = W2 + 2[(1-t) P_p + t P_{p+1}] + (1-t)^2 Q_p + 2t(1-t) R_p + t^2 Q_{p+1},
 //   W2 = sum phi_l w_l^2,  P_p = sum phi_l w_l E_{p+l},
 //   Q_p = sum phi_l E_{p+l}^2,  R_p = sum phi_l E_{p+l} E_{p+l+1}.
-// One table build per u1 update makes every candidate O(1).  The table value
-// differs from the serial quadrature only by rounding; a bound on that
-// difference screens each stage of the candidate list (Corollary 1's
-// pointwise argmin, eq. (2)'s neighbour set, the coarse set and the
-// refinement levels), and whenever two distinct values could still be the
-// first minimum, those values are re-costed by the serial FP64 quadrature
-// (kernels_plain.cu's arithmetic), so the winners are the plain path's.
+// One table build per u1 update makes every candidate O(1).  A table cost
+// differs from the serial FP64 quadrature only by rounding; a rigorous bound
+// on that difference screens each stage of the candidate list (Corollary 1's
+// pointwise argmin over eq. (2)'s neighbours, the coarse set and the
+// refinement levels).  Whenever two distinct values could still be the first
+// minimum, those values are re-costed by the serial FP64 quadrature (the
+// plain path's arithmetic, operation for operation), so the fast path makes
+// the plain path's decisions.
 //
 // u1 step.  U_j = E[x1 | y1 = y_j] (Newton on the quadratic C_1, Section
-// III-D; closed form of Section IV-C).  Along the uniform y grid the Gaussian
-// weight of a source obeys w_{j+1} = w_j rho_j, rho_{j+1} = rho_j e^{-delta^2},
-// so one exp per (source, run of 16 targets) replaces sixteen.  Pairs whose
-// exponent exceeds the run's minimum by more than 46 (weight below 1e-20 of
-// the largest) are skipped.
+// III-D; closed form of Section IV-C), as the ratio of Gaussian sums with
+// each target's exponents shifted by an estimate m_j of their minimum.
+// Along the uniform y grid the shifted weight of source i obeys
+//   w_{i,j+1} = w_{i,j} exp(delta f_i) Psi_j,
+//   Psi_j = exp(-delta y_j - delta^2/2 + m_{j+1} - m_j),
+// so one exp per (source, run of R targets) replaces R of them.  Weights
+// below e^-46 of a target's largest are skipped.
+//
+// Arithmetic: the bulk runs in double-float on the FP32 pipe (df.cuh); FP64
+// only combines partial sums and re-costs near-ties.
 #include <float.h>
 #include <limits.h>
 
+#include "df.cuh"
 #include "ucp_fast.cuh"
 
 namespace ucp {
 
 namespace {
 
-constexpr int kRun = 16;          // targets per thread in the u1 recurrence
-constexpr double kCut = 46.0;     // skip weights below e^-46 of the maximum
+constexpr float kCut = 46.0f;     // skip weights below e^-46 of the maximum
 
 __device__ __forceinline__ double inv_one(const Geom& g) {
     return __longlong_as_double((int64_t)(1023 - g.shift) << 52);
@@ -43,127 +49,182 @@ __device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
 __device__ __forceinline__ double x_of(const Geom& g, int64_t i) {
     return __dmul_rn((double)(i - g.hx), g.delta);
 }
+// exact double-float of an integer below 2^48 in magnitude
+__device__ __forceinline__ dfloat df_from_i64(int64_t m) {
+    const float h = (float)m;
+    return {h, (float)(m - (int64_t)h)};
+}
 
-// Serial FP64 quadrature, operation for operation the plain path's S.
-__device__ double S_exact(const Geom& g, const double* __restrict__ phi,
-                          const double* __restrict__ U,
-                          const double* __restrict__ Ud, int64_t nu) {
+// ---- exact serial FP64 cost (the plain path's arithmetic) -----------------
+
+__device__ __forceinline__ double exact_term(const Geom& g,
+                                             const double* __restrict__ phi,
+                                             const double* __restrict__ U,
+                                             const double* __restrict__ Ud,
+                                             int64_t jb, double t, double u,
+                                             int64_t l) {
+    const int64_t j = jb + l;
+    double uh;
+    if (j < 0) uh = __dadd_rn(U[0], __dmul_rn(t, 0.0));
+    else if (j >= g.n_y - 1) uh = __dadd_rn(U[g.n_y - 1], __dmul_rn(t, 0.0));
+    else uh = __dadd_rn(U[j], __dmul_rn(t, Ud[j]));
+    const double e = __dsub_rn(u, uh);
+    return __dmul_rn(phi[l], __dmul_rn(e, e));
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask();
+
+// k^2 (u - x_i)^2 + S(u) with S summed over l in order, computed by a group
+// of G lanes: lanes form terms in parallel, every lane adds them in index
+// order (identical sums on all lanes).
+template <int G>
+__device__ double exact_cost_group(const Geom& g, const FastView& f, int64_t i,
+                                   int64_t nu, int lane) {
     const int64_t cell = nu >> g.shift;
     const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
     const int64_t jb = cell - g.hw + g.hy;
     const double u = value_of(g, nu);
-    const int64_t ny1 = g.n_y - 1;
     double acc = 0.0;
-    int64_t l = 0;
-    const double eL = __dsub_rn(u, __dadd_rn(U[0], __dmul_rn(t, 0.0)));
-    const double eL2 = __dmul_rn(eL, eL);
-    for (; l < g.n_w && jb + l < 0; ++l)
-        acc = __dadd_rn(acc, __dmul_rn(phi[l], eL2));
-    for (; l < g.n_w && jb + l < ny1; ++l) {
-        const int64_t j = jb + l;
-        const double uh = __dadd_rn(U[j], __dmul_rn(t, Ud[j]));
-        const double e = __dsub_rn(u, uh);
-        acc = __dadd_rn(acc, __dmul_rn(phi[l], __dmul_rn(e, e)));
+    for (int64_t l0 = 0; l0 < g.n_w; l0 += G) {
+        const int64_t l = l0 + lane;
+        const double term = l < g.n_w ? exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l) : 0.0;
+        const int cnt = (int)min((int64_t)G, g.n_w - l0);
+        for (int k = 0; k < cnt; ++k)
+            acc = __dadd_rn(acc, __shfl_sync(group_mask<G>(), term, k, G));
     }
-    const double eR = __dsub_rn(u, __dadd_rn(U[ny1], __dmul_rn(t, 0.0)));
-    const double eR2 = __dmul_rn(eR, eR);
-    for (; l < g.n_w; ++l) acc = __dadd_rn(acc, __dmul_rn(phi[l], eR2));
-    return acc;
+    const double a = __dsub_rn(u, x_of(g, i));
+    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
 }
 
-__device__ __forceinline__ double control_term(const Geom& g, int64_t i,
-                                               int64_t nu) {
-    const double a = __dsub_rn(value_of(g, nu), x_of(g, i));
-    return __dmul_rn(g.kk, __dmul_rn(a, a));
+// single-lane variant (rare: candidates outside the table range)
+__device__ double exact_cost_lane(const Geom& g, const FastView& f, int64_t i,
+                                  int64_t nu) {
+    const int64_t cell = nu >> g.shift;
+    const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy;
+    const double u = value_of(g, nu);
+    double acc = 0.0;
+    for (int64_t l = 0; l < g.n_w; ++l)
+        acc = __dadd_rn(acc, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
+    const double a = __dsub_rn(u, x_of(g, i));
+    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
 }
+
+// ---- screened table cost ------------------------------------------------
 
 struct Eval {
-    double gv;    // cost (table value or exact)
-    double beta;  // bound on |gv - exact serial cost|, 0 when exact
+    dfloat gv;    // cost
+    float beta;   // bound on |gv - serial FP64 cost|
 };
 
-// Cost of candidate nu at x_i from the correlation tables, with the bound.
 __device__ __forceinline__ Eval eval_table(const Geom& g, const FastView& f,
                                            int64_t i, int64_t nu) {
     const int64_t cell = nu >> g.shift;
     const int64_t p = cell - f.c_lo;
-    const double ctl = control_term(g, i, nu);
     if (p < 0 || p + 1 >= f.n_pos) {
-        const double S = S_exact(g, f.phi, f.U, f.Ud, nu);
-        return {__dadd_rn(ctl, S), 0.0};
+        // outside the tables (rare): serial cost, bound covers its rounding
+        // to double-float
+        const double v = exact_cost_lane(g, f, i, nu);
+        return {df_from_double(v), 4.0e-15f * (float)fabs(v) + FLT_MIN};
     }
-    const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
-    const double omt = 1.0 - t;
-    const double P0 = f.P[p], P1 = f.P[p + 1];
-    const double Q0 = f.Q[p], Q1 = f.Q[p + 1];
-    const double R0 = f.R[p];
-    double S = f.W2 + 2.0 * (omt * P0 + t * P1) + omt * omt * Q0 +
-               2.0 * t * omt * R0 + t * t * Q1;
-    // M bounds the sum of the absolute values of every term (Cauchy-Schwarz:
-    // |P_p| <= sqrt(W2 Q_p), |R_p| <= sqrt(Q_p Q_{p+1})).
-    const float rm = sqrtf((float)f.W2) + (float)omt * sqrtf(fmaxf((float)Q0, 0.f)) +
-                     (float)t * sqrtf(fmaxf((float)Q1, 0.f));
-    const double M = (double)rm * (double)rm * (1.0 + 1e-5);
-    const double gv = ctl + S;
-    const double beta = f.beta_rel * M + f.beta_abs * (2.0 * (double)rm + 1.0) +
-                        2.3e-16 * fabs(gv);
+    const int64_t frac = nu - cell * g.one;
+    const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
+    const dfloat omt = df_add_f(df_neg(t), 1.0f);
+    const dfloat P0 = f.P[p], P1 = f.P[p + 1];
+    const dfloat Q0 = f.Q[p], Q1 = f.Q[p + 1];
+    const dfloat R0 = f.R[p];
+    dfloat lin = df_add(df_mul(omt, P0), df_mul(t, P1));
+    lin = {2.0f * lin.hi, 2.0f * lin.lo};
+    const dfloat to = df_mul(t, omt);
+    dfloat S = df_add(dfloat{f.W2hi, f.W2lo}, lin);
+    S = df_add(S, df_mul(df_mul(omt, omt), Q0));
+    S = df_add(S, df_mul(dfloat{2.0f * to.hi, 2.0f * to.lo}, R0));
+    S = df_add(S, df_mul(df_mul(t, t), Q1));
+    const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
+    const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
+    const dfloat gv = df_add(ctl, S);
+    const float rm = f.sqrtW2 + omt.hi * sqrtf(fmaxf(Q0.hi, 0.f)) +
+                     t.hi * sqrtf(fmaxf(Q1.hi, 0.f));
+    const float M = rm * rm * 1.0001f;
+    const float beta = f.beta_rel * M + f.beta_abs * (2.0f * rm + 1.0f) +
+                       3.0e-13f * fabsf(ctl.hi) + f.beta_ctl * sqrtf(fabsf(ctl.hi)) +
+                       4.0e-16f * fabsf(gv.hi);
     return {gv, beta};
 }
 
-__device__ __forceinline__ double exact_cost(const Geom& g, const FastView& f,
-                                             int64_t i, int64_t nu) {
-    return __dadd_rn(control_term(g, i, nu), S_exact(g, f.phi, f.U, f.Ud, nu));
-}
-
-__device__ __forceinline__ bool before(double ga, int32_t pa, double gb,
-                                       int32_t pb) {
-    return ga < gb || (ga == gb && pa < pb);
+// lanes of this thread's group of G (groups may diverge from each other)
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G == 32) return 0xffffffffu;
+    return (0xffffffffu >> (32 - G)) << ((threadIdx.x & 31) & ~(G - 1));
 }
 
 template <int G>
-__device__ __forceinline__ double gmin(double v) {
+__device__ __forceinline__ dfloat gmin_df(dfloat v) {
+    const unsigned gm = group_mask<G>();
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1)
-        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off, G));
+    for (int off = G / 2; off > 0; off >>= 1) {
+        dfloat o{__shfl_xor_sync(gm, v.hi, off, G),
+                 __shfl_xor_sync(gm, v.lo, off, G)};
+        if (df_lt(o, v)) v = o;
+    }
     return v;
 }
 template <int G>
 __device__ __forceinline__ int64_t gmin_i64(int64_t v) {
+    const unsigned gm = group_mask<G>();
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
-        const int64_t o = __shfl_xor_sync(0xffffffffu, v, off, G);
+        const int64_t o = __shfl_xor_sync(gm, v, off, G);
         v = o < v ? o : v;
     }
     return v;
 }
 template <int G>
 __device__ __forceinline__ int64_t gmax_i64(int64_t v) {
+    const unsigned gm = group_mask<G>();
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
-        const int64_t o = __shfl_xor_sync(0xffffffffu, v, off, G);
+        const int64_t o = __shfl_xor_sync(gm, v, off, G);
         v = o > v ? o : v;
     }
     return v;
 }
 template <int G>
+__device__ __forceinline__ int32_t gmin_i32(int32_t v) {
+    const unsigned gm = group_mask<G>();
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+        v = min(v, __shfl_xor_sync(gm, v, off, G));
+    return v;
+}
+__device__ __forceinline__ bool before(double ga, int32_t pa, double gb,
+                                       int32_t pb) {
+    return ga < gb || (ga == gb && pa < pb);
+}
+template <int G>
 __device__ __forceinline__ void glex(double& gv, int32_t& pos, int64_t& nu) {
+    const unsigned gm = group_mask<G>();
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
-        const double go = __shfl_xor_sync(0xffffffffu, gv, off, G);
-        const int32_t po = __shfl_xor_sync(0xffffffffu, pos, off, G);
-        const int64_t no = __shfl_xor_sync(0xffffffffu, nu, off, G);
+        const double go = __shfl_xor_sync(gm, gv, off, G);
+        const int32_t po = __shfl_xor_sync(gm, pos, off, G);
+        const int64_t no = __shfl_xor_sync(gm, nu, off, G);
         if (before(go, po, gv, pos)) { gv = go; pos = po; nu = no; }
     }
 }
 
-// The running winner: its value interval [gv - beta, gv + beta].
+// The running winner: cost interval [gv - beta, gv + beta] (beta 0: exact).
 struct Best {
-    double gv, beta;
+    dfloat gv;
+    float beta;
     int32_t pos;
     int64_t nu;
+    bool is_exact;  // `exact` holds the serial FP64 cost
+    double exact;
 };
 
-// Candidate position p of stage 0 (incumbent, neighbours, coarse).
 __device__ __forceinline__ int64_t stage0_nu(const Geom& g, const int64_t* nu_pre,
                                              const int64_t* coarse, int64_t i,
                                              int p) {
@@ -177,74 +238,87 @@ __device__ __forceinline__ int64_t stage0_nu(const Geom& g, const int64_t* nu_pr
     return coarse[p - 1 - 2 * g.n_nbr];
 }
 
-// Resolve one stage: the candidates are the carried winner `best` (owned by
-// lane 0) plus, for each lane, positions p0 + lane + k*G (k < per_lane) that
-// are < p_end; cand(p) gives the lattice value.  Returns the first minimum
-// of the exact serial costs over all of them, re-costing exactly only when
-// the screened intervals leave more than one distinct value in play.
+__device__ __forceinline__ dfloat df_pm(dfloat v, float b) { return df_add_f(v, b); }
+
+// Resolve one stage of the list: the carried winner (lane 0) plus positions
+// p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
+// costs over all of them.
 template <int G, typename CandFn>
 __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
-                        Best best, int p0, int p_end, CandFn cand,
+                        const Best& best, int p0, int p_end, CandFn cand,
                         int32_t* n_exact) {
-    // 1. smallest upper end among all candidates
-    double hi = lane == 0 ? best.gv + best.beta : DBL_MAX;
+    const bool have_best = best.pos != INT_MAX;
+    // 1. smallest upper end
+    dfloat hi = {FLT_MAX, 0.f};
+    if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
     for (int p = p0 + lane; p < p_end; p += G) {
         const Eval e = eval_table(g, f, i, cand(p));
-        hi = fmin(hi, e.gv + e.beta);
+        const dfloat h = df_pm(e.gv, e.beta);
+        if (df_lt(h, hi)) hi = h;
     }
-    hi = gmin<G>(hi);
-    // 2. which distinct values can still be the minimum
+    hi = gmin_df<G>(hi);
+    // 2. distinct values still in play, and their first position
     int64_t vmin = INT64_MAX, vmax = INT64_MIN;
-    double tg = DBL_MAX;        // table value of the candidates in play
-    int32_t tp = INT_MAX;
-    int64_t tn = 0;
-    if (lane == 0 && best.gv - best.beta <= hi) {
+    int32_t pmin = INT_MAX;
+    if (lane == 0 && have_best && !df_lt(hi, df_pm(best.gv, -best.beta))) {
         vmin = vmax = best.nu;
-        tg = best.gv; tp = best.pos; tn = best.nu;
+        pmin = best.pos;
     }
     for (int p = p0 + lane; p < p_end; p += G) {
         const int64_t nu = cand(p);
         const Eval e = eval_table(g, f, i, nu);
-        if (e.gv - e.beta <= hi) {
+        if (!df_lt(hi, df_pm(e.gv, -e.beta))) {
             vmin = nu < vmin ? nu : vmin;
             vmax = nu > vmax ? nu : vmax;
-            if (before(e.gv, p, tg, tp)) { tg = e.gv; tp = p; tn = nu; }
+            pmin = p < pmin ? p : pmin;
         }
     }
     vmin = gmin_i64<G>(vmin);
     vmax = gmax_i64<G>(vmax);
+    pmin = gmin_i32<G>(pmin);
     if (vmin == vmax) {
-        // one value in play: its first position wins; equal values carry
-        // identical table costs, so the table-order first minimum is it
-        glex<G>(tg, tp, tn);
-        double beta = 0.0;
-        if (tp == best.pos) beta = best.beta;
-        else {
-            const Eval e = eval_table(g, f, i, tn);
-            beta = e.beta;
-        }
-        return {tg, beta, tp, tn};
+        // one value in play: its first occurrence wins
+        if (have_best && pmin == best.pos) return best;
+        const Eval e = eval_table(g, f, i, vmin);
+        return {e.gv, e.beta, pmin, vmin, false, 0.0};
     }
-    // 3. several values in play: serial FP64 costs decide among them
+    // 3. several values in play: serial FP64 costs of each, group-parallel
     double xg = DBL_MAX;
     int32_t xp = INT_MAX;
     int64_t xn = 0;
-    if (lane == 0 && best.gv - best.beta <= hi) {
-        const double v = best.beta == 0.0 ? best.gv : exact_cost(g, f, i, best.nu);
-        xg = v; xp = best.pos; xn = best.nu;
-        if (best.beta != 0.0 && n_exact) atomicAdd(n_exact, 1);
+    if (have_best && !df_lt(hi, df_pm(best.gv, -best.beta))) {
+        double v = best.exact;
+        if (!best.is_exact) {
+            v = exact_cost_group<G>(g, f, i, best.nu, lane);
+            if (lane == 0 && n_exact) atomicAdd(n_exact, 1);
+        }
+        if (lane == 0) { xg = v; xp = best.pos; xn = best.nu; }
     }
-    for (int p = p0 + lane; p < p_end; p += G) {
-        const int64_t nu = cand(p);
-        const Eval e = eval_table(g, f, i, nu);
-        if (e.gv - e.beta <= hi) {
-            const double v = e.beta == 0.0 ? e.gv : exact_cost(g, f, i, nu);
-            if (e.beta != 0.0 && n_exact) atomicAdd(n_exact, 1);
-            if (before(v, p, xg, xp)) { xg = v; xp = p; xn = nu; }
+    // members in list order; each needs every lane for its re-costing
+    for (int pb = p0; pb < p_end; pb += G) {
+        const int p = pb + lane;
+        bool member = false;
+        int64_t nu = 0;
+        if (p < p_end) {
+            nu = cand(p);
+            const Eval e = eval_table(g, f, i, nu);
+            member = !df_lt(hi, df_pm(e.gv, -e.beta));
+        }
+        const unsigned gm = group_mask<G>();
+        unsigned mask = __ballot_sync(gm, member);
+        const int base = (threadIdx.x & 31) & ~(G - 1);
+        mask = (mask >> base) & (0xffffffffu >> (32 - G));
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int64_t mnu = __shfl_sync(gm, nu, src, G);
+            const double v = exact_cost_group<G>(g, f, i, mnu, lane);
+            if (lane == 0 && n_exact) atomicAdd(n_exact, 1);
+            if (lane == src && before(v, p, xg, xp)) { xg = v; xp = p; xn = mnu; }
         }
     }
     glex<G>(xg, xp, xn);
-    return {xg, 0.0, xp, xn};
+    return {df_from_double(xg), 4.0e-15f * (float)fabs(xg), xp, xn, true, xg};
 }
 
 template <int G>
@@ -259,7 +333,7 @@ __global__ void __launch_bounds__(256) k_search_fast(Geom g, FastView f,
     const int64_t ic = active ? i : g.n_x - 1;
     const int64_t* coarse = f.coarse;
 
-    Best best{DBL_MAX, 0.0, INT_MAX, 0};
+    Best best{{FLT_MAX, 0.f}, 0.f, INT_MAX, 0, false, 0.0};
     const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
     best = resolve<G>(g, f, ic, lane, best, 0, n0,
                       [&](int p) { return stage0_nu(g, nu_pre, coarse, ic, p); },
@@ -284,10 +358,11 @@ __global__ void __launch_bounds__(256) k_search_fast(Geom g, FastView f,
     }
 }
 
-// ---- correlation tables -------------------------------------------------
+// ---- correlation tables ---------------------------------------------------
 
 // E_m = U^(y_m) - y_m for table E-index m (y-index jlo + m, U held constant
-// beyond the table), its square, and E_m E_{m+1}; also Ud for exact costs.
+// beyond the table), E_m^2 and E_m E_{m+1}, in double-float; Ud for the
+// serial costs.
 __global__ void k_build_E(Geom g, FastView f, const double* __restrict__ U,
                           double* __restrict__ Ud) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,17 +373,18 @@ __global__ void k_build_E(Geom g, FastView f, const double* __restrict__ U,
     const int64_t b = jj + 1 < 0 ? 0 : (jj + 1 > g.n_y - 1 ? g.n_y - 1 : jj + 1);
     const double e0 = U[a] - (double)(jj - g.hy) * g.delta;
     const double e1 = U[b] - (double)(jj + 1 - g.hy) * g.delta;
-    f.E[m] = e0;
-    f.E2[m] = e0 * e0;
-    f.EE[m] = e0 * e1;
+    f.E[m] = df_from_double(e0);
+    f.E2[m] = df_from_double(e0 * e0);
+    f.EE[m] = df_from_double(e0 * e1);
 }
 
 constexpr int kTabT = 256;    // positions per block
-constexpr int kTabL = 1024;   // taps per shared-memory chunk
+constexpr int kTabL = 512;    // taps per shared-memory chunk
+constexpr int kTabB = 64;     // taps per double-float partial sum
 
 __global__ void __launch_bounds__(kTabT) k_tables(Geom g, FastView f) {
-    __shared__ double sE[kTabT + kTabL], sE2[kTabT + kTabL], sEE[kTabT + kTabL];
-    __shared__ double sa[kTabL], sphi[kTabL];
+    __shared__ dfloat sE[kTabT + kTabL], sE2[kTabT + kTabL], sEE[kTabT + kTabL];
+    __shared__ dfloat sa[kTabL], sphi[kTabL];
     const int64_t p0 = (int64_t)blockIdx.x * kTabT;
     const int t = threadIdx.x;
     double P = 0.0, Q = 0.0, R = 0.0;
@@ -318,46 +394,56 @@ __global__ void __launch_bounds__(kTabT) k_tables(Geom g, FastView f) {
         for (int k = t; k < kTabT + cl; k += kTabT) {
             const int64_t m = p0 + l0 + k;
             const bool ok = m < f.n_e;
-            sE[k] = ok ? f.E[m] : 0.0;
-            sE2[k] = ok ? f.E2[m] : 0.0;
-            sEE[k] = ok ? f.EE[m] : 0.0;
+            sE[k] = ok ? f.E[m] : dfloat{0.f, 0.f};
+            sE2[k] = ok ? f.E2[m] : dfloat{0.f, 0.f};
+            sEE[k] = ok ? f.EE[m] : dfloat{0.f, 0.f};
         }
         for (int k = t; k < cl; k += kTabT) {
             sa[k] = f.a[l0 + k];
-            sphi[k] = f.phi[l0 + k];
+            sphi[k] = f.phidf[l0 + k];
         }
         __syncthreads();
+        for (int b0 = 0; b0 < cl; b0 += kTabB) {
+            const int b1 = min(cl, b0 + kTabB);
+            dfloat aP{0.f, 0.f}, aQ{0.f, 0.f}, aR{0.f, 0.f};
 #pragma unroll 4
-        for (int l = 0; l < cl; ++l) {
-            P = fma(sa[l], sE[t + l], P);
-            Q = fma(sphi[l], sE2[t + l], Q);
-            R = fma(sphi[l], sEE[t + l], R);
+            for (int l = b0; l < b1; ++l) {
+                float pp, pe;
+                df_mul_raw(sa[l], sE[t + l], pp, pe);
+                aP = df_acc(aP, pp, pe);
+                df_mul_raw(sphi[l], sE2[t + l], pp, pe);
+                aQ = df_acc(aQ, pp, pe);
+                df_mul_raw(sphi[l], sEE[t + l], pp, pe);
+                aR = df_acc(aR, pp, pe);
+            }
+            P += df_to_double(aP);
+            Q += df_to_double(aQ);
+            R += df_to_double(aR);
         }
     }
     const int64_t p = p0 + t;
     if (p < f.n_pos) {
-        f.P[p] = P;
-        f.Q[p] = Q;
-        f.R[p] = R;
+        f.P[p] = df_from_double(P);
+        f.Q[p] = df_from_double(Q);
+        f.R[p] = df_from_double(R);
     }
 }
 
-// a_l = phi_l w_l, W2 = sum phi_l w_l^2 (serial), prior_i = x_i^2 / 2 sigma^2,
-// Yfac_j = exp(-delta y_j - delta^2 / 2).
+// Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
+// prior exponent x_i^2 / 2 sigma^2, W2 = sum phi_l w_l^2 (serial), and the
+// exp(k/64) table of df_exp.
 __global__ void k_fast_setup(Geom g, FastView f) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < g.n_w) {
         const double w = (double)(k - g.hw) * g.delta;
-        f.a[k] = f.phi[k] * w;
+        f.a[k] = df_from_double(f.phi[k] * w);
+        f.phidf[k] = df_from_double(f.phi[k]);
     }
     if (k < g.n_x) {
         const double x = x_of(g, k);
-        f.prior[k] = __ddiv_rn(__dmul_rn(x, x), g.two_s2);
+        f.prior[k] = df_from_double(__ddiv_rn(__dmul_rn(x, x), g.two_s2));
     }
-    if (k < g.n_y) {
-        const double y = (double)(k - g.hy) * g.delta;
-        f.Yfac[k] = exp(-g.delta * y - 0.5 * g.delta * g.delta);
-    }
+    if (k < 47) f.t64[k] = df_from_double(exp((double)(k - 23) / 64.0));
     if (k == 0) {
         double s = 0.0;
         for (int64_t l = 0; l < g.n_w; ++l) {
@@ -370,94 +456,125 @@ __global__ void k_fast_setup(Geom g, FastView f) {
 
 // ---- u1 step --------------------------------------------------------------
 
-// Per source: f_i and exp(delta f_i) for this sweep.
+// Per source: f_i (double-float) and exp(delta f_i).
 __global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_x) return;
     const double v = value_of(g, nu[i]);
-    f.src_f[i] = v;
-    f.src_F[i] = exp(g.delta * v);
+    f.src_nu[i] = nu[i];
+    f.src_f[i] = df_from_double(v);
+    f.src_F[i] = df_from_double(exp(g.delta * v));
 }
 
-// Approximate exponent minimum per target (FP32; only sets the scale).
+// m_j: minimum over sources of the exponent, in FP32 (it only sets scales).
 constexpr int kShiftCh = 1024;
-__global__ void __launch_bounds__(256) k_mmse_shift(Geom g, FastView f) {
+__global__ void __launch_bounds__(128) k_mmse_shift(Geom g, FastView f) {
     __shared__ float sp[kShiftCh], sf[kShiftCh];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const float y = (float)((double)((j < g.n_y ? j : g.n_y - 1) - g.hy) * g.delta);
-    float m = FLT_MAX;
+    float m0 = FLT_MAX, m1 = FLT_MAX, m2 = FLT_MAX, m3 = FLT_MAX;
     for (int64_t b = 0; b < g.n_x; b += kShiftCh) {
         const int cnt = (int)min((int64_t)kShiftCh, g.n_x - b);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            sp[k] = (float)f.prior[b + k];
-            sf[k] = (float)f.src_f[b + k];
+            sp[k] = f.prior[b + k].hi;
+            sf[k] = f.src_f[b + k].hi;
         }
         __syncthreads();
-        for (int k = 0; k < cnt; ++k) {
+        int k = 0;
+        for (; k + 3 < cnt; k += 4) {
+            float d0 = y - sf[k], d1 = y - sf[k + 1], d2 = y - sf[k + 2], d3 = y - sf[k + 3];
+            m0 = fminf(m0, fmaf(0.5f * d0, d0, sp[k]));
+            m1 = fminf(m1, fmaf(0.5f * d1, d1, sp[k + 1]));
+            m2 = fminf(m2, fmaf(0.5f * d2, d2, sp[k + 2]));
+            m3 = fminf(m3, fmaf(0.5f * d3, d3, sp[k + 3]));
+        }
+        for (; k < cnt; ++k) {
             const float d = y - sf[k];
-            m = fminf(m, fmaf(0.5f * d, d, sp[k]));
+            m0 = fminf(m0, fmaf(0.5f * d, d, sp[k]));
         }
     }
-    if (j < g.n_y) f.mshift[j] = m;
+    if (j < g.n_y) f.mshift[j] = fminf(fminf(m0, m1), fminf(m2, m3));
+}
+
+// Psi_j = exp(-delta y_j - delta^2/2 + m_{j+1} - m_j) (double-float).
+__global__ void k_mmse_psi(Geom g, FastView f) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_y) return;
+    const double y = (double)(j - g.hy) * g.delta;
+    const double dm = j + 1 < g.n_y ? (double)f.mshift[j + 1] - (double)f.mshift[j] : 0.0;
+    f.psi[j] = df_from_double(exp(-g.delta * y - 0.5 * g.delta * g.delta + dm));
 }
 
 constexpr int kMmseThreads = 64;
 constexpr int kMmseSrc = 256;   // sources staged in shared memory at a time
 
+template <int R>
 __global__ void __launch_bounds__(kMmseThreads) k_mmse_main(Geom g, FastView f) {
-    __shared__ double sf[kMmseSrc], sp[kMmseSrc], sF[kMmseSrc];
-    const int64_t j0 = ((int64_t)blockIdx.x * kMmseThreads + threadIdx.x) * kRun;
+    __shared__ int64_t snu[kMmseSrc];
+    __shared__ dfloat spr[kMmseSrc], sf[kMmseSrc], sF[kMmseSrc];
+    __shared__ dfloat st64[47];
+    if (threadIdx.x < 47) st64[threadIdx.x] = f.t64[threadIdx.x];
+    const int64_t j0 = ((int64_t)blockIdx.x * kMmseThreads + threadIdx.x) * R;
     const int64_t c0 = (int64_t)blockIdx.y * f.chunk;
     const int64_t c1 = min(c0 + f.chunk, g.n_x);
-    // shift of the run and its spread
-    float smin = FLT_MAX, smax = -FLT_MAX;
-    for (int k = 0; k < kRun; ++k) {
-        const int64_t j = j0 + k < g.n_y ? j0 + k : g.n_y - 1;
-        const float m = f.mshift[j];
-        smin = fminf(smin, m);
-        smax = fmaxf(smax, m);
-    }
-    const double srun = (double)smin;
-    const double ya = (double)(j0 - g.hy) * g.delta;
-    const double yb = (double)(j0 + kRun - 1 - g.hy) * g.delta;
-    const double rho0 = f.Yfac[j0 < g.n_y ? j0 : g.n_y - 1];
-    const double cstep = f.cstep;
-    const float cut = (float)kCut + smax;
-    double N[kRun], D[kRun];
+    const int64_t jc0 = j0 < g.n_y ? j0 : g.n_y - 1;
+    const float m0 = f.mshift[jc0];
+    float smax = -FLT_MAX;
+    dfloat psi[R > 1 ? R - 1 : 1];
 #pragma unroll
-    for (int k = 0; k < kRun; ++k) { N[k] = 0.0; D[k] = 0.0; }
+    for (int k = 0; k < R; ++k) {
+        const int64_t j = j0 + k < g.n_y ? j0 + k : g.n_y - 1;
+        smax = fmaxf(smax, f.mshift[j]);
+        if (k + 1 < R) psi[k] = f.psi[j];
+    }
+    const float ya = (float)((double)(j0 - g.hy) * g.delta);
+    const float yb = (float)((double)(j0 + R - 1 - g.hy) * g.delta);
+    const float cut = kCut + smax + 0.01f;
+    const int64_t ybase = (j0 - g.hy) * g.one;
+    dfloat N[R], D[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) { N[k] = {0.f, 0.f}; D[k] = {0.f, 0.f}; }
     for (int64_t b = c0; b < c1; b += kMmseSrc) {
         const int cnt = (int)min((int64_t)kMmseSrc, c1 - b);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += kMmseThreads) {
+            snu[k] = f.src_nu[b + k];
+            spr[k] = f.prior[b + k];
             sf[k] = f.src_f[b + k];
-            sp[k] = f.prior[b + k];
             sF[k] = f.src_F[b + k];
         }
         __syncthreads();
         for (int s = 0; s < cnt; ++s) {
-            const double fv = sf[s];
-            const double pr = sp[s];
-            const float dmin = fmaxf(0.f, fmaxf((float)(ya - fv), (float)(fv - yb)));
-            if (fmaf(0.5f * dmin, dmin, (float)pr) - 1e-3f > cut) continue;
-            const double d0 = ya - fv;
-            double w = exp(srun - (pr + 0.5 * d0 * d0));
-            double rho = rho0 * sF[s];
+            const dfloat fv = sf[s];
+            const dfloat pr = spr[s];
+            const float dmin = fmaxf(0.f, fmaxf(ya - fv.hi, fv.hi - yb));
+            if (fmaf(0.5f * dmin, dmin, pr.hi) > cut) continue;
+            // anchor weight exp(m_j0 - prior - (y_j0 - f)^2 / 2)
+            const dfloat d0 = df_mul(df_from_i64(ybase - snu[s]), dfloat{f.step_hi, f.step_lo});
+            dfloat ex = df_add(pr, df_mul_f(df_mul(d0, d0), 0.5f));
+            ex = df_add_f(df_neg(ex), m0);
+            if (ex.hi < -87.0f) ex = {-87.0f, 0.f};
+            dfloat w = df_exp(ex, st64);
+            const dfloat F = sF[s];
 #pragma unroll
-            for (int k = 0; k < kRun; ++k) {
-                N[k] = fma(w, fv, N[k]);
-                D[k] += w;
-                w *= rho;
-                rho *= cstep;
+            for (int k = 0; k < R; ++k) {
+                float pp, pe;
+                df_mul_raw(w, fv, pp, pe);
+                N[k] = df_acc(N[k], pp, pe);
+                D[k] = df_add(D[k], w);
+                if (k + 1 < R) w = df_mul(w, df_mul(F, psi[k]));
             }
         }
     }
     double* pN = f.partN + (size_t)blockIdx.y * g.n_y;
     double* pD = f.partD + (size_t)blockIdx.y * g.n_y;
 #pragma unroll
-    for (int k = 0; k < kRun; ++k)
-        if (j0 + k < g.n_y) { pN[j0 + k] = N[k]; pD[j0 + k] = D[k]; }
+    for (int k = 0; k < R; ++k)
+        if (j0 + k < g.n_y) {
+            pN[j0 + k] = df_to_double(N[k]);
+            pD[j0 + k] = df_to_double(D[k]);
+        }
 }
 
 __global__ void k_mmse_combine(Geom g, FastView f, double* __restrict__ U) {
@@ -480,7 +597,7 @@ __global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
     __shared__ double red[kJThreads];
     const int64_t i = (int64_t)blockIdx.x * kJThreads + threadIdx.x;
     double v = 0.0;
-    if (i < g.n_x) v = px[i] * eval_table(g, f, i, nu[i]).gv;
+    if (i < g.n_x) v = px[i] * df_to_double(eval_table(g, f, i, nu[i]).gv);
     red[threadIdx.x] = v;
     __syncthreads();
     for (int s = kJThreads / 2; s > 0; s >>= 1) {
@@ -503,6 +620,16 @@ inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs)
 
 // ---- host-side plan and launches ------------------------------------------
 
+int mmse_run_length(const Geom& g) {
+    // keep the exponent change along a run below ~15 (float range of the
+    // double-float weights): R * delta * (Y + max |f|) <= 15
+    const double F = (double)((g.hr + 2 * g.q) > g.hx ? (g.hr + 2 * g.q) : g.hx) * g.delta;
+    const double slope = g.delta * ((double)g.hy * g.delta + F);
+    int R = 16;
+    while (R > 1 && (R - 1) * slope > 15.0) R /= 2;
+    return R;
+}
+
 void fast_plan(const Geom& g, FastPlan* fp) {
     // cells reachable by any candidate: coarse extremes plus the refinement
     // reach (< 1.15 q), or the x0 range (identity init), with margin
@@ -512,8 +639,12 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     fp->n_pos = 2 * ext + 2;
     fp->jlo = fp->c_lo - g.hw + g.hy;
     fp->n_e = fp->n_pos + g.n_w + 1;
-    const int64_t jblocks = (g.n_y + kMmseThreads * kRun - 1) / (kMmseThreads * kRun);
+    fp->run = mmse_run_length(g);
+    const int64_t per_block = (int64_t)kMmseThreads * fp->run;
+    const int64_t jblocks = (g.n_y + per_block - 1) / per_block;
     int64_t chunks = (4 * 152 + jblocks - 1) / jblocks;
+    const int64_t min_chunks = (g.n_x + 4095) / 4096;   // accuracy of the sums
+    if (chunks < min_chunks) chunks = min_chunks;
     const int64_t max_chunks = (g.n_x + 127) / 128;
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
@@ -526,7 +657,7 @@ void fast_plan(const Geom& g, FastPlan* fp) {
 
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
     int64_t n = g.n_w > g.n_x ? g.n_w : g.n_x;
-    n = n > g.n_y ? n : g.n_y;
+    n = n > 47 ? n : 47;
     k_fast_setup<<<blocks(n, 256), 256, 0, s>>>(g, f);
 }
 
@@ -537,11 +668,18 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
     k_sources<<<blocks(g.n_x, 256), 256, 0, s>>>(g, f, nu);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_shift", &ev) : -1;
-    k_mmse_shift<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f);
+    k_mmse_shift<<<blocks(g.n_y, 128), 128, 0, s>>>(g, f);
+    k_mmse_psi<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_main", &ev) : -1;
     dim3 grid((unsigned)f.j_blocks, (unsigned)f.n_chunks);
-    k_mmse_main<<<grid, kMmseThreads, 0, s>>>(g, f);
+    switch (f.run) {
+        case 16: k_mmse_main<16><<<grid, kMmseThreads, 0, s>>>(g, f); break;
+        case 8: k_mmse_main<8><<<grid, kMmseThreads, 0, s>>>(g, f); break;
+        case 4: k_mmse_main<4><<<grid, kMmseThreads, 0, s>>>(g, f); break;
+        case 2: k_mmse_main<2><<<grid, kMmseThreads, 0, s>>>(g, f); break;
+        default: k_mmse_main<1><<<grid, kMmseThreads, 0, s>>>(g, f); break;
+    }
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_combine", &ev) : -1;
     k_mmse_combine<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f, U);

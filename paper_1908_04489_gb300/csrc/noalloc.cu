@@ -34,11 +34,12 @@ using namespace ucp;
 constexpr int64_t kMaxX = 32768;       // largest x0 grid
 constexpr int64_t kMaxY = 32768;       // largest y grid
 constexpr int kMaxChunks = 8;          // source columns of the u1 kernel
-constexpr int kRunTargets = 64 * 16;   // targets per block row (k_mmse_main)
+constexpr int kThreadsPerRow = 64;     // threads per block row (k_mmse_main)
 
-// nu, prior, src_f, src_F (x-sized); Yfac, mshift (y-sized); partials.
-constexpr size_t kScratchDoubles =
-    4 * (size_t)kMaxX + 2 * (size_t)kMaxY + 2 * (size_t)kMaxChunks * kMaxY;
+// 8-byte slots: nu, prior, src_nu, src_f, src_F (x-sized); mshift, psi
+// (y-sized); the exp(k/64) table; numerator and denominator partials.
+constexpr size_t kScratchDoubles = 5 * (size_t)kMaxX + 2 * (size_t)kMaxY + 64 +
+                                   2 * (size_t)kMaxChunks * kMaxY;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
@@ -47,19 +48,16 @@ static std::mutex g_mu;
 static double* g_addr[kMaxDevices] = {};
 
 __global__ void k_na_prepare(Geom g, const double* __restrict__ f,
-                             int64_t* __restrict__ nu, double* __restrict__ prior,
-                             double* __restrict__ Yfac) {
+                             int64_t* __restrict__ nu, dfloat* __restrict__ prior,
+                             dfloat* __restrict__ t64) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < g.n_x) {
         const double v = __dmul_rn(__ddiv_rn(f[k], g.delta), (double)g.one);
         nu[k] = llround(v);
         const double x = __dmul_rn((double)(k - g.hx), g.delta);
-        prior[k] = __ddiv_rn(__dmul_rn(x, x), g.two_s2);
+        prior[k] = df_from_double(__ddiv_rn(__dmul_rn(x, x), g.two_s2));
     }
-    if (k < g.n_y) {
-        const double y = (double)(k - g.hy) * g.delta;
-        Yfac[k] = exp(-g.delta * y - 0.5 * g.delta * g.delta);
-    }
+    if (k < 47) t64[k] = df_from_double(exp((double)(k - 23) / 64.0));
 }
 
 // Device address of g_scratch on the current device (looked up once).
@@ -113,7 +111,9 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
 
     // plan of the u1 kernels over at most kMaxChunks source columns
     FastView f{};
-    f.j_blocks = (g.n_y + kRunTargets - 1) / kRunTargets;
+    f.run = mmse_run_length(g);
+    const int64_t per_row = (int64_t)kThreadsPerRow * f.run;
+    f.j_blocks = (g.n_y + per_row - 1) / per_row;
     int64_t chunks = (4 * 152 + f.j_blocks - 1) / f.j_blocks;
     if (chunks > kMaxChunks) chunks = kMaxChunks;
     const int64_t max_chunks = (g.n_x + 127) / 128;
@@ -121,22 +121,26 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
     if (chunks < 1) chunks = 1;
     f.chunk = ((g.n_x + chunks - 1) / chunks + 63) / 64 * 64;
     f.n_chunks = (int)((g.n_x + f.chunk - 1) / f.chunk);
-    f.cstep = exp(-g.delta * g.delta);
+    const dfloat sd = df_from_double(ldexp(g.delta, -g.shift));
+    f.step_hi = sd.hi;
+    f.step_lo = sd.lo;
 
     double* q = base;
     int64_t* nu = (int64_t*)q;  q += kMaxX;
-    f.prior = q;                q += kMaxX;
-    f.src_f = q;                q += kMaxX;
-    f.src_F = q;                q += kMaxX;
-    f.Yfac = q;                 q += kMaxY;
+    f.prior = (dfloat*)q;       q += kMaxX;
+    f.src_nu = (int64_t*)q;     q += kMaxX;
+    f.src_f = (dfloat*)q;       q += kMaxX;
+    f.src_F = (dfloat*)q;       q += kMaxX;
     f.mshift = (float*)q;       q += kMaxY;
+    f.psi = (dfloat*)q;         q += kMaxY;
+    f.t64 = (dfloat*)q;         q += 64;
     f.partN = q;                q += (size_t)kMaxChunks * kMaxY;
     f.partD = q;
 
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = g.n_x > g.n_y ? g.n_x : g.n_y;
+    const int64_t n = g.n_x > 47 ? g.n_x : 47;
     k_na_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, f_dev, nu, f.prior,
-                                                          f.Yfac);
+                                                          f.t64);
     launch_mmse_fast(g, f, nu, u1_dev, s, nullptr);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

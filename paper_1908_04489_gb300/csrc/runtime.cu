@@ -181,11 +181,41 @@ size_t inst_bytes(const Geom& g, int precision) {
         FastPlan fp;
         fast_plan(g, &fp);
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
-             rnd(8 * nw) + 3 * rnd(8 * nx) + rnd(8 * ny) + rnd(4 * ny) +
-             2 * rnd(8 * (size_t)fp.n_chunks * ny) + rnd(8 * (size_t)fp.J_blocks) +
-             rnd(8) + rnd(4);
+             2 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
+             rnd(8 * 47) + 2 * rnd(8 * (size_t)fp.n_chunks * ny) +
+             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4);
     }
     return b;
+}
+
+// Largest |f| the search can produce from the current state, and |U|.
+static double value_bound(const Geom& g, double fmax) {
+    const double reach = (double)(g.hr + 2 * g.q) * g.delta;
+    const double x = (double)g.hx * g.delta;
+    double b = reach > x ? reach : x;
+    return b > fmax ? b : fmax;
+}
+
+// Error-bound coefficients of the screened table costs (kernels_fast.cu).
+static void fast_bounds(ucp_inst* in, double B) {
+    const Geom& g = in->g;
+    FastView& f = in->fv;
+    const double u = 0x1p-53, uf2 = 0x1p-48;
+    // serial sum of the plain path + double-float 64-tap blocks + FP64
+    // combination + double-float evaluation of the identity
+    const double rel = (double)g.n_w * u + (2.0 * 64 + 16) * uf2 +
+                       ((double)g.n_w / 64.0 + 8.0) * u + 60.0 * uf2;
+    f.beta_rel = (float)(1.25 * rel);
+    // rounding of grid positions, of E = U - y and of the residuals of both
+    // evaluations: |d(residual)| <= u A
+    const double W = (double)g.hw * g.delta;
+    const double y0 = (double)(f.jlo - g.hy) * g.delta;
+    const double y1 = (double)(f.jlo + f.n_e - g.hy) * g.delta;
+    const double Y = fabs(y0) > fabs(y1) ? fabs(y0) : fabs(y1);
+    const double A = 3.0 * W + 4.0 * Y + 9.0 * B + 8.0;
+    f.beta_abs = (float)(1.25 * u * A);
+    const double X = (double)g.hx * g.delta;
+    f.beta_ctl = (float)(4.0 * u * (2.0 * B + X) * g.k);
 }
 
 static ucp_status fast_alloc(ucp_inst* in) {
@@ -199,35 +229,50 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.Ud = d.Ud;
     f.coarse = d.coarse;
     const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
-    f.P = (double*)A.get(8 * (size_t)f.n_pos);
-    f.Q = (double*)A.get(8 * (size_t)f.n_pos);
-    f.R = (double*)A.get(8 * (size_t)f.n_pos);
-    f.E = (double*)A.get(8 * (size_t)f.n_e);
-    f.E2 = (double*)A.get(8 * (size_t)f.n_e);
-    f.EE = (double*)A.get(8 * (size_t)f.n_e);
-    f.a = (double*)A.get(8 * nw);
-    f.prior = (double*)A.get(8 * nx);
-    f.src_f = (double*)A.get(8 * nx);
-    f.src_F = (double*)A.get(8 * nx);
-    f.Yfac = (double*)A.get(8 * ny);
+    f.P = (dfloat*)A.get(8 * (size_t)f.n_pos);
+    f.Q = (dfloat*)A.get(8 * (size_t)f.n_pos);
+    f.R = (dfloat*)A.get(8 * (size_t)f.n_pos);
+    f.E = (dfloat*)A.get(8 * (size_t)f.n_e);
+    f.E2 = (dfloat*)A.get(8 * (size_t)f.n_e);
+    f.EE = (dfloat*)A.get(8 * (size_t)f.n_e);
+    f.a = (dfloat*)A.get(8 * nw);
+    f.phidf = (dfloat*)A.get(8 * nw);
+    f.prior = (dfloat*)A.get(8 * nx);
+    f.src_nu = (int64_t*)A.get(8 * nx);
+    f.src_f = (dfloat*)A.get(8 * nx);
+    f.src_F = (dfloat*)A.get(8 * nx);
     f.mshift = (float*)A.get(4 * ny);
+    f.psi = (dfloat*)A.get(8 * ny);
+    f.t64 = (dfloat*)A.get(8 * 47);
     f.partN = (double*)A.get(8 * (size_t)f.n_chunks * ny);
     f.partD = (double*)A.get(8 * (size_t)f.n_chunks * ny);
     f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
-    if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.prior ||
-        !f.src_f || !f.src_F || !f.Yfac || !f.mshift || !f.partN || !f.partD ||
-        !f.Jpart || !f.W2_dev || !f.n_exact) {
+    if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf ||
+        !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.psi ||
+        !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.W2_dev || !f.n_exact) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
     }
-    // bounds on |table cost - serial FP64 cost| (see kernels_fast.cu)
-    f.beta_rel = (double)(g.n_w + 48) * 0x1p-52;
-    const double A_ = 8.0 * ((double)(g.hw + g.hy + g.hr + 2 * g.q) * g.delta) + 16.0;
-    f.beta_abs = A_ * 0x1p-50;
-    f.cstep = exp(-g.delta * g.delta);
+    const double step = ldexp(g.delta, -g.shift);
+    const dfloat sd = df_from_double(step), kd = df_from_double(g.kk);
+    f.step_hi = sd.hi;
+    f.step_lo = sd.lo;
+    f.kk_hi = kd.hi;
+    f.kk_lo = kd.lo;
+    f.inv_one_f = (float)ldexp(1.0, -g.shift);
+    in->fbound = 0.0;
+    fast_bounds(in, value_bound(g, 0.0));
     return UCP_OK;
+}
+
+static void fast_set_W2(ucp_inst* in) {
+    FastView& f = in->fv;
+    const dfloat w = df_from_double(f.W2);
+    f.W2hi = w.hi;
+    f.W2lo = w.lo;
+    f.sqrtW2 = (float)sqrt(f.W2) * 1.0001f;
 }
 
 static ucp_status fast_refresh(ucp_inst* in, int slot) {
@@ -284,6 +329,14 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
+        fast_set_W2(in);
+        if (p.init_kind == 2) {
+            double fm = 0.0;
+            for (int64_t i = 0; i < g.n_x; ++i)
+                fm = fabs(p.init_table[i]) > fm ? fabs(p.init_table[i]) : fm;
+            in->fbound = fm;
+            fast_bounds(in, value_bound(g, fm));
+        }
     }
     if (p.init_kind == 2) {
         cudaMemcpyAsync(d.table, p.init_table, 8 * nx, cudaMemcpyHostToDevice, s);
@@ -361,6 +414,14 @@ ucp_status inst_set(ucp_inst* in, const double* f, const double* u1) {
     const Geom& g = in->g;
     DevState& d = in->d;
     cudaStream_t s = in->stream;
+    if (in->fast) {
+        double fm = in->fbound;
+        for (int64_t i = 0; i < g.n_x; ++i) fm = fabs(f[i]) > fm ? fabs(f[i]) : fm;
+        if (u1)
+            for (int64_t j = 0; j < g.n_y; ++j) fm = fabs(u1[j]) > fm ? fabs(u1[j]) : fm;
+        in->fbound = fm;
+        fast_bounds(in, value_bound(g, fm));
+    }
     cudaMemcpyAsync(d.table, f, 8 * (size_t)g.n_x, cudaMemcpyHostToDevice, s);
     UCP_LAUNCH(in, "init", launch_table_to_lattice(g, d.table, d.nu[in->cur], s));
     if (u1) {

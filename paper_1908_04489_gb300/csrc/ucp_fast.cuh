@@ -2,11 +2,13 @@
 #pragma once
 
 #include "ucp_internal.cuh"
+#include "df.cuh"
 #include "ucp_runtime.h"
 
 namespace ucp {
 
 void fast_plan(const Geom& g, FastPlan* fp);
+int mmse_run_length(const Geom& g);
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
                       double* U, cudaStream_t s, Prof* prof);

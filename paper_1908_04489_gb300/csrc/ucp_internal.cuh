@@ -58,37 +58,48 @@ struct FastPlan {
     int64_t n_e;       // length of E, E^2, E E_+ (n_pos + n_w + 1)
     int64_t chunk;     // sources per block column of the u1 kernel
     int n_chunks;      // block columns of the u1 kernel
+    int run;           // targets per thread of the u1 recurrence
     int64_t j_blocks;  // block rows of the u1 kernel
     int64_t J_blocks;  // blocks of the J reduction
 };
 
+struct dfloat;  // df.cuh
+
 // Everything the fast kernels read or write (device pointers + scalars).
 struct FastView : FastPlan {
-    const double* phi;   // [n_w] quadrature weights
+    const double* phi;   // [n_w] quadrature weights (FP64)
     const double* U;     // [n_y] u1 table
     const double* Ud;    // [n_y] U_{j+1} - U_j
     const int64_t* coarse;
-    double* P;           // [n_pos] correlation tables
-    double* Q;
-    double* R;
-    double* E;           // [n_e] U^(y) - y on the extended grid
-    double* E2;          // [n_e] E^2
-    double* EE;          // [n_e] E_m E_{m+1}
-    double* a;           // [n_w] phi_l w_l
-    double* prior;       // [n_x] x_i^2 / (2 sigma^2)
-    double* Yfac;        // [n_y] exp(-delta y_j - delta^2 / 2)
-    double* src_f;       // [n_x] f_i of the current sweep
-    double* src_F;       // [n_x] exp(delta f_i)
-    float* mshift;       // [n_y] approximate min_i of the u1 exponents
+    dfloat* P;           // [n_pos] correlation tables (double-float)
+    dfloat* Q;
+    dfloat* R;
+    dfloat* E;           // [n_e] U^(y) - y on the extended grid
+    dfloat* E2;          // [n_e] E^2
+    dfloat* EE;          // [n_e] E_m E_{m+1}
+    dfloat* a;           // [n_w] phi_l w_l
+    dfloat* phidf;       // [n_w] phi_l
+    dfloat* prior;       // [n_x] x_i^2 / (2 sigma^2)
+    int64_t* src_nu;     // [n_x] lattice index of f_i this sweep
+    dfloat* src_f;       // [n_x] f_i
+    dfloat* src_F;       // [n_x] exp(delta f_i)
+    float* mshift;       // [n_y] estimate of min_i of the u1 exponents
+    dfloat* psi;         // [n_y] exp(-delta y_j - delta^2/2 + m_{j+1} - m_j)
+    dfloat* t64;         // [47] exp(k / 64), k = -23..23
     double* partN;       // [n_chunks * n_y] numerator partials
     double* partD;       // [n_chunks * n_y] denominator partials
     double* Jpart;       // [J_blocks]
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
     double W2;           // host copy of *W2_dev
-    double beta_rel;     // table-value error bound: beta_rel * M + ...
-    double beta_abs;     //   ... + beta_abs * (2 sqrt(M) + 1)
-    double cstep;        // exp(-delta^2)
+    float W2hi, W2lo;    // W2 as double-float
+    float sqrtW2;
+    float step_hi, step_lo;   // delta 2^-shift as double-float
+    float kk_hi, kk_lo;       // k^2 as double-float
+    float inv_one_f;          // 2^-shift
+    float beta_rel;      // |table cost - serial cost| <= beta_rel M
+    float beta_abs;      //   + beta_abs (2 sqrt(M) + 1)
+    float beta_ctl;      //   + beta_ctl sqrt(control term) + ...
 };
 
 // ---- plain FP64 path (kernels_plain.cu) --------------------------------

@@ -72,6 +72,7 @@ struct ucp_inst {
     size_t bytes = 0;
     ucp::Prof prof;
     bool fast = false;           // precision 1
+    double fbound = 0.0;         // largest |f| or |U| set by the caller
     ucp::FastView fv{};
 };
 
