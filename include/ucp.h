@@ -168,6 +168,29 @@ UCP_API ucp_status ucp_profile(ucp_inst* inst, int32_t enable);
 UCP_API int32_t ucp_kernel_times(ucp_inst* inst, const char** names,
                          int64_t* launches, double* total_ms, int32_t cap);
 
+/* ---- batches ------------------------------------------------------------ */
+
+/* Many instances swept together: params is a host array of n parameter sets
+ * (different k, sigma, delta and grid widths allowed; all precision 1 and
+ * the same n_refine).  Each instance is set up as by ucp_create on `stream`;
+ * a batched sweep then runs each kernel once for all instances (blocks mapped
+ * to instances by a table) from a captured CUDA graph when `stream` is not
+ * the default stream.  Every instance gets the same results as alone: the
+ * kernels run the same per-instance arithmetic.  Section IV-A's independence
+ * of the grid points within one controller update is what lets instances and
+ * their grid points share one launch. */
+UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* params, int32_t n,
+                                    void* stream, ucp_batch** out);
+/* n_sweeps sweeps of every instance; returns when they are enqueued and the
+ * host-side descriptors are consumed. */
+UCP_API ucp_status ucp_batch_sweep(ucp_batch* b, int32_t n_sweeps);
+/* Synchronise; J_out[k] = J of instance k (host array of n). */
+UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out);
+/* Member k as an instance handle (for ucp_get_controllers, ucp_J_history,
+ * ...); owned by the batch, valid until ucp_batch_destroy. */
+UCP_API ucp_status ucp_batch_instance(ucp_batch* b, int32_t k, ucp_inst** out);
+UCP_API ucp_status ucp_batch_destroy(ucp_batch* b);
+
 /* Measured ALU throughput of the current device (no paper counterpart: the
  * denominators of the roofline fractions of the ALU-bound kernels): FP64
  * FMA and FP32 FMA in TFLOP/s (2 flops per FMA) and FP32 ex2 (SFU) in

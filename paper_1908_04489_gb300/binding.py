@@ -103,6 +103,11 @@ def load():
     L.ucp_kernel_times.restype = ctypes.c_int32
     L.ucp_tie_recosts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.ucp_probe_alu.argtypes = [_dp, _dp, _dp, _vp]
+    L.ucp_batch_create.argtypes = [_vp, P, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
+    L.ucp_batch_sweep.argtypes = [_vp, ctypes.c_int32]
+    L.ucp_batch_eval_J.argtypes = [_vp, _dp]
+    L.ucp_batch_instance.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp)]
+    L.ucp_batch_destroy.argtypes = [_vp]
     _lib = L
     return L
 
@@ -263,6 +268,73 @@ class Instance:
     def close(self):
         if getattr(self, "h", None):
             _check(load().ucp_destroy(self.h), "ucp_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Member(Instance):
+    """A batch member viewed as an instance (owned by the batch)."""
+
+    def __init__(self, handle, params):
+        self.h = handle
+        self.params = dict(params)
+        v = [ctypes.c_uint64() for _ in range(5)]
+        _check(load().ucp_sizes(handle, *(ctypes.byref(x) for x in v)), "ucp_sizes")
+        self.n_x, self.n_w, self.n_y, self.n_cand, self.device_bytes = \
+            (x.value for x in v)
+
+    def close(self):
+        self.h = None   # the batch destroys its members
+
+
+class Batch:
+    """Many instances swept together (``ucp_batch_*``)."""
+
+    def __init__(self, params_list, stream=None, ctx: Context | None = None):
+        import torch
+        L = load()
+        self.ctx = ctx or default_context()
+        self.params = [dict(p) for p in params_list]
+        if stream is None:
+            stream = torch.cuda.current_stream(self.ctx.device)
+        self.stream = stream
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        arr = (Params * len(self.params))(*[Params.from_dict(p) for p in self.params])
+        h = _vp()
+        _check(L.ucp_batch_create(self.ctx.h, arr, len(self.params), _vp(sp),
+                                  ctypes.byref(h)), "ucp_batch_create")
+        self.h = h
+        self.members = []
+        for k, p in enumerate(self.params):
+            m = _vp()
+            _check(L.ucp_batch_instance(h, k, ctypes.byref(m)), "ucp_batch_instance")
+            self.members.append(_Member(m, p))
+
+    def sweep(self, n: int = 1):
+        _check(load().ucp_batch_sweep(self.h, int(n)), "ucp_batch_sweep")
+
+    def eval_J(self) -> np.ndarray:
+        out = np.empty(len(self.params))
+        _check(load().ucp_batch_eval_J(self.h, _ptr(out, ctypes.c_double)),
+               "ucp_batch_eval_J")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            _check(load().ucp_batch_destroy(self.h), "ucp_batch_destroy")
             self.h = None
 
     def __enter__(self):

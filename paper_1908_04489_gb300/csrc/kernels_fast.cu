@@ -49,10 +49,12 @@ __device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
 __device__ __forceinline__ double x_of(const Geom& g, int64_t i) {
     return __dmul_rn((double)(i - g.hx), g.delta);
 }
-// exact double-float of an integer below 2^48 in magnitude
+// exact double-float of an integer below 2^44 in magnitude, from two 32-bit
+// conversions (64-bit integer conversions run on the FP64 pipe)
 __device__ __forceinline__ dfloat df_from_i64(int64_t m) {
-    const float h = (float)m;
-    return {h, (float)(m - (int64_t)h)};
+    const int32_t hi = (int32_t)(m >> 22);              // |hi| < 2^22
+    const int32_t lo = (int32_t)(m & ((1 << 22) - 1));  // [0, 2^22)
+    return df_norm(__int2float_rn(hi) * 4194304.0f, __int2float_rn(lo));
 }
 
 // ---- exact serial FP64 cost (the plain path's arithmetic) -----------------
@@ -322,13 +324,13 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_search_fast(Geom g, FastView f,
-                                                     const int64_t* __restrict__ nu_pre,
-                                                     int64_t* __restrict__ nu_out,
-                                                     int32_t* __restrict__ idx_out,
-                                                     int32_t* n_exact) {
+__device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
+                                            const int64_t* __restrict__ nu_pre,
+                                            int64_t* __restrict__ nu_out,
+                                            int32_t* __restrict__ idx_out,
+                                            int32_t* n_exact, int64_t bx) {
     const int lane = threadIdx.x & (G - 1);
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t i = (bx * blockDim.x + threadIdx.x) / G;
     const bool active = i < g.n_x;
     const int64_t ic = active ? i : g.n_x - 1;
     const int64_t* coarse = f.coarse;
@@ -358,14 +360,24 @@ __global__ void __launch_bounds__(256) k_search_fast(Geom g, FastView f,
     }
 }
 
+template <int G>
+__global__ void __launch_bounds__(256) k_search_fast(Geom g, FastView f,
+                                                     const int64_t* __restrict__ nu_pre,
+                                                     int64_t* __restrict__ nu_out,
+                                                     int32_t* __restrict__ idx_out,
+                                                     int32_t* n_exact) {
+    search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, blockIdx.x);
+}
+
 // ---- correlation tables ---------------------------------------------------
 
 // E_m = U^(y_m) - y_m for table E-index m (y-index jlo + m, U held constant
 // beyond the table), E_m^2 and E_m E_{m+1}, in double-float; Ud for the
 // serial costs.
-__global__ void k_build_E(Geom g, FastView f, const double* __restrict__ U,
-                          double* __restrict__ Ud) {
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void build_E_body(const Geom& g, const FastView& f,
+                                             const double* __restrict__ U,
+                                             double* __restrict__ Ud, int64_t bx) {
+    const int64_t m = bx * blockDim.x + threadIdx.x;
     if (m < g.n_y) Ud[m] = m + 1 < g.n_y ? __dsub_rn(U[m + 1], U[m]) : 0.0;
     if (m >= f.n_e) return;
     const int64_t jj = f.jlo + m;
@@ -378,18 +390,36 @@ __global__ void k_build_E(Geom g, FastView f, const double* __restrict__ U,
     f.EE[m] = df_from_double(e0 * e1);
 }
 
-constexpr int kTabT = 256;    // positions per block
+__global__ void k_build_E(Geom g, FastView f, const double* __restrict__ U,
+                          double* __restrict__ Ud) {
+    build_E_body(g, f, U, Ud, blockIdx.x);
+}
+
+constexpr int kTabT = 128;    // positions per block
 constexpr int kTabL = 512;    // taps per shared-memory chunk
 constexpr int kTabB = 64;     // taps per double-float partial sum
 
-__global__ void __launch_bounds__(kTabT) k_tables(Geom g, FastView f) {
-    __shared__ dfloat sE[kTabT + kTabL], sE2[kTabT + kTabL], sEE[kTabT + kTabL];
-    __shared__ dfloat sa[kTabL], sphi[kTabL];
-    const int64_t p0 = (int64_t)blockIdx.x * kTabT;
+// Partial correlations over the tap range of blockIdx.y (f.tab_span taps):
+// 64-tap double-float blocks accumulated into a double-float total.
+struct TabSmem {
+    dfloat sE[kTabT + kTabL], sE2[kTabT + kTabL], sEE[kTabT + kTabL];
+    dfloat sa[kTabL], sphi[kTabL];
+};
+
+__device__ __forceinline__ void tables_part_body(const Geom& g, const FastView& f,
+                                                 TabSmem& sm, int64_t bx, int64_t by) {
+    dfloat* sE = sm.sE;
+    dfloat* sE2 = sm.sE2;
+    dfloat* sEE = sm.sEE;
+    dfloat* sa = sm.sa;
+    dfloat* sphi = sm.sphi;
+    const int64_t p0 = bx * kTabT;
     const int t = threadIdx.x;
-    double P = 0.0, Q = 0.0, R = 0.0;
-    for (int64_t l0 = 0; l0 < g.n_w; l0 += kTabL) {
-        const int cl = (int)min((int64_t)kTabL, g.n_w - l0);
+    const int64_t lb = by * f.tab_span;
+    const int64_t le = min(lb + f.tab_span, g.n_w);
+    dfloat P{0.f, 0.f}, Q{0.f, 0.f}, R{0.f, 0.f};
+    for (int64_t l0 = lb; l0 < le; l0 += kTabL) {
+        const int cl = (int)min((int64_t)kTabL, le - l0);
         __syncthreads();
         for (int k = t; k < kTabT + cl; k += kTabT) {
             const int64_t m = p0 + l0 + k;
@@ -416,17 +446,44 @@ __global__ void __launch_bounds__(kTabT) k_tables(Geom g, FastView f) {
                 df_mul_raw(sphi[l], sEE[t + l], pp, pe);
                 aR = df_acc(aR, pp, pe);
             }
-            P += df_to_double(aP);
-            Q += df_to_double(aQ);
-            R += df_to_double(aR);
+            P = df_add(P, aP);
+            Q = df_add(Q, aQ);
+            R = df_add(R, aR);
         }
     }
     const int64_t p = p0 + t;
     if (p < f.n_pos) {
-        f.P[p] = df_from_double(P);
-        f.Q[p] = df_from_double(Q);
-        f.R[p] = df_from_double(R);
+        double* part = f.tab_part + (size_t)by * 3 * f.n_pos;
+        part[p] = df_to_double(P);
+        part[f.n_pos + p] = df_to_double(Q);
+        part[2 * f.n_pos + p] = df_to_double(R);
     }
+}
+
+__global__ void __launch_bounds__(kTabT) k_tables_part(Geom g, FastView f) {
+    __shared__ TabSmem sm;
+    tables_part_body(g, f, sm, blockIdx.x, blockIdx.y);
+}
+
+// Sum the tap-range partials in order (FP64) into the double-float tables.
+__device__ __forceinline__ void tables_combine_body(const Geom& g, const FastView& f,
+                                                    int64_t bx) {
+    const int64_t p = bx * blockDim.x + threadIdx.x;
+    if (p >= f.n_pos) return;
+    double P = 0.0, Q = 0.0, R = 0.0;
+    for (int s = 0; s < f.tab_splits; ++s) {
+        const double* part = f.tab_part + (size_t)s * 3 * f.n_pos;
+        P += part[p];
+        Q += part[f.n_pos + p];
+        R += part[2 * f.n_pos + p];
+    }
+    f.P[p] = df_from_double(P);
+    f.Q[p] = df_from_double(Q);
+    f.R[p] = df_from_double(R);
+}
+
+__global__ void k_tables_combine(Geom g, FastView f) {
+    tables_combine_body(g, f, blockIdx.x);
 }
 
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
@@ -457,8 +514,10 @@ __global__ void k_fast_setup(Geom g, FastView f) {
 // ---- u1 step --------------------------------------------------------------
 
 // Per source: f_i (double-float) and exp(delta f_i).
-__global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sources_body(const Geom& g, const FastView& f,
+                                             const int64_t* __restrict__ nu,
+                                             int64_t bx) {
+    const int64_t i = bx * blockDim.x + threadIdx.x;
     if (i >= g.n_x) return;
     const double v = value_of(g, nu[i]);
     f.src_nu[i] = nu[i];
@@ -466,11 +525,21 @@ __global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
     f.src_F[i] = df_from_double(exp(g.delta * v));
 }
 
+__global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
+    sources_body(g, f, nu, blockIdx.x);
+}
+
 // m_j: minimum over sources of the exponent, in FP32 (it only sets scales).
 constexpr int kShiftCh = 1024;
-__global__ void __launch_bounds__(128) k_mmse_shift(Geom g, FastView f) {
-    __shared__ float sp[kShiftCh], sf[kShiftCh];
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct ShiftSmem {
+    float sp[kShiftCh], sf[kShiftCh];
+};
+
+__device__ __forceinline__ void mmse_shift_body(const Geom& g, const FastView& f,
+                                                ShiftSmem& sm, int64_t bx) {
+    float* sp = sm.sp;
+    float* sf = sm.sf;
+    const int64_t j = bx * blockDim.x + threadIdx.x;
     const float y = (float)((double)((j < g.n_y ? j : g.n_y - 1) - g.hy) * g.delta);
     float m0 = FLT_MAX, m1 = FLT_MAX, m2 = FLT_MAX, m3 = FLT_MAX;
     for (int64_t b = 0; b < g.n_x; b += kShiftCh) {
@@ -497,26 +566,43 @@ __global__ void __launch_bounds__(128) k_mmse_shift(Geom g, FastView f) {
     if (j < g.n_y) f.mshift[j] = fminf(fminf(m0, m1), fminf(m2, m3));
 }
 
+__global__ void __launch_bounds__(128) k_mmse_shift(Geom g, FastView f) {
+    __shared__ ShiftSmem sm;
+    mmse_shift_body(g, f, sm, blockIdx.x);
+}
+
 // Psi_j = exp(-delta y_j - delta^2/2 + m_{j+1} - m_j) (double-float).
-__global__ void k_mmse_psi(Geom g, FastView f) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void mmse_psi_body(const Geom& g, const FastView& f,
+                                              int64_t bx) {
+    const int64_t j = bx * blockDim.x + threadIdx.x;
     if (j >= g.n_y) return;
     const double y = (double)(j - g.hy) * g.delta;
     const double dm = j + 1 < g.n_y ? (double)f.mshift[j + 1] - (double)f.mshift[j] : 0.0;
     f.psi[j] = df_from_double(exp(-g.delta * y - 0.5 * g.delta * g.delta + dm));
 }
 
+__global__ void k_mmse_psi(Geom g, FastView f) { mmse_psi_body(g, f, blockIdx.x); }
+
 constexpr int kMmseThreads = 64;
 constexpr int kMmseSrc = 256;   // sources staged in shared memory at a time
 
+struct MmseSmem {
+    int64_t snu[kMmseSrc];
+    dfloat spr[kMmseSrc], sf[kMmseSrc], sF[kMmseSrc];
+    dfloat st64[47];
+};
+
 template <int R>
-__global__ void __launch_bounds__(kMmseThreads) k_mmse_main(Geom g, FastView f) {
-    __shared__ int64_t snu[kMmseSrc];
-    __shared__ dfloat spr[kMmseSrc], sf[kMmseSrc], sF[kMmseSrc];
-    __shared__ dfloat st64[47];
+__device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
+                                               MmseSmem& sm, int64_t bx, int64_t by) {
+    int64_t* snu = sm.snu;
+    dfloat* spr = sm.spr;
+    dfloat* sf = sm.sf;
+    dfloat* sF = sm.sF;
+    dfloat* st64 = sm.st64;
     if (threadIdx.x < 47) st64[threadIdx.x] = f.t64[threadIdx.x];
-    const int64_t j0 = ((int64_t)blockIdx.x * kMmseThreads + threadIdx.x) * R;
-    const int64_t c0 = (int64_t)blockIdx.y * f.chunk;
+    const int64_t j0 = (bx * kMmseThreads + threadIdx.x) * R;
+    const int64_t c0 = by * f.chunk;
     const int64_t c1 = min(c0 + f.chunk, g.n_x);
     const int64_t jc0 = j0 < g.n_y ? j0 : g.n_y - 1;
     const float m0 = f.mshift[jc0];
@@ -545,30 +631,48 @@ __global__ void __launch_bounds__(kMmseThreads) k_mmse_main(Geom g, FastView f) 
             sF[k] = f.src_F[b + k];
         }
         __syncthreads();
-        for (int s = 0; s < cnt; ++s) {
-            const dfloat fv = sf[s];
-            const dfloat pr = spr[s];
-            const float dmin = fmaxf(0.f, fmaxf(ya - fv.hi, fv.hi - yb));
-            if (fmaf(0.5f * dmin, dmin, pr.hi) > cut) continue;
-            // anchor weight exp(m_j0 - prior - (y_j0 - f)^2 / 2)
-            const dfloat d0 = df_mul(df_from_i64(ybase - snu[s]), dfloat{f.step_hi, f.step_lo});
-            dfloat ex = df_add(pr, df_mul_f(df_mul(d0, d0), 0.5f));
-            ex = df_add_f(df_neg(ex), m0);
-            if (ex.hi < -87.0f) ex = {-87.0f, 0.f};
-            dfloat w = df_exp(ex, st64);
-            const dfloat F = sF[s];
+        // sources that touch this run, then two at a time (independent
+        // recurrences interleave)
+        int s = 0;
+        while (s < cnt) {
+            int sel[2];
+            int ns = 0;
+            for (; s < cnt && ns < 2; ++s) {
+                const float fh = sf[s].hi;
+                const float dmin = fmaxf(0.f, fmaxf(ya - fh, fh - yb));
+                if (fmaf(0.5f * dmin, dmin, spr[s].hi) <= cut) sel[ns++] = s;
+            }
+            if (ns == 0) break;
+            dfloat w[2], F[2], fv[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int src = sel[q < ns ? q : 0];
+                fv[q] = sf[src];
+                F[q] = sF[src];
+                // anchor weight exp(m_j0 - prior - (y_j0 - f)^2 / 2)
+                const dfloat d0 = df_mul(df_from_i64(ybase - snu[src]),
+                                         dfloat{f.step_hi, f.step_lo});
+                dfloat ex = df_add(spr[src], df_mul_f(df_mul(d0, d0), 0.5f));
+                ex = df_add_f(df_neg(ex), m0);
+                if (ex.hi < -87.0f) ex = {-87.0f, 0.f};
+                w[q] = df_exp(ex, st64);
+            }
+            if (ns == 1) w[1] = {0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                float pp, pe;
-                df_mul_raw(w, fv, pp, pe);
-                N[k] = df_acc(N[k], pp, pe);
-                D[k] = df_add(D[k], w);
-                if (k + 1 < R) w = df_mul(w, df_mul(F, psi[k]));
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    float pp, pe;
+                    df_mul_raw(w[q], fv[q], pp, pe);
+                    N[k] = df_acc(N[k], pp, pe);
+                    D[k] = df_add(D[k], w[q]);
+                    if (k + 1 < R) w[q] = df_mul(w[q], df_mul(F[q], psi[k]));
+                }
             }
         }
     }
-    double* pN = f.partN + (size_t)blockIdx.y * g.n_y;
-    double* pD = f.partD + (size_t)blockIdx.y * g.n_y;
+    double* pN = f.partN + (size_t)by * g.n_y;
+    double* pD = f.partD + (size_t)by * g.n_y;
 #pragma unroll
     for (int k = 0; k < R; ++k)
         if (j0 + k < g.n_y) {
@@ -577,8 +681,15 @@ __global__ void __launch_bounds__(kMmseThreads) k_mmse_main(Geom g, FastView f) 
         }
 }
 
-__global__ void k_mmse_combine(Geom g, FastView f, double* __restrict__ U) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <int R>
+__global__ void __launch_bounds__(kMmseThreads) k_mmse_main(Geom g, FastView f) {
+    __shared__ MmseSmem sm;
+    mmse_main_body<R>(g, f, sm, blockIdx.x, blockIdx.y);
+}
+
+__device__ __forceinline__ void mmse_combine_body(const Geom& g, const FastView& f,
+                                                  double* __restrict__ U, int64_t bx) {
+    const int64_t j = bx * blockDim.x + threadIdx.x;
     if (j >= g.n_y) return;
     double n = 0.0, d = 0.0;
     for (int c = 0; c < f.n_chunks; ++c) {
@@ -588,14 +699,18 @@ __global__ void k_mmse_combine(Geom g, FastView f, double* __restrict__ U) {
     U[j] = n / d;
 }
 
+__global__ void k_mmse_combine(Geom g, FastView f, double* __restrict__ U) {
+    mmse_combine_body(g, f, U, blockIdx.x);
+}
+
 // ---- J --------------------------------------------------------------------
 
 constexpr int kJThreads = 256;
-__global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
-                                                         const double* __restrict__ px,
-                                                         const int64_t* __restrict__ nu) {
-    __shared__ double red[kJThreads];
-    const int64_t i = (int64_t)blockIdx.x * kJThreads + threadIdx.x;
+__device__ __forceinline__ void J_partial_body(const Geom& g, const FastView& f,
+                                               const double* __restrict__ px,
+                                               const int64_t* __restrict__ nu,
+                                               double* red, int64_t bx) {
+    const int64_t i = bx * kJThreads + threadIdx.x;
     double v = 0.0;
     if (i < g.n_x) v = px[i] * df_to_double(eval_table(g, f, i, nu[i]).gv);
     red[threadIdx.x] = v;
@@ -604,7 +719,14 @@ __global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) f.Jpart[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) f.Jpart[bx] = red[0];
+}
+
+__global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
+                                                         const double* __restrict__ px,
+                                                         const int64_t* __restrict__ nu) {
+    __shared__ double red[kJThreads];
+    J_partial_body(g, f, px, nu, red, blockIdx.x);
 }
 
 __global__ void k_J_final(FastView f, int nblk, double* out) {
@@ -612,6 +734,109 @@ __global__ void k_J_final(FastView f, int nblk, double* out) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += f.Jpart[b];
     *out = s;
+}
+
+
+// ---- batched wrappers -------------------------------------------------------
+// Every block of a batched launch works on one instance: the block map gives
+// (instance, block of that instance's own grid); the instance descriptor is
+// staged in shared memory and the single-instance body runs unchanged.
+
+__device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* map,
+                                          InstDev& sd) {
+    const BlockRef r = map[blockIdx.x];
+    const int* src = (const int*)(insts + r.inst);
+    int* dst = (int*)&sd;
+    for (int k = threadIdx.x; k < (int)(sizeof(InstDev) / 4); k += blockDim.x)
+        dst[k] = src[k];
+    __syncthreads();
+    return r;
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) kb_search(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    search_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
+                   sd.f.n_exact, r.local);
+}
+
+__global__ void kb_sources(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    sources_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], r.local);
+}
+
+__global__ void __launch_bounds__(128) kb_mmse_shift(const InstDev* insts,
+                                                     const BlockRef* map) {
+    __shared__ InstDev sd;
+    __shared__ ShiftSmem sm;
+    const BlockRef r = stage(insts, map, sd);
+    mmse_shift_body(sd.g, sd.f, sm, r.local);
+}
+
+__global__ void kb_mmse_psi(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    mmse_psi_body(sd.g, sd.f, r.local);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kMmseThreads) kb_mmse_main(const InstDev* insts,
+                                                             const BlockRef* map) {
+    __shared__ InstDev sd;
+    __shared__ MmseSmem sm;
+    const BlockRef r = stage(insts, map, sd);
+    const int64_t jb = sd.f.j_blocks;
+    mmse_main_body<R>(sd.g, sd.f, sm, r.local % jb, r.local / jb);
+}
+
+__global__ void kb_mmse_combine(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    mmse_combine_body(sd.g, sd.f, sd.U, r.local);
+}
+
+__global__ void kb_build_E(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    build_E_body(sd.g, sd.f, sd.U, sd.Ud, r.local);
+}
+
+__global__ void __launch_bounds__(kTabT) kb_tables_part(const InstDev* insts,
+                                                        const BlockRef* map) {
+    __shared__ InstDev sd;
+    __shared__ TabSmem sm;
+    const BlockRef r = stage(insts, map, sd);
+    const int64_t pb = (sd.f.n_pos + kTabT - 1) / kTabT;
+    tables_part_body(sd.g, sd.f, sm, r.local % pb, r.local / pb);
+}
+
+__global__ void kb_tables_combine(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    tables_combine_body(sd.g, sd.f, r.local);
+}
+
+__global__ void __launch_bounds__(kJThreads) kb_J_partial(const InstDev* insts,
+                                                          const BlockRef* map) {
+    __shared__ InstDev sd;
+    __shared__ double red[kJThreads];
+    const BlockRef r = stage(insts, map, sd);
+    J_partial_body(sd.g, sd.f, sd.px, sd.nu[sd.cur ^ 1], red, r.local);
+}
+
+// Last kernel of a batched sweep: J into its history slot, then the sweep
+// counter and the double buffer advance (one thread per instance).
+__global__ void kb_J_final(InstDev* insts, int n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    InstDev& d = insts[b];
+    double s = 0.0;
+    for (int64_t k = 0; k < d.f.J_blocks; ++k) s += d.f.Jpart[k];
+    d.J[d.sweeps + 1] = s;
+    d.sweeps += 1;
+    d.cur ^= 1;
 }
 
 inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -642,7 +867,7 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     fp->run = mmse_run_length(g);
     const int64_t per_block = (int64_t)kMmseThreads * fp->run;
     const int64_t jblocks = (g.n_y + per_block - 1) / per_block;
-    int64_t chunks = (4 * 152 + jblocks - 1) / jblocks;
+    int64_t chunks = (12 * 152 + jblocks - 1) / jblocks;
     const int64_t min_chunks = (g.n_x + 4095) / 4096;   // accuracy of the sums
     if (chunks < min_chunks) chunks = min_chunks;
     const int64_t max_chunks = (g.n_x + 127) / 128;
@@ -653,6 +878,16 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     fp->n_chunks = (int)((g.n_x + chunk - 1) / chunk);
     fp->j_blocks = jblocks;
     fp->J_blocks = (g.n_x + kJThreads - 1) / kJThreads;
+    // split the taps so that the table kernel fills the GPU (~4 blocks/SM)
+    const int64_t pblocks = (fp->n_pos + kTabT - 1) / kTabT;
+    int64_t splits = (4 * 152 + pblocks - 1) / pblocks;
+    const int64_t max_splits = (g.n_w + kTabB - 1) / kTabB;
+    if (splits > max_splits) splits = max_splits;
+    if (splits < 1) splits = 1;
+    int64_t span = (g.n_w + splits - 1) / splits;
+    span = (span + kTabB - 1) / kTabB * kTabB;
+    fp->tab_span = span;
+    fp->tab_splits = (int)((g.n_w + span - 1) / span);
 }
 
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
@@ -694,7 +929,9 @@ void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud
     k_build_E<<<blocks(n, 256), 256, 0, s>>>(g, f, U, Ud);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("tables", &ev) : -1;
-    k_tables<<<blocks(f.n_pos, kTabT), kTabT, 0, s>>>(g, f);
+    dim3 grid(blocks(f.n_pos, kTabT), (unsigned)f.tab_splits);
+    k_tables_part<<<grid, kTabT, 0, s>>>(g, f);
+    k_tables_combine<<<blocks(f.n_pos, 256), 256, 0, s>>>(g, f);
     if (prof) prof->end(k, ev);
 }
 
@@ -717,6 +954,64 @@ void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
         default: break;
     }
 #undef UCP_FAST_CASE
+}
+
+int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
+    switch (kind) {
+        case kBSearch: return (g.n_x * g.n_refine + 255) / 256;
+        case kBPerX: return (g.n_x + 255) / 256;
+        case kBShift: return (g.n_y + 127) / 128;
+        case kBPerY: return (g.n_y + 255) / 256;
+        case kBTabPart: return (fp.n_pos + kTabT - 1) / kTabT * fp.tab_splits;
+        case kBTabComb: return (fp.n_pos + 255) / 256;
+        case kBBuildE: {
+            const int64_t n = fp.n_e > g.n_y ? fp.n_e : g.n_y;
+            return (n + 255) / 256;
+        }
+        case kBJPart: return fp.J_blocks;
+    }
+    return 0;
+}
+
+int64_t batch_mmse_blocks(const Geom&, const FastPlan& fp) {
+    return fp.j_blocks * fp.n_chunks;
+}
+
+void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
+    const InstDev* d = bl.insts;
+#define UCP_BS(G)                                                                   \
+    case G:                                                                         \
+        kb_search<G><<<(unsigned)bl.n_blocks[kBSearch], 256, 0, s>>>(d, bl.map[kBSearch]); \
+        break;
+    switch (bl.G) {
+        UCP_BS(2)
+        UCP_BS(4)
+        UCP_BS(8)
+        UCP_BS(16)
+        UCP_BS(32)
+        default: break;
+    }
+#undef UCP_BS
+    kb_sources<<<(unsigned)bl.n_blocks[kBPerX], 256, 0, s>>>(d, bl.map[kBPerX]);
+    kb_mmse_shift<<<(unsigned)bl.n_blocks[kBShift], 128, 0, s>>>(d, bl.map[kBShift]);
+    kb_mmse_psi<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
+    for (int r = 0; r < 5; ++r) {
+        if (bl.mmse_blocks[r] == 0) continue;
+        const unsigned nb = (unsigned)bl.mmse_blocks[r];
+        switch (r) {
+            case 0: kb_mmse_main<1><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
+            case 1: kb_mmse_main<2><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
+            case 2: kb_mmse_main<4><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
+            case 3: kb_mmse_main<8><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
+            default: kb_mmse_main<16><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
+        }
+    }
+    kb_mmse_combine<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
+    kb_build_E<<<(unsigned)bl.n_blocks[kBBuildE], 256, 0, s>>>(d, bl.map[kBBuildE]);
+    kb_tables_part<<<(unsigned)bl.n_blocks[kBTabPart], kTabT, 0, s>>>(d, bl.map[kBTabPart]);
+    kb_tables_combine<<<(unsigned)bl.n_blocks[kBTabComb], 256, 0, s>>>(d, bl.map[kBTabComb]);
+    kb_J_partial<<<(unsigned)bl.n_blocks[kBJPart], kJThreads, 0, s>>>(d, bl.map[kBJPart]);
+    kb_J_final<<<blocks(bl.n_inst, 128), 128, 0, s>>>(bl.insts, bl.n_inst);
 }
 
 void launch_J_fast(const Geom& g, const FastView& f, const double* px,

@@ -151,7 +151,7 @@ static ucp_status refresh_costs(ucp_inst* in, int slot) {
     return check(in, "refresh");
 }
 
-static ucp_status grow_history(ucp_inst* in, long long need) {
+ucp_status grow_history(ucp_inst* in, long long need) {
     if (need <= in->hist_cap) return UCP_OK;
     long long cap = in->hist_cap;
     while (cap < need) cap *= 2;
@@ -183,7 +183,8 @@ size_t inst_bytes(const Geom& g, int precision) {
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
              2 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
              rnd(8 * 47) + 2 * rnd(8 * (size_t)fp.n_chunks * ny) +
-             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4);
+             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) +
+             rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos);
     }
     return b;
 }
@@ -204,7 +205,8 @@ static void fast_bounds(ucp_inst* in, double B) {
     // serial sum of the plain path + double-float 64-tap blocks + FP64
     // combination + double-float evaluation of the identity
     const double rel = (double)g.n_w * u + (2.0 * 64 + 16) * uf2 +
-                       ((double)g.n_w / 64.0 + 8.0) * u + 60.0 * uf2;
+                       2.0 * ((double)in->fv.tab_span / 64.0 + 2.0) * uf2 +
+                       ((double)in->fv.tab_splits + 8.0) * u + 60.0 * uf2;
     f.beta_rel = (float)(1.25 * rel);
     // rounding of grid positions, of E = U - y and of the residuals of both
     // evaluations: |d(residual)| <= u A
@@ -247,11 +249,12 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.partN = (double*)A.get(8 * (size_t)f.n_chunks * ny);
     f.partD = (double*)A.get(8 * (size_t)f.n_chunks * ny);
     f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
+    f.tab_part = (double*)A.get(24 * (size_t)f.tab_splits * (size_t)f.n_pos);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf ||
         !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.psi ||
-        !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.W2_dev || !f.n_exact) {
+        !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.tab_part || !f.W2_dev || !f.n_exact) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
     }

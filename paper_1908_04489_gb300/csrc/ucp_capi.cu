@@ -69,7 +69,7 @@ const char* make_geom(const ucp_params& p, Geom* g) {
     g->q = 2 * c;
     // lattice indices of every reachable value must stay far inside int64
     const double reach = (double)(g->hr + g->hx + g->hy + 2 * g->q) * (double)g->one;
-    if (reach > 4.0e15) return "grid extent too large for the candidate lattice";
+    if (reach > 8.0e12) return "grid extent too large for the candidate lattice";
     g->k = p.k;
     g->kk = p.k * p.k;
     g->sigma = p.sigma;

@@ -61,6 +61,8 @@ struct FastPlan {
     int run;           // targets per thread of the u1 recurrence
     int64_t j_blocks;  // block rows of the u1 kernel
     int64_t J_blocks;  // blocks of the J reduction
+    int64_t tab_span;  // taps per block column of the table kernel
+    int tab_splits;    // block columns of the table kernel
 };
 
 struct dfloat;  // df.cuh
@@ -89,6 +91,7 @@ struct FastView : FastPlan {
     double* partN;       // [n_chunks * n_y] numerator partials
     double* partD;       // [n_chunks * n_y] denominator partials
     double* Jpart;       // [J_blocks]
+    double* tab_part;    // [tab_splits * 3 * n_pos] table partial sums
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
     double W2;           // host copy of *W2_dev
@@ -100,6 +103,44 @@ struct FastView : FastPlan {
     float beta_rel;      // |table cost - serial cost| <= beta_rel M
     float beta_abs;      //   + beta_abs (2 sqrt(M) + 1)
     float beta_ctl;      //   + beta_ctl sqrt(control term) + ...
+};
+
+// Device-resident descriptor of one instance of a batch: everything a batched
+// kernel needs, with the sweep state kept on the device so that one captured
+// sweep serves every sweep.
+struct InstDev {
+    Geom g;
+    FastView f;
+    int64_t* nu[2];    // controller, double buffered
+    int32_t* idx;      // winner list positions
+    double* px;        // prior weights
+    double* U;         // u1 table
+    double* Ud;        // U_{j+1} - U_j
+    double* J;         // J history
+    int32_t cur;       // nu[cur] holds f
+    int32_t sweeps;    // sweeps done (J history slot of the current J)
+};
+
+// Block of a batched launch: which instance, which block of its own grid.
+struct BlockRef {
+    int32_t inst;
+    int32_t local;
+};
+
+// Device arrays describing one batched sweep.
+struct BatchLaunch {
+    InstDev* insts;
+    int n_inst;
+    int G;                       // n_refine shared by the batch
+    const BlockRef* map[8];      // per kernel kind (see BatchKind)
+    int64_t n_blocks[8];
+    const BlockRef* mmse_map[5]; // mmse_main per run length 1, 2, 4, 8, 16
+    int64_t mmse_blocks[5];
+};
+
+enum BatchKind {
+    kBSearch = 0, kBPerX = 1, kBShift = 2, kBPerY = 3, kBTabPart = 4,
+    kBTabComb = 5, kBBuildE = 6, kBJPart = 7
 };
 
 // ---- plain FP64 path (kernels_plain.cu) --------------------------------

@@ -83,6 +83,8 @@ size_t inst_bytes(const Geom& g, int precision);
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
                      const Geom& g, cudaStream_t stream);
 ucp_status inst_sweep(ucp_inst* in, int n);
+// Make room in the J history for `need` entries (synchronises on growth).
+ucp_status grow_history(ucp_inst* in, long long need);
 ucp_status inst_sync(ucp_inst* in);
 ucp_status inst_read(ucp_inst* in, const void* dev, void* host, size_t bytes);
 ucp_status inst_get(ucp_inst* in, double* f, double* u1, int as_u0, int32_t* idx);
