@@ -64,27 +64,36 @@ def init_table(p):
     return np.where(a == 0, 0.0, np.sign(a) * 3.5 * (2 * m + 1))
 
 
-# ---- algorithmic work per kernel launch (FP64 flops) ----------------------
+# ---- algorithmic work per kernel launch ----------------------------------
+# The fast path runs in double-float on the FP32 pipe; work is counted in FP32
+# flops of its double-float operations (FADD/FMUL 1, FFMA 2):
+#   df_add 11, df_mul 10, product-and-accumulate 18.
+#   tables:    per (table position, w tap): 3 x 18 = 54.
+#   mmse_main: per evaluated (source, target): weight-times-f accumulate 18,
+#              weight accumulate 11, two recurrence products 20 = 49; plus
+#              per (source, run) the anchor exponent (40) and exp (90).
+#   search:    per (x_i, candidate): two screened evaluations of the
+#              three-correlation identity, 233 each.
+# The plain FP64 path counts FP64 flops: 6 per quadrature term.
+FLOPS_TABLE_TAP = 54.0
+FLOPS_U1_PAIR = 49.0
+FLOPS_U1_ANCHOR = 130.0
+FLOPS_SEARCH_CAND = 466.0
 
-def kernel_work(p, sizes):
-    """Algorithmic FP64 flops per launch of each kernel.
 
-    search: one quadrature term per (x_i, refinement candidate, w_l) =
-    lerp mul + add, residual sub, square, weight mul, accumulate = 6 flops.
-    mmse:   per (y_j, x_i): residual, square, halve, prior add, shift,
-    numerator multiply-add, denominator add = 8 flops (+ one exp).
-    S lists: 6 flops per (value, w_l).  J: 5 flops per x_i.
-    """
+def kernel_work(p, sizes, counters, launches):
     nx, nw, ny = sizes["n_x"], sizes["n_w"], sizes["n_y"]
     L, R = p["n_levels"], p["n_refine"]
+    if p["precision"] == 0:
+        return {"search": (nx * L * R * nw * 6.0, "fp64"),
+                "mmse": (nx * ny * 8.0, "fp64")}
+    run = sizes.get("run", 16)
+    n_pos = sizes.get("n_pos", 0)
+    pairs = counters.get("u1_pairs", 0) / max(1, launches.get("mmse_main", 1))
     return {
-        "search": nx * L * R * nw * 6.0,
-        "mmse": nx * ny * 8.0,
-        "mmse_main": nx * ny * 8.0,
-        "tables": sizes.get("n_pos", 0) * nw * 6.0,
-        "S_f": nx * nw * 6.0,
-        "S_coarse": p["n_coarse"] * nw * 6.0,
-        "J": nx * 5.0,
+        "tables": (n_pos * nw * FLOPS_TABLE_TAP, "fp32"),
+        "mmse_main": (pairs * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR), "fp32"),
+        "search": (nx * sizes["n_cand"] * FLOPS_SEARCH_CAND, "fp32"),
     }
 
 
@@ -94,9 +103,6 @@ def load_peaks():
         return json.load(open(path))
     except Exception:
         return {}
-
-
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (dense), from the platform table
 
 
 # ---- clocks ---------------------------------------------------------------
@@ -191,6 +197,95 @@ def oracle_sample(p, budget_s=12.0, threads=None):
 
 # ---- GPU arm --------------------------------------------------------------
 
+def fast_sizes(p, binding):
+    """Table positions and u1 run length of the fast path (mirrors the
+    library's plan: reach of the candidate lattice, run length rule)."""
+    d = p["delta"]
+    hx = round(p["x_half"] / d); hw = round(p["w_half"] / d)
+    hy = round(p["y_half"] / d); hr = round(p["cand_half"] / d)
+    q = 2 * max(1, -(-hr // (p["n_coarse"] - 1)))
+    reach = (p["n_coarse"] - 1) * (q // 2) + 2 * q
+    ext = max(reach, hx + 2 * q) + 2
+    s = dict(binding.plan(p))
+    s["n_pos"] = 2 * ext + 2
+    F = max(hr + 2 * q, hx) * d
+    slope = d * (hy * d + F)
+    run = 16
+    while run > 1 and (run - 1) * slope > 15.0:
+        run //= 2
+    s["run"] = run
+    return s
+
+
+def measure_batched(args, binding, torch, stream, flush):
+    """c3: 256 uneven instances solved (setup + 10 sweeps + J) as one batch,
+    one at a time on the same fast path, and one at a time on the plain FP64
+    path (a sample, extrapolated by grid work)."""
+    from paper_1908_04489_gb300 import workloads as W
+    ps = W.c3()
+    n = len(ps)
+
+    def batch_solve():
+        b = binding.Batch(ps, stream=stream)
+        b.sweep(10)
+        return b
+
+    for _ in range(2):
+        b = batch_solve(); b.eval_J(); b.close()
+    times = []
+    for _ in range(max(1, args.batch_steps)):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b = batch_solve()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        Jb = b.eval_J()
+        b.close()
+    t_batch = float(np.median(times)) / 1e3
+    # one at a time, same fast path
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    e0.record(stream)
+    insts = []
+    for p in ps:
+        inst = binding.Instance(p, stream=stream)
+        inst.sweep(10)
+        insts.append(inst)
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    Js = np.array([i.eval_J() for i in insts])
+    for i in insts:
+        i.close()
+    # plain FP64 path on a sample, extrapolated by sum of n_x * n_w
+    pick = list(range(0, n, max(1, n // args.plain_sample)))[:args.plain_sample]
+    work = lambda p: binding.plan(p)["n_x"] * binding.plan(p)["n_w"]
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in pick:
+        inst = binding.Instance(dict(ps[k], precision=0), stream=stream)
+        inst.sweep(10)
+        inst.close()
+    e1.record(stream)
+    e1.synchronize()
+    t_plain_sample = e0.elapsed_time(e1) / 1e3
+    t_plain = t_plain_sample * sum(work(p) for p in ps) / sum(work(ps[k]) for k in pick)
+    return {
+        "workload": "c3: 256 Witsenhausen instances (seed 1908), k log-U[0.05,0.5], "
+                    "sigma U[1,10], delta in {0.01,0.02}, 533..9959 x0 points, "
+                    "identity init, 10 sweeps",
+        "solves_per_s": n / t_batch, "ms_per_batch": t_batch * 1e3,
+        "one_at_a_time_fast_solves_per_s": n / t_seq,
+        "plain_fp64_solves_per_s": n / t_plain,
+        "plain_fp64_sample": f"{len(pick)} of {n} instances, extrapolated by n_x*n_w",
+        "batched_vs_one_at_a_time": t_seq / t_batch,
+        "batched_vs_plain_fp64": t_plain / t_batch,
+        "max_abs_J_batched_vs_one_at_a_time": float(np.max(np.abs(Jb - Js))),
+    }
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -209,19 +304,12 @@ def run_gpu(args):
     binding.load()
 
     p, desc = workload(args.workload, args.precision)
-    sizes = binding.plan(p)
+    sizes = fast_sizes(p, binding)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    peaks = binding.probe_alu(stream)
 
-    def solve(profile=False):
-        inst = binding.Instance(p, stream=stream)
-        if profile:
-            inst.profile(True)
-        inst.sweep(p["sweeps"])
-        return inst
-
-    # cpu baseline first (host only, before any timing)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample, spent = oracle_sample(p, args.cpu_budget)
@@ -229,7 +317,8 @@ def run_gpu(args):
                "sample": sample, "seconds": round(spent, 2)}
 
     for _ in range(args.warmup):
-        inst = solve()
+        inst = binding.Instance(p, stream=stream)
+        inst.sweep(p["sweeps"])
         inst.eval_J()
         inst.close()
     torch.cuda.synchronize()
@@ -238,6 +327,7 @@ def run_gpu(args):
     clocks = Clocks(local)
     clocks.start()
     step_ms, Js, kern = [], [], {}
+    counters = {"recosts": 0, "u1_pairs": 0}
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -252,13 +342,16 @@ def run_gpu(args):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        for k, (n, ms) in inst.kernel_times().items():
+        for k, (nl, ms) in inst.kernel_times().items():
             a = kern.setdefault(k, [0, 0.0])
-            a[0] += n
+            a[0] += nl
             a[1] += ms
         Js.append(inst.eval_J())
-        recosts = inst.tie_recosts()
-        last = inst
+        for k, v in inst.work_counters().items():
+            counters[k] += v
+        if len(Js) < args.steps:
+            inst.close()
+    last = inst
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -270,7 +363,6 @@ def run_gpu(args):
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
 
-    # parity of the reported J: recompute J with the oracle from the GPU state
     parity = None
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -306,17 +398,32 @@ def run_gpu(args):
            "h2d_bytes_per_step": int(table.nbytes),
            "d2h_bytes_per_step": int(out["f"].nbytes + out["U"].nbytes + 8)}
 
-    # ---- roofline of the dominant kernel (FP64 ALU bound)
-    work = kernel_work(p, sizes)
-    dom = max(kern, key=lambda k: kern[k][1])
-    launches, ms = kern[dom]
-    avg_s = ms / launches / 1e3
-    achieved = work.get(dom, 0.0) / avg_s / 1e12
-    peak = FP64_NOMINAL_TFLOPS
+    # ---- roofline of the dominant kernel (ALU bound)
+    launches = {k: v[0] for k, v in kern.items()}
+    work = kernel_work(p, sizes, {k: v / args.steps for k, v in counters.items()},
+                       {k: v / args.steps for k, v in launches.items()})
+    dom = max((k for k in kern if k in work), key=lambda k: kern[k][1])
+    nl, ms = kern[dom]
+    avg_s = ms / nl / 1e3
+    flops, pipe = work[dom]
+    peak = peaks["fp32_tflops"] if pipe == "fp32" else peaks["fp64_tflops"]
+    achieved = flops / avg_s / 1e12
+    per_kernel = {}
+    for k, (w, pp) in work.items():
+        if k in kern:
+            a_ = w / (kern[k][1] / kern[k][0] / 1e3) / 1e12
+            pk = peaks["fp32_tflops"] if pp == "fp32" else peaks["fp64_tflops"]
+            per_kernel[k] = {"achieved_tflops": a_, "frac": a_ / pk,
+                             "ms_per_launch": kern[k][1] / kern[k][0]}
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "FP64 dense nominal (no measured FP64 peak)",
-                "share_of_step": ms / total_ms}
+                "peak_source": f"measured {pipe.upper()} FMA throughput "
+                               "(ucp_probe_alu, this run)",
+                "share_of_step": ms / total_ms, "per_kernel": per_kernel}
+
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = measure_batched(args, binding, torch, stream, flush)
     if rank != 0:
         return
     line = {
@@ -333,8 +440,11 @@ def run_gpu(args):
         "gpu_launches": int(sum(v[0] for v in kern.values())),
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kern.items()},
         "roofline": roofline, "e2e": e2e, "clocks": clk, "parity": parity,
-        "tie_recosts_per_solve": recosts,
+        "work_per_solve": {k: v / args.steps for k, v in counters.items()},
+        "alu_peaks_measured": peaks,
     }
+    if batched is not None:
+        line["batched"] = batched
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -392,6 +502,9 @@ def main():
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="only build one instance and run this many sweeps "
                          "(a short, fixed launch sequence for ncu)")

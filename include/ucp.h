@@ -161,6 +161,13 @@ UCP_API ucp_status ucp_destroy(ucp_inst* inst);
  * creation; 0 on the plain path).  Synchronises. */
 UCP_API ucp_status ucp_tie_recosts(ucp_inst* inst, int64_t* out);
 
+/* Work counters since creation (fast path; zeros on the plain path):
+ * recosts = as ucp_tie_recosts; u1_pairs = (source, run of targets) pairs
+ * the u1 kernel evaluated (the rest were skipped as negligible).  Either
+ * output may be NULL.  Synchronises. */
+UCP_API ucp_status ucp_work_counters(ucp_inst* inst, int64_t* recosts,
+                                     int64_t* u1_pairs);
+
 /* Per-kernel CUDA-event timing on the instance stream (off by default).
  * ucp_kernel_times fills up to cap entries: name (static), launches and
  * total milliseconds since the last reset; returns the entry count. */

@@ -103,6 +103,8 @@ def load():
     L.ucp_kernel_times.restype = ctypes.c_int32
     L.ucp_tie_recosts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.ucp_probe_alu.argtypes = [_dp, _dp, _dp, _vp]
+    L.ucp_work_counters.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)]
     L.ucp_batch_create.argtypes = [_vp, P, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
     L.ucp_batch_sweep.argtypes = [_vp, ctypes.c_int32]
     L.ucp_batch_eval_J.argtypes = [_vp, _dp]
@@ -259,6 +261,12 @@ class Instance:
         ms = (ctypes.c_double * cap)()
         n = L.ucp_kernel_times(self.h, names, launches, ms, cap)
         return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+    def work_counters(self) -> dict:
+        r, p = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().ucp_work_counters(self.h, ctypes.byref(r), ctypes.byref(p)),
+               "ucp_work_counters")
+        return {"recosts": r.value, "u1_pairs": p.value}
 
     def tie_recosts(self) -> int:
         v = ctypes.c_int64()

@@ -621,6 +621,7 @@ __device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
     dfloat N[R], D[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) { N[k] = {0.f, 0.f}; D[k] = {0.f, 0.f}; }
+    unsigned evaluated = 0;   // (source, run) pairs not skipped
     for (int64_t b = c0; b < c1; b += kMmseSrc) {
         const int cnt = (int)min((int64_t)kMmseSrc, c1 - b);
         __syncthreads();
@@ -643,6 +644,7 @@ __device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
                 if (fmaf(0.5f * dmin, dmin, spr[s].hi) <= cut) sel[ns++] = s;
             }
             if (ns == 0) break;
+            evaluated += (unsigned)ns;
             dfloat w[2], F[2], fv[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -671,6 +673,8 @@ __device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
             }
         }
     }
+    if (f.n_pairs && evaluated) atomicAdd((unsigned long long*)f.n_pairs,
+                                          (unsigned long long)evaluated);
     double* pN = f.partN + (size_t)by * g.n_y;
     double* pD = f.partD + (size_t)by * g.n_y;
 #pragma unroll

@@ -183,7 +183,7 @@ size_t inst_bytes(const Geom& g, int precision) {
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
              2 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
              rnd(8 * 47) + 2 * rnd(8 * (size_t)fp.n_chunks * ny) +
-             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) +
+             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) + rnd(8) +
              rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos);
     }
     return b;
@@ -252,9 +252,10 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.tab_part = (double*)A.get(24 * (size_t)f.tab_splits * (size_t)f.n_pos);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
+    f.n_pairs = (int64_t*)A.get(8);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf ||
         !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.psi ||
-        !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.tab_part || !f.W2_dev || !f.n_exact) {
+        !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.tab_part || !f.W2_dev || !f.n_exact || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
     }
@@ -330,6 +331,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     if (in->fast) {
         UCP_LAUNCH(in, "fast_setup", launch_fast_setup(g, in->fv, s));
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
+        cudaMemsetAsync(in->fv.n_pairs, 0, 8, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
         fast_set_W2(in);

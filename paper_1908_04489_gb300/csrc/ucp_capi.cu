@@ -301,3 +301,19 @@ extern "C" ucp_status ucp_tie_recosts(ucp_inst* in, int64_t* out) {
     if (st == UCP_OK) *out = v;
     return st;
 }
+
+extern "C" ucp_status ucp_work_counters(ucp_inst* in, int64_t* recosts,
+                                        int64_t* u1_pairs) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    int32_t r = 0;
+    int64_t p = 0;
+    if (in->fast) {
+        cudaMemcpyAsync(&r, in->fv.n_exact, 4, cudaMemcpyDeviceToHost, in->stream);
+        ucp_status st = inst_read(in, in->fv.n_pairs, &p, 8);
+        if (st != UCP_OK) return st;
+    }
+    if (recosts) *recosts = r;
+    if (u1_pairs) *u1_pairs = p;
+    return UCP_OK;
+}

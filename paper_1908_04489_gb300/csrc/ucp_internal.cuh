@@ -94,6 +94,7 @@ struct FastView : FastPlan {
     double* tab_part;    // [tab_splits * 3 * n_pos] table partial sums
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
+    int64_t* n_pairs;    // (source, run) pairs evaluated by the u1 kernel
     double W2;           // host copy of *W2_dev
     float W2hi, W2lo;    // W2 as double-float
     float sqrtW2;
