@@ -178,8 +178,8 @@ UCP_API int32_t ucp_kernel_times(ucp_inst* inst, const char** names,
 /* ---- batches ------------------------------------------------------------ */
 
 /* Many instances swept together: params is a host array of n parameter sets
- * (different k, sigma, delta and grid widths allowed; all precision 1 and
- * the same n_refine).  Each instance is set up as by ucp_create on `stream`;
+ * (different k, sigma, delta, grid widths and n_refine allowed; all
+ * precision 1).  Each instance is set up as by ucp_create on `stream`;
  * a batched sweep then runs each kernel once for all instances (blocks mapped
  * to instances by a table) from a captured CUDA graph when `stream` is not
  * the default stream.  Every instance gets the same results as alone: the
@@ -197,6 +197,54 @@ UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out);
  * ...); owned by the batch, valid until ucp_batch_destroy. */
 UCP_API ucp_status ucp_batch_instance(ucp_batch* b, int32_t k, ucp_inst** out);
 UCP_API ucp_status ucp_batch_destroy(ucp_batch* b);
+
+/* ---- serving: continuous batching of solve requests ----------------------- */
+
+/* Result of a served request (times in seconds since the server started). */
+typedef struct {
+    double J;            /* J after the last sweep                         */
+    double t_submit;     /* ucp_submit returned                            */
+    double t_admit;      /* admitted to a slot (set up on the GPU)         */
+    double t_done;       /* results copied to host memory                  */
+    int32_t sweeps;
+    int32_t status;      /* ucp_status of the request                      */
+} ucp_result;
+
+typedef struct {
+    int64_t queued;       /* submitted, waiting for a slot or for HBM      */
+    int64_t in_flight;    /* admitted or done but not yet polled           */
+    int64_t steps;        /* batched sweeps launched                       */
+    int64_t completed;
+    int32_t max_active;   /* most requests swept together so far           */
+    uint64_t bytes_in_use;
+    double now;           /* seconds since the server started              */
+} ucp_srv_info;
+
+/* Start a server on ctx's device: at most max_slots requests on the GPU at
+ * once, and their device bytes (as ucp_plan reports, plus the J history)
+ * within hbm_budget_bytes.  A server thread runs the steps on `stream`;
+ * served instances take device memory from a pool owned by the server. */
+UCP_API ucp_status ucp_srv_create(ucp_ctx* ctx, uint64_t hbm_budget_bytes,
+                                  int32_t max_slots, void* stream, ucp_srv** out);
+/* Queue one solve (params copied, including an init table) of n_sweeps
+ * sweeps; never blocks.  UCP_E_BUDGET if the request alone exceeds the
+ * budget; otherwise it waits for a slot and memory.  Thread-safe. */
+UCP_API ucp_status ucp_submit(ucp_srv* s, const ucp_params* params, int32_t n_sweeps,
+                              uint64_t* ticket);
+/* UCP_PENDING until the request is done; then fills res (may be NULL) and
+ * the host buffers f (n_x) and u1 (n_y) (either may be NULL), forgets the
+ * ticket and returns the request's status.  UCP_E_NOTFOUND for an unknown
+ * or already collected ticket.  Thread-safe. */
+UCP_API ucp_status ucp_poll(ucp_srv* s, uint64_t ticket, ucp_result* res, double* f,
+                            uint64_t n_x, double* u1, uint64_t n_y);
+UCP_API ucp_status ucp_srv_stats(ucp_srv* s, ucp_srv_info* info);
+/* Failure drill on the host: the next step fails as a launch would (every
+ * request in flight and queued ends with UCP_E_CUDA, later submissions get
+ * UCP_E_STATE).  No device fault is involved. */
+UCP_API ucp_status ucp_srv_fail_next_step(ucp_srv* s);
+/* Stop the server thread and free everything; UCP_E_STATE if requests were
+ * still pending (they are discarded), else UCP_OK. */
+UCP_API ucp_status ucp_srv_destroy(ucp_srv* s);
 
 /* Measured ALU throughput of the current device (no paper counterpart: the
  * denominators of the roofline fractions of the ALU-bound kernels): FP64

@@ -53,6 +53,21 @@ class Params(ctypes.Structure):
         return obj
 
 
+class Result(ctypes.Structure):
+    """Mirror of ``ucp_result``."""
+    _fields_ = [("J", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("sweeps", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class SrvInfo(ctypes.Structure):
+    """Mirror of ``ucp_srv_info``."""
+    _fields_ = [("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("max_active", ctypes.c_int32), ("bytes_in_use", ctypes.c_uint64),
+                ("now", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -105,6 +120,14 @@ def load():
     L.ucp_probe_alu.argtypes = [_dp, _dp, _dp, _vp]
     L.ucp_work_counters.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]
+    L.ucp_srv_create.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int32, _vp,
+                                 ctypes.POINTER(_vp)]
+    L.ucp_submit.argtypes = [_vp, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+    L.ucp_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(Result), _dp, _u64,
+                           _dp, _u64]
+    L.ucp_srv_stats.argtypes = [_vp, ctypes.POINTER(SrvInfo)]
+    L.ucp_srv_fail_next_step.argtypes = [_vp]
+    L.ucp_srv_destroy.argtypes = [_vp]
     L.ucp_batch_create.argtypes = [_vp, P, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
     L.ucp_batch_sweep.argtypes = [_vp, ctypes.c_int32]
     L.ucp_batch_eval_J.argtypes = [_vp, _dp]
@@ -344,6 +367,78 @@ class Batch:
                 m.h = None
             _check(load().ucp_batch_destroy(self.h), "ucp_batch_destroy")
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (``ucp_srv_*``, ``ucp_submit``,
+    ``ucp_poll``)."""
+
+    def __init__(self, hbm_budget_bytes=8 << 30, max_slots=256, stream=None,
+                 ctx: Context | None = None):
+        import torch
+        L = load()
+        self.ctx = ctx or default_context()
+        if stream is None:
+            stream = torch.cuda.Stream(self.ctx.device)
+        self.stream = stream
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        h = _vp()
+        _check(L.ucp_srv_create(self.ctx.h, int(hbm_budget_bytes), int(max_slots),
+                                _vp(sp), ctypes.byref(h)), "ucp_srv_create")
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, params, sweeps=None, table=None) -> int:
+        p = Params.from_dict(params, table)
+        t = ctypes.c_uint64()
+        n = int(params.get("sweeps", 0) if sweeps is None else sweeps)
+        _check(load().ucp_submit(self.h, ctypes.byref(p), n, ctypes.byref(t)),
+               "ucp_submit")
+        pl = plan(params)
+        self._sizes[t.value] = (pl["n_x"], pl["n_y"])
+        return t.value
+
+    def poll(self, ticket, want_arrays=True):
+        """None while pending; else a dict with J, times, f, U."""
+        nx, ny = self._sizes.get(ticket, (0, 0))
+        f = np.empty(nx) if want_arrays else None
+        U = np.empty(ny) if want_arrays else None
+        res = Result()
+        st = load().ucp_poll(self.h, ticket, ctypes.byref(res), _ptr(f, ctypes.c_double),
+                             nx, _ptr(U, ctypes.c_double), ny)
+        if st == UCP_PENDING:
+            return None
+        self._sizes.pop(ticket, None)
+        _check(st, "ucp_poll")
+        return dict(J=res.J, t_submit=res.t_submit, t_admit=res.t_admit,
+                    t_done=res.t_done, sweeps=res.sweeps, f=f, U=U)
+
+    def stats(self) -> dict:
+        info = SrvInfo()
+        _check(load().ucp_srv_stats(self.h, ctypes.byref(info)), "ucp_srv_stats")
+        return {k: getattr(info, k) for k, _ in SrvInfo._fields_}
+
+    def fail_next_step(self):
+        _check(load().ucp_srv_fail_next_step(self.h), "ucp_srv_fail_next_step")
+
+    def close(self):
+        if getattr(self, "h", None):
+            st = load().ucp_srv_destroy(self.h)
+            self.h = None
+            return st
+        return 0
 
     def __enter__(self):
         return self

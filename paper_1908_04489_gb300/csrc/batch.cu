@@ -11,8 +11,7 @@
 
 #include <vector>
 
-#include "ucp_fast.cuh"
-#include "ucp_runtime.h"
+#include "batch_set.h"
 
 using namespace ucp;
 
@@ -21,24 +20,16 @@ struct ucp_batch {
     cudaStream_t stream = nullptr;
     std::vector<ucp_inst*> members;
     Arena arena;
-    BatchLaunch bl{};
-    std::vector<InstDev> desc;
+    BatchSet bs;
     double* J_gather = nullptr;   // [n] device
     bool poisoned = false;
     cudaGraphExec_t graph = nullptr;
     bool graph_tried = false;
 };
 
-namespace {
+namespace ucp {
 
-ucp_status fail(ucp_batch* b, const char* where) {
-    const cudaError_t e = cudaGetLastError();
-    b->poisoned = true;
-    set_error("%s: %s", where, cudaGetErrorString(e));
-    return UCP_E_CUDA;
-}
-
-InstDev describe(const ucp_inst* in) {
+InstDev describe_inst(const ucp_inst* in) {
     InstDev d;
     memset(&d, 0, sizeof(d));
     d.g = in->g;
@@ -55,7 +46,102 @@ InstDev describe(const ucp_inst* in) {
     return d;
 }
 
-int run_slot(int R) { return R >= 16 ? 4 : (R >= 8 ? 3 : (R >= 4 ? 2 : (R >= 2 ? 1 : 0))); }
+static int run_slot(int R) {
+    return R >= 16 ? 4 : (R >= 8 ? 3 : (R >= 4 ? 2 : (R >= 2 ? 1 : 0)));
+}
+
+static int refine_slot(int G) {
+    return G >= 32 ? 4 : (G >= 16 ? 3 : (G >= 8 ? 2 : (G >= 4 ? 1 : 0)));
+}
+
+ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
+                            cudaStream_t s) {
+    const size_t n = members.size();
+    bs.desc.resize(n);
+    for (size_t k = 0; k < n; ++k) bs.desc[k] = describe_inst(members[k]);
+    if (n) cudaMemcpyAsync(bs.insts, bs.desc.data(), sizeof(InstDev) * n,
+                           cudaMemcpyHostToDevice, s);
+    return cudaGetLastError() == cudaSuccess ? UCP_OK : UCP_E_CUDA;
+}
+
+ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
+                          cudaStream_t s) {
+    const size_t n = members.size();
+    std::vector<BlockRef> maps[8], smaps[5], mmaps[5];
+    for (size_t k = 0; k < n; ++k) {
+        const ucp_inst* in = members[k];
+        for (int kind = 1; kind < 8; ++kind) {
+            const int64_t nb = batch_blocks(in->g, in->fv, kind);
+            for (int64_t x = 0; x < nb; ++x) maps[kind].push_back({(int32_t)k, (int32_t)x});
+        }
+        std::vector<BlockRef>& sm = smaps[refine_slot(in->g.n_refine)];
+        const int64_t ns = batch_blocks(in->g, in->fv, kBSearch);
+        for (int64_t x = 0; x < ns; ++x) sm.push_back({(int32_t)k, (int32_t)x});
+        std::vector<BlockRef>& mm = mmaps[run_slot(in->fv.run)];
+        const int64_t nm = batch_mmse_blocks(in->g, in->fv);
+        for (int64_t x = 0; x < nm; ++x) mm.push_back({(int32_t)k, (int32_t)x});
+    }
+    bs.host_maps.clear();
+    size_t off[8], soff[5], moff[5];
+    for (int kind = 0; kind < 8; ++kind) {
+        off[kind] = bs.host_maps.size();
+        bs.host_maps.insert(bs.host_maps.end(), maps[kind].begin(), maps[kind].end());
+    }
+    for (int r = 0; r < 5; ++r) {
+        soff[r] = bs.host_maps.size();
+        bs.host_maps.insert(bs.host_maps.end(), smaps[r].begin(), smaps[r].end());
+    }
+    for (int r = 0; r < 5; ++r) {
+        moff[r] = bs.host_maps.size();
+        bs.host_maps.insert(bs.host_maps.end(), mmaps[r].begin(), mmaps[r].end());
+    }
+    // grow the device buffers (after the stream drains, as they may be in use)
+    if (n > bs.insts_cap || bs.host_maps.size() > bs.maps_cap) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return UCP_E_CUDA;
+        if (n > bs.insts_cap) {
+            if (bs.insts) bs.arena->put(bs.insts);
+            bs.insts_cap = n + n / 2 + 8;
+            bs.insts = (InstDev*)bs.arena->get(sizeof(InstDev) * bs.insts_cap);
+        }
+        if (bs.host_maps.size() > bs.maps_cap) {
+            if (bs.maps) bs.arena->put(bs.maps);
+            bs.maps_cap = bs.host_maps.size() + bs.host_maps.size() / 2 + 64;
+            bs.maps = (BlockRef*)bs.arena->get(sizeof(BlockRef) * bs.maps_cap);
+        }
+        if (!bs.insts || !bs.maps) {
+            bs.insts_cap = bs.maps_cap = 0;
+            return UCP_E_NOMEM;
+        }
+    }
+    if (!bs.host_maps.empty())
+        cudaMemcpyAsync(bs.maps, bs.host_maps.data(), sizeof(BlockRef) * bs.host_maps.size(),
+                        cudaMemcpyHostToDevice, s);
+    BatchLaunch& bl = bs.bl;
+    bl.insts = bs.insts;
+    bl.n_inst = (int)n;
+    for (int kind = 0; kind < 8; ++kind) {
+        bl.map[kind] = bs.maps + off[kind];
+        bl.n_blocks[kind] = (int64_t)maps[kind].size();
+    }
+    for (int r = 0; r < 5; ++r) {
+        bl.search_map[r] = bs.maps + soff[r];
+        bl.search_blocks[r] = (int64_t)smaps[r].size();
+        bl.mmse_map[r] = bs.maps + moff[r];
+        bl.mmse_blocks[r] = (int64_t)mmaps[r].size();
+    }
+    return batchset_refresh(bs, members, s);
+}
+
+}  // namespace ucp
+
+namespace {
+
+ucp_status fail(ucp_batch* b, const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    b->poisoned = true;
+    set_error("%s: %s", where, cudaGetErrorString(e));
+    return UCP_E_CUDA;
+}
 
 __global__ void k_gather_J(const InstDev* insts, int n, double* out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,10 +169,6 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
                       "(precision 1)", "");
             return UCP_E_ARG;
         }
-        if (params[k].n_refine != params[0].n_refine) {
-            set_error("ucp_batch_create: %s%s", "all instances must share n_refine", "");
-            return UCP_E_ARG;
-        }
     }
     ucp_batch* b = new ucp_batch();
     b->ctx = ctx;
@@ -102,54 +184,14 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
         }
         b->members.push_back(in);
     }
-    // block maps
-    std::vector<BlockRef> maps[8], mmaps[5];
-    for (int k = 0; k < n; ++k) {
-        const ucp_inst* in = b->members[k];
-        for (int kind = 0; kind < 8; ++kind) {
-            const int64_t nb = batch_blocks(in->g, in->fv, kind);
-            for (int64_t x = 0; x < nb; ++x) maps[kind].push_back({k, (int32_t)x});
-        }
-        const int64_t nb = batch_mmse_blocks(in->g, in->fv);
-        std::vector<BlockRef>& mm = mmaps[run_slot(in->fv.run)];
-        for (int64_t x = 0; x < nb; ++x) mm.push_back({k, (int32_t)x});
-    }
-    BatchLaunch& bl = b->bl;
-    bl.n_inst = n;
-    bl.G = params[0].n_refine;
-    bl.insts = (InstDev*)b->arena.get(sizeof(InstDev) * (size_t)n);
+    b->bs.arena = &b->arena;
     b->J_gather = (double*)b->arena.get(sizeof(double) * (size_t)n);
-    bool ok = bl.insts && b->J_gather;
-    for (int kind = 0; kind < 8 && ok; ++kind) {
-        BlockRef* p = (BlockRef*)b->arena.get(sizeof(BlockRef) * maps[kind].size());
-        ok = p != nullptr;
-        if (ok) cudaMemcpyAsync(p, maps[kind].data(), sizeof(BlockRef) * maps[kind].size(),
-                                cudaMemcpyHostToDevice, b->stream);
-        bl.map[kind] = p;
-        bl.n_blocks[kind] = (int64_t)maps[kind].size();
-    }
-    for (int r = 0; r < 5 && ok; ++r) {
-        bl.mmse_blocks[r] = (int64_t)mmaps[r].size();
-        bl.mmse_map[r] = nullptr;
-        if (mmaps[r].empty()) continue;
-        BlockRef* p = (BlockRef*)b->arena.get(sizeof(BlockRef) * mmaps[r].size());
-        ok = p != nullptr;
-        if (ok) cudaMemcpyAsync(p, mmaps[r].data(), sizeof(BlockRef) * mmaps[r].size(),
-                                cudaMemcpyHostToDevice, b->stream);
-        bl.mmse_map[r] = p;
-    }
-    if (!ok) {
-        set_error("%s%s", "ucp_batch_create: out of device memory", "");
+    ucp_status st = b->J_gather ? batchset_build(b->bs, b->members, b->stream) : UCP_E_NOMEM;
+    if (st == UCP_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = UCP_E_CUDA;
+    if (st != UCP_OK) {
+        set_error("%s%s", "ucp_batch_create: could not build the batch", "");
         for (ucp_inst* m : b->members) ucp_destroy(m);
         cudaStreamSynchronize(b->stream);
-        b->arena.release_all();
-        delete b;
-        return UCP_E_NOMEM;
-    }
-    // the host-side maps must stay valid until the copies are done
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
-        ucp_status st = fail(b, "ucp_batch_create");
-        for (ucp_inst* m : b->members) ucp_destroy(m);
         b->arena.release_all();
         delete b;
         return st;
@@ -162,23 +204,19 @@ extern "C" UCP_API ucp_status ucp_batch_sweep(ucp_batch* b, int32_t n_sweeps) {
     if (!b || n_sweeps < 0) return UCP_E_ARG;
     if (b->poisoned) return UCP_E_STATE;
     if (n_sweeps == 0) return UCP_OK;
-    const int n = (int)b->members.size();
-    b->desc.resize(n);
-    for (int k = 0; k < n; ++k) {
-        ucp_inst* in = b->members[k];
+    for (ucp_inst* in : b->members) {
         if (in->poisoned) return UCP_E_STATE;
         ucp_status st = grow_history(in, in->sweeps_done + 1 + n_sweeps);
         if (st != UCP_OK) return st;
-        b->desc[k] = describe(in);
     }
-    cudaMemcpyAsync(b->bl.insts, b->desc.data(), sizeof(InstDev) * (size_t)n,
-                    cudaMemcpyHostToDevice, b->stream);
+    if (batchset_refresh(b->bs, b->members, b->stream) != UCP_OK)
+        return fail(b, "ucp_batch_sweep");
     // capture one sweep as a graph on a capturable (non-default) stream
     if (!b->graph_tried && b->stream) {
         b->graph_tried = true;
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            launch_batch_sweep(b->bl, b->stream);
+            launch_batch_sweep(b->bs.bl, b->stream);
             if (cudaStreamEndCapture(b->stream, &graph) == cudaSuccess && graph) {
                 if (cudaGraphInstantiate(&b->graph, graph, 0) != cudaSuccess)
                     b->graph = nullptr;
@@ -189,15 +227,13 @@ extern "C" UCP_API ucp_status ucp_batch_sweep(ucp_batch* b, int32_t n_sweeps) {
     }
     for (int s = 0; s < n_sweeps; ++s) {
         if (b->graph) cudaGraphLaunch(b->graph, b->stream);
-        else launch_batch_sweep(b->bl, b->stream);
+        else launch_batch_sweep(b->bs.bl, b->stream);
     }
     if (cudaGetLastError() != cudaSuccess) return fail(b, "ucp_batch_sweep");
     for (ucp_inst* in : b->members) {
         in->sweeps_done += n_sweeps;
         in->cur ^= (n_sweeps & 1);
     }
-    // the descriptors' host copy must outlive the upload
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(b, "ucp_batch_sweep");
     return UCP_OK;
 }
 
@@ -205,11 +241,9 @@ extern "C" UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out) {
     if (!b || !J_out) return UCP_E_ARG;
     if (b->poisoned) return UCP_E_STATE;
     const int n = (int)b->members.size();
-    b->desc.resize(n);
-    for (int k = 0; k < n; ++k) b->desc[k] = describe(b->members[k]);
-    cudaMemcpyAsync(b->bl.insts, b->desc.data(), sizeof(InstDev) * (size_t)n,
-                    cudaMemcpyHostToDevice, b->stream);
-    k_gather_J<<<(n + 127) / 128, 128, 0, b->stream>>>(b->bl.insts, n, b->J_gather);
+    if (batchset_refresh(b->bs, b->members, b->stream) != UCP_OK)
+        return fail(b, "ucp_batch_eval_J");
+    k_gather_J<<<(n + 127) / 128, 128, 0, b->stream>>>(b->bs.insts, n, b->J_gather);
     cudaMemcpyAsync(J_out, b->J_gather, sizeof(double) * (size_t)n,
                     cudaMemcpyDeviceToHost, b->stream);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)

@@ -983,19 +983,18 @@ int64_t batch_mmse_blocks(const Geom&, const FastPlan& fp) {
 
 void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
     const InstDev* d = bl.insts;
-#define UCP_BS(G)                                                                   \
-    case G:                                                                         \
-        kb_search<G><<<(unsigned)bl.n_blocks[kBSearch], 256, 0, s>>>(d, bl.map[kBSearch]); \
-        break;
-    switch (bl.G) {
-        UCP_BS(2)
-        UCP_BS(4)
-        UCP_BS(8)
-        UCP_BS(16)
-        UCP_BS(32)
-        default: break;
+    for (int gi = 0; gi < 5; ++gi) {
+        if (bl.search_blocks[gi] == 0) continue;
+        const unsigned nb = (unsigned)bl.search_blocks[gi];
+        const BlockRef* m = bl.search_map[gi];
+        switch (gi) {
+            case 0: kb_search<2><<<nb, 256, 0, s>>>(d, m); break;
+            case 1: kb_search<4><<<nb, 256, 0, s>>>(d, m); break;
+            case 2: kb_search<8><<<nb, 256, 0, s>>>(d, m); break;
+            case 3: kb_search<16><<<nb, 256, 0, s>>>(d, m); break;
+            default: kb_search<32><<<nb, 256, 0, s>>>(d, m); break;
+        }
     }
-#undef UCP_BS
     kb_sources<<<(unsigned)bl.n_blocks[kBPerX], 256, 0, s>>>(d, bl.map[kBPerX]);
     kb_mmse_shift<<<(unsigned)bl.n_blocks[kBShift], 128, 0, s>>>(d, bl.map[kBShift]);
     kb_mmse_psi<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);

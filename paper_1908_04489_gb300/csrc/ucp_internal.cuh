@@ -132,10 +132,11 @@ struct BlockRef {
 struct BatchLaunch {
     InstDev* insts;
     int n_inst;
-    int G;                       // n_refine shared by the batch
-    const BlockRef* map[8];      // per kernel kind (see BatchKind)
+    const BlockRef* map[8];        // per kernel kind (see BatchKind)
     int64_t n_blocks[8];
-    const BlockRef* mmse_map[5]; // mmse_main per run length 1, 2, 4, 8, 16
+    const BlockRef* search_map[5]; // search per n_refine 2, 4, 8, 16, 32
+    int64_t search_blocks[5];
+    const BlockRef* mmse_map[5];   // mmse_main per run length 1, 2, 4, 8, 16
     int64_t mmse_blocks[5];
 };
 
