@@ -286,6 +286,51 @@ def measure_batched(args, binding, torch, stream, flush):
     }
 
 
+def measure_serving(args, binding, torch):
+    """c4-style stream: requests (k log-U[0.05,0.5], sigma U[1,10], delta in
+    {0.05, 0.01, 0.005}, 20 sweeps) submitted at Poisson arrival times at each
+    rate; latency = result on the host - submission."""
+    from paper_1908_04489_gb300 import workloads as W
+    out = []
+    for rate in args.serve_rates:
+        reqs, times = W.c4(n=args.serve_requests, rate=rate)
+        srv = binding.Server(hbm_budget_bytes=args.serve_budget_gb << 30,
+                             max_slots=args.serve_slots)
+        # warm the server's memory pool with a few requests
+        warm = [srv.submit(r) for r in reqs[:8]]
+        while warm:
+            warm = [t for t in warm if srv.poll(t, want_arrays=False) is None]
+        pending, lat, done_t = {}, [], []
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and times[k] <= now:
+                pending[srv.submit(reqs[k])] = k
+                k += 1
+            for t in list(pending):
+                r = srv.poll(t, want_arrays=False)
+                if r is not None:
+                    lat.append(r["t_done"] - r["t_submit"])
+                    done_t.append(r["t_done"])
+                    del pending[t]
+            if k < len(reqs) and not pending:
+                time.sleep(max(0.0, min(0.001, times[k] - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat) * 1e3
+        out.append({"rate_per_s": rate, "requests": len(reqs),
+                    "solves_per_s": len(reqs) / wall,
+                    "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)),
+                    "max_batch": st["max_active"], "steps": st["steps"]})
+    return {"workload": "c4: Poisson stream, 20 sweeps per request, delta in "
+                        "{0.05,0.01,0.005}, k log-U[0.05,0.5], sigma U[1,10] "
+                        f"({args.serve_requests} requests per rate)",
+            "rates": out}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -424,6 +469,9 @@ def run_gpu(args):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = measure_batched(args, binding, torch, stream, flush)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = measure_serving(args, binding, torch)
     if rank != 0:
         return
     line = {
@@ -445,6 +493,8 @@ def run_gpu(args):
     }
     if batched is not None:
         line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -505,6 +555,12 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--plain-sample", type=int, default=8)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rates", type=float, nargs="+",
+                    default=[100.0, 1000.0, 5000.0])
+    ap.add_argument("--serve-slots", type=int, default=512)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="only build one instance and run this many sweeps "
                          "(a short, fixed launch sequence for ncu)")

@@ -178,3 +178,34 @@ def test_errors_leave_instance_usable(binding):
             inst.sweep(-1)
         inst.sweep(1)
         assert np.isfinite(inst.eval_J())
+
+
+def test_full_size_c5_sampled(binding):
+    """Config c5 at full size (100001 / 14001 / 120001 points, 6 levels): after
+    one sweep, sampled x_i and y_j are recomputed by the oracle from the
+    GPU's own pre-sweep state; decisions must match exactly."""
+    p = W.c5(precision=1)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(13)
+    with binding.Instance(p) as inst:
+        inst.sweep(1)
+        pre = inst.get_controllers()
+        inst.sweep(1)
+        post = inst.get_controllers()
+        Jg = inst.eval_J()
+        recosts = inst.tie_recosts()
+    nu_pre = o.init(2, pre["f"])
+    assert np.array_equal(o.value(nu_pre), pre["f"])
+    oracle.set_threads(16)
+    sel = np.unique(np.concatenate([[0, o.n_x - 1, (o.n_x - 1) // 2],
+                                    rng.integers(0, o.n_x, 29)]))
+    for i in sel:
+        nu1, idx = o.search(nu_pre, pre["U"], i, i + 1)
+        assert idx[i] == post["idx"][i]
+        assert o.value(nu1[i]) == post["f"][i]
+    nu_post = o.init(2, post["f"])
+    for j in np.unique(np.concatenate([[0, o.n_y - 1], rng.integers(0, o.n_y, 12)])):
+        assert abs(o.mmse(nu_post, j, j + 1)[j] - post["U"][j]) <= TOL_U
+    assert abs(o.J(nu_post, post["U"]) - Jg) <= TOL_J
+    oracle.set_threads(1)
+    assert recosts > 0     # level-6 gaps reach the rounding scale
