@@ -77,28 +77,6 @@ __device__ __forceinline__ double exact_term(const Geom& g,
 template <int G>
 __device__ __forceinline__ unsigned group_mask();
 
-// k^2 (u - x_i)^2 + S(u) with S summed over l in order, computed by a group
-// of G lanes: lanes form terms in parallel, every lane adds them in index
-// order (identical sums on all lanes).
-template <int G>
-__device__ double exact_cost_group(const Geom& g, const FastView& f, int64_t i,
-                                   int64_t nu, int lane) {
-    const int64_t cell = nu >> g.shift;
-    const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
-    const int64_t jb = cell - g.hw + g.hy;
-    const double u = value_of(g, nu);
-    double acc = 0.0;
-    for (int64_t l0 = 0; l0 < g.n_w; l0 += G) {
-        const int64_t l = l0 + lane;
-        const double term = l < g.n_w ? exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l) : 0.0;
-        const int cnt = (int)min((int64_t)G, g.n_w - l0);
-        for (int k = 0; k < cnt; ++k)
-            acc = __dadd_rn(acc, __shfl_sync(group_mask<G>(), term, k, G));
-    }
-    const double a = __dsub_rn(u, x_of(g, i));
-    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
-}
-
 // single-lane variant (rare: candidates outside the table range)
 __device__ double exact_cost_lane(const Geom& g, const FastView& f, int64_t i,
                                   int64_t nu) {
@@ -109,6 +87,40 @@ __device__ double exact_cost_lane(const Geom& g, const FastView& f, int64_t i,
     double acc = 0.0;
     for (int64_t l = 0; l < g.n_w; ++l)
         acc = __dadd_rn(acc, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
+    const double a = __dsub_rn(u, x_of(g, i));
+    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
+}
+
+// Serial FP64 costs of up to kTieBatch candidates at once: lane m < M holds
+// candidate m.  For each block of G taps the group forms the terms of every
+// candidate (in `terms`, this group's shared-memory slice of kTieBatch * G
+// doubles); then lane m adds candidate m's terms in tap order.  Each lane's
+// sum is the plain path's serial sum, bit for bit.  Valid in lanes < M.
+constexpr int kTieBatch = 8;
+
+template <int G>
+__device__ double exact_costs_batch(const Geom& g, const FastView& f, int64_t i,
+                                    int lane, int64_t nu, int M, double* terms) {
+    const unsigned gm = group_mask<G>();
+    const int64_t cell = nu >> g.shift;
+    const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy;
+    const double u = value_of(g, nu);
+    double acc = 0.0;
+    for (int64_t l0 = 0; l0 < g.n_w; l0 += G) {
+        const int cnt = (int)min((int64_t)G, g.n_w - l0);
+        for (int m = 0; m < M; ++m) {
+            const int64_t jbm = __shfl_sync(gm, jb, m, G);
+            const double tm = __shfl_sync(gm, t, m, G);
+            const double um = __shfl_sync(gm, u, m, G);
+            terms[m * G + lane] =
+                lane < cnt ? exact_term(g, f.phi, f.U, f.Ud, jbm, tm, um, l0 + lane) : 0.0;
+        }
+        __syncwarp(gm);
+        if (lane < M)
+            for (int k = 0; k < cnt; ++k) acc = __dadd_rn(acc, terms[lane * G + k]);
+        __syncwarp(gm);
+    }
     const double a = __dsub_rn(u, x_of(g, i));
     return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
 }
@@ -248,7 +260,7 @@ __device__ __forceinline__ dfloat df_pm(dfloat v, float b) { return df_add_f(v, 
 template <int G, typename CandFn>
 __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
                         const Best& best, int p0, int p_end, CandFn cand,
-                        int32_t* n_exact) {
+                        int32_t* n_exact, double* tie_terms) {
     const bool have_best = best.pos != INT_MAX;
     // 1. smallest upper end
     dfloat hi = {FLT_MAX, 0.f};
@@ -284,19 +296,33 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         const Eval e = eval_table(g, f, i, vmin);
         return {e.gv, e.beta, pmin, vmin, false, 0.0};
     }
-    // 3. several values in play: serial FP64 costs of each, group-parallel
+    // 3. several values in play: serial FP64 costs of each.  Members are
+    // gathered into lanes (up to kTieBatch per pass) and re-costed together:
+    // the group forms every member's terms, each member's lane adds its own
+    // terms in index order, so all serial chains share one instruction stream.
     double xg = DBL_MAX;
     int32_t xp = INT_MAX;
     int64_t xn = 0;
+    int M = 0;
+    int64_t mnu = 0;
+    int32_t mpos = INT_MAX;
+    auto flush = [&]() {
+        if (M == 0) return;
+        const double v = exact_costs_batch<G>(g, f, i, lane, mnu, M, tie_terms);
+        if (lane < M && before(v, mpos, xg, xp)) { xg = v; xp = mpos; xn = mnu; }
+        if (lane == 0 && n_exact) atomicAdd(n_exact, M);
+        M = 0;
+    };
     if (have_best && !df_lt(hi, df_pm(best.gv, -best.beta))) {
-        double v = best.exact;
-        if (!best.is_exact) {
-            v = exact_cost_group<G>(g, f, i, best.nu, lane);
-            if (lane == 0 && n_exact) atomicAdd(n_exact, 1);
+        if (best.is_exact) {
+            if (lane == 0) { xg = best.exact; xp = best.pos; xn = best.nu; }
+        } else {
+            if (lane == 0) { mnu = best.nu; mpos = best.pos; }
+            M = 1;
         }
-        if (lane == 0) { xg = v; xp = best.pos; xn = best.nu; }
     }
-    // members in list order; each needs every lane for its re-costing
+    const unsigned gm = group_mask<G>();
+    const int base = (threadIdx.x & 31) & ~(G - 1);
     for (int pb = p0; pb < p_end; pb += G) {
         const int p = pb + lane;
         bool member = false;
@@ -306,19 +332,17 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
             const Eval e = eval_table(g, f, i, nu);
             member = !df_lt(hi, df_pm(e.gv, -e.beta));
         }
-        const unsigned gm = group_mask<G>();
-        unsigned mask = __ballot_sync(gm, member);
-        const int base = (threadIdx.x & 31) & ~(G - 1);
-        mask = (mask >> base) & (0xffffffffu >> (32 - G));
+        unsigned mask = (__ballot_sync(gm, member) >> base) & (0xffffffffu >> (32 - G));
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const int64_t mnu = __shfl_sync(gm, nu, src, G);
-            const double v = exact_cost_group<G>(g, f, i, mnu, lane);
-            if (lane == 0 && n_exact) atomicAdd(n_exact, 1);
-            if (lane == src && before(v, p, xg, xp)) { xg = v; xp = p; xn = mnu; }
+            const int64_t cn = __shfl_sync(gm, nu, src, G);
+            if (lane == M) { mnu = cn; mpos = pb + src; }
+            ++M;
+            if (M == kTieBatch) flush();
         }
     }
+    flush();
     glex<G>(xg, xp, xn);
     return {df_from_double(xg), 4.0e-15f * (float)fabs(xg), xp, xn, true, xg};
 }
@@ -328,18 +352,20 @@ __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
                                             const int64_t* __restrict__ nu_pre,
                                             int64_t* __restrict__ nu_out,
                                             int32_t* __restrict__ idx_out,
-                                            int32_t* n_exact, int64_t bx) {
+                                            int32_t* n_exact, double* tie_smem,
+                                            int64_t bx) {
     const int lane = threadIdx.x & (G - 1);
     const int64_t i = (bx * blockDim.x + threadIdx.x) / G;
     const bool active = i < g.n_x;
     const int64_t ic = active ? i : g.n_x - 1;
     const int64_t* coarse = f.coarse;
+    double* tie_terms = tie_smem + (threadIdx.x / G) * (kTieBatch * G);
 
     Best best{{FLT_MAX, 0.f}, 0.f, INT_MAX, 0, false, 0.0};
     const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
     best = resolve<G>(g, f, ic, lane, best, 0, n0,
                       [&](int p) { return stage0_nu(g, nu_pre, coarse, ic, p); },
-                      active ? n_exact : nullptr);
+                      active ? n_exact : nullptr, tie_terms);
     const int half = G / 2;
     int pos = n0;
     for (int lv = 1; lv <= g.n_levels; ++lv) {
@@ -351,7 +377,7 @@ __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
                               const int64_t m = k < half ? k - half : k - half + 1;
                               return centre + m * h;
                           },
-                          active ? n_exact : nullptr);
+                          active ? n_exact : nullptr, tie_terms);
         pos += G;
     }
     if (active && lane == 0) {
@@ -361,12 +387,13 @@ __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_search_fast(Geom g, FastView f,
+__global__ void __launch_bounds__(256, 2) k_search_fast(Geom g, FastView f,
                                                      const int64_t* __restrict__ nu_pre,
                                                      int64_t* __restrict__ nu_out,
                                                      int32_t* __restrict__ idx_out,
                                                      int32_t* n_exact) {
-    search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, blockIdx.x);
+    __shared__ double tie_smem[256 * kTieBatch];
+    search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
 }
 
 // ---- correlation tables ---------------------------------------------------
@@ -530,20 +557,25 @@ __global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
 }
 
 // m_j: minimum over sources of the exponent, in FP32 (it only sets scales).
+// Block (bx, by) takes targets bx*128.. and the sources of chunk by; the
+// per-chunk minima are reduced by the Psi kernel (min is order free).
 constexpr int kShiftCh = 1024;
+constexpr int kShiftT = 128;
 struct ShiftSmem {
     float sp[kShiftCh], sf[kShiftCh];
 };
 
 __device__ __forceinline__ void mmse_shift_body(const Geom& g, const FastView& f,
-                                                ShiftSmem& sm, int64_t bx) {
+                                                ShiftSmem& sm, int64_t bx, int64_t by) {
     float* sp = sm.sp;
     float* sf = sm.sf;
     const int64_t j = bx * blockDim.x + threadIdx.x;
     const float y = (float)((double)((j < g.n_y ? j : g.n_y - 1) - g.hy) * g.delta);
     float m0 = FLT_MAX, m1 = FLT_MAX, m2 = FLT_MAX, m3 = FLT_MAX;
-    for (int64_t b = 0; b < g.n_x; b += kShiftCh) {
-        const int cnt = (int)min((int64_t)kShiftCh, g.n_x - b);
+    const int64_t c0 = by * f.chunk;
+    const int64_t c1 = min(c0 + f.chunk, g.n_x);
+    for (int64_t b = c0; b < c1; b += kShiftCh) {
+        const int cnt = (int)min((int64_t)kShiftCh, c1 - b);
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             sp[k] = f.prior[b + k].hi;
@@ -563,21 +595,31 @@ __device__ __forceinline__ void mmse_shift_body(const Geom& g, const FastView& f
             m0 = fminf(m0, fmaf(0.5f * d, d, sp[k]));
         }
     }
-    if (j < g.n_y) f.mshift[j] = fminf(fminf(m0, m1), fminf(m2, m3));
+    if (j < g.n_y)
+        f.mshift_part[(size_t)by * g.n_y + j] = fminf(fminf(m0, m1), fminf(m2, m3));
 }
 
-__global__ void __launch_bounds__(128) k_mmse_shift(Geom g, FastView f) {
+__global__ void __launch_bounds__(kShiftT) k_mmse_shift(Geom g, FastView f) {
     __shared__ ShiftSmem sm;
-    mmse_shift_body(g, f, sm, blockIdx.x);
+    mmse_shift_body(g, f, sm, blockIdx.x, blockIdx.y);
 }
 
+// m_j = min over the source chunks, and
 // Psi_j = exp(-delta y_j - delta^2/2 + m_{j+1} - m_j) (double-float).
+__device__ __forceinline__ float shift_min(const Geom& g, const FastView& f, int64_t j) {
+    float m = FLT_MAX;
+    for (int c = 0; c < f.n_chunks; ++c) m = fminf(m, f.mshift_part[(size_t)c * g.n_y + j]);
+    return m;
+}
+
 __device__ __forceinline__ void mmse_psi_body(const Geom& g, const FastView& f,
                                               int64_t bx) {
     const int64_t j = bx * blockDim.x + threadIdx.x;
     if (j >= g.n_y) return;
+    const float mj = shift_min(g, f, j);
+    f.mshift[j] = mj;
     const double y = (double)(j - g.hy) * g.delta;
-    const double dm = j + 1 < g.n_y ? (double)f.mshift[j + 1] - (double)f.mshift[j] : 0.0;
+    const double dm = j + 1 < g.n_y ? (double)shift_min(g, f, j + 1) - (double)mj : 0.0;
     f.psi[j] = df_from_double(exp(-g.delta * y - 0.5 * g.delta * g.delta + dm));
 }
 
@@ -590,6 +632,7 @@ struct MmseSmem {
     int64_t snu[kMmseSrc];
     dfloat spr[kMmseSrc], sf[kMmseSrc], sF[kMmseSrc];
     dfloat st64[47];
+    dfloat spsi[15][kMmseThreads];   // Psi along each thread's run
 };
 
 template <int R>
@@ -607,12 +650,11 @@ __device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
     const int64_t jc0 = j0 < g.n_y ? j0 : g.n_y - 1;
     const float m0 = f.mshift[jc0];
     float smax = -FLT_MAX;
-    dfloat psi[R > 1 ? R - 1 : 1];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int64_t j = j0 + k < g.n_y ? j0 + k : g.n_y - 1;
         smax = fmaxf(smax, f.mshift[j]);
-        if (k + 1 < R) psi[k] = f.psi[j];
+        if (k + 1 < R) sm.spsi[k][threadIdx.x] = f.psi[j];
     }
     const float ya = (float)((double)(j0 - g.hy) * g.delta);
     const float yb = (float)((double)(j0 + R - 1 - g.hy) * g.delta);
@@ -668,7 +710,8 @@ __device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
                     df_mul_raw(w[q], fv[q], pp, pe);
                     N[k] = df_acc(N[k], pp, pe);
                     D[k] = df_add(D[k], w[q]);
-                    if (k + 1 < R) w[q] = df_mul(w[q], df_mul(F[q], psi[k]));
+                    if (k + 1 < R)
+                        w[q] = df_mul(w[q], df_mul(F[q], sm.spsi[k][threadIdx.x]));
                 }
             }
         }
@@ -761,8 +804,9 @@ template <int G>
 __global__ void __launch_bounds__(256) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
+    __shared__ double tie_smem[256 * kTieBatch];
     search_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
-                   sd.f.n_exact, r.local);
+                   sd.f.n_exact, tie_smem, r.local);
 }
 
 __global__ void kb_sources(const InstDev* insts, const BlockRef* map) {
@@ -776,7 +820,8 @@ __global__ void __launch_bounds__(128) kb_mmse_shift(const InstDev* insts,
     __shared__ InstDev sd;
     __shared__ ShiftSmem sm;
     const BlockRef r = stage(insts, map, sd);
-    mmse_shift_body(sd.g, sd.f, sm, r.local);
+    const int64_t jb = (sd.g.n_y + kShiftT - 1) / kShiftT;
+    mmse_shift_body(sd.g, sd.f, sm, r.local % jb, r.local / jb);
 }
 
 __global__ void kb_mmse_psi(const InstDev* insts, const BlockRef* map) {
@@ -907,7 +952,7 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
     k_sources<<<blocks(g.n_x, 256), 256, 0, s>>>(g, f, nu);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_shift", &ev) : -1;
-    k_mmse_shift<<<blocks(g.n_y, 128), 128, 0, s>>>(g, f);
+    k_mmse_shift<<<dim3(blocks(g.n_y, kShiftT), (unsigned)f.n_chunks), kShiftT, 0, s>>>(g, f);
     k_mmse_psi<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_main", &ev) : -1;
@@ -964,7 +1009,7 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
         case kBSearch: return (g.n_x * g.n_refine + 255) / 256;
         case kBPerX: return (g.n_x + 255) / 256;
-        case kBShift: return (g.n_y + 127) / 128;
+        case kBShift: return (g.n_y + kShiftT - 1) / kShiftT * fp.n_chunks;
         case kBPerY: return (g.n_y + 255) / 256;
         case kBTabPart: return (fp.n_pos + kTabT - 1) / kTabT * fp.tab_splits;
         case kBTabComb: return (fp.n_pos + 255) / 256;
@@ -996,7 +1041,7 @@ void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
         }
     }
     kb_sources<<<(unsigned)bl.n_blocks[kBPerX], 256, 0, s>>>(d, bl.map[kBPerX]);
-    kb_mmse_shift<<<(unsigned)bl.n_blocks[kBShift], 128, 0, s>>>(d, bl.map[kBShift]);
+    kb_mmse_shift<<<(unsigned)bl.n_blocks[kBShift], kShiftT, 0, s>>>(d, bl.map[kBShift]);
     kb_mmse_psi<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
     for (int r = 0; r < 5; ++r) {
         if (bl.mmse_blocks[r] == 0) continue;

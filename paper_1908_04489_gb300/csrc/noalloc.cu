@@ -37,9 +37,11 @@ constexpr int kMaxChunks = 8;          // source columns of the u1 kernel
 constexpr int kThreadsPerRow = 64;     // threads per block row (k_mmse_main)
 
 // 8-byte slots: nu, prior, src_nu, src_f, src_F (x-sized); mshift, psi
-// (y-sized); the exp(k/64) table; numerator and denominator partials.
+// (y-sized); the exp(k/64) table; numerator and denominator partials; the
+// per-chunk exponent minima (floats, two per slot).
 constexpr size_t kScratchDoubles = 5 * (size_t)kMaxX + 2 * (size_t)kMaxY + 64 +
-                                   2 * (size_t)kMaxChunks * kMaxY;
+                                   2 * (size_t)kMaxChunks * kMaxY +
+                                   (size_t)kMaxChunks * kMaxY / 2;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
@@ -135,7 +137,8 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
     f.psi = (dfloat*)q;         q += kMaxY;
     f.t64 = (dfloat*)q;         q += 64;
     f.partN = q;                q += (size_t)kMaxChunks * kMaxY;
-    f.partD = q;
+    f.partD = q;                q += (size_t)kMaxChunks * kMaxY;
+    f.mshift_part = (float*)q;
 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g.n_x > 47 ? g.n_x : 47;

@@ -184,7 +184,8 @@ size_t inst_bytes(const Geom& g, int precision) {
              2 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
              rnd(8 * 47) + 2 * rnd(8 * (size_t)fp.n_chunks * ny) +
              rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) + rnd(8) +
-             rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos);
+             rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
+             rnd(4 * (size_t)fp.n_chunks * ny);
     }
     return b;
 }
@@ -244,6 +245,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.src_f = (dfloat*)A.get(8 * nx);
     f.src_F = (dfloat*)A.get(8 * nx);
     f.mshift = (float*)A.get(4 * ny);
+    f.mshift_part = (float*)A.get(4 * (size_t)f.n_chunks * ny);
     f.psi = (dfloat*)A.get(8 * ny);
     f.t64 = (dfloat*)A.get(8 * 47);
     f.partN = (double*)A.get(8 * (size_t)f.n_chunks * ny);
@@ -254,7 +256,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.n_exact = (int32_t*)A.get(4);
     f.n_pairs = (int64_t*)A.get(8);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf ||
-        !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.psi ||
+        !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.mshift_part || !f.psi ||
         !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.tab_part || !f.W2_dev || !f.n_exact || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;

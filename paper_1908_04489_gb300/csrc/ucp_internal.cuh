@@ -86,6 +86,7 @@ struct FastView : FastPlan {
     dfloat* src_f;       // [n_x] f_i
     dfloat* src_F;       // [n_x] exp(delta f_i)
     float* mshift;       // [n_y] estimate of min_i of the u1 exponents
+    float* mshift_part;  // [n_chunks * n_y] per-chunk minima
     dfloat* psi;         // [n_y] exp(-delta y_j - delta^2/2 + m_{j+1} - m_j)
     dfloat* t64;         // [47] exp(k / 64), k = -23..23
     double* partN;       // [n_chunks * n_y] numerator partials
