@@ -195,6 +195,24 @@ def oracle_sample(p, budget_s=12.0, threads=None):
     return 1.0 / solve_s, threads, sample, t_search + t_mmse_full + t_J
 
 
+# ---- multi-rank aggregation -------------------------------------------------
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks (x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_rank / max_seconds
+
+
 # ---- GPU arm --------------------------------------------------------------
 
 def fast_sizes(p, binding):
@@ -401,12 +419,8 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, "cuda")
+    value = whole_job_rate(world, args.steps, total_ms / 1e3)
 
     parity = None
     if rank == 0 and not args.no_cpu:
@@ -434,12 +448,8 @@ def run_gpu(args):
         inst.close()
         e2e_s.append(time.perf_counter() - t0)
     assert abs(Je - Js[-1]) <= 1e-9, (Je, Js[-1])
-    e2e_total = float(np.sum(e2e_s))
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = {"value": world * args.steps / e2e_total, "unit": UNIT,
+    e2e_total = max_over_ranks(float(np.sum(e2e_s)), world, "cuda")
+    e2e = {"value": whole_job_rate(world, args.steps, e2e_total), "unit": UNIT,
            "h2d_bytes_per_step": int(table.nbytes),
            "d2h_bytes_per_step": int(out["f"].nbytes + out["U"].nbytes + 8)}
 

@@ -50,36 +50,59 @@ class _Params(ctypes.Structure):
 _lib = None
 
 
+def build_variant(src_text: str, out_path: str) -> str:
+    """Compile a variant of the oracle source (tests plant mistakes this way
+    to check that the pins catch them)."""
+    src = out_path[:-3] + ".c"
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-fno-fast-math", "-fopenmp", "-I", _HERE, "-o", out_path, src, "-lm"],
+                   check=True)
+    return out_path
+
+
+def source() -> str:
+    return open(_SRC).read()
+
+
+def load_library(path: str):
+    """ctypes handle of an oracle library at `path`, argument types set."""
+    return _configure(ctypes.CDLL(path))
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = build()
-        L = ctypes.CDLL(path)
-        P = ctypes.POINTER(_Params)
-        dp = ctypes.POINTER(ctypes.c_double)
-        i64p = ctypes.POINTER(ctypes.c_int64)
-        i32p = ctypes.POINTER(ctypes.c_int32)
-        L.orc_sizes.argtypes = [P, i64p, i64p, i64p, i64p, i32p]
-        L.orc_grids.argtypes = [P, dp, dp, dp, dp, dp]
-        L.orc_value.argtypes = [P, ctypes.c_int64]
-        L.orc_value.restype = ctypes.c_double
-        L.orc_init.argtypes = [P, ctypes.c_int, dp, i64p]
-        L.orc_S.argtypes = [P, dp, ctypes.c_int64]
-        L.orc_S.restype = ctypes.c_double
-        L.orc_cost.argtypes = [P, dp, ctypes.c_int64, ctypes.c_int64]
-        L.orc_cost.restype = ctypes.c_double
-        L.orc_search.argtypes = [P, i64p, dp, i64p, i32p, ctypes.c_int64,
-                                 ctypes.c_int64]
-        L.orc_candidates.argtypes = [P, i64p, dp, ctypes.c_int64, i64p, dp]
-        L.orc_mmse.argtypes = [P, i64p, dp, ctypes.c_int64, ctypes.c_int64]
-        L.orc_J.argtypes = [P, i64p, dp]
-        L.orc_J.restype = ctypes.c_double
-        L.orc_solve.argtypes = [P, ctypes.c_int, dp, ctypes.c_int, i64p, dp,
-                                dp, i32p]
-        L.orc_set_threads.argtypes = [ctypes.c_int]
-        L.orc_get_threads.restype = ctypes.c_int
-        _lib = L
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(L):
+    P = ctypes.POINTER(_Params)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.orc_sizes.argtypes = [P, i64p, i64p, i64p, i64p, i32p]
+    L.orc_grids.argtypes = [P, dp, dp, dp, dp, dp]
+    L.orc_value.argtypes = [P, ctypes.c_int64]
+    L.orc_value.restype = ctypes.c_double
+    L.orc_init.argtypes = [P, ctypes.c_int, dp, i64p]
+    L.orc_S.argtypes = [P, dp, ctypes.c_int64]
+    L.orc_S.restype = ctypes.c_double
+    L.orc_cost.argtypes = [P, dp, ctypes.c_int64, ctypes.c_int64]
+    L.orc_cost.restype = ctypes.c_double
+    L.orc_search.argtypes = [P, i64p, dp, i64p, i32p, ctypes.c_int64,
+                             ctypes.c_int64]
+    L.orc_candidates.argtypes = [P, i64p, dp, ctypes.c_int64, i64p, dp]
+    L.orc_mmse.argtypes = [P, i64p, dp, ctypes.c_int64, ctypes.c_int64]
+    L.orc_J.argtypes = [P, i64p, dp]
+    L.orc_J.restype = ctypes.c_double
+    L.orc_solve.argtypes = [P, ctypes.c_int, dp, ctypes.c_int, i64p, dp,
+                            dp, i32p]
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_get_threads.restype = ctypes.c_int
+    return L
 
 
 def _dp(a):
@@ -110,7 +133,8 @@ class Oracle:
     Controllers f are int64 lattice indices nu; ``value(nu)`` converts.
     """
 
-    def __init__(self, params):
+    def __init__(self, params, library=None):
+        self._L = library
         self.params = dict(params)
         self._p = _Params(*(float(params[k]) for k in
                             ("k", "sigma", "delta", "x_half", "w_half",
@@ -119,18 +143,21 @@ class Oracle:
                             ("n_coarse", "n_refine", "n_levels", "n_nbr")))
         n = [ctypes.c_int64() for _ in range(4)]
         sh = ctypes.c_int32()
-        if lib().orc_sizes(ctypes.byref(self._p), *(ctypes.byref(v) for v in n),
+        if self._lib().orc_sizes(ctypes.byref(self._p), *(ctypes.byref(v) for v in n),
                            ctypes.byref(sh)) != 0:
             raise ValueError(f"invalid oracle parameters: {params}")
         self.n_x, self.n_w, self.n_y, self.n_cand = (v.value for v in n)
         self.shift = sh.value
+
+    def _lib(self):
+        return self._L if self._L is not None else lib()
 
     # -- grids ----------------------------------------------------------
     def grids(self):
         x = np.empty(self.n_x); px = np.empty(self.n_x)
         w = np.empty(self.n_w); phi = np.empty(self.n_w)
         y = np.empty(self.n_y)
-        lib().orc_grids(ctypes.byref(self._p), _dp(x), _dp(px), _dp(w),
+        self._lib().orc_grids(ctypes.byref(self._p), _dp(x), _dp(px), _dp(w),
                         _dp(phi), _dp(y))
         return dict(x=x, px=px, w=w, phi=phi, y=y)
 
@@ -141,7 +168,7 @@ class Oracle:
     def init(self, kind: int, table=None):
         nu = np.empty(self.n_x, dtype=np.int64)
         tab = None if table is None else np.ascontiguousarray(table, np.float64)
-        rc = lib().orc_init(ctypes.byref(self._p), int(kind),
+        rc = self._lib().orc_init(ctypes.byref(self._p), int(kind),
                             _dp(tab) if tab is not None else None, _i64p(nu))
         if rc != 0:
             raise ValueError("oracle init failed")
@@ -150,11 +177,11 @@ class Oracle:
     # -- pieces of the sweep ------------------------------------------------
     def S(self, U, nu) -> float:
         U = np.ascontiguousarray(U, np.float64)
-        return float(lib().orc_S(ctypes.byref(self._p), _dp(U), int(nu)))
+        return float(self._lib().orc_S(ctypes.byref(self._p), _dp(U), int(nu)))
 
     def cost(self, U, i, nu) -> float:
         U = np.ascontiguousarray(U, np.float64)
-        return float(lib().orc_cost(ctypes.byref(self._p), _dp(U), int(i),
+        return float(self._lib().orc_cost(ctypes.byref(self._p), _dp(U), int(i),
                                     int(nu)))
 
     def search(self, nu_pre, U, i0=0, i1=None):
@@ -163,7 +190,7 @@ class Oracle:
         U = np.ascontiguousarray(U, np.float64)
         out = nu_pre.copy()
         idx = np.full(self.n_x, -1, dtype=np.int32)
-        lib().orc_search(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
+        self._lib().orc_search(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
                          _i64p(out), _i32p(idx), int(i0), int(i1))
         return out, idx
 
@@ -172,7 +199,7 @@ class Oracle:
         U = np.ascontiguousarray(U, np.float64)
         nus = np.empty(self.n_cand, dtype=np.int64)
         gs = np.empty(self.n_cand)
-        idx = lib().orc_candidates(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
+        idx = self._lib().orc_candidates(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
                                    int(i), _i64p(nus), _dp(gs))
         return nus, gs, int(idx)
 
@@ -180,13 +207,13 @@ class Oracle:
         j1 = self.n_y if j1 is None else j1
         nu = np.ascontiguousarray(nu, np.int64)
         U = np.full(self.n_y, np.nan)
-        lib().orc_mmse(ctypes.byref(self._p), _i64p(nu), _dp(U), int(j0), int(j1))
+        self._lib().orc_mmse(ctypes.byref(self._p), _i64p(nu), _dp(U), int(j0), int(j1))
         return U
 
     def J(self, nu, U) -> float:
         nu = np.ascontiguousarray(nu, np.int64)
         U = np.ascontiguousarray(U, np.float64)
-        return float(lib().orc_J(ctypes.byref(self._p), _i64p(nu), _dp(U)))
+        return float(self._lib().orc_J(ctypes.byref(self._p), _i64p(nu), _dp(U)))
 
     def solve(self, init_kind: int, n_sweeps: int, table=None, want_idx=False):
         nu = np.empty(self.n_x, dtype=np.int64)
@@ -194,7 +221,7 @@ class Oracle:
         Jh = np.empty(n_sweeps + 1)
         idx = np.empty((n_sweeps, self.n_x), dtype=np.int32) if want_idx else None
         tab = None if table is None else np.ascontiguousarray(table, np.float64)
-        rc = lib().orc_solve(ctypes.byref(self._p), int(init_kind),
+        rc = self._lib().orc_solve(ctypes.byref(self._p), int(init_kind),
                              _dp(tab) if tab is not None else None, int(n_sweeps),
                              _i64p(nu), _dp(U), _dp(Jh),
                              _i32p(idx) if idx is not None else None)
