@@ -11,8 +11,9 @@
 // error bounds for basic building blocks of double-word arithmetic", ACM
 // TOMS 2017).  Rounded products use __fmul_rn so that no multiply-add is
 // formed across an error-free transformation.  With u = 2^-24:
-//   df_add   |err| <= 2 u^2 (|a| + |b|)
-//   df_mul   |err| <= 5 u^2 |a b|
+//   df_add     |err| <= 2 u^2 (|a| + |b|)
+//   df_add_acc |err| <= 3 u^2 |a + b|
+//   df_mul     |err| <= 5 u^2 |a b|
 #pragma once
 
 #include <cuda_runtime.h>
@@ -54,6 +55,19 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
     two_sum(a.hi, b.hi, s, e);
     e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
     return df_norm(s, e);
+}
+
+// Accurate addition (Joldes, Muller, Popescu, Algorithm 6): relative error
+// <= 3 u^2 of the result, so small sums of large operands stay accurate.
+__device__ __forceinline__ dfloat df_add_acc(dfloat a, dfloat b) {
+    float sh, sl, th, tl;
+    two_sum(a.hi, b.hi, sh, sl);
+    two_sum(a.lo, b.lo, th, tl);
+    const float c = __fadd_rn(sl, th);
+    float vh, vl;
+    fast_two_sum(sh, c, vh, vl);
+    const float w = __fadd_rn(tl, vl);
+    return df_norm(vh, w);
 }
 
 __device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {

@@ -125,6 +125,70 @@ __device__ double exact_costs_batch(const Geom& g, const FastView& f, int64_t i,
     return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
 }
 
+// Second screening tier: the direct w quadrature of S from the E table,
+// taps split over the group.  The residual
+//   d_l = (w_l + E_{p+l}) + t (E_{p+l+1} - E_{p+l})
+// is formed with accurate double-float additions (error relative to the
+// small results, not to the operands), each term phi_l d_l^2 in double-float,
+// 8-term double-float blocks summed in FP64 and reduced over the lanes in a
+// fixed order (every lane gets the same value).  The sum has no cancellation, so its
+// bound is several times tighter than the table identity's.  Candidates
+// outside the tables get an infinite bound (no second tier).
+template <int G>
+__device__ void direct_df_cost(const Geom& g, const FastView& f, int64_t i, int64_t nu,
+                               int lane, double& g2, double& b2) {
+    const unsigned gm = group_mask<G>();
+    const int64_t cell = nu >> g.shift;
+    const int64_t p = cell - f.c_lo;
+    if (p < 0 || p + 1 >= f.n_pos) {
+        g2 = 0.0;
+        b2 = INFINITY;
+        return;
+    }
+    const int64_t frac = nu - cell * g.one;
+    const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
+    double acc = 0.0;
+    dfloat blk{0.f, 0.f};
+    int cnt = 0;
+    float emax = 0.f, demax = 0.f;
+    for (int64_t l = lane; l < g.n_w; l += G) {
+        const dfloat E0 = f.E[p + l], E1 = f.E[p + l + 1];
+        const dfloat dE = df_add_acc(E1, df_neg(E0));
+        const dfloat d = df_add_acc(df_add_acc(f.wdf[l], E0), df_mul(t, dE));
+        blk = df_add(blk, df_mul(f.phidf[l], df_mul(d, d)));
+        if (++cnt == 8) {
+            acc += df_to_double(blk);
+            blk = {0.f, 0.f};
+            cnt = 0;
+        }
+        emax = fmaxf(emax, fmaxf(fabsf(E0.hi), fabsf(E1.hi)));
+        demax = fmaxf(demax, fabsf(dE.hi));
+    }
+    acc += df_to_double(blk);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        acc += __shfl_down_sync(gm, acc, off, G);
+        emax = fmaxf(emax, __shfl_down_sync(gm, emax, off, G));
+        demax = fmaxf(demax, __shfl_down_sync(gm, demax, off, G));
+    }
+    const double S2 = __shfl_sync(gm, acc, 0, G);
+    emax = __shfl_sync(gm, emax, 0, G);
+    demax = __shfl_sync(gm, demax, 0, G);
+    const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
+    const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
+    const double c = df_to_double(ctl);
+    g2 = c + S2;
+    // |error of d_l| <= uf^2 (|w_l| + |E_{p+l}| + |E_{p+l+1}|) from the
+    // double-float representations plus 8 uf^2 (|d_l| + |dE_l|) from the
+    // operations; summed against phi_l 2|d_l| this gives the terms below.
+    const double uf2 = 0x1p-48;
+    const double rs = sqrt(fmax(S2, 0.0));
+    const double eps = (double)f.beta_abs + uf2 * ((double)f.w_half + 2.0 * emax);
+    b2 = (double)f.beta2_rel * S2 + 1.25 * 16.0 * uf2 * (S2 + rs * demax) +
+         1.25 * (2.0 * rs + 1.0) * eps + 3.0e-13 * c + (double)f.beta_ctl * sqrt(c) +
+         4.0e-16 * fabs(g2);
+}
+
 // ---- screened table cost ------------------------------------------------
 
 struct Eval {
@@ -254,52 +318,13 @@ __device__ __forceinline__ int64_t stage0_nu(const Geom& g, const int64_t* nu_pr
 
 __device__ __forceinline__ dfloat df_pm(dfloat v, float b) { return df_add_f(v, b); }
 
-// Resolve one stage of the list: the carried winner (lane 0) plus positions
-// p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
-// costs over all of them.
+// All candidates in play re-costed by the serial FP64 quadrature (used when
+// more distinct values are in play than the group has lanes).
 template <int G, typename CandFn>
-__device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
-                        const Best& best, int p0, int p_end, CandFn cand,
-                        int32_t* n_exact, double* tie_terms) {
-    const bool have_best = best.pos != INT_MAX;
-    // 1. smallest upper end
-    dfloat hi = {FLT_MAX, 0.f};
-    if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
-    for (int p = p0 + lane; p < p_end; p += G) {
-        const Eval e = eval_table(g, f, i, cand(p));
-        const dfloat h = df_pm(e.gv, e.beta);
-        if (df_lt(h, hi)) hi = h;
-    }
-    hi = gmin_df<G>(hi);
-    // 2. distinct values still in play, and their first position
-    int64_t vmin = INT64_MAX, vmax = INT64_MIN;
-    int32_t pmin = INT_MAX;
-    if (lane == 0 && have_best && !df_lt(hi, df_pm(best.gv, -best.beta))) {
-        vmin = vmax = best.nu;
-        pmin = best.pos;
-    }
-    for (int p = p0 + lane; p < p_end; p += G) {
-        const int64_t nu = cand(p);
-        const Eval e = eval_table(g, f, i, nu);
-        if (!df_lt(hi, df_pm(e.gv, -e.beta))) {
-            vmin = nu < vmin ? nu : vmin;
-            vmax = nu > vmax ? nu : vmax;
-            pmin = p < pmin ? p : pmin;
-        }
-    }
-    vmin = gmin_i64<G>(vmin);
-    vmax = gmax_i64<G>(vmax);
-    pmin = gmin_i32<G>(pmin);
-    if (vmin == vmax) {
-        // one value in play: its first occurrence wins
-        if (have_best && pmin == best.pos) return best;
-        const Eval e = eval_table(g, f, i, vmin);
-        return {e.gv, e.beta, pmin, vmin, false, 0.0};
-    }
-    // 3. several values in play: serial FP64 costs of each.  Members are
-    // gathered into lanes (up to kTieBatch per pass) and re-costed together:
-    // the group forms every member's terms, each member's lane adds its own
-    // terms in index order, so all serial chains share one instruction stream.
+__device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int lane,
+                               const Best& best, bool have_best, dfloat hi, int p0,
+                               int p_end, CandFn cand, int32_t* n_exact,
+                               double* tie_terms) {
     double xg = DBL_MAX;
     int32_t xp = INT_MAX;
     int64_t xn = 0;
@@ -343,6 +368,153 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         }
     }
     flush();
+    glex<G>(xg, xp, xn);
+    return {df_from_double(xg), 4.0e-15f * (float)fabs(xg), xp, xn, true, xg};
+}
+
+// Resolve one stage of the list: the carried winner (lane 0) plus positions
+// p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
+// costs over all of them.
+template <int G, typename CandFn>
+__device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
+                        const Best& best, int p0, int p_end, CandFn cand,
+                        int32_t* n_exact, double* tie_terms) {
+    const bool have_best = best.pos != INT_MAX;
+    // 1. smallest upper end
+    dfloat hi = {FLT_MAX, 0.f};
+    if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
+    for (int p = p0 + lane; p < p_end; p += G) {
+        const Eval e = eval_table(g, f, i, cand(p));
+        const dfloat h = df_pm(e.gv, e.beta);
+        if (df_lt(h, hi)) hi = h;
+    }
+    hi = gmin_df<G>(hi);
+    // 2. distinct values still in play, and their first position
+    int64_t vmin = INT64_MAX, vmax = INT64_MIN;
+    int32_t pmin = INT_MAX;
+    if (lane == 0 && have_best && !df_lt(hi, df_pm(best.gv, -best.beta))) {
+        vmin = vmax = best.nu;
+        pmin = best.pos;
+    }
+    for (int p = p0 + lane; p < p_end; p += G) {
+        const int64_t nu = cand(p);
+        const Eval e = eval_table(g, f, i, nu);
+        if (!df_lt(hi, df_pm(e.gv, -e.beta))) {
+            vmin = nu < vmin ? nu : vmin;
+            vmax = nu > vmax ? nu : vmax;
+            pmin = p < pmin ? p : pmin;
+        }
+    }
+    vmin = gmin_i64<G>(vmin);
+    vmax = gmax_i64<G>(vmax);
+    pmin = gmin_i32<G>(pmin);
+    if (vmin == vmax) {
+        // one value in play: its first occurrence wins
+        if (have_best && pmin == best.pos) return best;
+        const Eval e = eval_table(g, f, i, vmin);
+        return {e.gv, e.beta, pmin, vmin, false, 0.0};
+    }
+    // 3. several values in play.  Gather them into lanes (member m in lane
+    // m; the carried winner first), cost each by the direct double-float
+    // quadrature (second tier) and keep those whose tighter intervals can
+    // still hold the first minimum; if they are one value, its first position
+    // wins, otherwise their serial FP64 costs decide (third tier).
+    const unsigned gm = group_mask<G>();
+    const int base = (threadIdx.x & 31) & ~(G - 1);
+    int M = 0;
+    bool overflow = false;
+    int64_t mnu = 0;
+    int32_t mpos = INT_MAX;
+    bool mexact = false;
+    double mval = 0.0;
+    if (have_best && !df_lt(hi, df_pm(best.gv, -best.beta))) {
+        if (lane == 0) { mnu = best.nu; mpos = best.pos; mexact = best.is_exact; mval = best.exact; }
+        M = 1;
+    }
+    for (int pb = p0; pb < p_end; pb += G) {
+        const int p = pb + lane;
+        bool member = false;
+        int64_t nu = 0;
+        if (p < p_end) {
+            nu = cand(p);
+            const Eval e = eval_table(g, f, i, nu);
+            member = !df_lt(hi, df_pm(e.gv, -e.beta));
+        }
+        unsigned mask = (__ballot_sync(gm, member) >> base) & (0xffffffffu >> (32 - G));
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int64_t cn = __shfl_sync(gm, nu, src, G);
+            if (M < G) {
+                if (lane == M) { mnu = cn; mpos = pb + src; mexact = false; }
+                ++M;
+            } else {
+                overflow = true;
+            }
+        }
+    }
+    if (overflow)   // more distinct candidates in play than lanes (rare)
+        return resolve_serial<G>(g, f, i, lane, best, have_best, hi, p0, p_end, cand,
+                                 n_exact, tie_terms);
+    // second tier
+    double g2 = 0.0, b2 = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const int64_t cn = __shfl_sync(gm, mnu, m, G);
+        const bool ex = __shfl_sync(gm, (int)mexact, m, G) != 0;
+        double v, bv;
+        if (ex) {
+            v = __shfl_sync(gm, mval, m, G);
+            bv = 0.0;
+        } else {
+            direct_df_cost<G>(g, f, i, cn, lane, v, bv);
+        }
+        if (lane == m) { g2 = v; b2 = bv; }
+    }
+    double hi2 = lane < M ? g2 + b2 : DBL_MAX;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+        hi2 = fmin(hi2, __shfl_xor_sync(gm, hi2, off, G));
+    const bool in2 = lane < M && g2 - b2 <= hi2;
+    int64_t v2min = in2 ? mnu : INT64_MAX, v2max = in2 ? mnu : INT64_MIN;
+    int32_t p2min = in2 ? mpos : INT_MAX;
+    v2min = gmin_i64<G>(v2min);
+    v2max = gmax_i64<G>(v2max);
+    p2min = gmin_i32<G>(p2min);
+    if (v2min == v2max) {
+        if (have_best && p2min == best.pos) return best;
+        const unsigned wmask = (__ballot_sync(gm, in2 && mpos == p2min) >> base) &
+                               (0xffffffffu >> (32 - G));
+        const int wl = __ffs(wmask) - 1;
+        const double wg = __shfl_sync(gm, g2, wl, G);
+        const double wb = __shfl_sync(gm, b2, wl, G);
+        return {df_from_double(wg), (float)(wb + 4.0e-15 * fabs(wg)) * 1.0001f, p2min,
+                v2min, false, 0.0};
+    }
+    // third tier: serial FP64 costs of the members still in play
+    double xg = DBL_MAX;
+    int32_t xp = INT_MAX;
+    int64_t xn = 0;
+    if (lane < M && in2 && mexact) { xg = mval; xp = mpos; xn = mnu; }
+    const bool need = in2 && !mexact;
+    const unsigned nmask = (__ballot_sync(gm, need) >> base) & (0xffffffffu >> (32 - G));
+    int K = 0;
+    int64_t knu = 0;
+    int32_t kpos = INT_MAX;
+    unsigned rest = nmask;
+    while (rest) {
+        const int src = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const int64_t cn = __shfl_sync(gm, mnu, src, G);
+        const int32_t cp = __shfl_sync(gm, mpos, src, G);
+        if (lane == K) { knu = cn; kpos = cp; }
+        ++K;
+        if (K == kTieBatch || rest == 0) {
+            const double v = exact_costs_batch<G>(g, f, i, lane, knu, K, tie_terms);
+            if (lane < K && before(v, kpos, xg, xp)) { xg = v; xp = kpos; xn = knu; }
+            if (lane == 0 && n_exact) atomicAdd(n_exact, K);
+            K = 0;
+        }
+    }
     glex<G>(xg, xp, xn);
     return {df_from_double(xg), 4.0e-15f * (float)fabs(xg), xp, xn, true, xg};
 }
@@ -522,6 +694,7 @@ __global__ void k_fast_setup(Geom g, FastView f) {
         const double w = (double)(k - g.hw) * g.delta;
         f.a[k] = df_from_double(f.phi[k] * w);
         f.phidf[k] = df_from_double(f.phi[k]);
+        f.wdf[k] = df_from_double(w);
     }
     if (k < g.n_x) {
         const double x = x_of(g, k);
@@ -801,7 +974,7 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) kb_search(const InstDev* insts, const BlockRef* map) {
+__global__ void __launch_bounds__(256, 2) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
     __shared__ double tie_smem[256 * kTieBatch];

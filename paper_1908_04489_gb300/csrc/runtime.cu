@@ -181,7 +181,7 @@ size_t inst_bytes(const Geom& g, int precision) {
         FastPlan fp;
         fast_plan(g, &fp);
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
-             2 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
+             3 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
              rnd(8 * 47) + 2 * rnd(8 * (size_t)fp.n_chunks * ny) +
              rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) + rnd(8) +
              rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
@@ -219,6 +219,12 @@ static void fast_bounds(ucp_inst* in, double B) {
     f.beta_abs = (float)(1.25 * u * A);
     const double X = (double)g.hx * g.delta;
     f.beta_ctl = (float)(4.0 * u * (2.0 * B + X) * g.k);
+    // direct quadrature (second screening tier): the plain path's serial-sum
+    // error, the double-float term products (24 uf^2), 8-term double-float
+    // blocks (16 uf^2) and the FP64 sum of the blocks
+    f.beta2_rel = (float)(1.25 * (((double)g.n_w + 8.0) * u + 40.0 * uf2 +
+                                  ((double)g.n_w / 16.0 + 8.0) * u));
+    f.w_half = (float)W;
 }
 
 static ucp_status fast_alloc(ucp_inst* in) {
@@ -240,6 +246,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.EE = (dfloat*)A.get(8 * (size_t)f.n_e);
     f.a = (dfloat*)A.get(8 * nw);
     f.phidf = (dfloat*)A.get(8 * nw);
+    f.wdf = (dfloat*)A.get(8 * nw);
     f.prior = (dfloat*)A.get(8 * nx);
     f.src_nu = (int64_t*)A.get(8 * nx);
     f.src_f = (dfloat*)A.get(8 * nx);
@@ -255,7 +262,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
     f.n_pairs = (int64_t*)A.get(8);
-    if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf ||
+    if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf || !f.wdf ||
         !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.mshift_part || !f.psi ||
         !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.tab_part || !f.W2_dev || !f.n_exact || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");

@@ -81,6 +81,7 @@ struct FastView : FastPlan {
     dfloat* EE;          // [n_e] E_m E_{m+1}
     dfloat* a;           // [n_w] phi_l w_l
     dfloat* phidf;       // [n_w] phi_l
+    dfloat* wdf;         // [n_w] w_l
     dfloat* prior;       // [n_x] x_i^2 / (2 sigma^2)
     int64_t* src_nu;     // [n_x] lattice index of f_i this sweep
     dfloat* src_f;       // [n_x] f_i
@@ -105,6 +106,8 @@ struct FastView : FastPlan {
     float beta_rel;      // |table cost - serial cost| <= beta_rel M
     float beta_abs;      //   + beta_abs (2 sqrt(M) + 1)
     float beta_ctl;      //   + beta_ctl sqrt(control term) + ...
+    float beta2_rel;     // direct double-float quadrature: beta2_rel S + ...
+    float w_half;        // W (largest |w_l|)
 };
 
 // Device-resident descriptor of one instance of a batch: everything a batched
