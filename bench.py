@@ -69,15 +69,21 @@ def init_table(p):
 # flops of its double-float operations (FADD/FMUL 1, FFMA 2):
 #   df_add 11, df_mul 10, product-and-accumulate 18.
 #   tables:    per (table position, w tap): 3 x 18 = 54.
-#   mmse_main: per evaluated (source, target): weight-times-f accumulate 18,
-#              weight accumulate 11, two recurrence products 20 = 49; plus
-#              per (source, run) the anchor exponent (40) and exp (90).
+#   mmse_main: per directly summed (source, target): weight-times-f
+#              accumulate 18, weight accumulate 11, recurrence product 10 = 39;
+#              per (source, run) the anchor exponent (40) and exp (90).  Per
+#              Taylor-expanded (box, run): the anchor (130) and per target the
+#              shift of z (11), the recurrence product (10) and two scaled
+#              accumulates (42); per Taylor term 21 in double-float, 2 in FP32.
 #   search:    per (x_i, candidate): two screened evaluations of the
 #              three-correlation identity, 233 each.
 # The plain FP64 path counts FP64 flops: 6 per quadrature term.
 FLOPS_TABLE_TAP = 54.0
-FLOPS_U1_PAIR = 49.0
+FLOPS_U1_PAIR = 39.0
 FLOPS_U1_ANCHOR = 130.0
+FLOPS_U1_BOX_TARGET = 63.0
+FLOPS_U1_TERM_DF = 21.0
+FLOPS_U1_TERM_F32 = 2.0
 FLOPS_SEARCH_CAND = 466.0
 
 
@@ -89,10 +95,14 @@ def kernel_work(p, sizes, counters, launches):
                 "mmse": (nx * ny * 8.0, "fp64")}
     run = sizes.get("run", 16)
     n_pos = sizes.get("n_pos", 0)
-    pairs = counters.get("u1_pairs", 0) / max(1, launches.get("mmse_main", 1))
+    per = 1.0 / max(1, launches.get("mmse_main", 1))
+    u1 = (counters.get("u1_pairs", 0) * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR) +
+          counters.get("u1_boxes", 0) * (run * FLOPS_U1_BOX_TARGET + FLOPS_U1_ANCHOR) +
+          counters.get("u1_df_terms", 0) * FLOPS_U1_TERM_DF +
+          counters.get("u1_f32_terms", 0) * FLOPS_U1_TERM_F32) * per
     return {
         "tables": (n_pos * nw * FLOPS_TABLE_TAP, "fp32"),
-        "mmse_main": (pairs * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR), "fp32"),
+        "mmse_main": (u1, "fp32"),
         "search": (nx * sizes["n_cand"] * FLOPS_SEARCH_CAND, "fp32"),
     }
 
@@ -390,7 +400,7 @@ def run_gpu(args):
     clocks = Clocks(local)
     clocks.start()
     step_ms, Js, kern = [], [], {}
-    counters = {"recosts": 0, "u1_pairs": 0}
+    counters = dict.fromkeys(binding.Instance.COUNTERS, 0)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()

@@ -161,12 +161,19 @@ UCP_API ucp_status ucp_destroy(ucp_inst* inst);
  * creation; 0 on the plain path).  Synchronises. */
 UCP_API ucp_status ucp_tie_recosts(ucp_inst* inst, int64_t* out);
 
-/* Work counters since creation (fast path; zeros on the plain path):
- * recosts = as ucp_tie_recosts; u1_pairs = (source, run of targets) pairs
- * the u1 kernel evaluated (the rest were skipped as negligible).  Either
- * output may be NULL.  Synchronises. */
-UCP_API ucp_status ucp_work_counters(ucp_inst* inst, int64_t* recosts,
-                                     int64_t* u1_pairs);
+/* Work counters since creation (fast path; zeros on the plain path), the
+ * first n of, in order:
+ *   0 recosts     as ucp_tie_recosts;
+ *   1 u1_pairs    (source, run of targets) pairs the u1 step summed directly;
+ *   2 u1_boxes    (box of sources, run of targets) pairs it summed by the
+ *                 boxes' Taylor expansions (pairs in neither were skipped as
+ *                 negligible);
+ *   3 u1_df_terms Taylor terms evaluated in double-float, over those box
+ *                 pairs (per target of the run, each of two polynomials);
+ *   4 u1_f32_terms Taylor terms evaluated in FP32, likewise.
+ * out holds n >= 0 entries (n <= 5).  Synchronises. */
+#define UCP_N_COUNTERS 5
+UCP_API ucp_status ucp_work_counters(ucp_inst* inst, int64_t* out, int32_t n);
 
 /* Per-kernel CUDA-event timing on the instance stream (off by default).
  * ucp_kernel_times fills up to cap entries: name (static), launches and
@@ -270,7 +277,7 @@ UCP_API ucp_status ucp_probe_alu(double* fp64_tflops, double* fp32_tflops,
  *   stream  cudaStream_t as void* (NULL: default stream); the call is
  *           asynchronous on it.
  * It allocates nothing: its intermediate buffers live in one fixed device
- * array of 6.75 MiB that every GPU loading the library holds until exit.
+ * array of 5.6 MiB that every GPU loading the library holds until exit.
  * Limits: n_x <= 32768 and n_y <= 32768, else UCP_E_ARG.  The first call on
  * a device looks up that array's address with the device current; make it
  * before any stream capture.  All calls share the array: calls that overlap

@@ -119,7 +119,7 @@ def load():
     L.ucp_tie_recosts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.ucp_probe_alu.argtypes = [_dp, _dp, _dp, _vp]
     L.ucp_work_counters.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64),
-                                    ctypes.POINTER(ctypes.c_int64)]
+                                    ctypes.c_int32]
     L.ucp_srv_create.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int32, _vp,
                                  ctypes.POINTER(_vp)]
     L.ucp_submit.argtypes = [_vp, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
@@ -285,11 +285,13 @@ class Instance:
         n = L.ucp_kernel_times(self.h, names, launches, ms, cap)
         return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
 
+    COUNTERS = ("recosts", "u1_pairs", "u1_boxes", "u1_df_terms", "u1_f32_terms")
+
     def work_counters(self) -> dict:
-        r, p = ctypes.c_int64(), ctypes.c_int64()
-        _check(load().ucp_work_counters(self.h, ctypes.byref(r), ctypes.byref(p)),
+        out = (ctypes.c_int64 * len(self.COUNTERS))()
+        _check(load().ucp_work_counters(self.h, out, len(self.COUNTERS)),
                "ucp_work_counters")
-        return {"recosts": r.value, "u1_pairs": p.value}
+        return dict(zip(self.COUNTERS, (int(v) for v in out)))
 
     def tie_recosts(self) -> int:
         v = ctypes.c_int64()

@@ -67,10 +67,10 @@ ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
 ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
                           cudaStream_t s) {
     const size_t n = members.size();
-    std::vector<BlockRef> maps[8], smaps[5], mmaps[5];
+    std::vector<BlockRef> maps[kBKinds], smaps[5], mmaps[5];
     for (size_t k = 0; k < n; ++k) {
         const ucp_inst* in = members[k];
-        for (int kind = 1; kind < 8; ++kind) {
+        for (int kind = 1; kind < kBKinds; ++kind) {
             const int64_t nb = batch_blocks(in->g, in->fv, kind);
             for (int64_t x = 0; x < nb; ++x) maps[kind].push_back({(int32_t)k, (int32_t)x});
         }
@@ -82,8 +82,8 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
         for (int64_t x = 0; x < nm; ++x) mm.push_back({(int32_t)k, (int32_t)x});
     }
     bs.host_maps.clear();
-    size_t off[8], soff[5], moff[5];
-    for (int kind = 0; kind < 8; ++kind) {
+    size_t off[kBKinds], soff[5], moff[5];
+    for (int kind = 0; kind < kBKinds; ++kind) {
         off[kind] = bs.host_maps.size();
         bs.host_maps.insert(bs.host_maps.end(), maps[kind].begin(), maps[kind].end());
     }
@@ -119,7 +119,7 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
     BatchLaunch& bl = bs.bl;
     bl.insts = bs.insts;
     bl.n_inst = (int)n;
-    for (int kind = 0; kind < 8; ++kind) {
+    for (int kind = 0; kind < kBKinds; ++kind) {
         bl.map[kind] = bs.maps + off[kind];
         bl.n_blocks[kind] = (int64_t)maps[kind].size();
     }

@@ -114,6 +114,14 @@ __device__ __forceinline__ dfloat df_acc(dfloat acc, float p, float e) {
     return df_norm(s, t);
 }
 
+// Exact double-float of an integer below 2^44 in magnitude, from two 32-bit
+// conversions (64-bit integer conversions run on the FP64 pipe).
+__device__ __forceinline__ dfloat df_from_i64(long long m) {
+    const int hi = (int)(m >> 22);              // |hi| < 2^22
+    const int lo = (int)(m & ((1 << 22) - 1));  // [0, 2^22)
+    return df_norm(__int2float_rn(hi) * 4194304.0f, __int2float_rn(lo));
+}
+
 __device__ __forceinline__ bool df_lt(dfloat a, dfloat b) {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }

@@ -17,14 +17,7 @@
 // plain path's arithmetic, operation for operation), so the fast path makes
 // the plain path's decisions.
 //
-// u1 step.  U_j = E[x1 | y1 = y_j] (Newton on the quadratic C_1, Section
-// III-D; closed form of Section IV-C), as the ratio of Gaussian sums with
-// each target's exponents shifted by an estimate m_j of their minimum.
-// Along the uniform y grid the shifted weight of source i obeys
-//   w_{i,j+1} = w_{i,j} exp(delta f_i) Psi_j,
-//   Psi_j = exp(-delta y_j - delta^2/2 + m_{j+1} - m_j),
-// so one exp per (source, run of R targets) replaces R of them.  Weights
-// below e^-46 of a target's largest are skipped.
+// The u1 step (U_j = E[x1 | y1 = y_j]) is in kernels_u1.cu.
 //
 // Arithmetic: the bulk runs in double-float on the FP32 pipe (df.cuh); FP64
 // only combines partial sums and re-costs near-ties.
@@ -38,7 +31,6 @@ namespace ucp {
 
 namespace {
 
-constexpr float kCut = 46.0f;     // skip weights below e^-46 of the maximum
 
 __device__ __forceinline__ double inv_one(const Geom& g) {
     return __longlong_as_double((int64_t)(1023 - g.shift) << 52);
@@ -48,13 +40,6 @@ __device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
 }
 __device__ __forceinline__ double x_of(const Geom& g, int64_t i) {
     return __dmul_rn((double)(i - g.hx), g.delta);
-}
-// exact double-float of an integer below 2^44 in magnitude, from two 32-bit
-// conversions (64-bit integer conversions run on the FP64 pipe)
-__device__ __forceinline__ dfloat df_from_i64(int64_t m) {
-    const int32_t hi = (int32_t)(m >> 22);              // |hi| < 2^22
-    const int32_t lo = (int32_t)(m & ((1 << 22) - 1));  // [0, 2^22)
-    return df_norm(__int2float_rn(hi) * 4194304.0f, __int2float_rn(lo));
 }
 
 // ---- exact serial FP64 cost (the plain path's arithmetic) -----------------
@@ -711,218 +696,6 @@ __global__ void k_fast_setup(Geom g, FastView f) {
     }
 }
 
-// ---- u1 step --------------------------------------------------------------
-
-// Per source: f_i (double-float) and exp(delta f_i).
-__device__ __forceinline__ void sources_body(const Geom& g, const FastView& f,
-                                             const int64_t* __restrict__ nu,
-                                             int64_t bx) {
-    const int64_t i = bx * blockDim.x + threadIdx.x;
-    if (i >= g.n_x) return;
-    const double v = value_of(g, nu[i]);
-    f.src_nu[i] = nu[i];
-    f.src_f[i] = df_from_double(v);
-    f.src_F[i] = df_from_double(exp(g.delta * v));
-}
-
-__global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
-    sources_body(g, f, nu, blockIdx.x);
-}
-
-// m_j: minimum over sources of the exponent, in FP32 (it only sets scales).
-// Block (bx, by) takes targets bx*128.. and the sources of chunk by; the
-// per-chunk minima are reduced by the Psi kernel (min is order free).
-constexpr int kShiftCh = 1024;
-constexpr int kShiftT = 128;
-struct ShiftSmem {
-    float sp[kShiftCh], sf[kShiftCh];
-};
-
-__device__ __forceinline__ void mmse_shift_body(const Geom& g, const FastView& f,
-                                                ShiftSmem& sm, int64_t bx, int64_t by) {
-    float* sp = sm.sp;
-    float* sf = sm.sf;
-    const int64_t j = bx * blockDim.x + threadIdx.x;
-    const float y = (float)((double)((j < g.n_y ? j : g.n_y - 1) - g.hy) * g.delta);
-    float m0 = FLT_MAX, m1 = FLT_MAX, m2 = FLT_MAX, m3 = FLT_MAX;
-    const int64_t c0 = by * f.chunk;
-    const int64_t c1 = min(c0 + f.chunk, g.n_x);
-    for (int64_t b = c0; b < c1; b += kShiftCh) {
-        const int cnt = (int)min((int64_t)kShiftCh, c1 - b);
-        __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            sp[k] = f.prior[b + k].hi;
-            sf[k] = f.src_f[b + k].hi;
-        }
-        __syncthreads();
-        int k = 0;
-        for (; k + 3 < cnt; k += 4) {
-            float d0 = y - sf[k], d1 = y - sf[k + 1], d2 = y - sf[k + 2], d3 = y - sf[k + 3];
-            m0 = fminf(m0, fmaf(0.5f * d0, d0, sp[k]));
-            m1 = fminf(m1, fmaf(0.5f * d1, d1, sp[k + 1]));
-            m2 = fminf(m2, fmaf(0.5f * d2, d2, sp[k + 2]));
-            m3 = fminf(m3, fmaf(0.5f * d3, d3, sp[k + 3]));
-        }
-        for (; k < cnt; ++k) {
-            const float d = y - sf[k];
-            m0 = fminf(m0, fmaf(0.5f * d, d, sp[k]));
-        }
-    }
-    if (j < g.n_y)
-        f.mshift_part[(size_t)by * g.n_y + j] = fminf(fminf(m0, m1), fminf(m2, m3));
-}
-
-__global__ void __launch_bounds__(kShiftT) k_mmse_shift(Geom g, FastView f) {
-    __shared__ ShiftSmem sm;
-    mmse_shift_body(g, f, sm, blockIdx.x, blockIdx.y);
-}
-
-// m_j = min over the source chunks, and
-// Psi_j = exp(-delta y_j - delta^2/2 + m_{j+1} - m_j) (double-float).
-__device__ __forceinline__ float shift_min(const Geom& g, const FastView& f, int64_t j) {
-    float m = FLT_MAX;
-    for (int c = 0; c < f.n_chunks; ++c) m = fminf(m, f.mshift_part[(size_t)c * g.n_y + j]);
-    return m;
-}
-
-__device__ __forceinline__ void mmse_psi_body(const Geom& g, const FastView& f,
-                                              int64_t bx) {
-    const int64_t j = bx * blockDim.x + threadIdx.x;
-    if (j >= g.n_y) return;
-    const float mj = shift_min(g, f, j);
-    f.mshift[j] = mj;
-    const double y = (double)(j - g.hy) * g.delta;
-    const double dm = j + 1 < g.n_y ? (double)shift_min(g, f, j + 1) - (double)mj : 0.0;
-    f.psi[j] = df_from_double(exp(-g.delta * y - 0.5 * g.delta * g.delta + dm));
-}
-
-__global__ void k_mmse_psi(Geom g, FastView f) { mmse_psi_body(g, f, blockIdx.x); }
-
-constexpr int kMmseThreads = 64;
-constexpr int kMmseSrc = 256;   // sources staged in shared memory at a time
-
-struct MmseSmem {
-    int64_t snu[kMmseSrc];
-    dfloat spr[kMmseSrc], sf[kMmseSrc], sF[kMmseSrc];
-    dfloat st64[47];
-    dfloat spsi[15][kMmseThreads];   // Psi along each thread's run
-};
-
-template <int R>
-__device__ __forceinline__ void mmse_main_body(const Geom& g, const FastView& f,
-                                               MmseSmem& sm, int64_t bx, int64_t by) {
-    int64_t* snu = sm.snu;
-    dfloat* spr = sm.spr;
-    dfloat* sf = sm.sf;
-    dfloat* sF = sm.sF;
-    dfloat* st64 = sm.st64;
-    if (threadIdx.x < 47) st64[threadIdx.x] = f.t64[threadIdx.x];
-    const int64_t j0 = (bx * kMmseThreads + threadIdx.x) * R;
-    const int64_t c0 = by * f.chunk;
-    const int64_t c1 = min(c0 + f.chunk, g.n_x);
-    const int64_t jc0 = j0 < g.n_y ? j0 : g.n_y - 1;
-    const float m0 = f.mshift[jc0];
-    float smax = -FLT_MAX;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int64_t j = j0 + k < g.n_y ? j0 + k : g.n_y - 1;
-        smax = fmaxf(smax, f.mshift[j]);
-        if (k + 1 < R) sm.spsi[k][threadIdx.x] = f.psi[j];
-    }
-    const float ya = (float)((double)(j0 - g.hy) * g.delta);
-    const float yb = (float)((double)(j0 + R - 1 - g.hy) * g.delta);
-    const float cut = kCut + smax + 0.01f;
-    const int64_t ybase = (j0 - g.hy) * g.one;
-    dfloat N[R], D[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) { N[k] = {0.f, 0.f}; D[k] = {0.f, 0.f}; }
-    unsigned evaluated = 0;   // (source, run) pairs not skipped
-    for (int64_t b = c0; b < c1; b += kMmseSrc) {
-        const int cnt = (int)min((int64_t)kMmseSrc, c1 - b);
-        __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += kMmseThreads) {
-            snu[k] = f.src_nu[b + k];
-            spr[k] = f.prior[b + k];
-            sf[k] = f.src_f[b + k];
-            sF[k] = f.src_F[b + k];
-        }
-        __syncthreads();
-        // sources that touch this run, then two at a time (independent
-        // recurrences interleave)
-        int s = 0;
-        while (s < cnt) {
-            int sel[2];
-            int ns = 0;
-            for (; s < cnt && ns < 2; ++s) {
-                const float fh = sf[s].hi;
-                const float dmin = fmaxf(0.f, fmaxf(ya - fh, fh - yb));
-                if (fmaf(0.5f * dmin, dmin, spr[s].hi) <= cut) sel[ns++] = s;
-            }
-            if (ns == 0) break;
-            evaluated += (unsigned)ns;
-            dfloat w[2], F[2], fv[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int src = sel[q < ns ? q : 0];
-                fv[q] = sf[src];
-                F[q] = sF[src];
-                // anchor weight exp(m_j0 - prior - (y_j0 - f)^2 / 2)
-                const dfloat d0 = df_mul(df_from_i64(ybase - snu[src]),
-                                         dfloat{f.step_hi, f.step_lo});
-                dfloat ex = df_add(spr[src], df_mul_f(df_mul(d0, d0), 0.5f));
-                ex = df_add_f(df_neg(ex), m0);
-                if (ex.hi < -87.0f) ex = {-87.0f, 0.f};
-                w[q] = df_exp(ex, st64);
-            }
-            if (ns == 1) w[1] = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    float pp, pe;
-                    df_mul_raw(w[q], fv[q], pp, pe);
-                    N[k] = df_acc(N[k], pp, pe);
-                    D[k] = df_add(D[k], w[q]);
-                    if (k + 1 < R)
-                        w[q] = df_mul(w[q], df_mul(F[q], sm.spsi[k][threadIdx.x]));
-                }
-            }
-        }
-    }
-    if (f.n_pairs && evaluated) atomicAdd((unsigned long long*)f.n_pairs,
-                                          (unsigned long long)evaluated);
-    double* pN = f.partN + (size_t)by * g.n_y;
-    double* pD = f.partD + (size_t)by * g.n_y;
-#pragma unroll
-    for (int k = 0; k < R; ++k)
-        if (j0 + k < g.n_y) {
-            pN[j0 + k] = df_to_double(N[k]);
-            pD[j0 + k] = df_to_double(D[k]);
-        }
-}
-
-template <int R>
-__global__ void __launch_bounds__(kMmseThreads) k_mmse_main(Geom g, FastView f) {
-    __shared__ MmseSmem sm;
-    mmse_main_body<R>(g, f, sm, blockIdx.x, blockIdx.y);
-}
-
-__device__ __forceinline__ void mmse_combine_body(const Geom& g, const FastView& f,
-                                                  double* __restrict__ U, int64_t bx) {
-    const int64_t j = bx * blockDim.x + threadIdx.x;
-    if (j >= g.n_y) return;
-    double n = 0.0, d = 0.0;
-    for (int c = 0; c < f.n_chunks; ++c) {
-        n += f.partN[(size_t)c * g.n_y + j];
-        d += f.partD[(size_t)c * g.n_y + j];
-    }
-    U[j] = n / d;
-}
-
-__global__ void k_mmse_combine(Geom g, FastView f, double* __restrict__ U) {
-    mmse_combine_body(g, f, U, blockIdx.x);
-}
-
 // ---- J --------------------------------------------------------------------
 
 constexpr int kJThreads = 256;
@@ -982,43 +755,6 @@ __global__ void __launch_bounds__(256, 2) kb_search(const InstDev* insts, const 
                    sd.f.n_exact, tie_smem, r.local);
 }
 
-__global__ void kb_sources(const InstDev* insts, const BlockRef* map) {
-    __shared__ InstDev sd;
-    const BlockRef r = stage(insts, map, sd);
-    sources_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], r.local);
-}
-
-__global__ void __launch_bounds__(128) kb_mmse_shift(const InstDev* insts,
-                                                     const BlockRef* map) {
-    __shared__ InstDev sd;
-    __shared__ ShiftSmem sm;
-    const BlockRef r = stage(insts, map, sd);
-    const int64_t jb = (sd.g.n_y + kShiftT - 1) / kShiftT;
-    mmse_shift_body(sd.g, sd.f, sm, r.local % jb, r.local / jb);
-}
-
-__global__ void kb_mmse_psi(const InstDev* insts, const BlockRef* map) {
-    __shared__ InstDev sd;
-    const BlockRef r = stage(insts, map, sd);
-    mmse_psi_body(sd.g, sd.f, r.local);
-}
-
-template <int R>
-__global__ void __launch_bounds__(kMmseThreads) kb_mmse_main(const InstDev* insts,
-                                                             const BlockRef* map) {
-    __shared__ InstDev sd;
-    __shared__ MmseSmem sm;
-    const BlockRef r = stage(insts, map, sd);
-    const int64_t jb = sd.f.j_blocks;
-    mmse_main_body<R>(sd.g, sd.f, sm, r.local % jb, r.local / jb);
-}
-
-__global__ void kb_mmse_combine(const InstDev* insts, const BlockRef* map) {
-    __shared__ InstDev sd;
-    const BlockRef r = stage(insts, map, sd);
-    mmse_combine_body(sd.g, sd.f, sd.U, r.local);
-}
-
 __global__ void kb_build_E(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
@@ -1067,16 +803,6 @@ inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs)
 
 // ---- host-side plan and launches ------------------------------------------
 
-int mmse_run_length(const Geom& g) {
-    // keep the exponent change along a run below ~15 (float range of the
-    // double-float weights): R * delta * (Y + max |f|) <= 15
-    const double F = (double)((g.hr + 2 * g.q) > g.hx ? (g.hr + 2 * g.q) : g.hx) * g.delta;
-    const double slope = g.delta * ((double)g.hy * g.delta + F);
-    int R = 16;
-    while (R > 1 && (R - 1) * slope > 15.0) R /= 2;
-    return R;
-}
-
 void fast_plan(const Geom& g, FastPlan* fp) {
     // cells reachable by any candidate: coarse extremes plus the refinement
     // reach (< 1.15 q), or the x0 range (identity init), with margin
@@ -1086,19 +812,7 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     fp->n_pos = 2 * ext + 2;
     fp->jlo = fp->c_lo - g.hw + g.hy;
     fp->n_e = fp->n_pos + g.n_w + 1;
-    fp->run = mmse_run_length(g);
-    const int64_t per_block = (int64_t)kMmseThreads * fp->run;
-    const int64_t jblocks = (g.n_y + per_block - 1) / per_block;
-    int64_t chunks = (12 * 152 + jblocks - 1) / jblocks;
-    const int64_t min_chunks = (g.n_x + 4095) / 4096;   // accuracy of the sums
-    if (chunks < min_chunks) chunks = min_chunks;
-    const int64_t max_chunks = (g.n_x + 127) / 128;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
-    const int64_t chunk = ((g.n_x + chunks - 1) / chunks + 63) / 64 * 64;
-    fp->chunk = chunk;
-    fp->n_chunks = (int)((g.n_x + chunk - 1) / chunk);
-    fp->j_blocks = jblocks;
+    u1_plan(g, 32, fp);
     fp->J_blocks = (g.n_x + kJThreads - 1) / kJThreads;
     // split the taps so that the table kernel fills the GPU (~4 blocks/SM)
     const int64_t pblocks = (fp->n_pos + kTabT - 1) / kTabT;
@@ -1116,31 +830,6 @@ void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
     int64_t n = g.n_w > g.n_x ? g.n_w : g.n_x;
     n = n > 47 ? n : 47;
     k_fast_setup<<<blocks(n, 256), 256, 0, s>>>(g, f);
-}
-
-void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
-                      double* U, cudaStream_t s, Prof* prof) {
-    cudaEvent_t ev;
-    int k = prof ? prof->begin("mmse_sources", &ev) : -1;
-    k_sources<<<blocks(g.n_x, 256), 256, 0, s>>>(g, f, nu);
-    if (prof) prof->end(k, ev);
-    k = prof ? prof->begin("mmse_shift", &ev) : -1;
-    k_mmse_shift<<<dim3(blocks(g.n_y, kShiftT), (unsigned)f.n_chunks), kShiftT, 0, s>>>(g, f);
-    k_mmse_psi<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f);
-    if (prof) prof->end(k, ev);
-    k = prof ? prof->begin("mmse_main", &ev) : -1;
-    dim3 grid((unsigned)f.j_blocks, (unsigned)f.n_chunks);
-    switch (f.run) {
-        case 16: k_mmse_main<16><<<grid, kMmseThreads, 0, s>>>(g, f); break;
-        case 8: k_mmse_main<8><<<grid, kMmseThreads, 0, s>>>(g, f); break;
-        case 4: k_mmse_main<4><<<grid, kMmseThreads, 0, s>>>(g, f); break;
-        case 2: k_mmse_main<2><<<grid, kMmseThreads, 0, s>>>(g, f); break;
-        default: k_mmse_main<1><<<grid, kMmseThreads, 0, s>>>(g, f); break;
-    }
-    if (prof) prof->end(k, ev);
-    k = prof ? prof->begin("mmse_combine", &ev) : -1;
-    k_mmse_combine<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f, U);
-    if (prof) prof->end(k, ev);
 }
 
 void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
@@ -1182,7 +871,9 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
         case kBSearch: return (g.n_x * g.n_refine + 255) / 256;
         case kBPerX: return (g.n_x + 255) / 256;
-        case kBShift: return (g.n_y + kShiftT - 1) / kShiftT * fp.n_chunks;
+        case kBTile:
+        case kBBox:
+        case kBRun: return u1_batch_blocks(g, fp, kind);
         case kBPerY: return (g.n_y + 255) / 256;
         case kBTabPart: return (fp.n_pos + kTabT - 1) / kTabT * fp.tab_splits;
         case kBTabComb: return (fp.n_pos + 255) / 256;
@@ -1193,10 +884,6 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
         case kBJPart: return fp.J_blocks;
     }
     return 0;
-}
-
-int64_t batch_mmse_blocks(const Geom&, const FastPlan& fp) {
-    return fp.j_blocks * fp.n_chunks;
 }
 
 void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
@@ -1213,21 +900,7 @@ void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
             default: kb_search<32><<<nb, 256, 0, s>>>(d, m); break;
         }
     }
-    kb_sources<<<(unsigned)bl.n_blocks[kBPerX], 256, 0, s>>>(d, bl.map[kBPerX]);
-    kb_mmse_shift<<<(unsigned)bl.n_blocks[kBShift], kShiftT, 0, s>>>(d, bl.map[kBShift]);
-    kb_mmse_psi<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
-    for (int r = 0; r < 5; ++r) {
-        if (bl.mmse_blocks[r] == 0) continue;
-        const unsigned nb = (unsigned)bl.mmse_blocks[r];
-        switch (r) {
-            case 0: kb_mmse_main<1><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
-            case 1: kb_mmse_main<2><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
-            case 2: kb_mmse_main<4><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
-            case 3: kb_mmse_main<8><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
-            default: kb_mmse_main<16><<<nb, kMmseThreads, 0, s>>>(d, bl.mmse_map[r]); break;
-        }
-    }
-    kb_mmse_combine<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
+    launch_batch_u1(bl, s);
     kb_build_E<<<(unsigned)bl.n_blocks[kBBuildE], 256, 0, s>>>(d, bl.map[kBBuildE]);
     kb_tables_part<<<(unsigned)bl.n_blocks[kBTabPart], kTabT, 0, s>>>(d, bl.map[kBTabPart]);
     kb_tables_combine<<<(unsigned)bl.n_blocks[kBTabComb], 256, 0, s>>>(d, bl.map[kBTabComb]);

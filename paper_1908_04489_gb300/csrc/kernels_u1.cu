@@ -1,0 +1,713 @@
+// kernels_u1.cu -- the u1 step of the fast path (precision = 1):
+//   U_j = E[x1 | y1 = y_j] = sum_i e^{-e_ij} f_i / sum_i e^{-e_ij},
+//   e_ij = p_i + (y_j - f_i)^2 / 2,  p_i = x_i^2 / (2 sigma^2),
+// the closed form of Section IV-C with x1 = f(x0) on the x0 grid and the
+// Gaussian noise of Section V-A.
+//
+// Runs.  Targets are taken in runs of R (j0 = rR, ..., j0 + R - 1).  Within a
+// run every weight of target j is scaled by the same factor
+// exp(m_r + (y_j^2 - y_j0^2) / 2), which cancels in the ratio, leaving
+//   w_ik = exp(m_r - e_{i,j0}) exp(k delta f_i)        (j = j0 + k),
+// one exponential per (source, run) and one product per target.  m_r is a
+// lower bound of min_i e_{i,j0}; it only sets the floating-point scale.
+//
+// Boxes.  Sources are cut into tiles of consecutive x0 points and each tile,
+// greedily, into at most kBoxMax boxes of consecutive sources whose f values
+// lie within 2 kHMax.  For a box with centre c, d_i = f_i - c (|d_i| <= h),
+// a power of two s >= h, pm = min_i (p_i + d_i^2/2), q_i = exp(pm - p_i -
+// d_i^2/2) and moments M_n = sum_i q_i (d_i / s)^n, the box's share of a
+// target with z = y_j - c and u = z s is
+//   sum_i w_ik     = A C^k sum_n u^n M_n / n!,
+//   sum_i w_ik f_i = A C^k sum_n u^n (c M_n + s M_{n+1}) / n!,
+//   A = exp(m_r - pm - (y_j0 - c)^2 / 2),  C = exp(delta c),
+// the Taylor form of the fast Gauss transform (Greengard and Strain, SIAM J.
+// Sci. Stat. Comput. 12, 1991).  With zeta = |z| h the tail after p terms is
+// at most e^{2 zeta} zeta^p / p! of the box's exact share; p is chosen per
+// (box, run) so that this is below 2^-64, and the expansion is used only
+// where zeta <= kZetaMax and it is cheaper than the direct sum over the
+// box's sources, which is taken otherwise.  Terms whose bound is below 2^-40
+// are summed in FP32, the rest in double-float.
+//
+// Negligible work is skipped: a (box, run) or (source, run) pair is left out
+// when every weight it holds is below e^-46 of its target's largest.
+//
+// Every sum runs in a fixed order (per run: the boxes of a tile in order;
+// per target: the tiles in order), so results are bit-reproducible and the
+// same alone or in a batch.
+#include <float.h>
+
+#include "df.cuh"
+#include "ucp_fast.cuh"
+
+namespace ucp {
+
+namespace {
+
+constexpr float kCut = 46.0f;       // skip weights below e^-46 of the maximum
+constexpr float kHMax = 0.05f;      // box half width aimed at when grouping
+constexpr float kHMoments = 0.25f;  // boxes wider than this get no moments
+constexpr float kZetaMax = 1.0f;    // largest |y - c| h expanded
+constexpr int kU1Runs = 32;         // runs per block of the u1 kernel (1 warp)
+constexpr int kMomT = 128;          // threads per box of the moment kernel
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
+    const double inv = __longlong_as_double((int64_t)(1023 - g.shift) << 52);
+    return __dmul_rn(__dmul_rn((double)nu, g.delta), inv);
+}
+
+// ---- sources ----------------------------------------------------------------
+
+// Per source: f_i (double-float) and exp(delta f_i).
+__device__ __forceinline__ void sources_body(const Geom& g, const FastView& f,
+                                             const int64_t* __restrict__ nu,
+                                             int64_t bx) {
+    const int64_t i = bx * blockDim.x + threadIdx.x;
+    if (i >= g.n_x) return;
+    const double v = value_of(g, nu[i]);
+    f.src_nu[i] = nu[i];
+    f.src_f[i] = df_from_double(v);
+    f.src_F[i] = df_from_double(exp(g.delta * v));
+}
+
+// ---- boxes ------------------------------------------------------------------
+
+// One warp per tile: greedy grouping of consecutive sources into boxes whose
+// f values (leading floats) span at most 2 kHMax; the last box of a tile
+// takes whatever is left once kBoxMax - 1 boxes are closed.
+__device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
+                                              int64_t t) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t0 = t * f.tile;
+    const int64_t t1 = min(t0 + f.tile, g.n_x);
+    const int64_t slot0 = t * kBoxMax;
+    const float wmax = 2.0f * kHMax;
+    int nb = 0;
+    int64_t sb = t0;
+    float bmin = FLT_MAX, bmax = -FLT_MAX;
+    for (int64_t base = t0; base < t1; base += 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < t1;
+        const float fi = valid ? f.src_f[i].hi : 0.0f;
+        int from = 0;
+        for (;;) {
+            const bool part = valid && lane >= from;
+            float vmin = part ? fi : FLT_MAX, vmax = part ? fi : -FLT_MAX;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float a = __shfl_up_sync(kFull, vmin, d);
+                const float b = __shfl_up_sync(kFull, vmax, d);
+                if (lane >= d) {
+                    vmin = fminf(vmin, a);
+                    vmax = fmaxf(vmax, b);
+                }
+            }
+            const float rmin = fminf(bmin, vmin), rmax = fmaxf(bmax, vmax);
+            const bool bad = part && nb < kBoxMax - 1 && rmax - rmin > wmax;
+            const unsigned m = __ballot_sync(kFull, bad);
+            if (m == 0) {
+                bmin = __shfl_sync(kFull, rmin, 31);
+                bmax = __shfl_sync(kFull, rmax, 31);
+                break;
+            }
+            const int l = __ffs(m) - 1;   // first source that does not fit
+            const float cmin = __shfl_sync(kFull, rmin, l > 0 ? l - 1 : 0);
+            const float cmax = __shfl_sync(kFull, rmax, l > 0 ? l - 1 : 0);
+            if (lane == 0) {
+                f.box_s0[slot0 + nb] = (int32_t)sb;
+                f.box_n[slot0 + nb] = (int32_t)(base + l - sb);
+                f.box_rng[slot0 + nb] = make_float4(l > from ? cmin : bmin,
+                                                    l > from ? cmax : bmax, 0.f, 0.f);
+            }
+            ++nb;
+            sb = base + l;
+            bmin = FLT_MAX;
+            bmax = -FLT_MAX;
+            from = l;
+        }
+    }
+    if (lane == 0) {
+        f.box_s0[slot0 + nb] = (int32_t)sb;
+        f.box_n[slot0 + nb] = (int32_t)(t1 - sb);
+        f.box_rng[slot0 + nb] = make_float4(bmin, bmax, 0.f, 0.f);
+        f.box_cnt[t] = nb + 1;
+    }
+}
+
+// One block per box slot: centre c, half width h, scale pm, smallest prior,
+// exp(delta c) and, for boxes narrow enough to be expanded, the Taylor
+// coefficients.  Partial moments are summed over the block in a fixed tree.
+struct MomSmem {
+    dfloat red[kMomT][kBoxTerms + 1];
+    float fr[3][kMomT / 32];
+};
+
+__device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& f,
+                                                 MomSmem& sm, int64_t slot) {
+    const int64_t t = slot / kBoxMax;
+    if (slot - t * kBoxMax >= f.box_cnt[t]) return;   // the same for the block
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t s0 = f.box_s0[slot];
+    const int n = f.box_n[slot];
+    const float4 rg = f.box_rng[slot];
+    const float c = 0.5f * (rg.x + rg.y);
+    float hv = 0.0f, pv = FLT_MAX, pmn = FLT_MAX;
+    for (int s = tid; s < n; s += kMomT) {
+        const dfloat d = df_add_f(f.src_f[s0 + s], -c);
+        const float pr = f.prior[s0 + s].hi;
+        hv = fmaxf(hv, fabsf(d.hi) + fabsf(d.lo));
+        pv = fminf(pv, fmaf(0.5f * d.hi, d.hi, pr));
+        pmn = fminf(pmn, pr);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hv = fmaxf(hv, __shfl_xor_sync(kFull, hv, o));
+        pv = fminf(pv, __shfl_xor_sync(kFull, pv, o));
+        pmn = fminf(pmn, __shfl_xor_sync(kFull, pmn, o));
+    }
+    if (lane == 0) {
+        sm.fr[0][warp] = hv;
+        sm.fr[1][warp] = pv;
+        sm.fr[2][warp] = pmn;
+    }
+    __syncthreads();
+    hv = sm.fr[0][0];
+    pv = sm.fr[1][0];
+    pmn = sm.fr[2][0];
+#pragma unroll
+    for (int w = 1; w < kMomT / 32; ++w) {
+        hv = fmaxf(hv, sm.fr[0][w]);
+        pv = fminf(pv, sm.fr[1][w]);
+        pmn = fminf(pmn, sm.fr[2][w]);
+    }
+    const float h = hv * (1.0f + 0x1p-20f);
+    const float pm = pv;
+    const bool expand = h <= kHMoments;
+    int e2 = 0;
+    frexpf(h, &e2);                        // h < 2^e2
+    const float sc = h > 0.0f ? ldexpf(1.0f, e2) : 1.0f;
+    const float inv_sc = 1.0f / sc;        // exact: a power of two
+    if (tid == 0) {
+        f.box_geo[slot] = make_float4(c, h, pm, pmn);
+        f.box_rng[slot] = make_float4(rg.x, rg.y, expand ? h : INFINITY, sc);
+        f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
+    }
+    if (!expand) return;   // the same for the block
+    dfloat M[kBoxTerms + 1];
+#pragma unroll
+    for (int m = 0; m <= kBoxTerms; ++m) M[m] = {0.0f, 0.0f};
+    for (int s = tid; s < n; s += kMomT) {
+        const dfloat d = df_add_f(f.src_f[s0 + s], -c);
+        dfloat ex = df_add_f(df_neg(f.prior[s0 + s]), pm);
+        ex = df_add(ex, df_mul_f(df_mul(d, d), -0.5f));
+        if (ex.hi < -87.0f) ex = {-87.0f, 0.0f};
+        dfloat q = df_exp(ex, f.t64);
+        const dfloat ds = {d.hi * inv_sc, d.lo * inv_sc};   // d / s, |d / s| <= 1
+#pragma unroll
+        for (int m = 0; m <= kBoxTerms; ++m) {
+            M[m] = df_add(M[m], q);
+            if (m < kBoxTerms) q = df_mul(q, ds);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m <= kBoxTerms; ++m) sm.red[tid][m] = M[m];
+    __syncthreads();
+    for (int w = kMomT / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+#pragma unroll
+            for (int m = 0; m <= kBoxTerms; ++m)
+                sm.red[tid][m] = df_add(sm.red[tid][m], sm.red[tid + w][m]);
+        }
+        __syncthreads();
+    }
+    if (tid < kBoxTerms) {
+        double fact = 1.0;
+        for (int m = 2; m <= tid; ++m) fact *= (double)m;   // n! (rounded above 22!)
+        const dfloat inv = df_from_double(1.0 / fact);
+        const dfloat Mn = sm.red[0][tid], Mn1 = sm.red[0][tid + 1];
+        dfloat* co = f.box_coef + slot * (2 * kBoxTerms);
+        co[tid] = df_mul(Mn, inv);
+        co[kBoxTerms + tid] = df_mul(df_add(df_mul_f(Mn, c), df_mul_f(Mn1, sc)), inv);
+    }
+}
+
+// ---- per-run scale and cut --------------------------------------------------
+
+// One warp per run, from the box summaries:
+//   run_lo <= min_i e_{i,j0}          (lower bound; the run's scale m_r)
+//   run_hi >= min_i e_ij for every j of the run (upper bound; the cut).
+// Over a box, e_i(y) >= pmin + dist(y, [fmin, fmax])^2 / 2 and
+// e_i(y) >= pm + z^2/2 - h|z|; the source attaining pm has
+// e(y) <= pm + z^2/2 + h|z| (z = y - c), convex in y.
+constexpr int kRunT = 256;
+
+__device__ __forceinline__ void run_shift_body(const Geom& g, const FastView& f,
+                                               int64_t bx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = bx * (kRunT / 32) + (threadIdx.x >> 5);
+    if (r >= f.n_runs) return;   // the same for the warp
+    const int64_t j0 = r * f.run;
+    const float ya = (float)((double)(j0 - g.hy) * g.delta);
+    const float yb = (float)((double)(j0 + f.run - 1 - g.hy) * g.delta);
+    float lo = FLT_MAX, hi = FLT_MAX;
+    const int nslot = f.n_tiles * kBoxMax;
+    for (int s = lane; s < nslot; s += 32) {
+        const int t = s / kBoxMax;
+        if (s - t * kBoxMax >= f.box_cnt[t]) continue;
+        const float4 geo = f.box_geo[s];
+        const float4 rg = f.box_rng[s];
+        const float d1 = fmaxf(0.0f, fmaxf(rg.x - ya, ya - rg.y));
+        const float lb1 = fmaf(0.5f * d1, d1, geo.w);
+        const float za = fabsf(ya - geo.x);
+        const float lb2 = za >= geo.y ? geo.z + za * (0.5f * za - geo.y)
+                                      : geo.z - 0.5f * geo.y * geo.y;
+        lo = fminf(lo, fmaxf(lb1, lb2));
+        const float zm = fmaxf(za, fabsf(yb - geo.x));
+        hi = fminf(hi, geo.z + zm * (0.5f * zm + geo.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = fminf(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    if (lane == 0) {
+        f.run_lo[r] = lo - (0.01f + 1e-5f * fabsf(lo));
+        f.run_hi[r] = hi + (0.01f + 1e-5f * fabsf(hi));
+    }
+}
+
+// ---- the u1 sums ------------------------------------------------------------
+
+// Taylor terms for zeta = |z| h: p = terms kept (tail bound <= 2^-64 of the
+// box's share; -1 if more than kBoxTerms would be needed), n1 = first term
+// summed in FP32 (its tail bound <= 2^-40).
+__device__ __forceinline__ void taylor_terms(float zeta, int& n1, int& p) {
+    float term = expf(2.0f * zeta) * 1.001f;   // e^{2 zeta} zeta^n / n!, n = 0
+    n1 = -1;
+    p = -1;
+    for (int n = 0; n <= kBoxTerms; ++n) {
+        if (n1 < 0 && term <= 0x1p-40f) n1 = n;
+        if (term <= 0x1p-64f) {
+            p = n;
+            break;
+        }
+        term *= zeta * 1.001f / (float)(n + 1);
+    }
+    if (n1 < 0) n1 = p;
+}
+
+// Box share by its Taylor expansion, added to the run's sums.
+template <int R>
+__device__ __forceinline__ void fgt_box(const FastView& f, int64_t slot, float c,
+                                        float pm, float sc, dfloat y0, dfloat dl,
+                                        float m_lo, int p, int n1, const dfloat* st64,
+                                        dfloat (&N)[R], dfloat (&D)[R]) {
+    const dfloat* __restrict__ ca = f.box_coef + slot * (2 * kBoxTerms);
+    const dfloat* __restrict__ cb = ca + kBoxTerms;
+    const dfloat z0 = df_add_f(y0, -c);
+    float sh, sl;
+    two_sum(m_lo, -pm, sh, sl);
+    dfloat ex = df_add(df_norm(sh, sl), df_mul_f(df_mul(z0, z0), -0.5f));
+    if (ex.hi < -87.0f) ex = {-87.0f, 0.0f};
+    dfloat E = df_exp(ex, st64);
+    const dfloat C = f.box_C[slot];
+    // u = z s and its step delta s (scaling by a power of two is exact)
+    dfloat z = {z0.hi * sc, z0.lo * sc};
+    const dfloat du = {dl.hi * sc, dl.lo * sc};
+    constexpr int Q = R < 4 ? R : 4;
+#pragma unroll
+    for (int k0 = 0; k0 < R; k0 += Q) {
+        dfloat zq[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            zq[q] = z;
+            z = df_add(z, du);
+        }
+        float tD[Q], tN[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) tD[q] = tN[q] = 0.0f;
+        for (int n = p - 1; n >= n1; --n) {
+            const float an = ca[n].hi, bn = cb[n].hi;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                tD[q] = fmaf(tD[q], zq[q].hi, an);
+                tN[q] = fmaf(tN[q], zq[q].hi, bn);
+            }
+        }
+        dfloat aD[Q], aN[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            aD[q] = {tD[q], 0.0f};
+            aN[q] = {tN[q], 0.0f};
+        }
+        for (int n = n1 - 1; n >= 0; --n) {
+            const dfloat an = ca[n], bn = cb[n];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                aD[q] = df_add(df_mul(aD[q], zq[q]), an);
+                aN[q] = df_add(df_mul(aN[q], zq[q]), bn);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            D[k0 + q] = df_add(D[k0 + q], df_mul(E, aD[q]));
+            N[k0 + q] = df_add(N[k0 + q], df_mul(E, aN[q]));
+            if (k0 + q + 1 < R) E = df_mul(E, C);
+        }
+    }
+}
+
+// Box share by the direct sum over its sources (two recurrences at a time),
+// skipping sources whose weights are all negligible.  Returns the number of
+// (source, run) pairs evaluated.
+template <int R>
+__device__ __forceinline__ unsigned direct_box(const FastView& f, int64_t s0, int n,
+                                               float ya, float yb, float cut,
+                                               float m_lo, int64_t ybase,
+                                               const dfloat* st64, dfloat (&N)[R],
+                                               dfloat (&D)[R]) {
+    const dfloat step = {f.step_hi, f.step_lo};
+    unsigned evaluated = 0;
+    int s = 0;
+    while (s < n) {
+        int64_t sel0 = 0, sel1 = 0;
+        int ns = 0;
+        for (; s < n && ns < 2; ++s) {
+            const int64_t i = s0 + s;
+            const float fh = f.src_f[i].hi;
+            const float dmin = fmaxf(0.0f, fmaxf(ya - fh, fh - yb));
+            if (fmaf(0.5f * dmin, dmin, f.prior[i].hi) <= cut) {
+                if (ns == 0) sel0 = i;
+                else sel1 = i;
+                ++ns;
+            }
+        }
+        if (ns == 0) break;
+        if (ns == 1) sel1 = sel0;
+        evaluated += (unsigned)ns;
+        dfloat w[2], F[2], fv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int64_t i = q == 0 ? sel0 : sel1;
+            fv[q] = f.src_f[i];
+            F[q] = f.src_F[i];
+            // w = exp(m_r - p_i - (y_j0 - f_i)^2 / 2), y_j0 - f_i exact in units of step
+            const dfloat d0 = df_mul(df_from_i64(ybase - f.src_nu[i]), step);
+            dfloat ex = df_add(f.prior[i], df_mul_f(df_mul(d0, d0), 0.5f));
+            ex = df_add_f(df_neg(ex), m_lo);
+            if (ex.hi < -87.0f) ex = {-87.0f, 0.0f};
+            w[q] = df_exp(ex, st64);
+        }
+        if (ns == 1) w[1] = {0.0f, 0.0f};
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                float pp, pe;
+                df_mul_raw(w[q], fv[q], pp, pe);
+                N[k] = df_acc(N[k], pp, pe);
+                D[k] = df_add(D[k], w[q]);
+                if (k + 1 < R) w[q] = df_mul(w[q], F[q]);
+            }
+        }
+    }
+    return evaluated;
+}
+
+// Block (bx, t): runs bx*kU1Runs.. (one per thread) against the boxes of
+// tile t; writes the tile's partial sums of every target of those runs.
+template <int R>
+__device__ __forceinline__ void u1_main_body(const Geom& g, const FastView& f,
+                                             dfloat* st64, int64_t bx, int64_t t) {
+    for (int k = threadIdx.x; k < 47; k += blockDim.x) st64[k] = f.t64[k];
+    __syncthreads();
+    const int64_t r0 = bx * kU1Runs + threadIdx.x;
+    const int64_t r = r0 < f.n_runs ? r0 : f.n_runs - 1;
+    const int64_t j0 = r * R;
+    const float m_lo = f.run_lo[r];
+    const float cut = kCut + f.run_hi[r] + 0.01f;
+    const float ya = (float)((double)(j0 - g.hy) * g.delta);
+    const float yb = (float)((double)(j0 + R - 1 - g.hy) * g.delta);
+    const dfloat dl = {f.delta_hi, f.delta_lo};
+    const dfloat y0 = df_mul(df_from_i64(j0 - g.hy), dl);
+    const int64_t ybase = (j0 - g.hy) * g.one;
+    dfloat N[R], D[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) N[k] = D[k] = {0.0f, 0.0f};
+    unsigned n_dir = 0, n_box = 0, t_df = 0, t_f32 = 0;
+    const int nb = f.box_cnt[t];
+    for (int k = 0; k < nb; ++k) {
+        const int64_t slot = t * kBoxMax + k;
+        const float4 geo = f.box_geo[slot];   // c, h, pm, pmin
+        const float4 rg = f.box_rng[slot];    // fmin, fmax, h (expandable) or inf
+        // lower bound of e over (box, run); skip the box if it exceeds the cut
+        const float d1 = fmaxf(0.0f, fmaxf(rg.x - yb, ya - rg.y));
+        const float lb1 = fmaf(0.5f * d1, d1, geo.w);
+        const float dz = fmaxf(0.0f, fmaxf(geo.x - yb, ya - geo.x));
+        const float lb2 = dz >= geo.y ? geo.z + dz * (0.5f * dz - geo.y)
+                                      : geo.z - 0.5f * geo.y * geo.y;
+        const float lb = fmaxf(lb1, lb2);
+        if (lb - 1e-5f * (1.0f + fabsf(lb)) > cut) continue;
+        const int n = f.box_n[slot];
+        const float zeta = rg.z * fmaxf(fabsf(ya - geo.x), fabsf(yb - geo.x)) * 1.001f;
+        int p = -1, n1 = 0;
+        if (zeta <= kZetaMax) {
+            taylor_terms(zeta, n1, p);
+            if (p >= 0) {
+                const int cf = R * (2 * (18 * n1 + 2 * (p - n1)) + 40) + 300;
+                const int cd = n * (30 * R + 130);
+                if (cf >= cd) p = -1;
+            }
+        }
+        if (p >= 0) {
+            fgt_box<R>(f, slot, geo.x, geo.z, rg.w, y0, dl, m_lo, p, n1, st64, N, D);
+            ++n_box;
+            t_df += (unsigned)n1;
+            t_f32 += (unsigned)(p - n1);
+        } else {
+            n_dir += direct_box<R>(f, f.box_s0[slot], n, ya, yb, cut, m_lo, ybase,
+                                   st64, N, D);
+        }
+    }
+    if (r0 >= f.n_runs) return;
+    if (f.n_pairs) {
+        if (n_dir) atomicAdd((unsigned long long*)f.n_pairs, (unsigned long long)n_dir);
+        if (n_box) {
+            atomicAdd((unsigned long long*)f.n_pairs + 1, (unsigned long long)n_box);
+            atomicAdd((unsigned long long*)f.n_pairs + 2, (unsigned long long)t_df * (2 * R));
+            atomicAdd((unsigned long long*)f.n_pairs + 3, (unsigned long long)t_f32 * (2 * R));
+        }
+    }
+    double* pN = f.partN + (size_t)t * g.n_y;
+    double* pD = f.partD + (size_t)t * g.n_y;
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (j0 + k < g.n_y) {
+            pN[j0 + k] = df_to_double(N[k]);
+            pD[j0 + k] = df_to_double(D[k]);
+        }
+}
+
+// U_j = sum over tiles of the numerator partials / of the denominator partials.
+__device__ __forceinline__ void u1_combine_body(const Geom& g, const FastView& f,
+                                                double* __restrict__ U, int64_t bx) {
+    const int64_t j = bx * blockDim.x + threadIdx.x;
+    if (j >= g.n_y) return;
+    double n = 0.0, d = 0.0;
+    for (int t = 0; t < f.n_tiles; ++t) {
+        n += f.partN[(size_t)t * g.n_y + j];
+        d += f.partD[(size_t)t * g.n_y + j];
+    }
+    U[j] = n / d;
+}
+
+// ---- single-instance kernels --------------------------------------------------
+
+__global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
+    sources_body(g, f, nu, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32) k_box_plan(Geom g, FastView f) {
+    box_plan_body(g, f, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kMomT) k_box_moments(Geom g, FastView f) {
+    __shared__ MomSmem sm;
+    box_moments_body(g, f, sm, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kRunT) k_run_shift(Geom g, FastView f) {
+    run_shift_body(g, f, blockIdx.x);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kU1Runs) k_u1_main(Geom g, FastView f) {
+    __shared__ dfloat st64[47];
+    u1_main_body<R>(g, f, st64, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_u1_combine(Geom g, FastView f, double* __restrict__ U) {
+    u1_combine_body(g, f, U, blockIdx.x);
+}
+
+// ---- batched wrappers -----------------------------------------------------------
+// The block map gives (instance, block of that instance's own grid); the
+// instance descriptor is staged in shared memory and the body runs unchanged.
+
+__device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* map,
+                                          InstDev& sd) {
+    const BlockRef r = map[blockIdx.x];
+    const int* src = (const int*)(insts + r.inst);
+    int* dst = (int*)&sd;
+    for (int k = threadIdx.x; k < (int)(sizeof(InstDev) / 4); k += blockDim.x)
+        dst[k] = src[k];
+    __syncthreads();
+    return r;
+}
+
+__global__ void kb_sources(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    sources_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], r.local);
+}
+
+__global__ void __launch_bounds__(32) kb_box_plan(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    box_plan_body(sd.g, sd.f, r.local);
+}
+
+__global__ void __launch_bounds__(kMomT) kb_box_moments(const InstDev* insts,
+                                                        const BlockRef* map) {
+    __shared__ InstDev sd;
+    __shared__ MomSmem sm;
+    const BlockRef r = stage(insts, map, sd);
+    box_moments_body(sd.g, sd.f, sm, r.local);
+}
+
+__global__ void __launch_bounds__(kRunT) kb_run_shift(const InstDev* insts,
+                                                      const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    run_shift_body(sd.g, sd.f, r.local);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kU1Runs) kb_u1_main(const InstDev* insts,
+                                                      const BlockRef* map) {
+    __shared__ InstDev sd;
+    __shared__ dfloat st64[47];
+    const BlockRef r = stage(insts, map, sd);
+    const int64_t rb = sd.f.r_blocks;
+    u1_main_body<R>(sd.g, sd.f, st64, r.local % rb, r.local / rb);
+}
+
+__global__ void kb_u1_combine(const InstDev* insts, const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    u1_combine_body(sd.g, sd.f, sd.U, r.local);
+}
+
+inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ---- host side ------------------------------------------------------------------
+
+int mmse_run_length(const Geom& g) {
+    // keep the exponent change along a run below ~15 (float range of the
+    // double-float weights): R * delta * (Y + max |f|) <= 15
+    const double F = (double)((g.hr + 2 * g.q) > g.hx ? (g.hr + 2 * g.q) : g.hx) * g.delta;
+    const double slope = g.delta * ((double)g.hy * g.delta + F);
+    int R = 16;
+    while (R > 1 && (R - 1) * slope > 15.0) R /= 2;
+    return R;
+}
+
+void u1_plan(const Geom& g, int max_tiles, FastPlan* fp) {
+    fp->run = mmse_run_length(g);
+    fp->n_runs = (g.n_y + fp->run - 1) / fp->run;
+    fp->r_blocks = (fp->n_runs + kU1Runs - 1) / kU1Runs;
+    int64_t tile = (g.n_x + max_tiles - 1) / max_tiles;
+    tile = (tile + 31) / 32 * 32;
+    if (tile < 512) tile = 512;
+    fp->tile = tile;
+    fp->n_tiles = (int)((g.n_x + tile - 1) / tile);
+}
+
+size_t u1_scratch_bytes(const Geom& g, const FastPlan& fp, size_t align) {
+    auto rnd = [align](size_t n) { return (n + align - 1) / align * align; };
+    const size_t slots = (size_t)fp.n_tiles * kBoxMax;
+    return 3 * rnd(8 * (size_t)g.n_x) +                       // src_nu, src_f, src_F
+           rnd(4 * (size_t)fp.n_tiles) + 2 * rnd(4 * slots) +   // box_cnt, box_s0, box_n
+           2 * rnd(16 * slots) + rnd(8 * slots) +                // box_geo, box_rng, box_C
+           rnd(8 * slots * 2 * kBoxTerms) +                      // box_coef
+           2 * rnd(4 * (size_t)fp.n_runs) +                      // run_lo, run_hi
+           2 * rnd(8 * (size_t)fp.n_tiles * (size_t)g.n_y);     // partN, partD
+}
+
+bool u1_carve(const Geom& g, FastView* f, void* (*get)(void*, size_t), void* ctx) {
+    const size_t slots = (size_t)f->n_tiles * kBoxMax;
+    f->src_nu = (int64_t*)get(ctx, 8 * (size_t)g.n_x);
+    f->src_f = (dfloat*)get(ctx, 8 * (size_t)g.n_x);
+    f->src_F = (dfloat*)get(ctx, 8 * (size_t)g.n_x);
+    f->box_cnt = (int32_t*)get(ctx, 4 * (size_t)f->n_tiles);
+    f->box_s0 = (int32_t*)get(ctx, 4 * slots);
+    f->box_n = (int32_t*)get(ctx, 4 * slots);
+    f->box_geo = (float4*)get(ctx, 16 * slots);
+    f->box_rng = (float4*)get(ctx, 16 * slots);
+    f->box_C = (dfloat*)get(ctx, 8 * slots);
+    f->box_coef = (dfloat*)get(ctx, 8 * slots * 2 * kBoxTerms);
+    f->run_lo = (float*)get(ctx, 4 * (size_t)f->n_runs);
+    f->run_hi = (float*)get(ctx, 4 * (size_t)f->n_runs);
+    f->partN = (double*)get(ctx, 8 * (size_t)f->n_tiles * (size_t)g.n_y);
+    f->partD = (double*)get(ctx, 8 * (size_t)f->n_tiles * (size_t)g.n_y);
+    return f->src_nu && f->src_f && f->src_F && f->box_cnt && f->box_s0 && f->box_n &&
+           f->box_geo && f->box_rng && f->box_C && f->box_coef && f->run_lo &&
+           f->run_hi && f->partN && f->partD;
+}
+
+void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
+                      double* U, cudaStream_t s, Prof* prof) {
+    cudaEvent_t ev;
+    int k = prof ? prof->begin("mmse_sources", &ev) : -1;
+    k_sources<<<blocks(g.n_x, 256), 256, 0, s>>>(g, f, nu);
+    if (prof) prof->end(k, ev);
+    k = prof ? prof->begin("u1_boxes", &ev) : -1;
+    k_box_plan<<<(unsigned)f.n_tiles, 32, 0, s>>>(g, f);
+    k_box_moments<<<(unsigned)(f.n_tiles * kBoxMax), kMomT, 0, s>>>(g, f);
+    if (prof) prof->end(k, ev);
+    k = prof ? prof->begin("u1_shift", &ev) : -1;
+    k_run_shift<<<blocks(f.n_runs, kRunT / 32), kRunT, 0, s>>>(g, f);
+    if (prof) prof->end(k, ev);
+    k = prof ? prof->begin("mmse_main", &ev) : -1;
+    dim3 grid((unsigned)f.r_blocks, (unsigned)f.n_tiles);
+    switch (f.run) {
+        case 16: k_u1_main<16><<<grid, kU1Runs, 0, s>>>(g, f); break;
+        case 8: k_u1_main<8><<<grid, kU1Runs, 0, s>>>(g, f); break;
+        case 4: k_u1_main<4><<<grid, kU1Runs, 0, s>>>(g, f); break;
+        case 2: k_u1_main<2><<<grid, kU1Runs, 0, s>>>(g, f); break;
+        default: k_u1_main<1><<<grid, kU1Runs, 0, s>>>(g, f); break;
+    }
+    if (prof) prof->end(k, ev);
+    k = prof ? prof->begin("mmse_combine", &ev) : -1;
+    k_u1_combine<<<blocks(g.n_y, 256), 256, 0, s>>>(g, f, U);
+    if (prof) prof->end(k, ev);
+}
+
+int64_t u1_batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
+    switch (kind) {
+        case kBTile: return fp.n_tiles;
+        case kBBox: return (int64_t)fp.n_tiles * kBoxMax;
+        case kBRun: return (fp.n_runs + kRunT / 32 - 1) / (kRunT / 32);
+    }
+    (void)g;
+    return 0;
+}
+
+int64_t batch_mmse_blocks(const Geom&, const FastPlan& fp) {
+    return fp.r_blocks * fp.n_tiles;
+}
+
+void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s) {
+    const InstDev* d = bl.insts;
+    kb_sources<<<(unsigned)bl.n_blocks[kBPerX], 256, 0, s>>>(d, bl.map[kBPerX]);
+    kb_box_plan<<<(unsigned)bl.n_blocks[kBTile], 32, 0, s>>>(d, bl.map[kBTile]);
+    kb_box_moments<<<(unsigned)bl.n_blocks[kBBox], kMomT, 0, s>>>(d, bl.map[kBBox]);
+    kb_run_shift<<<(unsigned)bl.n_blocks[kBRun], kRunT, 0, s>>>(d, bl.map[kBRun]);
+    for (int r = 0; r < 5; ++r) {
+        if (bl.mmse_blocks[r] == 0) continue;
+        const unsigned nb = (unsigned)bl.mmse_blocks[r];
+        const BlockRef* m = bl.mmse_map[r];
+        switch (r) {
+            case 0: kb_u1_main<1><<<nb, kU1Runs, 0, s>>>(d, m); break;
+            case 1: kb_u1_main<2><<<nb, kU1Runs, 0, s>>>(d, m); break;
+            case 2: kb_u1_main<4><<<nb, kU1Runs, 0, s>>>(d, m); break;
+            case 3: kb_u1_main<8><<<nb, kU1Runs, 0, s>>>(d, m); break;
+            default: kb_u1_main<16><<<nb, kU1Runs, 0, s>>>(d, m); break;
+        }
+    }
+    kb_u1_combine<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
+}
+
+}  // namespace ucp

@@ -33,17 +33,36 @@ using namespace ucp;
 
 constexpr int64_t kMaxX = 32768;       // largest x0 grid
 constexpr int64_t kMaxY = 32768;       // largest y grid
-constexpr int kMaxChunks = 8;          // source columns of the u1 kernel
-constexpr int kThreadsPerRow = 64;     // threads per block row (k_mmse_main)
+constexpr int kMaxTiles = 8;           // source tiles of the u1 step
 
-// 8-byte slots: nu, prior, src_nu, src_f, src_F (x-sized); mshift, psi
-// (y-sized); the exp(k/64) table; numerator and denominator partials; the
-// per-chunk exponent minima (floats, two per slot).
-constexpr size_t kScratchDoubles = 5 * (size_t)kMaxX + 2 * (size_t)kMaxY + 64 +
-                                   2 * (size_t)kMaxChunks * kMaxY +
-                                   (size_t)kMaxChunks * kMaxY / 2;
+constexpr size_t rnd256(size_t n) { return (n + 255) / 256 * 256; }
+// nu and prior (x-sized), the exp(k/64) table, then the u1 buffers at the
+// largest sizes: src_nu, src_f, src_F; per tile the box count, per box slot
+// its first source, size, geometry, range, exp(delta c) and 2 kBoxTerms
+// coefficients; per run (at most n_y runs) two bounds; per tile and target
+// the numerator and denominator partials.
+constexpr size_t kSlots = (size_t)kMaxTiles * kBoxMax;
+constexpr size_t kScratchBytes =
+    5 * rnd256(8 * kMaxX) + rnd256(8 * 64) + rnd256(4 * kMaxTiles) +
+    2 * rnd256(4 * kSlots) + 2 * rnd256(16 * kSlots) + rnd256(8 * kSlots) +
+    rnd256(8 * kSlots * 2 * kBoxTerms) + 2 * rnd256(4 * kMaxY) +
+    2 * rnd256(8 * (size_t)kMaxTiles * kMaxY);
 
-static __device__ __align__(256) double g_scratch[kScratchDoubles];
+static __device__ __align__(256) double g_scratch[kScratchBytes / 8];
+
+// Bump allocation from the static array (256-byte steps).
+struct Bump {
+    char* p;
+    char* end;
+};
+static void* bump_get(void* ctx, size_t n) {
+    Bump* b = (Bump*)ctx;
+    n = rnd256(n);
+    if ((size_t)(b->end - b->p) < n) return nullptr;
+    void* r = b->p;
+    b->p += n;
+    return r;
+}
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_mu;
@@ -111,34 +130,24 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
     ucp_status st = scratch_address(&base);
     if (st != UCP_OK) return st;
 
-    // plan of the u1 kernels over at most kMaxChunks source columns
+    // plan of the u1 kernels over at most kMaxTiles source tiles
     FastView f{};
-    f.run = mmse_run_length(g);
-    const int64_t per_row = (int64_t)kThreadsPerRow * f.run;
-    f.j_blocks = (g.n_y + per_row - 1) / per_row;
-    int64_t chunks = (4 * 152 + f.j_blocks - 1) / f.j_blocks;
-    if (chunks > kMaxChunks) chunks = kMaxChunks;
-    const int64_t max_chunks = (g.n_x + 127) / 128;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
-    f.chunk = ((g.n_x + chunks - 1) / chunks + 63) / 64 * 64;
-    f.n_chunks = (int)((g.n_x + f.chunk - 1) / f.chunk);
+    u1_plan(g, kMaxTiles, &f);
     const dfloat sd = df_from_double(ldexp(g.delta, -g.shift));
     f.step_hi = sd.hi;
     f.step_lo = sd.lo;
+    const dfloat dd = df_from_double(g.delta);
+    f.delta_hi = dd.hi;
+    f.delta_lo = dd.lo;
 
-    double* q = base;
-    int64_t* nu = (int64_t*)q;  q += kMaxX;
-    f.prior = (dfloat*)q;       q += kMaxX;
-    f.src_nu = (int64_t*)q;     q += kMaxX;
-    f.src_f = (dfloat*)q;       q += kMaxX;
-    f.src_F = (dfloat*)q;       q += kMaxX;
-    f.mshift = (float*)q;       q += kMaxY;
-    f.psi = (dfloat*)q;         q += kMaxY;
-    f.t64 = (dfloat*)q;         q += 64;
-    f.partN = q;                q += (size_t)kMaxChunks * kMaxY;
-    f.partD = q;                q += (size_t)kMaxChunks * kMaxY;
-    f.mshift_part = (float*)q;
+    Bump bump{(char*)base, (char*)base + kScratchBytes};
+    int64_t* nu = (int64_t*)bump_get(&bump, 8 * (size_t)g.n_x);
+    f.prior = (dfloat*)bump_get(&bump, 8 * (size_t)g.n_x);
+    f.t64 = (dfloat*)bump_get(&bump, 8 * 64);
+    if (!nu || !f.prior || !f.t64 || !u1_carve(g, &f, bump_get, &bump)) {
+        set_error("ucp_u1_update_noalloc: %s%s", "static scratch too small", "");
+        return UCP_E_ARG;
+    }
 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g.n_x > 47 ? g.n_x : 47;

@@ -181,11 +181,10 @@ size_t inst_bytes(const Geom& g, int precision) {
         FastPlan fp;
         fast_plan(g, &fp);
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
-             3 * rnd(8 * nw) + 4 * rnd(8 * nx) + rnd(4 * ny) + rnd(8 * ny) +
-             rnd(8 * 47) + 2 * rnd(8 * (size_t)fp.n_chunks * ny) +
-             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) + rnd(8) +
+             3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
+             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) + rnd(32) +
              rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
-             rnd(4 * (size_t)fp.n_chunks * ny);
+             u1_scratch_bytes(g, fp, 256);
     }
     return b;
 }
@@ -237,7 +236,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.U = d.U;
     f.Ud = d.Ud;
     f.coarse = d.coarse;
-    const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
+    const size_t nx = (size_t)g.n_x, nw = (size_t)g.n_w;
     f.P = (dfloat*)A.get(8 * (size_t)f.n_pos);
     f.Q = (dfloat*)A.get(8 * (size_t)f.n_pos);
     f.R = (dfloat*)A.get(8 * (size_t)f.n_pos);
@@ -248,23 +247,17 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.phidf = (dfloat*)A.get(8 * nw);
     f.wdf = (dfloat*)A.get(8 * nw);
     f.prior = (dfloat*)A.get(8 * nx);
-    f.src_nu = (int64_t*)A.get(8 * nx);
-    f.src_f = (dfloat*)A.get(8 * nx);
-    f.src_F = (dfloat*)A.get(8 * nx);
-    f.mshift = (float*)A.get(4 * ny);
-    f.mshift_part = (float*)A.get(4 * (size_t)f.n_chunks * ny);
-    f.psi = (dfloat*)A.get(8 * ny);
     f.t64 = (dfloat*)A.get(8 * 47);
-    f.partN = (double*)A.get(8 * (size_t)f.n_chunks * ny);
-    f.partD = (double*)A.get(8 * (size_t)f.n_chunks * ny);
     f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
     f.tab_part = (double*)A.get(24 * (size_t)f.tab_splits * (size_t)f.n_pos);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
-    f.n_pairs = (int64_t*)A.get(8);
+    f.n_pairs = (int64_t*)A.get(32);
+    const bool u1_ok = u1_carve(
+        g, &f, [](void* a, size_t n) { return ((Arena*)a)->get(n); }, &A);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf || !f.wdf ||
-        !f.prior || !f.src_nu || !f.src_f || !f.src_F || !f.mshift || !f.mshift_part || !f.psi ||
-        !f.t64 || !f.partN || !f.partD || !f.Jpart || !f.tab_part || !f.W2_dev || !f.n_exact || !f.n_pairs) {
+        !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tab_part || !f.W2_dev ||
+        !f.n_exact || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
     }
@@ -272,6 +265,9 @@ static ucp_status fast_alloc(ucp_inst* in) {
     const dfloat sd = df_from_double(step), kd = df_from_double(g.kk);
     f.step_hi = sd.hi;
     f.step_lo = sd.lo;
+    const dfloat dd = df_from_double(g.delta);
+    f.delta_hi = dd.hi;
+    f.delta_lo = dd.lo;
     f.kk_hi = kd.hi;
     f.kk_lo = kd.lo;
     f.inv_one_f = (float)ldexp(1.0, -g.shift);
@@ -340,7 +336,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     if (in->fast) {
         UCP_LAUNCH(in, "fast_setup", launch_fast_setup(g, in->fv, s));
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
-        cudaMemsetAsync(in->fv.n_pairs, 0, 8, s);
+        cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
         fast_set_W2(in);

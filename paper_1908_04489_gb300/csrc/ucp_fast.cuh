@@ -1,4 +1,5 @@
-// ucp_fast.cuh -- state and launches of the fast path (kernels_fast.cu).
+// ucp_fast.cuh -- state and launches of the fast path (kernels_fast.cu,
+// kernels_u1.cu).
 #pragma once
 
 #include "ucp_internal.cuh"
@@ -8,7 +9,15 @@
 namespace ucp {
 
 void fast_plan(const Geom& g, FastPlan* fp);
+// u1 step (kernels_u1.cu): run length, tiles (at most max_tiles), buffers.
 int mmse_run_length(const Geom& g);
+void u1_plan(const Geom& g, int max_tiles, FastPlan* fp);
+// Bytes of the u1 buffers (each rounded up to align) and their carving from
+// an allocator get(ctx, bytes); false if an allocation failed.
+size_t u1_scratch_bytes(const Geom& g, const FastPlan& fp, size_t align);
+bool u1_carve(const Geom& g, FastView* f, void* (*get)(void*, size_t), void* ctx);
+int64_t u1_batch_blocks(const Geom& g, const FastPlan& fp, int kind);
+void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s);
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
                       double* U, cudaStream_t s, Prof* prof);

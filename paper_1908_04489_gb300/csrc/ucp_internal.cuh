@@ -56,16 +56,21 @@ struct FastPlan {
     int64_t n_pos;     // table positions (cells c_lo .. c_lo + n_pos - 1)
     int64_t jlo;       // y-index of table E-index 0
     int64_t n_e;       // length of E, E^2, E E_+ (n_pos + n_w + 1)
-    int64_t chunk;     // sources per block column of the u1 kernel
-    int n_chunks;      // block columns of the u1 kernel
-    int run;           // targets per thread of the u1 recurrence
-    int64_t j_blocks;  // block rows of the u1 kernel
+    int64_t tile;      // sources per tile of the u1 step (consecutive x0)
+    int n_tiles;       // tiles; the u1 partial sums are kept per tile
+    int run;           // targets per run of the u1 step
+    int64_t n_runs;    // runs covering the y grid
+    int64_t r_blocks;  // run blocks of the u1 kernel (kU1Runs runs each)
     int64_t J_blocks;  // blocks of the J reduction
     int64_t tab_span;  // taps per block column of the table kernel
     int tab_splits;    // block columns of the table kernel
 };
 
 struct dfloat;  // df.cuh
+
+// u1 boxes: at most kBoxMax boxes per tile, kBoxTerms Taylor terms per box.
+constexpr int kBoxMax = 32;
+constexpr int kBoxTerms = 24;
 
 // Everything the fast kernels read or write (device pointers + scalars).
 struct FastView : FastPlan {
@@ -86,21 +91,29 @@ struct FastView : FastPlan {
     int64_t* src_nu;     // [n_x] lattice index of f_i this sweep
     dfloat* src_f;       // [n_x] f_i
     dfloat* src_F;       // [n_x] exp(delta f_i)
-    float* mshift;       // [n_y] estimate of min_i of the u1 exponents
-    float* mshift_part;  // [n_chunks * n_y] per-chunk minima
-    dfloat* psi;         // [n_y] exp(-delta y_j - delta^2/2 + m_{j+1} - m_j)
     dfloat* t64;         // [47] exp(k / 64), k = -23..23
-    double* partN;       // [n_chunks * n_y] numerator partials
-    double* partD;       // [n_chunks * n_y] denominator partials
+    int32_t* box_cnt;    // [n_tiles] boxes of each tile
+    int32_t* box_s0;     // [n_tiles * kBoxMax] first source of a box
+    int32_t* box_n;      //   sources in the box
+    float4* box_geo;     //   (c, h, pm, pmin): centre, half width, scale, min prior
+    float4* box_rng;     //   (min f, max f, h if moments exist else inf, s)
+    dfloat* box_C;       //   exp(delta c)
+    dfloat* box_coef;    //   [2 kBoxTerms]: M_n / n!, then (c M_n + s M_{n+1}) / n!
+    float* run_lo;       // [n_runs] lower bound of min_i e_{i,j0} (scale)
+    float* run_hi;       // [n_runs] upper bound of min_i e_ij over the run
+    double* partN;       // [n_tiles * n_y] numerator partials
+    double* partD;       // [n_tiles * n_y] denominator partials
     double* Jpart;       // [J_blocks]
     double* tab_part;    // [tab_splits * 3 * n_pos] table partial sums
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
-    int64_t* n_pairs;    // (source, run) pairs evaluated by the u1 kernel
+    int64_t* n_pairs;    // [4] u1 work: direct (source, run) pairs, (box, run)
+                         // expansions, double-float and FP32 Taylor terms
     double W2;           // host copy of *W2_dev
     float W2hi, W2lo;    // W2 as double-float
     float sqrtW2;
     float step_hi, step_lo;   // delta 2^-shift as double-float
+    float delta_hi, delta_lo; // delta as double-float
     float kk_hi, kk_lo;       // k^2 as double-float
     float inv_one_f;          // 2^-shift
     float beta_rel;      // |table cost - serial cost| <= beta_rel M
@@ -132,21 +145,22 @@ struct BlockRef {
     int32_t local;
 };
 
+enum BatchKind {
+    kBSearch = 0, kBPerX = 1, kBTile = 2, kBPerY = 3, kBTabPart = 4,
+    kBTabComb = 5, kBBuildE = 6, kBJPart = 7, kBBox = 8, kBRun = 9,
+    kBKinds = 10
+};
+
 // Device arrays describing one batched sweep.
 struct BatchLaunch {
     InstDev* insts;
     int n_inst;
-    const BlockRef* map[8];        // per kernel kind (see BatchKind)
-    int64_t n_blocks[8];
+    const BlockRef* map[kBKinds];  // per kernel kind (see BatchKind)
+    int64_t n_blocks[kBKinds];
     const BlockRef* search_map[5]; // search per n_refine 2, 4, 8, 16, 32
     int64_t search_blocks[5];
-    const BlockRef* mmse_map[5];   // mmse_main per run length 1, 2, 4, 8, 16
+    const BlockRef* mmse_map[5];   // u1 main kernel per run length 1, 2, 4, 8, 16
     int64_t mmse_blocks[5];
-};
-
-enum BatchKind {
-    kBSearch = 0, kBPerX = 1, kBShift = 2, kBPerY = 3, kBTabPart = 4,
-    kBTabComb = 5, kBBuildE = 6, kBJPart = 7
 };
 
 // ---- plain FP64 path (kernels_plain.cu) --------------------------------

@@ -89,8 +89,11 @@ def test_requests_join_while_others_run(binding):
 
 def test_budget_admission_and_rejection(binding):
     reqs = small_requests(3, seed=8)
-    need = max(binding.plan(p)["device_bytes"] for p in reqs)
-    with binding.Server(hbm_budget_bytes=need + (1 << 16), max_slots=8) as srv:
+    needs = sorted(binding.plan(p)["device_bytes"] for p in reqs)
+    # the largest fits alone, no two fit together
+    budget = min(needs[-1] + (1 << 16), needs[0] + needs[1] - 1)
+    assert budget >= needs[-1]
+    with binding.Server(hbm_budget_bytes=budget, max_slots=8) as srv:
         with pytest.raises(binding.UcpError) as e:
             srv.submit(W.c2())
         assert e.value.status == -3                      # UCP_E_BUDGET
