@@ -170,9 +170,11 @@ UCP_API ucp_status ucp_tie_recosts(ucp_inst* inst, int64_t* out);
  *                 negligible);
  *   3 u1_df_terms Taylor terms evaluated in double-float, over those box
  *                 pairs (per target of the run, each of two polynomials);
- *   4 u1_f32_terms Taylor terms evaluated in FP32, likewise.
- * out holds n >= 0 entries (n <= 5).  Synchronises. */
-#define UCP_N_COUNTERS 5
+ *   4 u1_f32_terms Taylor terms evaluated in FP32, likewise;
+ *   5 direct_costs candidate costs re-computed by the direct double-float
+ *                 quadrature (the screening tier before ucp_tie_recosts).
+ * out holds n >= 0 entries (n <= 6).  Synchronises. */
+#define UCP_N_COUNTERS 6
 UCP_API ucp_status ucp_work_counters(ucp_inst* inst, int64_t* out, int32_t n);
 
 /* Per-kernel CUDA-event timing on the instance stream (off by default).

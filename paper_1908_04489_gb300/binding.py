@@ -285,7 +285,8 @@ class Instance:
         n = L.ucp_kernel_times(self.h, names, launches, ms, cap)
         return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
 
-    COUNTERS = ("recosts", "u1_pairs", "u1_boxes", "u1_df_terms", "u1_f32_terms")
+    COUNTERS = ("recosts", "u1_pairs", "u1_boxes", "u1_df_terms", "u1_f32_terms",
+                "direct_costs")
 
     def work_counters(self) -> dict:
         out = (ctypes.c_int64 * len(self.COUNTERS))()

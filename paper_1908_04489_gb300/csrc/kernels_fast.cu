@@ -120,58 +120,79 @@ __device__ double exact_costs_batch(const Geom& g, const FastView& f, int64_t i,
 // bound is several times tighter than the table identity's.  Candidates
 // outside the tables get an infinite bound (no second tier).
 template <int G>
-__device__ void direct_df_cost(const Geom& g, const FastView& f, int64_t i, int64_t nu,
-                               int lane, double& g2, double& b2) {
+__device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
+                                const int64_t (&nu)[2], int lane, double (&g2)[2],
+                                double (&b2)[2]) {
+    // two candidates per pass over the taps (independent chains interleave)
     const unsigned gm = group_mask<G>();
-    const int64_t cell = nu >> g.shift;
-    const int64_t p = cell - f.c_lo;
-    if (p < 0 || p + 1 >= f.n_pos) {
-        g2 = 0.0;
-        b2 = INFINITY;
-        return;
+    int64_t p[2];
+    dfloat t[2];
+    bool ok[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int64_t cell = nu[b] >> g.shift;
+        p[b] = cell - f.c_lo;
+        ok[b] = p[b] >= 0 && p[b] + 1 < f.n_pos;
+        if (!ok[b]) p[b] = 0;
+        t[b] = df_mul_f(df_from_i64(nu[b] - cell * g.one), f.inv_one_f);
     }
-    const int64_t frac = nu - cell * g.one;
-    const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
-    double acc = 0.0;
-    dfloat blk{0.f, 0.f};
+    double acc[2] = {0.0, 0.0};
+    dfloat blk[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    float emax[2] = {0.f, 0.f}, demax[2] = {0.f, 0.f};
     int cnt = 0;
-    float emax = 0.f, demax = 0.f;
+#pragma unroll 2
     for (int64_t l = lane; l < g.n_w; l += G) {
-        const dfloat E0 = f.E[p + l], E1 = f.E[p + l + 1];
-        const dfloat dE = df_add_acc(E1, df_neg(E0));
-        const dfloat d = df_add_acc(df_add_acc(f.wdf[l], E0), df_mul(t, dE));
-        blk = df_add(blk, df_mul(f.phidf[l], df_mul(d, d)));
+        const dfloat w = f.wdf[l], ph = f.phidf[l];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const dfloat E0 = f.E[p[b] + l], E1 = f.E[p[b] + l + 1];
+            const dfloat dE = df_add_acc(E1, df_neg(E0));
+            const dfloat d = df_add_acc(df_add_acc(w, E0), df_mul(t[b], dE));
+            blk[b] = df_add(blk[b], df_mul(ph, df_mul(d, d)));
+            emax[b] = fmaxf(emax[b], fmaxf(fabsf(E0.hi), fabsf(E1.hi)));
+            demax[b] = fmaxf(demax[b], fabsf(dE.hi));
+        }
         if (++cnt == 8) {
-            acc += df_to_double(blk);
-            blk = {0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                acc[b] += df_to_double(blk[b]);
+                blk[b] = {0.f, 0.f};
+            }
             cnt = 0;
         }
-        emax = fmaxf(emax, fmaxf(fabsf(E0.hi), fabsf(E1.hi)));
-        demax = fmaxf(demax, fabsf(dE.hi));
     }
-    acc += df_to_double(blk);
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-        acc += __shfl_down_sync(gm, acc, off, G);
-        emax = fmaxf(emax, __shfl_down_sync(gm, emax, off, G));
-        demax = fmaxf(demax, __shfl_down_sync(gm, demax, off, G));
+    for (int b = 0; b < 2; ++b) {
+        acc[b] += df_to_double(blk[b]);
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            acc[b] += __shfl_down_sync(gm, acc[b], off, G);
+            emax[b] = fmaxf(emax[b], __shfl_down_sync(gm, emax[b], off, G));
+            demax[b] = fmaxf(demax[b], __shfl_down_sync(gm, demax[b], off, G));
+        }
+        const double S2 = __shfl_sync(gm, acc[b], 0, G);
+        const float em = __shfl_sync(gm, emax[b], 0, G);
+        const float dm = __shfl_sync(gm, demax[b], 0, G);
+        if (!ok[b]) {
+            g2[b] = 0.0;
+            b2[b] = INFINITY;
+            continue;
+        }
+        const dfloat a = df_mul(df_from_i64(nu[b] - (i - g.hx) * g.one),
+                                dfloat{f.step_hi, f.step_lo});
+        const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
+        const double c = df_to_double(ctl);
+        g2[b] = c + S2;
+        // |error of d_l| <= uf^2 (|w_l| + |E_{p+l}| + |E_{p+l+1}|) from the
+        // double-float representations plus 8 uf^2 (|d_l| + |dE_l|) from the
+        // operations; summed against phi_l 2|d_l| this gives the terms below.
+        const double uf2 = 0x1p-48;
+        const double rs = sqrt(fmax(S2, 0.0));
+        const double eps = (double)f.beta_abs + uf2 * ((double)f.w_half + 2.0 * em);
+        b2[b] = (double)f.beta2_rel * S2 + 1.25 * 16.0 * uf2 * (S2 + rs * dm) +
+                1.25 * (2.0 * rs + 1.0) * eps + 3.0e-13 * c +
+                (double)f.beta_ctl * sqrt(c) + 4.0e-16 * fabs(g2[b]);
     }
-    const double S2 = __shfl_sync(gm, acc, 0, G);
-    emax = __shfl_sync(gm, emax, 0, G);
-    demax = __shfl_sync(gm, demax, 0, G);
-    const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
-    const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
-    const double c = df_to_double(ctl);
-    g2 = c + S2;
-    // |error of d_l| <= uf^2 (|w_l| + |E_{p+l}| + |E_{p+l+1}|) from the
-    // double-float representations plus 8 uf^2 (|d_l| + |dE_l|) from the
-    // operations; summed against phi_l 2|d_l| this gives the terms below.
-    const double uf2 = 0x1p-48;
-    const double rs = sqrt(fmax(S2, 0.0));
-    const double eps = (double)f.beta_abs + uf2 * ((double)f.w_half + 2.0 * emax);
-    b2 = (double)f.beta2_rel * S2 + 1.25 * 16.0 * uf2 * (S2 + rs * demax) +
-         1.25 * (2.0 * rs + 1.0) * eps + 3.0e-13 * c + (double)f.beta_ctl * sqrt(c) +
-         4.0e-16 * fabs(g2);
 }
 
 // ---- screened table cost ------------------------------------------------
@@ -360,15 +381,31 @@ __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int 
 // Resolve one stage of the list: the carried winner (lane 0) plus positions
 // p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
 // costs over all of them.
+constexpr int kKeep = 6;   // candidates per lane whose screened bounds are kept
+constexpr int kSearchT = 128;   // threads per block of the search
+
 template <int G, typename CandFn>
 __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
                         const Best& best, int p0, int p_end, CandFn cand,
                         int32_t* n_exact, double* tie_terms) {
     const bool have_best = best.pos != INT_MAX;
-    // 1. smallest upper end
+    // 1. smallest upper end; the lower ends of this lane's first kKeep
+    // candidates are kept (the rest are evaluated again below)
     dfloat hi = {FLT_MAX, 0.f};
     if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
-    for (int p = p0 + lane; p < p_end; p += G) {
+    dfloat lo_k[kKeep];
+#pragma unroll
+    for (int k = 0; k < kKeep; ++k) {
+        lo_k[k] = {FLT_MAX, 0.f};
+        const int p = p0 + lane + k * G;
+        if (p < p_end) {
+            const Eval e = eval_table(g, f, i, cand(p));
+            const dfloat h = df_pm(e.gv, e.beta);
+            if (df_lt(h, hi)) hi = h;
+            lo_k[k] = df_pm(e.gv, -e.beta);
+        }
+    }
+    for (int p = p0 + lane + kKeep * G; p < p_end; p += G) {
         const Eval e = eval_table(g, f, i, cand(p));
         const dfloat h = df_pm(e.gv, e.beta);
         if (df_lt(h, hi)) hi = h;
@@ -381,7 +418,17 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         vmin = vmax = best.nu;
         pmin = best.pos;
     }
-    for (int p = p0 + lane; p < p_end; p += G) {
+#pragma unroll
+    for (int k = 0; k < kKeep; ++k) {
+        const int p = p0 + lane + k * G;
+        if (p < p_end && !df_lt(hi, lo_k[k])) {
+            const int64_t nu = cand(p);
+            vmin = nu < vmin ? nu : vmin;
+            vmax = nu > vmax ? nu : vmax;
+            pmin = p < pmin ? p : pmin;
+        }
+    }
+    for (int p = p0 + lane + kKeep * G; p < p_end; p += G) {
         const int64_t nu = cand(p);
         const Eval e = eval_table(g, f, i, nu);
         if (!df_lt(hi, df_pm(e.gv, -e.beta))) {
@@ -416,15 +463,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         if (lane == 0) { mnu = best.nu; mpos = best.pos; mexact = best.is_exact; mval = best.exact; }
         M = 1;
     }
-    for (int pb = p0; pb < p_end; pb += G) {
-        const int p = pb + lane;
-        bool member = false;
-        int64_t nu = 0;
-        if (p < p_end) {
-            nu = cand(p);
-            const Eval e = eval_table(g, f, i, nu);
-            member = !df_lt(hi, df_pm(e.gv, -e.beta));
-        }
+    auto gather = [&](int pb, bool member, int64_t nu) {
         unsigned mask = (__ballot_sync(gm, member) >> base) & (0xffffffffu >> (32 - G));
         while (mask) {
             const int src = __ffs(mask) - 1;
@@ -437,24 +476,42 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
                 overflow = true;
             }
         }
+    };
+#pragma unroll
+    for (int k = 0; k < kKeep; ++k) {
+        const int pb = p0 + k * G;
+        if (pb < p_end) {   // the same for the group
+            const int p = pb + lane;
+            const bool member = p < p_end && !df_lt(hi, lo_k[k]);
+            gather(pb, member, member ? cand(p) : 0);
+        }
+    }
+    for (int pb = p0 + kKeep * G; pb < p_end; pb += G) {
+        const int p = pb + lane;
+        bool member = false;
+        int64_t nu = 0;
+        if (p < p_end) {
+            nu = cand(p);
+            const Eval e = eval_table(g, f, i, nu);
+            member = !df_lt(hi, df_pm(e.gv, -e.beta));
+        }
+        gather(pb, member, nu);
     }
     if (overflow)   // more distinct candidates in play than lanes (rare)
         return resolve_serial<G>(g, f, i, lane, best, have_best, hi, p0, p_end, cand,
                                  n_exact, tie_terms);
     // second tier
     double g2 = 0.0, b2 = 0.0;
-    for (int m = 0; m < M; ++m) {
-        const int64_t cn = __shfl_sync(gm, mnu, m, G);
-        const bool ex = __shfl_sync(gm, (int)mexact, m, G) != 0;
-        double v, bv;
-        if (ex) {
-            v = __shfl_sync(gm, mval, m, G);
-            bv = 0.0;
-        } else {
-            direct_df_cost<G>(g, f, i, cn, lane, v, bv);
-        }
-        if (lane == m) { g2 = v; b2 = bv; }
+    if (lane == 0 && n_exact && f.n_tier2) atomicAdd(f.n_tier2, M);
+    for (int m = 0; m < M; m += 2) {
+        const int m1 = m + 1 < M ? m + 1 : m;
+        const int64_t cn[2] = {__shfl_sync(gm, mnu, m, G), __shfl_sync(gm, mnu, m1, G)};
+        double v[2], bv[2];
+        direct_df_cost2<G>(g, f, i, cn, lane, v, bv);
+        if (lane == m) { g2 = v[0]; b2 = bv[0]; }
+        if (m1 != m && lane == m1) { g2 = v[1]; b2 = bv[1]; }
     }
+    if (lane < M && mexact) { g2 = mval; b2 = 0.0; }   // serial cost already known
     double hi2 = lane < M ? g2 + b2 : DBL_MAX;
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1)
@@ -544,12 +601,12 @@ __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
 }
 
 template <int G>
-__global__ void __launch_bounds__(256, 2) k_search_fast(Geom g, FastView f,
+__global__ void __launch_bounds__(kSearchT) k_search_fast(Geom g, FastView f,
                                                      const int64_t* __restrict__ nu_pre,
                                                      int64_t* __restrict__ nu_out,
                                                      int32_t* __restrict__ idx_out,
                                                      int32_t* n_exact) {
-    __shared__ double tie_smem[256 * kTieBatch];
+    __shared__ double tie_smem[kSearchT * kTieBatch];
     search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
 }
 
@@ -747,10 +804,10 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
 }
 
 template <int G>
-__global__ void __launch_bounds__(256, 2) kb_search(const InstDev* insts, const BlockRef* map) {
+__global__ void __launch_bounds__(kSearchT) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
-    __shared__ double tie_smem[256 * kTieBatch];
+    __shared__ double tie_smem[kSearchT * kTieBatch];
     search_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
                    sd.f.n_exact, tie_smem, r.local);
 }
@@ -849,7 +906,7 @@ void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
                         int64_t* nu_out, int32_t* idx, cudaStream_t s) {
     const int64_t threads = g.n_x * (int64_t)g.n_refine;
-    const int bs = 256;
+    const int bs = kSearchT;
 #define UCP_FAST_CASE(G)                                                   \
     case G:                                                                \
         k_search_fast<G><<<blocks(threads, bs), bs, 0, s>>>(g, f, nu_in,   \
@@ -869,7 +926,7 @@ void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
 
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
-        case kBSearch: return (g.n_x * g.n_refine + 255) / 256;
+        case kBSearch: return (g.n_x * g.n_refine + kSearchT - 1) / kSearchT;
         case kBPerX: return (g.n_x + 255) / 256;
         case kBTile:
         case kBBox:
@@ -893,11 +950,11 @@ void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
         const unsigned nb = (unsigned)bl.search_blocks[gi];
         const BlockRef* m = bl.search_map[gi];
         switch (gi) {
-            case 0: kb_search<2><<<nb, 256, 0, s>>>(d, m); break;
-            case 1: kb_search<4><<<nb, 256, 0, s>>>(d, m); break;
-            case 2: kb_search<8><<<nb, 256, 0, s>>>(d, m); break;
-            case 3: kb_search<16><<<nb, 256, 0, s>>>(d, m); break;
-            default: kb_search<32><<<nb, 256, 0, s>>>(d, m); break;
+            case 0: kb_search<2><<<nb, kSearchT, 0, s>>>(d, m); break;
+            case 1: kb_search<4><<<nb, kSearchT, 0, s>>>(d, m); break;
+            case 2: kb_search<8><<<nb, kSearchT, 0, s>>>(d, m); break;
+            case 3: kb_search<16><<<nb, kSearchT, 0, s>>>(d, m); break;
+            default: kb_search<32><<<nb, kSearchT, 0, s>>>(d, m); break;
         }
     }
     launch_batch_u1(bl, s);

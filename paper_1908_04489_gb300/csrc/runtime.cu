@@ -182,7 +182,7 @@ size_t inst_bytes(const Geom& g, int precision) {
         fast_plan(g, &fp);
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
              3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
-             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + rnd(4) + rnd(32) +
+             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 2 * rnd(4) + rnd(32) +
              rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
              u1_scratch_bytes(g, fp, 256);
     }
@@ -252,12 +252,13 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.tab_part = (double*)A.get(24 * (size_t)f.tab_splits * (size_t)f.n_pos);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
+    f.n_tier2 = (int32_t*)A.get(4);
     f.n_pairs = (int64_t*)A.get(32);
     const bool u1_ok = u1_carve(
         g, &f, [](void* a, size_t n) { return ((Arena*)a)->get(n); }, &A);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf || !f.wdf ||
         !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tab_part || !f.W2_dev ||
-        !f.n_exact || !f.n_pairs) {
+        !f.n_exact || !f.n_tier2 || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
     }
@@ -336,6 +337,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     if (in->fast) {
         UCP_LAUNCH(in, "fast_setup", launch_fast_setup(g, in->fv, s));
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
+        cudaMemsetAsync(in->fv.n_tier2, 0, 4, s);
         cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");

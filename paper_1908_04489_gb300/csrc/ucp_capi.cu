@@ -305,14 +305,15 @@ extern "C" ucp_status ucp_tie_recosts(ucp_inst* in, int64_t* out) {
 extern "C" ucp_status ucp_work_counters(ucp_inst* in, int64_t* out, int32_t n) {
     if (!in || n < 0 || n > UCP_N_COUNTERS || (n > 0 && !out)) return UCP_E_ARG;
     if (in->poisoned) return UCP_E_STATE;
-    int32_t r = 0;
+    int32_t r = 0, t2 = 0;
     int64_t p[4] = {0, 0, 0, 0};
     if (in->fast) {
         cudaMemcpyAsync(&r, in->fv.n_exact, 4, cudaMemcpyDeviceToHost, in->stream);
+        cudaMemcpyAsync(&t2, in->fv.n_tier2, 4, cudaMemcpyDeviceToHost, in->stream);
         ucp_status st = inst_read(in, in->fv.n_pairs, p, sizeof(p));
         if (st != UCP_OK) return st;
     }
-    const int64_t all[UCP_N_COUNTERS] = {r, p[0], p[1], p[2], p[3]};
+    const int64_t all[UCP_N_COUNTERS] = {r, p[0], p[1], p[2], p[3], t2};
     for (int32_t k = 0; k < n; ++k) out[k] = all[k];
     return UCP_OK;
 }

@@ -107,6 +107,7 @@ struct FastView : FastPlan {
     double* tab_part;    // [tab_splits * 3 * n_pos] table partial sums
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
+    int32_t* n_tier2;    // count of direct double-float quadratures (second tier)
     int64_t* n_pairs;    // [4] u1 work: direct (source, run) pairs, (box, run)
                          // expansions, double-float and FP32 Taylor terms
     double W2;           // host copy of *W2_dev
