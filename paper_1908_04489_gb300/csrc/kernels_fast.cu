@@ -927,7 +927,6 @@ void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
         case kBSearch: return (g.n_x * g.n_refine + kSearchT - 1) / kSearchT;
-        case kBPerX: return (g.n_x + 255) / 256;
         case kBTile:
         case kBBox:
         case kBRun: return u1_batch_blocks(g, fp, kind);

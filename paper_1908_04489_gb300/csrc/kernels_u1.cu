@@ -48,7 +48,9 @@ constexpr float kHMax = 0.05f;      // box half width aimed at when grouping
 constexpr float kHMoments = 0.25f;  // boxes wider than this get no moments
 constexpr float kZetaMax = 1.0f;    // largest |y - c| h expanded
 constexpr int kU1Runs = 32;         // runs per block of the u1 kernel (1 warp)
-constexpr int kMomT = 128;          // threads per box of the moment kernel
+constexpr int kMomT = 256;          // threads per box of the moment kernel
+constexpr int kPlanT = 128;         // threads per tile of the planning kernel
+constexpr int kBoxDF = 16;          // moments up to this order in double-float
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
@@ -56,30 +58,26 @@ __device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
     return __dmul_rn(__dmul_rn((double)nu, g.delta), inv);
 }
 
-// ---- sources ----------------------------------------------------------------
+// ---- sources and boxes ----------------------------------------------------------
 
-// Per source: f_i (double-float) and exp(delta f_i).
-__device__ __forceinline__ void sources_body(const Geom& g, const FastView& f,
-                                             const int64_t* __restrict__ nu,
-                                             int64_t bx) {
-    const int64_t i = bx * blockDim.x + threadIdx.x;
-    if (i >= g.n_x) return;
-    const double v = value_of(g, nu[i]);
-    f.src_nu[i] = nu[i];
-    f.src_f[i] = df_from_double(v);
-    f.src_F[i] = df_from_double(exp(g.delta * v));
-}
-
-// ---- boxes ------------------------------------------------------------------
-
-// One warp per tile: greedy grouping of consecutive sources into boxes whose
-// f values (leading floats) span at most 2 kHMax; the last box of a tile
-// takes whatever is left once kBoxMax - 1 boxes are closed.
+// One block per tile.  Every thread: per source f_i (double-float) and
+// exp(delta f_i).  Then warp 0: greedy grouping of consecutive sources into
+// boxes whose f values (leading floats) span at most 2 kHMax; the last box of
+// a tile takes whatever is left once kBoxMax - 1 boxes are closed.
 __device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
+                                              const int64_t* __restrict__ nu,
                                               int64_t t) {
-    const int lane = threadIdx.x & 31;
     const int64_t t0 = t * f.tile;
     const int64_t t1 = min(t0 + f.tile, g.n_x);
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
+        const double v = value_of(g, nu[i]);
+        f.src_nu[i] = nu[i];
+        f.src_f[i] = df_from_double(v);
+        f.src_F[i] = df_from_double(exp(g.delta * v));
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const int64_t slot0 = t * kBoxMax;
     const float wmax = 2.0f * kHMax;
     int nb = 0;
@@ -138,9 +136,24 @@ __device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
 // exp(delta c) and, for boxes narrow enough to be expanded, the Taylor
 // coefficients.  Partial moments are summed over the block in a fixed tree.
 struct MomSmem {
-    dfloat red[kMomT][kBoxTerms + 1];
+    dfloat wd[kMomT / 32][kBoxDF + 1];           // per-warp moment sums
+    float wf[kMomT / 32][kBoxTerms - kBoxDF];
     float fr[3][kMomT / 32];
 };
+
+// Moment of order m summed over the warps in order.
+__device__ __forceinline__ dfloat moment_sum(const MomSmem& sm, int m) {
+    if (m <= kBoxDF) {
+        dfloat a = sm.wd[0][m];
+#pragma unroll
+        for (int w = 1; w < kMomT / 32; ++w) a = df_add(a, sm.wd[w][m]);
+        return a;
+    }
+    float a = sm.wf[0][m - kBoxDF - 1];
+#pragma unroll
+    for (int w = 1; w < kMomT / 32; ++w) a += sm.wf[w][m - kBoxDF - 1];
+    return {a, 0.0f};
+}
 
 __device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& f,
                                                  MomSmem& sm, int64_t slot) {
@@ -193,9 +206,14 @@ __device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& 
         f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
     }
     if (!expand) return;   // the same for the block
-    dfloat M[kBoxTerms + 1];
+    // moments: orders 0..kBoxDF in double-float; the higher ones only enter
+    // the expansions' FP32 tails
+    dfloat M[kBoxDF + 1];
+    float Mf[kBoxTerms - kBoxDF];
 #pragma unroll
-    for (int m = 0; m <= kBoxTerms; ++m) M[m] = {0.0f, 0.0f};
+    for (int m = 0; m <= kBoxDF; ++m) M[m] = {0.0f, 0.0f};
+#pragma unroll
+    for (int m = 0; m < kBoxTerms - kBoxDF; ++m) Mf[m] = 0.0f;
     for (int s = tid; s < n; s += kMomT) {
         const dfloat d = df_add_f(f.src_f[s0 + s], -c);
         dfloat ex = df_add_f(df_neg(f.prior[s0 + s]), pm);
@@ -204,27 +222,41 @@ __device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& 
         dfloat q = df_exp(ex, f.t64);
         const dfloat ds = {d.hi * inv_sc, d.lo * inv_sc};   // d / s, |d / s| <= 1
 #pragma unroll
-        for (int m = 0; m <= kBoxTerms; ++m) {
+        for (int m = 0; m <= kBoxDF; ++m) {
             M[m] = df_add(M[m], q);
-            if (m < kBoxTerms) q = df_mul(q, ds);
+            q = df_mul(q, ds);
+        }
+        float qf = q.hi;
+#pragma unroll
+        for (int m = 0; m < kBoxTerms - kBoxDF; ++m) {
+            Mf[m] += qf;
+            qf *= ds.hi;
         }
     }
 #pragma unroll
-    for (int m = 0; m <= kBoxTerms; ++m) sm.red[tid][m] = M[m];
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int m = 0; m <= kBoxDF; ++m) {
+            const dfloat other = {__shfl_down_sync(kFull, M[m].hi, o),
+                                  __shfl_down_sync(kFull, M[m].lo, o)};
+            M[m] = df_add(M[m], other);
+        }
+#pragma unroll
+        for (int m = 0; m < kBoxTerms - kBoxDF; ++m)
+            Mf[m] += __shfl_down_sync(kFull, Mf[m], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int m = 0; m <= kBoxDF; ++m) sm.wd[warp][m] = M[m];
+#pragma unroll
+        for (int m = 0; m < kBoxTerms - kBoxDF; ++m) sm.wf[warp][m] = Mf[m];
+    }
     __syncthreads();
-    for (int w = kMomT / 2; w > 0; w >>= 1) {
-        if (tid < w) {
-#pragma unroll
-            for (int m = 0; m <= kBoxTerms; ++m)
-                sm.red[tid][m] = df_add(sm.red[tid][m], sm.red[tid + w][m]);
-        }
-        __syncthreads();
-    }
     if (tid < kBoxTerms) {
         double fact = 1.0;
         for (int m = 2; m <= tid; ++m) fact *= (double)m;   // n! (rounded above 22!)
         const dfloat inv = df_from_double(1.0 / fact);
-        const dfloat Mn = sm.red[0][tid], Mn1 = sm.red[0][tid + 1];
+        const dfloat Mn = moment_sum(sm, tid), Mn1 = moment_sum(sm, tid + 1);
         dfloat* co = f.box_coef + slot * (2 * kBoxTerms);
         co[tid] = df_mul(Mn, inv);
         co[kBoxTerms + tid] = df_mul(df_add(df_mul_f(Mn, c), df_mul_f(Mn1, sc)), inv);
@@ -250,10 +282,9 @@ __device__ __forceinline__ void run_shift_body(const Geom& g, const FastView& f,
     const float ya = (float)((double)(j0 - g.hy) * g.delta);
     const float yb = (float)((double)(j0 + f.run - 1 - g.hy) * g.delta);
     float lo = FLT_MAX, hi = FLT_MAX;
-    const int nslot = f.n_tiles * kBoxMax;
-    for (int s = lane; s < nslot; s += 32) {
-        const int t = s / kBoxMax;
-        if (s - t * kBoxMax >= f.box_cnt[t]) continue;
+    const int nb = lane < f.n_tiles ? f.box_cnt[lane] : 0;   // lane = tile
+    for (int k = 0; k < nb; ++k) {
+        const int64_t s = (int64_t)lane * kBoxMax + k;
         const float4 geo = f.box_geo[s];
         const float4 rg = f.box_rng[s];
         const float d1 = fmaxf(0.0f, fmaxf(rg.x - ya, ya - rg.y));
@@ -494,21 +525,29 @@ __device__ __forceinline__ void u1_combine_body(const Geom& g, const FastView& f
     const int64_t j = bx * blockDim.x + threadIdx.x;
     if (j >= g.n_y) return;
     double n = 0.0, d = 0.0;
-    for (int t = 0; t < f.n_tiles; ++t) {
-        n += f.partN[(size_t)t * g.n_y + j];
-        d += f.partD[(size_t)t * g.n_y + j];
+    for (int t0 = 0; t0 < f.n_tiles; t0 += 8) {
+        double pn[8], pd[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {   // issue the loads, then sum in order
+            const int t = t0 + k < f.n_tiles ? t0 + k : t0;
+            pn[k] = f.partN[(size_t)t * g.n_y + j];
+            pd[k] = f.partD[(size_t)t * g.n_y + j];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (t0 + k < f.n_tiles) {
+                n += pn[k];
+                d += pd[k];
+            }
     }
     U[j] = n / d;
 }
 
 // ---- single-instance kernels --------------------------------------------------
 
-__global__ void k_sources(Geom g, FastView f, const int64_t* __restrict__ nu) {
-    sources_body(g, f, nu, blockIdx.x);
-}
-
-__global__ void __launch_bounds__(32) k_box_plan(Geom g, FastView f) {
-    box_plan_body(g, f, blockIdx.x);
+__global__ void __launch_bounds__(kPlanT) k_box_plan(Geom g, FastView f,
+                                                    const int64_t* __restrict__ nu) {
+    box_plan_body(g, f, nu, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kMomT) k_box_moments(Geom g, FastView f) {
@@ -545,16 +584,11 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
     return r;
 }
 
-__global__ void kb_sources(const InstDev* insts, const BlockRef* map) {
+__global__ void __launch_bounds__(kPlanT) kb_box_plan(const InstDev* insts,
+                                                     const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
-    sources_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], r.local);
-}
-
-__global__ void __launch_bounds__(32) kb_box_plan(const InstDev* insts, const BlockRef* map) {
-    __shared__ InstDev sd;
-    const BlockRef r = stage(insts, map, sd);
-    box_plan_body(sd.g, sd.f, r.local);
+    box_plan_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], r.local);
 }
 
 __global__ void __launch_bounds__(kMomT) kb_box_moments(const InstDev* insts,
@@ -650,11 +684,8 @@ bool u1_carve(const Geom& g, FastView* f, void* (*get)(void*, size_t), void* ctx
 void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
                       double* U, cudaStream_t s, Prof* prof) {
     cudaEvent_t ev;
-    int k = prof ? prof->begin("mmse_sources", &ev) : -1;
-    k_sources<<<blocks(g.n_x, 256), 256, 0, s>>>(g, f, nu);
-    if (prof) prof->end(k, ev);
-    k = prof ? prof->begin("u1_boxes", &ev) : -1;
-    k_box_plan<<<(unsigned)f.n_tiles, 32, 0, s>>>(g, f);
+    int k = prof ? prof->begin("u1_boxes", &ev) : -1;
+    k_box_plan<<<(unsigned)f.n_tiles, kPlanT, 0, s>>>(g, f, nu);
     k_box_moments<<<(unsigned)(f.n_tiles * kBoxMax), kMomT, 0, s>>>(g, f);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("u1_shift", &ev) : -1;
@@ -691,8 +722,7 @@ int64_t batch_mmse_blocks(const Geom&, const FastPlan& fp) {
 
 void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s) {
     const InstDev* d = bl.insts;
-    kb_sources<<<(unsigned)bl.n_blocks[kBPerX], 256, 0, s>>>(d, bl.map[kBPerX]);
-    kb_box_plan<<<(unsigned)bl.n_blocks[kBTile], 32, 0, s>>>(d, bl.map[kBTile]);
+    kb_box_plan<<<(unsigned)bl.n_blocks[kBTile], kPlanT, 0, s>>>(d, bl.map[kBTile]);
     kb_box_moments<<<(unsigned)bl.n_blocks[kBBox], kMomT, 0, s>>>(d, bl.map[kBBox]);
     kb_run_shift<<<(unsigned)bl.n_blocks[kBRun], kRunT, 0, s>>>(d, bl.map[kBRun]);
     for (int r = 0; r < 5; ++r) {

@@ -8,6 +8,7 @@
 
 #include "ucp_fast.cuh"
 #include "ucp_runtime.h"
+#include "batch_set.h"
 
 namespace ucp {
 
@@ -369,6 +370,42 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     return refresh_costs(in, 0);
 }
 
+// Fast-path sweeps replayed from a captured graph (non-default stream,
+// profiler off).  Returns false when the graph is not available (the caller
+// launches kernel by kernel); the kernels are the batched ones over a batch
+// of this instance alone, so results are the same either way.
+static bool solo_sweeps(ucp_inst* in, int n) {
+    if (!in->stream || in->prof.on) return false;
+    if (!in->solo_tried) {
+        in->solo_tried = true;
+        in->solo = new BatchSet();
+        in->solo->arena = &in->arena;
+        std::vector<ucp_inst*> one{in};
+        if (batchset_build(*in->solo, one, in->stream) != UCP_OK) {
+            cudaGetLastError();
+            return false;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess) {
+            launch_batch_sweep(in->solo->bl, in->stream);
+            if (cudaStreamEndCapture(in->stream, &graph) == cudaSuccess && graph) {
+                if (cudaGraphInstantiate(&in->solo_graph, graph, 0) != cudaSuccess)
+                    in->solo_graph = nullptr;
+                cudaGraphDestroy(graph);
+            }
+        }
+        cudaGetLastError();  // a failed capture falls back to plain launches
+    }
+    if (!in->solo_graph) return false;
+    std::vector<ucp_inst*> one{in};
+    if (batchset_refresh(*in->solo, one, in->stream) != UCP_OK) return false;
+    for (int k = 0; k < n; ++k) cudaGraphLaunch(in->solo_graph, in->stream);
+    in->sweeps_done += n;
+    in->cur ^= (n & 1);
+    return true;
+}
+
 ucp_status inst_sweep(ucp_inst* in, int n) {
     if (n == 0) return UCP_OK;
     ucp_status st = grow_history(in, in->sweeps_done + 1 + n);
@@ -376,6 +413,7 @@ ucp_status inst_sweep(ucp_inst* in, int n) {
     const Geom& g = in->g;
     DevState& d = in->d;
     cudaStream_t s = in->stream;
+    if (in->fast && solo_sweeps(in, n)) return check(in, "sweep");
     if (in->fast) {
         for (int k = 0; k < n; ++k) {
             UCP_LAUNCH(in, "search", launch_search_fast(g, in->fv, d.nu[in->cur],
@@ -452,6 +490,10 @@ ucp_status inst_set(ucp_inst* in, const double* f, const double* u1) {
 
 void inst_release(ucp_inst* in) {
     if (in->stream) cudaStreamSynchronize(in->stream);
+    if (in->solo_graph) cudaGraphExecDestroy(in->solo_graph);
+    in->solo_graph = nullptr;
+    delete in->solo;
+    in->solo = nullptr;
     in->prof.drain();
     in->arena.release_all();
     if (in->own_stream && in->stream) cudaStreamDestroy(in->stream);

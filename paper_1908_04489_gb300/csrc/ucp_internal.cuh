@@ -147,9 +147,8 @@ struct BlockRef {
 };
 
 enum BatchKind {
-    kBSearch = 0, kBPerX = 1, kBTile = 2, kBPerY = 3, kBTabPart = 4,
-    kBTabComb = 5, kBBuildE = 6, kBJPart = 7, kBBox = 8, kBRun = 9,
-    kBKinds = 10
+    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBTabComb, kBBuildE, kBJPart, kBBox,
+    kBRun, kBKinds
 };
 
 // Device arrays describing one batched sweep.

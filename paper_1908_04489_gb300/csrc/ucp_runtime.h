@@ -45,6 +45,8 @@ ucp_status prof_enable(Prof* p, cudaStream_t s, bool on);
 int prof_collect(Prof* p, const char** names, int64_t* launches, double* ms,
                  int cap);
 
+struct BatchSet;  // batch_set.h
+
 // Owner of device allocations made through a context.
 struct Arena {
     ucp_ctx* ctx = nullptr;
@@ -74,6 +76,11 @@ struct ucp_inst {
     bool fast = false;           // precision 1
     double fbound = 0.0;         // largest |f| or |U| set by the caller
     ucp::FastView fv{};
+    // fast path on a non-default stream: one sweep captured as a CUDA graph
+    // over a one-member batch set (device-side sweep state), replayed
+    ucp::BatchSet* solo = nullptr;
+    cudaGraphExec_t solo_graph = nullptr;
+    bool solo_tried = false;
 };
 
 namespace ucp {
