@@ -54,11 +54,18 @@ static int refine_slot(int G) {
     return G >= 32 ? 4 : (G >= 16 ? 3 : (G >= 8 ? 2 : (G >= 4 ? 1 : 0)));
 }
 
+static int defer_blocks_per_inst(size_t n) {
+    return n >= 16 ? kDeferBlocksBatch : (int)(64 / n);
+}
+
 ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
                             cudaStream_t s) {
     const size_t n = members.size();
     bs.desc.resize(n);
-    for (size_t k = 0; k < n; ++k) bs.desc[k] = describe_inst(members[k]);
+    for (size_t k = 0; k < n; ++k) {
+        bs.desc[k] = describe_inst(members[k]);
+        bs.desc[k].defer_blocks = defer_blocks_per_inst(n);
+    }
     if (n) cudaMemcpyAsync(bs.insts, bs.desc.data(), sizeof(InstDev) * n,
                            cudaMemcpyHostToDevice, s);
     return cudaGetLastError() == cudaSuccess ? UCP_OK : UCP_E_CUDA;
@@ -67,7 +74,8 @@ ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
 ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
                           cudaStream_t s) {
     const size_t n = members.size();
-    std::vector<BlockRef> maps[kBKinds], smaps[5], mmaps[5];
+    std::vector<BlockRef> maps[kBKinds], smaps[5], mmaps[5], dmaps[5];
+    const int defer_blocks = defer_blocks_per_inst(n);
     for (size_t k = 0; k < n; ++k) {
         const ucp_inst* in = members[k];
         for (int kind = 1; kind < kBKinds; ++kind) {
@@ -77,12 +85,14 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
         std::vector<BlockRef>& sm = smaps[refine_slot(in->g.n_refine)];
         const int64_t ns = batch_blocks(in->g, in->fv, kBSearch);
         for (int64_t x = 0; x < ns; ++x) sm.push_back({(int32_t)k, (int32_t)x});
+        std::vector<BlockRef>& dm = dmaps[refine_slot(in->g.n_refine)];
+        for (int x = 0; x < defer_blocks; ++x) dm.push_back({(int32_t)k, x});
         std::vector<BlockRef>& mm = mmaps[run_slot(in->fv.run)];
         const int64_t nm = batch_mmse_blocks(in->g, in->fv);
         for (int64_t x = 0; x < nm; ++x) mm.push_back({(int32_t)k, (int32_t)x});
     }
     bs.host_maps.clear();
-    size_t off[kBKinds], soff[5], moff[5];
+    size_t off[kBKinds], soff[5], moff[5], doff[5];
     for (int kind = 0; kind < kBKinds; ++kind) {
         off[kind] = bs.host_maps.size();
         bs.host_maps.insert(bs.host_maps.end(), maps[kind].begin(), maps[kind].end());
@@ -94,6 +104,10 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
     for (int r = 0; r < 5; ++r) {
         moff[r] = bs.host_maps.size();
         bs.host_maps.insert(bs.host_maps.end(), mmaps[r].begin(), mmaps[r].end());
+    }
+    for (int r = 0; r < 5; ++r) {
+        doff[r] = bs.host_maps.size();
+        bs.host_maps.insert(bs.host_maps.end(), dmaps[r].begin(), dmaps[r].end());
     }
     // grow the device buffers (after the stream drains, as they may be in use)
     if (n > bs.insts_cap || bs.host_maps.size() > bs.maps_cap) {
@@ -128,6 +142,8 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
         bl.search_blocks[r] = (int64_t)smaps[r].size();
         bl.mmse_map[r] = bs.maps + moff[r];
         bl.mmse_blocks[r] = (int64_t)mmaps[r].size();
+        bl.defer_map[r] = bs.maps + doff[r];
+        bl.defer_blocks[r] = (int64_t)dmaps[r].size();
     }
     return batchset_refresh(bs, members, s);
 }

@@ -119,12 +119,24 @@ __device__ double exact_costs_batch(const Geom& g, const FastView& f, int64_t i,
 // fixed order (every lane gets the same value).  The sum has no cancellation, so its
 // bound is several times tighter than the table identity's.  Candidates
 // outside the tables get an infinite bound (no second tier).
+// Cross-group partial sums of the block-cooperative second tier.
+constexpr int kCoopT = 256;   // threads per block of the deferred search
+struct CoopSmem {
+    double acc[kCoopT / 2][2];
+    float emax[kCoopT / 2][2], demax[kCoopT / 2][2];
+};
+
+// With cs == nullptr the group's G lanes take every tap; otherwise the
+// blockDim.x / G groups of the block (all costing the same candidates) split
+// the taps and their partial sums are combined in group order.
 template <int G>
 __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
                                 const int64_t (&nu)[2], int lane, double (&g2)[2],
-                                double (&b2)[2]) {
+                                double (&b2)[2], CoopSmem* cs = nullptr) {
     // two candidates per pass over the taps (independent chains interleave)
     const unsigned gm = group_mask<G>();
+    const int part = cs ? (int)(threadIdx.x / G) : 0;
+    const int nparts = cs ? (int)(blockDim.x / G) : 1;
     int64_t p[2];
     dfloat t[2];
     bool ok[2];
@@ -140,8 +152,8 @@ __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
     dfloat blk[2] = {{0.f, 0.f}, {0.f, 0.f}};
     float emax[2] = {0.f, 0.f}, demax[2] = {0.f, 0.f};
     int cnt = 0;
-#pragma unroll 2
-    for (int64_t l = lane; l < g.n_w; l += G) {
+#pragma unroll 1
+    for (int64_t l = part * G + lane; l < g.n_w; l += G * nparts) {
         const dfloat w = f.wdf[l], ph = f.phidf[l];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -170,9 +182,35 @@ __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
             emax[b] = fmaxf(emax[b], __shfl_down_sync(gm, emax[b], off, G));
             demax[b] = fmaxf(demax[b], __shfl_down_sync(gm, demax[b], off, G));
         }
-        const double S2 = __shfl_sync(gm, acc[b], 0, G);
-        const float em = __shfl_sync(gm, emax[b], 0, G);
-        const float dm = __shfl_sync(gm, demax[b], 0, G);
+    }
+    if (cs) {
+        if (lane == 0) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                cs->acc[part][b] = acc[b];
+                cs->emax[part][b] = emax[b];
+                cs->demax[part][b] = demax[b];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            acc[b] = cs->acc[0][b];
+            emax[b] = cs->emax[0][b];
+            demax[b] = cs->demax[0][b];
+            for (int q = 1; q < nparts; ++q) {
+                acc[b] += cs->acc[q][b];
+                emax[b] = fmaxf(emax[b], cs->emax[q][b]);
+                demax[b] = fmaxf(demax[b], cs->demax[q][b]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const double S2 = cs ? acc[b] : __shfl_sync(gm, acc[b], 0, G);
+        const float em = cs ? emax[b] : __shfl_sync(gm, emax[b], 0, G);
+        const float dm = cs ? demax[b] : __shfl_sync(gm, demax[b], 0, G);
         if (!ok[b]) {
             g2[b] = 0.0;
             b2[b] = INFINITY;
@@ -381,28 +419,46 @@ __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int 
 // Resolve one stage of the list: the carried winner (lane 0) plus positions
 // p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
 // costs over all of them.
-constexpr int kKeep = 6;   // candidates per lane whose screened bounds are kept
+constexpr int kKeep = kTieBatch;   // candidates per lane whose screened bounds are kept
+
+// How resolve() settles a stage with several values still in play:
+// kTierInline runs the second and third tiers in the group; kTierDefer gives
+// up (the x0 point is searched again by the deferred kernel); kTierCoop runs
+// them with the whole block, whose groups all search the same x0 point.
+enum TierMode { kTierInline = 0, kTierDefer = 1, kTierCoop = 2 };
+constexpr int32_t kDeferPos = -2;   // Best.pos of a deferred search
+
+// A deferred search: the x0 point, the stage whose near-tie stopped it and
+// the winner carried into that stage.
+struct DeferRec {
+    int64_t i;
+    int32_t stage;
+    Best best;
+};
+static_assert(sizeof(DeferRec) <= kDeferRecBytes, "deferred-search record size");
 constexpr int kSearchT = 128;   // threads per block of the search
 
-template <int G, typename CandFn>
+template <int G, int Mode, typename CandFn>
 __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
                         const Best& best, int p0, int p_end, CandFn cand,
-                        int32_t* n_exact, double* tie_terms) {
+                        int32_t* n_exact, double* tie_terms, CoopSmem* cs) {
     const bool have_best = best.pos != INT_MAX;
     // 1. smallest upper end; the lower ends of this lane's first kKeep
     // candidates are kept (the rest are evaluated again below)
     dfloat hi = {FLT_MAX, 0.f};
     if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
-    dfloat lo_k[kKeep];
-#pragma unroll
+    // kept in this lane's column of the group's shared scratch (free until
+    // the third tier, which runs after the last use)
+    dfloat* lo_k = (dfloat*)tie_terms + lane;   // lo_k[k * G]
+#pragma unroll 1
     for (int k = 0; k < kKeep; ++k) {
-        lo_k[k] = {FLT_MAX, 0.f};
+        lo_k[k * G] = {FLT_MAX, 0.f};
         const int p = p0 + lane + k * G;
         if (p < p_end) {
             const Eval e = eval_table(g, f, i, cand(p));
             const dfloat h = df_pm(e.gv, e.beta);
             if (df_lt(h, hi)) hi = h;
-            lo_k[k] = df_pm(e.gv, -e.beta);
+            lo_k[k * G] = df_pm(e.gv, -e.beta);
         }
     }
     for (int p = p0 + lane + kKeep * G; p < p_end; p += G) {
@@ -418,10 +474,10 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         vmin = vmax = best.nu;
         pmin = best.pos;
     }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < kKeep; ++k) {
         const int p = p0 + lane + k * G;
-        if (p < p_end && !df_lt(hi, lo_k[k])) {
+        if (p < p_end && !df_lt(hi, lo_k[k * G])) {
             const int64_t nu = cand(p);
             vmin = nu < vmin ? nu : vmin;
             vmax = nu > vmax ? nu : vmax;
@@ -446,6 +502,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         const Eval e = eval_table(g, f, i, vmin);
         return {e.gv, e.beta, pmin, vmin, false, 0.0};
     }
+    if (Mode == kTierDefer) return {{0.f, 0.f}, 0.f, kDeferPos, 0, false, 0.0};
     // 3. several values in play.  Gather them into lanes (member m in lane
     // m; the carried winner first), cost each by the direct double-float
     // quadrature (second tier) and keep those whose tighter intervals can
@@ -477,12 +534,12 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
             }
         }
     };
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < kKeep; ++k) {
         const int pb = p0 + k * G;
         if (pb < p_end) {   // the same for the group
             const int p = pb + lane;
-            const bool member = p < p_end && !df_lt(hi, lo_k[k]);
+            const bool member = p < p_end && !df_lt(hi, lo_k[k * G]);
             gather(pb, member, member ? cand(p) : 0);
         }
     }
@@ -507,7 +564,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         const int m1 = m + 1 < M ? m + 1 : m;
         const int64_t cn[2] = {__shfl_sync(gm, mnu, m, G), __shfl_sync(gm, mnu, m1, G)};
         double v[2], bv[2];
-        direct_df_cost2<G>(g, f, i, cn, lane, v, bv);
+        direct_df_cost2<G>(g, f, i, cn, lane, v, bv, Mode == kTierCoop ? cs : nullptr);
         if (lane == m) { g2 = v[0]; b2 = bv[0]; }
         if (m1 != m && lane == m1) { g2 = v[1]; b2 = bv[1]; }
     }
@@ -561,6 +618,58 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
     return {df_from_double(xg), 4.0e-15f * (float)fabs(xg), xp, xn, true, xg};
 }
 
+// Corollary 1's pointwise argmin for x0 point i over eq. (2)'s list: stage 0
+// (previous value, neighbours, coarse set), then the refinement levels
+// around the running winner, from stage `stage0` with carried winner `best`.
+// The group's lane 0 of a `writer` group stores the result; a deferred
+// search records where it stopped instead.
+template <int G, int Mode>
+__device__ __forceinline__ void search_one(const Geom& g, const FastView& f,
+                                           const int64_t* __restrict__ nu_pre,
+                                           int64_t* __restrict__ nu_out,
+                                           int32_t* __restrict__ idx_out,
+                                           int32_t* n_exact, double* tie_terms,
+                                           CoopSmem* cs, int64_t i, bool active,
+                                           bool writer, int stage0, Best best) {
+    const int lane = threadIdx.x & (G - 1);
+    const int64_t ic = active ? i : g.n_x - 1;
+    const int64_t* coarse = f.coarse;
+    int32_t* cnt = active && writer ? n_exact : nullptr;
+    const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
+    const int half = G / 2;
+    Best carried = best;
+    int stage = stage0;
+    for (; stage <= g.n_levels; ++stage) {
+        carried = best;
+        if (stage == 0) {
+            best = resolve<G, Mode>(g, f, ic, lane, best, 0, n0,
+                                    [&](int p) { return stage0_nu(g, nu_pre, coarse, ic, p); },
+                                    cnt, tie_terms, cs);
+        } else {
+            const int64_t h = g.q << (g.bits * (g.n_levels - stage));
+            const int64_t centre = best.nu;
+            const int pos = n0 + (stage - 1) * G;
+            best = resolve<G, Mode>(g, f, ic, lane, best, pos, pos + G,
+                                    [&](int p) {
+                                        const int k = p - pos;
+                                        const int64_t m = k < half ? k - half : k - half + 1;
+                                        return centre + m * h;
+                                    },
+                                    cnt, tie_terms, cs);
+        }
+        if (best.pos == kDeferPos) break;
+    }
+    if (!active || !writer || lane != 0) return;
+    if (best.pos == kDeferPos) {
+        DeferRec* rec = (DeferRec*)f.defer_list;
+        rec[atomicAdd(f.defer_cnt, 1)] = {i, stage, carried};
+        return;
+    }
+    nu_out[i] = best.nu;
+    idx_out[i] = best.pos;
+}
+
+// One group of G lanes per x0 point; near-ties are deferred.
 template <int G>
 __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
                                             const int64_t* __restrict__ nu_pre,
@@ -568,46 +677,58 @@ __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
                                             int32_t* __restrict__ idx_out,
                                             int32_t* n_exact, double* tie_smem,
                                             int64_t bx) {
-    const int lane = threadIdx.x & (G - 1);
     const int64_t i = (bx * blockDim.x + threadIdx.x) / G;
-    const bool active = i < g.n_x;
-    const int64_t ic = active ? i : g.n_x - 1;
-    const int64_t* coarse = f.coarse;
     double* tie_terms = tie_smem + (threadIdx.x / G) * (kTieBatch * G);
+    const Best none{{FLT_MAX, 0.f}, 0.f, INT_MAX, 0, false, 0.0};
+    search_one<G, kTierDefer>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_terms,
+                              nullptr, i, i < g.n_x, true, 0, none);
+}
 
-    Best best{{FLT_MAX, 0.f}, 0.f, INT_MAX, 0, false, 0.0};
-    const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
-    best = resolve<G>(g, f, ic, lane, best, 0, n0,
-                      [&](int p) { return stage0_nu(g, nu_pre, coarse, ic, p); },
-                      active ? n_exact : nullptr, tie_terms);
-    const int half = G / 2;
-    int pos = n0;
-    for (int lv = 1; lv <= g.n_levels; ++lv) {
-        const int64_t h = g.q << (g.bits * (g.n_levels - lv));
-        const int64_t centre = best.nu;
-        best = resolve<G>(g, f, ic, lane, best, pos, pos + G,
-                          [&](int p) {
-                              const int k = p - pos;
-                              const int64_t m = k < half ? k - half : k - half + 1;
-                              return centre + m * h;
-                          },
-                          active ? n_exact : nullptr, tie_terms);
-        pos += G;
-    }
-    if (active && lane == 0) {
-        nu_out[i] = best.nu;
-        idx_out[i] = best.pos;
+// The deferred x0 points, one per block at a time (blocks bx, bx + nbx, ...
+// of the list), each resumed at the stage that stopped it: every group of
+// the block searches the same point, the second tier is split over the
+// block, group 0 stores the result.
+template <int G>
+__device__ __forceinline__ void search_deferred_body(const Geom& g, const FastView& f,
+                                                     const int64_t* __restrict__ nu_pre,
+                                                     int64_t* __restrict__ nu_out,
+                                                     int32_t* __restrict__ idx_out,
+                                                     int32_t* n_exact, double* tie_smem,
+                                                     CoopSmem& cs, int64_t bx,
+                                                     int64_t nbx) {
+    const int n = *(volatile int32_t*)f.defer_cnt;
+    double* tie_terms = tie_smem + (threadIdx.x / G) * (kTieBatch * G);
+    const DeferRec* rec = (const DeferRec*)f.defer_list;
+    for (int64_t k = bx; k < n; k += nbx) {
+        const DeferRec r = rec[k];
+        search_one<G, kTierCoop>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_terms,
+                                 &cs, r.i, true, threadIdx.x < G, r.stage, r.best);
+        __syncthreads();   // tie_smem and cs are reused by the next point
     }
 }
 
 template <int G>
-__global__ void __launch_bounds__(kSearchT) k_search_fast(Geom g, FastView f,
+__global__ void __launch_bounds__(kSearchT, 6) k_search_fast(Geom g, FastView f,
                                                      const int64_t* __restrict__ nu_pre,
                                                      int64_t* __restrict__ nu_out,
                                                      int32_t* __restrict__ idx_out,
                                                      int32_t* n_exact) {
     __shared__ double tie_smem[kSearchT * kTieBatch];
     search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
+}
+
+constexpr int kDeferBlocks = 64;        // blocks of the deferred search (one instance)
+
+template <int G>
+__global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
+                                                           const int64_t* __restrict__ nu_pre,
+                                                           int64_t* __restrict__ nu_out,
+                                                           int32_t* __restrict__ idx_out,
+                                                           int32_t* n_exact) {
+    __shared__ double tie_smem[kCoopT * kTieBatch];
+    __shared__ CoopSmem cs;
+    search_deferred_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, cs,
+                            blockIdx.x, gridDim.x);
 }
 
 // ---- correlation tables ---------------------------------------------------
@@ -728,8 +849,8 @@ __global__ void k_tables_combine(Geom g, FastView f) {
 }
 
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
-// prior exponent x_i^2 / 2 sigma^2, W2 = sum phi_l w_l^2 (serial), and the
-// exp(k/64) table of df_exp.
+// prior exponent x_i^2 / 2 sigma^2, W2 = sum phi_l w_l^2 (fixed-order tree),
+// and the exp(k/64) table of df_exp.
 __global__ void k_fast_setup(Geom g, FastView f) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < g.n_w) {
@@ -743,13 +864,20 @@ __global__ void k_fast_setup(Geom g, FastView f) {
         f.prior[k] = df_from_double(__ddiv_rn(__dmul_rn(x, x), g.two_s2));
     }
     if (k < 47) f.t64[k] = df_from_double(exp((double)(k - 23) / 64.0));
-    if (k == 0) {
+    if (blockIdx.x == 0) {   // W2: strided partial sums, then a fixed tree
+        __shared__ double red[256];
         double s = 0.0;
-        for (int64_t l = 0; l < g.n_w; ++l) {
+        for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x) {
             const double w = (double)(l - g.hw) * g.delta;
             s += f.phi[l] * (w * w);
         }
-        *f.W2_dev = s;
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *f.W2_dev = red[0];
     }
 }
 
@@ -779,11 +907,14 @@ __global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
     J_partial_body(g, f, px, nu, red, blockIdx.x);
 }
 
+// J from the block partials (in order); also empties the deferred-search list
+// for the next sweep.
 __global__ void k_J_final(FastView f, int nblk, double* out) {
     if (threadIdx.x != 0) return;
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += f.Jpart[b];
     *out = s;
+    *f.defer_cnt = 0;
 }
 
 
@@ -804,12 +935,23 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
 }
 
 template <int G>
-__global__ void __launch_bounds__(kSearchT) kb_search(const InstDev* insts, const BlockRef* map) {
+__global__ void __launch_bounds__(kSearchT, 5) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
     __shared__ double tie_smem[kSearchT * kTieBatch];
     search_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
                    sd.f.n_exact, tie_smem, r.local);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kCoopT) kb_search_deferred(const InstDev* insts,
+                                                            const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage(insts, map, sd);
+    __shared__ double tie_smem[kCoopT * kTieBatch];
+    __shared__ CoopSmem cs;
+    search_deferred_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
+                            sd.f.n_exact, tie_smem, cs, r.local, sd.defer_blocks);
 }
 
 __global__ void kb_build_E(const InstDev* insts, const BlockRef* map) {
@@ -852,6 +994,7 @@ __global__ void kb_J_final(InstDev* insts, int n) {
     d.J[d.sweeps + 1] = s;
     d.sweeps += 1;
     d.cur ^= 1;
+    *d.f.defer_cnt = 0;
 }
 
 inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -922,6 +1065,20 @@ void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
         default: break;
     }
 #undef UCP_FAST_CASE
+#define UCP_DEFER_CASE(G)                                                          \
+    case G:                                                                        \
+        k_search_deferred<G><<<kDeferBlocks, kCoopT, 0, s>>>(g, f, nu_in, nu_out,   \
+                                                            idx, f.n_exact);       \
+        break;
+    switch (g.n_refine) {
+        UCP_DEFER_CASE(2)
+        UCP_DEFER_CASE(4)
+        UCP_DEFER_CASE(8)
+        UCP_DEFER_CASE(16)
+        UCP_DEFER_CASE(32)
+        default: break;
+    }
+#undef UCP_DEFER_CASE
 }
 
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
@@ -943,6 +1100,11 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
 }
 
 void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
+    launch_batch_search(bl, s);
+    launch_batch_rest(bl, s);
+}
+
+void launch_batch_search(const BatchLaunch& bl, cudaStream_t s) {
     const InstDev* d = bl.insts;
     for (int gi = 0; gi < 5; ++gi) {
         if (bl.search_blocks[gi] == 0) continue;
@@ -956,6 +1118,22 @@ void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
             default: kb_search<32><<<nb, kSearchT, 0, s>>>(d, m); break;
         }
     }
+    for (int gi = 0; gi < 5; ++gi) {
+        if (bl.defer_blocks[gi] == 0) continue;
+        const unsigned nb = (unsigned)bl.defer_blocks[gi];
+        const BlockRef* m = bl.defer_map[gi];
+        switch (gi) {
+            case 0: kb_search_deferred<2><<<nb, kCoopT, 0, s>>>(d, m); break;
+            case 1: kb_search_deferred<4><<<nb, kCoopT, 0, s>>>(d, m); break;
+            case 2: kb_search_deferred<8><<<nb, kCoopT, 0, s>>>(d, m); break;
+            case 3: kb_search_deferred<16><<<nb, kCoopT, 0, s>>>(d, m); break;
+            default: kb_search_deferred<32><<<nb, kCoopT, 0, s>>>(d, m); break;
+        }
+    }
+}
+
+void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s) {
+    const InstDev* d = bl.insts;
     launch_batch_u1(bl, s);
     kb_build_E<<<(unsigned)bl.n_blocks[kBBuildE], 256, 0, s>>>(d, bl.map[kBBuildE]);
     kb_tables_part<<<(unsigned)bl.n_blocks[kBTabPart], kTabT, 0, s>>>(d, bl.map[kBTabPart]);

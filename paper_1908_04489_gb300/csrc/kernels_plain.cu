@@ -89,34 +89,41 @@ __device__ __forceinline__ void group_argmin(double& gv, int32_t& pos,
 
 // ---- setup ------------------------------------------------------------
 
+// Normalised prior weights p_i and quadrature weights phi_l (one block of
+// 1024 threads).  phi's sum runs serially in index order, as the oracle's
+// does (the serial re-costing of near ties must see the same phi); p_i only
+// weight J, so their sum is a fixed-order tree, which overlaps phi's chain.
 __global__ void k_weights(Geom g, double* px, double* phi) {
-    __shared__ double total;
-    for (int64_t i = threadIdx.x; i < g.n_x; i += blockDim.x) {
+    __shared__ double red[1024];
+    __shared__ double tot_phi;
+    const int tid = threadIdx.x;
+    for (int64_t i = tid; i < g.n_x; i += blockDim.x) {
         const double xi = x_of(g, i);
         px[i] = exp(-__ddiv_rn(__dmul_rn(xi, xi), g.two_s2));
     }
-    for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x) {
+    for (int64_t l = tid; l < g.n_w; l += blockDim.x) {
         const double wl = __dmul_rn((double)(l - g.hw), g.delta);
         phi[l] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int64_t i = 0; i < g.n_x; ++i) s = __dadd_rn(s, px[i]);
-        total = s;
-    }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < g.n_x; i += blockDim.x)
-        px[i] = __ddiv_rn(px[i], total);
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    double part = 0.0;
+    if (tid == 0) {
         double s = 0.0;
         for (int64_t l = 0; l < g.n_w; ++l) s = __dadd_rn(s, phi[l]);
-        total = s;
+        tot_phi = s;
+    } else {
+        for (int64_t i = tid - 1; i < g.n_x; i += blockDim.x - 1)
+            part = __dadd_rn(part, px[i]);
     }
+    red[tid] = part;
     __syncthreads();
-    for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x)
-        phi[l] = __ddiv_rn(phi[l], total);
+    for (int w = 512; w > 0; w >>= 1) {
+        if (tid < w) red[tid] = __dadd_rn(red[tid], red[tid + w]);
+        __syncthreads();
+    }
+    const double tot_px = red[0];
+    for (int64_t i = tid; i < g.n_x; i += blockDim.x) px[i] = __ddiv_rn(px[i], tot_px);
+    for (int64_t l = tid; l < g.n_w; l += blockDim.x) phi[l] = __ddiv_rn(phi[l], tot_phi);
 }
 
 // kind 0: identity f(x) = x; kind 1: odd staircase with step n7 (units of

@@ -183,7 +183,7 @@ size_t inst_bytes(const Geom& g, int precision) {
         fast_plan(g, &fp);
         b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
              3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
-             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 2 * rnd(4) + rnd(32) +
+             rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 3 * rnd(4) + rnd(kDeferRecBytes * nx) + rnd(32) +
              rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
              u1_scratch_bytes(g, fp, 256);
     }
@@ -254,12 +254,14 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
     f.n_tier2 = (int32_t*)A.get(4);
+    f.defer_cnt = (int32_t*)A.get(4);
+    f.defer_list = A.get(kDeferRecBytes * nx);
     f.n_pairs = (int64_t*)A.get(32);
     const bool u1_ok = u1_carve(
         g, &f, [](void* a, size_t n) { return ((Arena*)a)->get(n); }, &A);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf || !f.wdf ||
         !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tab_part || !f.W2_dev ||
-        !f.n_exact || !f.n_tier2 || !f.n_pairs) {
+        !f.n_exact || !f.n_tier2 || !f.defer_cnt || !f.defer_list || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
     }
@@ -339,6 +341,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
         UCP_LAUNCH(in, "fast_setup", launch_fast_setup(g, in->fv, s));
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
         cudaMemsetAsync(in->fv.n_tier2, 0, 4, s);
+        cudaMemsetAsync(in->fv.defer_cnt, 0, 4, s);
         cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
@@ -370,39 +373,55 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     return refresh_costs(in, 0);
 }
 
-// Fast-path sweeps replayed from a captured graph (non-default stream,
-// profiler off).  Returns false when the graph is not available (the caller
-// launches kernel by kernel); the kernels are the batched ones over a batch
-// of this instance alone, so results are the same either way.
+// Fast-path sweeps replayed from captured graphs (non-default stream,
+// profiler off).  Returns false when the graphs are not available (the
+// caller launches kernel by kernel); the kernels are the same computations
+// either way, so the results are too.
+static void solo_drop(ucp_inst* in) {
+    for (int c = 0; c < 2; ++c) {
+        if (in->solo_graph[c]) cudaGraphExecDestroy(in->solo_graph[c]);
+        in->solo_graph[c] = nullptr;
+    }
+    in->solo_tried = false;
+}
+
 static bool solo_sweeps(ucp_inst* in, int n) {
     if (!in->stream || in->prof.on) return false;
     if (!in->solo_tried) {
         in->solo_tried = true;
-        in->solo = new BatchSet();
-        in->solo->arena = &in->arena;
-        std::vector<ucp_inst*> one{in};
-        if (batchset_build(*in->solo, one, in->stream) != UCP_OK) {
-            cudaGetLastError();
-            return false;
+        if (!in->solo) {
+            in->solo = new BatchSet();
+            in->solo->arena = &in->arena;
+            std::vector<ucp_inst*> one{in};
+            if (batchset_build(*in->solo, one, in->stream) != UCP_OK) {
+                cudaGetLastError();
+                return false;
+            }
         }
-        cudaGraph_t graph = nullptr;
-        if (cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) ==
-            cudaSuccess) {
-            launch_batch_sweep(in->solo->bl, in->stream);
+        for (int c = 0; c < 2; ++c) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess)
+                break;
+            launch_search_fast(in->g, in->fv, in->d.nu[c], in->d.nu[c ^ 1], in->d.idx,
+                               in->stream);
+            launch_batch_rest(in->solo->bl, in->stream);
             if (cudaStreamEndCapture(in->stream, &graph) == cudaSuccess && graph) {
-                if (cudaGraphInstantiate(&in->solo_graph, graph, 0) != cudaSuccess)
-                    in->solo_graph = nullptr;
+                if (cudaGraphInstantiate(&in->solo_graph[c], graph, 0) != cudaSuccess)
+                    in->solo_graph[c] = nullptr;
                 cudaGraphDestroy(graph);
             }
         }
         cudaGetLastError();  // a failed capture falls back to plain launches
     }
-    if (!in->solo_graph) return false;
+    if (!in->solo_graph[0] || !in->solo_graph[1]) return false;
     std::vector<ucp_inst*> one{in};
     if (batchset_refresh(*in->solo, one, in->stream) != UCP_OK) return false;
-    for (int k = 0; k < n; ++k) cudaGraphLaunch(in->solo_graph, in->stream);
+    for (int k = 0; k < n; ++k) {
+        cudaGraphLaunch(in->solo_graph[in->cur], in->stream);
+        in->cur ^= 1;
+    }
     in->sweeps_done += n;
-    in->cur ^= (n & 1);
     return true;
 }
 
@@ -464,6 +483,8 @@ ucp_status inst_set(ucp_inst* in, const double* f, const double* u1) {
     const Geom& g = in->g;
     DevState& d = in->d;
     cudaStream_t s = in->stream;
+    if (in->stream) cudaStreamSynchronize(in->stream);
+    solo_drop(in);   // the captured searches hold the screening bounds by value
     if (in->fast) {
         double fm = in->fbound;
         for (int64_t i = 0; i < g.n_x; ++i) fm = fabs(f[i]) > fm ? fabs(f[i]) : fm;
@@ -490,8 +511,7 @@ ucp_status inst_set(ucp_inst* in, const double* f, const double* u1) {
 
 void inst_release(ucp_inst* in) {
     if (in->stream) cudaStreamSynchronize(in->stream);
-    if (in->solo_graph) cudaGraphExecDestroy(in->solo_graph);
-    in->solo_graph = nullptr;
+    solo_drop(in);
     delete in->solo;
     in->solo = nullptr;
     in->prof.drain();

@@ -29,8 +29,10 @@ void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind);
 int64_t batch_mmse_blocks(const Geom& g, const FastPlan& fp);
 // One sweep of every instance of the batch (search, u1, tables, J; then the
-// device-side cur / sweep counters advance).
+// device-side cur / sweep counters advance); or its search alone, or the rest.
 void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s);
+void launch_batch_search(const BatchLaunch& bl, cudaStream_t s);
+void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s);
 void launch_J_fast(const Geom& g, const FastView& f, const double* px,
                    const int64_t* nu, double* out, cudaStream_t s, Prof* prof);
 

@@ -108,6 +108,8 @@ struct FastView : FastPlan {
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
     int32_t* n_tier2;    // count of direct double-float quadratures (second tier)
+    int32_t* defer_cnt;  // x0 points whose search was deferred this sweep
+    void* defer_list;    // [n_x] their records (search position, carried winner)
     int64_t* n_pairs;    // [4] u1 work: direct (source, run) pairs, (box, run)
                          // expansions, double-float and FP32 Taylor terms
     double W2;           // host copy of *W2_dev
@@ -138,6 +140,7 @@ struct InstDev {
     double* J;         // J history
     int32_t cur;       // nu[cur] holds f
     int32_t sweeps;    // sweeps done (J history slot of the current J)
+    int32_t defer_blocks;  // blocks of the deferred search for this instance
 };
 
 // Block of a batched launch: which instance, which block of its own grid.
@@ -161,7 +164,15 @@ struct BatchLaunch {
     int64_t search_blocks[5];
     const BlockRef* mmse_map[5];   // u1 main kernel per run length 1, 2, 4, 8, 16
     int64_t mmse_blocks[5];
+    const BlockRef* defer_map[5];  // deferred search per n_refine
+    int64_t defer_blocks[5];
 };
+
+// Blocks of the deferred (near-tie) search per instance of a batch of 16 or
+// more (smaller batches get 64 / n), and the bytes of one deferred-search
+// record (kernels_fast.cu checks the size).
+constexpr int kDeferBlocksBatch = 4;
+constexpr size_t kDeferRecBytes = 64;
 
 // ---- plain FP64 path (kernels_plain.cu) --------------------------------
 void launch_weights(const Geom& g, DevState& d, cudaStream_t s);

@@ -77,9 +77,11 @@ struct ucp_inst {
     double fbound = 0.0;         // largest |f| or |U| set by the caller
     ucp::FastView fv{};
     // fast path on a non-default stream: one sweep captured as a CUDA graph
-    // over a one-member batch set (device-side sweep state), replayed
+    // per buffer parity (the search with this instance's own launch
+    // parameters, the rest over a one-member batch set with device-side
+    // sweep state), replayed
     ucp::BatchSet* solo = nullptr;
-    cudaGraphExec_t solo_graph = nullptr;
+    cudaGraphExec_t solo_graph[2] = {nullptr, nullptr};
     bool solo_tried = false;
 };
 
