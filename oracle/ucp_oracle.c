@@ -26,9 +26,13 @@
  *     (Section III-D, "Initialization"); u1 is linearly interpolated between
  *     samples and held constant beyond them.
  *
- * Arithmetic: every sum runs in index order in FP64; compile with
- * -ffp-contract=off so that no multiply-add is fused.  The parallel loops over
- * i and j give results independent of the thread count.
+ * Arithmetic: FP64; compile with -ffp-contract=off so that no multiply-add
+ * is fused.  The w quadrature S(u) and the normalising sums of the prior and
+ * quadrature weights are fixed_sum(): serial within chunks of 32 consecutive
+ * terms, then the chunk sums pairwise by levels (the paper does not fix a
+ * summation order; this one is the same on any machine and parallelises).
+ * The u1 sums and J run in index order.  The parallel loops over i and j
+ * give results independent of the thread count.
  *
  * Parity status: S, g, the search, the u1 update and J are pinned by the
  * tests in tests/test_oracle_pins.py (closed forms, library interpolation,
@@ -137,13 +141,38 @@ int orc_sizes(const orc_params* p, int64_t* n_x, int64_t* n_w, int64_t* n_y,
 }
 
 /* phi_l proportional to exp(-w_l^2 / 2), summing to 1 (rectangle rule). */
+/* Sum of t[0..n) in a fixed order: chunk k = t[32k] + ... + t[32k + 31]
+ * added left to right, then level by level the neighbours (2m, 2m + 1) of
+ * the previous level are added, an unpaired last entry moving up as it is. */
+#define ORC_CHUNK 32
+static double fixed_sum(const double* t, int64_t n) {
+    if (n <= 0) return 0.0;
+    int64_t m = (n + ORC_CHUNK - 1) / ORC_CHUNK;
+    double stack_buf[256];
+    double* c = m <= 256 ? stack_buf : (double*)malloc(sizeof(double) * (size_t)m);
+    for (int64_t k = 0; k < m; ++k) {
+        double a = 0.0;
+        int64_t e = (k + 1) * ORC_CHUNK < n ? (k + 1) * ORC_CHUNK : n;
+        for (int64_t j = k * ORC_CHUNK; j < e; ++j) a = a + t[j];
+        c[k] = a;
+    }
+    while (m > 1) {
+        int64_t h = m / 2;
+        for (int64_t k = 0; k < h; ++k) c[k] = c[2 * k] + c[2 * k + 1];
+        if (m & 1) c[h] = c[m - 1];
+        m = h + (m & 1);
+    }
+    double r = c[0];
+    if (c != stack_buf) free(c);
+    return r;
+}
+
 static void phi_weights(const geom* g, double* phi) {
-    double sum = 0.0;
     for (int64_t l = 0; l < g->n_w; ++l) {
         double w = w_of(g, l);
         phi[l] = exp(-(w * w) / 2.0);
-        sum = sum + phi[l];
     }
+    double sum = fixed_sum(phi, g->n_w);
     for (int64_t l = 0; l < g->n_w; ++l) phi[l] = phi[l] / sum;
 }
 
@@ -151,15 +180,18 @@ int orc_grids(const orc_params* p, double* x, double* px, double* w,
               double* phi, double* y) {
     geom g;
     if (make_geom(p, &g)) return -1;
-    double s2 = p->sigma * p->sigma, sum = 0.0;
+    double s2 = p->sigma * p->sigma;
+    double* pr = (double*)malloc(sizeof(double) * (size_t)g.n_x);
+    if (!pr) return -1;
     for (int64_t i = 0; i < g.n_x; ++i) {
         double xi = x_of(&g, i);
         if (x) x[i] = xi;
-        if (px) px[i] = exp(-(xi * xi) / (2.0 * s2));
-        sum = sum + exp(-(xi * xi) / (2.0 * s2));
+        pr[i] = exp(-(xi * xi) / (2.0 * s2));
     }
+    double sum = fixed_sum(pr, g.n_x);
     if (px)
-        for (int64_t i = 0; i < g.n_x; ++i) px[i] = px[i] / sum;
+        for (int64_t i = 0; i < g.n_x; ++i) px[i] = pr[i] / sum;
+    free(pr);
     for (int64_t l = 0; l < g.n_w; ++l)
         if (w) w[l] = w_of(&g, l);
     if (phi) phi_weights(&g, phi);
@@ -225,15 +257,18 @@ static double S_of(const geom* g, const double* phi, const double* U,
     double t = ldexp((double)(nu - cell * g->one), -g->shift);
     int64_t jb = cell - g->hw + g->hy;
     double u = value_of(g, nu);
-    double acc = 0.0;
+    double buf[4096];
+    double* terms = g->n_w <= 4096 ? buf : (double*)malloc(sizeof(double) * (size_t)g->n_w);
     for (int64_t l = 0; l < g->n_w; ++l) {
         int64_t j = jb + l;
         int64_t jl = j < 0 ? 0 : (j > g->n_y - 1 ? g->n_y - 1 : j);
         int64_t jr = j + 1 < 0 ? 0 : (j + 1 > g->n_y - 1 ? g->n_y - 1 : j + 1);
         double uh = U[jl] + t * (U[jr] - U[jl]);
         double e = u - uh;
-        acc = acc + phi[l] * (e * e);
+        terms[l] = phi[l] * (e * e);
     }
+    double acc = fixed_sum(terms, g->n_w);
+    if (terms != buf) free(terms);
     return acc;
 }
 

@@ -25,6 +25,7 @@
 #include <limits.h>
 
 #include "df.cuh"
+#include "fixed_sum.cuh"
 #include "ucp_fast.cuh"
 
 namespace ucp {
@@ -69,46 +70,13 @@ __device__ double exact_cost_lane(const Geom& g, const FastView& f, int64_t i,
     const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
     const int64_t jb = cell - g.hw + g.hy;
     const double u = value_of(g, nu);
-    double acc = 0.0;
-    for (int64_t l = 0; l < g.n_w; ++l)
-        acc = __dadd_rn(acc, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
+    FixedSum acc;
+    for (int64_t l = 0; l < g.n_w; ++l) acc.add(exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
     const double a = __dsub_rn(u, x_of(g, i));
-    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
+    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc.result());
 }
 
-// Serial FP64 costs of up to kTieBatch candidates at once: lane m < M holds
-// candidate m.  For each block of G taps the group forms the terms of every
-// candidate (in `terms`, this group's shared-memory slice of kTieBatch * G
-// doubles); then lane m adds candidate m's terms in tap order.  Each lane's
-// sum is the plain path's serial sum, bit for bit.  Valid in lanes < M.
-constexpr int kTieBatch = 8;
-
-template <int G>
-__device__ double exact_costs_batch(const Geom& g, const FastView& f, int64_t i,
-                                    int lane, int64_t nu, int M, double* terms) {
-    const unsigned gm = group_mask<G>();
-    const int64_t cell = nu >> g.shift;
-    const double t = __dmul_rn((double)(nu - cell * g.one), inv_one(g));
-    const int64_t jb = cell - g.hw + g.hy;
-    const double u = value_of(g, nu);
-    double acc = 0.0;
-    for (int64_t l0 = 0; l0 < g.n_w; l0 += G) {
-        const int cnt = (int)min((int64_t)G, g.n_w - l0);
-        for (int m = 0; m < M; ++m) {
-            const int64_t jbm = __shfl_sync(gm, jb, m, G);
-            const double tm = __shfl_sync(gm, t, m, G);
-            const double um = __shfl_sync(gm, u, m, G);
-            terms[m * G + lane] =
-                lane < cnt ? exact_term(g, f.phi, f.U, f.Ud, jbm, tm, um, l0 + lane) : 0.0;
-        }
-        __syncwarp(gm);
-        if (lane < M)
-            for (int k = 0; k < cnt; ++k) acc = __dadd_rn(acc, terms[lane * G + k]);
-        __syncwarp(gm);
-    }
-    const double a = __dsub_rn(u, x_of(g, i));
-    return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc);
-}
+constexpr int kTieBatch = 8;   // candidates re-costed exactly per pass
 
 // Second screening tier: the direct w quadrature of S from the E table,
 // taps split over the group.  The residual
@@ -119,12 +87,68 @@ __device__ double exact_costs_batch(const Geom& g, const FastView& f, int64_t i,
 // fixed order (every lane gets the same value).  The sum has no cancellation, so its
 // bound is several times tighter than the table identity's.  Candidates
 // outside the tables get an infinite bound (no second tier).
-// Cross-group partial sums of the block-cooperative second tier.
+// Shared state of the block-cooperative tiers: cross-group partial sums of
+// the second tier, the members and results of the exact costs, and the
+// block's scratch (the groups' shared columns, free once screening is done).
 constexpr int kCoopT = 256;   // threads per block of the deferred search
 struct CoopSmem {
     double acc[kCoopT / 2][2];
     float emax[kCoopT / 2][2], demax[kCoopT / 2][2];
+    int64_t mem_nu[32];
+    double res[32];
+    double* scratch;   // kCoopT * kTieBatch doubles
 };
+
+// Exact FP64 costs (the plain path's arithmetic, terms summed in the fixed
+// order of fixed_sum.cuh) of the M <= 32 candidates held in lanes m < M of
+// every group; all groups of the block call this with the same candidates.
+// The block forms the chunk sums of all candidates in parallel, then thread
+// m merges candidate m's chunks in order.  Valid in lanes < M.
+template <int G>
+__device__ double exact_costs_coop(const Geom& g, const FastView& f, int64_t i,
+                                   int lane, int64_t nu, int M, CoopSmem* cs) {
+    __syncthreads();   // every group is done with its scratch column
+    if (threadIdx.x < (unsigned)M) cs->mem_nu[threadIdx.x] = nu;   // group 0's lanes
+    __syncthreads();
+    const int64_t nch = sum_chunks(g.n_w);
+    const int64_t cap = (int64_t)kCoopT * kTieBatch;
+    double* ch = cs->scratch;
+    const int per = (int)max((int64_t)1, min((int64_t)M, cap / nch));
+    for (int m0 = 0; m0 < M; m0 += per) {
+        const int mb = min(per, M - m0);
+        const int64_t span = cap / mb;   // chunks per pass and candidate
+        FixedSum acc;
+        for (int64_t c0 = 0; c0 < nch; c0 += span) {
+            const int64_t cn = min(span, nch - c0);
+            for (int64_t idx = threadIdx.x; idx < mb * cn; idx += blockDim.x) {
+                const int m = (int)(idx / cn);
+                const int64_t k = c0 + idx % cn;
+                const int64_t cnu = cs->mem_nu[m0 + m];
+                const int64_t cell = cnu >> g.shift;
+                const double t = __dmul_rn((double)(cnu - cell * g.one), inv_one(g));
+                const int64_t jb = cell - g.hw + g.hy;
+                const double u = value_of(g, cnu);
+                const int64_t e = min((k + 1) * kSumChunk, g.n_w);
+                double a = 0.0;
+                for (int64_t l = k * kSumChunk; l < e; ++l)
+                    a = __dadd_rn(a, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
+                ch[m * cn + (k - c0)] = a;
+            }
+            __syncthreads();
+            if (threadIdx.x < (unsigned)mb)
+                for (int64_t k = 0; k < cn; ++k) acc.push_chunk(ch[threadIdx.x * cn + k]);
+            __syncthreads();
+        }
+        if (threadIdx.x < (unsigned)mb) {
+            const int64_t cnu = cs->mem_nu[m0 + threadIdx.x];
+            const double a = __dsub_rn(value_of(g, cnu), x_of(g, i));
+            cs->res[m0 + threadIdx.x] =
+                __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc.result());
+        }
+    }
+    __syncthreads();
+    return lane < M ? cs->res[lane] : 0.0;
+}
 
 // With cs == nullptr the group's G lanes take every tap; otherwise the
 // blockDim.x / G groups of the block (all costing the same candidates) split
@@ -368,7 +392,7 @@ template <int G, typename CandFn>
 __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int lane,
                                const Best& best, bool have_best, dfloat hi, int p0,
                                int p_end, CandFn cand, int32_t* n_exact,
-                               double* tie_terms) {
+                               CoopSmem* cs) {
     double xg = DBL_MAX;
     int32_t xp = INT_MAX;
     int64_t xn = 0;
@@ -377,7 +401,7 @@ __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int 
     int32_t mpos = INT_MAX;
     auto flush = [&]() {
         if (M == 0) return;
-        const double v = exact_costs_batch<G>(g, f, i, lane, mnu, M, tie_terms);
+        const double v = exact_costs_coop<G>(g, f, i, lane, mnu, M, cs);
         if (lane < M && before(v, mpos, xg, xp)) { xg = v; xp = mpos; xn = mnu; }
         if (lane == 0 && n_exact) atomicAdd(n_exact, M);
         M = 0;
@@ -422,10 +446,10 @@ __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int 
 constexpr int kKeep = kTieBatch;   // candidates per lane whose screened bounds are kept
 
 // How resolve() settles a stage with several values still in play:
-// kTierInline runs the second and third tiers in the group; kTierDefer gives
-// up (the x0 point is searched again by the deferred kernel); kTierCoop runs
-// them with the whole block, whose groups all search the same x0 point.
-enum TierMode { kTierInline = 0, kTierDefer = 1, kTierCoop = 2 };
+// kTierDefer gives up (the x0 point is searched again by the deferred
+// kernel); kTierCoop runs the second and third tiers with the whole block,
+// whose groups all search the same x0 point.
+enum TierMode { kTierDefer = 1, kTierCoop = 2 };
 constexpr int32_t kDeferPos = -2;   // Best.pos of a deferred search
 
 // A deferred search: the x0 point, the stage whose near-tie stopped it and
@@ -556,7 +580,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
     }
     if (overflow)   // more distinct candidates in play than lanes (rare)
         return resolve_serial<G>(g, f, i, lane, best, have_best, hi, p0, p_end, cand,
-                                 n_exact, tie_terms);
+                                 n_exact, cs);
     // second tier
     double g2 = 0.0, b2 = 0.0;
     if (lane == 0 && n_exact && f.n_tier2) atomicAdd(f.n_tier2, M);
@@ -608,7 +632,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         if (lane == K) { knu = cn; kpos = cp; }
         ++K;
         if (K == kTieBatch || rest == 0) {
-            const double v = exact_costs_batch<G>(g, f, i, lane, knu, K, tie_terms);
+            const double v = exact_costs_coop<G>(g, f, i, lane, knu, K, cs);
             if (lane < K && before(v, kpos, xg, xp)) { xg = v; xp = kpos; xn = knu; }
             if (lane == 0 && n_exact) atomicAdd(n_exact, K);
             K = 0;
@@ -727,6 +751,8 @@ __global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
                                                            int32_t* n_exact) {
     __shared__ double tie_smem[kCoopT * kTieBatch];
     __shared__ CoopSmem cs;
+    if (threadIdx.x == 0) cs.scratch = tie_smem;
+    __syncthreads();
     search_deferred_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, cs,
                             blockIdx.x, gridDim.x);
 }
@@ -950,6 +976,8 @@ __global__ void __launch_bounds__(kCoopT) kb_search_deferred(const InstDev* inst
     const BlockRef r = stage(insts, map, sd);
     __shared__ double tie_smem[kCoopT * kTieBatch];
     __shared__ CoopSmem cs;
+    if (threadIdx.x == 0) cs.scratch = tie_smem;
+    __syncthreads();
     search_deferred_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
                             sd.f.n_exact, tie_smem, cs, r.local, sd.defer_blocks);
 }

@@ -2,15 +2,14 @@
 //
 // Every marginal cost is the direct w quadrature of Section V-A's objective,
 //   g(u; x_i) = k^2 (u - x_i)^2 + sum_l phi_l (u - U^(u + w_l))^2,
-// summed over l in index order with one rounding per operation (no fused
-// multiply-add): the same value, bit for bit, as a straightforward serial
-// FP64 evaluation of the definition.  The fast path uses these kernels'
-// device functions to re-decide near-ties, so both paths make the same
-// decisions.  Parallelism follows Section IV-A: all x_i (and all y_j) are
+// with one rounding per operation (no fused multiply-add) and the terms
+// summed in the fixed order of fixed_sum.cuh: the same value, bit for bit,
+// as any FP64 evaluation of the definition in that order.  Parallelism follows Section IV-A: all x_i (and all y_j) are
 // independent within one controller update.
 #include <float.h>
 #include <limits.h>
 
+#include "fixed_sum.cuh"
 #include "ucp_internal.cuh"
 
 namespace ucp {
@@ -40,27 +39,26 @@ __device__ double S_plain(const Geom& g, const double* __restrict__ phi,
     const int64_t jb = cell - g.hw + g.hy;
     const double u = value_of(g, nu);
     const int64_t ny1 = g.n_y - 1;
-    double acc = 0.0;
+    FixedSum acc;
     int64_t l = 0;
     // left clamp: j = jb + l < 0 -> U^ = U_0
     const double u0 = U[0];
     const double eL = __dsub_rn(u, __dadd_rn(u0, __dmul_rn(t, 0.0)));
     const double eL2 = __dmul_rn(eL, eL);
-    for (; l < g.n_w && jb + l < 0; ++l)
-        acc = __dadd_rn(acc, __dmul_rn(phi[l], eL2));
+    for (; l < g.n_w && jb + l < 0; ++l) acc.add(__dmul_rn(phi[l], eL2));
     // interior: 0 <= j < n_y - 1
     for (; l < g.n_w && jb + l < ny1; ++l) {
         const int64_t j = jb + l;
         const double uh = __dadd_rn(U[j], __dmul_rn(t, Ud[j]));
         const double e = __dsub_rn(u, uh);
-        acc = __dadd_rn(acc, __dmul_rn(phi[l], __dmul_rn(e, e)));
+        acc.add(__dmul_rn(phi[l], __dmul_rn(e, e)));
     }
     // right clamp: j >= n_y - 1 -> U^ = U_{n_y - 1}
     const double uN = U[ny1];
     const double eR = __dsub_rn(u, __dadd_rn(uN, __dmul_rn(t, 0.0)));
     const double eR2 = __dmul_rn(eR, eR);
-    for (; l < g.n_w; ++l) acc = __dadd_rn(acc, __dmul_rn(phi[l], eR2));
-    return acc;
+    for (; l < g.n_w; ++l) acc.add(__dmul_rn(phi[l], eR2));
+    return acc.result();
 }
 
 __device__ __forceinline__ double cost_from_S(const Geom& g, int64_t i,
@@ -90,12 +88,36 @@ __device__ __forceinline__ void group_argmin(double& gv, int32_t& pos,
 // ---- setup ------------------------------------------------------------
 
 // Normalised prior weights p_i and quadrature weights phi_l (one block of
-// 1024 threads).  phi's sum runs serially in index order, as the oracle's
-// does (the serial re-costing of near ties must see the same phi); p_i only
-// weight J, so their sum is a fixed-order tree, which overlaps phi's chain.
+// 1024 threads), each normalising sum in the fixed order of fixed_sum.cuh:
+// the chunk sums in parallel, then thread 0 merges them in order.
+constexpr int kWeightChunks = 1024;   // chunk sums held in shared memory per pass
+
+__device__ double block_fixed_sum(const double* __restrict__ v, int64_t n,
+                                  double* s_chunk) {
+    __shared__ double total;
+    FixedSum acc;   // used by thread 0
+    const int64_t nch = sum_chunks(n);
+    for (int64_t c0 = 0; c0 < nch; c0 += kWeightChunks) {
+        const int64_t cn = min((int64_t)kWeightChunks, nch - c0);
+        for (int64_t k = threadIdx.x; k < cn; k += blockDim.x) {
+            const int64_t b = (c0 + k) * kSumChunk;
+            const int64_t e = min(b + kSumChunk, n);
+            double a = 0.0;
+            for (int64_t j = b; j < e; ++j) a = __dadd_rn(a, v[j]);
+            s_chunk[k] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int64_t k = 0; k < cn; ++k) acc.push_chunk(s_chunk[k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) total = acc.result();
+    __syncthreads();
+    return total;
+}
+
 __global__ void k_weights(Geom g, double* px, double* phi) {
-    __shared__ double red[1024];
-    __shared__ double tot_phi;
+    __shared__ double s_chunk[kWeightChunks];
     const int tid = threadIdx.x;
     for (int64_t i = tid; i < g.n_x; i += blockDim.x) {
         const double xi = x_of(g, i);
@@ -106,22 +128,8 @@ __global__ void k_weights(Geom g, double* px, double* phi) {
         phi[l] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
     }
     __syncthreads();
-    double part = 0.0;
-    if (tid == 0) {
-        double s = 0.0;
-        for (int64_t l = 0; l < g.n_w; ++l) s = __dadd_rn(s, phi[l]);
-        tot_phi = s;
-    } else {
-        for (int64_t i = tid - 1; i < g.n_x; i += blockDim.x - 1)
-            part = __dadd_rn(part, px[i]);
-    }
-    red[tid] = part;
-    __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
-        if (tid < w) red[tid] = __dadd_rn(red[tid], red[tid + w]);
-        __syncthreads();
-    }
-    const double tot_px = red[0];
+    const double tot_px = block_fixed_sum(px, g.n_x, s_chunk);
+    const double tot_phi = block_fixed_sum(phi, g.n_w, s_chunk);
     for (int64_t i = tid; i < g.n_x; i += blockDim.x) px[i] = __ddiv_rn(px[i], tot_px);
     for (int64_t l = tid; l < g.n_w; l += blockDim.x) phi[l] = __ddiv_rn(phi[l], tot_phi);
 }

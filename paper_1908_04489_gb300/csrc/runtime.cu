@@ -9,6 +9,7 @@
 #include "ucp_fast.cuh"
 #include "ucp_runtime.h"
 #include "batch_set.h"
+#include "fixed_sum.cuh"
 
 namespace ucp {
 
@@ -203,9 +204,12 @@ static void fast_bounds(ucp_inst* in, double B) {
     const Geom& g = in->g;
     FastView& f = in->fv;
     const double u = 0x1p-53, uf2 = 0x1p-48;
-    // serial sum of the plain path + double-float 64-tap blocks + FP64
-    // combination + double-float evaluation of the identity
-    const double rel = (double)g.n_w * u + (2.0 * 64 + 16) * uf2 +
+    // the plain path's sum in the fixed order (a term passes through at most
+    // 31 additions in its chunk and one per level), + double-float 64-tap
+    // blocks + FP64 combination + double-float evaluation of the identity
+    const double levels = ceil(log2((double)sum_chunks(g.n_w) + 1.0));
+    const double ser = (kSumChunk - 1 + levels + 1) * u;
+    const double rel = ser + (2.0 * 64 + 16) * uf2 +
                        2.0 * ((double)in->fv.tab_span / 64.0 + 2.0) * uf2 +
                        ((double)in->fv.tab_splits + 8.0) * u + 60.0 * uf2;
     f.beta_rel = (float)(1.25 * rel);
@@ -219,10 +223,10 @@ static void fast_bounds(ucp_inst* in, double B) {
     f.beta_abs = (float)(1.25 * u * A);
     const double X = (double)g.hx * g.delta;
     f.beta_ctl = (float)(4.0 * u * (2.0 * B + X) * g.k);
-    // direct quadrature (second screening tier): the plain path's serial-sum
+    // direct quadrature (second screening tier): the plain path's sum
     // error, the double-float term products (24 uf^2), 8-term double-float
     // blocks (16 uf^2) and the FP64 sum of the blocks
-    f.beta2_rel = (float)(1.25 * (((double)g.n_w + 8.0) * u + 40.0 * uf2 +
+    f.beta2_rel = (float)(1.25 * (ser + 8.0 * u + 40.0 * uf2 +
                                   ((double)g.n_w / 16.0 + 8.0) * u));
     f.w_half = (float)W;
 }
