@@ -88,7 +88,7 @@ FLOPS_SEARCH_CAND = 466.0
 
 # kernels launched per timed group of the library's profiler (the groups not
 # listed launch one kernel)
-KERNELS_PER_GROUP = {"u1_boxes": 2, "tables": 2}
+KERNELS_PER_GROUP = {"u1_boxes": 2}
 
 
 def kernel_work(p, sizes, counters, launches):

@@ -126,7 +126,7 @@ __device__ __forceinline__ bool df_lt(dfloat a, dfloat b) {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 
-// exp(x) for a double-float x in [-87, 0.5]; relative error about 1e-14.
+// exp(x) for a double-float x in [-87, 87]; relative error about 1e-14.
 // Cody-Waite reduction x = n ln2 + r with ln2 split as C1 + C2 + C3 (C1 has
 // 15 significant bits, so n C1 and x_hi - n C1 are exact), r = k/64 + s with
 // |s| <= 1/128, exp(k/64) from the table `t64` (index k + 23, 47 entries), and

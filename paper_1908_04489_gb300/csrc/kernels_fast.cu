@@ -792,6 +792,7 @@ constexpr int kTabB = 64;     // taps per double-float partial sum
 struct TabSmem {
     dfloat sE[kTabT + kTabL], sE2[kTabT + kTabL], sEE[kTabT + kTabL];
     dfloat sa[kTabL], sphi[kTabL];
+    int last;
 };
 
 __device__ __forceinline__ void tables_part_body(const Geom& g, const FastView& f,
@@ -846,32 +847,44 @@ __device__ __forceinline__ void tables_part_body(const Geom& g, const FastView& 
         part[f.n_pos + p] = df_to_double(Q);
         part[2 * f.n_pos + p] = df_to_double(R);
     }
+    // the last of the tap ranges of these positions sums the partials in
+    // range order (FP64) into the double-float tables
+    __threadfence();
+    __syncthreads();
+    if (t == 0) sm.last = atomicAdd(f.tab_done + bx, 1) == f.tab_splits - 1;
+    __syncthreads();
+    if (!sm.last) return;
+    __threadfence();
+    if (p < f.n_pos) {
+        double Pd = 0.0, Qd = 0.0, Rd = 0.0;
+        for (int s0 = 0; s0 < f.tab_splits; s0 += 4) {
+            double v[4][3];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {   // issue the loads, then add in order
+                const int s = s0 + k < f.tab_splits ? s0 + k : s0;
+                const double* part = f.tab_part + (size_t)s * 3 * f.n_pos;
+                v[k][0] = __ldcg(part + p);
+                v[k][1] = __ldcg(part + f.n_pos + p);
+                v[k][2] = __ldcg(part + 2 * f.n_pos + p);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (s0 + k < f.tab_splits) {
+                    Pd += v[k][0];
+                    Qd += v[k][1];
+                    Rd += v[k][2];
+                }
+        }
+        f.P[p] = df_from_double(Pd);
+        f.Q[p] = df_from_double(Qd);
+        f.R[p] = df_from_double(Rd);
+    }
+    if (t == 0) f.tab_done[bx] = 0;
 }
 
 __global__ void __launch_bounds__(kTabT) k_tables_part(Geom g, FastView f) {
     __shared__ TabSmem sm;
     tables_part_body(g, f, sm, blockIdx.x, blockIdx.y);
-}
-
-// Sum the tap-range partials in order (FP64) into the double-float tables.
-__device__ __forceinline__ void tables_combine_body(const Geom& g, const FastView& f,
-                                                    int64_t bx) {
-    const int64_t p = bx * blockDim.x + threadIdx.x;
-    if (p >= f.n_pos) return;
-    double P = 0.0, Q = 0.0, R = 0.0;
-    for (int s = 0; s < f.tab_splits; ++s) {
-        const double* part = f.tab_part + (size_t)s * 3 * f.n_pos;
-        P += part[p];
-        Q += part[f.n_pos + p];
-        R += part[2 * f.n_pos + p];
-    }
-    f.P[p] = df_from_double(P);
-    f.Q[p] = df_from_double(Q);
-    f.R[p] = df_from_double(R);
-}
-
-__global__ void k_tables_combine(Geom g, FastView f) {
-    tables_combine_body(g, f, blockIdx.x);
 }
 
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
@@ -910,10 +923,14 @@ __global__ void k_fast_setup(Geom g, FastView f) {
 // ---- J --------------------------------------------------------------------
 
 constexpr int kJThreads = 256;
-__device__ __forceinline__ void J_partial_body(const Geom& g, const FastView& f,
+// J = sum_i p_i g(f_i; x_i): block partials (fixed tree), then the last
+// block to finish adds the partials in block order.  Returns true in thread
+// 0 of that block, with J in *J_out (the counter is left at zero).
+__device__ __forceinline__ bool J_partial_body(const Geom& g, const FastView& f,
                                                const double* __restrict__ px,
                                                const int64_t* __restrict__ nu,
-                                               double* red, int64_t bx) {
+                                               double* red, int* last, int64_t bx,
+                                               double* J_out) {
     const int64_t i = bx * kJThreads + threadIdx.x;
     double v = 0.0;
     if (i < g.n_x) v = px[i] * df_to_double(eval_table(g, f, i, nu[i]).gv);
@@ -923,24 +940,41 @@ __device__ __forceinline__ void J_partial_body(const Geom& g, const FastView& f,
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) f.Jpart[bx] = red[0];
+    if (threadIdx.x == 0) {
+        f.Jpart[bx] = red[0];
+        __threadfence();
+        *last = atomicAdd(f.J_done, 1) == (int)(f.J_blocks - 1);
+    }
+    __syncthreads();
+    if (!*last || threadIdx.x != 0) return false;
+    __threadfence();
+    double sum = 0.0;
+    for (int64_t b0 = 0; b0 < f.J_blocks; b0 += 8) {
+        double v8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)   // issue the loads, then add in order
+            v8[k] = b0 + k < f.J_blocks ? __ldcg(f.Jpart + b0 + k) : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (b0 + k < f.J_blocks) sum += v8[k];
+    }
+    *J_out = sum;
+    *f.J_done = 0;
+    return true;
 }
 
+// J into *out; also empties the deferred-search list for the next sweep.
 __global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
                                                          const double* __restrict__ px,
-                                                         const int64_t* __restrict__ nu) {
+                                                         const int64_t* __restrict__ nu,
+                                                         double* out) {
     __shared__ double red[kJThreads];
-    J_partial_body(g, f, px, nu, red, blockIdx.x);
-}
-
-// J from the block partials (in order); also empties the deferred-search list
-// for the next sweep.
-__global__ void k_J_final(FastView f, int nblk, double* out) {
-    if (threadIdx.x != 0) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += f.Jpart[b];
-    *out = s;
-    *f.defer_cnt = 0;
+    __shared__ int last;
+    double J;
+    if (J_partial_body(g, f, px, nu, red, &last, blockIdx.x, &J)) {
+        *out = J;
+        *f.defer_cnt = 0;
+    }
 }
 
 
@@ -997,32 +1031,23 @@ __global__ void __launch_bounds__(kTabT) kb_tables_part(const InstDev* insts,
     tables_part_body(sd.g, sd.f, sm, r.local % pb, r.local / pb);
 }
 
-__global__ void kb_tables_combine(const InstDev* insts, const BlockRef* map) {
-    __shared__ InstDev sd;
-    const BlockRef r = stage(insts, map, sd);
-    tables_combine_body(sd.g, sd.f, r.local);
-}
 
-__global__ void __launch_bounds__(kJThreads) kb_J_partial(const InstDev* insts,
+// Last kernel of a batched sweep: J into its history slot, then the sweep
+// counter and the double buffer advance (by the instance's last J block).
+__global__ void __launch_bounds__(kJThreads) kb_J_partial(InstDev* insts,
                                                           const BlockRef* map) {
     __shared__ InstDev sd;
     __shared__ double red[kJThreads];
+    __shared__ int last;
     const BlockRef r = stage(insts, map, sd);
-    J_partial_body(sd.g, sd.f, sd.px, sd.nu[sd.cur ^ 1], red, r.local);
-}
-
-// Last kernel of a batched sweep: J into its history slot, then the sweep
-// counter and the double buffer advance (one thread per instance).
-__global__ void kb_J_final(InstDev* insts, int n) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    InstDev& d = insts[b];
-    double s = 0.0;
-    for (int64_t k = 0; k < d.f.J_blocks; ++k) s += d.f.Jpart[k];
-    d.J[d.sweeps + 1] = s;
-    d.sweeps += 1;
-    d.cur ^= 1;
-    *d.f.defer_cnt = 0;
+    double J;
+    if (J_partial_body(sd.g, sd.f, sd.px, sd.nu[sd.cur ^ 1], red, &last, r.local, &J)) {
+        InstDev& d = insts[r.inst];
+        d.J[d.sweeps + 1] = J;
+        d.sweeps += 1;
+        d.cur ^= 1;
+        *d.f.defer_cnt = 0;
+    }
 }
 
 inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -1052,6 +1077,7 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     span = (span + kTabB - 1) / kTabB * kTabB;
     fp->tab_span = span;
     fp->tab_splits = (int)((g.n_w + span - 1) / span);
+    fp->tab_pblocks = pblocks;
 }
 
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
@@ -1070,7 +1096,6 @@ void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud
     k = prof ? prof->begin("tables", &ev) : -1;
     dim3 grid(blocks(f.n_pos, kTabT), (unsigned)f.tab_splits);
     k_tables_part<<<grid, kTabT, 0, s>>>(g, f);
-    k_tables_combine<<<blocks(f.n_pos, 256), 256, 0, s>>>(g, f);
     if (prof) prof->end(k, ev);
 }
 
@@ -1117,7 +1142,6 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
         case kBRun: return u1_batch_blocks(g, fp, kind);
         case kBPerY: return (g.n_y + 255) / 256;
         case kBTabPart: return (fp.n_pos + kTabT - 1) / kTabT * fp.tab_splits;
-        case kBTabComb: return (fp.n_pos + 255) / 256;
         case kBBuildE: {
             const int64_t n = fp.n_e > g.n_y ? fp.n_e : g.n_y;
             return (n + 255) / 256;
@@ -1165,19 +1189,15 @@ void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s) {
     launch_batch_u1(bl, s);
     kb_build_E<<<(unsigned)bl.n_blocks[kBBuildE], 256, 0, s>>>(d, bl.map[kBBuildE]);
     kb_tables_part<<<(unsigned)bl.n_blocks[kBTabPart], kTabT, 0, s>>>(d, bl.map[kBTabPart]);
-    kb_tables_combine<<<(unsigned)bl.n_blocks[kBTabComb], 256, 0, s>>>(d, bl.map[kBTabComb]);
-    kb_J_partial<<<(unsigned)bl.n_blocks[kBJPart], kJThreads, 0, s>>>(d, bl.map[kBJPart]);
-    kb_J_final<<<blocks(bl.n_inst, 128), 128, 0, s>>>(bl.insts, bl.n_inst);
+    kb_J_partial<<<(unsigned)bl.n_blocks[kBJPart], kJThreads, 0, s>>>(bl.insts,
+                                                                   bl.map[kBJPart]);
 }
 
 void launch_J_fast(const Geom& g, const FastView& f, const double* px,
                    const int64_t* nu, double* out, cudaStream_t s, Prof* prof) {
     cudaEvent_t ev;
-    int k = prof ? prof->begin("J_partial", &ev) : -1;
-    k_J_partial<<<(unsigned)f.J_blocks, kJThreads, 0, s>>>(g, f, px, nu);
-    if (prof) prof->end(k, ev);
-    k = prof ? prof->begin("J_final", &ev) : -1;
-    k_J_final<<<1, 32, 0, s>>>(f, (int)f.J_blocks, out);
+    int k = prof ? prof->begin("J", &ev) : -1;
+    k_J_partial<<<(unsigned)f.J_blocks, kJThreads, 0, s>>>(g, f, px, nu, out);
     if (prof) prof->end(k, ev);
 }
 

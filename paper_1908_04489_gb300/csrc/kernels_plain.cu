@@ -87,10 +87,23 @@ __device__ __forceinline__ void group_argmin(double& gv, int32_t& pos,
 
 // ---- setup ------------------------------------------------------------
 
-// Normalised prior weights p_i and quadrature weights phi_l (one block of
-// 1024 threads), each normalising sum in the fixed order of fixed_sum.cuh:
-// the chunk sums in parallel, then thread 0 merges them in order.
+// Normalised prior weights p_i and quadrature weights phi_l: the
+// exponentials over the grid, the two normalising sums in the fixed order of
+// fixed_sum.cuh (one block: chunk sums in parallel, thread 0 merges them in
+// order), then the divisions over the grid.
 constexpr int kWeightChunks = 1024;   // chunk sums held in shared memory per pass
+
+__global__ void k_weights_exp(Geom g, double* px, double* phi) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < g.n_x) {
+        const double xi = x_of(g, k);
+        px[k] = exp(-__ddiv_rn(__dmul_rn(xi, xi), g.two_s2));
+    }
+    if (k < g.n_w) {
+        const double wl = __dmul_rn((double)(k - g.hw), g.delta);
+        phi[k] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
+    }
+}
 
 __device__ double block_fixed_sum(const double* __restrict__ v, int64_t n,
                                   double* s_chunk) {
@@ -116,22 +129,22 @@ __device__ double block_fixed_sum(const double* __restrict__ v, int64_t n,
     return total;
 }
 
-__global__ void k_weights(Geom g, double* px, double* phi) {
+__global__ void k_weights_sum(Geom g, const double* px, const double* phi,
+                              double* tot) {
     __shared__ double s_chunk[kWeightChunks];
-    const int tid = threadIdx.x;
-    for (int64_t i = tid; i < g.n_x; i += blockDim.x) {
-        const double xi = x_of(g, i);
-        px[i] = exp(-__ddiv_rn(__dmul_rn(xi, xi), g.two_s2));
+    const double a = block_fixed_sum(px, g.n_x, s_chunk);
+    const double b = block_fixed_sum(phi, g.n_w, s_chunk);
+    if (threadIdx.x == 0) {
+        tot[0] = a;
+        tot[1] = b;
     }
-    for (int64_t l = tid; l < g.n_w; l += blockDim.x) {
-        const double wl = __dmul_rn((double)(l - g.hw), g.delta);
-        phi[l] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
-    }
-    __syncthreads();
-    const double tot_px = block_fixed_sum(px, g.n_x, s_chunk);
-    const double tot_phi = block_fixed_sum(phi, g.n_w, s_chunk);
-    for (int64_t i = tid; i < g.n_x; i += blockDim.x) px[i] = __ddiv_rn(px[i], tot_px);
-    for (int64_t l = tid; l < g.n_w; l += blockDim.x) phi[l] = __ddiv_rn(phi[l], tot_phi);
+}
+
+__global__ void k_weights_scale(Geom g, double* px, double* phi,
+                                const double* __restrict__ tot) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < g.n_x) px[k] = __ddiv_rn(px[k], tot[0]);
+    if (k < g.n_w) phi[k] = __ddiv_rn(phi[k], tot[1]);
 }
 
 // kind 0: identity f(x) = x; kind 1: odd staircase with step n7 (units of
@@ -313,7 +326,11 @@ inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs)
 // ---- launch wrappers ----------------------------------------------------
 
 void launch_weights(const Geom& g, DevState& d, cudaStream_t s) {
-    k_weights<<<1, 1024, 0, s>>>(g, d.px, d.phi);
+    const int64_t n = g.n_x > g.n_w ? g.n_x : g.n_w;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    k_weights_exp<<<nb, 256, 0, s>>>(g, d.px, d.phi);
+    k_weights_sum<<<1, 1024, 0, s>>>(g, d.px, d.phi, d.scratch);
+    k_weights_scale<<<nb, 256, 0, s>>>(g, d.px, d.phi, d.scratch);
 }
 
 void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s) {

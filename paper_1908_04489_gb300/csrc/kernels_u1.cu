@@ -60,8 +60,8 @@ __device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
 
 // ---- sources and boxes ----------------------------------------------------------
 
-// One block per tile.  Every thread: per source f_i (double-float) and
-// exp(delta f_i).  Then warp 0: greedy grouping of consecutive sources into
+// One block per tile.  Every thread: per source f_i and exp(delta f_i)
+// (double-float).  Then warp 0: greedy grouping of consecutive sources into
 // boxes whose f values (leading floats) span at most 2 kHMax; the last box of
 // a tile takes whatever is left once kBoxMax - 1 boxes are closed.
 __device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
@@ -69,11 +69,13 @@ __device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
                                               int64_t t) {
     const int64_t t0 = t * f.tile;
     const int64_t t1 = min(t0 + f.tile, g.n_x);
+    const dfloat dl = {f.delta_hi, f.delta_lo};
     for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
-        const double v = value_of(g, nu[i]);
+        const dfloat fv = df_from_double(value_of(g, nu[i]));
         f.src_nu[i] = nu[i];
-        f.src_f[i] = df_from_double(v);
-        f.src_F[i] = df_from_double(exp(g.delta * v));
+        f.src_f[i] = fv;
+        // exp(delta f_i) in double-float (|delta f_i| stays below ~0.8)
+        f.src_F[i] = df_exp(df_mul(fv, dl), f.t64);
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;

@@ -186,6 +186,7 @@ size_t inst_bytes(const Geom& g, int precision) {
              3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
              rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 3 * rnd(4) + rnd(kDeferRecBytes * nx) + rnd(32) +
              rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
+             rnd(4 * (size_t)fp.tab_pblocks) + rnd(4) +
              u1_scratch_bytes(g, fp, 256);
     }
     return b;
@@ -255,6 +256,8 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.t64 = (dfloat*)A.get(8 * 47);
     f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
     f.tab_part = (double*)A.get(24 * (size_t)f.tab_splits * (size_t)f.n_pos);
+    f.tab_done = (int32_t*)A.get(4 * (size_t)f.tab_pblocks);
+    f.J_done = (int32_t*)A.get(4);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
     f.n_tier2 = (int32_t*)A.get(4);
@@ -264,7 +267,8 @@ static ucp_status fast_alloc(ucp_inst* in) {
     const bool u1_ok = u1_carve(
         g, &f, [](void* a, size_t n) { return ((Arena*)a)->get(n); }, &A);
     if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf || !f.wdf ||
-        !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tab_part || !f.W2_dev ||
+        !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tab_part || !f.tab_done ||
+        !f.J_done || !f.W2_dev ||
         !f.n_exact || !f.n_tier2 || !f.defer_cnt || !f.defer_list || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
@@ -346,6 +350,8 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
         cudaMemsetAsync(in->fv.n_tier2, 0, 4, s);
         cudaMemsetAsync(in->fv.defer_cnt, 0, 4, s);
+        cudaMemsetAsync(in->fv.J_done, 0, 4, s);
+        cudaMemsetAsync(in->fv.tab_done, 0, 4 * (size_t)in->fv.tab_pblocks, s);
         cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");

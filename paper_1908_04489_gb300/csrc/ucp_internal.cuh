@@ -64,6 +64,7 @@ struct FastPlan {
     int64_t J_blocks;  // blocks of the J reduction
     int64_t tab_span;  // taps per block column of the table kernel
     int tab_splits;    // block columns of the table kernel
+    int64_t tab_pblocks;  // block rows (position blocks) of the table kernel
 };
 
 struct dfloat;  // df.cuh
@@ -105,6 +106,8 @@ struct FastView : FastPlan {
     double* partD;       // [n_tiles * n_y] denominator partials
     double* Jpart;       // [J_blocks]
     double* tab_part;    // [tab_splits * 3 * n_pos] table partial sums
+    int32_t* tab_done;   // [position blocks] tap ranges finished (reset by the last)
+    int32_t* J_done;     // J blocks finished (reset by the last)
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
     int32_t* n_tier2;    // count of direct double-float quadratures (second tier)
@@ -150,8 +153,7 @@ struct BlockRef {
 };
 
 enum BatchKind {
-    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBTabComb, kBBuildE, kBJPart, kBBox,
-    kBRun, kBKinds
+    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBBuildE, kBJPart, kBBox, kBRun, kBKinds
 };
 
 // Device arrays describing one batched sweep.
