@@ -75,8 +75,8 @@ def init_table(p):
 #              Taylor-expanded (box, run): the anchor (130) and per target the
 #              shift of z (11), the recurrence product (10) and two scaled
 #              accumulates (42); per Taylor term 21 in double-float, 2 in FP32.
-#   search:    per (x_i, candidate): two screened evaluations of the
-#              three-correlation identity, 233 each.
+#   search:    per (x_i, candidate): one screened evaluation of the
+#              three-correlation identity, 233.
 # The plain FP64 path counts FP64 flops: 6 per quadrature term.
 FLOPS_TABLE_TAP = 54.0
 FLOPS_U1_PAIR = 39.0
@@ -84,7 +84,7 @@ FLOPS_U1_ANCHOR = 130.0
 FLOPS_U1_BOX_TARGET = 63.0
 FLOPS_U1_TERM_DF = 21.0
 FLOPS_U1_TERM_F32 = 2.0
-FLOPS_SEARCH_CAND = 466.0
+FLOPS_SEARCH_CAND = 233.0
 
 # kernels launched per timed group of the library's profiler (the groups not
 # listed launch one kernel)
@@ -535,10 +535,14 @@ def run_profile(args):
     from paper_1908_04489_gb300 import binding, build
     build.build()
     p, _ = workload(args.workload, args.precision)
-    with binding.Instance(p) as inst:
+    # on a non-default stream the sweeps replay captured graphs (the bench's
+    # timed path); on the default stream they launch kernel by kernel
+    stream = torch.cuda.Stream() if args.profile_graph else None
+    with binding.Instance(p, stream=stream) as inst:
         inst.sweep(args.profile_sweeps)
         print(json.dumps({"workload": args.workload, "J": inst.eval_J(),
-                          "sweeps": args.profile_sweeps}))
+                          "sweeps": args.profile_sweeps,
+                          "graph": bool(args.profile_graph)}))
     torch.cuda.synchronize()
 
 
@@ -590,6 +594,9 @@ def main():
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="only build one instance and run this many sweeps "
                          "(a short, fixed launch sequence for ncu)")
+    ap.add_argument("--profile-graph", action="store_true",
+                    help="with --profile-sweeps: run on a non-default stream "
+                         "(captured-graph sweeps, as in the timed steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
