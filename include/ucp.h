@@ -161,6 +161,23 @@ UCP_API ucp_status ucp_destroy(ucp_inst* inst);
  * creation; 0 on the plain path).  Synchronises. */
 UCP_API ucp_status ucp_tie_recosts(ucp_inst* inst, int64_t* out);
 
+/* The fast path's correlation tables of the current u1 table, for tests and
+ * diagnostics (Section V-A's w quadrature rewritten as three correlations of
+ * E = U^(y) - y against the Gaussian weights: P_p = sum_l phi_l w_l E_{p+l},
+ * Q_p = sum_l phi_l E_{p+l}^2, R_p = sum_l phi_l E_{p+l} E_{p+l+1}; E-index m
+ * is y-index jlo + m, table position p covers candidate lattice cell
+ * c_lo + p).  sizes (4 entries, required) receives n_pos, n_cols, c_lo and
+ * jlo.  P, Q, R (host, n_pos entries each, may be NULL together) receive the
+ * double-float table values as doubles; bound (host, n_cols entries, may be
+ * NULL) the device's per-column bound on the error of S(u) = W2 +
+ * 2[(1-t)P_p + t P_{p+1}] + (1-t)^2 Q_p + 2t(1-t) R_p + t^2 Q_{p+1} that the
+ * tables cause at cells whose positions p, p + 1 lie in column p / 128.
+ * UCP_E_ARG if a buffer is shorter than the instance's size, UCP_E_STATE on
+ * the plain path.  Synchronises. */
+UCP_API ucp_status ucp_get_tables(ucp_inst* inst, double* P, double* Q, double* R,
+                                  int64_t n_pos, float* bound, int64_t n_cols,
+                                  int64_t* sizes);
+
 /* Work counters since creation (fast path; zeros on the plain path), the
  * first n of, in order:
  *   0 recosts     as ucp_tie_recosts;

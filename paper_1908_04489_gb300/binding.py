@@ -117,6 +117,9 @@ def load():
                                    ctypes.c_int32]
     L.ucp_kernel_times.restype = ctypes.c_int32
     L.ucp_tie_recosts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.ucp_get_tables.argtypes = [_vp, _dp, _dp, _dp, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_int64)]
     L.ucp_probe_alu.argtypes = [_dp, _dp, _dp, _vp]
     L.ucp_work_counters.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.c_int32]
@@ -293,6 +296,22 @@ class Instance:
         _check(load().ucp_work_counters(self.h, out, len(self.COUNTERS)),
                "ucp_work_counters")
         return dict(zip(self.COUNTERS, (int(v) for v in out)))
+
+    def get_tables(self) -> dict:
+        """Correlation tables P, Q, R of the current u1 table, the per-column
+        error bound of the table identity, and the index offsets (c_lo: lattice
+        cell of position 0; jlo: y-index of E-index 0)."""
+        L = load()
+        sz = (ctypes.c_int64 * 4)()
+        _check(L.ucp_get_tables(self.h, None, None, None, 0, None, 0, sz), "ucp_get_tables")
+        n_pos, n_cols = int(sz[0]), int(sz[1])
+        P, Q, R = (np.empty(n_pos) for _ in range(3))
+        bt = np.empty(n_cols, dtype=np.float32)
+        _check(L.ucp_get_tables(self.h, _ptr(P, ctypes.c_double), _ptr(Q, ctypes.c_double),
+                                _ptr(R, ctypes.c_double), n_pos,
+                                bt.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                n_cols, sz), "ucp_get_tables")
+        return {"P": P, "Q": Q, "R": R, "bound": bt, "c_lo": int(sz[2]), "jlo": int(sz[3])}
 
     def tie_recosts(self) -> int:
         v = ctypes.c_int64()

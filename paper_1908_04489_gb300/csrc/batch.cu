@@ -21,7 +21,7 @@ struct ucp_batch {
     std::vector<ucp_inst*> members;
     Arena arena;
     BatchSet bs;
-    double* J_gather = nullptr;   // [n] device
+    double* J_gather = nullptr;   // [2 n] device: J, then the tensor-core error flags
     bool poisoned = false;
     cudaGraphExec_t graph = nullptr;
     bool graph_tried = false;
@@ -161,7 +161,10 @@ ucp_status fail(ucp_batch* b, const char* where) {
 
 __global__ void k_gather_J(const InstDev* insts, int n, double* out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < n) out[b] = insts[b].J[insts[b].sweeps];
+    if (b < n) {
+        out[b] = insts[b].J[insts[b].sweeps];
+        out[n + b] = (double)*insts[b].f.tc_err;
+    }
 }
 
 }  // namespace
@@ -201,7 +204,7 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
         b->members.push_back(in);
     }
     b->bs.arena = &b->arena;
-    b->J_gather = (double*)b->arena.get(sizeof(double) * (size_t)n);
+    b->J_gather = (double*)b->arena.get(2 * sizeof(double) * (size_t)n);
     ucp_status st = b->J_gather ? batchset_build(b->bs, b->members, b->stream) : UCP_E_NOMEM;
     if (st == UCP_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = UCP_E_CUDA;
     if (st != UCP_OK) {
@@ -260,10 +263,19 @@ extern "C" UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out) {
     if (batchset_refresh(b->bs, b->members, b->stream) != UCP_OK)
         return fail(b, "ucp_batch_eval_J");
     k_gather_J<<<(n + 127) / 128, 128, 0, b->stream>>>(b->bs.insts, n, b->J_gather);
+    std::vector<double> flags((size_t)n);
     cudaMemcpyAsync(J_out, b->J_gather, sizeof(double) * (size_t)n,
+                    cudaMemcpyDeviceToHost, b->stream);
+    cudaMemcpyAsync(flags.data(), b->J_gather + n, sizeof(double) * (size_t)n,
                     cudaMemcpyDeviceToHost, b->stream);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return fail(b, "ucp_batch_eval_J");
+    for (double e : flags)
+        if (e != 0.0) {
+            b->poisoned = true;
+            set_error("%s%s", "ucp_batch_eval_J: a tensor-core wait timed out", "");
+            return UCP_E_TIMEOUT;
+        }
     return UCP_OK;
 }
 

@@ -8,7 +8,8 @@
 //   S = W2 + 2[(1-t) P_p + t P_{p+1}] + (1-t)^2 Q_p + 2t(1-t) R_p + t^2 Q_{p+1},
 //   W2 = sum phi_l w_l^2,  P_p = sum phi_l w_l E_{p+l},
 //   Q_p = sum phi_l E_{p+l}^2,  R_p = sum phi_l E_{p+l} E_{p+l+1}.
-// One table build per u1 update makes every candidate O(1).  A table cost
+// One table build per u1 update (on the tensor cores, kernels_tc.cu) makes
+// every candidate O(1).  A table cost
 // differs from the serial FP64 quadrature only by rounding; a rigorous bound
 // on that difference screens each stage of the candidate list (Corollary 1's
 // pointwise argmin over eq. (2)'s neighbours, the coarse set and the
@@ -19,8 +20,8 @@
 //
 // The u1 step (U_j = E[x1 | y1 = y_j]) is in kernels_u1.cu.
 //
-// Arithmetic: the bulk runs in double-float on the FP32 pipe (df.cuh); FP64
-// only combines partial sums and re-costs near-ties.
+// Arithmetic: the screening runs in double-float on the FP32 pipe (df.cuh);
+// FP64 only combines partial sums and re-costs near-ties.
 #include <float.h>
 #include <limits.h>
 
@@ -293,7 +294,10 @@ __device__ __forceinline__ Eval eval_table(const Geom& g, const FastView& f,
     const float rm = f.sqrtW2 + omt.hi * sqrtf(fmaxf(Q0.hi, 0.f)) +
                      t.hi * sqrtf(fmaxf(Q1.hi, 0.f));
     const float M = rm * rm * 1.0001f;
-    const float beta = f.beta_rel * M + f.beta_abs * (2.0f * rm + 1.0f) +
+    // table error: the column bound, or both columns' at a column boundary
+    const int64_t a1 = p >> 7, a2 = (p + 1) >> 7;
+    const float bt = f.tc_bt[a1] + (a2 != a1 ? f.tc_bt[a2] : 0.f);
+    const float beta = bt + f.beta_rel * M + f.beta_abs * (2.0f * rm + 1.0f) +
                        3.0e-13f * fabsf(ctl.hi) + f.beta_ctl * sqrtf(fabsf(ctl.hi)) +
                        4.0e-16f * fabsf(gv.hi);
     return {gv, beta};
@@ -757,136 +761,6 @@ __global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
                             blockIdx.x, gridDim.x);
 }
 
-// ---- correlation tables ---------------------------------------------------
-
-// E_m = U^(y_m) - y_m for table E-index m (y-index jlo + m, U held constant
-// beyond the table), E_m^2 and E_m E_{m+1}, in double-float; Ud for the
-// serial costs.
-__device__ __forceinline__ void build_E_body(const Geom& g, const FastView& f,
-                                             const double* __restrict__ U,
-                                             double* __restrict__ Ud, int64_t bx) {
-    const int64_t m = bx * blockDim.x + threadIdx.x;
-    if (m < g.n_y) Ud[m] = m + 1 < g.n_y ? __dsub_rn(U[m + 1], U[m]) : 0.0;
-    if (m >= f.n_e) return;
-    const int64_t jj = f.jlo + m;
-    const int64_t a = jj < 0 ? 0 : (jj > g.n_y - 1 ? g.n_y - 1 : jj);
-    const int64_t b = jj + 1 < 0 ? 0 : (jj + 1 > g.n_y - 1 ? g.n_y - 1 : jj + 1);
-    const double e0 = U[a] - (double)(jj - g.hy) * g.delta;
-    const double e1 = U[b] - (double)(jj + 1 - g.hy) * g.delta;
-    f.E[m] = df_from_double(e0);
-    f.E2[m] = df_from_double(e0 * e0);
-    f.EE[m] = df_from_double(e0 * e1);
-}
-
-__global__ void k_build_E(Geom g, FastView f, const double* __restrict__ U,
-                          double* __restrict__ Ud) {
-    build_E_body(g, f, U, Ud, blockIdx.x);
-}
-
-constexpr int kTabT = 128;    // positions per block
-constexpr int kTabL = 512;    // taps per shared-memory chunk
-constexpr int kTabB = 64;     // taps per double-float partial sum
-
-// Partial correlations over the tap range of blockIdx.y (f.tab_span taps):
-// 64-tap double-float blocks accumulated into a double-float total.
-struct TabSmem {
-    dfloat sE[kTabT + kTabL], sE2[kTabT + kTabL], sEE[kTabT + kTabL];
-    dfloat sa[kTabL], sphi[kTabL];
-    int last;
-};
-
-__device__ __forceinline__ void tables_part_body(const Geom& g, const FastView& f,
-                                                 TabSmem& sm, int64_t bx, int64_t by) {
-    dfloat* sE = sm.sE;
-    dfloat* sE2 = sm.sE2;
-    dfloat* sEE = sm.sEE;
-    dfloat* sa = sm.sa;
-    dfloat* sphi = sm.sphi;
-    const int64_t p0 = bx * kTabT;
-    const int t = threadIdx.x;
-    const int64_t lb = by * f.tab_span;
-    const int64_t le = min(lb + f.tab_span, g.n_w);
-    dfloat P{0.f, 0.f}, Q{0.f, 0.f}, R{0.f, 0.f};
-    for (int64_t l0 = lb; l0 < le; l0 += kTabL) {
-        const int cl = (int)min((int64_t)kTabL, le - l0);
-        __syncthreads();
-        for (int k = t; k < kTabT + cl; k += kTabT) {
-            const int64_t m = p0 + l0 + k;
-            const bool ok = m < f.n_e;
-            sE[k] = ok ? f.E[m] : dfloat{0.f, 0.f};
-            sE2[k] = ok ? f.E2[m] : dfloat{0.f, 0.f};
-            sEE[k] = ok ? f.EE[m] : dfloat{0.f, 0.f};
-        }
-        for (int k = t; k < cl; k += kTabT) {
-            sa[k] = f.a[l0 + k];
-            sphi[k] = f.phidf[l0 + k];
-        }
-        __syncthreads();
-        for (int b0 = 0; b0 < cl; b0 += kTabB) {
-            const int b1 = min(cl, b0 + kTabB);
-            dfloat aP{0.f, 0.f}, aQ{0.f, 0.f}, aR{0.f, 0.f};
-#pragma unroll 4
-            for (int l = b0; l < b1; ++l) {
-                float pp, pe;
-                df_mul_raw(sa[l], sE[t + l], pp, pe);
-                aP = df_acc(aP, pp, pe);
-                df_mul_raw(sphi[l], sE2[t + l], pp, pe);
-                aQ = df_acc(aQ, pp, pe);
-                df_mul_raw(sphi[l], sEE[t + l], pp, pe);
-                aR = df_acc(aR, pp, pe);
-            }
-            P = df_add(P, aP);
-            Q = df_add(Q, aQ);
-            R = df_add(R, aR);
-        }
-    }
-    const int64_t p = p0 + t;
-    if (p < f.n_pos) {
-        double* part = f.tab_part + (size_t)by * 3 * f.n_pos;
-        part[p] = df_to_double(P);
-        part[f.n_pos + p] = df_to_double(Q);
-        part[2 * f.n_pos + p] = df_to_double(R);
-    }
-    // the last of the tap ranges of these positions sums the partials in
-    // range order (FP64) into the double-float tables
-    __threadfence();
-    __syncthreads();
-    if (t == 0) sm.last = atomicAdd(f.tab_done + bx, 1) == f.tab_splits - 1;
-    __syncthreads();
-    if (!sm.last) return;
-    __threadfence();
-    if (p < f.n_pos) {
-        double Pd = 0.0, Qd = 0.0, Rd = 0.0;
-        for (int s0 = 0; s0 < f.tab_splits; s0 += 4) {
-            double v[4][3];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {   // issue the loads, then add in order
-                const int s = s0 + k < f.tab_splits ? s0 + k : s0;
-                const double* part = f.tab_part + (size_t)s * 3 * f.n_pos;
-                v[k][0] = __ldcg(part + p);
-                v[k][1] = __ldcg(part + f.n_pos + p);
-                v[k][2] = __ldcg(part + 2 * f.n_pos + p);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (s0 + k < f.tab_splits) {
-                    Pd += v[k][0];
-                    Qd += v[k][1];
-                    Rd += v[k][2];
-                }
-        }
-        f.P[p] = df_from_double(Pd);
-        f.Q[p] = df_from_double(Qd);
-        f.R[p] = df_from_double(Rd);
-    }
-    if (t == 0) f.tab_done[bx] = 0;
-}
-
-__global__ void __launch_bounds__(kTabT) k_tables_part(Geom g, FastView f) {
-    __shared__ TabSmem sm;
-    tables_part_body(g, f, sm, blockIdx.x, blockIdx.y);
-}
-
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
 // prior exponent x_i^2 / 2 sigma^2, W2 = sum phi_l w_l^2 (fixed-order tree),
 // and the exp(k/64) table of df_exp.
@@ -1016,22 +890,6 @@ __global__ void __launch_bounds__(kCoopT) kb_search_deferred(const InstDev* inst
                             sd.f.n_exact, tie_smem, cs, r.local, sd.defer_blocks);
 }
 
-__global__ void kb_build_E(const InstDev* insts, const BlockRef* map) {
-    __shared__ InstDev sd;
-    const BlockRef r = stage(insts, map, sd);
-    build_E_body(sd.g, sd.f, sd.U, sd.Ud, r.local);
-}
-
-__global__ void __launch_bounds__(kTabT) kb_tables_part(const InstDev* insts,
-                                                        const BlockRef* map) {
-    __shared__ InstDev sd;
-    __shared__ TabSmem sm;
-    const BlockRef r = stage(insts, map, sd);
-    const int64_t pb = (sd.f.n_pos + kTabT - 1) / kTabT;
-    tables_part_body(sd.g, sd.f, sm, r.local % pb, r.local / pb);
-}
-
-
 // Last kernel of a batched sweep: J into its history slot, then the sweep
 // counter and the double buffer advance (by the instance's last J block).
 __global__ void __launch_bounds__(kJThreads) kb_J_partial(InstDev* insts,
@@ -1067,36 +925,13 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     fp->n_e = fp->n_pos + g.n_w + 1;
     u1_plan(g, 32, fp);
     fp->J_blocks = (g.n_x + kJThreads - 1) / kJThreads;
-    // split the taps so that the table kernel fills the GPU (~4 blocks/SM)
-    const int64_t pblocks = (fp->n_pos + kTabT - 1) / kTabT;
-    int64_t splits = (4 * 152 + pblocks - 1) / pblocks;
-    const int64_t max_splits = (g.n_w + kTabB - 1) / kTabB;
-    if (splits > max_splits) splits = max_splits;
-    if (splits < 1) splits = 1;
-    int64_t span = (g.n_w + splits - 1) / splits;
-    span = (span + kTabB - 1) / kTabB * kTabB;
-    fp->tab_span = span;
-    fp->tab_splits = (int)((g.n_w + span - 1) / span);
-    fp->tab_pblocks = pblocks;
+    tc_plan(g, fp);
 }
 
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
     int64_t n = g.n_w > g.n_x ? g.n_w : g.n_x;
     n = n > 47 ? n : 47;
     k_fast_setup<<<blocks(n, 256), 256, 0, s>>>(g, f);
-}
-
-void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
-                   cudaStream_t s, Prof* prof) {
-    cudaEvent_t ev;
-    const int64_t n = f.n_e > g.n_y ? f.n_e : g.n_y;
-    int k = prof ? prof->begin("build_E", &ev) : -1;
-    k_build_E<<<blocks(n, 256), 256, 0, s>>>(g, f, U, Ud);
-    if (prof) prof->end(k, ev);
-    k = prof ? prof->begin("tables", &ev) : -1;
-    dim3 grid(blocks(f.n_pos, kTabT), (unsigned)f.tab_splits);
-    k_tables_part<<<grid, kTabT, 0, s>>>(g, f);
-    if (prof) prof->end(k, ev);
 }
 
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
@@ -1141,11 +976,9 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
         case kBBox:
         case kBRun: return u1_batch_blocks(g, fp, kind);
         case kBPerY: return (g.n_y + 255) / 256;
-        case kBTabPart: return (fp.n_pos + kTabT - 1) / kTabT * fp.tab_splits;
-        case kBBuildE: {
-            const int64_t n = fp.n_e > g.n_y ? fp.n_e : g.n_y;
-            return (n + 255) / 256;
-        }
+        case kBTabPart: return tc_table_blocks(fp);
+        case kBTabComb: return tc_combine_blocks(fp);
+        case kBBuildE: return tc_build_E_blocks(g, fp);
         case kBJPart: return fp.J_blocks;
     }
     return 0;
@@ -1185,10 +1018,8 @@ void launch_batch_search(const BatchLaunch& bl, cudaStream_t s) {
 }
 
 void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s) {
-    const InstDev* d = bl.insts;
     launch_batch_u1(bl, s);
-    kb_build_E<<<(unsigned)bl.n_blocks[kBBuildE], 256, 0, s>>>(d, bl.map[kBBuildE]);
-    kb_tables_part<<<(unsigned)bl.n_blocks[kBTabPart], kTabT, 0, s>>>(d, bl.map[kBTabPart]);
+    launch_batch_tables(bl, s);
     kb_J_partial<<<(unsigned)bl.n_blocks[kBJPart], kJThreads, 0, s>>>(bl.insts,
                                                                    bl.map[kBJPart]);
 }

@@ -1,0 +1,506 @@
+// kernels_tc.cu -- the correlation tables of the fast path on the tensor
+// cores (tcgen05, sm_103a).
+//
+// The u0 search evaluates S(u) through three correlations of the fixed
+// Gaussian weights against E = U^(y) - y (kernels_fast.cu):
+//   P_p = sum_l a_l E_{p+l} (a_l = phi_l w_l),  Q_p = sum_l phi_l E_{p+l}^2,
+//   R_p = sum_l phi_l E_{p+l} E_{p+l+1}.
+// Each is a Toeplitz product.  With p = 128 a + b and m = b + l,
+//   y_{128a+b} = sum_m h_{m-b} x_{128a+m},
+// i.e. D[b][a] = sum_m H[b][m] X[m][a]: a 128-row Toeplitz matrix of the
+// filter times a Hankel matrix of the signal -- a GEMM with M = 128 phases,
+// N = table columns (128 positions each), K = taps.
+//
+// Exactness (an Ozaki-style split).  The screening needs the tables to
+// ~2^-40 of the cost, far beyond bf16.  The taps are cut into chunks of 128;
+// per chunk the filter is scaled by a power of two sigma_h(c) >= its largest
+// |h|, per 128-value block beta of the signal by sigma_x(beta) >= its largest
+// |x|, and each scaled value v (|v| < 1) is cut into seven 7-bit integer
+// slices, v = sum_t s_t 2^-7(t+1) + r with |s_0| <= 128, |s_t| <= 64 and
+// |r| <= 2^-50.  Integers of at most 8 bits are exact in bf16, a product of
+// two is exact in FP32, and every accumulator below sums at most seven
+// products over 128 taps: |sum| <= 7 * 2^14 * 128 < 2^24, so the tensor
+// core's FP32 accumulation is exact.  Products (s, t) with s + t = k share
+// accumulator k (k = 0..6, 28 products; s + t >= 7 is dropped); the seven
+// exact accumulators are folded in double-float and scaled.  Chunks are added
+// in a fixed tree of accurate double-float additions.  Every rounding and
+// truncation is bounded (tc_combine_body), and the bound per table column
+// replaces the table term of the screening bound.
+#include <cudaTypedefs.h>
+#include <float.h>
+
+#include <atomic>
+
+#include "df.cuh"
+#include "tc.cuh"
+#include "ucp_fast.cuh"
+
+namespace ucp {
+
+namespace {
+
+constexpr int kSl = kTcSlices;        // slices per operand
+constexpr int kTcT = 256;             // threads of the tensor-core kernel
+constexpr uint32_t kTcATile = 128 * 128 * 2;   // filter tile: 128 phases x 128 taps
+constexpr uint32_t kTcBTile = 64 * 128 * 2;    // signal tile: 64 columns x 128 taps
+constexpr uint32_t kTcHBytes = kSl * 8 * 256 * 2;   // a chunk's filter slices
+constexpr size_t kTcSmem = kSl * kTcBTile + 2 * kTcATile + kTcHBytes + 1024;
+constexpr uint32_t kTmemCols = 512;   // accumulator k at columns 64 k .. 64 k + 63
+constexpr int64_t kTcPolls = 4000000; // bound of every mbarrier wait
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {   // exact for |v| <= 256 integers
+    return (uint16_t)(__float_as_uint(v) >> 16);
+}
+
+// ---- filter slices (once per instance) ------------------------------------
+
+// Chunk c of filter `flt` (0: a_l = phi_l w_l, 1: phi_l): window
+// G[i] = h[128 c - 127 + i], i < 256, cut into slices, stored as 8 copies
+// shifted by r = 0..7 elements so that every 16-byte chunk of a Toeplitz tile
+// row is one aligned load.
+__global__ void __launch_bounds__(256) k_tc_filter(Geom g, FastView f) {
+    __shared__ float sl[kSl][256];
+    __shared__ double red[256];
+    const int c = blockIdx.x, flt = blockIdx.y, i = threadIdx.x;
+    const int64_t l = (int64_t)kTcK * c - 127 + i;
+    double h = 0.0;
+    if (l >= 0 && l < g.n_w) {
+        h = f.phi[l];
+        if (flt == 0) h = h * ((double)(l - g.hw) * g.delta);
+    }
+    red[i] = fabs(h);
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (i < s) red[i] = fmax(red[i], red[i + s]);
+        __syncthreads();
+    }
+    int e = 0;
+    if (red[0] > 0.0) frexp(red[0], &e);   // 2^e > max |h|
+    double v = ldexp(h, -e);
+#pragma unroll
+    for (int t = 0; t < kSl; ++t) {
+        const double s = rint(v * 128.0);
+        v = v * 128.0 - s;   // exact
+        sl[t][i] = (float)s;
+    }
+    __syncthreads();
+    uint16_t* out = f.tc_h + (size_t)(flt * f.tc_nch + c) * kSl * 8 * 256;
+    for (int t = 0; t < kSl; ++t)
+        for (int r = 0; r < 8; ++r)
+            out[((size_t)t * 8 + r) * 256 + i] = bf16_bits(i + r < 256 ? sl[t][i + r] : 0.f);
+    if (i == 0) f.tc_he[flt * f.tc_nch + c] = e;
+}
+
+// ---- E and the signal slices (every sweep) ------------------------------
+
+// Block bx: E-indices m = 128 bx + j.  E_m = U^(y_{jlo+m}) - y (U constant
+// beyond the table) in double-float for the second screening tier; the three
+// signals E, E^2 = E_m E_m and E E_+ = E_m E_{m+1} (FP64 products) as
+// double-float, scaled by the block's power of two and cut into slices.  Ud
+// for the serial costs rides along on the same blocks.
+__device__ __forceinline__ void build_E_tc_body(const Geom& g, const FastView& f,
+                                                const double* __restrict__ U,
+                                                double* __restrict__ Ud, int64_t bx) {
+    __shared__ float wmax[3][4];
+    const int j = threadIdx.x;
+    const int64_t m = bx * 128 + j;
+    if (m < g.n_y) Ud[m] = m + 1 < g.n_y ? __dsub_rn(U[m + 1], U[m]) : 0.0;
+    dfloat x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (m < f.n_e) {
+        const int64_t jj = f.jlo + m;
+        const int64_t a = jj < 0 ? 0 : (jj > g.n_y - 1 ? g.n_y - 1 : jj);
+        const int64_t b = jj + 1 < 0 ? 0 : (jj + 1 > g.n_y - 1 ? g.n_y - 1 : jj + 1);
+        const double e0 = U[a] - (double)(jj - g.hy) * g.delta;
+        const double e1 = U[b] - (double)(jj + 1 - g.hy) * g.delta;
+        x[0] = df_from_double(e0);
+        x[1] = df_from_double(e0 * e0);
+        x[2] = df_from_double(e0 * e1);
+        f.E[m] = x[0];
+    }
+    if (bx >= f.tc_nblk) return;   // uniform over the block
+    float mx[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        mx[s] = fabsf(x[s].hi);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            mx[s] = fmaxf(mx[s], __shfl_xor_sync(0xffffffffu, mx[s], off));
+        if ((j & 31) == 0) wmax[s][j >> 5] = mx[s];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const float M = fmaxf(fmaxf(wmax[s][0], wmax[s][1]), fmaxf(wmax[s][2], wmax[s][3]));
+        int e = 0;
+        if (M > 0.f) frexpf(M, &e);   // 2^e > max |hi|, hence > |hi + lo|
+        float rh = ldexpf(x[s].hi, -e), rl = ldexpf(x[s].lo, -e);
+        uint16_t* out = f.tc_x + ((size_t)s * kSl * f.tc_nblk + bx) * 128 + j;
+#pragma unroll
+        for (int t = 0; t < kSl; ++t) {
+            const float y = rh * 128.f, z = rl * 128.f;   // exact
+            const float st = rintf(y);
+            const float d = __fsub_rn(y, st);              // exact
+            two_sum(d, z, rh, rl);                         // exact
+            out[(size_t)t * f.tc_nblk * 128] = bf16_bits(st);
+        }
+        if (j == 0) f.tc_xe[s * f.tc_nblk + bx] = e;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_build_E_tc(Geom g, FastView f,
+                                                     const double* __restrict__ U,
+                                                     double* __restrict__ Ud) {
+    build_E_tc_body(g, f, U, Ud, blockIdx.x);
+}
+
+// ---- the slice products on the tensor cores ------------------------------
+
+struct TcShared {
+    uint64_t bar[2];   // MMAs of slice group s done: bar[s & 1]
+    uint64_t bar_x;    // signal tiles landed (TMA)
+    uint64_t bar_h;    // filter slices landed (bulk copy)
+    uint32_t tmem;
+};
+
+// Table tau (0: P from E and a; 1: Q from E^2 and phi; 2: R from E E_+ and
+// phi), column group grp (columns a = 64 grp .. + 63), tap chunk c: the
+// double-float partial D_c[b][a] of positions 128 a + b into tc_part.
+// `tmap` is the signal's TMA map (kernel parameter or global memory).
+__device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensorMap* tmap,
+                                               int tau, int grp, int c, char* smem_raw,
+                                               TcShared& ts) {
+    char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    char* tB = base;                     // kSl signal tiles (all slices)
+    char* tA = base + kSl * kTcBTile;    // two filter tiles (double buffer)
+    char* tH = tA + 2 * kTcATile;        // the chunk's filter slices, 8 shifts each
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int flt = tau == 0 ? 0 : 1;
+    if (tid == 0) {
+        mbar_init(&ts.bar[0], 1);
+        mbar_init(&ts.bar[1], 1);
+        mbar_init(&ts.bar_x, 1);
+        mbar_init(&ts.bar_h, 1);
+        fence_mbar_init();
+        // filter slices of the chunk (contiguous), then the signal tiles: row
+        // r of slice t is block 64 grp + r + c, two 64-wide boxes per slice
+        mbar_expect_tx(&ts.bar_h, kTcHBytes);
+        bulk_load(tH, f.tc_h + (size_t)(flt * f.tc_nch + c) * kSl * 8 * 256, kTcHBytes,
+                  &ts.bar_h);
+        mbar_expect_tx(&ts.bar_x, kSl * kTcBTile);
+        const int row0 = 64 * grp + c;
+        for (int t = 0; t < kSl; ++t) {
+            const int y = (int)(t * f.tc_nblk) + row0;
+            tma_load_2d(tB + t * kTcBTile, tmap, 0, y, &ts.bar_x);
+            tma_load_2d(tB + t * kTcBTile + 64 * 128, tmap, 64, y, &ts.bar_x);
+        }
+    }
+    if (warp == 0) tmem_alloc(&ts.tmem, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // filter tile of slice s: row b holds G[m - b + 127], m < 128
+    auto build_A = [&](int s, char* dst) {
+        const char* hs = tH + (size_t)s * 8 * 256 * 2;
+#pragma unroll
+        for (int k0 = 0; k0 < 128 * 16; k0 += kTcT) {
+            const int k = k0 + tid;
+            const int b = k >> 4, jc = k & 15;
+            const int r = 7 - (b & 7);
+            const int q = jc + 15 - (b >> 3);
+            *(uint4*)(dst + sw128_offset(128, b, jc)) =
+                *(const uint4*)(hs + (r * 256 + 8 * q) * 2);
+        }
+    };
+    bool ok = mbar_wait(&ts.bar_h, 0, kTcPolls);
+    ok = __syncthreads_and(ok);
+    if (ok) build_A(0, tA);
+    fence_proxy_async_smem();
+    __syncthreads();
+    const uint32_t tmem = ts.tmem;
+    constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
+    if (tid == 0 && ok) ok = mbar_wait(&ts.bar_x, 0, kTcPolls);
+    for (int s = 0; s < kSl; ++s) {
+        if (tid == 0 && ok) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(tA + (s & 1) * kTcATile);
+            for (int t = 0; s + t < kSl; ++t) {
+                const uint32_t b0 = smem_u32(tB + t * kTcBTile);
+                const uint32_t d = tmem + (uint32_t)((s + t) * 64);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const uint32_t off = (uint32_t)((kk & 3) * 32);
+                    umma_bf16(d, umma_desc_sw128(a0 + (kk >> 2) * (128 * 128) + off),
+                              umma_desc_sw128(b0 + (kk >> 2) * (64 * 128) + off), idesc,
+                              (s > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            umma_commit(&ts.bar[s & 1]);
+        }
+        if (s + 1 < kSl) {
+            // the other buffer was read by slice group s - 1
+            if (s >= 1 && ok) ok = mbar_wait(&ts.bar[(s - 1) & 1], ((s - 1) >> 1) & 1, kTcPolls);
+            ok = __syncthreads_and(ok);
+            fence_proxy_async_smem();   // the tensor core's reads before our writes
+            if (ok) build_A(s + 1, tA + ((s + 1) & 1) * kTcATile);
+            fence_proxy_async_smem();
+            ok = __syncthreads_and(ok);
+        }
+    }
+    // the last commit covers every MMA of this thread
+    if (ok) ok = mbar_wait(&ts.bar[(kSl - 1) & 1], ((kSl - 1) >> 1) & 1, kTcPolls);
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (ok) {
+        const int qd = warp & 3, hh = warp >> 2;
+        const int b = 32 * qd + lane;
+        const uint32_t lbase = tmem + ((uint32_t)(32 * qd) << 16);
+        const int he = f.tc_he[flt * f.tc_nch + c];
+        const int32_t* xe = f.tc_xe + (size_t)tau * f.tc_nblk;
+        float2* part = f.tc_part + (size_t)(tau * f.tc_nch + c) * f.tc_ng * 64 * 128;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+            const int col0 = 32 * hh + c0;
+            float v[16];
+            dfloat acc[16];
+            // smallest terms first: D_6 2^-42 + ... + D_1 2^-7, then D_0
+            tmem_ld16(lbase + (uint32_t)(6 * 64 + col0), v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[e] = {v[e] * 0x1p-42f, 0.f};
+#pragma unroll 1
+            for (int k = 5; k >= 0; --k) {
+                tmem_ld16(lbase + (uint32_t)(k * 64 + col0), v);
+                const float sc = __int_as_float((127 - 7 * k) << 23);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) acc[e] = df_add_f(acc[e], v[e] * sc);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int64_t a = (int64_t)64 * grp + col0 + e;
+                const int ex = he + xe[a + c] - 14;
+                part[a * 128 + b] = make_float2(ldexpf(acc[e].hi, ex), ldexpf(acc[e].lo, ex));
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(f.tc_err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+__global__ void __launch_bounds__(kTcT, 1) k_tc_tables(const __grid_constant__ FastView f) {
+    extern __shared__ char tc_smem[];
+    __shared__ TcShared ts;
+    const int per = f.tc_ng * f.tc_nch;
+    const int tau = blockIdx.x / per, rest = blockIdx.x % per;
+    tc_tables_body(f, &f.tc_map[tau], tau, rest / f.tc_nch, rest % f.tc_nch, tc_smem, ts);
+}
+
+// ---- chunk sums and the error bound ---------------------------------------
+
+constexpr int kCombT = 384;   // three tables x 128 positions
+
+// Column a (128 positions); thread (tau, b): table tau at p = 128 a + b as the
+// chunk partials added in chunk order by accurate double-float additions
+// (df_add_acc: |error| <= 3 u^2 |result|, u = 2^-24), and tc_bt[a], a bound
+// on the error of the table identity's S at any cell whose two positions lie
+// in column a: 2 max_p beta_P(p) + max_p max(beta_Q(p), beta_R(p)) with, per
+// table,
+//   beta(p) = 1.25 [2^-39 sum_c 2^(he(c) + xe(a + c))      slices, products, fold
+//                   + 3.01 u^2 sum_c |running sum|         chunk additions
+//                   + 2^-130]                              underflow of scaled lows
+// The first term: per product term 2.32 2^-48 sigma_h sigma_x (double-float
+// and FP64 rounding of the signal 2^-48 + 2^-53, slice truncations 2 x 2^-50,
+// FP64 a_l 2^-53, dropped products s + t >= 7 0.76 2^-48), 128 terms per chunk,
+// plus 146 2^-48 sigma_h sigma_x for folding the seven accumulators
+// (smallest first, df_add_f error <= u^2 (2 |a| + |b|)): <= 2^-39 per chunk.
+__device__ __forceinline__ void tc_combine_body(const FastView& f, int64_t a) {
+    __shared__ float colterm[3];
+    __shared__ float wmax[kCombT / 32];
+    const int tid = threadIdx.x, tau = tid >> 7, b = tid & 127;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int64_t p = a * 128 + b;
+    if (b < 32) {   // the slice term of this table and column
+        const int flt = tau == 0 ? 0 : 1;
+        float sum = 0.f;
+        for (int c = lane; c < f.tc_nch; c += 32)
+            sum += ldexpf(1.f, f.tc_he[flt * f.tc_nch + c] +
+                                   f.tc_xe[(size_t)tau * f.tc_nblk + a + c] - 39);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) colterm[tau] = sum * 1.0001f;
+    }
+    const size_t stride = (size_t)f.tc_ng * 64 * 128;
+    const float2* part = f.tc_part + (size_t)tau * f.tc_nch * stride + p;
+    dfloat r = {0.f, 0.f};
+    float mag = 0.f;
+    for (int c0 = 0; c0 < f.tc_nch; c0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)   // issue the loads, then add in order
+            v[k] = c0 + k < f.tc_nch ? __ldcg(part + (size_t)(c0 + k) * stride)
+                                     : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (c0 + k < f.tc_nch) {
+                r = df_add_acc(r, dfloat{v[k].x, v[k].y});
+                mag += fabsf(r.hi);
+            }
+    }
+    dfloat* out = tau == 0 ? f.P : (tau == 1 ? f.Q : f.R);
+    if (p < f.n_pos) out[p] = r;
+    __syncthreads();
+    float beta = p < f.n_pos ? 1.25f * (colterm[tau] + 3.01f * 0x1p-48f * mag * 1.0001f +
+                                        0x1p-130f)
+                             : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) beta = fmaxf(beta, __shfl_xor_sync(0xffffffffu, beta, off));
+    if (lane == 0) wmax[warp] = beta;
+    __syncthreads();
+    if (tid == 0) {
+        float mp = 0.f, mq = 0.f;
+        for (int w = 0; w < 4; ++w) mp = fmaxf(mp, wmax[w]);
+        for (int w = 4; w < kCombT / 32; ++w) mq = fmaxf(mq, wmax[w]);
+        f.tc_bt[a] = (2.f * mp + mq) * 1.0001f;
+    }
+}
+
+__global__ void __launch_bounds__(kCombT) k_tc_combine(FastView f) {
+    tc_combine_body(f, blockIdx.x);
+}
+
+// ---- batched wrappers -------------------------------------------------------
+
+__device__ __forceinline__ BlockRef stage_tc(const InstDev* insts, const BlockRef* map,
+                                             InstDev& sd) {
+    const BlockRef r = map[blockIdx.x];
+    const int* src = (const int*)(insts + r.inst);
+    int* dst = (int*)&sd;
+    for (int k = threadIdx.x; k < (int)(sizeof(InstDev) / 4); k += blockDim.x)
+        dst[k] = src[k];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(128) kb_build_E_tc(const InstDev* insts,
+                                                     const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage_tc(insts, map, sd);
+    build_E_tc_body(sd.g, sd.f, sd.U, sd.Ud, r.local);
+}
+
+__global__ void __launch_bounds__(kTcT, 1) kb_tc_tables(const InstDev* insts,
+                                                        const BlockRef* map) {
+    extern __shared__ char tc_smem[];
+    __shared__ InstDev sd;
+    __shared__ TcShared ts;
+    const BlockRef r = stage_tc(insts, map, sd);
+    const int per = sd.f.tc_ng * sd.f.tc_nch;
+    const int tau = r.local / per, rest = r.local % per;
+    const CUtensorMap* tmap = &insts[r.inst].f.tc_map[tau];   // global memory
+    if (threadIdx.x == 0) tmap_acquire(tmap);
+    tc_tables_body(sd.f, tmap, tau, rest / sd.f.tc_nch, rest % sd.f.tc_nch, tc_smem, ts);
+}
+
+__global__ void __launch_bounds__(kCombT) kb_tc_combine(const InstDev* insts,
+                                                     const BlockRef* map) {
+    __shared__ InstDev sd;
+    const BlockRef r = stage_tc(insts, map, sd);
+    tc_combine_body(sd.f, r.local);
+}
+
+}  // namespace
+
+// ---- host side --------------------------------------------------------------
+
+void tc_plan(const Geom& g, FastPlan* fp) {
+    fp->tc_na = (fp->n_pos + 127) / 128;
+    fp->tc_ng = (int)((fp->tc_na + 63) / 64);
+    fp->tc_nch = (int)((g.n_w + 127 + kTcK - 1) / kTcK);
+    fp->tc_nblk = (int64_t)64 * fp->tc_ng + fp->tc_nch - 1;
+}
+
+size_t tc_bytes(const FastPlan& fp, size_t align, size_t* sizes) {
+    sizes[0] = (size_t)2 * fp.tc_nch * kSl * 8 * 256 * 2;       // tc_h
+    sizes[1] = (size_t)2 * fp.tc_nch * 4;                       // tc_he
+    sizes[2] = (size_t)3 * kSl * fp.tc_nblk * 128 * 2;          // tc_x
+    sizes[3] = (size_t)3 * fp.tc_nblk * 4;                      // tc_xe
+    sizes[4] = (size_t)3 * fp.tc_nch * fp.tc_ng * 64 * 128 * 8; // tc_part
+    sizes[5] = (size_t)(fp.tc_na + 1) * 4;                      // tc_bt
+    sizes[6] = 4;                                               // tc_err
+    size_t total = 0;
+    for (int k = 0; k < 7; ++k) total += (sizes[k] + align - 1) / align * align;
+    return total;
+}
+
+bool tc_encode_maps(FastView* f) {
+    static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> encode{nullptr};
+    if (!encode.load()) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode.store((PFN_cuTensorMapEncodeTiled_v12000)fn);
+    }
+    for (int sig = 0; sig < 3; ++sig) {
+        void* base = f->tc_x + (size_t)sig * kSl * f->tc_nblk * 128;
+        const cuuint64_t dims[2] = {128, (cuuint64_t)kSl * (cuuint64_t)f->tc_nblk};
+        const cuuint64_t strides[1] = {256};
+        const cuuint32_t box[2] = {64, 64};
+        const cuuint32_t estr[2] = {1, 1};
+        if (encode.load()(&f->tc_map[sig], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+int64_t tc_build_E_blocks(const Geom& g, const FastPlan& fp) {
+    int64_t n = fp.tc_nblk * 128;
+    if (fp.n_e > n) n = fp.n_e;
+    if (g.n_y > n) n = g.n_y;
+    return (n + 127) / 128;
+}
+
+int64_t tc_table_blocks(const FastPlan& fp) { return (int64_t)3 * fp.tc_ng * fp.tc_nch; }
+
+int64_t tc_combine_blocks(const FastPlan& fp) { return fp.tc_na; }
+
+cudaError_t tc_init_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kb_tc_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTcSmem);
+}
+
+void launch_tc_setup(const Geom& g, const FastView& f, cudaStream_t s) {
+    k_tc_filter<<<dim3((unsigned)f.tc_nch, 2), 256, 0, s>>>(g, f);
+}
+
+void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
+                   cudaStream_t s, Prof* prof) {
+    cudaEvent_t ev;
+    int k = prof ? prof->begin("build_E", &ev) : -1;
+    k_build_E_tc<<<(unsigned)tc_build_E_blocks(g, f), 128, 0, s>>>(g, f, U, Ud);
+    if (prof) prof->end(k, ev);
+    k = prof ? prof->begin("tables", &ev) : -1;
+    k_tc_tables<<<(unsigned)tc_table_blocks(f), kTcT, kTcSmem, s>>>(f);
+    if (prof) prof->end(k, ev);
+    k = prof ? prof->begin("tab_combine", &ev) : -1;
+    k_tc_combine<<<(unsigned)tc_combine_blocks(f), kCombT, 0, s>>>(f);
+    if (prof) prof->end(k, ev);
+}
+
+void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s) {
+    const InstDev* d = bl.insts;
+    kb_build_E_tc<<<(unsigned)bl.n_blocks[kBBuildE], 128, 0, s>>>(d, bl.map[kBBuildE]);
+    kb_tc_tables<<<(unsigned)bl.n_blocks[kBTabPart], kTcT, kTcSmem, s>>>(d, bl.map[kBTabPart]);
+    kb_tc_combine<<<(unsigned)bl.n_blocks[kBTabComb], kCombT, 0, s>>>(d, bl.map[kBTabComb]);
+}
+
+}  // namespace ucp

@@ -182,11 +182,11 @@ size_t inst_bytes(const Geom& g, int precision) {
     if (precision == 1) {
         FastPlan fp;
         fast_plan(g, &fp);
-        b += 3 * rnd(8 * (size_t)fp.n_pos) + 3 * rnd(8 * (size_t)fp.n_e) +
+        size_t tcs[7];
+        b += 3 * rnd(8 * (size_t)fp.n_pos) + rnd(8 * (size_t)fp.n_e) +
              3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
              rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 3 * rnd(4) + rnd(kDeferRecBytes * nx) + rnd(32) +
-             rnd(24 * (size_t)fp.tab_splits * (size_t)fp.n_pos) +
-             rnd(4 * (size_t)fp.tab_pblocks) + rnd(4) +
+             tc_bytes(fp, 256, tcs) + rnd(4) +
              u1_scratch_bytes(g, fp, 256);
     }
     return b;
@@ -206,13 +206,12 @@ static void fast_bounds(ucp_inst* in, double B) {
     FastView& f = in->fv;
     const double u = 0x1p-53, uf2 = 0x1p-48;
     // the plain path's sum in the fixed order (a term passes through at most
-    // 31 additions in its chunk and one per level), + double-float 64-tap
-    // blocks + FP64 combination + double-float evaluation of the identity
+    // 31 additions in its chunk and one per level) + double-float evaluation
+    // of the identity; the tables' own error is bounded per column on the
+    // device (tc_bt)
     const double levels = ceil(log2((double)sum_chunks(g.n_w) + 1.0));
     const double ser = (kSumChunk - 1 + levels + 1) * u;
-    const double rel = ser + (2.0 * 64 + 16) * uf2 +
-                       2.0 * ((double)in->fv.tab_span / 64.0 + 2.0) * uf2 +
-                       ((double)in->fv.tab_splits + 8.0) * u + 60.0 * uf2;
+    const double rel = ser + 60.0 * uf2;
     f.beta_rel = (float)(1.25 * rel);
     // rounding of grid positions, of E = U - y and of the residuals of both
     // evaluations: |d(residual)| <= u A
@@ -247,16 +246,21 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.Q = (dfloat*)A.get(8 * (size_t)f.n_pos);
     f.R = (dfloat*)A.get(8 * (size_t)f.n_pos);
     f.E = (dfloat*)A.get(8 * (size_t)f.n_e);
-    f.E2 = (dfloat*)A.get(8 * (size_t)f.n_e);
-    f.EE = (dfloat*)A.get(8 * (size_t)f.n_e);
     f.a = (dfloat*)A.get(8 * nw);
     f.phidf = (dfloat*)A.get(8 * nw);
     f.wdf = (dfloat*)A.get(8 * nw);
     f.prior = (dfloat*)A.get(8 * nx);
     f.t64 = (dfloat*)A.get(8 * 47);
     f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
-    f.tab_part = (double*)A.get(24 * (size_t)f.tab_splits * (size_t)f.n_pos);
-    f.tab_done = (int32_t*)A.get(4 * (size_t)f.tab_pblocks);
+    size_t tcs[7];
+    tc_bytes(f, 256, tcs);
+    f.tc_h = (uint16_t*)A.get(tcs[0]);
+    f.tc_he = (int32_t*)A.get(tcs[1]);
+    f.tc_x = (uint16_t*)A.get(tcs[2]);
+    f.tc_xe = (int32_t*)A.get(tcs[3]);
+    f.tc_part = (float2*)A.get(tcs[4]);
+    f.tc_bt = (float*)A.get(tcs[5]);
+    f.tc_err = (int32_t*)A.get(tcs[6]);
     f.J_done = (int32_t*)A.get(4);
     f.W2_dev = (double*)A.get(8);
     f.n_exact = (int32_t*)A.get(4);
@@ -266,12 +270,17 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.n_pairs = (int64_t*)A.get(32);
     const bool u1_ok = u1_carve(
         g, &f, [](void* a, size_t n) { return ((Arena*)a)->get(n); }, &A);
-    if (!f.P || !f.Q || !f.R || !f.E || !f.E2 || !f.EE || !f.a || !f.phidf || !f.wdf ||
-        !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tab_part || !f.tab_done ||
-        !f.J_done || !f.W2_dev ||
+    if (!f.P || !f.Q || !f.R || !f.E || !f.a || !f.phidf || !f.wdf ||
+        !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tc_h || !f.tc_he || !f.tc_x ||
+        !f.tc_xe || !f.tc_part || !f.tc_bt || !f.tc_err || !f.J_done || !f.W2_dev ||
         !f.n_exact || !f.n_tier2 || !f.defer_cnt || !f.defer_list || !f.n_pairs) {
         set_error("%s%s", "ucp_create: out of device memory (fast path)", "");
         return UCP_E_NOMEM;
+    }
+    if (!tc_encode_maps(&f)) {
+        set_error("%s%s", "ucp_create: TMA tensor maps of the table signals ",
+                  "could not be encoded");
+        return UCP_E_CUDA;
     }
     const double step = ldexp(g.delta, -g.shift);
     const dfloat sd = df_from_double(step), kd = df_from_double(g.kk);
@@ -338,6 +347,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     }
     in->fast = p.precision == 1;
     if (in->fast) {
+        if (tc_init_attributes() != cudaSuccess) return check(in, "tensor-core kernel attributes");
         ucp_status st = fast_alloc(in);
         if (st != UCP_OK) return st;
     }
@@ -347,11 +357,12 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     UCP_LAUNCH(in, "coarse", launch_coarse_list(g, d, s));
     if (in->fast) {
         UCP_LAUNCH(in, "fast_setup", launch_fast_setup(g, in->fv, s));
+        UCP_LAUNCH(in, "tc_setup", launch_tc_setup(g, in->fv, s));
         cudaMemsetAsync(in->fv.n_exact, 0, 4, s);
         cudaMemsetAsync(in->fv.n_tier2, 0, 4, s);
         cudaMemsetAsync(in->fv.defer_cnt, 0, 4, s);
         cudaMemsetAsync(in->fv.J_done, 0, 4, s);
-        cudaMemsetAsync(in->fv.tab_done, 0, 4 * (size_t)in->fv.tab_pblocks, s);
+        cudaMemsetAsync(in->fv.tc_err, 0, 4, s);
         cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
         cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
@@ -468,6 +479,16 @@ ucp_status inst_sweep(ucp_inst* in, int n) {
 
 ucp_status inst_sync(ucp_inst* in) {
     if (cudaStreamSynchronize(in->stream) != cudaSuccess) return check(in, "sync");
+    if (in->fast) {
+        int32_t e = 0;
+        if (cudaMemcpy(&e, in->fv.tc_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return check(in, "sync");
+        if (e) {
+            in->poisoned = true;
+            set_error("%s%s", "sync: a tensor-core wait timed out", "");
+            return UCP_E_TIMEOUT;
+        }
+    }
     return check(in, "sync");
 }
 

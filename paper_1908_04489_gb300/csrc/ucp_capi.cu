@@ -302,6 +302,44 @@ extern "C" ucp_status ucp_tie_recosts(ucp_inst* in, int64_t* out) {
     return st;
 }
 
+extern "C" ucp_status ucp_get_tables(ucp_inst* in, double* P, double* Q, double* R,
+                                     int64_t n_pos, float* bound, int64_t n_cols,
+                                     int64_t* sizes) {
+    if (!in || !sizes) return UCP_E_ARG;
+    if (in->poisoned || !in->fast) return UCP_E_STATE;
+    const FastView& f = in->fv;
+    sizes[0] = f.n_pos;
+    sizes[1] = f.tc_na;
+    sizes[2] = f.c_lo;
+    sizes[3] = f.jlo;
+    const bool want_tab = P || Q || R;
+    if ((want_tab && (!P || !Q || !R || n_pos < f.n_pos)) || (bound && n_cols < f.tc_na)) {
+        set_error("ucp_get_tables: %s%s", "NULL table buffer or buffers shorter than the ",
+                  "instance's tables");
+        return UCP_E_ARG;
+    }
+    std::vector<float2> h(want_tab ? (size_t)f.n_pos * 3 : 0);
+    if (want_tab) {
+        const dfloat* src[3] = {f.P, f.Q, f.R};
+        for (int k = 0; k < 3; ++k)
+            cudaMemcpyAsync(h.data() + (size_t)k * f.n_pos, src[k], 8 * (size_t)f.n_pos,
+                            cudaMemcpyDeviceToHost, in->stream);
+    }
+    if (bound)
+        cudaMemcpyAsync(bound, f.tc_bt, 4 * (size_t)f.tc_na, cudaMemcpyDeviceToHost,
+                        in->stream);
+    const ucp_status st = inst_sync(in);
+    if (st != UCP_OK) return st;
+    double* dst[3] = {P, Q, R};
+    if (want_tab)
+        for (int k = 0; k < 3; ++k)
+            for (int64_t p = 0; p < f.n_pos; ++p) {
+                const float2 v = h[(size_t)k * f.n_pos + p];
+                dst[k][p] = (double)v.x + (double)v.y;
+            }
+    return UCP_OK;
+}
+
 extern "C" ucp_status ucp_work_counters(ucp_inst* in, int64_t* out, int32_t n) {
     if (!in || n < 0 || n > UCP_N_COUNTERS || (n > 0 && !out)) return UCP_E_ARG;
     if (in->poisoned) return UCP_E_STATE;

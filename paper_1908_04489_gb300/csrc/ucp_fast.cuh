@@ -21,8 +21,23 @@ void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s);
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
                       double* U, cudaStream_t s, Prof* prof);
+// Correlation tables on the tensor cores (kernels_tc.cu): plan, buffer
+// sizes (7 arrays, each rounded up to align; sizes[] gets the raw sizes),
+// block counts, one-time kernel attributes, per-instance filter slices, and
+// the per-sweep build (E and slices, slice products, chunk sums + bound).
+void tc_plan(const Geom& g, FastPlan* fp);
+size_t tc_bytes(const FastPlan& fp, size_t align, size_t* sizes);
+// TMA maps of the signal slices (after tc_x is allocated); false if the
+// driver's encoder is unavailable or rejects them.
+bool tc_encode_maps(FastView* f);
+int64_t tc_build_E_blocks(const Geom& g, const FastPlan& fp);
+int64_t tc_table_blocks(const FastPlan& fp);
+int64_t tc_combine_blocks(const FastPlan& fp);
+cudaError_t tc_init_attributes();
+void launch_tc_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
                    cudaStream_t s, Prof* prof);
+void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s);
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
                         int64_t* nu_out, int32_t* idx, cudaStream_t s);
 // Blocks of each batched kernel kind for one instance (fast_plan sizes).

@@ -3,6 +3,7 @@
 // the grids of Section III-D, and the launch wrappers of every kernel.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; the library does not link libcuda)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,12 +63,18 @@ struct FastPlan {
     int64_t n_runs;    // runs covering the y grid
     int64_t r_blocks;  // run blocks of the u1 kernel (kU1Runs runs each)
     int64_t J_blocks;  // blocks of the J reduction
-    int64_t tab_span;  // taps per block column of the table kernel
-    int tab_splits;    // block columns of the table kernel
-    int64_t tab_pblocks;  // block rows (position blocks) of the table kernel
+    int64_t tc_na;     // table columns of the tensor-core build (128 positions each)
+    int tc_ng;         // column groups (64 columns, one CTA row each)
+    int tc_nch;        // tap chunks (kTcK taps each)
+    int64_t tc_nblk;   // 128-value signal blocks sliced per sweep
 };
 
 struct dfloat;  // df.cuh
+
+// Tensor-core correlation tables (kernels_tc.cu): 7-bit slices per operand,
+// taps per chunk.
+constexpr int kTcSlices = 7;
+constexpr int kTcK = 128;
 
 // u1 boxes: at most kBoxMax boxes per tile, kBoxTerms Taylor terms per box.
 constexpr int kBoxMax = 32;
@@ -83,8 +90,6 @@ struct FastView : FastPlan {
     dfloat* Q;
     dfloat* R;
     dfloat* E;           // [n_e] U^(y) - y on the extended grid
-    dfloat* E2;          // [n_e] E^2
-    dfloat* EE;          // [n_e] E_m E_{m+1}
     dfloat* a;           // [n_w] phi_l w_l
     dfloat* phidf;       // [n_w] phi_l
     dfloat* wdf;         // [n_w] w_l
@@ -105,8 +110,14 @@ struct FastView : FastPlan {
     double* partN;       // [n_tiles * n_y] numerator partials
     double* partD;       // [n_tiles * n_y] denominator partials
     double* Jpart;       // [J_blocks]
-    double* tab_part;    // [tab_splits * 3 * n_pos] table partial sums
-    int32_t* tab_done;   // [position blocks] tap ranges finished (reset by the last)
+    uint16_t* tc_h;      // [2][tc_nch][kTcSlices][8][256] filter slices (bf16), shifted copies
+    int32_t* tc_he;      // [2][tc_nch] filter chunk scales (exponents)
+    uint16_t* tc_x;      // [3][kTcSlices][tc_nblk][128] signal slices (bf16)
+    int32_t* tc_xe;      // [3][tc_nblk] signal block scales (exponents)
+    float2* tc_part;     // [3][tc_nch][64 tc_ng][128] chunk partials (double-float)
+    float* tc_bt;        // [tc_na + 1] per-column bound on the table error of S
+    int32_t* tc_err;     // set when a wait of the tensor-core kernel timed out
+    CUtensorMap tc_map[3];  // TMA maps of tc_x per signal: rows of 128 bf16, 64 x 64 boxes
     int32_t* J_done;     // J blocks finished (reset by the last)
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
     int32_t* n_exact;    // count of serial re-costings (near ties)
@@ -122,7 +133,7 @@ struct FastView : FastPlan {
     float delta_hi, delta_lo; // delta as double-float
     float kk_hi, kk_lo;       // k^2 as double-float
     float inv_one_f;          // 2^-shift
-    float beta_rel;      // |table cost - serial cost| <= beta_rel M
+    float beta_rel;      // |table cost - serial cost| <= tc_bt(cell) + beta_rel M
     float beta_abs;      //   + beta_abs (2 sqrt(M) + 1)
     float beta_ctl;      //   + beta_ctl sqrt(control term) + ...
     float beta2_rel;     // direct double-float quadrature: beta2_rel S + ...
@@ -153,7 +164,8 @@ struct BlockRef {
 };
 
 enum BatchKind {
-    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBBuildE, kBJPart, kBBox, kBRun, kBKinds
+    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBBuildE, kBJPart, kBBox, kBRun, kBTabComb,
+    kBKinds
 };
 
 // Device arrays describing one batched sweep.

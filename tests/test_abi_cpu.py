@@ -47,7 +47,9 @@ def test_plan_sizes_match_the_configs(lib):
     s = binding.plan(workloads.c5())
     assert (s["n_x"], s["n_w"], s["n_y"], s["n_cand"]) == (100001, 14001, 120001,
                                                            1 + 4 + 64 + 96)
-    assert 0 < s["device_bytes"] < 256 << 20
+    # c5's largest buffer is the tensor-core table partials (3 tables x 111 tap
+    # chunks x 106k positions, double-float)
+    assert 0 < s["device_bytes"] < 512 << 20
 
 
 @pytest.mark.parametrize("field,value,msg", [
