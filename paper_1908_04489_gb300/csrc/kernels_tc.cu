@@ -15,14 +15,15 @@
 // ~2^-40 of the cost, far beyond bf16.  The taps are cut into chunks of 128;
 // per chunk the filter is scaled by a power of two sigma_h(c) >= its largest
 // |h|, per 128-value block beta of the signal by sigma_x(beta) >= its largest
-// |x|, and each scaled value v (|v| < 1) is cut into seven 7-bit integer
-// slices, v = sum_t s_t 2^-7(t+1) + r with |s_0| <= 128, |s_t| <= 64 and
-// |r| <= 2^-50.  Integers of at most 8 bits are exact in bf16, a product of
-// two is exact in FP32, and every accumulator below sums at most seven
-// products over 128 taps: |sum| <= 7 * 2^14 * 128 < 2^24, so the tensor
-// core's FP32 accumulation is exact.  Products (s, t) with s + t = k share
-// accumulator k (k = 0..6, 28 products; s + t >= 7 is dropped); the seven
-// exact accumulators are folded in double-float and scaled.  Chunks are added
+// |x|, and each scaled value v (|v| < 1) is cut into six 8-bit integer
+// slices, v = sum_t s_t 2^-8(t+1) + r with |s_0| <= 256, |s_t| <= 128 and
+// |r| <= 2^-49.  Integers up to 256 in magnitude are exact in bf16 and a
+// product of two is exact in FP32.  Products (s, t) with s + t = k share
+// accumulator k (k = 0..5, 21 products; s + t >= 6 is dropped); over 128 taps
+// accumulator k sums at most 2 products bounded by 2^15 and k - 1 bounded by
+// 2^14 (2^16 alone for k = 0): |sum| <= 2^23 + (k - 1) 2^21 <= 2^24, so the
+// tensor core's FP32 accumulation is exact.  The six exact accumulators are
+// folded in double-float and scaled.  Chunks are added
 // in a fixed tree of accurate double-float additions.  Every rounding and
 // truncation is bounded (tc_combine_body), and the bound per table column
 // replaces the table term of the screening bound.
@@ -40,12 +41,12 @@ namespace ucp {
 namespace {
 
 constexpr int kSl = kTcSlices;        // slices per operand
-constexpr int kTcT = 256;             // threads of the tensor-core kernel
+constexpr int kTcT = 512;             // threads of the tensor-core kernel
 constexpr uint32_t kTcATile = 128 * 128 * 2;   // filter tile: 128 phases x 128 taps
 constexpr uint32_t kTcBTile = 64 * 128 * 2;    // signal tile: 64 columns x 128 taps
 constexpr uint32_t kTcHBytes = kSl * 8 * 256 * 2;   // a chunk's filter slices
 constexpr size_t kTcSmem = kSl * kTcBTile + 2 * kTcATile + kTcHBytes + 1024;
-constexpr uint32_t kTmemCols = 512;   // accumulator k at columns 64 k .. 64 k + 63
+constexpr uint32_t kTmemCols = 512;   // accumulator k at columns 64 k .. 64 k + 63 (k < 6)
 constexpr int64_t kTcPolls = 4000000; // bound of every mbarrier wait
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) {   // exact for |v| <= 256 integers
@@ -79,8 +80,8 @@ __global__ void __launch_bounds__(256) k_tc_filter(Geom g, FastView f) {
     double v = ldexp(h, -e);
 #pragma unroll
     for (int t = 0; t < kSl; ++t) {
-        const double s = rint(v * 128.0);
-        v = v * 128.0 - s;   // exact
+        const double s = rint(v * 256.0);
+        v = v * 256.0 - s;   // exact
         sl[t][i] = (float)s;
     }
     __syncthreads();
@@ -137,7 +138,7 @@ __device__ __forceinline__ void build_E_tc_body(const Geom& g, const FastView& f
         uint16_t* out = f.tc_x + ((size_t)s * kSl * f.tc_nblk + bx) * 128 + j;
 #pragma unroll
         for (int t = 0; t < kSl; ++t) {
-            const float y = rh * 128.f, z = rl * 128.f;   // exact
+            const float y = rh * 256.f, z = rl * 256.f;   // exact
             const float st = rintf(y);
             const float d = __fsub_rn(y, st);              // exact
             two_sum(d, z, rh, rl);                         // exact
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(128) k_build_E_tc(Geom g, FastView f,
 
 struct TcShared {
     uint64_t bar[2];   // MMAs of slice group s done: bar[s & 1]
-    uint64_t bar_x;    // signal tiles landed (TMA)
+    uint64_t bar_x[kTcSlices];   // signal tile of slice t landed (TMA)
     uint64_t bar_h;    // filter slices landed (bulk copy)
     uint32_t tmem;
 };
@@ -178,7 +179,7 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     if (tid == 0) {
         mbar_init(&ts.bar[0], 1);
         mbar_init(&ts.bar[1], 1);
-        mbar_init(&ts.bar_x, 1);
+        for (int t = 0; t < kSl; ++t) mbar_init(&ts.bar_x[t], 1);
         mbar_init(&ts.bar_h, 1);
         fence_mbar_init();
         // filter slices of the chunk (contiguous), then the signal tiles: row
@@ -186,12 +187,12 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
         mbar_expect_tx(&ts.bar_h, kTcHBytes);
         bulk_load(tH, f.tc_h + (size_t)(flt * f.tc_nch + c) * kSl * 8 * 256, kTcHBytes,
                   &ts.bar_h);
-        mbar_expect_tx(&ts.bar_x, kSl * kTcBTile);
         const int row0 = 64 * grp + c;
         for (int t = 0; t < kSl; ++t) {
             const int y = (int)(t * f.tc_nblk) + row0;
-            tma_load_2d(tB + t * kTcBTile, tmap, 0, y, &ts.bar_x);
-            tma_load_2d(tB + t * kTcBTile + 64 * 128, tmap, 64, y, &ts.bar_x);
+            mbar_expect_tx(&ts.bar_x[t], kTcBTile);
+            tma_load_2d(tB + t * kTcBTile, tmap, 0, y, &ts.bar_x[t]);
+            tma_load_2d(tB + t * kTcBTile + 64 * 128, tmap, 64, y, &ts.bar_x[t]);
         }
     }
     if (warp == 0) tmem_alloc(&ts.tmem, kTmemCols);
@@ -218,12 +219,14 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     __syncthreads();
     const uint32_t tmem = ts.tmem;
     constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
-    if (tid == 0 && ok) ok = mbar_wait(&ts.bar_x, 0, kTcPolls);
     for (int s = 0; s < kSl; ++s) {
         if (tid == 0 && ok) {
             tc_fence_after();
             const uint32_t a0 = smem_u32(tA + (s & 1) * kTcATile);
-            for (int t = 0; s + t < kSl; ++t) {
+            for (int t = 0; s + t < kSl && ok; ++t) {
+                // the first slice group starts as the signal tiles land
+                if (s == 0) ok = mbar_wait(&ts.bar_x[t], 0, kTcPolls);
+                if (!ok) break;
                 const uint32_t b0 = smem_u32(tB + t * kTcBTile);
                 const uint32_t d = tmem + (uint32_t)((s + t) * 64);
 #pragma unroll
@@ -251,34 +254,40 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     ok = __syncthreads_and(ok);
     tc_fence_after();
     if (ok) {
-        const int qd = warp & 3, hh = warp >> 2;
+        const int qd = warp & 3, col0 = 16 * (warp >> 2);
         const int b = 32 * qd + lane;
-        const uint32_t lbase = tmem + ((uint32_t)(32 * qd) << 16);
+        const uint32_t lbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)col0;
         const int he = f.tc_he[flt * f.tc_nch + c];
         const int32_t* xe = f.tc_xe + (size_t)tau * f.tc_nblk;
         float2* part = f.tc_part + (size_t)(tau * f.tc_nch + c) * f.tc_ng * 64 * 128;
+        float v[16], w[16];
+        dfloat acc[16];
+        // D_5 2^-40 + D_4 2^-32 in FP32 (one rounding of a sum below
+        // 2^-23.7 sigma_h sigma_x 2^16), then D_3 .. D_0 in double-float,
+        // smallest first
+        tmem_ld16(lbase + 5 * 64, v);
+        tmem_ld16(lbase + 4 * 64, w);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = {__fmaf_rn(w[e], 0x1p-32f, v[e] * 0x1p-40f), 0.f};
 #pragma unroll 1
-        for (int c0 = 0; c0 < 32; c0 += 16) {
-            const int col0 = 32 * hh + c0;
-            float v[16];
-            dfloat acc[16];
-            // smallest terms first: D_6 2^-42 + ... + D_1 2^-7, then D_0
-            tmem_ld16(lbase + (uint32_t)(6 * 64 + col0), v);
+        for (int k = 3; k >= 0; --k) {
+            tmem_ld16(lbase + (uint32_t)(k * 64), v);
+            const float sc = __int_as_float((127 - 8 * k) << 23);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) acc[e] = {v[e] * 0x1p-42f, 0.f};
-#pragma unroll 1
-            for (int k = 5; k >= 0; --k) {
-                tmem_ld16(lbase + (uint32_t)(k * 64 + col0), v);
-                const float sc = __int_as_float((127 - 7 * k) << 23);
+            for (int e = 0; e < 16; ++e) acc[e] = df_add_f(acc[e], v[e] * sc);
+        }
 #pragma unroll
-                for (int e = 0; e < 16; ++e) acc[e] = df_add_f(acc[e], v[e] * sc);
+        for (int e = 0; e < 16; ++e) {
+            const int64_t a = (int64_t)64 * grp + col0 + e;
+            const int ex = he + xe[a + c] - 16;
+            float2 o;
+            if (ex >= -126 && ex <= 127) {
+                const float sc = __int_as_float((ex + 127) << 23);
+                o = make_float2(acc[e].hi * sc, acc[e].lo * sc);
+            } else {
+                o = make_float2(ldexpf(acc[e].hi, ex), ldexpf(acc[e].lo, ex));
             }
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int64_t a = (int64_t)64 * grp + col0 + e;
-                const int ex = he + xe[a + c] - 14;
-                part[a * 128 + b] = make_float2(ldexpf(acc[e].hi, ex), ldexpf(acc[e].lo, ex));
-            }
+            part[a * 128 + b] = o;
         }
     } else if (tid == 0) {
         atomicExch(f.tc_err, 1);
@@ -299,21 +308,25 @@ __global__ void __launch_bounds__(kTcT, 1) k_tc_tables(const __grid_constant__ F
 // ---- chunk sums and the error bound ---------------------------------------
 
 constexpr int kCombT = 384;   // three tables x 128 positions
+constexpr int kCombBatch = 24; // chunk partials loaded at once per thread
 
 // Column a (128 positions); thread (tau, b): table tau at p = 128 a + b as the
-// chunk partials added in chunk order by accurate double-float additions
-// (df_add_acc: |error| <= 3 u^2 |result|, u = 2^-24), and tc_bt[a], a bound
+// chunk partials added in a fixed order (four interleaved chains, then
+// pairwise) by accurate double-float additions (df_add_acc: |error| <=
+// 3 u^2 |result|, u = 2^-24), and tc_bt[a], a bound
 // on the error of the table identity's S at any cell whose two positions lie
 // in column a: 2 max_p beta_P(p) + max_p max(beta_Q(p), beta_R(p)) with, per
 // table,
-//   beta(p) = 1.25 [2^-39 sum_c 2^(he(c) + xe(a + c))      slices, products, fold
-//                   + 3.01 u^2 sum_c |running sum|         chunk additions
+//   beta(p) = 1.25 [1.25 2^-39 sum_c 2^(he(c) + xe(a + c)) slices, products, fold
+//                   + 3.01 u^2 sum over additions |result|  chunk additions
 //                   + 2^-130]                              underflow of scaled lows
-// The first term: per product term 2.32 2^-48 sigma_h sigma_x (double-float
-// and FP64 rounding of the signal 2^-48 + 2^-53, slice truncations 2 x 2^-50,
-// FP64 a_l 2^-53, dropped products s + t >= 7 0.76 2^-48), 128 terms per chunk,
-// plus 146 2^-48 sigma_h sigma_x for folding the seven accumulators
-// (smallest first, df_add_f error <= u^2 (2 |a| + |b|)): <= 2^-39 per chunk.
+// The first term: per product term 3.32 2^-48 sigma_h sigma_x (double-float
+// and FP64 rounding of the signal 2^-48 + 2^-53, slice truncations 2 x 2^-49,
+// FP64 a_l 2^-53, dropped products s + t >= 6 1.26 2^-48), 128 terms per chunk,
+// plus 142 2^-48 sigma_h sigma_x for folding the six accumulators (the two
+// smallest in FP32: <= 1.2 2^-48; then smallest first in double-float,
+// df_add_f error <= u^2 (2 |a| + |b|): <= 141 2^-48): 567 2^-48 <= 1.25 2^-39
+// per chunk.
 __device__ __forceinline__ void tc_combine_body(const FastView& f, int64_t a) {
     __shared__ float colterm[3];
     __shared__ float wmax[kCombT / 32];
@@ -328,25 +341,31 @@ __device__ __forceinline__ void tc_combine_body(const FastView& f, int64_t a) {
                                    f.tc_xe[(size_t)tau * f.tc_nblk + a + c] - 39);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-        if (lane == 0) colterm[tau] = sum * 1.0001f;
+        if (lane == 0) colterm[tau] = 1.25f * sum * 1.0001f;
     }
     const size_t stride = (size_t)f.tc_ng * 64 * 128;
     const float2* part = f.tc_part + (size_t)tau * f.tc_nch * stride + p;
-    dfloat r = {0.f, 0.f};
+    // four interleaved chains (chunk c into chain c % 4), then
+    // (chain 0 + chain 1) + (chain 2 + chain 3)
+    dfloat ch[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     float mag = 0.f;
-    for (int c0 = 0; c0 < f.tc_nch; c0 += 8) {
-        float2 v[8];
+    for (int c0 = 0; c0 < f.tc_nch; c0 += kCombBatch) {
+        float2 v[kCombBatch];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)   // issue the loads, then add in order
+        for (int k = 0; k < kCombBatch; ++k)   // issue the loads, then add in order
             v[k] = c0 + k < f.tc_nch ? __ldcg(part + (size_t)(c0 + k) * stride)
                                      : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < kCombBatch; ++k)
             if (c0 + k < f.tc_nch) {
-                r = df_add_acc(r, dfloat{v[k].x, v[k].y});
-                mag += fabsf(r.hi);
+                dfloat& a = ch[k & 3];   // kCombBatch is a multiple of 4
+                a = df_add_acc(a, dfloat{v[k].x, v[k].y});
+                mag += fabsf(a.hi);
             }
     }
+    const dfloat s01 = df_add_acc(ch[0], ch[1]), s23 = df_add_acc(ch[2], ch[3]);
+    const dfloat r = df_add_acc(s01, s23);
+    mag += fabsf(s01.hi) + fabsf(s23.hi) + fabsf(r.hi);
     dfloat* out = tau == 0 ? f.P : (tau == 1 ? f.Q : f.R);
     if (p < f.n_pos) out[p] = r;
     __syncthreads();

@@ -71,9 +71,9 @@ struct FastPlan {
 
 struct dfloat;  // df.cuh
 
-// Tensor-core correlation tables (kernels_tc.cu): 7-bit slices per operand,
+// Tensor-core correlation tables (kernels_tc.cu): 8-bit slices per operand,
 // taps per chunk.
-constexpr int kTcSlices = 7;
+constexpr int kTcSlices = 6;
 constexpr int kTcK = 128;
 
 // u1 boxes: at most kBoxMax boxes per tile, kBoxTerms Taylor terms per box.
