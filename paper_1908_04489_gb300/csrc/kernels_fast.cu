@@ -265,42 +265,94 @@ struct Eval {
     float beta;   // bound on |gv - serial FP64 cost|
 };
 
+// The table identity at cell p (positions p and p + 1) as a quadratic in the
+// cell fraction t:
+//   S = A0 + t (A1 + t A2),  A0 = W2 + 2 P_p + Q_p,
+//   A1 = 2 (P_{p+1} - P_p) + 2 (R_p - Q_p),  A2 = Q_p + Q_{p+1} - 2 R_p,
+// in double-float, and B, the cell's bound on |table S - serial FP64 S| at
+// any t in [0, 1]: the tables' own error (tc_bt of the cell's columns), the
+// serial path's rounding beta_rel M and beta_abs (2 sqrt(M) + 1) with
+// M = (sqrt(W2) + max(sqrt(Q_p), sqrt(Q_{p+1})))^2, which bounds the sum of
+// |terms| of the w quadrature (Cauchy-Schwarz), and the rounding of the
+// quadratic itself from the actual magnitudes (double-float additions err by
+// <= 2 u^2 (|a| + |b|), products by <= 5 u^2 |a b|, u = 2^-24; t is exact):
+//   coefficients  2 (W2 + 4|P_p| + 2 Q_p) + 8 (|P_p| + |P_{p+1}| + |R_p| + Q_p)
+//                 + 4 (Q_p + Q_{p+1} + |R_p|),
+//   Horner and the sum with the control term
+//                 5 |A2| + 7 (|A1| + |A2|) + 4 (|A0| + |A1| + |A2|),  times u^2.
+struct Coef {
+    dfloat a0, a1, a2;
+    float b;
+};
+
+__device__ __forceinline__ dfloat df_x2(dfloat v) { return {2.0f * v.hi, 2.0f * v.lo}; }
+
+__device__ __forceinline__ Coef coef_of(const FastView& f, int64_t p) {
+    const dfloat P0 = f.P[p], P1 = f.P[p + 1];
+    const dfloat Q0 = f.Q[p], Q1 = f.Q[p + 1];
+    const dfloat R0 = f.R[p];
+    Coef c;
+    c.a0 = df_add(dfloat{f.W2hi, f.W2lo}, df_add(df_x2(P0), Q0));
+    c.a1 = df_add(df_add(df_x2(P1), df_neg(df_x2(P0))), df_add(df_x2(R0), df_neg(df_x2(Q0))));
+    c.a2 = df_add(df_add(Q0, Q1), df_neg(df_x2(R0)));
+    const float q0 = fmaxf(Q0.hi, 0.f), q1 = fmaxf(Q1.hi, 0.f);
+    const float rm = (f.sqrtW2 + fmaxf(sqrtf(q0), sqrtf(q1))) * 1.0001f;
+    const float M = rm * rm * 1.0001f;
+    const int64_t a1 = p >> 7, a2 = (p + 1) >> 7;
+    const float bt = f.tc_bt[a1] + (a2 != a1 ? f.tc_bt[a2] : 0.f);
+    const float p0 = fabsf(P0.hi), p1 = fabsf(P1.hi), r0 = fabsf(R0.hi);
+    const float b0 = fabsf(c.a0.hi), b1 = fabsf(c.a1.hi), b2 = fabsf(c.a2.hi);
+    const float e_coef = 2.0f * (f.W2hi + 4.0f * p0 + 2.0f * q0) +
+                         8.0f * (p0 + p1 + r0 + q0) + 4.0f * (q0 + q1 + r0);
+    const float e_eval = 5.0f * b2 + 7.0f * (b1 + b2) + 4.0f * (b0 + b1 + b2);
+    c.b = (bt + f.beta_rel * M + f.beta_abs * (2.0f * rm + 1.0f) +
+           1.25f * 1.01f * 0x1p-48f * (e_coef + e_eval)) * 1.0001f;
+    return c;
+}
+
+// g(u; x_i) = k^2 (u - x_i)^2 + S from the cell's quadratic; the bound adds
+// the control term's rounding (k |u - x_i| = sqrt of the control term).
+__device__ __forceinline__ Eval eval_poly(const Geom& g, const FastView& f, int64_t i,
+                                          int64_t nu, dfloat t, const Coef& c) {
+    const dfloat S = df_add(c.a0, df_mul(t, df_add(c.a1, df_mul(t, c.a2))));
+    const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
+    const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
+    const dfloat gv = df_add(ctl, S);
+    const float beta = c.b + 3.0e-13f * fabsf(ctl.hi) +
+                       f.beta_ctl * (f.k_f * fabsf(a.hi) * 1.0001f) + 4.0e-16f * fabsf(gv.hi);
+    return {gv, beta};
+}
+
+// Outside the tables (rare): the serial cost, the bound covering its rounding
+// to double-float.
+__device__ __forceinline__ Eval eval_outside(const Geom& g, const FastView& f, int64_t i,
+                                             int64_t nu) {
+    const double v = exact_cost_lane(g, f, i, nu);
+    return {df_from_double(v), 4.0e-15f * (float)fabs(v) + FLT_MIN};
+}
+
+// Screened cost of candidate nu for x0 point i from the stored cell
+// coefficients (search).
 __device__ __forceinline__ Eval eval_table(const Geom& g, const FastView& f,
                                            int64_t i, int64_t nu) {
     const int64_t cell = nu >> g.shift;
     const int64_t p = cell - f.c_lo;
-    if (p < 0 || p + 1 >= f.n_pos) {
-        // outside the tables (rare): serial cost, bound covers its rounding
-        // to double-float
-        const double v = exact_cost_lane(g, f, i, nu);
-        return {df_from_double(v), 4.0e-15f * (float)fabs(v) + FLT_MIN};
-    }
-    const int64_t frac = nu - cell * g.one;
-    const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
-    const dfloat omt = df_add_f(df_neg(t), 1.0f);
-    const dfloat P0 = f.P[p], P1 = f.P[p + 1];
-    const dfloat Q0 = f.Q[p], Q1 = f.Q[p + 1];
-    const dfloat R0 = f.R[p];
-    dfloat lin = df_add(df_mul(omt, P0), df_mul(t, P1));
-    lin = {2.0f * lin.hi, 2.0f * lin.lo};
-    const dfloat to = df_mul(t, omt);
-    dfloat S = df_add(dfloat{f.W2hi, f.W2lo}, lin);
-    S = df_add(S, df_mul(df_mul(omt, omt), Q0));
-    S = df_add(S, df_mul(dfloat{2.0f * to.hi, 2.0f * to.lo}, R0));
-    S = df_add(S, df_mul(df_mul(t, t), Q1));
-    const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
-    const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
-    const dfloat gv = df_add(ctl, S);
-    const float rm = f.sqrtW2 + omt.hi * sqrtf(fmaxf(Q0.hi, 0.f)) +
-                     t.hi * sqrtf(fmaxf(Q1.hi, 0.f));
-    const float M = rm * rm * 1.0001f;
-    // table error: the column bound, or both columns' at a column boundary
-    const int64_t a1 = p >> 7, a2 = (p + 1) >> 7;
-    const float bt = f.tc_bt[a1] + (a2 != a1 ? f.tc_bt[a2] : 0.f);
-    const float beta = bt + f.beta_rel * M + f.beta_abs * (2.0f * rm + 1.0f) +
-                       3.0e-13f * fabsf(ctl.hi) + f.beta_ctl * sqrtf(fabsf(ctl.hi)) +
-                       4.0e-16f * fabsf(gv.hi);
-    return {gv, beta};
+    if (p < 0 || p + 1 >= f.n_pos) return eval_outside(g, f, i, nu);
+    const dfloat t = df_mul_f(df_from_i64(nu - cell * g.one), f.inv_one_f);
+    const Coef c{f.C0[p], f.C1[p], f.C2[p], f.Cb[p]};
+    return eval_poly(g, f, i, nu, t, c);
+}
+
+// The same cost with the cell coefficients formed from the tables (J, which
+// runs beside the pass that stores them); the same arithmetic, hence the
+// same value.
+__device__ __forceinline__ Eval eval_table_direct(const Geom& g, const FastView& f,
+                                                  int64_t i, int64_t nu) {
+    const int64_t cell = nu >> g.shift;
+    const int64_t p = cell - f.c_lo;
+    if (p < 0 || p + 1 >= f.n_pos) return eval_outside(g, f, i, nu);
+    const dfloat t = df_mul_f(df_from_i64(nu - cell * g.one), f.inv_one_f);
+    return eval_poly(g, f, i, nu, t, coef_of(f, p));
 }
 
 // lanes of this thread's group of G (groups may diverge from each other)
@@ -807,7 +859,7 @@ __device__ __forceinline__ bool J_partial_body(const Geom& g, const FastView& f,
                                                double* J_out) {
     const int64_t i = bx * kJThreads + threadIdx.x;
     double v = 0.0;
-    if (i < g.n_x) v = px[i] * df_to_double(eval_table(g, f, i, nu[i]).gv);
+    if (i < g.n_x) v = px[i] * df_to_double(eval_table_direct(g, f, i, nu[i]).gv);
     red[threadIdx.x] = v;
     __syncthreads();
     for (int s = kJThreads / 2; s > 0; s >>= 1) {
@@ -837,13 +889,30 @@ __device__ __forceinline__ bool J_partial_body(const Geom& g, const FastView& f,
     return true;
 }
 
+// Cell coefficients of the new tables for the next search (blocks after the
+// J blocks of the same launch).
+__device__ __forceinline__ void cells_body(const FastView& f, int64_t bx) {
+    const int64_t p = bx * kJThreads + threadIdx.x;
+    if (p + 1 >= f.n_pos) return;
+    const Coef c = coef_of(f, p);
+    f.C0[p] = c.a0;
+    f.C1[p] = c.a1;
+    f.C2[p] = c.a2;
+    f.Cb[p] = c.b;
+}
+
 // J into *out; also empties the deferred-search list for the next sweep.
+// Blocks from J_blocks on store the cell coefficients.
 __global__ void __launch_bounds__(kJThreads) k_J_partial(Geom g, FastView f,
                                                          const double* __restrict__ px,
                                                          const int64_t* __restrict__ nu,
                                                          double* out) {
     __shared__ double red[kJThreads];
     __shared__ int last;
+    if (blockIdx.x >= f.J_blocks) {
+        cells_body(f, blockIdx.x - f.J_blocks);
+        return;
+    }
     double J;
     if (J_partial_body(g, f, px, nu, red, &last, blockIdx.x, &J)) {
         *out = J;
@@ -898,6 +967,10 @@ __global__ void __launch_bounds__(kJThreads) kb_J_partial(InstDev* insts,
     __shared__ double red[kJThreads];
     __shared__ int last;
     const BlockRef r = stage(insts, map, sd);
+    if (r.local >= sd.f.J_blocks) {
+        cells_body(sd.f, r.local - sd.f.J_blocks);
+        return;
+    }
     double J;
     if (J_partial_body(sd.g, sd.f, sd.px, sd.nu[sd.cur ^ 1], red, &last, r.local, &J)) {
         InstDev& d = insts[r.inst];
@@ -925,6 +998,7 @@ void fast_plan(const Geom& g, FastPlan* fp) {
     fp->n_e = fp->n_pos + g.n_w + 1;
     u1_plan(g, 32, fp);
     fp->J_blocks = (g.n_x + kJThreads - 1) / kJThreads;
+    fp->cell_blocks = (fp->n_pos - 1 + kJThreads - 1) / kJThreads;
     tc_plan(g, fp);
 }
 
@@ -979,7 +1053,7 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
         case kBTabPart: return tc_table_blocks(fp);
         case kBTabComb: return tc_combine_blocks(fp);
         case kBBuildE: return tc_build_E_blocks(g, fp);
-        case kBJPart: return fp.J_blocks;
+        case kBJPart: return fp.J_blocks + fp.cell_blocks;
     }
     return 0;
 }
@@ -1028,7 +1102,7 @@ void launch_J_fast(const Geom& g, const FastView& f, const double* px,
                    const int64_t* nu, double* out, cudaStream_t s, Prof* prof) {
     cudaEvent_t ev;
     int k = prof ? prof->begin("J", &ev) : -1;
-    k_J_partial<<<(unsigned)f.J_blocks, kJThreads, 0, s>>>(g, f, px, nu, out);
+    k_J_partial<<<(unsigned)(f.J_blocks + f.cell_blocks), kJThreads, 0, s>>>(g, f, px, nu, out);
     if (prof) prof->end(k, ev);
 }
 

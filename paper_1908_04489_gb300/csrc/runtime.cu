@@ -183,7 +183,7 @@ size_t inst_bytes(const Geom& g, int precision) {
         FastPlan fp;
         fast_plan(g, &fp);
         size_t tcs[7];
-        b += 3 * rnd(8 * (size_t)fp.n_pos) + rnd(8 * (size_t)fp.n_e) +
+        b += 6 * rnd(8 * (size_t)fp.n_pos) + rnd(4 * (size_t)fp.n_pos) + rnd(8 * (size_t)fp.n_e) +
              3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
              rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 3 * rnd(4) + rnd(kDeferRecBytes * nx) + rnd(32) +
              tc_bytes(fp, 256, tcs) + rnd(4) +
@@ -206,12 +206,11 @@ static void fast_bounds(ucp_inst* in, double B) {
     FastView& f = in->fv;
     const double u = 0x1p-53, uf2 = 0x1p-48;
     // the plain path's sum in the fixed order (a term passes through at most
-    // 31 additions in its chunk and one per level) + double-float evaluation
-    // of the identity; the tables' own error is bounded per column on the
-    // device (tc_bt)
+    // 31 additions in its chunk and one per level); the tables' own error and
+    // the rounding of the cell quadratic are bounded per cell on the device
     const double levels = ceil(log2((double)sum_chunks(g.n_w) + 1.0));
     const double ser = (kSumChunk - 1 + levels + 1) * u;
-    const double rel = ser + 60.0 * uf2;
+    const double rel = ser;
     f.beta_rel = (float)(1.25 * rel);
     // rounding of grid positions, of E = U - y and of the residuals of both
     // evaluations: |d(residual)| <= u A
@@ -242,6 +241,10 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.Ud = d.Ud;
     f.coarse = d.coarse;
     const size_t nx = (size_t)g.n_x, nw = (size_t)g.n_w;
+    f.C0 = (dfloat*)A.get(8 * (size_t)f.n_pos);
+    f.C1 = (dfloat*)A.get(8 * (size_t)f.n_pos);
+    f.C2 = (dfloat*)A.get(8 * (size_t)f.n_pos);
+    f.Cb = (float*)A.get(4 * (size_t)f.n_pos);
     f.P = (dfloat*)A.get(8 * (size_t)f.n_pos);
     f.Q = (dfloat*)A.get(8 * (size_t)f.n_pos);
     f.R = (dfloat*)A.get(8 * (size_t)f.n_pos);
@@ -270,7 +273,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.n_pairs = (int64_t*)A.get(32);
     const bool u1_ok = u1_carve(
         g, &f, [](void* a, size_t n) { return ((Arena*)a)->get(n); }, &A);
-    if (!f.P || !f.Q || !f.R || !f.E || !f.a || !f.phidf || !f.wdf ||
+    if (!f.C0 || !f.C1 || !f.C2 || !f.Cb || !f.P || !f.Q || !f.R || !f.E || !f.a || !f.phidf || !f.wdf ||
         !f.prior || !f.t64 || !u1_ok || !f.Jpart || !f.tc_h || !f.tc_he || !f.tc_x ||
         !f.tc_xe || !f.tc_part || !f.tc_bt || !f.tc_err || !f.J_done || !f.W2_dev ||
         !f.n_exact || !f.n_tier2 || !f.defer_cnt || !f.defer_list || !f.n_pairs) {
@@ -291,6 +294,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.delta_lo = dd.lo;
     f.kk_hi = kd.hi;
     f.kk_lo = kd.lo;
+    f.k_f = (float)g.k * 1.0000001f;
     f.inv_one_f = (float)ldexp(1.0, -g.shift);
     in->fbound = 0.0;
     fast_bounds(in, value_bound(g, 0.0));

@@ -63,6 +63,7 @@ struct FastPlan {
     int64_t n_runs;    // runs covering the y grid
     int64_t r_blocks;  // run blocks of the u1 kernel (kU1Runs runs each)
     int64_t J_blocks;  // blocks of the J reduction
+    int64_t cell_blocks;  // blocks storing the cell coefficients (same launch)
     int64_t tc_na;     // table columns of the tensor-core build (128 positions each)
     int tc_ng;         // column groups (64 columns, one CTA row each)
     int tc_nch;        // tap chunks (kTcK taps each)
@@ -86,6 +87,10 @@ struct FastView : FastPlan {
     const double* U;     // [n_y] u1 table
     const double* Ud;    // [n_y] U_{j+1} - U_j
     const int64_t* coarse;
+    dfloat* C0;          // [n_pos - 1] cell quadratic S = C0 + t (C1 + t C2)
+    dfloat* C1;
+    dfloat* C2;
+    float* Cb;           // [n_pos - 1] cell bound (tables, identity, E rounding)
     dfloat* P;           // [n_pos] correlation tables (double-float)
     dfloat* Q;
     dfloat* R;
@@ -132,8 +137,9 @@ struct FastView : FastPlan {
     float step_hi, step_lo;   // delta 2^-shift as double-float
     float delta_hi, delta_lo; // delta as double-float
     float kk_hi, kk_lo;       // k^2 as double-float
+    float k_f;                // k (FP32, bound terms)
     float inv_one_f;          // 2^-shift
-    float beta_rel;      // |table cost - serial cost| <= tc_bt(cell) + beta_rel M
+    float beta_rel;      // |table cost - serial cost| <= Cb = tc_bt(cell) + beta_rel M
     float beta_abs;      //   + beta_abs (2 sqrt(M) + 1)
     float beta_ctl;      //   + beta_ctl sqrt(control term) + ...
     float beta2_rel;     // direct double-float quadrature: beta2_rel S + ...
