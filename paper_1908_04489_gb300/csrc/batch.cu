@@ -50,10 +50,6 @@ static int run_slot(int R) {
     return R >= 16 ? 4 : (R >= 8 ? 3 : (R >= 4 ? 2 : (R >= 2 ? 1 : 0)));
 }
 
-static int refine_slot(int G) {
-    return G >= 32 ? 4 : (G >= 16 ? 3 : (G >= 8 ? 2 : (G >= 4 ? 1 : 0)));
-}
-
 static int defer_blocks_per_inst(size_t n) {
     return n >= 16 ? kDeferBlocksBatch : (int)(64 / n);
 }
@@ -74,7 +70,7 @@ ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
 ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
                           cudaStream_t s) {
     const size_t n = members.size();
-    std::vector<BlockRef> maps[kBKinds], smaps[5], mmaps[5], dmaps[5];
+    std::vector<BlockRef> maps[kBKinds], smap, mmaps[5], dmap;
     const int defer_blocks = defer_blocks_per_inst(n);
     for (size_t k = 0; k < n; ++k) {
         const ucp_inst* in = members[k];
@@ -82,33 +78,27 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
             const int64_t nb = batch_blocks(in->g, in->fv, kind);
             for (int64_t x = 0; x < nb; ++x) maps[kind].push_back({(int32_t)k, (int32_t)x});
         }
-        std::vector<BlockRef>& sm = smaps[refine_slot(in->g.n_refine)];
         const int64_t ns = batch_blocks(in->g, in->fv, kBSearch);
-        for (int64_t x = 0; x < ns; ++x) sm.push_back({(int32_t)k, (int32_t)x});
-        std::vector<BlockRef>& dm = dmaps[refine_slot(in->g.n_refine)];
-        for (int x = 0; x < defer_blocks; ++x) dm.push_back({(int32_t)k, x});
+        for (int64_t x = 0; x < ns; ++x) smap.push_back({(int32_t)k, (int32_t)x});
+        for (int x = 0; x < defer_blocks; ++x) dmap.push_back({(int32_t)k, x});
         std::vector<BlockRef>& mm = mmaps[run_slot(in->fv.run)];
         const int64_t nm = batch_mmse_blocks(in->g, in->fv);
         for (int64_t x = 0; x < nm; ++x) mm.push_back({(int32_t)k, (int32_t)x});
     }
     bs.host_maps.clear();
-    size_t off[kBKinds], soff[5], moff[5], doff[5];
+    size_t off[kBKinds], moff[5];
     for (int kind = 0; kind < kBKinds; ++kind) {
         off[kind] = bs.host_maps.size();
         bs.host_maps.insert(bs.host_maps.end(), maps[kind].begin(), maps[kind].end());
     }
-    for (int r = 0; r < 5; ++r) {
-        soff[r] = bs.host_maps.size();
-        bs.host_maps.insert(bs.host_maps.end(), smaps[r].begin(), smaps[r].end());
-    }
+    const size_t soff = bs.host_maps.size();
+    bs.host_maps.insert(bs.host_maps.end(), smap.begin(), smap.end());
     for (int r = 0; r < 5; ++r) {
         moff[r] = bs.host_maps.size();
         bs.host_maps.insert(bs.host_maps.end(), mmaps[r].begin(), mmaps[r].end());
     }
-    for (int r = 0; r < 5; ++r) {
-        doff[r] = bs.host_maps.size();
-        bs.host_maps.insert(bs.host_maps.end(), dmaps[r].begin(), dmaps[r].end());
-    }
+    const size_t doff = bs.host_maps.size();
+    bs.host_maps.insert(bs.host_maps.end(), dmap.begin(), dmap.end());
     // grow the device buffers (after the stream drains, as they may be in use)
     if (n > bs.insts_cap || bs.host_maps.size() > bs.maps_cap) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return UCP_E_CUDA;
@@ -137,13 +127,13 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
         bl.map[kind] = bs.maps + off[kind];
         bl.n_blocks[kind] = (int64_t)maps[kind].size();
     }
+    bl.search_map = bs.maps + soff;
+    bl.search_blocks = (int64_t)smap.size();
+    bl.defer_map = bs.maps + doff;
+    bl.defer_blocks = (int64_t)dmap.size();
     for (int r = 0; r < 5; ++r) {
-        bl.search_map[r] = bs.maps + soff[r];
-        bl.search_blocks[r] = (int64_t)smaps[r].size();
         bl.mmse_map[r] = bs.maps + moff[r];
         bl.mmse_blocks[r] = (int64_t)mmaps[r].size();
-        bl.defer_map[r] = bs.maps + doff[r];
-        bl.defer_blocks[r] = (int64_t)dmaps[r].size();
     }
     return batchset_refresh(bs, members, s);
 }

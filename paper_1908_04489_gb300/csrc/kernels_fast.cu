@@ -499,7 +499,13 @@ __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int 
 // Resolve one stage of the list: the carried winner (lane 0) plus positions
 // p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
 // costs over all of them.
-constexpr int kKeep = kTieBatch;   // candidates per lane whose screened bounds are kept
+constexpr int kKeep = 12;   // candidates per lane whose screened bounds are kept
+// doubles of shared scratch per lane (lower ends kept; exact-tier terms)
+constexpr int kGroupScratch = kKeep > kTieBatch ? kKeep : kTieBatch;
+// lanes per x0 point: the screening search, and the deferred (block-
+// cooperative) search, whose second tier takes up to kCoopG members at once
+constexpr int kFastG = 8;
+constexpr int kCoopG = 16;
 
 // How resolve() settles a stage with several values still in play:
 // kTierDefer gives up (the x0 point is searched again by the deferred
@@ -716,7 +722,8 @@ __device__ __forceinline__ void search_one(const Geom& g, const FastView& f,
     const int64_t* coarse = f.coarse;
     int32_t* cnt = active && writer ? n_exact : nullptr;
     const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
-    const int half = G / 2;
+    const int R = g.n_refine;   // candidates per refinement level
+    const int half = R / 2;
     Best carried = best;
     int stage = stage0;
     for (; stage <= g.n_levels; ++stage) {
@@ -728,8 +735,8 @@ __device__ __forceinline__ void search_one(const Geom& g, const FastView& f,
         } else {
             const int64_t h = g.q << (g.bits * (g.n_levels - stage));
             const int64_t centre = best.nu;
-            const int pos = n0 + (stage - 1) * G;
-            best = resolve<G, Mode>(g, f, ic, lane, best, pos, pos + G,
+            const int pos = n0 + (stage - 1) * R;
+            best = resolve<G, Mode>(g, f, ic, lane, best, pos, pos + R,
                                     [&](int p) {
                                         const int k = p - pos;
                                         const int64_t m = k < half ? k - half : k - half + 1;
@@ -758,7 +765,7 @@ __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
                                             int32_t* n_exact, double* tie_smem,
                                             int64_t bx) {
     const int64_t i = (bx * blockDim.x + threadIdx.x) / G;
-    double* tie_terms = tie_smem + (threadIdx.x / G) * (kTieBatch * G);
+    double* tie_terms = tie_smem + (threadIdx.x / G) * (kGroupScratch * G);
     const Best none{{FLT_MAX, 0.f}, 0.f, INT_MAX, 0, false, 0.0};
     search_one<G, kTierDefer>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_terms,
                               nullptr, i, i < g.n_x, true, 0, none);
@@ -777,7 +784,7 @@ __device__ __forceinline__ void search_deferred_body(const Geom& g, const FastVi
                                                      CoopSmem& cs, int64_t bx,
                                                      int64_t nbx) {
     const int n = *(volatile int32_t*)f.defer_cnt;
-    double* tie_terms = tie_smem + (threadIdx.x / G) * (kTieBatch * G);
+    double* tie_terms = tie_smem + (threadIdx.x / G) * (kGroupScratch * G);
     const DeferRec* rec = (const DeferRec*)f.defer_list;
     for (int64_t k = bx; k < n; k += nbx) {
         const DeferRec r = rec[k];
@@ -787,30 +794,28 @@ __device__ __forceinline__ void search_deferred_body(const Geom& g, const FastVi
     }
 }
 
-template <int G>
 __global__ void __launch_bounds__(kSearchT, 6) k_search_fast(Geom g, FastView f,
                                                      const int64_t* __restrict__ nu_pre,
                                                      int64_t* __restrict__ nu_out,
                                                      int32_t* __restrict__ idx_out,
                                                      int32_t* n_exact) {
-    __shared__ double tie_smem[kSearchT * kTieBatch];
-    search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
+    __shared__ double tie_smem[kSearchT * kGroupScratch];
+    search_body<kFastG>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
 }
 
 constexpr int kDeferBlocks = 64;        // blocks of the deferred search (one instance)
 
-template <int G>
 __global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
                                                            const int64_t* __restrict__ nu_pre,
                                                            int64_t* __restrict__ nu_out,
                                                            int32_t* __restrict__ idx_out,
                                                            int32_t* n_exact) {
-    __shared__ double tie_smem[kCoopT * kTieBatch];
+    __shared__ double tie_smem[kCoopT * kGroupScratch];
     __shared__ CoopSmem cs;
     if (threadIdx.x == 0) cs.scratch = tie_smem;
     __syncthreads();
-    search_deferred_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, cs,
-                            blockIdx.x, gridDim.x);
+    search_deferred_body<kCoopG>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, cs,
+                                 blockIdx.x, gridDim.x);
 }
 
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
@@ -937,26 +942,24 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
     return r;
 }
 
-template <int G>
 __global__ void __launch_bounds__(kSearchT, 5) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
-    __shared__ double tie_smem[kSearchT * kTieBatch];
-    search_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
-                   sd.f.n_exact, tie_smem, r.local);
+    __shared__ double tie_smem[kSearchT * kGroupScratch];
+    search_body<kFastG>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
+                        sd.f.n_exact, tie_smem, r.local);
 }
 
-template <int G>
 __global__ void __launch_bounds__(kCoopT) kb_search_deferred(const InstDev* insts,
                                                             const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
-    __shared__ double tie_smem[kCoopT * kTieBatch];
+    __shared__ double tie_smem[kCoopT * kGroupScratch];
     __shared__ CoopSmem cs;
     if (threadIdx.x == 0) cs.scratch = tie_smem;
     __syncthreads();
-    search_deferred_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
-                            sd.f.n_exact, tie_smem, cs, r.local, sd.defer_blocks);
+    search_deferred_body<kCoopG>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
+                                 sd.f.n_exact, tie_smem, cs, r.local, sd.defer_blocks);
 }
 
 // Last kernel of a batched sweep: J into its history slot, then the sweep
@@ -1010,42 +1013,15 @@ void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
 
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
                         int64_t* nu_out, int32_t* idx, cudaStream_t s) {
-    const int64_t threads = g.n_x * (int64_t)g.n_refine;
-    const int bs = kSearchT;
-#define UCP_FAST_CASE(G)                                                   \
-    case G:                                                                \
-        k_search_fast<G><<<blocks(threads, bs), bs, 0, s>>>(g, f, nu_in,   \
-                                                          nu_out, idx,     \
-                                                          f.n_exact);      \
-        break;
-    switch (g.n_refine) {
-        UCP_FAST_CASE(2)
-        UCP_FAST_CASE(4)
-        UCP_FAST_CASE(8)
-        UCP_FAST_CASE(16)
-        UCP_FAST_CASE(32)
-        default: break;
-    }
-#undef UCP_FAST_CASE
-#define UCP_DEFER_CASE(G)                                                          \
-    case G:                                                                        \
-        k_search_deferred<G><<<kDeferBlocks, kCoopT, 0, s>>>(g, f, nu_in, nu_out,   \
-                                                            idx, f.n_exact);       \
-        break;
-    switch (g.n_refine) {
-        UCP_DEFER_CASE(2)
-        UCP_DEFER_CASE(4)
-        UCP_DEFER_CASE(8)
-        UCP_DEFER_CASE(16)
-        UCP_DEFER_CASE(32)
-        default: break;
-    }
-#undef UCP_DEFER_CASE
+    const int64_t threads = g.n_x * (int64_t)kFastG;
+    k_search_fast<<<blocks(threads, kSearchT), kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx,
+                                                                  f.n_exact);
+    k_search_deferred<<<kDeferBlocks, kCoopT, 0, s>>>(g, f, nu_in, nu_out, idx, f.n_exact);
 }
 
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
-        case kBSearch: return (g.n_x * g.n_refine + kSearchT - 1) / kSearchT;
+        case kBSearch: return (g.n_x * kFastG + kSearchT - 1) / kSearchT;
         case kBTile:
         case kBBox:
         case kBRun: return u1_batch_blocks(g, fp, kind);
@@ -1065,30 +1041,10 @@ void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
 
 void launch_batch_search(const BatchLaunch& bl, cudaStream_t s) {
     const InstDev* d = bl.insts;
-    for (int gi = 0; gi < 5; ++gi) {
-        if (bl.search_blocks[gi] == 0) continue;
-        const unsigned nb = (unsigned)bl.search_blocks[gi];
-        const BlockRef* m = bl.search_map[gi];
-        switch (gi) {
-            case 0: kb_search<2><<<nb, kSearchT, 0, s>>>(d, m); break;
-            case 1: kb_search<4><<<nb, kSearchT, 0, s>>>(d, m); break;
-            case 2: kb_search<8><<<nb, kSearchT, 0, s>>>(d, m); break;
-            case 3: kb_search<16><<<nb, kSearchT, 0, s>>>(d, m); break;
-            default: kb_search<32><<<nb, kSearchT, 0, s>>>(d, m); break;
-        }
-    }
-    for (int gi = 0; gi < 5; ++gi) {
-        if (bl.defer_blocks[gi] == 0) continue;
-        const unsigned nb = (unsigned)bl.defer_blocks[gi];
-        const BlockRef* m = bl.defer_map[gi];
-        switch (gi) {
-            case 0: kb_search_deferred<2><<<nb, kCoopT, 0, s>>>(d, m); break;
-            case 1: kb_search_deferred<4><<<nb, kCoopT, 0, s>>>(d, m); break;
-            case 2: kb_search_deferred<8><<<nb, kCoopT, 0, s>>>(d, m); break;
-            case 3: kb_search_deferred<16><<<nb, kCoopT, 0, s>>>(d, m); break;
-            default: kb_search_deferred<32><<<nb, kCoopT, 0, s>>>(d, m); break;
-        }
-    }
+    if (bl.search_blocks)
+        kb_search<<<(unsigned)bl.search_blocks, kSearchT, 0, s>>>(d, bl.search_map);
+    if (bl.defer_blocks)
+        kb_search_deferred<<<(unsigned)bl.defer_blocks, kCoopT, 0, s>>>(d, bl.defer_map);
 }
 
 void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s) {

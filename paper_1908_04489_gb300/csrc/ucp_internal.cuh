@@ -180,12 +180,12 @@ struct BatchLaunch {
     int n_inst;
     const BlockRef* map[kBKinds];  // per kernel kind (see BatchKind)
     int64_t n_blocks[kBKinds];
-    const BlockRef* search_map[5]; // search per n_refine 2, 4, 8, 16, 32
-    int64_t search_blocks[5];
+    const BlockRef* search_map;    // screening search
+    int64_t search_blocks;
     const BlockRef* mmse_map[5];   // u1 main kernel per run length 1, 2, 4, 8, 16
     int64_t mmse_blocks[5];
-    const BlockRef* defer_map[5];  // deferred search per n_refine
-    int64_t defer_blocks[5];
+    const BlockRef* defer_map;     // deferred (near-tie) search
+    int64_t defer_blocks;
 };
 
 // Blocks of the deferred (near-tie) search per instance of a batch of 16 or
