@@ -499,9 +499,10 @@ __device__ Best resolve_serial(const Geom& g, const FastView& f, int64_t i, int 
 // Resolve one stage of the list: the carried winner (lane 0) plus positions
 // p0 + lane + k G < p_end.  Returns the first minimum of the serial FP64
 // costs over all of them.
-constexpr int kKeep = 12;   // candidates per lane whose screened bounds are kept
-// doubles of shared scratch per lane (lower ends kept; exact-tier terms)
-constexpr int kGroupScratch = kKeep > kTieBatch ? kKeep : kTieBatch;
+constexpr int kKeep = 12;   // candidates per lane whose screened costs are kept
+// doubles of shared scratch per lane: kept costs (double-float) and bounds
+// (float), or exact-tier terms
+constexpr int kGroupScratch = kKeep * 3 / 2 > kTieBatch ? kKeep * 3 / 2 : kTieBatch;
 // lanes per x0 point: the screening search, and the deferred (block-
 // cooperative) search, whose second tier takes up to kCoopG members at once
 constexpr int kFastG = 8;
@@ -529,22 +530,23 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
                         const Best& best, int p0, int p_end, CandFn cand,
                         int32_t* n_exact, double* tie_terms, CoopSmem* cs) {
     const bool have_best = best.pos != INT_MAX;
-    // 1. smallest upper end; the lower ends of this lane's first kKeep
-    // candidates are kept (the rest are evaluated again below)
+    // 1. smallest upper end; the costs and bounds of this lane's first kKeep
+    // candidates are kept (the rest are evaluated again below), in this
+    // lane's column of the group's shared scratch (free until the third
+    // tier, which runs after the last use)
     dfloat hi = {FLT_MAX, 0.f};
     if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
-    // kept in this lane's column of the group's shared scratch (free until
-    // the third tier, which runs after the last use)
-    dfloat* lo_k = (dfloat*)tie_terms + lane;   // lo_k[k * G]
-#pragma unroll 1
+    dfloat* gv_k = (dfloat*)tie_terms;                 // gv_k[k * G + lane]
+    float* be_k = (float*)(gv_k + kKeep * G);          // be_k[k * G + lane]
+#pragma unroll 2
     for (int k = 0; k < kKeep; ++k) {
-        lo_k[k * G] = {FLT_MAX, 0.f};
         const int p = p0 + lane + k * G;
         if (p < p_end) {
             const Eval e = eval_table(g, f, i, cand(p));
             const dfloat h = df_pm(e.gv, e.beta);
             if (df_lt(h, hi)) hi = h;
-            lo_k[k * G] = df_pm(e.gv, -e.beta);
+            gv_k[k * G + lane] = e.gv;
+            be_k[k * G + lane] = e.beta;
         }
     }
     for (int p = p0 + lane + kKeep * G; p < p_end; p += G) {
@@ -563,7 +565,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
 #pragma unroll 1
     for (int k = 0; k < kKeep; ++k) {
         const int p = p0 + lane + k * G;
-        if (p < p_end && !df_lt(hi, lo_k[k * G])) {
+        if (p < p_end && !df_lt(hi, df_pm(gv_k[k * G + lane], -be_k[k * G + lane]))) {
             const int64_t nu = cand(p);
             vmin = nu < vmin ? nu : vmin;
             vmax = nu > vmax ? nu : vmax;
@@ -583,8 +585,14 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
     vmax = gmax_i64<G>(vmax);
     pmin = gmin_i32<G>(pmin);
     if (vmin == vmax) {
-        // one value in play: its first occurrence wins
+        // one value in play: its first occurrence wins, with the cost its
+        // lane kept (every candidate of that value has the same cost)
         if (have_best && pmin == best.pos) return best;
+        const int kk = (pmin - p0) / G, owner = (pmin - p0) % G;
+        if (kk < kKeep) {
+            __syncwarp(group_mask<G>());
+            return {gv_k[kk * G + owner], be_k[kk * G + owner], pmin, vmin, false, 0.0};
+        }
         const Eval e = eval_table(g, f, i, vmin);
         return {e.gv, e.beta, pmin, vmin, false, 0.0};
     }
@@ -625,7 +633,8 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         const int pb = p0 + k * G;
         if (pb < p_end) {   // the same for the group
             const int p = pb + lane;
-            const bool member = p < p_end && !df_lt(hi, lo_k[k * G]);
+            const bool member = p < p_end &&
+                                !df_lt(hi, df_pm(gv_k[k * G + lane], -be_k[k * G + lane]));
             gather(pb, member, member ? cand(p) : 0);
         }
     }
