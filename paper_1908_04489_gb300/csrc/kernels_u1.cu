@@ -329,12 +329,15 @@ __device__ __forceinline__ void taylor_terms(float zeta, int& n1, int& p) {
     if (n1 < 0) n1 = p;
 }
 
-// Box share by its Taylor expansion, added to the run's sums.
-template <int R>
+// Box share by its Taylor expansion, added to the sums of targets
+// kq0 .. kq0 + TR - 1 of the run (R targets).  z and the factor E C^k of
+// target k are advanced from target 0 one step at a time, so every target
+// gets the same operations whichever thread evaluates it.
+template <int R, int TR>
 __device__ __forceinline__ void fgt_box(const FastView& f, int64_t slot, float c,
                                         float pm, float sc, dfloat y0, dfloat dl,
                                         float m_lo, int p, int n1, const dfloat* st64,
-                                        dfloat (&N)[R], dfloat (&D)[R]) {
+                                        int kq0, dfloat (&N)[TR], dfloat (&D)[TR]) {
     const dfloat* __restrict__ ca = f.box_coef + slot * (2 * kBoxTerms);
     const dfloat* __restrict__ cb = ca + kBoxTerms;
     const dfloat z0 = df_add_f(y0, -c);
@@ -347,9 +350,13 @@ __device__ __forceinline__ void fgt_box(const FastView& f, int64_t slot, float c
     // u = z s and its step delta s (scaling by a power of two is exact)
     dfloat z = {z0.hi * sc, z0.lo * sc};
     const dfloat du = {dl.hi * sc, dl.lo * sc};
-    constexpr int Q = R < 4 ? R : 4;
+    for (int k = 0; k < kq0; ++k) {
+        z = df_add(z, du);
+        E = df_mul(E, C);
+    }
+    constexpr int Q = TR < 4 ? TR : 4;
 #pragma unroll
-    for (int k0 = 0; k0 < R; k0 += Q) {
+    for (int k0 = 0; k0 < TR; k0 += Q) {
         dfloat zq[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -385,20 +392,21 @@ __device__ __forceinline__ void fgt_box(const FastView& f, int64_t slot, float c
         for (int q = 0; q < Q; ++q) {
             D[k0 + q] = df_add(D[k0 + q], df_mul(E, aD[q]));
             N[k0 + q] = df_add(N[k0 + q], df_mul(E, aN[q]));
-            if (k0 + q + 1 < R) E = df_mul(E, C);
+            if (kq0 + k0 + q + 1 < R) E = df_mul(E, C);
         }
     }
 }
 
 // Box share by the direct sum over its sources (two recurrences at a time),
-// skipping sources whose weights are all negligible.  Returns the number of
-// (source, run) pairs evaluated.
-template <int R>
+// skipping sources whose weights are all negligible, for targets kq0 .. kq0 +
+// TR - 1 of the run (the weight advanced from target 0 one step at a time).
+// Returns the number of (source, run) pairs evaluated.
+template <int R, int TR>
 __device__ __forceinline__ unsigned direct_box(const FastView& f, int64_t s0, int n,
                                                float ya, float yb, float cut,
                                                float m_lo, int64_t ybase,
-                                               const dfloat* st64, dfloat (&N)[R],
-                                               dfloat (&D)[R]) {
+                                               const dfloat* st64, int kq0,
+                                               dfloat (&N)[TR], dfloat (&D)[TR]) {
     const dfloat step = {f.step_hi, f.step_lo};
     unsigned evaluated = 0;
     int s = 0;
@@ -432,29 +440,41 @@ __device__ __forceinline__ unsigned direct_box(const FastView& f, int64_t s0, in
             w[q] = df_exp(ex, st64);
         }
         if (ns == 1) w[1] = {0.0f, 0.0f};
+        for (int k = 0; k < kq0; ++k) {
+            w[0] = df_mul(w[0], F[0]);
+            w[1] = df_mul(w[1], F[1]);
+        }
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
+        for (int k = 0; k < TR; ++k) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 float pp, pe;
                 df_mul_raw(w[q], fv[q], pp, pe);
                 N[k] = df_acc(N[k], pp, pe);
                 D[k] = df_add(D[k], w[q]);
-                if (k + 1 < R) w[q] = df_mul(w[q], F[q]);
+                if (kq0 + k + 1 < R) w[q] = df_mul(w[q], F[q]);
             }
         }
     }
     return evaluated;
 }
 
-// Block (bx, t): runs bx*kU1Runs.. (one per thread) against the boxes of
-// tile t; writes the tile's partial sums of every target of those runs.
+// Threads per run of R targets (each takes R / u1_parts<R>() consecutive ones).
+template <int R>
+constexpr int u1_parts() { return R >= 4 ? 4 : 1; }
+
+// Block (bx, t): runs bx*kU1Runs.. against the boxes of tile t, thread
+// (part, run) taking targets part * TR .. + TR - 1 of its run; writes the
+// tile's partial sums of those targets.
 template <int R>
 __device__ __forceinline__ void u1_main_body(const Geom& g, const FastView& f,
                                              dfloat* st64, int64_t bx, int64_t t) {
+    constexpr int TR = R / u1_parts<R>();
     for (int k = threadIdx.x; k < 47; k += blockDim.x) st64[k] = f.t64[k];
     __syncthreads();
-    const int64_t r0 = bx * kU1Runs + threadIdx.x;
+    const int part = threadIdx.x / kU1Runs;
+    const int kq0 = part * TR;
+    const int64_t r0 = bx * kU1Runs + threadIdx.x % kU1Runs;
     const int64_t r = r0 < f.n_runs ? r0 : f.n_runs - 1;
     const int64_t j0 = r * R;
     const float m_lo = f.run_lo[r];
@@ -464,9 +484,9 @@ __device__ __forceinline__ void u1_main_body(const Geom& g, const FastView& f,
     const dfloat dl = {f.delta_hi, f.delta_lo};
     const dfloat y0 = df_mul(df_from_i64(j0 - g.hy), dl);
     const int64_t ybase = (j0 - g.hy) * g.one;
-    dfloat N[R], D[R];
+    dfloat N[TR], D[TR];
 #pragma unroll
-    for (int k = 0; k < R; ++k) N[k] = D[k] = {0.0f, 0.0f};
+    for (int k = 0; k < TR; ++k) N[k] = D[k] = {0.0f, 0.0f};
     unsigned n_dir = 0, n_box = 0, t_df = 0, t_f32 = 0;
     const int nb = f.box_cnt[t];
     for (int k = 0; k < nb; ++k) {
@@ -493,17 +513,17 @@ __device__ __forceinline__ void u1_main_body(const Geom& g, const FastView& f,
             }
         }
         if (p >= 0) {
-            fgt_box<R>(f, slot, geo.x, geo.z, rg.w, y0, dl, m_lo, p, n1, st64, N, D);
+            fgt_box<R, TR>(f, slot, geo.x, geo.z, rg.w, y0, dl, m_lo, p, n1, st64, kq0, N, D);
             ++n_box;
             t_df += (unsigned)n1;
             t_f32 += (unsigned)(p - n1);
         } else {
-            n_dir += direct_box<R>(f, f.box_s0[slot], n, ya, yb, cut, m_lo, ybase,
-                                   st64, N, D);
+            n_dir += direct_box<R, TR>(f, f.box_s0[slot], n, ya, yb, cut, m_lo, ybase,
+                                       st64, kq0, N, D);
         }
     }
     if (r0 >= f.n_runs) return;
-    if (f.n_pairs) {
+    if (f.n_pairs && part == 0) {
         if (n_dir) atomicAdd((unsigned long long*)f.n_pairs, (unsigned long long)n_dir);
         if (n_box) {
             atomicAdd((unsigned long long*)f.n_pairs + 1, (unsigned long long)n_box);
@@ -514,10 +534,10 @@ __device__ __forceinline__ void u1_main_body(const Geom& g, const FastView& f,
     double* pN = f.partN + (size_t)t * g.n_y;
     double* pD = f.partD + (size_t)t * g.n_y;
 #pragma unroll
-    for (int k = 0; k < R; ++k)
-        if (j0 + k < g.n_y) {
-            pN[j0 + k] = df_to_double(N[k]);
-            pD[j0 + k] = df_to_double(D[k]);
+    for (int k = 0; k < TR; ++k)
+        if (j0 + kq0 + k < g.n_y) {
+            pN[j0 + kq0 + k] = df_to_double(N[k]);
+            pD[j0 + kq0 + k] = df_to_double(D[k]);
         }
 }
 
@@ -562,7 +582,7 @@ __global__ void __launch_bounds__(kRunT) k_run_shift(Geom g, FastView f) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kU1Runs) k_u1_main(Geom g, FastView f) {
+__global__ void __launch_bounds__(kU1Runs * 4) k_u1_main(Geom g, FastView f) {
     __shared__ dfloat st64[47];
     u1_main_body<R>(g, f, st64, blockIdx.x, blockIdx.y);
 }
@@ -609,7 +629,7 @@ __global__ void __launch_bounds__(kRunT) kb_run_shift(const InstDev* insts,
 }
 
 template <int R>
-__global__ void __launch_bounds__(kU1Runs) kb_u1_main(const InstDev* insts,
+__global__ void __launch_bounds__(kU1Runs * 4) kb_u1_main(const InstDev* insts,
                                                       const BlockRef* map) {
     __shared__ InstDev sd;
     __shared__ dfloat st64[47];
@@ -696,11 +716,11 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
     k = prof ? prof->begin("mmse_main", &ev) : -1;
     dim3 grid((unsigned)f.r_blocks, (unsigned)f.n_tiles);
     switch (f.run) {
-        case 16: k_u1_main<16><<<grid, kU1Runs, 0, s>>>(g, f); break;
-        case 8: k_u1_main<8><<<grid, kU1Runs, 0, s>>>(g, f); break;
-        case 4: k_u1_main<4><<<grid, kU1Runs, 0, s>>>(g, f); break;
-        case 2: k_u1_main<2><<<grid, kU1Runs, 0, s>>>(g, f); break;
-        default: k_u1_main<1><<<grid, kU1Runs, 0, s>>>(g, f); break;
+        case 16: k_u1_main<16><<<grid, kU1Runs * u1_parts<16>(), 0, s>>>(g, f); break;
+        case 8: k_u1_main<8><<<grid, kU1Runs * u1_parts<8>(), 0, s>>>(g, f); break;
+        case 4: k_u1_main<4><<<grid, kU1Runs * u1_parts<4>(), 0, s>>>(g, f); break;
+        case 2: k_u1_main<2><<<grid, kU1Runs * u1_parts<2>(), 0, s>>>(g, f); break;
+        default: k_u1_main<1><<<grid, kU1Runs * u1_parts<1>(), 0, s>>>(g, f); break;
     }
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_combine", &ev) : -1;
@@ -732,11 +752,11 @@ void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s) {
         const unsigned nb = (unsigned)bl.mmse_blocks[r];
         const BlockRef* m = bl.mmse_map[r];
         switch (r) {
-            case 0: kb_u1_main<1><<<nb, kU1Runs, 0, s>>>(d, m); break;
-            case 1: kb_u1_main<2><<<nb, kU1Runs, 0, s>>>(d, m); break;
-            case 2: kb_u1_main<4><<<nb, kU1Runs, 0, s>>>(d, m); break;
-            case 3: kb_u1_main<8><<<nb, kU1Runs, 0, s>>>(d, m); break;
-            default: kb_u1_main<16><<<nb, kU1Runs, 0, s>>>(d, m); break;
+            case 0: kb_u1_main<1><<<nb, kU1Runs * u1_parts<1>(), 0, s>>>(d, m); break;
+            case 1: kb_u1_main<2><<<nb, kU1Runs * u1_parts<2>(), 0, s>>>(d, m); break;
+            case 2: kb_u1_main<4><<<nb, kU1Runs * u1_parts<4>(), 0, s>>>(d, m); break;
+            case 3: kb_u1_main<8><<<nb, kU1Runs * u1_parts<8>(), 0, s>>>(d, m); break;
+            default: kb_u1_main<16><<<nb, kU1Runs * u1_parts<16>(), 0, s>>>(d, m); break;
         }
     }
     kb_u1_combine<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
