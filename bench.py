@@ -65,30 +65,38 @@ def init_table(p):
 
 
 # ---- algorithmic work per kernel launch ----------------------------------
-# The fast path runs in double-float on the FP32 pipe; work is counted in FP32
+# Correlation tables: bf16 tensor-core products, counted as issued: per table
+# (3), column group (64 columns of 128 positions), tap chunk (128 taps) and
+# slice product (21 of the six 8-bit slices per operand): one M=128 (phases)
+# x N=64 (columns) x K=128 product, 2 flops per multiply-add.
+TC_PRODUCTS = 21
+# The rest runs in double-float on the FP32 pipe; work is counted in FP32
 # flops of its double-float operations (FADD/FMUL 1, FFMA 2):
 #   df_add 11, df_mul 10, product-and-accumulate 18.
-#   tables:    per (table position, w tap): 3 x 18 = 54.
 #   mmse_main: per directly summed (source, target): weight-times-f
 #              accumulate 18, weight accumulate 11, recurrence product 10 = 39;
 #              per (source, run) the anchor exponent (40) and exp (90).  Per
 #              Taylor-expanded (box, run): the anchor (130) and per target the
 #              shift of z (11), the recurrence product (10) and two scaled
 #              accumulates (42); per Taylor term 21 in double-float, 2 in FP32.
-#   search:    per (x_i, candidate): one screened evaluation of the
-#              three-correlation identity, 233.
+#   search:    per (x_i, candidate): one screened evaluation of the cell
+#              quadratic, S = A0 + t (A1 + t A2) (2 df_mul + 2 df_add), the
+#              control term k^2 (u - x)^2 (3 df_mul), their sum and the bound:
+#              104.
 # The plain FP64 path counts FP64 flops: 6 per quadrature term.
-FLOPS_TABLE_TAP = 54.0
 FLOPS_U1_PAIR = 39.0
 FLOPS_U1_ANCHOR = 130.0
 FLOPS_U1_BOX_TARGET = 63.0
 FLOPS_U1_TERM_DF = 21.0
 FLOPS_U1_TERM_F32 = 2.0
-FLOPS_SEARCH_CAND = 233.0
+FLOPS_SEARCH_CAND = 104.0
 
 # kernels launched per timed group of the library's profiler (the groups not
-# listed launch one kernel)
-KERNELS_PER_GROUP = {"u1_boxes": 2}
+# listed launch one kernel), and the instance set-up launches of one solve
+# (weights 3, coarse list, fast set-up, filter slices, init, the first u1
+# step 5, tables 3, J), which run before the profiler is switched on
+KERNELS_PER_GROUP = {"u1_boxes": 2, "search": 2}
+SETUP_LAUNCHES = 16
 
 
 def kernel_work(p, sizes, counters, launches):
@@ -98,14 +106,14 @@ def kernel_work(p, sizes, counters, launches):
         return {"search": (nx * L * R * nw * 6.0, "fp64"),
                 "mmse": (nx * ny * 8.0, "fp64")}
     run = sizes.get("run", 16)
-    n_pos = sizes.get("n_pos", 0)
     per = 1.0 / max(1, launches.get("mmse_main", 1))
     u1 = (counters.get("u1_pairs", 0) * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR) +
           counters.get("u1_boxes", 0) * (run * FLOPS_U1_BOX_TARGET + FLOPS_U1_ANCHOR) +
           counters.get("u1_df_terms", 0) * FLOPS_U1_TERM_DF +
           counters.get("u1_f32_terms", 0) * FLOPS_U1_TERM_F32) * per
+    tab = 3 * sizes["tc_ng"] * sizes["tc_nch"] * TC_PRODUCTS * 2.0 * 128 * 64 * 128
     return {
-        "tables": (n_pos * nw * FLOPS_TABLE_TAP, "fp32"),
+        "tables": (tab, "bf16"),
         "mmse_main": (u1, "fp32"),
         "search": (nx * sizes["n_cand"] * FLOPS_SEARCH_CAND, "fp32"),
     }
@@ -230,8 +238,9 @@ def whole_job_rate(world: int, units_per_rank: float, max_seconds: float) -> flo
 # ---- GPU arm --------------------------------------------------------------
 
 def fast_sizes(p, binding):
-    """Table positions and u1 run length of the fast path (mirrors the
-    library's plan: reach of the candidate lattice, run length rule)."""
+    """Table positions, tensor-core grid and u1 run length of the fast path
+    (mirrors the library's plan: reach of the candidate lattice, 64-column
+    groups of 128 positions, 128-tap chunks, run length rule)."""
     d = p["delta"]
     hx = round(p["x_half"] / d); hw = round(p["w_half"] / d)
     hy = round(p["y_half"] / d); hr = round(p["cand_half"] / d)
@@ -240,6 +249,9 @@ def fast_sizes(p, binding):
     ext = max(reach, hx + 2 * q) + 2
     s = dict(binding.plan(p))
     s["n_pos"] = 2 * ext + 2
+    na = -(-s["n_pos"] // 128)
+    s["tc_ng"] = -(-na // 64)
+    s["tc_nch"] = -(-(s["n_w"] + 127) // 128)
     F = max(hr + 2 * q, hx) * d
     slope = d * (hy * d + F)
     run = 16
@@ -468,28 +480,35 @@ def run_gpu(args):
            "h2d_bytes_per_step": int(table.nbytes),
            "d2h_bytes_per_step": int(out["f"].nbytes + out["U"].nbytes + 8)}
 
-    # ---- roofline of the dominant kernel (ALU bound)
+    # ---- roofline of the dominant kernel, and of every modelled kernel
     launches = {k: v[0] for k, v in kern.items()}
     work = kernel_work(p, sizes, {k: v / args.steps for k, v in counters.items()},
                        {k: v / args.steps for k, v in launches.items()})
-    dom = max((k for k in kern if k in work), key=lambda k: kern[k][1])
-    nl, ms = kern[dom]
-    avg_s = ms / nl / 1e3
-    flops, pipe = work[dom]
-    peak = peaks["fp32_tflops"] if pipe == "fp32" else peaks["fp64_tflops"]
-    achieved = flops / avg_s / 1e12
+    mp = load_peaks()
+    pipe_peak = {
+        "fp32": (peaks["fp32_tflops"], "alu", "measured FP32 FMA throughput (ucp_probe_alu, this run)"),
+        "fp64": (peaks["fp64_tflops"], "alu", "measured FP64 FMA throughput (ucp_probe_alu, this run)"),
+        "bf16": (mp.get("bf16_tflops_sustained", 1700.0), "tensor",
+                 "measured dense bf16 cuBLAS throughput, sustained (MEASURED_PEAKS.json)"
+                 if "bf16_tflops_sustained" in mp else "fallback dense bf16 1.7 PFLOP/s"),
+    }
     per_kernel = {}
     for k, (w, pp) in work.items():
         if k in kern:
-            a_ = w / (kern[k][1] / kern[k][0] / 1e3) / 1e12
-            pk = peaks["fp32_tflops"] if pp == "fp32" else peaks["fp64_tflops"]
-            per_kernel[k] = {"achieved_tflops": a_, "frac": a_ / pk,
-                             "ms_per_launch": kern[k][1] / kern[k][0]}
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+            ms_l = kern[k][1] / kern[k][0]
+            a_ = w / (ms_l / 1e3) / 1e12
+            pk, bound, _ = pipe_peak[pp]
+            per_kernel[k] = {"bound": bound, "pipe": pp, "achieved_tflops": a_,
+                             "frac": a_ / pk, "ms_per_launch": ms_l}
+    dom = max((k for k in kern if k in work), key=lambda k: kern[k][1])
+    nl, ms = kern[dom]
+    flops, pipe = work[dom]
+    peak, bound, src = pipe_peak[pipe]
+    achieved = flops / (ms / nl / 1e3) / 1e12
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"measured {pipe.upper()} FMA throughput "
-                               "(ucp_probe_alu, this run)",
-                "share_of_step": ms / total_ms, "per_kernel": per_kernel}
+                "peak_source": src, "share_of_step": ms / total_ms,
+                "per_kernel": per_kernel}
 
     batched = None
     if rank == 0 and not args.no_batched:
@@ -511,7 +530,7 @@ def run_gpu(args):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "gpu_launches": int(sum(v[0] * KERNELS_PER_GROUP.get(k, 1)
-                                for k, v in kern.items())),
+                                for k, v in kern.items()) + SETUP_LAUNCHES * args.steps),
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kern.items()},
         "roofline": roofline, "e2e": e2e, "clocks": clk, "parity": parity,
         "work_per_solve": {k: v / args.steps for k, v in counters.items()},
@@ -575,7 +594,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ucp", choices=["ucp", "reference"])
     ap.add_argument("--workload", default="c2")
