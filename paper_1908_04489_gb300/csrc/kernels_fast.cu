@@ -95,6 +95,7 @@ constexpr int kCoopT = 256;   // threads per block of the deferred search
 struct CoopSmem {
     double acc[kCoopT / 2][2];
     float emax[kCoopT / 2][2], demax[kCoopT / 2][2];
+    double res2[2][2];   // second-tier cost and bound of the two candidates
     int64_t mem_nu[32];
     double res[32];
     double* scratch;   // kCoopT * kTieBatch doubles
@@ -177,7 +178,7 @@ __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
     dfloat blk[2] = {{0.f, 0.f}, {0.f, 0.f}};
     float emax[2] = {0.f, 0.f}, demax[2] = {0.f, 0.f};
     int cnt = 0;
-#pragma unroll 1
+#pragma unroll 2
     for (int64_t l = part * G + lane; l < g.n_w; l += G * nparts) {
         const dfloat w = f.wdf[l], ph = f.phidf[l];
 #pragma unroll
@@ -208,7 +209,39 @@ __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
             demax[b] = fmaxf(demax[b], __shfl_down_sync(gm, demax[b], off, G));
         }
     }
+    // cost and bound of candidate b from the combined sums (every lane of a
+    // group, or one thread of the block, gets the same values).  The bound is
+    // formed in FP32 from positive terms (at most ~12 roundings of 2^-24 each,
+    // covered by the factor 1.00001); the cost stays FP64.
+    auto finish = [&](int b, double S2, float em, float dm, double& gv, double& bv) {
+        if (!ok[b]) {
+            gv = 0.0;
+            bv = INFINITY;
+            return;
+        }
+        const dfloat a = df_mul(df_from_i64(nu[b] - (i - g.hx) * g.one),
+                                dfloat{f.step_hi, f.step_lo});
+        const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
+        const double c = df_to_double(ctl);
+        gv = c + S2;
+        // |error of d_l| <= uf^2 (|w_l| + |E_{p+l}| + |E_{p+l+1}|) from the
+        // double-float representations plus 8 uf^2 (|d_l| + |dE_l|) from the
+        // operations; summed against phi_l 2|d_l| this gives the terms below.
+        const float uf2 = 0x1p-48f;
+        const float s2 = fmaxf((float)S2, 0.0f) * 1.000001f;
+        const float rs = sqrtf(s2) * 1.000001f;
+        const float cf = fabsf(ctl.hi) * 1.000001f;
+        const float eps = f.beta_abs + uf2 * (f.w_half + 2.0f * em);
+        const float bf = f.beta2_rel * s2 + 1.25f * 16.0f * uf2 * (s2 + rs * dm) +
+                         1.25f * (2.0f * rs + 1.0f) * eps + 3.0e-13f * cf +
+                         f.beta_ctl * (f.k_f * fabsf(a.hi) * 1.0001f) +
+                         4.0e-16f * (float)fabs(gv) * 1.000001f;
+        bv = (double)(bf * 1.00001f);
+    };
     if (cs) {
+        // the groups' partials are reduced by warp 0 (a fixed tree) and the
+        // tail runs once per candidate (lanes 0 and 1), shared through
+        // shared memory
         if (lane == 0) {
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
@@ -218,44 +251,41 @@ __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
             }
         }
         __syncthreads();
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            double S[2];
+            float em[2], dm[2];
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            acc[b] = cs->acc[0][b];
-            emax[b] = cs->emax[0][b];
-            demax[b] = cs->demax[0][b];
-            for (int q = 1; q < nparts; ++q) {
-                acc[b] += cs->acc[q][b];
-                emax[b] = fmaxf(emax[b], cs->emax[q][b]);
-                demax[b] = fmaxf(demax[b], cs->demax[q][b]);
+            for (int b = 0; b < 2; ++b) {
+                S[b] = q < nparts ? cs->acc[q][b] : 0.0;
+                em[b] = q < nparts ? cs->emax[q][b] : 0.0f;
+                dm[b] = q < nparts ? cs->demax[q][b] : 0.0f;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    S[b] += __shfl_down_sync(0xffffffffu, S[b], off);
+                    em[b] = fmaxf(em[b], __shfl_down_sync(0xffffffffu, em[b], off));
+                    dm[b] = fmaxf(dm[b], __shfl_down_sync(0xffffffffu, dm[b], off));
+                }
             }
+            const double S1 = __shfl_sync(0xffffffffu, S[1], 0);
+            const float em1 = __shfl_sync(0xffffffffu, em[1], 0);
+            const float dm1 = __shfl_sync(0xffffffffu, dm[1], 0);
+            if (q == 0) finish(0, S[0], em[0], dm[0], cs->res2[0][0], cs->res2[0][1]);
+            if (q == 1) finish(1, S1, em1, dm1, cs->res2[1][0], cs->res2[1][1]);
         }
         __syncthreads();
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            g2[b] = cs->res2[b][0];
+            b2[b] = cs->res2[b][1];
+        }
+        __syncthreads();
+        return;
     }
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        const double S2 = cs ? acc[b] : __shfl_sync(gm, acc[b], 0, G);
-        const float em = cs ? emax[b] : __shfl_sync(gm, emax[b], 0, G);
-        const float dm = cs ? demax[b] : __shfl_sync(gm, demax[b], 0, G);
-        if (!ok[b]) {
-            g2[b] = 0.0;
-            b2[b] = INFINITY;
-            continue;
-        }
-        const dfloat a = df_mul(df_from_i64(nu[b] - (i - g.hx) * g.one),
-                                dfloat{f.step_hi, f.step_lo});
-        const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
-        const double c = df_to_double(ctl);
-        g2[b] = c + S2;
-        // |error of d_l| <= uf^2 (|w_l| + |E_{p+l}| + |E_{p+l+1}|) from the
-        // double-float representations plus 8 uf^2 (|d_l| + |dE_l|) from the
-        // operations; summed against phi_l 2|d_l| this gives the terms below.
-        const double uf2 = 0x1p-48;
-        const double rs = sqrt(fmax(S2, 0.0));
-        const double eps = (double)f.beta_abs + uf2 * ((double)f.w_half + 2.0 * em);
-        b2[b] = (double)f.beta2_rel * S2 + 1.25 * 16.0 * uf2 * (S2 + rs * dm) +
-                1.25 * (2.0 * rs + 1.0) * eps + 3.0e-13 * c +
-                (double)f.beta_ctl * sqrt(c) + 4.0e-16 * fabs(g2[b]);
-    }
+    for (int b = 0; b < 2; ++b)
+        finish(b, __shfl_sync(gm, acc[b], 0, G), __shfl_sync(gm, emax[b], 0, G),
+               __shfl_sync(gm, demax[b], 0, G), g2[b], b2[b]);
 }
 
 // ---- screened table cost ------------------------------------------------
