@@ -362,15 +362,28 @@ __device__ __forceinline__ Eval eval_outside(const Geom& g, const FastView& f, i
 }
 
 // Screened cost of candidate nu for x0 point i from the stored cell
-// coefficients (search).
+// coefficients (search).  On the y grid (t = 0, every coarse candidate) the
+// quadratic is A0 itself: the Horner step would add exact zeros, so it is
+// skipped with the same result.
 __device__ __forceinline__ Eval eval_table(const Geom& g, const FastView& f,
                                            int64_t i, int64_t nu) {
     const int64_t cell = nu >> g.shift;
     const int64_t p = cell - f.c_lo;
     if (p < 0 || p + 1 >= f.n_pos) return eval_outside(g, f, i, nu);
-    const dfloat t = df_mul_f(df_from_i64(nu - cell * g.one), f.inv_one_f);
-    const Coef c{f.C0[p], f.C1[p], f.C2[p], f.Cb[p]};
-    return eval_poly(g, f, i, nu, t, c);
+    const int64_t frac = nu - cell * g.one;
+    const dfloat a0 = f.C0[p];
+    const float b = f.Cb[p];
+    dfloat S = a0;
+    if (frac != 0) {
+        const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
+        S = df_add(a0, df_mul(t, df_add(f.C1[p], df_mul(t, f.C2[p]))));
+    }
+    const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
+    const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
+    const dfloat gv = df_add(ctl, S);
+    const float beta = b + 3.0e-13f * fabsf(ctl.hi) +
+                       f.beta_ctl * (f.k_f * fabsf(a.hi) * 1.0001f) + 4.0e-16f * fabsf(gv.hi);
+    return {gv, beta};
 }
 
 // The same cost with the cell coefficients formed from the tables (J, which

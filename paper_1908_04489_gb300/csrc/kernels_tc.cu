@@ -45,7 +45,8 @@ constexpr int kTcT = 512;             // threads of the tensor-core kernel
 constexpr uint32_t kTcATile = 128 * 128 * 2;   // filter tile: 128 phases x 128 taps
 constexpr uint32_t kTcBTile = 64 * 128 * 2;    // signal tile: 64 columns x 128 taps
 constexpr uint32_t kTcHBytes = kSl * 8 * 256 * 2;   // a chunk's filter slices
-constexpr size_t kTcSmem = kSl * kTcBTile + 2 * kTcATile + kTcHBytes + 1024;
+constexpr int kTcABuf = 3;   // filter tiles in flight: group s runs while s + 2 is built
+constexpr size_t kTcSmem = kSl * kTcBTile + kTcABuf * kTcATile + kTcHBytes + 1024;
 constexpr uint32_t kTmemCols = 512;   // accumulator k at columns 64 k .. 64 k + 63 (k < 6)
 constexpr int64_t kTcPolls = 4000000; // bound of every mbarrier wait
 
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(128) k_build_E_tc(Geom g, FastView f,
 // ---- the slice products on the tensor cores ------------------------------
 
 struct TcShared {
-    uint64_t bar[2];   // MMAs of slice group s done: bar[s & 1]
+    uint64_t bar[kTcABuf];   // MMAs of slice group s done: bar[s % kTcABuf]
     uint64_t bar_x[kTcSlices];   // signal tile of slice t landed (TMA)
     uint64_t bar_h;    // filter slices landed (bulk copy)
     uint32_t tmem;
@@ -172,13 +173,12 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
                                                TcShared& ts) {
     char* base = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     char* tB = base;                     // kSl signal tiles (all slices)
-    char* tA = base + kSl * kTcBTile;    // two filter tiles (double buffer)
-    char* tH = tA + 2 * kTcATile;        // the chunk's filter slices, 8 shifts each
+    char* tA = base + kSl * kTcBTile;    // kTcABuf filter tiles (ring)
+    char* tH = tA + kTcABuf * kTcATile;  // the chunk's filter slices, 8 shifts each
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int flt = tau == 0 ? 0 : 1;
     if (tid == 0) {
-        mbar_init(&ts.bar[0], 1);
-        mbar_init(&ts.bar[1], 1);
+        for (int k = 0; k < kTcABuf; ++k) mbar_init(&ts.bar[k], 1);
         for (int t = 0; t < kSl; ++t) mbar_init(&ts.bar_x[t], 1);
         mbar_init(&ts.bar_h, 1);
         fence_mbar_init();
@@ -214,15 +214,20 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     };
     bool ok = mbar_wait(&ts.bar_h, 0, kTcPolls);
     ok = __syncthreads_and(ok);
-    if (ok) build_A(0, tA);
+    if (ok) {
+        build_A(0, tA);
+        build_A(1, tA + kTcATile);
+    }
     fence_proxy_async_smem();
     __syncthreads();
     const uint32_t tmem = ts.tmem;
     constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
+    // group s reads filter buffer s % kTcABuf and commits to bar[s % kTcABuf];
+    // its completion is that barrier's use s / kTcABuf (phase parity)
     for (int s = 0; s < kSl; ++s) {
         if (tid == 0 && ok) {
             tc_fence_after();
-            const uint32_t a0 = smem_u32(tA + (s & 1) * kTcATile);
+            const uint32_t a0 = smem_u32(tA + (s % kTcABuf) * kTcATile);
             for (int t = 0; s + t < kSl && ok; ++t) {
                 // the first slice group starts as the signal tiles land
                 if (s == 0) ok = mbar_wait(&ts.bar_x[t], 0, kTcPolls);
@@ -237,20 +242,22 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
                               (s > 0 || kk > 0) ? 1u : 0u);
                 }
             }
-            umma_commit(&ts.bar[s & 1]);
+            umma_commit(&ts.bar[s % kTcABuf]);
         }
-        if (s + 1 < kSl) {
-            // the other buffer was read by slice group s - 1
-            if (s >= 1 && ok) ok = mbar_wait(&ts.bar[(s - 1) & 1], ((s - 1) >> 1) & 1, kTcPolls);
+        if (s + 2 < kSl) {
+            // filter tile s + 2 goes into the buffer slice group s - 1 read
+            if (s >= 1 && ok)
+                ok = mbar_wait(&ts.bar[(s - 1) % kTcABuf], ((s - 1) / kTcABuf) & 1, kTcPolls);
             ok = __syncthreads_and(ok);
             fence_proxy_async_smem();   // the tensor core's reads before our writes
-            if (ok) build_A(s + 1, tA + ((s + 1) & 1) * kTcATile);
+            if (ok) build_A(s + 2, tA + ((s + 2) % kTcABuf) * kTcATile);
             fence_proxy_async_smem();
             ok = __syncthreads_and(ok);
         }
     }
     // the last commit covers every MMA of this thread
-    if (ok) ok = mbar_wait(&ts.bar[(kSl - 1) & 1], ((kSl - 1) >> 1) & 1, kTcPolls);
+    if (ok)
+        ok = mbar_wait(&ts.bar[(kSl - 1) % kTcABuf], ((kSl - 1) / kTcABuf) & 1, kTcPolls);
     ok = __syncthreads_and(ok);
     tc_fence_after();
     if (ok) {

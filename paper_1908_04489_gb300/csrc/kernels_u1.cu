@@ -459,17 +459,22 @@ __device__ __forceinline__ unsigned direct_box(const FastView& f, int64_t s0, in
     return evaluated;
 }
 
-// Threads per run of R targets (each takes R / u1_parts<R>() consecutive ones).
+// Threads per run of R targets when a launch is small: P = 4 (each takes R / 4
+// consecutive targets and repeats the run's exponentials), so that a single
+// instance's few runs fill more of the GPU; launches that fill it anyway run
+// one thread per run (P = 1).  Every target gets the same operations either
+// way.
 template <int R>
 constexpr int u1_parts() { return R >= 4 ? 4 : 1; }
+constexpr int64_t kU1SplitMaxBlocks = 4 * 152;   // launches up to this many blocks split
 
 // Block (bx, t): runs bx*kU1Runs.. against the boxes of tile t, thread
-// (part, run) taking targets part * TR .. + TR - 1 of its run; writes the
-// tile's partial sums of those targets.
-template <int R>
+// (part, run) taking targets part * TR .. + TR - 1 of its run (TR = R / P);
+// writes the tile's partial sums of those targets.
+template <int R, int P>
 __device__ __forceinline__ void u1_main_body(const Geom& g, const FastView& f,
                                              dfloat* st64, int64_t bx, int64_t t) {
-    constexpr int TR = R / u1_parts<R>();
+    constexpr int TR = R / P;
     for (int k = threadIdx.x; k < 47; k += blockDim.x) st64[k] = f.t64[k];
     __syncthreads();
     const int part = threadIdx.x / kU1Runs;
@@ -581,10 +586,10 @@ __global__ void __launch_bounds__(kRunT) k_run_shift(Geom g, FastView f) {
     run_shift_body(g, f, blockIdx.x);
 }
 
-template <int R>
-__global__ void __launch_bounds__(kU1Runs * 4) k_u1_main(Geom g, FastView f) {
+template <int R, int P>
+__global__ void __launch_bounds__(kU1Runs * P) k_u1_main(Geom g, FastView f) {
     __shared__ dfloat st64[47];
-    u1_main_body<R>(g, f, st64, blockIdx.x, blockIdx.y);
+    u1_main_body<R, P>(g, f, st64, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_u1_combine(Geom g, FastView f, double* __restrict__ U) {
@@ -628,14 +633,30 @@ __global__ void __launch_bounds__(kRunT) kb_run_shift(const InstDev* insts,
     run_shift_body(sd.g, sd.f, r.local);
 }
 
-template <int R>
-__global__ void __launch_bounds__(kU1Runs * 4) kb_u1_main(const InstDev* insts,
-                                                      const BlockRef* map) {
+template <int R, int P>
+__global__ void __launch_bounds__(kU1Runs * P) kb_u1_main(const InstDev* insts,
+                                                          const BlockRef* map) {
     __shared__ InstDev sd;
     __shared__ dfloat st64[47];
     const BlockRef r = stage(insts, map, sd);
     const int64_t rb = sd.f.r_blocks;
-    u1_main_body<R>(sd.g, sd.f, st64, r.local % rb, r.local / rb);
+    u1_main_body<R, P>(sd.g, sd.f, st64, r.local % rb, r.local / rb);
+}
+
+template <int R>
+void launch_kb_u1_main(unsigned nb, const InstDev* d, const BlockRef* m, cudaStream_t s) {
+    if (nb <= kU1SplitMaxBlocks)
+        kb_u1_main<R, u1_parts<R>()><<<nb, kU1Runs * u1_parts<R>(), 0, s>>>(d, m);
+    else
+        kb_u1_main<R, 1><<<nb, kU1Runs, 0, s>>>(d, m);
+}
+
+template <int R>
+void launch_k_u1_main(dim3 grid, const Geom& g, const FastView& f, cudaStream_t s) {
+    if ((int64_t)grid.x * grid.y <= kU1SplitMaxBlocks)
+        k_u1_main<R, u1_parts<R>()><<<grid, kU1Runs * u1_parts<R>(), 0, s>>>(g, f);
+    else
+        k_u1_main<R, 1><<<grid, kU1Runs, 0, s>>>(g, f);
 }
 
 __global__ void kb_u1_combine(const InstDev* insts, const BlockRef* map) {
@@ -716,11 +737,11 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
     k = prof ? prof->begin("mmse_main", &ev) : -1;
     dim3 grid((unsigned)f.r_blocks, (unsigned)f.n_tiles);
     switch (f.run) {
-        case 16: k_u1_main<16><<<grid, kU1Runs * u1_parts<16>(), 0, s>>>(g, f); break;
-        case 8: k_u1_main<8><<<grid, kU1Runs * u1_parts<8>(), 0, s>>>(g, f); break;
-        case 4: k_u1_main<4><<<grid, kU1Runs * u1_parts<4>(), 0, s>>>(g, f); break;
-        case 2: k_u1_main<2><<<grid, kU1Runs * u1_parts<2>(), 0, s>>>(g, f); break;
-        default: k_u1_main<1><<<grid, kU1Runs * u1_parts<1>(), 0, s>>>(g, f); break;
+        case 16: launch_k_u1_main<16>(grid, g, f, s); break;
+        case 8: launch_k_u1_main<8>(grid, g, f, s); break;
+        case 4: launch_k_u1_main<4>(grid, g, f, s); break;
+        case 2: launch_k_u1_main<2>(grid, g, f, s); break;
+        default: launch_k_u1_main<1>(grid, g, f, s); break;
     }
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("mmse_combine", &ev) : -1;
@@ -752,11 +773,11 @@ void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s) {
         const unsigned nb = (unsigned)bl.mmse_blocks[r];
         const BlockRef* m = bl.mmse_map[r];
         switch (r) {
-            case 0: kb_u1_main<1><<<nb, kU1Runs * u1_parts<1>(), 0, s>>>(d, m); break;
-            case 1: kb_u1_main<2><<<nb, kU1Runs * u1_parts<2>(), 0, s>>>(d, m); break;
-            case 2: kb_u1_main<4><<<nb, kU1Runs * u1_parts<4>(), 0, s>>>(d, m); break;
-            case 3: kb_u1_main<8><<<nb, kU1Runs * u1_parts<8>(), 0, s>>>(d, m); break;
-            default: kb_u1_main<16><<<nb, kU1Runs * u1_parts<16>(), 0, s>>>(d, m); break;
+            case 0: launch_kb_u1_main<1>(nb, d, m, s); break;
+            case 1: launch_kb_u1_main<2>(nb, d, m, s); break;
+            case 2: launch_kb_u1_main<4>(nb, d, m, s); break;
+            case 3: launch_kb_u1_main<8>(nb, d, m, s); break;
+            default: launch_kb_u1_main<16>(nb, d, m, s); break;
         }
     }
     kb_u1_combine<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
