@@ -687,7 +687,7 @@ void u1_plan(const Geom& g, int max_tiles, FastPlan* fp) {
     fp->r_blocks = (fp->n_runs + kU1Runs - 1) / kU1Runs;
     int64_t tile = (g.n_x + max_tiles - 1) / max_tiles;
     tile = (tile + 31) / 32 * 32;
-    if (tile < 512) tile = 512;
+    if (tile < g.u1_tile_min) tile = g.u1_tile_min;
     fp->tile = tile;
     fp->n_tiles = (int)((g.n_x + tile - 1) / tile);
 }

@@ -24,6 +24,7 @@ struct Geom {
     int64_t q;                  // coarse spacing in units of delta (even)
     int32_t n_coarse, n_refine, n_levels, n_nbr;
     int32_t n_cand;             // 1 + 2 n_nbr + n_coarse + L n_refine
+    int32_t u1_tile_min;        // fewest x0 points per tile of the u1 step
 };
 
 // Fills g from params; returns nullptr or a static reason string.
