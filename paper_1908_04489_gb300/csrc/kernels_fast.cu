@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
 
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
 // prior exponent x_i^2 / 2 sigma^2, W2 = sum phi_l w_l^2 (fixed-order tree),
-// and the exp(k/64) table of df_exp.
+// and the constant table (df_exp's exp(k/64), the inverse factorials).
 __global__ void k_fast_setup(Geom g, FastView f) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < g.n_w) {
@@ -885,7 +885,7 @@ __global__ void k_fast_setup(Geom g, FastView f) {
         const double x = x_of(g, k);
         f.prior[k] = df_from_double(__ddiv_rn(__dmul_rn(x, x), g.two_s2));
     }
-    if (k < 47) f.t64[k] = df_from_double(exp((double)(k - 23) / 64.0));
+    if (k < kConstTab) f.t64[k] = const_table_entry((int)k);
     if (blockIdx.x == 0) {   // W2: strided partial sums, then a fixed tree
         __shared__ double red[256];
         double s = 0.0;
@@ -1059,7 +1059,7 @@ void fast_plan(const Geom& g, FastPlan* fp) {
 
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
     int64_t n = g.n_w > g.n_x ? g.n_w : g.n_x;
-    n = n > 47 ? n : 47;
+    n = n > kConstTab ? n : kConstTab;
     k_fast_setup<<<blocks(n, 256), 256, 0, s>>>(g, f);
 }
 

@@ -205,7 +205,6 @@ __device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& 
     if (tid == 0) {
         f.box_geo[slot] = make_float4(c, h, pm, pmn);
         f.box_rng[slot] = make_float4(rg.x, rg.y, expand ? h : INFINITY, sc);
-        f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
     }
     if (!expand) return;   // the same for the block
     // moments: orders 0..kBoxDF in double-float; the higher ones only enter
@@ -254,10 +253,10 @@ __device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& 
         for (int m = 0; m < kBoxTerms - kBoxDF; ++m) sm.wf[warp][m] = Mf[m];
     }
     __syncthreads();
+    // exp(delta c), used only by expanded boxes, on an otherwise idle thread
+    if (tid == kBoxTerms) f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
     if (tid < kBoxTerms) {
-        double fact = 1.0;
-        for (int m = 2; m <= tid; ++m) fact *= (double)m;   // n! (rounded above 22!)
-        const dfloat inv = df_from_double(1.0 / fact);
+        const dfloat inv = f.t64[47 + tid];   // 1 / tid!
         const dfloat Mn = moment_sum(sm, tid), Mn1 = moment_sum(sm, tid + 1);
         dfloat* co = f.box_coef + slot * (2 * kBoxTerms);
         co[tid] = df_mul(Mn, inv);

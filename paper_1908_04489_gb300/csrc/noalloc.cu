@@ -36,14 +36,14 @@ constexpr int64_t kMaxY = 32768;       // largest y grid
 constexpr int kMaxTiles = 8;           // source tiles of the u1 step
 
 constexpr size_t rnd256(size_t n) { return (n + 255) / 256 * 256; }
-// nu and prior (x-sized), the exp(k/64) table, then the u1 buffers at the
+// nu and prior (x-sized), the constant table, then the u1 buffers at the
 // largest sizes: src_nu, src_f, src_F; per tile the box count, per box slot
 // its first source, size, geometry, range, exp(delta c) and 2 kBoxTerms
 // coefficients; per run (at most n_y runs) two bounds; per tile and target
 // the numerator and denominator partials.
 constexpr size_t kSlots = (size_t)kMaxTiles * kBoxMax;
 constexpr size_t kScratchBytes =
-    5 * rnd256(8 * kMaxX) + rnd256(8 * 64) + rnd256(4 * kMaxTiles) +
+    5 * rnd256(8 * kMaxX) + rnd256(8 * kConstTab) + rnd256(4 * kMaxTiles) +
     2 * rnd256(4 * kSlots) + 2 * rnd256(16 * kSlots) + rnd256(8 * kSlots) +
     rnd256(8 * kSlots * 2 * kBoxTerms) + 2 * rnd256(4 * kMaxY) +
     2 * rnd256(8 * (size_t)kMaxTiles * kMaxY);
@@ -78,7 +78,7 @@ __global__ void k_na_prepare(Geom g, const double* __restrict__ f,
         const double x = __dmul_rn((double)(k - g.hx), g.delta);
         prior[k] = df_from_double(__ddiv_rn(__dmul_rn(x, x), g.two_s2));
     }
-    if (k < 47) t64[k] = df_from_double(exp((double)(k - 23) / 64.0));
+    if (k < kConstTab) t64[k] = const_table_entry((int)k);
 }
 
 // Device address of g_scratch on the current device (looked up once).
@@ -143,14 +143,14 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
     Bump bump{(char*)base, (char*)base + kScratchBytes};
     int64_t* nu = (int64_t*)bump_get(&bump, 8 * (size_t)g.n_x);
     f.prior = (dfloat*)bump_get(&bump, 8 * (size_t)g.n_x);
-    f.t64 = (dfloat*)bump_get(&bump, 8 * 64);
+    f.t64 = (dfloat*)bump_get(&bump, 8 * kConstTab);
     if (!nu || !f.prior || !f.t64 || !u1_carve(g, &f, bump_get, &bump)) {
         set_error("ucp_u1_update_noalloc: %s%s", "static scratch too small", "");
         return UCP_E_ARG;
     }
 
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = g.n_x > 47 ? g.n_x : 47;
+    const int64_t n = g.n_x > kConstTab ? g.n_x : kConstTab;
     k_na_prepare<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, f_dev, nu, f.prior,
                                                           f.t64);
     launch_mmse_fast(g, f, nu, u1_dev, s, nullptr);

@@ -184,7 +184,7 @@ size_t inst_bytes(const Geom& g, int precision) {
         fast_plan(g, &fp);
         size_t tcs[7];
         b += 6 * rnd(8 * (size_t)fp.n_pos) + rnd(4 * (size_t)fp.n_pos) + rnd(8 * (size_t)fp.n_e) +
-             3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * 47) +
+             3 * rnd(8 * nw) + rnd(8 * nx) + rnd(8 * kConstTab) +
              rnd(8 * (size_t)fp.J_blocks) + rnd(8) + 3 * rnd(4) + rnd(kDeferRecBytes * nx) + rnd(32) +
              tc_bytes(fp, 256, tcs) + rnd(4) +
              u1_scratch_bytes(g, fp, 256);
@@ -253,7 +253,7 @@ static ucp_status fast_alloc(ucp_inst* in) {
     f.phidf = (dfloat*)A.get(8 * nw);
     f.wdf = (dfloat*)A.get(8 * nw);
     f.prior = (dfloat*)A.get(8 * nx);
-    f.t64 = (dfloat*)A.get(8 * 47);
+    f.t64 = (dfloat*)A.get(8 * kConstTab);
     f.Jpart = (double*)A.get(8 * (size_t)f.J_blocks);
     size_t tcs[7];
     tc_bytes(f, 256, tcs);

@@ -8,6 +8,17 @@
 
 namespace ucp {
 
+// The constant table of the fast path (FastView::t64): entry k < 47 is
+// exp((k - 23) / 64) (df_exp's table), entry 47 + n is 1 / n! for
+// n <= kBoxTerms (the Taylor coefficients of the u1 boxes), in double-float.
+constexpr int kConstTab = 47 + kBoxTerms + 1;
+__device__ __forceinline__ dfloat const_table_entry(int k) {
+    if (k < 47) return df_from_double(exp((double)(k - 23) / 64.0));
+    double fact = 1.0;
+    for (int m = 2; m <= k - 47; ++m) fact *= (double)m;   // n! (rounded above 22!)
+    return df_from_double(1.0 / fact);
+}
+
 void fast_plan(const Geom& g, FastPlan* fp);
 // u1 step (kernels_u1.cu): run length, tiles (at most max_tiles), buffers.
 int mmse_run_length(const Geom& g);
