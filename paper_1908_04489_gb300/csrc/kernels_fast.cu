@@ -907,7 +907,7 @@ __global__ void k_fast_setup(Geom g, FastView f) {
 
 constexpr int kJThreads = 256;
 // J = sum_i p_i g(f_i; x_i): block partials (fixed tree), then the last
-// block to finish adds the partials in block order.  Returns true in thread
+// block to finish adds the partials (lane-strided, then a warp tree).  Returns true in thread
 // 0 of that block, with J in *J_out (the counter is left at zero).
 __device__ __forceinline__ bool J_partial_body(const Geom& g, const FastView& f,
                                                const double* __restrict__ px,
@@ -929,18 +929,14 @@ __device__ __forceinline__ bool J_partial_body(const Geom& g, const FastView& f,
         *last = atomicAdd(f.J_done, 1) == (int)(f.J_blocks - 1);
     }
     __syncthreads();
-    if (!*last || threadIdx.x != 0) return false;
+    if (!*last || threadIdx.x >= 32) return false;
     __threadfence();
+    // the block partials: lane-strided sums, then a warp tree (fixed order)
     double sum = 0.0;
-    for (int64_t b0 = 0; b0 < f.J_blocks; b0 += 8) {
-        double v8[8];
+    for (int64_t b = threadIdx.x; b < f.J_blocks; b += 32) sum += __ldcg(f.Jpart + b);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)   // issue the loads, then add in order
-            v8[k] = b0 + k < f.J_blocks ? __ldcg(f.Jpart + b0 + k) : 0.0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (b0 + k < f.J_blocks) sum += v8[k];
-    }
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+    if (threadIdx.x != 0) return false;
     *J_out = sum;
     *f.J_done = 0;
     return true;

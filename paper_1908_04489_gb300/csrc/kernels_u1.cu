@@ -550,21 +550,27 @@ __device__ __forceinline__ void u1_combine_body(const Geom& g, const FastView& f
                                                 double* __restrict__ U, int64_t bx) {
     const int64_t j = bx * blockDim.x + threadIdx.x;
     if (j >= g.n_y) return;
+    // tiles in groups of 8: each group summed as a pairwise tree, the group
+    // sums added in order (a fixed order, depth 3 + groups)
     double n = 0.0, d = 0.0;
     for (int t0 = 0; t0 < f.n_tiles; t0 += 8) {
         double pn[8], pd[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {   // issue the loads, then sum in order
-            const int t = t0 + k < f.n_tiles ? t0 + k : t0;
-            pn[k] = f.partN[(size_t)t * g.n_y + j];
-            pd[k] = f.partD[(size_t)t * g.n_y + j];
+        for (int k = 0; k < 8; ++k) {   // issue the loads, then sum
+            const bool in = t0 + k < f.n_tiles;
+            const int t = in ? t0 + k : t0;
+            pn[k] = in ? f.partN[(size_t)t * g.n_y + j] : 0.0;
+            pd[k] = in ? f.partD[(size_t)t * g.n_y + j] : 0.0;
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (t0 + k < f.n_tiles) {
-                n += pn[k];
-                d += pd[k];
+        for (int w = 1; w < 8; w <<= 1)
+#pragma unroll
+            for (int k = 0; k < 8; k += 2 * w) {
+                pn[k] += pn[k + w];
+                pd[k] += pd[k + w];
             }
+        n += pn[0];
+        d += pd[0];
     }
     U[j] = n / d;
 }
