@@ -53,11 +53,6 @@ constexpr int kPlanT = 128;         // threads per tile of the planning kernel
 constexpr int kBoxDF = 16;          // moments up to this order in double-float
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ double value_of(const Geom& g, int64_t nu) {
-    const double inv = __longlong_as_double((int64_t)(1023 - g.shift) << 52);
-    return __dmul_rn(__dmul_rn((double)nu, g.delta), inv);
-}
-
 // ---- sources and boxes ----------------------------------------------------------
 
 // One block per tile.  Every thread: per source f_i and exp(delta f_i)
@@ -70,8 +65,10 @@ __device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
     const int64_t t0 = t * f.tile;
     const int64_t t1 = min(t0 + f.tile, g.n_x);
     const dfloat dl = {f.delta_hi, f.delta_lo};
+    const dfloat step = {f.step_hi, f.step_lo};
     for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
-        const dfloat fv = df_from_double(value_of(g, nu[i]));
+        // f_i = nu_i delta 2^-shift in double-float (the lattice index is exact)
+        const dfloat fv = df_mul(df_from_i64(nu[i]), step);
         f.src_nu[i] = nu[i];
         f.src_f[i] = fv;
         // exp(delta f_i) in double-float (|delta f_i| stays below ~0.8)
