@@ -55,11 +55,14 @@ def workload(name: str, precision: int):
 
 
 def init_table(p):
-    """Host-side initial controller f (the staircase of init_kind 1) for the
-    end-to-end leg, which passes it through init_kind 2."""
+    """Host-side initial controller f of the workload's start (identity for
+    init_kind 0, the staircase for init_kind 1) for the end-to-end leg, which
+    passes it through init_kind 2 (the same lattice values)."""
     d = p["delta"]
     n = int(round(2 * p["x_half"] / d)) + 1
     a = np.arange(n) - (n - 1) // 2
+    if p["init_kind"] == 0:
+        return a * d
     m = np.minimum(np.abs(a) // int(round(7.0 / d)), 2)
     return np.where(a == 0, 0.0, np.sign(a) * 3.5 * (2 * m + 1))
 

@@ -81,11 +81,19 @@ const char* make_geom(const ucp_params& p, Geom* g) {
     g->n_nbr = p.n_nbr;
     g->n_cand = 1 + 2 * p.n_nbr + p.n_coarse + p.n_levels * p.n_refine;
     // A tile of the u1 step holds at most 32 boxes of f-width 0.1: controllers
-    // that vary steadily across x0 (the identity start and its first sweeps)
-    // need narrow tiles to keep their sources in boxes (256 points); piecewise
-    // flat ones (staircase or table starts) fill few boxes, and wider tiles
-    // (512 points) keep the number of per-tile partial sums down.
-    g->u1_tile_min = p.init_kind == 0 ? 256 : 512;
+    // that vary steadily across x0 (the identity start, or a table start
+    // whose increments are mostly nonzero, and their first sweeps) need
+    // narrow tiles to keep their sources in boxes (256 points); piecewise flat
+    // ones (the staircase, flat tables) fill few boxes, and wider tiles (512
+    // points) keep the number of per-tile partial sums down.
+    bool steady = p.init_kind == 0;
+    if (p.init_kind == 2 && p.init_table && p.init_len == (uint64_t)g->n_x && g->n_x > 1) {
+        int64_t moving = 0;
+        for (int64_t i = 0; i + 1 < g->n_x; ++i)
+            moving += p.init_table[i + 1] != p.init_table[i];
+        steady = 2 * moving > g->n_x - 1;
+    }
+    g->u1_tile_min = steady ? 256 : 512;
     if (p.init_kind == 1) {
         int64_t n7;
         if (half_steps(7.0, p.delta, &n7) || n7 < 1)
