@@ -264,6 +264,26 @@ def fast_sizes(p, binding):
     return s
 
 
+def batched_work(ps, b, binding, sweeps):
+    """Algorithmic work of one batched sweep per modelled kernel group,
+    summed over the members (the single-instance model of kernel_work).  The
+    u1 counters cover the set-up's u1 step and the sweeps; they are scaled
+    to one sweep by 1 / (sweeps + 1)."""
+    tot = {"search": 0.0, "tables": 0.0, "mmse_main": 0.0}
+    for p, m in zip(ps, b.members):
+        sz = fast_sizes(p, binding)
+        c = m.work_counters()
+        run = sz["run"]
+        tot["search"] += m.n_x * m.n_cand * FLOPS_SEARCH_CAND
+        tot["tables"] += 3 * sz["tc_ng"] * sz["tc_nch"] * TC_PRODUCTS * 2.0 * 128 * 64 * 128
+        tot["mmse_main"] += (c["u1_pairs"] * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR) +
+                             c["u1_boxes"] * (run * FLOPS_U1_BOX_TARGET + FLOPS_U1_ANCHOR) +
+                             c["u1_df_terms"] * FLOPS_U1_TERM_DF +
+                             c["u1_f32_terms"] * FLOPS_U1_TERM_F32) / (sweeps + 1)
+    return {"search": (tot["search"], "fp32"), "tables": (tot["tables"], "bf16"),
+            "mmse_main": (tot["mmse_main"], "fp32")}
+
+
 def measure_batched(args, binding, torch, stream, flush):
     """c3: 256 uneven instances solved (setup + 10 sweeps + J) as one batch,
     one at a time on the same fast path, and one at a time on the plain FP64
@@ -291,6 +311,25 @@ def measure_batched(args, binding, torch, stream, flush):
         Jb = b.eval_J()
         b.close()
     t_batch = float(np.median(times)) / 1e3
+    # one more batch, untimed, with per-kernel CUDA events around each kernel
+    # group of the 10 batched sweeps (kernel by kernel, no graph replay)
+    flush.fill_(1)
+    b = binding.Batch(ps, stream=stream)
+    b.profile(True)
+    b.sweep(10)
+    kern = b.kernel_times()
+    work = batched_work(ps, b, binding, sweeps=10)
+    b.close()
+    mp = load_peaks()
+    peak = {"fp32": binding.probe_alu(stream)["fp32_tflops"],
+            "bf16": mp.get("bf16_tflops_sustained", 1700.0)}
+    per_kernel = {}
+    for k, (w, pp) in work.items():
+        if k in kern and kern[k][0]:
+            ms_l = kern[k][1] / kern[k][0]
+            a_ = w / (ms_l / 1e3) / 1e12
+            per_kernel[k] = {"pipe": pp, "achieved_tflops": a_, "frac": a_ / peak[pp],
+                             "ms_per_launch": ms_l}
     # one at a time, same fast path
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     flush.fill_(1)
@@ -330,6 +369,8 @@ def measure_batched(args, binding, torch, stream, flush):
         "batched_vs_one_at_a_time": t_seq / t_batch,
         "batched_vs_plain_fp64": t_plain / t_batch,
         "max_abs_J_batched_vs_one_at_a_time": float(np.max(np.abs(Jb - Js))),
+        "kernels_ms_per_batch": {k: v[1] for k, v in kern.items()},
+        "roofline_per_kernel": per_kernel,
     }
 
 
@@ -556,6 +597,19 @@ def run_profile(args):
     import torch
     from paper_1908_04489_gb300 import binding, build
     build.build()
+    if args.workload == "c3":
+        # the first --batch-n instances of the batched workload, swept as one
+        # batch (captured-graph sweeps on a non-default stream)
+        from paper_1908_04489_gb300 import workloads as W
+        ps = W.c3()[:args.batch_n]
+        stream = torch.cuda.Stream() if args.profile_graph else None
+        with binding.Batch(ps, stream=stream) as b:
+            b.sweep(args.profile_sweeps)
+            J = b.eval_J()
+        print(json.dumps({"workload": "c3", "instances": len(ps), "J_mean": float(np.mean(J)),
+                          "sweeps": args.profile_sweeps, "graph": bool(args.profile_graph)}))
+        torch.cuda.synchronize()
+        return
     p, _ = workload(args.workload, args.precision)
     # on a non-default stream the sweeps replay captured graphs (the bench's
     # timed path); on the default stream they launch kernel by kernel
@@ -606,6 +660,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-n", type=int, default=256,
+                    help="with --workload c3 --profile-sweeps: batch size")
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=600)

@@ -219,6 +219,14 @@ UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* params, int3
 UCP_API ucp_status ucp_batch_sweep(ucp_batch* b, int32_t n_sweeps);
 /* Synchronise; J_out[k] = J of instance k (host array of n). */
 UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out);
+/* Per-kernel CUDA-event timing of batched sweeps (off by default), as
+ * ucp_profile / ucp_kernel_times for one instance: while on, batched sweeps
+ * launch kernel by kernel (no graph replay) with events around each kernel
+ * group (search, u1_boxes, u1_shift, mmse_main, mmse_combine, build_E,
+ * tables, tab_combine, J); enabling resets the totals. */
+UCP_API ucp_status ucp_batch_profile(ucp_batch* b, int32_t enable);
+UCP_API int32_t ucp_batch_kernel_times(ucp_batch* b, const char** names,
+                                       int64_t* launches, double* total_ms, int32_t cap);
 /* Member k as an instance handle (for ucp_get_controllers, ucp_J_history,
  * ...); owned by the batch, valid until ucp_batch_destroy. */
 UCP_API ucp_status ucp_batch_instance(ucp_batch* b, int32_t k, ucp_inst** out);

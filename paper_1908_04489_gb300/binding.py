@@ -136,6 +136,11 @@ def load():
     L.ucp_batch_eval_J.argtypes = [_vp, _dp]
     L.ucp_batch_instance.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(_vp)]
     L.ucp_batch_destroy.argtypes = [_vp]
+    L.ucp_batch_profile.argtypes = [_vp, ctypes.c_int32]
+    L.ucp_batch_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_char_p),
+                                         ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
+    L.ucp_batch_kernel_times.restype = ctypes.c_int32
     _lib = L
     return L
 
@@ -376,6 +381,17 @@ class Batch:
 
     def sweep(self, n: int = 1):
         _check(load().ucp_batch_sweep(self.h, int(n)), "ucp_batch_sweep")
+
+    def profile(self, on=True):
+        _check(load().ucp_batch_profile(self.h, int(bool(on))), "ucp_batch_profile")
+
+    def kernel_times(self) -> dict:
+        cap = 64
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = load().ucp_batch_kernel_times(self.h, names, launches, ms, cap)
+        return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
 
     def eval_J(self) -> np.ndarray:
         out = np.empty(len(self.params))

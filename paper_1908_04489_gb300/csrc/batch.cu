@@ -25,6 +25,7 @@ struct ucp_batch {
     bool poisoned = false;
     cudaGraphExec_t graph = nullptr;
     bool graph_tried = false;
+    Prof prof;   // per-kernel events (sweeps launch kernel by kernel while on)
 };
 
 namespace ucp {
@@ -138,6 +139,23 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
     return batchset_refresh(bs, members, s);
 }
 
+ucp_status batchset_first_step(BatchSet& bs, const std::vector<ucp_inst*>& members,
+                               cudaStream_t s) {
+    // descriptors under which the rest of a sweep acts on nu[0] (the initial
+    // f) and stores J in history slot 0; its last kernel then leaves cur = 0
+    // and sweeps = 0 on the device, the host-side state
+    for (InstDev& d : bs.desc) {
+        d.cur = 1;
+        d.sweeps = -1;
+    }
+    if (!bs.desc.empty())
+        cudaMemcpyAsync(bs.insts, bs.desc.data(), sizeof(InstDev) * bs.desc.size(),
+                        cudaMemcpyHostToDevice, s);
+    launch_batch_rest(bs.bl, s);
+    if (cudaGetLastError() != cudaSuccess) return UCP_E_CUDA;
+    return batchset_refresh(bs, members, s);
+}
+
 }  // namespace ucp
 
 namespace {
@@ -185,7 +203,7 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
     b->arena.ctx = ctx;
     for (int k = 0; k < n; ++k) {
         ucp_inst* in = nullptr;
-        ucp_status st = ucp_create(ctx, &params[k], stream, &in);
+        ucp_status st = inst_create(ctx, &params[k], (cudaStream_t)stream, false, &in);
         if (st != UCP_OK) {
             for (ucp_inst* m : b->members) ucp_destroy(m);
             delete b;
@@ -196,7 +214,8 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
     b->bs.arena = &b->arena;
     b->J_gather = (double*)b->arena.get(2 * sizeof(double) * (size_t)n);
     ucp_status st = b->J_gather ? batchset_build(b->bs, b->members, b->stream) : UCP_E_NOMEM;
-    if (st == UCP_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = UCP_E_CUDA;
+    // every member's first u1 update, tables and J in one batched launch
+    if (st == UCP_OK) st = batchset_first_step(b->bs, b->members, b->stream);
     if (st != UCP_OK) {
         set_error("%s%s", "ucp_batch_create: could not build the batch", "");
         for (ucp_inst* m : b->members) ucp_destroy(m);
@@ -235,7 +254,8 @@ extern "C" UCP_API ucp_status ucp_batch_sweep(ucp_batch* b, int32_t n_sweeps) {
         cudaGetLastError();  // a failed capture falls back to plain launches
     }
     for (int s = 0; s < n_sweeps; ++s) {
-        if (b->graph) cudaGraphLaunch(b->graph, b->stream);
+        if (b->prof.on) launch_batch_sweep(b->bs.bl, b->stream, &b->prof);
+        else if (b->graph) cudaGraphLaunch(b->graph, b->stream);
         else launch_batch_sweep(b->bs.bl, b->stream);
     }
     if (cudaGetLastError() != cudaSuccess) return fail(b, "ucp_batch_sweep");
@@ -269,6 +289,18 @@ extern "C" UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out) {
     return UCP_OK;
 }
 
+extern "C" UCP_API ucp_status ucp_batch_profile(ucp_batch* b, int32_t enable) {
+    if (!b) return UCP_E_ARG;
+    return prof_enable(&b->prof, b->stream, enable != 0);
+}
+
+extern "C" UCP_API int32_t ucp_batch_kernel_times(ucp_batch* b, const char** names,
+                                                  int64_t* launches, double* total_ms,
+                                                  int32_t cap) {
+    if (!b) return -1;
+    return prof_collect(&b->prof, names, launches, total_ms, cap);
+}
+
 extern "C" UCP_API ucp_status ucp_batch_instance(ucp_batch* b, int32_t k, ucp_inst** out) {
     if (!b || !out || k < 0 || k >= (int32_t)b->members.size()) return UCP_E_ARG;
     *out = b->members[k];
@@ -278,6 +310,7 @@ extern "C" UCP_API ucp_status ucp_batch_instance(ucp_batch* b, int32_t k, ucp_in
 extern "C" UCP_API ucp_status ucp_batch_destroy(ucp_batch* b) {
     if (!b) return UCP_E_ARG;
     cudaStreamSynchronize(b->stream);
+    b->prof.drain();
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (ucp_inst* m : b->members) ucp_destroy(m);
     b->arena.release_all();

@@ -31,4 +31,10 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
 ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
                             cudaStream_t s);
 
+// The set-up step of members created without it (inst_init with
+// first_step = false): the first u1 update, tables and J of every member in
+// one batched launch, then the descriptors as the host sees them.
+ucp_status batchset_first_step(BatchSet& bs, const std::vector<ucp_inst*>& members,
+                               cudaStream_t s);
+
 }  // namespace ucp

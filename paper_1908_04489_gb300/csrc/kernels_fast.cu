@@ -317,22 +317,33 @@ struct Coef {
 
 __device__ __forceinline__ dfloat df_x2(dfloat v) { return {2.0f * v.hi, 2.0f * v.lo}; }
 
-__device__ __forceinline__ Coef coef_of(const FastView& f, int64_t p) {
+// W2 = sum phi_l w_l^2 (set-up kernel's fixed-order sum, read from the
+// device) as double-float, and sqrt(W2) rounded up by 1e-4 in FP32.
+struct W2v {
+    dfloat w;
+    float sq;
+};
+__device__ __forceinline__ W2v w2_of(const FastView& f) {
+    const double W2 = __ldg(f.W2_dev);
+    return {df_from_double(W2), __fmul_rn(__double2float_rn(__dsqrt_rn(W2)), 1.0001f)};
+}
+
+__device__ __forceinline__ Coef coef_of(const FastView& f, int64_t p, const W2v& W2) {
     const dfloat P0 = f.P[p], P1 = f.P[p + 1];
     const dfloat Q0 = f.Q[p], Q1 = f.Q[p + 1];
     const dfloat R0 = f.R[p];
     Coef c;
-    c.a0 = df_add(dfloat{f.W2hi, f.W2lo}, df_add(df_x2(P0), Q0));
+    c.a0 = df_add(W2.w, df_add(df_x2(P0), Q0));
     c.a1 = df_add(df_add(df_x2(P1), df_neg(df_x2(P0))), df_add(df_x2(R0), df_neg(df_x2(Q0))));
     c.a2 = df_add(df_add(Q0, Q1), df_neg(df_x2(R0)));
     const float q0 = fmaxf(Q0.hi, 0.f), q1 = fmaxf(Q1.hi, 0.f);
-    const float rm = (f.sqrtW2 + fmaxf(sqrtf(q0), sqrtf(q1))) * 1.0001f;
+    const float rm = (W2.sq + fmaxf(sqrtf(q0), sqrtf(q1))) * 1.0001f;
     const float M = rm * rm * 1.0001f;
     const int64_t a1 = p >> 7, a2 = (p + 1) >> 7;
     const float bt = f.tc_bt[a1] + (a2 != a1 ? f.tc_bt[a2] : 0.f);
     const float p0 = fabsf(P0.hi), p1 = fabsf(P1.hi), r0 = fabsf(R0.hi);
     const float b0 = fabsf(c.a0.hi), b1 = fabsf(c.a1.hi), b2 = fabsf(c.a2.hi);
-    const float e_coef = 2.0f * (f.W2hi + 4.0f * p0 + 2.0f * q0) +
+    const float e_coef = 2.0f * (W2.w.hi + 4.0f * p0 + 2.0f * q0) +
                          8.0f * (p0 + p1 + r0 + q0) + 4.0f * (q0 + q1 + r0);
     const float e_eval = 5.0f * b2 + 7.0f * (b1 + b2) + 4.0f * (b0 + b1 + b2);
     c.b = (bt + f.beta_rel * M + f.beta_abs * (2.0f * rm + 1.0f) +
@@ -395,7 +406,7 @@ __device__ __forceinline__ Eval eval_table_direct(const Geom& g, const FastView&
     const int64_t p = cell - f.c_lo;
     if (p < 0 || p + 1 >= f.n_pos) return eval_outside(g, f, i, nu);
     const dfloat t = df_mul_f(df_from_i64(nu - cell * g.one), f.inv_one_f);
-    return eval_poly(g, f, i, nu, t, coef_of(f, p));
+    return eval_poly(g, f, i, nu, t, coef_of(f, p, w2_of(f)));
 }
 
 // lanes of this thread's group of G (groups may diverge from each other)
@@ -947,7 +958,7 @@ __device__ __forceinline__ bool J_partial_body(const Geom& g, const FastView& f,
 __device__ __forceinline__ void cells_body(const FastView& f, int64_t bx) {
     const int64_t p = bx * kJThreads + threadIdx.x;
     if (p + 1 >= f.n_pos) return;
-    const Coef c = coef_of(f, p);
+    const Coef c = coef_of(f, p, w2_of(f));
     f.C0[p] = c.a0;
     f.C1[p] = c.a1;
     f.C2[p] = c.a2;
@@ -1082,22 +1093,24 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     return 0;
 }
 
-void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s) {
-    launch_batch_search(bl, s);
-    launch_batch_rest(bl, s);
+void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
+    launch_batch_search(bl, s, prof);
+    launch_batch_rest(bl, s, prof);
 }
 
-void launch_batch_search(const BatchLaunch& bl, cudaStream_t s) {
+void launch_batch_search(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
     const InstDev* d = bl.insts;
+    ProfScope ps(prof, "search");
     if (bl.search_blocks)
         kb_search<<<(unsigned)bl.search_blocks, kSearchT, 0, s>>>(d, bl.search_map);
     if (bl.defer_blocks)
         kb_search_deferred<<<(unsigned)bl.defer_blocks, kCoopT, 0, s>>>(d, bl.defer_map);
 }
 
-void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s) {
-    launch_batch_u1(bl, s);
-    launch_batch_tables(bl, s);
+void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
+    launch_batch_u1(bl, s, prof);
+    launch_batch_tables(bl, s, prof);
+    ProfScope ps(prof, "J");
     kb_J_partial<<<(unsigned)bl.n_blocks[kBJPart], kJThreads, 0, s>>>(bl.insts,
                                                                    bl.map[kBJPart]);
 }

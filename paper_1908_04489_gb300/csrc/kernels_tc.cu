@@ -522,10 +522,17 @@ void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud
     if (prof) prof->end(k, ev);
 }
 
-void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s) {
+void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
     const InstDev* d = bl.insts;
-    kb_build_E_tc<<<(unsigned)bl.n_blocks[kBBuildE], 128, 0, s>>>(d, bl.map[kBBuildE]);
-    kb_tc_tables<<<(unsigned)bl.n_blocks[kBTabPart], kTcT, kTcSmem, s>>>(d, bl.map[kBTabPart]);
+    {
+        ProfScope ps(prof, "build_E");
+        kb_build_E_tc<<<(unsigned)bl.n_blocks[kBBuildE], 128, 0, s>>>(d, bl.map[kBBuildE]);
+    }
+    {
+        ProfScope ps(prof, "tables");
+        kb_tc_tables<<<(unsigned)bl.n_blocks[kBTabPart], kTcT, kTcSmem, s>>>(d, bl.map[kBTabPart]);
+    }
+    ProfScope ps(prof, "tab_combine");
     kb_tc_combine<<<(unsigned)bl.n_blocks[kBTabComb], kCombT, 0, s>>>(d, bl.map[kBTabComb]);
 }
 

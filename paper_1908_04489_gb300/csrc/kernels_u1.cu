@@ -765,23 +765,33 @@ int64_t batch_mmse_blocks(const Geom&, const FastPlan& fp) {
     return fp.r_blocks * fp.n_tiles;
 }
 
-void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s) {
+void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
     const InstDev* d = bl.insts;
-    kb_box_plan<<<(unsigned)bl.n_blocks[kBTile], kPlanT, 0, s>>>(d, bl.map[kBTile]);
-    kb_box_moments<<<(unsigned)bl.n_blocks[kBBox], kMomT, 0, s>>>(d, bl.map[kBBox]);
-    kb_run_shift<<<(unsigned)bl.n_blocks[kBRun], kRunT, 0, s>>>(d, bl.map[kBRun]);
-    for (int r = 0; r < 5; ++r) {
-        if (bl.mmse_blocks[r] == 0) continue;
-        const unsigned nb = (unsigned)bl.mmse_blocks[r];
-        const BlockRef* m = bl.mmse_map[r];
-        switch (r) {
-            case 0: launch_kb_u1_main<1>(nb, d, m, s); break;
-            case 1: launch_kb_u1_main<2>(nb, d, m, s); break;
-            case 2: launch_kb_u1_main<4>(nb, d, m, s); break;
-            case 3: launch_kb_u1_main<8>(nb, d, m, s); break;
-            default: launch_kb_u1_main<16>(nb, d, m, s); break;
+    {
+        ProfScope ps(prof, "u1_boxes");
+        kb_box_plan<<<(unsigned)bl.n_blocks[kBTile], kPlanT, 0, s>>>(d, bl.map[kBTile]);
+        kb_box_moments<<<(unsigned)bl.n_blocks[kBBox], kMomT, 0, s>>>(d, bl.map[kBBox]);
+    }
+    {
+        ProfScope ps(prof, "u1_shift");
+        kb_run_shift<<<(unsigned)bl.n_blocks[kBRun], kRunT, 0, s>>>(d, bl.map[kBRun]);
+    }
+    {
+        ProfScope ps(prof, "mmse_main");
+        for (int r = 0; r < 5; ++r) {
+            if (bl.mmse_blocks[r] == 0) continue;
+            const unsigned nb = (unsigned)bl.mmse_blocks[r];
+            const BlockRef* m = bl.mmse_map[r];
+            switch (r) {
+                case 0: launch_kb_u1_main<1>(nb, d, m, s); break;
+                case 1: launch_kb_u1_main<2>(nb, d, m, s); break;
+                case 2: launch_kb_u1_main<4>(nb, d, m, s); break;
+                case 3: launch_kb_u1_main<8>(nb, d, m, s); break;
+                default: launch_kb_u1_main<16>(nb, d, m, s); break;
+            }
         }
     }
+    ProfScope ps(prof, "mmse_combine");
     kb_u1_combine<<<(unsigned)bl.n_blocks[kBPerY], 256, 0, s>>>(d, bl.map[kBPerY]);
 }
 

@@ -99,8 +99,7 @@ int prof_collect(Prof* p, const char** names, int64_t* launches, double* ms,
 
 // ---- device memory --------------------------------------------------------
 
-void* Arena::get(size_t n) {
-    n = (n + 255) & ~(size_t)255;
+static void* raw_alloc(ucp_ctx* ctx, size_t n) {
     void* p = nullptr;
     if (ctx && ctx->alloc) {
         p = ctx->alloc(n, ctx->user);
@@ -108,26 +107,53 @@ void* Arena::get(size_t n) {
         cudaGetLastError();
         p = nullptr;
     }
+    return p;
+}
+
+static void raw_free(ucp_ctx* ctx, void* p) {
+    if (ctx && ctx->free_fn) ctx->free_fn(p, ctx->user);
+    else cudaFree(p);
+}
+
+bool Arena::reserve(size_t n) {
+    if (slab) return false;
+    n = (n + 255) & ~(size_t)255;
+    slab = (char*)raw_alloc(ctx, n);
+    if (!slab) return false;
+    slab_size = n;
+    slab_used = 0;
+    bytes += n;
+    return true;
+}
+
+void* Arena::get(size_t n) {
+    n = (n + 255) & ~(size_t)255;
+    if (slab && slab_used + n <= slab_size) {
+        void* p = slab + slab_used;
+        slab_used += n;
+        return p;
+    }
+    void* p = raw_alloc(ctx, n);
     if (p) { ptrs.push_back(p); bytes += n; }
     return p;
 }
 
 void Arena::put(void* p) {
+    if (slab && (char*)p >= slab && (char*)p < slab + slab_size) return;
     for (size_t k = 0; k < ptrs.size(); ++k)
         if (ptrs[k] == p) {
-            if (ctx && ctx->free_fn) ctx->free_fn(p, ctx->user);
-            else cudaFree(p);
+            raw_free(ctx, p);
             ptrs.erase(ptrs.begin() + k);
             return;
         }
 }
 
 void Arena::release_all() {
-    for (void* p : ptrs) {
-        if (ctx && ctx->free_fn) ctx->free_fn(p, ctx->user);
-        else cudaFree(p);
-    }
+    for (void* p : ptrs) raw_free(ctx, p);
     ptrs.clear();
+    if (slab) raw_free(ctx, slab);
+    slab = nullptr;
+    slab_size = slab_used = 0;
     bytes = 0;
 }
 
@@ -301,14 +327,6 @@ static ucp_status fast_alloc(ucp_inst* in) {
     return UCP_OK;
 }
 
-static void fast_set_W2(ucp_inst* in) {
-    FastView& f = in->fv;
-    const dfloat w = df_from_double(f.W2);
-    f.W2hi = w.hi;
-    f.W2lo = w.lo;
-    f.sqrtW2 = (float)sqrt(f.W2) * 1.0001f;
-}
-
 static ucp_status fast_refresh(ucp_inst* in, int slot) {
     const Geom& g = in->g;
     DevState& d = in->d;
@@ -318,7 +336,7 @@ static ucp_status fast_refresh(ucp_inst* in, int slot) {
 }
 
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
-                     const Geom& g, cudaStream_t stream) {
+                     const Geom& g, cudaStream_t stream, bool first_step) {
     in->ctx = ctx;
     in->params = p;
     in->params.init_table = nullptr;
@@ -331,6 +349,8 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     DevState& d = in->d;
     Arena& A = in->arena;
     const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
+    // every buffer below from one allocation (inst_bytes counts them all)
+    A.reserve(inst_bytes(g, p.precision));
     d.px = (double*)A.get(8 * nx);
     d.phi = (double*)A.get(8 * nw);
     d.U = (double*)A.get(8 * ny);
@@ -368,9 +388,6 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
         cudaMemsetAsync(in->fv.J_done, 0, 4, s);
         cudaMemsetAsync(in->fv.tc_err, 0, 4, s);
         cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
-        cudaMemcpyAsync(&in->fv.W2, in->fv.W2_dev, 8, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "fast setup");
-        fast_set_W2(in);
         if (p.init_kind == 2) {
             double fm = 0.0;
             for (int64_t i = 0; i < g.n_x; ++i)
@@ -390,6 +407,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     cudaMemsetAsync(d.idx, 0xff, 4 * nx, s);
     in->cur = 0;
     in->sweeps_done = 0;
+    if (in->fast && !first_step) return check(in, "set-up");
     if (in->fast) {
         launch_mmse_fast(g, in->fv, d.nu[0], d.U, s, &in->prof);
         return fast_refresh(in, 0);

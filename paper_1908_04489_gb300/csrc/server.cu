@@ -53,9 +53,23 @@ struct Pool {
     std::vector<void*> all;
 };
 
+// Block sizes are rounded up to buckets spaced by an eighth of their power of
+// two, so that instances of nearby sizes (sigma and the grid widths vary
+// continuously across requests) reuse each other's blocks.  Admission counts
+// the bytes a request uses; the pooled blocks holding them are at most 12.5%
+// larger.
+size_t pool_bucket(size_t n) {
+    n = (n + 255) & ~(size_t)255;
+    size_t b = 256;
+    while (b * 2 <= n) b *= 2;
+    const size_t step = b / 8 > 256 ? b / 8 : 256;
+    return (n + step - 1) / step * step;
+}
+
 void pool_free(void* q, void* user);
 void* pool_alloc(size_t n, void* user) {
     Pool* p = (Pool*)user;
+    n = pool_bucket(n);
     {
         std::lock_guard<std::mutex> lock(p->mu);
         auto it = p->free_blocks.find(n);
@@ -104,7 +118,8 @@ struct ucp_srv {
     ucp_status fail_status = UCP_OK;
     std::thread th;
     Arena arena;
-    BatchSet bs;
+    BatchSet bs;    // the active requests (one batched sweep per step)
+    BatchSet adm;   // the requests admitted in a step (their set-up step)
     Clock::time_point t0;
     uint64_t steps = 0, completed = 0;
     int max_active = 0;
@@ -165,10 +180,11 @@ void loop(ucp_srv* s) {
                 admitted.push_back(r);
             }
         }
+        std::vector<ucp_inst*> fresh;
         for (auto& r : admitted) {
             if (!r->table.empty()) r->p.init_table = r->table.data();
             ucp_inst* in = nullptr;
-            ucp_status st = ucp_create(&s->own, &r->p, s->stream, &in);
+            ucp_status st = inst_create(&s->own, &r->p, s->stream, false, &in);
             if (st == UCP_OK) st = grow_history(in, r->sweeps + 1);
             if (st != UCP_OK) {
                 if (in) ucp_destroy(in);
@@ -181,7 +197,17 @@ void loop(ucp_srv* s) {
             }
             r->inst = in;
             s->active.push_back(r);
+            fresh.push_back(in);
             membership_changed = true;
+        }
+        if (!fresh.empty()) {
+            // the admitted requests' first u1 update, tables and J, batched
+            ucp_status st = batchset_build(s->adm, fresh, s->stream);
+            if (st == UCP_OK) st = batchset_first_step(s->adm, fresh, s->stream);
+            if (st != UCP_OK) {
+                fail_all(s, st);
+                continue;
+            }
         }
         if (s->active.empty()) continue;
         bool inject = false;
@@ -269,6 +295,7 @@ extern "C" UCP_API ucp_status ucp_srv_create(ucp_ctx* ctx, uint64_t hbm_budget_b
     s->own.user = &s->pool;
     s->arena.ctx = &s->own;
     s->bs.arena = &s->arena;
+    s->adm.arena = &s->arena;
     s->t0 = Clock::now();
     s->th = std::thread(loop, s);
     *out = s;

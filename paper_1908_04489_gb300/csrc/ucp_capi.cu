@@ -185,8 +185,8 @@ extern "C" ucp_status ucp_ctx_destroy(ucp_ctx* ctx) {
 
 // ---- instance ---------------------------------------------------------
 
-extern "C" ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params,
-                                 void* stream, ucp_inst** out) {
+ucp_status ucp::inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t stream,
+                            bool first_step, ucp_inst** out) {
     if (!params || !out) {
         set_error("ucp_create: %s%s", "NULL argument", "");
         return UCP_E_ARG;
@@ -202,7 +202,7 @@ extern "C" ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params,
         return UCP_E_ARG;
     }
     ucp_inst* in = new ucp_inst();
-    ucp_status st = inst_init(in, ctx, *params, g, (cudaStream_t)stream);
+    ucp_status st = inst_init(in, ctx, *params, g, stream, first_step);
     if (st != UCP_OK) {
         inst_release(in);
         delete in;
@@ -210,6 +210,11 @@ extern "C" ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params,
     }
     *out = in;
     return UCP_OK;
+}
+
+extern "C" ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params,
+                                 void* stream, ucp_inst** out) {
+    return inst_create(ctx, params, (cudaStream_t)stream, true, out);
 }
 
 extern "C" ucp_status ucp_sizes(const ucp_inst* in, uint64_t* n_x, uint64_t* n_w,

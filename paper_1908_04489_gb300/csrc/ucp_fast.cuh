@@ -28,7 +28,7 @@ void u1_plan(const Geom& g, int max_tiles, FastPlan* fp);
 size_t u1_scratch_bytes(const Geom& g, const FastPlan& fp, size_t align);
 bool u1_carve(const Geom& g, FastView* f, void* (*get)(void*, size_t), void* ctx);
 int64_t u1_batch_blocks(const Geom& g, const FastPlan& fp, int kind);
-void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s);
+void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
                       double* U, cudaStream_t s, Prof* prof);
@@ -48,7 +48,7 @@ cudaError_t tc_init_attributes();
 void launch_tc_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
                    cudaStream_t s, Prof* prof);
-void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s);
+void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
                         int64_t* nu_out, int32_t* idx, cudaStream_t s);
 // Blocks of each batched kernel kind for one instance (fast_plan sizes).
@@ -56,9 +56,10 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind);
 int64_t batch_mmse_blocks(const Geom& g, const FastPlan& fp);
 // One sweep of every instance of the batch (search, u1, tables, J; then the
 // device-side cur / sweep counters advance); or its search alone, or the rest.
-void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s);
-void launch_batch_search(const BatchLaunch& bl, cudaStream_t s);
-void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s);
+// With a profiler, each kernel group is timed by CUDA events on `s`.
+void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
+void launch_batch_search(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
+void launch_batch_rest(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
 void launch_J_fast(const Geom& g, const FastView& f, const double* px,
                    const int64_t* nu, double* out, cudaStream_t s, Prof* prof);
 

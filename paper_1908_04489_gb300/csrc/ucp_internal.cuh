@@ -132,9 +132,6 @@ struct FastView : FastPlan {
     void* defer_list;    // [n_x] their records (search position, carried winner)
     int64_t* n_pairs;    // [4] u1 work: direct (source, run) pairs, (box, run)
                          // expansions, double-float and FP32 Taylor terms
-    double W2;           // host copy of *W2_dev
-    float W2hi, W2lo;    // W2 as double-float
-    float sqrtW2;
     float step_hi, step_lo;   // delta 2^-shift as double-float
     float delta_hi, delta_lo; // delta as double-float
     float kk_hi, kk_lo;       // k^2 as double-float

@@ -41,19 +41,39 @@ struct Prof {
     ~Prof();
 };
 
+// Times the launches made during its lifetime as one entry of `p` (no-op
+// when p is null or off).
+struct ProfScope {
+    Prof* p;
+    int k = -1;
+    cudaEvent_t a = nullptr;
+    ProfScope(Prof* p_, const char* name) : p(p_) {
+        if (p) k = p->begin(name, &a);
+    }
+    ~ProfScope() {
+        if (p) p->end(k, a);
+    }
+};
+
 ucp_status prof_enable(Prof* p, cudaStream_t s, bool on);
 int prof_collect(Prof* p, const char** names, int64_t* launches, double* ms,
                  int cap);
 
 struct BatchSet;  // batch_set.h
 
-// Owner of device allocations made through a context.
+// Owner of device allocations made through a context.  After reserve(n),
+// get() carves 256-byte aligned pieces from that one allocation while it
+// lasts (one allocator call per instance instead of one per buffer); carved
+// pieces are returned with the slab by release_all().
 struct Arena {
     ucp_ctx* ctx = nullptr;
     std::vector<void*> ptrs;
     size_t bytes = 0;
-    void* get(size_t n);   // nullptr on failure
-    void put(void* p);
+    char* slab = nullptr;
+    size_t slab_size = 0, slab_used = 0;
+    bool reserve(size_t n);   // false if the allocation failed (get() still works)
+    void* get(size_t n);      // nullptr on failure
+    void put(void* p);        // frees a separately allocated block; no-op in the slab
     void release_all();
 };
 
@@ -89,8 +109,15 @@ namespace ucp {
 
 // Device bytes one instance allocates (matches inst_init).
 size_t inst_bytes(const Geom& g, int precision);
+// Set up an instance on `stream`: buffers, grids, weights, init and, with
+// first_step, the first u1 update, tables and J (J history slot 0).  A fast
+// instance set up without it gets that step from a batched launch
+// (batch_first_step) before its first sweep.
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
-                     const Geom& g, cudaStream_t stream);
+                     const Geom& g, cudaStream_t stream, bool first_step = true);
+// ucp_create with the choice above (validates the parameters).
+ucp_status inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t stream,
+                       bool first_step, ucp_inst** out);
 ucp_status inst_sweep(ucp_inst* in, int n);
 // Make room in the J history for `need` entries (synchronises on growth).
 ucp_status grow_history(ucp_inst* in, long long need);
