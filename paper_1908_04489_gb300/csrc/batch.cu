@@ -26,6 +26,7 @@ struct ucp_batch {
     cudaGraphExec_t graph = nullptr;
     bool graph_tried = false;
     Prof prof;   // per-kernel events (sweeps launch kernel by kernel while on)
+    SetupSet ss;
 };
 
 namespace ucp {
@@ -139,18 +140,80 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
     return batchset_refresh(bs, members, s);
 }
 
-ucp_status batchset_first_step(BatchSet& bs, const std::vector<ucp_inst*>& members,
-                               cudaStream_t s) {
-    // descriptors under which the rest of a sweep acts on nu[0] (the initial
-    // f) and stores J in history slot 0; its last kernel then leaves cur = 0
-    // and sweeps = 0 on the device, the host-side state
+// Grow a device array of `cap` elements to hold n (after the stream drains,
+// as the old one may be in use).
+template <typename T>
+static ucp_status grow(Arena* arena, T*& p, size_t& cap, size_t n, cudaStream_t s) {
+    if (n <= cap && p) return UCP_OK;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return UCP_E_CUDA;
+    if (p) arena->put(p);
+    cap = n + n / 2 + 8;
+    p = (T*)arena->get(sizeof(T) * cap);
+    if (!p) {
+        cap = 0;
+        return UCP_E_NOMEM;
+    }
+    return UCP_OK;
+}
+
+ucp_status batchset_setup(SetupSet& ss, BatchSet& bs, const std::vector<ucp_inst*>& members,
+                          cudaStream_t s) {
+    const size_t n = members.size();
+    if (n == 0) return UCP_OK;
+    ss.desc.resize(n);
+    std::vector<BlockRef> elem, inst, filt;
+    for (size_t k = 0; k < n; ++k) {
+        const ucp_inst* in = members[k];
+        SetupDev& d = ss.desc[k];
+        memset(&d, 0, sizeof(d));
+        d.g = in->g;
+        d.f = in->fv;
+        d.px = in->d.px;
+        d.phi = in->d.phi;
+        d.coarse = in->d.coarse;
+        d.scratch = in->d.scratch;
+        d.nu0 = in->d.nu[0];
+        d.idx = in->d.idx;
+        d.table = in->d.table;
+        d.init_kind = in->params.init_kind;
+        init_levels(in->g, d.init_kind, &d.n7, d.lv);
+        const int64_t ne = setup_elem_blocks(in->g);
+        for (int64_t x = 0; x < ne; ++x) elem.push_back({(int32_t)k, (int32_t)x});
+        inst.push_back({(int32_t)k, 0});
+        for (int64_t x = 0; x < 2 * (int64_t)in->fv.tc_nch + 1; ++x)
+            filt.push_back({(int32_t)k, (int32_t)x});
+    }
+    ss.host_maps.clear();
+    ss.host_maps.insert(ss.host_maps.end(), elem.begin(), elem.end());
+    ss.host_maps.insert(ss.host_maps.end(), inst.begin(), inst.end());
+    ss.host_maps.insert(ss.host_maps.end(), filt.begin(), filt.end());
+    ucp_status st = grow(ss.arena, ss.descs, ss.descs_cap, n, s);
+    if (st == UCP_OK) st = grow(ss.arena, ss.maps, ss.maps_cap, ss.host_maps.size(), s);
+    if (st != UCP_OK) return st;
+    cudaMemcpyAsync(ss.descs, ss.desc.data(), sizeof(SetupDev) * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(ss.maps, ss.host_maps.data(), sizeof(BlockRef) * ss.host_maps.size(),
+                    cudaMemcpyHostToDevice, s);
+    SetupLaunch sl;
+    sl.descs = ss.descs;
+    sl.elem_map = ss.maps;
+    sl.elem_blocks = (int64_t)elem.size();
+    sl.inst_map = ss.maps + elem.size();
+    sl.inst_blocks = (int64_t)inst.size();
+    sl.filter_map = ss.maps + elem.size() + inst.size();
+    sl.filter_blocks = (int64_t)filt.size();
+    launch_batch_setup_plain(sl, s);
+    launch_batch_setup_fast(sl, s);
+    launch_batch_setup_tc(sl, s);
+    if (cudaGetLastError() != cudaSuccess) return UCP_E_CUDA;
+    // the first step: the rest of a sweep under descriptors that make it act
+    // on nu[0] (the initial f) and store J in history slot 0; its last kernel
+    // then leaves cur = 0 and sweeps = 0 on the device, the host-side state
     for (InstDev& d : bs.desc) {
         d.cur = 1;
         d.sweeps = -1;
     }
-    if (!bs.desc.empty())
-        cudaMemcpyAsync(bs.insts, bs.desc.data(), sizeof(InstDev) * bs.desc.size(),
-                        cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(bs.insts, bs.desc.data(), sizeof(InstDev) * bs.desc.size(),
+                    cudaMemcpyHostToDevice, s);
     launch_batch_rest(bs.bl, s);
     if (cudaGetLastError() != cudaSuccess) return UCP_E_CUDA;
     return batchset_refresh(bs, members, s);
@@ -212,10 +275,11 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
         b->members.push_back(in);
     }
     b->bs.arena = &b->arena;
+    b->ss.arena = &b->arena;
     b->J_gather = (double*)b->arena.get(2 * sizeof(double) * (size_t)n);
     ucp_status st = b->J_gather ? batchset_build(b->bs, b->members, b->stream) : UCP_E_NOMEM;
-    // every member's first u1 update, tables and J in one batched launch
-    if (st == UCP_OK) st = batchset_first_step(b->bs, b->members, b->stream);
+    // every member's set-up and first u1 update, tables and J, batched
+    if (st == UCP_OK) st = batchset_setup(b->ss, b->bs, b->members, b->stream);
     if (st != UCP_OK) {
         set_error("%s%s", "ucp_batch_create: could not build the batch", "");
         for (ucp_inst* m : b->members) ucp_destroy(m);

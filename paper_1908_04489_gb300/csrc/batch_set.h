@@ -31,10 +31,21 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
 ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
                             cudaStream_t s);
 
-// The set-up step of members created without it (inst_init with
-// first_step = false): the first u1 update, tables and J of every member in
-// one batched launch, then the descriptors as the host sees them.
-ucp_status batchset_first_step(BatchSet& bs, const std::vector<ucp_inst*>& members,
-                               cudaStream_t s);
+// Batched set-up of members created without their own (inst_init with
+// own_setup = false): weights, coarse list, init, counters, the fast path's
+// constants and filter slices (five launches for all members), then the first
+// u1 update, tables and J as the rest of one batched sweep (bs built for the
+// same members), and the descriptors as the host sees them.
+struct SetupSet {
+    Arena* arena = nullptr;
+    SetupDev* descs = nullptr;
+    size_t descs_cap = 0;
+    BlockRef* maps = nullptr;
+    size_t maps_cap = 0;
+    std::vector<SetupDev> desc;
+    std::vector<BlockRef> host_maps;
+};
+ucp_status batchset_setup(SetupSet& ss, BatchSet& bs, const std::vector<ucp_inst*>& members,
+                          cudaStream_t s);
 
 }  // namespace ucp

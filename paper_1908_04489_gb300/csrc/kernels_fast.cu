@@ -882,10 +882,11 @@ __global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
 }
 
 // Per-instance constants: a_l = phi_l w_l and phi_l in double-float, the
-// prior exponent x_i^2 / 2 sigma^2, W2 = sum phi_l w_l^2 (fixed-order tree),
-// and the constant table (df_exp's exp(k/64), the inverse factorials).
-__global__ void k_fast_setup(Geom g, FastView f) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// prior exponent x_i^2 / 2 sigma^2 and the constant table (df_exp's
+// exp(k/64), the inverse factorials).  W2 = sum phi_l w_l^2 is formed with
+// the filter slices (kernels_tc.cu).
+static_assert(kConstTab <= 128, "constant table within the set-up blocks");
+__device__ __forceinline__ void fast_setup_elem(const Geom& g, const FastView& f, int64_t k) {
     if (k < g.n_w) {
         const double w = (double)(k - g.hw) * g.delta;
         f.a[k] = df_from_double(f.phi[k] * w);
@@ -897,21 +898,17 @@ __global__ void k_fast_setup(Geom g, FastView f) {
         f.prior[k] = df_from_double(__ddiv_rn(__dmul_rn(x, x), g.two_s2));
     }
     if (k < kConstTab) f.t64[k] = const_table_entry((int)k);
-    if (blockIdx.x == 0) {   // W2: strided partial sums, then a fixed tree
-        __shared__ double red[256];
-        double s = 0.0;
-        for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x) {
-            const double w = (double)(l - g.hw) * g.delta;
-            s += f.phi[l] * (w * w);
-        }
-        red[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) *f.W2_dev = red[0];
-    }
+}
+
+__global__ void k_fast_setup(Geom g, FastView f) {
+    fast_setup_elem(g, f, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256) kb_fast_setup(const SetupDev* descs,
+                                                     const BlockRef* map) {
+    const BlockRef r = map[blockIdx.x];
+    const SetupDev& d = descs[r.inst];
+    fast_setup_elem(d.g, d.f, (int64_t)r.local * blockDim.x + threadIdx.x);
 }
 
 // ---- J --------------------------------------------------------------------
@@ -1068,6 +1065,11 @@ void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s) {
     int64_t n = g.n_w > g.n_x ? g.n_w : g.n_x;
     n = n > kConstTab ? n : kConstTab;
     k_fast_setup<<<blocks(n, 256), 256, 0, s>>>(g, f);
+}
+
+void launch_batch_setup_fast(const SetupLaunch& sl, cudaStream_t s) {
+    if (sl.elem_blocks)
+        kb_fast_setup<<<(unsigned)sl.elem_blocks, 256, 0, s>>>(sl.descs, sl.elem_map);
 }
 
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,

@@ -93,8 +93,8 @@ __device__ __forceinline__ void group_argmin(double& gv, int32_t& pos,
 // order), then the divisions over the grid.
 constexpr int kWeightChunks = 1024;   // chunk sums held in shared memory per pass
 
-__global__ void k_weights_exp(Geom g, double* px, double* phi) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void weights_exp_elem(const Geom& g, double* px, double* phi,
+                                                 int64_t k) {
     if (k < g.n_x) {
         const double xi = x_of(g, k);
         px[k] = exp(-__ddiv_rn(__dmul_rn(xi, xi), g.two_s2));
@@ -103,6 +103,10 @@ __global__ void k_weights_exp(Geom g, double* px, double* phi) {
         const double wl = __dmul_rn((double)(k - g.hw), g.delta);
         phi[k] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
     }
+}
+
+__global__ void k_weights_exp(Geom g, double* px, double* phi) {
+    weights_exp_elem(g, px, phi, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __device__ double block_fixed_sum(const double* __restrict__ v, int64_t n,
@@ -129,8 +133,8 @@ __device__ double block_fixed_sum(const double* __restrict__ v, int64_t n,
     return total;
 }
 
-__global__ void k_weights_sum(Geom g, const double* px, const double* phi,
-                              double* tot) {
+__device__ __forceinline__ void weights_sum_body(const Geom& g, const double* px,
+                                                 const double* phi, double* tot) {
     __shared__ double s_chunk[kWeightChunks];
     const double a = block_fixed_sum(px, g.n_x, s_chunk);
     const double b = block_fixed_sum(phi, g.n_w, s_chunk);
@@ -140,18 +144,28 @@ __global__ void k_weights_sum(Geom g, const double* px, const double* phi,
     }
 }
 
-__global__ void k_weights_scale(Geom g, double* px, double* phi,
-                                const double* __restrict__ tot) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_weights_sum(Geom g, const double* px, const double* phi,
+                              double* tot) {
+    weights_sum_body(g, px, phi, tot);
+}
+
+__device__ __forceinline__ void weights_scale_elem(const Geom& g, double* px, double* phi,
+                                                   const double* __restrict__ tot,
+                                                   int64_t k) {
     if (k < g.n_x) px[k] = __ddiv_rn(px[k], tot[0]);
     if (k < g.n_w) phi[k] = __ddiv_rn(phi[k], tot[1]);
 }
 
+__global__ void k_weights_scale(Geom g, double* px, double* phi,
+                                const double* __restrict__ tot) {
+    weights_scale_elem(g, px, phi, tot, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // kind 0: identity f(x) = x; kind 1: odd staircase with step n7 (units of
 // delta) and level lattice indices lv[0..2].
-__global__ void k_init(Geom g, int kind, int64_t n7, int64_t lv0, int64_t lv1,
-                       int64_t lv2, int64_t* nu) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void init_elem(const Geom& g, int kind, int64_t n7, int64_t lv0,
+                                          int64_t lv1, int64_t lv2, int64_t* nu,
+                                          int64_t i) {
     if (i >= g.n_x) return;
     const int64_t a = i - g.hx;
     if (kind == 0) {
@@ -164,17 +178,69 @@ __global__ void k_init(Geom g, int kind, int64_t n7, int64_t lv0, int64_t lv1,
     }
 }
 
-__global__ void k_table_to_lattice(Geom g, const double* table, int64_t* nu) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_init(Geom g, int kind, int64_t n7, int64_t lv0, int64_t lv1,
+                       int64_t lv2, int64_t* nu) {
+    init_elem(g, kind, n7, lv0, lv1, lv2, nu, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__device__ __forceinline__ void table_to_lattice_elem(const Geom& g, const double* table,
+                                                      int64_t* nu, int64_t i) {
     if (i >= g.n_x) return;
     const double v = __dmul_rn(__ddiv_rn(table[i], g.delta), (double)g.one);
     nu[i] = llround(v);
 }
 
-__global__ void k_coarse(Geom g, int64_t* coarse) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_table_to_lattice(Geom g, const double* table, int64_t* nu) {
+    table_to_lattice_elem(g, table, nu, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__device__ __forceinline__ void coarse_elem(const Geom& g, int64_t* coarse, int64_t j) {
     if (j >= g.n_coarse) return;
     coarse[j] = (int64_t)(2 * j - (g.n_coarse - 1)) * (g.q / 2) * g.one;
+}
+
+__global__ void k_coarse(Geom g, int64_t* coarse) {
+    coarse_elem(g, coarse, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- batched set-up (one launch per step for many instances) ----------------
+// Block r of a map works on element block r.local of instance r.inst, with
+// the single-instance kernels' per-element code.
+
+// Exponentials of the weights, coarse list, initial controller, cleared
+// counters and winner positions.
+__global__ void __launch_bounds__(256) kb_setup_elem(const SetupDev* descs,
+                                                     const BlockRef* map) {
+    const BlockRef r = map[blockIdx.x];
+    const SetupDev& d = descs[r.inst];
+    const int64_t k = (int64_t)r.local * blockDim.x + threadIdx.x;
+    weights_exp_elem(d.g, d.px, d.phi, k);
+    coarse_elem(d.g, d.coarse, k);
+    if (d.init_kind == 2) table_to_lattice_elem(d.g, d.table, d.nu0, k);
+    else init_elem(d.g, d.init_kind, d.n7, d.lv[0], d.lv[1], d.lv[2], d.nu0, k);
+    if (k < d.g.n_x) d.idx[k] = -1;
+    if (k == 0) {
+        *d.f.n_exact = 0;
+        *d.f.n_tier2 = 0;
+        *d.f.defer_cnt = 0;
+        *d.f.J_done = 0;
+        *d.f.tc_err = 0;
+    }
+    if (k < 4) d.f.n_pairs[k] = 0;
+}
+
+__global__ void __launch_bounds__(1024) kb_weights_sum(const SetupDev* descs,
+                                                      const BlockRef* map) {
+    const SetupDev& d = descs[map[blockIdx.x].inst];
+    weights_sum_body(d.g, d.px, d.phi, d.scratch);
+}
+
+__global__ void __launch_bounds__(256) kb_weights_scale(const SetupDev* descs,
+                                                        const BlockRef* map) {
+    const BlockRef r = map[blockIdx.x];
+    const SetupDev& d = descs[r.inst];
+    weights_scale_elem(d.g, d.px, d.phi, d.scratch,
+                       (int64_t)r.local * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_f_values(Geom g, const int64_t* nu, double* out, int as_u0) {
@@ -333,13 +399,33 @@ void launch_weights(const Geom& g, DevState& d, cudaStream_t s) {
     k_weights_scale<<<nb, 256, 0, s>>>(g, d.px, d.phi, d.scratch);
 }
 
-void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s) {
-    int64_t n7 = 1, lv[3] = {0, 0, 0};
+void init_levels(const Geom& g, int kind, int64_t* n7, int64_t lv[3]) {
+    *n7 = 1;
+    lv[0] = lv[1] = lv[2] = 0;
     if (kind == 1) {
-        n7 = llround(7.0 / g.delta);
+        *n7 = llround(7.0 / g.delta);
         for (int m = 0; m < 3; ++m)
             lv[m] = llround(3.5 * (double)(2 * m + 1) / g.delta * (double)g.one);
     }
+}
+
+int64_t setup_elem_blocks(const Geom& g) {
+    int64_t n = g.n_x > g.n_w ? g.n_x : g.n_w;
+    n = n > g.n_coarse ? n : g.n_coarse;
+    n = n > 128 ? n : 128;   // the fast path's constant table (<= 128 entries)
+    return (n + 255) / 256;
+}
+
+void launch_batch_setup_plain(const SetupLaunch& sl, cudaStream_t s) {
+    if (!sl.elem_blocks) return;
+    kb_setup_elem<<<(unsigned)sl.elem_blocks, 256, 0, s>>>(sl.descs, sl.elem_map);
+    kb_weights_sum<<<(unsigned)sl.inst_blocks, 1024, 0, s>>>(sl.descs, sl.inst_map);
+    kb_weights_scale<<<(unsigned)sl.elem_blocks, 256, 0, s>>>(sl.descs, sl.elem_map);
+}
+
+void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s) {
+    int64_t n7, lv[3];
+    init_levels(g, kind, &n7, lv);
     k_init<<<blocks(g.n_x, 256), 256, 0, s>>>(g, kind, n7, lv[0], lv[1], lv[2],
                                               d.nu[buf]);
 }

@@ -56,14 +56,32 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) {   // exact for |v| <= 2
 
 // ---- filter slices (once per instance) ------------------------------------
 
-// Chunk c of filter `flt` (0: a_l = phi_l w_l, 1: phi_l): window
-// G[i] = h[128 c - 127 + i], i < 256, cut into slices, stored as 8 copies
-// shifted by r = 0..7 elements so that every 16-byte chunk of a Toeplitz tile
-// row is one aligned load.
-__global__ void __launch_bounds__(256) k_tc_filter(Geom g, FastView f) {
+// Block b < 2 tc_nch: chunk c = b mod tc_nch of filter flt = b / tc_nch
+// (0: a_l = phi_l w_l, 1: phi_l): window G[i] = h[128 c - 127 + i], i < 256,
+// cut into slices, stored as 8 copies shifted by r = 0..7 elements so that
+// every 16-byte chunk of a Toeplitz tile row is one aligned load.
+// Block 2 tc_nch: W2 = sum phi_l w_l^2 (strided partial sums, then a fixed
+// tree).  256 threads.
+__device__ __forceinline__ void tc_filter_body(const Geom& g, const FastView& f, int b) {
     __shared__ float sl[kSl][256];
     __shared__ double red[256];
-    const int c = blockIdx.x, flt = blockIdx.y, i = threadIdx.x;
+    const int i = threadIdx.x;
+    if (b == 2 * f.tc_nch) {
+        double s = 0.0;
+        for (int64_t l = threadIdx.x; l < g.n_w; l += blockDim.x) {
+            const double w = (double)(l - g.hw) * g.delta;
+            s += f.phi[l] * (w * w);
+        }
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *f.W2_dev = red[0];
+        return;
+    }
+    const int c = b % f.tc_nch, flt = b / f.tc_nch;
     const int64_t l = (int64_t)kTcK * c - 127 + i;
     double h = 0.0;
     if (l >= 0 && l < g.n_w) {
@@ -91,6 +109,17 @@ __global__ void __launch_bounds__(256) k_tc_filter(Geom g, FastView f) {
         for (int r = 0; r < 8; ++r)
             out[((size_t)t * 8 + r) * 256 + i] = bf16_bits(i + r < 256 ? sl[t][i + r] : 0.f);
     if (i == 0) f.tc_he[flt * f.tc_nch + c] = e;
+}
+
+__global__ void __launch_bounds__(256) k_tc_filter(Geom g, FastView f) {
+    tc_filter_body(g, f, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) kb_tc_filter(const SetupDev* descs,
+                                                   const BlockRef* map) {
+    const BlockRef r = map[blockIdx.x];
+    const SetupDev& d = descs[r.inst];
+    tc_filter_body(d.g, d.f, r.local);
 }
 
 // ---- E and the signal slices (every sweep) ------------------------------
@@ -505,7 +534,12 @@ cudaError_t tc_init_attributes() {
 }
 
 void launch_tc_setup(const Geom& g, const FastView& f, cudaStream_t s) {
-    k_tc_filter<<<dim3((unsigned)f.tc_nch, 2), 256, 0, s>>>(g, f);
+    k_tc_filter<<<(unsigned)(2 * f.tc_nch + 1), 256, 0, s>>>(g, f);
+}
+
+void launch_batch_setup_tc(const SetupLaunch& sl, cudaStream_t s) {
+    if (sl.filter_blocks)
+        kb_tc_filter<<<(unsigned)sl.filter_blocks, 256, 0, s>>>(sl.descs, sl.filter_map);
 }
 
 void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,

@@ -336,7 +336,7 @@ static ucp_status fast_refresh(ucp_inst* in, int slot) {
 }
 
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
-                     const Geom& g, cudaStream_t stream, bool first_step) {
+                     const Geom& g, cudaStream_t stream, bool own_setup) {
     in->ctx = ctx;
     in->params = p;
     in->params.init_table = nullptr;
@@ -377,6 +377,23 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     }
     in->bytes = A.bytes;
     cudaStream_t s = in->stream;
+    if (in->fast && !own_setup) {
+        // the set-up kernels and the first step come from batched launches
+        // (batchset_setup); only the host-side state and the table copy here
+        if (p.init_kind == 2) {
+            double fm = 0.0;
+            for (int64_t i = 0; i < g.n_x; ++i)
+                fm = fabs(p.init_table[i]) > fm ? fabs(p.init_table[i]) : fm;
+            in->fbound = fm;
+            fast_bounds(in, value_bound(g, fm));
+            cudaMemcpyAsync(d.table, p.init_table, 8 * nx, cudaMemcpyHostToDevice, s);
+            // the caller's host buffer must not be read after we return
+            if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "init copy");
+        }
+        in->cur = 0;
+        in->sweeps_done = 0;
+        return check(in, "set-up");
+    }
     UCP_LAUNCH(in, "weights", launch_weights(g, d, s));
     UCP_LAUNCH(in, "coarse", launch_coarse_list(g, d, s));
     if (in->fast) {
@@ -407,7 +424,6 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     cudaMemsetAsync(d.idx, 0xff, 4 * nx, s);
     in->cur = 0;
     in->sweeps_done = 0;
-    if (in->fast && !first_step) return check(in, "set-up");
     if (in->fast) {
         launch_mmse_fast(g, in->fv, d.nu[0], d.U, s, &in->prof);
         return fast_refresh(in, 0);

@@ -119,7 +119,8 @@ struct ucp_srv {
     std::thread th;
     Arena arena;
     BatchSet bs;    // the active requests (one batched sweep per step)
-    BatchSet adm;   // the requests admitted in a step (their set-up step)
+    BatchSet adm;   // the requests admitted in a step (their set-up)
+    SetupSet ss;
     Clock::time_point t0;
     uint64_t steps = 0, completed = 0;
     int max_active = 0;
@@ -203,7 +204,7 @@ void loop(ucp_srv* s) {
         if (!fresh.empty()) {
             // the admitted requests' first u1 update, tables and J, batched
             ucp_status st = batchset_build(s->adm, fresh, s->stream);
-            if (st == UCP_OK) st = batchset_first_step(s->adm, fresh, s->stream);
+            if (st == UCP_OK) st = batchset_setup(s->ss, s->adm, fresh, s->stream);
             if (st != UCP_OK) {
                 fail_all(s, st);
                 continue;
@@ -296,6 +297,7 @@ extern "C" UCP_API ucp_status ucp_srv_create(ucp_ctx* ctx, uint64_t hbm_budget_b
     s->arena.ctx = &s->own;
     s->bs.arena = &s->arena;
     s->adm.arena = &s->arena;
+    s->ss.arena = &s->arena;
     s->t0 = Clock::now();
     s->th = std::thread(loop, s);
     *out = s;

@@ -186,6 +186,44 @@ struct BatchLaunch {
     int64_t defer_blocks;
 };
 
+// Set-up of a fast instance done by batched launches (instances created
+// without their own set-up kernels): what those kernels read and write.
+struct SetupDev {
+    Geom g;
+    FastView f;
+    double* px;         // prior weights (exponentials, then normalised)
+    double* phi;        // quadrature weights, likewise
+    int64_t* coarse;    // coarse candidate list
+    double* scratch;    // the two normalising sums
+    int64_t* nu0;       // initial controller (lattice indices)
+    int32_t* idx;       // winner positions (set to -1)
+    const double* table;  // device copy of an init table (init_kind 2)
+    int32_t init_kind;
+    int64_t n7, lv[3];  // staircase step and levels (init_kind 1)
+};
+
+// Elementwise set-up blocks per instance (256 threads each): the largest of
+// n_x, n_w, the coarse list and the fast path's constant table.
+int64_t setup_elem_blocks(const Geom& g);
+// Staircase step (units of delta) and level lattice indices of init kind 1.
+void init_levels(const Geom& g, int kind, int64_t* n7, int64_t lv[3]);
+
+struct SetupLaunch {
+    const SetupDev* descs;
+    const BlockRef* elem_map;     // setup_elem_blocks per instance
+    int64_t elem_blocks;
+    const BlockRef* inst_map;     // one block per instance
+    int64_t inst_blocks;
+    const BlockRef* filter_map;   // 2 tc_nch + 1 per instance (filter slices, W2)
+    int64_t filter_blocks;
+};
+// kernels_plain.cu: exponentials, coarse list, init, counters; normalising
+// sums; normalisation.  kernels_fast.cu: the fast path's constants.
+// kernels_tc.cu: filter slices and W2.
+void launch_batch_setup_plain(const SetupLaunch& sl, cudaStream_t s);
+void launch_batch_setup_fast(const SetupLaunch& sl, cudaStream_t s);
+void launch_batch_setup_tc(const SetupLaunch& sl, cudaStream_t s);
+
 // Blocks of the deferred (near-tie) search per instance of a batch of 16 or
 // more (smaller batches get 64 / n), and the bytes of one deferred-search
 // record (kernels_fast.cu checks the size).

@@ -109,15 +109,16 @@ namespace ucp {
 
 // Device bytes one instance allocates (matches inst_init).
 size_t inst_bytes(const Geom& g, int precision);
-// Set up an instance on `stream`: buffers, grids, weights, init and, with
-// first_step, the first u1 update, tables and J (J history slot 0).  A fast
-// instance set up without it gets that step from a batched launch
-// (batch_first_step) before its first sweep.
+// Set up an instance on `stream`: buffers, then (own_setup) the grids,
+// weights, init, the first u1 update, tables and J (J history slot 0).  A
+// fast instance created without own_setup gets its buffers and host-side
+// state only; its set-up kernels and first step come from batched launches
+// (batchset_setup) before its first sweep.
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
-                     const Geom& g, cudaStream_t stream, bool first_step = true);
+                     const Geom& g, cudaStream_t stream, bool own_setup = true);
 // ucp_create with the choice above (validates the parameters).
 ucp_status inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t stream,
-                       bool first_step, ucp_inst** out);
+                       bool own_setup, ucp_inst** out);
 ucp_status inst_sweep(ucp_inst* in, int n);
 // Make room in the J history for `need` entries (synchronises on growth).
 ucp_status grow_history(ucp_inst* in, long long need);
