@@ -23,9 +23,9 @@
 // the Taylor form of the fast Gauss transform (Greengard and Strain, SIAM J.
 // Sci. Stat. Comput. 12, 1991).  With zeta = |z| h the tail after p terms is
 // at most e^{2 zeta} zeta^p / p! of the box's exact share; p is chosen per
-// (box, run) so that this is below 2^-64, and the expansion is used only
+// (box, run) so that this is below 2^-52, and the expansion is used only
 // where zeta <= kZetaMax and it is cheaper than the direct sum over the
-// box's sources, which is taken otherwise.  Terms whose bound is below 2^-40
+// box's sources, which is taken otherwise.  Terms whose bound is below 2^-28
 // are summed in FP32, the rest in double-float.
 //
 // Negligible work is skipped: a (box, run) or (source, run) pair is left out
@@ -307,20 +307,28 @@ __device__ __forceinline__ void run_shift_body(const Geom& g, const FastView& f,
 
 // ---- the u1 sums ------------------------------------------------------------
 
-// Taylor terms for zeta = |z| h: p = terms kept (tail bound <= 2^-64 of the
+// Taylor terms for zeta = |z| h: p = terms kept (tail bound <= 2^-52 of the
 // box's share; -1 if more than kBoxTerms would be needed), n1 = first term
-// summed in FP32 (its tail bound <= 2^-40).
+// summed in FP32 (its tail bound <= 2^-28, so the FP32 rounding of the tail
+// is ~2^-52 of the share, below the double-float Horner steps' own).
+// 1 / (n + 1) from a table (the factor 1.001 on zeta covers its rounding).
+__constant__ float kInvN[kBoxTerms + 1] = {
+    1.0f / 1, 1.0f / 2, 1.0f / 3, 1.0f / 4, 1.0f / 5, 1.0f / 6, 1.0f / 7, 1.0f / 8, 1.0f / 9,
+    1.0f / 10, 1.0f / 11, 1.0f / 12, 1.0f / 13, 1.0f / 14, 1.0f / 15, 1.0f / 16, 1.0f / 17,
+    1.0f / 18, 1.0f / 19, 1.0f / 20, 1.0f / 21, 1.0f / 22, 1.0f / 23, 1.0f / 24, 1.0f / 25};
+static_assert(kBoxTerms == 24, "reciprocal table length");
 __device__ __forceinline__ void taylor_terms(float zeta, int& n1, int& p) {
     float term = expf(2.0f * zeta) * 1.001f;   // e^{2 zeta} zeta^n / n!, n = 0
+    const float zs = zeta * 1.001f;
     n1 = -1;
     p = -1;
     for (int n = 0; n <= kBoxTerms; ++n) {
-        if (n1 < 0 && term <= 0x1p-40f) n1 = n;
-        if (term <= 0x1p-64f) {
+        if (n1 < 0 && term <= 0x1p-28f) n1 = n;
+        if (term <= 0x1p-52f) {
             p = n;
             break;
         }
-        term *= zeta * 1.001f / (float)(n + 1);
+        term *= zs * kInvN[n];
     }
     if (n1 < 0) n1 = p;
 }
