@@ -1084,7 +1084,6 @@ int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
         case kBSearch: return (g.n_x * kFastG + kSearchT - 1) / kSearchT;
         case kBTile:
-        case kBBox:
         case kBRun: return u1_batch_blocks(g, fp, kind);
         case kBPerY: return (g.n_y + 255) / 256;
         case kBTabPart: return tc_table_blocks(fp);

@@ -48,20 +48,143 @@ constexpr float kHMax = 0.05f;      // box half width aimed at when grouping
 constexpr float kHMoments = 0.25f;  // boxes wider than this get no moments
 constexpr float kZetaMax = 1.0f;    // largest |y - c| h expanded
 constexpr int kU1Runs = 32;         // runs per block of the u1 kernel (1 warp)
-constexpr int kMomT = 256;          // threads per box of the moment kernel
-constexpr int kPlanT = 128;         // threads per tile of the planning kernel
+constexpr int kBuildT = 256;        // threads per tile of the box kernel (one warp per box)
 constexpr int kBoxDF = 16;          // moments up to this order in double-float
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---- sources and boxes ----------------------------------------------------------
 
-// One block per tile.  Every thread: per source f_i and exp(delta f_i)
-// (double-float).  Then warp 0: greedy grouping of consecutive sources into
-// boxes whose f values (leading floats) span at most 2 kHMax; the last box of
-// a tile takes whatever is left once kBoxMax - 1 boxes are closed.
-__device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
-                                              const int64_t* __restrict__ nu,
-                                              int64_t t) {
+// One block per tile (kBuildT threads).
+//  1. Every thread: per source f_i and exp(delta f_i) (double-float).
+//  2. Warp 0: greedy grouping of consecutive sources into boxes whose f
+//     values (leading floats) span at most 2 kHMax; the last box of a tile
+//     takes whatever is left once kBoxMax - 1 boxes are closed.
+//  3. One warp per box: centre c, half width h, scale pm, smallest prior.
+//  4. The 32-source chunks of the boxes narrow enough to be expanded, spread
+//     over the warps: every lane forms its source's terms q_i (d_i / s)^n,
+//     n <= kBoxTerms, in shared memory, and lane n adds term n over the
+//     chunk's sources in index order (the chunk's partial moment n).
+//  5. One warp per expanded box: lane n adds the box's chunk partials in
+//     chunk order (a fixed order), then the Taylor coefficients and exp(delta c).
+struct BoxTerms {
+    dfloat d[kBoxDF + 1];             // orders 0..kBoxDF in double-float
+    float f[kBoxTerms - kBoxDF];      // the higher ones in FP32
+};
+struct BuildSmem {
+    int32_t s0[kBoxMax], n[kBoxMax];
+    float fmin[kBoxMax], fmax[kBoxMax];
+    float c[kBoxMax], pm[kBoxMax], sc[kBoxMax];
+    int32_t ch0[kBoxMax + 1];          // first chunk of each box (expanded boxes)
+    int32_t nch[kBoxMax];              // chunks of each box (0: not expanded)
+    int nb;
+    BoxTerms terms[kBuildT / 32][32];   // per warp, per lane (source)
+};
+
+__device__ __forceinline__ void box_range(const FastView& f, BuildSmem& sm, int64_t slot,
+                                          int k, int lane) {
+    const int64_t s0 = sm.s0[k];
+    const int n = sm.n[k];
+    const float c = 0.5f * (sm.fmin[k] + sm.fmax[k]);
+    float hv = 0.0f, pv = FLT_MAX, pmn = FLT_MAX;
+    for (int s = lane; s < n; s += 32) {
+        const dfloat d = df_add_f(f.src_f[s0 + s], -c);
+        const float pr = f.prior[s0 + s].hi;
+        hv = fmaxf(hv, fabsf(d.hi) + fabsf(d.lo));
+        pv = fminf(pv, fmaf(0.5f * d.hi, d.hi, pr));
+        pmn = fminf(pmn, pr);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hv = fmaxf(hv, __shfl_xor_sync(kFull, hv, o));
+        pv = fminf(pv, __shfl_xor_sync(kFull, pv, o));
+        pmn = fminf(pmn, __shfl_xor_sync(kFull, pmn, o));
+    }
+    const float h = hv * (1.0f + 0x1p-20f);
+    const bool expand = h <= kHMoments;
+    int e2 = 0;
+    frexpf(h, &e2);                        // h < 2^e2
+    const float sc = h > 0.0f ? ldexpf(1.0f, e2) : 1.0f;
+    if (lane == 0) {
+        f.box_geo[slot] = make_float4(c, h, pv, pmn);
+        f.box_rng[slot] = make_float4(sm.fmin[k], sm.fmax[k], expand ? h : INFINITY, sc);
+        sm.c[k] = c;
+        sm.pm[k] = pv;
+        sm.sc[k] = sc;
+        sm.nch[k] = expand ? (n + 31) / 32 : 0;
+    }
+}
+
+// Partial moments of sources b .. b + 31 of box k into part[0 .. kBoxTerms].
+__device__ __forceinline__ void chunk_moments(const FastView& f, BuildSmem& sm, int k, int b,
+                                              int warp, int lane, dfloat* part) {
+    const int64_t s0 = sm.s0[k];
+    const int cn = min(32, sm.n[k] - b);
+    const float c = sm.c[k], pm = sm.pm[k];
+    const float inv_sc = 1.0f / sm.sc[k];   // exact: a power of two
+    BoxTerms* tw = sm.terms[warp];
+    if (lane < cn) {
+        const int64_t i = s0 + b + lane;
+        const dfloat d = df_add_f(f.src_f[i], -c);
+        dfloat ex = df_add_f(df_neg(f.prior[i]), pm);
+        ex = df_add(ex, df_mul_f(df_mul(d, d), -0.5f));
+        if (ex.hi < -87.0f) ex = {-87.0f, 0.0f};
+        dfloat q = df_exp(ex, f.t64);
+        const dfloat ds = {d.hi * inv_sc, d.lo * inv_sc};   // d / s, |d / s| <= 1
+        BoxTerms& t = tw[lane];
+#pragma unroll
+        for (int m = 0; m <= kBoxDF; ++m) {
+            t.d[m] = q;
+            q = df_mul(q, ds);
+        }
+        float qf = q.hi;
+#pragma unroll
+        for (int m = 0; m < kBoxTerms - kBoxDF; ++m) {
+            t.f[m] = qf;
+            qf *= ds.hi;
+        }
+    }
+    __syncwarp();
+    if (lane <= kBoxDF) {
+        dfloat M = {0.0f, 0.0f};
+        for (int q = 0; q < cn; ++q) M = df_add(M, tw[q].d[lane]);
+        part[lane] = M;
+    } else if (lane <= kBoxTerms) {
+        float a = 0.0f;
+        for (int q = 0; q < cn; ++q) a += tw[q].f[lane - kBoxDF - 1];
+        part[lane] = {a, 0.0f};
+    }
+    __syncwarp();
+}
+
+// Box k's moments from its chunk partials (in chunk order), Taylor
+// coefficients and exp(delta c).
+__device__ __forceinline__ void box_coefs(const Geom& g, const FastView& f, BuildSmem& sm,
+                                          int64_t slot, int k, int lane,
+                                          const dfloat* part) {
+    const int q0 = sm.ch0[k], q1 = sm.ch0[k + 1];
+    const float c = sm.c[k], sc = sm.sc[k];
+    dfloat M = {0.0f, 0.0f};   // lane n <= kBoxTerms: moment n
+    if (lane <= kBoxDF) {
+        for (int q = q0; q < q1; ++q) M = df_add(M, part[(size_t)q * (kBoxTerms + 1) + lane]);
+    } else if (lane <= kBoxTerms) {
+        float a = 0.0f;
+        for (int q = q0; q < q1; ++q) a += part[(size_t)q * (kBoxTerms + 1) + lane].hi;
+        M = {a, 0.0f};
+    }
+    const dfloat M1 = {__shfl_down_sync(kFull, M.hi, 1), __shfl_down_sync(kFull, M.lo, 1)};
+    if (lane < kBoxTerms) {
+        const dfloat inv = f.t64[47 + lane];   // 1 / lane!
+        dfloat* co = f.box_coef + slot * (2 * kBoxTerms);
+        co[lane] = df_mul(M, inv);
+        co[kBoxTerms + lane] = df_mul(df_add(df_mul_f(M, c), df_mul_f(M1, sc)), inv);
+    }
+    // exp(delta c), used only by expanded boxes, on a lane without a moment
+    if (lane == 31) f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
+}
+
+__device__ __forceinline__ void box_build_body(const Geom& g, const FastView& f,
+                                               const int64_t* __restrict__ nu,
+                                               BuildSmem& sm, int64_t t) {
     const int64_t t0 = t * f.tile;
     const int64_t t1 = min(t0 + f.tile, g.n_x);
     const dfloat dl = {f.delta_hi, f.delta_lo};
@@ -75,190 +198,92 @@ __device__ __forceinline__ void box_plan_body(const Geom& g, const FastView& f,
         f.src_F[i] = df_exp(df_mul(fv, dl), f.t64);
     }
     __syncthreads();
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t slot0 = t * kBoxMax;
-    const float wmax = 2.0f * kHMax;
-    int nb = 0;
-    int64_t sb = t0;
-    float bmin = FLT_MAX, bmax = -FLT_MAX;
-    for (int64_t base = t0; base < t1; base += 32) {
-        const int64_t i = base + lane;
-        const bool valid = i < t1;
-        const float fi = valid ? f.src_f[i].hi : 0.0f;
-        int from = 0;
-        for (;;) {
-            const bool part = valid && lane >= from;
-            float vmin = part ? fi : FLT_MAX, vmax = part ? fi : -FLT_MAX;
+    if (warp == 0) {
+        const float wmax = 2.0f * kHMax;
+        int nb = 0;
+        int64_t sb = t0;
+        float bmin = FLT_MAX, bmax = -FLT_MAX;
+        for (int64_t base = t0; base < t1; base += 32) {
+            const int64_t i = base + lane;
+            const bool valid = i < t1;
+            const float fi = valid ? f.src_f[i].hi : 0.0f;
+            int from = 0;
+            for (;;) {
+                const bool part = valid && lane >= from;
+                float vmin = part ? fi : FLT_MAX, vmax = part ? fi : -FLT_MAX;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float a = __shfl_up_sync(kFull, vmin, d);
-                const float b = __shfl_up_sync(kFull, vmax, d);
-                if (lane >= d) {
-                    vmin = fminf(vmin, a);
-                    vmax = fmaxf(vmax, b);
+                for (int d = 1; d < 32; d <<= 1) {
+                    const float a = __shfl_up_sync(kFull, vmin, d);
+                    const float b = __shfl_up_sync(kFull, vmax, d);
+                    if (lane >= d) {
+                        vmin = fminf(vmin, a);
+                        vmax = fmaxf(vmax, b);
+                    }
                 }
+                const float rmin = fminf(bmin, vmin), rmax = fmaxf(bmax, vmax);
+                const bool bad = part && nb < kBoxMax - 1 && rmax - rmin > wmax;
+                const unsigned m = __ballot_sync(kFull, bad);
+                if (m == 0) {
+                    bmin = __shfl_sync(kFull, rmin, 31);
+                    bmax = __shfl_sync(kFull, rmax, 31);
+                    break;
+                }
+                const int l = __ffs(m) - 1;   // first source that does not fit
+                const float cmin = __shfl_sync(kFull, rmin, l > 0 ? l - 1 : 0);
+                const float cmax = __shfl_sync(kFull, rmax, l > 0 ? l - 1 : 0);
+                if (lane == 0) {
+                    sm.s0[nb] = (int32_t)sb;
+                    sm.n[nb] = (int32_t)(base + l - sb);
+                    sm.fmin[nb] = l > from ? cmin : bmin;
+                    sm.fmax[nb] = l > from ? cmax : bmax;
+                }
+                ++nb;
+                sb = base + l;
+                bmin = FLT_MAX;
+                bmax = -FLT_MAX;
+                from = l;
             }
-            const float rmin = fminf(bmin, vmin), rmax = fmaxf(bmax, vmax);
-            const bool bad = part && nb < kBoxMax - 1 && rmax - rmin > wmax;
-            const unsigned m = __ballot_sync(kFull, bad);
-            if (m == 0) {
-                bmin = __shfl_sync(kFull, rmin, 31);
-                bmax = __shfl_sync(kFull, rmax, 31);
-                break;
-            }
-            const int l = __ffs(m) - 1;   // first source that does not fit
-            const float cmin = __shfl_sync(kFull, rmin, l > 0 ? l - 1 : 0);
-            const float cmax = __shfl_sync(kFull, rmax, l > 0 ? l - 1 : 0);
-            if (lane == 0) {
-                f.box_s0[slot0 + nb] = (int32_t)sb;
-                f.box_n[slot0 + nb] = (int32_t)(base + l - sb);
-                f.box_rng[slot0 + nb] = make_float4(l > from ? cmin : bmin,
-                                                    l > from ? cmax : bmax, 0.f, 0.f);
-            }
-            ++nb;
-            sb = base + l;
-            bmin = FLT_MAX;
-            bmax = -FLT_MAX;
-            from = l;
         }
-    }
-    if (lane == 0) {
-        f.box_s0[slot0 + nb] = (int32_t)sb;
-        f.box_n[slot0 + nb] = (int32_t)(t1 - sb);
-        f.box_rng[slot0 + nb] = make_float4(bmin, bmax, 0.f, 0.f);
-        f.box_cnt[t] = nb + 1;
-    }
-}
-
-// One block per box slot: centre c, half width h, scale pm, smallest prior,
-// exp(delta c) and, for boxes narrow enough to be expanded, the Taylor
-// coefficients.  Partial moments are summed over the block in a fixed tree.
-struct MomSmem {
-    dfloat wd[kMomT / 32][kBoxDF + 1];           // per-warp moment sums
-    float wf[kMomT / 32][kBoxTerms - kBoxDF];
-    float fr[3][kMomT / 32];
-};
-
-// Moment of order m summed over the warps in order.
-__device__ __forceinline__ dfloat moment_sum(const MomSmem& sm, int m) {
-    if (m <= kBoxDF) {
-        dfloat a = sm.wd[0][m];
-#pragma unroll
-        for (int w = 1; w < kMomT / 32; ++w) a = df_add(a, sm.wd[w][m]);
-        return a;
-    }
-    float a = sm.wf[0][m - kBoxDF - 1];
-#pragma unroll
-    for (int w = 1; w < kMomT / 32; ++w) a += sm.wf[w][m - kBoxDF - 1];
-    return {a, 0.0f};
-}
-
-__device__ __forceinline__ void box_moments_body(const Geom& g, const FastView& f,
-                                                 MomSmem& sm, int64_t slot) {
-    const int64_t t = slot / kBoxMax;
-    if (slot - t * kBoxMax >= f.box_cnt[t]) return;   // the same for the block
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t s0 = f.box_s0[slot];
-    const int n = f.box_n[slot];
-    const float4 rg = f.box_rng[slot];
-    const float c = 0.5f * (rg.x + rg.y);
-    float hv = 0.0f, pv = FLT_MAX, pmn = FLT_MAX;
-    for (int s = tid; s < n; s += kMomT) {
-        const dfloat d = df_add_f(f.src_f[s0 + s], -c);
-        const float pr = f.prior[s0 + s].hi;
-        hv = fmaxf(hv, fabsf(d.hi) + fabsf(d.lo));
-        pv = fminf(pv, fmaf(0.5f * d.hi, d.hi, pr));
-        pmn = fminf(pmn, pr);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        hv = fmaxf(hv, __shfl_xor_sync(kFull, hv, o));
-        pv = fminf(pv, __shfl_xor_sync(kFull, pv, o));
-        pmn = fminf(pmn, __shfl_xor_sync(kFull, pmn, o));
-    }
-    if (lane == 0) {
-        sm.fr[0][warp] = hv;
-        sm.fr[1][warp] = pv;
-        sm.fr[2][warp] = pmn;
+        if (lane == 0) {
+            sm.s0[nb] = (int32_t)sb;
+            sm.n[nb] = (int32_t)(t1 - sb);
+            sm.fmin[nb] = bmin;
+            sm.fmax[nb] = bmax;
+            sm.nb = nb + 1;
+            f.box_cnt[t] = nb + 1;
+        }
     }
     __syncthreads();
-    hv = sm.fr[0][0];
-    pv = sm.fr[1][0];
-    pmn = sm.fr[2][0];
-#pragma unroll
-    for (int w = 1; w < kMomT / 32; ++w) {
-        hv = fmaxf(hv, sm.fr[0][w]);
-        pv = fminf(pv, sm.fr[1][w]);
-        pmn = fminf(pmn, sm.fr[2][w]);
+    const int nb = sm.nb;
+    if (threadIdx.x < nb) {
+        f.box_s0[slot0 + threadIdx.x] = sm.s0[threadIdx.x];
+        f.box_n[slot0 + threadIdx.x] = sm.n[threadIdx.x];
     }
-    const float h = hv * (1.0f + 0x1p-20f);
-    const float pm = pv;
-    const bool expand = h <= kHMoments;
-    int e2 = 0;
-    frexpf(h, &e2);                        // h < 2^e2
-    const float sc = h > 0.0f ? ldexpf(1.0f, e2) : 1.0f;
-    const float inv_sc = 1.0f / sc;        // exact: a power of two
-    if (tid == 0) {
-        f.box_geo[slot] = make_float4(c, h, pm, pmn);
-        f.box_rng[slot] = make_float4(rg.x, rg.y, expand ? h : INFINITY, sc);
-    }
-    if (!expand) return;   // the same for the block
-    // moments: orders 0..kBoxDF in double-float; the higher ones only enter
-    // the expansions' FP32 tails
-    dfloat M[kBoxDF + 1];
-    float Mf[kBoxTerms - kBoxDF];
-#pragma unroll
-    for (int m = 0; m <= kBoxDF; ++m) M[m] = {0.0f, 0.0f};
-#pragma unroll
-    for (int m = 0; m < kBoxTerms - kBoxDF; ++m) Mf[m] = 0.0f;
-    for (int s = tid; s < n; s += kMomT) {
-        const dfloat d = df_add_f(f.src_f[s0 + s], -c);
-        dfloat ex = df_add_f(df_neg(f.prior[s0 + s]), pm);
-        ex = df_add(ex, df_mul_f(df_mul(d, d), -0.5f));
-        if (ex.hi < -87.0f) ex = {-87.0f, 0.0f};
-        dfloat q = df_exp(ex, f.t64);
-        const dfloat ds = {d.hi * inv_sc, d.lo * inv_sc};   // d / s, |d / s| <= 1
-#pragma unroll
-        for (int m = 0; m <= kBoxDF; ++m) {
-            M[m] = df_add(M[m], q);
-            q = df_mul(q, ds);
+    constexpr int kWarps = kBuildT / 32;
+    for (int k = warp; k < nb; k += kWarps) box_range(f, sm, slot0 + k, k, lane);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int k = 0; k < nb; ++k) {
+            sm.ch0[k] = a;
+            a += sm.nch[k];
         }
-        float qf = q.hi;
-#pragma unroll
-        for (int m = 0; m < kBoxTerms - kBoxDF; ++m) {
-            Mf[m] += qf;
-            qf *= ds.hi;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int m = 0; m <= kBoxDF; ++m) {
-            const dfloat other = {__shfl_down_sync(kFull, M[m].hi, o),
-                                  __shfl_down_sync(kFull, M[m].lo, o)};
-            M[m] = df_add(M[m], other);
-        }
-#pragma unroll
-        for (int m = 0; m < kBoxTerms - kBoxDF; ++m)
-            Mf[m] += __shfl_down_sync(kFull, Mf[m], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int m = 0; m <= kBoxDF; ++m) sm.wd[warp][m] = M[m];
-#pragma unroll
-        for (int m = 0; m < kBoxTerms - kBoxDF; ++m) sm.wf[warp][m] = Mf[m];
+        sm.ch0[nb] = a;   // <= tile / 32 + nb <= box_cap
     }
     __syncthreads();
-    // exp(delta c), used only by expanded boxes, on an otherwise idle thread
-    if (tid == kBoxTerms) f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
-    if (tid < kBoxTerms) {
-        const dfloat inv = f.t64[47 + tid];   // 1 / tid!
-        const dfloat Mn = moment_sum(sm, tid), Mn1 = moment_sum(sm, tid + 1);
-        dfloat* co = f.box_coef + slot * (2 * kBoxTerms);
-        co[tid] = df_mul(Mn, inv);
-        co[kBoxTerms + tid] = df_mul(df_add(df_mul_f(Mn, c), df_mul_f(Mn1, sc)), inv);
+    const int total = sm.ch0[nb];
+    dfloat* part = f.box_part + (size_t)t * (size_t)f.box_cap * (kBoxTerms + 1);
+    for (int q = warp; q < total; q += kWarps) {
+        int k = 0;
+        while (sm.ch0[k + 1] <= q) ++k;   // the box of chunk q (the same for the warp)
+        chunk_moments(f, sm, k, (q - sm.ch0[k]) * 32, warp, lane,
+                      part + (size_t)q * (kBoxTerms + 1));
     }
+    __syncthreads();
+    for (int k = warp; k < nb; k += kWarps)
+        if (sm.nch[k]) box_coefs(g, f, sm, slot0 + k, k, lane, part);
 }
 
 // ---- per-run scale and cut --------------------------------------------------
@@ -582,14 +607,10 @@ __device__ __forceinline__ void u1_combine_body(const Geom& g, const FastView& f
 
 // ---- single-instance kernels --------------------------------------------------
 
-__global__ void __launch_bounds__(kPlanT) k_box_plan(Geom g, FastView f,
-                                                    const int64_t* __restrict__ nu) {
-    box_plan_body(g, f, nu, blockIdx.x);
-}
-
-__global__ void __launch_bounds__(kMomT) k_box_moments(Geom g, FastView f) {
-    __shared__ MomSmem sm;
-    box_moments_body(g, f, sm, blockIdx.x);
+__global__ void __launch_bounds__(kBuildT) k_box_build(Geom g, FastView f,
+                                                      const int64_t* __restrict__ nu) {
+    __shared__ BuildSmem sm;
+    box_build_body(g, f, nu, sm, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kRunT) k_run_shift(Geom g, FastView f) {
@@ -621,19 +642,12 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
     return r;
 }
 
-__global__ void __launch_bounds__(kPlanT) kb_box_plan(const InstDev* insts,
-                                                     const BlockRef* map) {
+__global__ void __launch_bounds__(kBuildT) kb_box_build(const InstDev* insts,
+                                                       const BlockRef* map) {
     __shared__ InstDev sd;
+    __shared__ BuildSmem sm;
     const BlockRef r = stage(insts, map, sd);
-    box_plan_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], r.local);
-}
-
-__global__ void __launch_bounds__(kMomT) kb_box_moments(const InstDev* insts,
-                                                        const BlockRef* map) {
-    __shared__ InstDev sd;
-    __shared__ MomSmem sm;
-    const BlockRef r = stage(insts, map, sd);
-    box_moments_body(sd.g, sd.f, sm, r.local);
+    box_build_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], sm, r.local);
 }
 
 __global__ void __launch_bounds__(kRunT) kb_run_shift(const InstDev* insts,
@@ -700,6 +714,7 @@ void u1_plan(const Geom& g, int max_tiles, FastPlan* fp) {
     if (tile < g.u1_tile_min) tile = g.u1_tile_min;
     fp->tile = tile;
     fp->n_tiles = (int)((g.n_x + tile - 1) / tile);
+    fp->box_cap = (tile + 31) / 32 + kBoxMax;
 }
 
 size_t u1_scratch_bytes(const Geom& g, const FastPlan& fp, size_t align) {
@@ -709,6 +724,7 @@ size_t u1_scratch_bytes(const Geom& g, const FastPlan& fp, size_t align) {
            rnd(4 * (size_t)fp.n_tiles) + 2 * rnd(4 * slots) +   // box_cnt, box_s0, box_n
            2 * rnd(16 * slots) + rnd(8 * slots) +                // box_geo, box_rng, box_C
            rnd(8 * slots * 2 * kBoxTerms) +                      // box_coef
+           rnd(8 * (size_t)fp.n_tiles * (size_t)fp.box_cap * (kBoxTerms + 1)) +  // box_part
            2 * rnd(4 * (size_t)fp.n_runs) +                      // run_lo, run_hi
            2 * rnd(8 * (size_t)fp.n_tiles * (size_t)g.n_y);     // partN, partD
 }
@@ -725,12 +741,14 @@ bool u1_carve(const Geom& g, FastView* f, void* (*get)(void*, size_t), void* ctx
     f->box_rng = (float4*)get(ctx, 16 * slots);
     f->box_C = (dfloat*)get(ctx, 8 * slots);
     f->box_coef = (dfloat*)get(ctx, 8 * slots * 2 * kBoxTerms);
+    f->box_part = (dfloat*)get(ctx, 8 * (size_t)f->n_tiles * (size_t)f->box_cap *
+                                        (kBoxTerms + 1));
     f->run_lo = (float*)get(ctx, 4 * (size_t)f->n_runs);
     f->run_hi = (float*)get(ctx, 4 * (size_t)f->n_runs);
     f->partN = (double*)get(ctx, 8 * (size_t)f->n_tiles * (size_t)g.n_y);
     f->partD = (double*)get(ctx, 8 * (size_t)f->n_tiles * (size_t)g.n_y);
     return f->src_nu && f->src_f && f->src_F && f->box_cnt && f->box_s0 && f->box_n &&
-           f->box_geo && f->box_rng && f->box_C && f->box_coef && f->run_lo &&
+           f->box_geo && f->box_rng && f->box_C && f->box_coef && f->box_part && f->run_lo &&
            f->run_hi && f->partN && f->partD;
 }
 
@@ -738,8 +756,7 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
                       double* U, cudaStream_t s, Prof* prof) {
     cudaEvent_t ev;
     int k = prof ? prof->begin("u1_boxes", &ev) : -1;
-    k_box_plan<<<(unsigned)f.n_tiles, kPlanT, 0, s>>>(g, f, nu);
-    k_box_moments<<<(unsigned)(f.n_tiles * kBoxMax), kMomT, 0, s>>>(g, f);
+    k_box_build<<<(unsigned)f.n_tiles, kBuildT, 0, s>>>(g, f, nu);
     if (prof) prof->end(k, ev);
     k = prof ? prof->begin("u1_shift", &ev) : -1;
     k_run_shift<<<blocks(f.n_runs, kRunT / 32), kRunT, 0, s>>>(g, f);
@@ -762,7 +779,6 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
 int64_t u1_batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
         case kBTile: return fp.n_tiles;
-        case kBBox: return (int64_t)fp.n_tiles * kBoxMax;
         case kBRun: return (fp.n_runs + kRunT / 32 - 1) / (kRunT / 32);
     }
     (void)g;
@@ -777,8 +793,7 @@ void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
     const InstDev* d = bl.insts;
     {
         ProfScope ps(prof, "u1_boxes");
-        kb_box_plan<<<(unsigned)bl.n_blocks[kBTile], kPlanT, 0, s>>>(d, bl.map[kBTile]);
-        kb_box_moments<<<(unsigned)bl.n_blocks[kBBox], kMomT, 0, s>>>(d, bl.map[kBBox]);
+        kb_box_build<<<(unsigned)bl.n_blocks[kBTile], kBuildT, 0, s>>>(d, bl.map[kBTile]);
     }
     {
         ProfScope ps(prof, "u1_shift");

@@ -39,14 +39,17 @@ constexpr size_t rnd256(size_t n) { return (n + 255) / 256 * 256; }
 // nu and prior (x-sized), the constant table, then the u1 buffers at the
 // largest sizes: src_nu, src_f, src_F; per tile the box count, per box slot
 // its first source, size, geometry, range, exp(delta c) and 2 kBoxTerms
-// coefficients; per run (at most n_y runs) two bounds; per tile and target
-// the numerator and denominator partials.
+// coefficients; per tile the partial moments of its 32-source chunks (at
+// most tile / 32 + kBoxMax, tiles of at most kMaxX / kMaxTiles sources);
+// per run (at most n_y runs) two bounds; per tile and target the numerator
+// and denominator partials.
 constexpr size_t kSlots = (size_t)kMaxTiles * kBoxMax;
+constexpr size_t kChunks = (size_t)kMaxTiles * (kMaxX / kMaxTiles / 32 + kBoxMax);
 constexpr size_t kScratchBytes =
     5 * rnd256(8 * kMaxX) + rnd256(8 * kConstTab) + rnd256(4 * kMaxTiles) +
     2 * rnd256(4 * kSlots) + 2 * rnd256(16 * kSlots) + rnd256(8 * kSlots) +
-    rnd256(8 * kSlots * 2 * kBoxTerms) + 2 * rnd256(4 * kMaxY) +
-    2 * rnd256(8 * (size_t)kMaxTiles * kMaxY);
+    rnd256(8 * kSlots * 2 * kBoxTerms) + rnd256(8 * kChunks * (kBoxTerms + 1)) +
+    2 * rnd256(4 * kMaxY) + 2 * rnd256(8 * (size_t)kMaxTiles * kMaxY);
 
 static __device__ __align__(256) double g_scratch[kScratchBytes / 8];
 

@@ -60,6 +60,7 @@ struct FastPlan {
     int64_t n_e;       // length of E, E^2, E E_+ (n_pos + n_w + 1)
     int64_t tile;      // sources per tile of the u1 step (consecutive x0)
     int n_tiles;       // tiles; the u1 partial sums are kept per tile
+    int64_t box_cap;   // 32-source chunk partials per tile (tile / 32 + kBoxMax)
     int run;           // targets per run of the u1 step
     int64_t n_runs;    // runs covering the y grid
     int64_t r_blocks;  // run blocks of the u1 kernel (kU1Runs runs each)
@@ -111,6 +112,7 @@ struct FastView : FastPlan {
     float4* box_rng;     //   (min f, max f, h if moments exist else inf, s)
     dfloat* box_C;       //   exp(delta c)
     dfloat* box_coef;    //   [2 kBoxTerms]: M_n / n!, then (c M_n + s M_{n+1}) / n!
+    dfloat* box_part;    // [n_tiles * box_cap * (kBoxTerms + 1)] chunk partial moments
     float* run_lo;       // [n_runs] lower bound of min_i e_{i,j0} (scale)
     float* run_hi;       // [n_runs] upper bound of min_i e_ij over the run
     double* partN;       // [n_tiles * n_y] numerator partials
@@ -168,7 +170,7 @@ struct BlockRef {
 };
 
 enum BatchKind {
-    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBBuildE, kBJPart, kBBox, kBRun, kBTabComb,
+    kBSearch = 0, kBTile, kBPerY, kBTabPart, kBBuildE, kBJPart, kBRun, kBTabComb,
     kBKinds
 };
 
