@@ -96,10 +96,10 @@ FLOPS_SEARCH_CAND = 104.0
 
 # kernels launched per timed group of the library's profiler (the groups not
 # listed launch one kernel), and the instance set-up launches of one solve
-# (weights 3, coarse list, fast set-up, filter slices, init, the first u1
-# step 5, tables 3, J), which run before the profiler is switched on
-KERNELS_PER_GROUP = {"u1_boxes": 2, "search": 2}
-SETUP_LAUNCHES = 16
+# (weights 3, coarse list, fast set-up, filter slices and W2, init, the first
+# u1 step 4, tables 3, J), which run before the profiler is switched on
+KERNELS_PER_GROUP = {"search": 2}
+SETUP_LAUNCHES = 15
 
 
 def kernel_work(p, sizes, counters, launches):

@@ -155,11 +155,12 @@ def _ptr(a, typ):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(typ))
 
 
-def plan(params) -> dict:
-    """Validate parameters on the host (no GPU needed): sizes and bytes."""
+def plan(params, table=None) -> dict:
+    """Validate parameters on the host (no GPU needed): sizes and bytes.
+    table: the initial controller table of an init_kind 2 start."""
     L = load()
     v = [ctypes.c_uint64() for _ in range(5)]
-    _check(L.ucp_plan(ctypes.byref(Params.from_dict(params)),
+    _check(L.ucp_plan(ctypes.byref(Params.from_dict(params, table)),
                       *(ctypes.byref(x) for x in v)), "ucp_plan")
     return dict(zip(("n_x", "n_w", "n_y", "n_cand", "device_bytes"),
                     (x.value for x in v)))
@@ -359,7 +360,9 @@ class _Member(Instance):
 class Batch:
     """Many instances swept together (``ucp_batch_*``)."""
 
-    def __init__(self, params_list, stream=None, ctx: Context | None = None):
+    def __init__(self, params_list, stream=None, ctx: Context | None = None, tables=None):
+        """tables: None, or one entry per member: None or the member's initial
+        controller table (members with init_kind 2)."""
         import torch
         L = load()
         self.ctx = ctx or default_context()
@@ -368,7 +371,10 @@ class Batch:
             stream = torch.cuda.current_stream(self.ctx.device)
         self.stream = stream
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-        arr = (Params * len(self.params))(*[Params.from_dict(p) for p in self.params])
+        tables = tables or [None] * len(self.params)
+        # the Params objects own the table arrays until the call returns
+        objs = [Params.from_dict(p, t) for p, t in zip(self.params, tables)]
+        arr = (Params * len(self.params))(*objs)
         h = _vp()
         _check(L.ucp_batch_create(self.ctx.h, arr, len(self.params), _vp(sp),
                                   ctypes.byref(h)), "ucp_batch_create")
@@ -444,7 +450,7 @@ class Server:
         n = int(params.get("sweeps", 0) if sweeps is None else sweeps)
         _check(load().ucp_submit(self.h, ctypes.byref(p), n, ctypes.byref(t)),
                "ucp_submit")
-        pl = plan(params)
+        pl = plan(params, table)
         self._sizes[t.value] = (pl["n_x"], pl["n_y"])
         return t.value
 

@@ -52,6 +52,23 @@ def test_plan_sizes_match_the_configs(lib):
     assert 0 < s["device_bytes"] < 512 << 20
 
 
+def test_plan_of_a_table_start(lib):
+    """A start from a host table (init_kind 2) is planned with its table; the
+    sizes are those of the same grids, and a table of the wrong length or no
+    table is rejected."""
+    import numpy as np
+    from paper_1908_04489_gb300 import binding, workloads
+    p = workloads.c1()
+    n = binding.plan(p)["n_x"]
+    q = dict(p, init_kind=2)
+    s = binding.plan(q, np.linspace(-25.0, 25.0, n))
+    assert (s["n_x"], s["n_y"]) == (1001, 1401)
+    for bad in (None, np.zeros(n - 1)):
+        with pytest.raises(binding.UcpError) as e:
+            binding.plan(q, bad)
+        assert e.value.status == -1
+
+
 @pytest.mark.parametrize("field,value,msg", [
     ("k", 0.0, "k must"), ("sigma", -1.0, "sigma"), ("delta", 0.0, "delta"),
     ("x_half", 25.02, "x_half"), ("w_half", 0.0, "w_half"),

@@ -62,6 +62,41 @@ def test_batch_members_equal_single_instances(binding, use_stream):
         assert J == ref["J"][-1]
 
 
+def start_table(binding, p):
+    """A smooth, odd, non-affine start on the x0 grid of p."""
+    n = binding.plan(p)["n_x"]
+    x = (np.arange(n) - (n - 1) // 2) * p["delta"]
+    return 0.8 * x + 0.5 * np.sin(0.7 * x)
+
+
+def test_batch_mixed_starts_equal_single_instances(binding):
+    """Members started from the identity, the odd staircase and a host table
+    (all set up by the batched set-up kernels) equal standalone solves."""
+    import torch
+    stream = torch.cuda.Stream()
+    ps = mixed_small(6, seed=11)
+    tables = []
+    for k, p in enumerate(ps):
+        ps[k] = dict(p, init_kind=k % 3)
+        tables.append(start_table(binding, p) if k % 3 == 2 else None)
+    with binding.Batch(ps, stream=stream, tables=tables) as b:
+        b.sweep(2)
+        got = []
+        for m in b.members:
+            st = m.get_controllers()
+            st["J"] = m.J_history()
+            got.append(st)
+    for p, t, st in zip(ps, tables, got):
+        with binding.Instance(p, table=t, stream=stream) as inst:
+            inst.sweep(2)
+            ref = inst.get_controllers()
+            ref["J"] = inst.J_history()
+        np.testing.assert_array_equal(st["f"], ref["f"])
+        np.testing.assert_array_equal(st["U"], ref["U"])
+        np.testing.assert_array_equal(st["idx"], ref["idx"])
+        np.testing.assert_array_equal(st["J"], ref["J"])
+
+
 def test_batch_against_oracle(binding):
     ps = mixed_small(4, seed=9)
     with binding.Batch(ps) as b:

@@ -87,6 +87,29 @@ def test_requests_join_while_others_run(binding):
     np.testing.assert_array_equal(res[t2]["f"], ref["f"])
 
 
+def test_served_table_starts_equal_standalone_solves(binding):
+    """Requests started from host tables (copied at submission, set up by the
+    batched set-up kernels at admission) equal the same solves alone."""
+    reqs = small_requests(4, seed=23)
+    tables = []
+    for k, p in enumerate(reqs):
+        n = binding.plan(p)["n_x"]
+        x = (np.arange(n) - (n - 1) // 2) * p["delta"]
+        tables.append(0.9 * x + 0.4 * np.sin(0.5 * x))
+        reqs[k] = dict(p, init_kind=2)
+    with binding.Server(max_slots=8) as srv:
+        tickets = [srv.submit(p, table=t) for p, t in zip(reqs, tables)]
+        res = wait_all(srv, tickets)
+    for p, t, tk in zip(reqs, tables, tickets):
+        with binding.Instance(p, table=t) as inst:
+            inst.sweep(p["sweeps"])
+            ref = inst.get_controllers(want=("f", "U"))
+            J = inst.eval_J()
+        np.testing.assert_array_equal(res[tk]["f"], ref["f"])
+        np.testing.assert_array_equal(res[tk]["U"], ref["U"])
+        assert res[tk]["J"] == J
+
+
 def test_budget_admission_and_rejection(binding):
     reqs = small_requests(3, seed=8)
     needs = sorted(binding.plan(p)["device_bytes"] for p in reqs)
