@@ -115,8 +115,8 @@ struct FastView : FastPlan {
     dfloat* box_part;    // [n_tiles * box_cap * (kBoxTerms + 1)] chunk partial moments
     float* run_lo;       // [n_runs] lower bound of min_i e_{i,j0} (scale)
     float* run_hi;       // [n_runs] upper bound of min_i e_ij over the run
-    double* partN;       // [n_tiles * n_y] numerator partials
-    double* partD;       // [n_tiles * n_y] denominator partials
+    dfloat* partN;       // [n_tiles * n_y] numerator partials (double-float)
+    dfloat* partD;       // [n_tiles * n_y] denominator partials
     double* Jpart;       // [J_blocks]
     uint16_t* tc_h;      // [2][tc_nch][kTcSlices][8][256] filter slices (bf16), shifted copies
     int32_t* tc_he;      // [2][tc_nch] filter chunk scales (exponents)
