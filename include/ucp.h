@@ -304,7 +304,7 @@ UCP_API ucp_status ucp_probe_alu(double* fp64_tflops, double* fp32_tflops,
  *   stream  cudaStream_t as void* (NULL: default stream); the call is
  *           asynchronous on it.
  * It allocates nothing: its intermediate buffers live in one fixed device
- * array of 5.6 MiB that every GPU loading the library holds until exit.
+ * array of 5.9 MiB that every GPU loading the library holds until exit.
  * Limits: n_x <= 32768 and n_y <= 32768, else UCP_E_ARG.  The first call on
  * a device looks up that array's address with the device current; make it
  * before any stream capture.  All calls share the array: calls that overlap

@@ -376,18 +376,26 @@ __device__ __forceinline__ Eval eval_outside(const Geom& g, const FastView& f, i
 // coefficients (search).  On the y grid (t = 0, every coarse candidate) the
 // quadratic is A0 itself: the Horner step would add exact zeros, so it is
 // skipped with the same result.
+// With a lattice of at most 2^24 points per cell (shift <= 24) the cell
+// fraction t is one exact float, and the products by t take the float form
+// of the double-float product (the same roundings, as t has no low part).
 __device__ __forceinline__ Eval eval_table(const Geom& g, const FastView& f,
                                            int64_t i, int64_t nu) {
     const int64_t cell = nu >> g.shift;
     const int64_t p = cell - f.c_lo;
-    if (p < 0 || p + 1 >= f.n_pos) return eval_outside(g, f, i, nu);
-    const int64_t frac = nu - cell * g.one;
+    if ((uint64_t)p >= (uint64_t)(f.n_pos - 1)) return eval_outside(g, f, i, nu);
+    const int64_t frac = nu & (g.one - 1);
     const dfloat a0 = f.C0[p];
     const float b = f.Cb[p];
     dfloat S = a0;
     if (frac != 0) {
-        const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
-        S = df_add(a0, df_mul(t, df_add(f.C1[p], df_mul(t, f.C2[p]))));
+        if (g.shift <= 24) {
+            const float t = __fmul_rn(__int2float_rn((int)frac), f.inv_one_f);   // exact
+            S = df_add(a0, df_mul_f(df_add(f.C1[p], df_mul_f(f.C2[p], t)), t));
+        } else {
+            const dfloat t = df_mul_f(df_from_i64(frac), f.inv_one_f);
+            S = df_add(a0, df_mul(t, df_add(f.C1[p], df_mul(t, f.C2[p]))));
+        }
     }
     const dfloat a = df_mul(df_from_i64(nu - (i - g.hx) * g.one), dfloat{f.step_hi, f.step_lo});
     const dfloat ctl = df_mul(dfloat{f.kk_hi, f.kk_lo}, df_mul(a, a));
@@ -998,7 +1006,7 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
     return r;
 }
 
-__global__ void __launch_bounds__(kSearchT, 5) kb_search(const InstDev* insts, const BlockRef* map) {
+__global__ void __launch_bounds__(kSearchT, 6) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
     __shared__ double tie_smem[kSearchT * kGroupScratch];
