@@ -264,11 +264,27 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
     b->ctx = ctx;
     b->stream = (cudaStream_t)stream;
     b->arena.ctx = ctx;
+    // one allocation holds every member's buffers (the members carve it)
+    std::vector<size_t> off((size_t)n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        Geom g;
+        make_geom(params[k], &g);
+        off[k + 1] = off[k] + ((inst_bytes(g, 1) + 255) & ~(size_t)255);
+    }
+    char* slab = (char*)b->arena.get(off[n]);
+    if (!slab) {
+        set_error("%s%s", "ucp_batch_create: out of device memory", "");
+        delete b;
+        return UCP_E_NOMEM;
+    }
     for (int k = 0; k < n; ++k) {
         ucp_inst* in = nullptr;
-        ucp_status st = inst_create(ctx, &params[k], (cudaStream_t)stream, false, &in);
+        ucp_status st = inst_create(ctx, &params[k], (cudaStream_t)stream, false, &in,
+                                    slab + off[k]);
         if (st != UCP_OK) {
             for (ucp_inst* m : b->members) ucp_destroy(m);
+            cudaStreamSynchronize(b->stream);
+            b->arena.release_all();
             delete b;
             return st;
         }

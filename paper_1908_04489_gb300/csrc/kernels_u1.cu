@@ -301,20 +301,40 @@ __device__ __forceinline__ void box_build_body(const Geom& g, const FastView& f,
 // e(y) <= pm + z^2/2 + h|z| (z = y - c), convex in y.
 constexpr int kRunT = 256;
 
+// The instance's boxes, compacted in tile order, are spread over the lanes:
+// each warp forms the prefix of the tiles' box counts (a shuffle scan; at
+// most 32 tiles) and finds the tile of its box s by a binary search over the
+// lanes.  The bounds are minima, so their order does not matter.
 __device__ __forceinline__ void run_shift_body(const Geom& g, const FastView& f,
                                                int64_t bx) {
     const int lane = threadIdx.x & 31;
     const int64_t r = bx * (kRunT / 32) + (threadIdx.x >> 5);
     if (r >= f.n_runs) return;   // the same for the warp
+    int end = lane < f.n_tiles ? f.box_cnt[lane] : 0;   // boxes of tiles 0..lane
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(kFull, end, d);
+        if (lane >= d) end += o;
+    }
+    const int nbox = __shfl_sync(kFull, end, 31);
     const int64_t j0 = r * f.run;
     const float ya = (float)((double)(j0 - g.hy) * g.delta);
     const float yb = (float)((double)(j0 + f.run - 1 - g.hy) * g.delta);
     float lo = FLT_MAX, hi = FLT_MAX;
-    const int nb = lane < f.n_tiles ? f.box_cnt[lane] : 0;   // lane = tile
-    for (int k = 0; k < nb; ++k) {
-        const int64_t s = (int64_t)lane * kBoxMax + k;
-        const float4 geo = f.box_geo[s];
-        const float4 rg = f.box_rng[s];
+    for (int b0 = 0; b0 < nbox; b0 += 32) {
+        const int s = b0 + lane;
+        // first tile whose running count exceeds s
+        int t = 0;
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) {
+            const int e = __shfl_sync(kFull, end, t + w - 1);
+            if (e <= s) t += w;
+        }
+        const int prev = __shfl_sync(kFull, end, t > 0 ? t - 1 : 0);   // boxes before tile t
+        if (s >= nbox) continue;
+        const int64_t slot = (int64_t)t * kBoxMax + (s - (t > 0 ? prev : 0));
+        const float4 geo = f.box_geo[slot];
+        const float4 rg = f.box_rng[slot];
         const float d1 = fmaxf(0.0f, fmaxf(rg.x - ya, ya - rg.y));
         const float lb1 = fmaf(0.5f * d1, d1, geo.w);
         const float za = fabsf(ya - geo.x);

@@ -122,8 +122,18 @@ bool Arena::reserve(size_t n) {
     if (!slab) return false;
     slab_size = n;
     slab_used = 0;
+    slab_owned = true;
     bytes += n;
     return true;
+}
+
+void Arena::adopt(void* p, size_t n) {
+    if (slab || !p) return;
+    slab = (char*)p;
+    slab_size = n;
+    slab_used = 0;
+    slab_owned = false;
+    bytes += n;
 }
 
 void* Arena::get(size_t n) {
@@ -151,9 +161,10 @@ void Arena::put(void* p) {
 void Arena::release_all() {
     for (void* p : ptrs) raw_free(ctx, p);
     ptrs.clear();
-    if (slab) raw_free(ctx, slab);
+    if (slab && slab_owned) raw_free(ctx, slab);
     slab = nullptr;
     slab_size = slab_used = 0;
+    slab_owned = false;
     bytes = 0;
 }
 
@@ -336,7 +347,7 @@ static ucp_status fast_refresh(ucp_inst* in, int slot) {
 }
 
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
-                     const Geom& g, cudaStream_t stream, bool own_setup) {
+                     const Geom& g, cudaStream_t stream, bool own_setup, void* slab) {
     in->ctx = ctx;
     in->params = p;
     in->params.init_table = nullptr;
@@ -350,7 +361,8 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     Arena& A = in->arena;
     const size_t nx = (size_t)g.n_x, ny = (size_t)g.n_y, nw = (size_t)g.n_w;
     // every buffer below from one allocation (inst_bytes counts them all)
-    A.reserve(inst_bytes(g, p.precision));
+    if (slab) A.adopt(slab, inst_bytes(g, p.precision));
+    else A.reserve(inst_bytes(g, p.precision));
     d.px = (double*)A.get(8 * nx);
     d.phi = (double*)A.get(8 * nw);
     d.U = (double*)A.get(8 * ny);

@@ -186,7 +186,7 @@ extern "C" ucp_status ucp_ctx_destroy(ucp_ctx* ctx) {
 // ---- instance ---------------------------------------------------------
 
 ucp_status ucp::inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t stream,
-                            bool own_setup, ucp_inst** out) {
+                            bool own_setup, ucp_inst** out, void* slab) {
     if (!params || !out) {
         set_error("ucp_create: %s%s", "NULL argument", "");
         return UCP_E_ARG;
@@ -202,7 +202,7 @@ ucp_status ucp::inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t
         return UCP_E_ARG;
     }
     ucp_inst* in = new ucp_inst();
-    ucp_status st = inst_init(in, ctx, *params, g, stream, own_setup);
+    ucp_status st = inst_init(in, ctx, *params, g, stream, own_setup, slab);
     if (st != UCP_OK) {
         inst_release(in);
         delete in;

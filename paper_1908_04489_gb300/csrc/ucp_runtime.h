@@ -71,7 +71,9 @@ struct Arena {
     size_t bytes = 0;
     char* slab = nullptr;
     size_t slab_size = 0, slab_used = 0;
+    bool slab_owned = false;
     bool reserve(size_t n);   // false if the allocation failed (get() still works)
+    void adopt(void* p, size_t n);   // carve from memory owned elsewhere
     void* get(size_t n);      // nullptr on failure
     void put(void* p);        // frees a separately allocated block; no-op in the slab
     void release_all();
@@ -114,11 +116,14 @@ size_t inst_bytes(const Geom& g, int precision);
 // fast instance created without own_setup gets its buffers and host-side
 // state only; its set-up kernels and first step come from batched launches
 // (batchset_setup) before its first sweep.
+// `slab`: inst_bytes(g, precision) bytes of device memory owned by the
+// caller (a batch), carved for the buffers instead of an allocation.
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
-                     const Geom& g, cudaStream_t stream, bool own_setup = true);
-// ucp_create with the choice above (validates the parameters).
+                     const Geom& g, cudaStream_t stream, bool own_setup = true,
+                     void* slab = nullptr);
+// ucp_create with the choices above (validates the parameters).
 ucp_status inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t stream,
-                       bool own_setup, ucp_inst** out);
+                       bool own_setup, ucp_inst** out, void* slab = nullptr);
 ucp_status inst_sweep(ucp_inst* in, int n);
 // Make room in the J history for `need` entries (synchronises on growth).
 ucp_status grow_history(ucp_inst* in, long long need);
