@@ -44,7 +44,7 @@ class _Params(ctypes.Structure):
                 ("w_half", ctypes.c_double), ("y_half", ctypes.c_double),
                 ("cand_half", ctypes.c_double), ("n_coarse", ctypes.c_int32),
                 ("n_refine", ctypes.c_int32), ("n_levels", ctypes.c_int32),
-                ("n_nbr", ctypes.c_int32)]
+                ("n_nbr", ctypes.c_int32), ("problem", ctypes.c_int32)]
 
 
 _lib = None
@@ -126,10 +126,12 @@ def get_threads() -> int:
 
 
 class Oracle:
-    """One Witsenhausen instance on the oracle.
+    """One instance on the oracle: Witsenhausen's counterexample (problem 0,
+    Section V-A) or zero-delay source-channel coding (problem 1, Section V-B).
 
     ``params`` is a mapping with keys k, sigma, delta, x_half, w_half, y_half,
-    cand_half, n_coarse, n_refine, n_levels, n_nbr (extra keys are ignored).
+    cand_half, n_coarse, n_refine, n_levels, n_nbr and optionally problem
+    (default 0; extra keys are ignored).
     Controllers f are int64 lattice indices nu; ``value(nu)`` converts.
     """
 
@@ -140,7 +142,8 @@ class Oracle:
                             ("k", "sigma", "delta", "x_half", "w_half",
                              "y_half", "cand_half")),
                           *(int(params[k]) for k in
-                            ("n_coarse", "n_refine", "n_levels", "n_nbr")))
+                            ("n_coarse", "n_refine", "n_levels", "n_nbr")),
+                          int(params.get("problem", 0)))
         n = [ctypes.c_int64() for _ in range(4)]
         sh = ctypes.c_int32()
         if self._lib().orc_sizes(ctypes.byref(self._p), *(ctypes.byref(v) for v in n),

@@ -34,6 +34,11 @@
  * The u1 sums and J run in index order.  The parallel loops over i and j
  * give results independent of the thread count.
  *
+ * Second problem (Section V-B, zero-delay source-channel coding): the same
+ * sweep with x1 = u0(x0) + w, w ~ U(-W, W), J = E[k^2 u0^2 + (u1(x1) - x0)^2];
+ * f = u0, equal quadrature weights, and u1(y) = E[x0 | x1 = y], a
+ * prior-weighted mean over the sources within W of y (see ucp_oracle.h).
+ *
  * Parity status: S, g, the search, the u1 update and J are pinned by the
  * tests in tests/test_oracle_pins.py (closed forms, library interpolation,
  * brute force, invariants).  The converged J printed in Section V-A is a
@@ -84,6 +89,7 @@ static int make_geom(const orc_params* p, geom* g) {
     if (half_steps(p->cand_half, p->delta, &g->hr)) return -1;
     if (p->n_coarse < 2 || p->n_refine < 2 || (p->n_refine & 1)) return -1;
     if (p->n_levels < 0 || p->n_nbr < 0) return -1;
+    if (p->problem != 0 && p->problem != 1) return -1;
     int32_t half_ref = p->n_refine / 2, bits = 0;
     while ((1 << bits) < half_ref) ++bits;
     if ((1 << bits) != half_ref) return -1;     /* ratio must be 2^bits */
@@ -171,6 +177,7 @@ static void phi_weights(const geom* g, double* phi) {
     for (int64_t l = 0; l < g->n_w; ++l) {
         double w = w_of(g, l);
         phi[l] = exp(-(w * w) / 2.0);
+        if (g->p.problem == 1) phi[l] = 1.0;   /* w ~ U(-w_half, w_half) */
     }
     double sum = fixed_sum(phi, g->n_w);
     for (int64_t l = 0; l < g->n_w; ++l) phi[l] = phi[l] / sum;
@@ -272,15 +279,38 @@ static double S_of(const geom* g, const double* phi, const double* U,
     return acc;
 }
 
+/* Problem 1: k^2 u^2 + sum_l phi_l (U^(u + w_l) - x_i)^2 at u = value(nu),
+ * the same positions and interpolation as S_of, the same summation order. */
+static double cost_sc(const geom* g, const double* phi, const double* U,
+                      int64_t i, int64_t nu) {
+    int64_t cell = floor_div(nu, g->one);
+    double t = ldexp((double)(nu - cell * g->one), -g->shift);
+    int64_t jb = cell - g->hw + g->hy;
+    double u = value_of(g, nu), x = x_of(g, i);
+    double* terms = (double*)malloc(sizeof(double) * (size_t)g->n_w);
+    for (int64_t l = 0; l < g->n_w; ++l) {
+        int64_t j = jb + l;
+        int64_t jl = j < 0 ? 0 : (j > g->n_y - 1 ? g->n_y - 1 : j);
+        int64_t jr = j + 1 < 0 ? 0 : (j + 1 > g->n_y - 1 ? g->n_y - 1 : j + 1);
+        double uh = U[jl] + t * (U[jr] - U[jl]);
+        double d = uh - x;
+        terms[l] = phi[l] * (d * d);
+    }
+    double acc = fixed_sum(terms, g->n_w);
+    free(terms);
+    return g->kk * (u * u) + acc;
+}
+
 static double cost_of(const geom* g, const double* phi, const double* U,
                       int64_t i, int64_t nu) {
+    if (g->p.problem == 1) return cost_sc(g, phi, U, i, nu);
     double a = value_of(g, nu) - x_of(g, i);
     return g->kk * (a * a) + S_of(g, phi, U, nu);
 }
 
 double orc_S(const orc_params* p, const double* U, int64_t nu) {
     geom g;
-    if (make_geom(p, &g)) return NAN;
+    if (make_geom(p, &g) || p->problem != 0) return NAN;
     double* phi = (double*)malloc(sizeof(double) * (size_t)g.n_w);
     phi_weights(&g, phi);
     double s = S_of(&g, phi, U, nu);
@@ -383,10 +413,51 @@ int orc_candidates(const orc_params* p, const int64_t* nu_pre, const double* U,
  * continuous phi.  Writing each weight as exp(-E_ij), the minimum of E_ij
  * over i is subtracted first; this cancels in the ratio and keeps the
  * largest weight at exactly 1. */
+/* Problem 1: the likelihood of x1 = y given x0 = x_i is constant for
+ * |y - f_i| <= w_half and zero beyond, so U_j is the mean of those x_i
+ * weighted by the prior alone (exponents shifted by their minimum, as in the
+ * Gaussian case).  Where no source is that close, the sources nearest to y
+ * take their place (the limit of a slightly wider window). */
+static void mmse_uniform(const geom* g, const int64_t* nu, double* U, int64_t j0,
+                         int64_t j1) {
+    const double W = g->p.w_half;
+    const double two_s2 = 2.0 * g->p.sigma * g->p.sigma;
+#pragma omp parallel for schedule(dynamic, 8) num_threads(g_threads)
+    for (int64_t j = j0; j < j1; ++j) {
+        double yj = y_of(g, j);
+        double dmin = INFINITY;
+        for (int64_t i = 0; i < g->n_x; ++i) {
+            double d = fabs(yj - value_of(g, nu[i]));
+            if (d < dmin) dmin = d;
+        }
+        double reach = dmin <= W ? W : dmin;
+        double emin = INFINITY;
+        for (int64_t i = 0; i < g->n_x; ++i) {
+            double xi = x_of(g, i);
+            if (fabs(yj - value_of(g, nu[i])) > reach) continue;
+            double e = (xi * xi) / two_s2;
+            if (e < emin) emin = e;
+        }
+        double num = 0.0, den = 0.0;
+        for (int64_t i = 0; i < g->n_x; ++i) {
+            double xi = x_of(g, i);
+            if (fabs(yj - value_of(g, nu[i])) > reach) continue;
+            double wgt = exp(-((xi * xi) / two_s2 - emin));
+            num = num + wgt * xi;
+            den = den + wgt;
+        }
+        U[j] = num / den;
+    }
+}
+
 void orc_mmse(const orc_params* p, const int64_t* nu, double* U, int64_t j0,
               int64_t j1) {
     geom g;
     if (make_geom(p, &g)) return;
+    if (p->problem == 1) {
+        mmse_uniform(&g, nu, U, j0, j1);
+        return;
+    }
     double two_s2 = 2.0 * p->sigma * p->sigma;
 #pragma omp parallel for schedule(dynamic, 8) num_threads(g_threads)
     for (int64_t j = j0; j < j1; ++j) {

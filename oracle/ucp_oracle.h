@@ -38,7 +38,18 @@ typedef struct {
     int32_t n_refine;  /* candidates per refinement level (16)                 */
     int32_t n_levels;  /* refinement levels L                                  */
     int32_t n_nbr;     /* neighbours per side in the partial exhaustion (2)    */
+    int32_t problem;   /* 0 Witsenhausen (Section V-A), 1 zero-delay source-
+                          channel coding (Section V-B)                          */
 } orc_params;
+
+/* Problem 1 (Section V-B): x0 ~ N(0, sigma^2), x1 = u0(x0) + w,
+ * w ~ U(-w_half, w_half), J = E[lambda u0^2 + (u1(x1) - x0)^2] with
+ * lambda = k^2.  The first controller is carried as f = u0 itself; the
+ * marginal cost of u0 at x_i is, up to p(x_i),
+ *   g(u; x_i) = k^2 u^2 + sum_l phi_l (U^(u + w_l) - x_i)^2
+ * with equal weights phi_l on the w grid, and u1(y) = E[x0 | x1 = y] is the
+ * prior-weighted mean of the x_i whose |y - f_i| <= w_half (those nearest to
+ * y when none is that close).  orc_S is defined for problem 0 only. */
 
 /* Sizes; returns 0 on success, -1 on invalid parameters. */
 int orc_sizes(const orc_params* p, int64_t* n_x, int64_t* n_w, int64_t* n_y,
@@ -58,7 +69,7 @@ int orc_init(const orc_params* p, int kind, const double* table,
 /* S(u) = sum_l phi_l (u - U^(u + w_l))^2 at u = value(nu). */
 double orc_S(const orc_params* p, const double* U, int64_t nu);
 
-/* g(u; x_i) = k^2 (u - x_i)^2 + S(u). */
+/* g(u; x_i) = k^2 (u - x_i)^2 + S(u) (problem 1: the cost above). */
 double orc_cost(const orc_params* p, const double* U, int64_t i, int64_t nu);
 
 /* Candidate search for x_i, i in [i0, i1): Jacobi, reads nu_pre, writes
@@ -70,11 +81,12 @@ void orc_search(const orc_params* p, const int64_t* nu_pre, const double* U,
 int orc_candidates(const orc_params* p, const int64_t* nu_pre, const double* U,
                    int64_t i, int64_t* nu_list, double* g_list);
 
-/* u1 update U_j = E[x1 | y1 = y_j] for j in [j0, j1). */
+/* u1 update U_j = E[x1 | y1 = y_j] (problem 1: E[x0 | x1 = y_j]) for j in
+ * [j0, j1). */
 void orc_mmse(const orc_params* p, const int64_t* nu, double* U, int64_t j0,
               int64_t j1);
 
-/* J = sum_i px_i (k^2 (f_i - x_i)^2 + S(f_i)). */
+/* J = sum_i px_i g(f_i; x_i). */
 double orc_J(const orc_params* p, const int64_t* nu, const double* U);
 
 /* init -> U = mmse(f) -> n_sweeps x {search, mmse, J}.  J_hist[0] is J of

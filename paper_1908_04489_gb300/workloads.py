@@ -83,6 +83,17 @@ def random_instance(rng: SplitMix64, deltas, sweeps: int, precision: int):
                 sweeps=sweeps, precision=precision)
 
 
+def source_channel(precision: int = 0, **kw):
+    """Zero-delay source-channel coding (Section V-B): lambda = 2 (k = sqrt 2,
+    the control cost k^2 u0^2), x0 ~ N(0, 1), w ~ U(-1, 1); x0 grid [-5, 5],
+    w grid [-1, 1], y grid [-7, 7] at delta = 0.02, coarse candidates in
+    [-6, 6], 4 levels of 16, identity start, 20 sweeps; plain FP64 path."""
+    p = base(k=math.sqrt(2.0), sigma=1.0, delta=0.02, x_half=5.0, w_half=1.0,
+             y_half=7.0, cand_half=6.0, problem=1, sweeps=20, precision=precision)
+    p.update(kw)
+    return p
+
+
 def c3(n: int = 256, seed: int = 1908, precision: int = 1):
     """Batched: n instances, seed 1908 stream 0, delta in {0.01, 0.02},
     identity init, 10 sweeps."""
