@@ -374,6 +374,60 @@ def measure_batched(args, binding, torch, stream, flush):
     }
 
 
+def measure_source_channel(args, binding, torch, stream, flush):
+    """Section V-B's second problem on the same sweep (zero-delay
+    source-channel coding, lambda = 2, w ~ U(-1, 1)), plain FP64 path: whole
+    solves (set-up + 20 sweeps) timed with CUDA events, J checked against the
+    oracle recomputing it from the GPU's final state."""
+    from paper_1908_04489_gb300 import workloads as W
+    p = W.source_channel()
+    for _ in range(2):
+        with binding.Instance(p, stream=stream) as inst:
+            inst.sweep(p["sweeps"])
+            inst.eval_J()
+    times = []
+    for _ in range(max(3, args.batch_steps)):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst = binding.Instance(p, stream=stream)
+        inst.sweep(p["sweeps"])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        J = inst.eval_J()
+        st = inst.get_controllers()
+        inst.close()
+    t = float(np.median(times)) / 1e3
+    out = {"workload": "zero-delay source-channel coding (Section V-B): lambda = 2, "
+                       "x0 ~ N(0,1), w ~ U(-1,1), delta = 0.02 (501 x0 / 101 w / 701 y), "
+                       "identity start, 20 sweeps, plain FP64 path",
+           "solves_per_s": 1.0 / t, "ms_per_solve": t * 1e3, "J": J,
+           "J_paper": 0.890756}
+    # FP64 work of the plain search: 6 flops per quadrature term, every
+    # candidate of every x0 point each sweep (the u1 and J passes are small)
+    sz = binding.plan(p)
+    flops = sz["n_x"] * sz["n_cand"] * sz["n_w"] * 6.0 * p["sweeps"]
+    fp64 = binding.probe_alu(stream)["fp64_tflops"]
+    out["search_fp64_tflops"] = flops / t / 1e12
+    out["search_fp64_frac"] = flops / t / 1e12 / fp64
+    if not args.no_cpu:
+        import oracle
+        o = oracle.Oracle(p)
+        Jo = o.J(o.init(2, st["f"]), st["U"])
+        out["abs_dJ_oracle_from_gpu_state"] = abs(J - Jo)
+        cores = os.cpu_count() or 1
+        oracle.set_threads(cores)
+        t0 = time.perf_counter()
+        ref = o.solve(0, p["sweeps"])
+        tc = time.perf_counter() - t0
+        oracle.set_threads(1)
+        out["cpu_oracle"] = {"solves_per_s": 1.0 / tc, "cores": cores,
+                             "sample": "one whole solve (20 sweeps) from the identity"}
+        out["abs_dJ_vs_oracle_trajectory"] = abs(J - float(ref["J"][-1]))
+    return out
+
+
 def measure_serving(args, binding, torch):
     """c4-style stream: requests (k log-U[0.05,0.5], sigma U[1,10], delta in
     {0.05, 0.01, 0.005}, 20 sweeps) submitted at Poisson arrival times at each
@@ -557,6 +611,9 @@ def run_gpu(args):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = measure_batched(args, binding, torch, stream, flush)
+    source_channel = None
+    if rank == 0 and not args.no_batched:
+        source_channel = measure_source_channel(args, binding, torch, stream, flush)
     serving = None
     if rank == 0 and not args.no_serving:
         serving = measure_serving(args, binding, torch)
@@ -582,6 +639,8 @@ def run_gpu(args):
     }
     if batched is not None:
         line["batched"] = batched
+    if source_channel is not None:
+        line["source_channel"] = source_channel
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:

@@ -94,6 +94,14 @@ typedef struct {
     const double* init_table; /* host, n_x values of f, init_kind 2 only     */
     uint64_t init_len;        /* must equal n_x for init_kind 2              */
     uint64_t flags;           /* reserved, must be 0                         */
+    int32_t problem;    /* 0: Witsenhausen's counterexample (Section V-A):
+                           x1 = x0 + u0(x0), y1 = x1 + w, w ~ N(0, 1),
+                           J = E[k^2 u0^2 + (x1 - u1(y1))^2], f = x1.
+                           1: zero-delay source-channel coding (Section V-B):
+                           x1 = u0(x0) + w, w ~ U(-w_half, w_half),
+                           J = E[k^2 u0^2 + (u1(x1) - x0)^2] (lambda = k^2),
+                           f = u0; plain FP64 path only (precision 0).       */
+    int32_t reserved;   /* must be 0                                         */
 } ucp_params;
 
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc

@@ -37,7 +37,8 @@ class Params(ctypes.Structure):
                 ("n_nbr", ctypes.c_int32), ("init_kind", ctypes.c_int32),
                 ("precision", ctypes.c_int32),
                 ("init_table", ctypes.POINTER(ctypes.c_double)),
-                ("init_len", ctypes.c_uint64), ("flags", ctypes.c_uint64)]
+                ("init_len", ctypes.c_uint64), ("flags", ctypes.c_uint64),
+                ("problem", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     @classmethod
     def from_dict(cls, p, table=None):
@@ -45,7 +46,8 @@ class Params(ctypes.Structure):
                   float(p["x_half"]), float(p["w_half"]), float(p["y_half"]),
                   float(p["cand_half"]), int(p["n_coarse"]), int(p["n_refine"]),
                   int(p["n_levels"]), int(p["n_nbr"]), int(p.get("init_kind", 0)),
-                  int(p.get("precision", 0)), None, 0, int(p.get("flags", 0)))
+                  int(p.get("precision", 0)), None, 0, int(p.get("flags", 0)),
+                  int(p.get("problem", 0)), 0)
         if table is not None:
             obj._table = np.ascontiguousarray(table, dtype=np.float64)
             obj.init_table = obj._table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -61,8 +61,50 @@ __device__ double S_plain(const Geom& g, const double* __restrict__ phi,
     return acc.result();
 }
 
+// Problem 1 (source-channel coding, Section V-B): the quadrature of the
+// estimation error, sum_l phi_l (U^(u + w_l) - x)^2, with the positions,
+// interpolation and fixed summation order of S_plain.
+__device__ double Q_plain(const Geom& g, const double* __restrict__ phi,
+                          const double* __restrict__ U,
+                          const double* __restrict__ Ud, int64_t nu, double x) {
+    const int64_t cell = nu >> g.shift;
+    const double t = __dmul_rn((double)(nu - (cell << g.shift)), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy;
+    const int64_t ny1 = g.n_y - 1;
+    FixedSum acc;
+    int64_t l = 0;
+    const double dL = __dsub_rn(__dadd_rn(U[0], __dmul_rn(t, 0.0)), x);
+    const double dL2 = __dmul_rn(dL, dL);
+    for (; l < g.n_w && jb + l < 0; ++l) acc.add(__dmul_rn(phi[l], dL2));
+    for (; l < g.n_w && jb + l < ny1; ++l) {
+        const int64_t j = jb + l;
+        const double d = __dsub_rn(__dadd_rn(U[j], __dmul_rn(t, Ud[j])), x);
+        acc.add(__dmul_rn(phi[l], __dmul_rn(d, d)));
+    }
+    const double dR = __dsub_rn(__dadd_rn(U[ny1], __dmul_rn(t, 0.0)), x);
+    const double dR2 = __dmul_rn(dR, dR);
+    for (; l < g.n_w; ++l) acc.add(__dmul_rn(phi[l], dR2));
+    return acc.result();
+}
+
+// The quadrature part of candidate nu's cost for x0 point i: S(u)
+// (problem 0, the same for every i) or the estimation error at x_i.
+__device__ __forceinline__ double quad_plain(const Geom& g, const double* __restrict__ phi,
+                                             const double* __restrict__ U,
+                                             const double* __restrict__ Ud, int64_t nu,
+                                             int64_t i) {
+    return g.problem == 1 ? Q_plain(g, phi, U, Ud, nu, x_of(g, i))
+                          : S_plain(g, phi, U, Ud, nu);
+}
+
+// g(u; x_i) from the quadrature part: k^2 (u - x_i)^2 + S (problem 0), or
+// k^2 u^2 + Q (problem 1, where f = u0 itself).
 __device__ __forceinline__ double cost_from_S(const Geom& g, int64_t i,
                                               int64_t nu, double S) {
+    if (g.problem == 1) {
+        const double u = value_of(g, nu);
+        return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(u, u)), S);
+    }
     const double a = __dsub_rn(value_of(g, nu), x_of(g, i));
     return __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), S);
 }
@@ -101,7 +143,8 @@ __device__ __forceinline__ void weights_exp_elem(const Geom& g, double* px, doub
     }
     if (k < g.n_w) {
         const double wl = __dmul_rn((double)(k - g.hw), g.delta);
-        phi[k] = exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
+        // problem 1: w ~ U(-w_half, w_half), equal weights
+        phi[k] = g.problem == 1 ? 1.0 : exp(-__ddiv_rn(__dmul_rn(wl, wl), 2.0));
     }
 }
 
@@ -247,7 +290,7 @@ __global__ void k_f_values(Geom g, const int64_t* nu, double* out, int as_u0) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_x) return;
     const double f = value_of(g, nu[i]);
-    out[i] = as_u0 ? __dsub_rn(f, x_of(g, i)) : f;
+    out[i] = as_u0 && g.problem == 0 ? __dsub_rn(f, x_of(g, i)) : f;   // problem 1: f = u0
 }
 
 // ---- u1 step: U_j = E[x1 | y1 = y_j] -----------------------------------
@@ -297,20 +340,66 @@ __global__ void __launch_bounds__(128) k_mmse_plain(Geom g, const int64_t* nu,
     }
 }
 
+// Problem 1 (Section V-B): U_j = E[x0 | x1 = y_j] with w uniform on
+// [-W, W]: the x_i with |y_j - f_i| <= W, weighted by the prior alone
+// (exponents x_i^2 / (2 sigma^2) shifted by their minimum over those x_i), or
+// the x_i nearest to y_j when none is within W.  Three passes over the x_i in
+// index order: the nearest distance, the minimum exponent, the sums.
+__global__ void __launch_bounds__(128) k_mmse_uniform(Geom g, const int64_t* nu,
+                                                      double* U) {
+    __shared__ double s_pri[kMmseChunk];
+    __shared__ double s_x[kMmseChunk];
+    __shared__ double s_f[kMmseChunk];
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double yj = __dmul_rn((double)((j < g.n_y ? j : g.n_y - 1) - g.hy), g.delta);
+    double dmin = DBL_MAX, reach = 0.0, emin = DBL_MAX, num = 0.0, den = 0.0;
+    for (int pass = 0; pass < 3; ++pass) {
+        if (pass == 1) reach = dmin <= g.w_noise ? g.w_noise : dmin;
+        for (int64_t base = 0; base < g.n_x; base += kMmseChunk) {
+            const int cnt = (int)min((int64_t)kMmseChunk, g.n_x - base);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                const double xi = x_of(g, base + t);
+                s_x[t] = xi;
+                s_pri[t] = __ddiv_rn(__dmul_rn(xi, xi), g.two_s2);
+                s_f[t] = value_of(g, nu[base + t]);
+            }
+            __syncthreads();
+            for (int t = 0; t < cnt; ++t) {
+                const double d = fabs(__dsub_rn(yj, s_f[t]));
+                if (pass == 0) {
+                    dmin = d < dmin ? d : dmin;
+                } else if (d <= reach) {
+                    if (pass == 1) {
+                        emin = s_pri[t] < emin ? s_pri[t] : emin;
+                    } else {
+                        const double wgt = exp(-__dsub_rn(s_pri[t], emin));
+                        num = __dadd_rn(num, __dmul_rn(wgt, s_x[t]));
+                        den = __dadd_rn(den, wgt);
+                    }
+                }
+            }
+        }
+    }
+    if (j < g.n_y) U[j] = __ddiv_rn(num, den);
+}
+
 __global__ void k_udiff(Geom g, const double* U, double* Ud) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= g.n_y) return;
     Ud[j] = j + 1 < g.n_y ? __dsub_rn(U[j + 1], U[j]) : 0.0;
 }
 
+// out[k] = quadrature part of the cost of nus[k]; with at_x (the list of
+// f_i) the estimation error of problem 1 is taken at x0 point k.
 __global__ void k_S_list(Geom g, const double* __restrict__ phi,
                          const double* __restrict__ U,
                          const double* __restrict__ Ud,
                          const int64_t* __restrict__ nus, int64_t n,
-                         double* out) {
+                         double* out, int at_x) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    out[k] = S_plain(g, phi, U, Ud, nus[k]);
+    out[k] = at_x ? quad_plain(g, phi, U, Ud, nus[k], k) : S_plain(g, phi, U, Ud, nus[k]);
 }
 
 // ---- u0 step: candidate search, one group of n_refine lanes per x_i ----
@@ -346,8 +435,11 @@ __global__ void __launch_bounds__(256) k_search_plain(
         } else {
             const int c = p - 1 - 2 * g.n_nbr;
             nu = coarse[c];
-            S = Sc[c];
+            S = g.problem == 1 ? 0.0 : Sc[c];
         }
+        // problem 1: the estimation error depends on x_i, so only the
+        // incumbent's comes precomputed
+        if (g.problem == 1 && p != 0) S = Q_plain(g, phi, U, Ud, nu, x_of(g, ic));
         const double gv = cost_from_S(g, ic, nu, S);
         if (before(gv, p, best_g, best_p)) { best_g = gv; best_p = p; best_nu = nu; }
     }
@@ -360,7 +452,7 @@ __global__ void __launch_bounds__(256) k_search_plain(
     for (int lv = 1; lv <= g.n_levels; ++lv) {
         const int64_t h = g.q << (g.bits * (g.n_levels - lv));
         const int64_t nu = best_nu + m * h;
-        const double gv = cost_from_S(g, ic, nu, S_plain(g, phi, U, Ud, nu));
+        const double gv = cost_from_S(g, ic, nu, quad_plain(g, phi, U, Ud, nu, ic));
         double cg = best_g;
         int32_t cp = best_p;
         int64_t cn = best_nu;
@@ -440,7 +532,10 @@ void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s) {
 }
 
 void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s) {
-    k_mmse_plain<<<blocks(g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+    if (g.problem == 1)
+        k_mmse_uniform<<<blocks(g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+    else
+        k_mmse_plain<<<blocks(g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
 }
 
 void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {
@@ -448,9 +543,9 @@ void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {
 }
 
 void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
-                   double* out, cudaStream_t s) {
+                   double* out, cudaStream_t s, int at_x) {
     if (n <= 0) return;
-    k_S_list<<<blocks(n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out);
+    k_S_list<<<blocks(n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out, at_x);
 }
 
 void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s) {

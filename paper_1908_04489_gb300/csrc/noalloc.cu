@@ -123,6 +123,10 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
         set_error("ucp_u1_update_noalloc: %s%s", why, "");
         return UCP_E_ARG;
     }
+    if (g.problem != 0) {
+        set_error("ucp_u1_update_noalloc: %s%s", "Witsenhausen's problem (problem 0) only", "");
+        return UCP_E_ARG;
+    }
     if (g.n_x > kMaxX || g.n_y > kMaxY) {
         set_error("ucp_u1_update_noalloc: %s%s",
                   "grid too large for the static scratch (needs n_x <= 32768 "

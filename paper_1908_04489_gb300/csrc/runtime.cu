@@ -184,8 +184,11 @@ static ucp_status refresh_costs(ucp_inst* in, int slot) {
     const Geom& g = in->g;
     DevState& d = in->d;
     UCP_LAUNCH(in, "udiff", launch_udiff(g, d, in->stream));
-    UCP_LAUNCH(in, "S_coarse", launch_S_list(g, d, d.coarse, g.n_coarse, d.Sc, in->stream));
-    UCP_LAUNCH(in, "S_f", launch_S_list(g, d, d.nu[in->cur], g.n_x, d.Sf, in->stream));
+    // S at the coarse candidates is shared by every x0 point in problem 0;
+    // problem 1's estimation error depends on x0 and is formed in the search
+    if (g.problem == 0)
+        UCP_LAUNCH(in, "S_coarse", launch_S_list(g, d, d.coarse, g.n_coarse, d.Sc, in->stream, 0));
+    UCP_LAUNCH(in, "S_f", launch_S_list(g, d, d.nu[in->cur], g.n_x, d.Sf, in->stream, 1));
     UCP_LAUNCH(in, "J", launch_J_plain(g, d, in->cur, slot, in->stream));
     return check(in, "refresh");
 }

@@ -25,6 +25,8 @@ struct Geom {
     int32_t n_coarse, n_refine, n_levels, n_nbr;
     int32_t n_cand;             // 1 + 2 n_nbr + n_coarse + L n_refine
     int32_t u1_tile_min;        // fewest x0 points per tile of the u1 step
+    int32_t problem;            // 0 Witsenhausen, 1 source-channel coding
+    double w_noise;             // problem 1: noise half width (w_half)
 };
 
 // Fills g from params; returns nullptr or a static reason string.
@@ -240,8 +242,9 @@ void launch_table_to_lattice(const Geom& g, const double* table, int64_t* nu,
 void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s);
 void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s);
 void launch_udiff(const Geom& g, DevState& d, cudaStream_t s);
+// out[k] = quadrature part of the cost of nus[k] (at_x: for x0 point k).
 void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
-                   double* out, cudaStream_t s);
+                   double* out, cudaStream_t s, int at_x);
 void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s);
 void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
                     cudaStream_t s);

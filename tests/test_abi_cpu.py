@@ -75,7 +75,7 @@ def test_plan_of_a_table_start(lib):
     ("n_refine", 12, "n_refine"), ("n_levels", 9, "n_levels"),
     ("n_coarse", 1, "n_coarse"), ("n_nbr", -1, "n_nbr"),
     ("precision", 2, "precision"), ("init_kind", 5, "init_kind"),
-    ("flags", 1, "flags"),
+    ("flags", 1, "flags"), ("problem", 2, "problem"),
 ])
 def test_plan_rejects_invalid_fields(lib, field, value, msg):
     from paper_1908_04489_gb300 import binding, workloads
@@ -84,6 +84,18 @@ def test_plan_rejects_invalid_fields(lib, field, value, msg):
     with pytest.raises(binding.UcpError) as e:
         binding.plan(p)
     assert e.value.status == -1 and msg in str(e.value)
+
+
+def test_source_channel_problem_is_planned_on_the_plain_path(lib):
+    """Problem 1 (Section V-B) runs on the plain FP64 path: its plan has the
+    grids of its parameters, and the fast path is refused."""
+    from paper_1908_04489_gb300 import binding, workloads
+    p = workloads.source_channel()
+    s = binding.plan(p)
+    assert (s["n_x"], s["n_w"], s["n_y"], s["n_cand"]) == (501, 101, 701, 133)
+    with pytest.raises(binding.UcpError) as e:
+        binding.plan(dict(p, precision=1))
+    assert e.value.status == -1 and "plain FP64 path" in str(e.value)
 
 
 def test_create_validates_before_touching_the_device(lib):
