@@ -47,6 +47,10 @@ def workload(name: str, precision: int):
         return W.c1() | {"precision": precision}, (
             "c1: k=0.2 sigma=5, delta=0.05 (1001/241/1401), identity init, "
             "10 sweeps")
+    if name == "sc":
+        return W.source_channel(), (
+            "zero-delay source-channel coding (Section V-B): lambda=2, x0 ~ N(0,1), "
+            "w ~ U(-1,1), delta=0.02 (501/101/701), identity init, 20 sweeps, plain FP64")
     if name == "c5":
         return W.c5(precision=precision), (
             "c5: k=0.2 sigma=10, delta=0.001 (100001/14001/120001), 6 levels, "
@@ -399,11 +403,16 @@ def measure_source_channel(args, binding, torch, stream, flush):
         st = inst.get_controllers()
         inst.close()
     t = float(np.median(times)) / 1e3
+    # one more solve with per-kernel events (kernel by kernel on the stream)
+    with binding.Instance(p, stream=stream) as inst:
+        inst.profile(True)
+        inst.sweep(p["sweeps"])
+        kern = {k: v[1] for k, v in inst.kernel_times().items()}
     out = {"workload": "zero-delay source-channel coding (Section V-B): lambda = 2, "
                        "x0 ~ N(0,1), w ~ U(-1,1), delta = 0.02 (501 x0 / 101 w / 701 y), "
                        "identity start, 20 sweeps, plain FP64 path",
            "solves_per_s": 1.0 / t, "ms_per_solve": t * 1e3, "J": J,
-           "J_paper": 0.890756}
+           "J_paper": 0.890756, "kernels_ms_per_solve": kern}
     # FP64 work of the plain search: 6 flops per quadrature term, every
     # candidate of every x0 point each sweep (the u1 and J passes are small)
     sz = binding.plan(p)

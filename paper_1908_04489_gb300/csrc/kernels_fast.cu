@@ -132,7 +132,17 @@ __device__ double exact_costs_coop(const Geom& g, const FastView& f, int64_t i,
                 const double u = value_of(g, cnu);
                 const int64_t e = min((k + 1) * kSumChunk, g.n_w);
                 double a = 0.0;
-                for (int64_t l = k * kSumChunk; l < e; ++l)
+                int64_t l = k * kSumChunk;
+                // eight terms as independent chains, then added in order
+                for (; l + 8 <= e; l += 8) {
+                    double tm[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        tm[q] = exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l + q);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) a = __dadd_rn(a, tm[q]);
+                }
+                for (; l < e; ++l)
                     a = __dadd_rn(a, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
                 ch[m * cn + (k - c0)] = a;
             }

@@ -46,8 +46,22 @@ __device__ double S_plain(const Geom& g, const double* __restrict__ phi,
     const double eL = __dsub_rn(u, __dadd_rn(u0, __dmul_rn(t, 0.0)));
     const double eL2 = __dmul_rn(eL, eL);
     for (; l < g.n_w && jb + l < 0; ++l) acc.add(__dmul_rn(phi[l], eL2));
-    // interior: 0 <= j < n_y - 1
-    for (; l < g.n_w && jb + l < ny1; ++l) {
+    // interior: 0 <= j < n_y - 1; eight terms formed as independent chains,
+    // then added in order (the same additions as one term at a time)
+    const int64_t lend = min(g.n_w, ny1 - jb);
+    for (; l + 8 <= lend; l += 8) {
+        double term[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t j = jb + l + q;
+            const double uh = __dadd_rn(U[j], __dmul_rn(t, Ud[j]));
+            const double e = __dsub_rn(u, uh);
+            term[q] = __dmul_rn(phi[l + q], __dmul_rn(e, e));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc.add(term[q]);
+    }
+    for (; l < lend; ++l) {
         const int64_t j = jb + l;
         const double uh = __dadd_rn(U[j], __dmul_rn(t, Ud[j]));
         const double e = __dsub_rn(u, uh);
@@ -76,7 +90,19 @@ __device__ double Q_plain(const Geom& g, const double* __restrict__ phi,
     const double dL = __dsub_rn(__dadd_rn(U[0], __dmul_rn(t, 0.0)), x);
     const double dL2 = __dmul_rn(dL, dL);
     for (; l < g.n_w && jb + l < 0; ++l) acc.add(__dmul_rn(phi[l], dL2));
-    for (; l < g.n_w && jb + l < ny1; ++l) {
+    const int64_t lend = min(g.n_w, ny1 - jb);
+    for (; l + 8 <= lend; l += 8) {
+        double term[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t j = jb + l + q;
+            const double d = __dsub_rn(__dadd_rn(U[j], __dmul_rn(t, Ud[j])), x);
+            term[q] = __dmul_rn(phi[l + q], __dmul_rn(d, d));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc.add(term[q]);
+    }
+    for (; l < lend; ++l) {
         const int64_t j = jb + l;
         const double d = __dsub_rn(__dadd_rn(U[j], __dmul_rn(t, Ud[j])), x);
         acc.add(__dmul_rn(phi[l], __dmul_rn(d, d)));
@@ -294,9 +320,11 @@ __global__ void k_f_values(Geom g, const int64_t* nu, double* out, int as_u0) {
 }
 
 // ---- u1 step: U_j = E[x1 | y1 = y_j] -----------------------------------
-// One thread per y_j sums over all x_i in index order (same order as a
-// serial evaluation), after subtracting min_i E_ij from the exponents
-// E_ij = x_i^2 / (2 sigma^2) + (y_j - f_i)^2 / 2.
+// One thread per y_j sums over all x_i in index order (the order of a
+// serial evaluation) after subtracting min_i E_ij from the exponents
+// E_ij = x_i^2 / (2 sigma^2) + (y_j - f_i)^2 / 2.  The minimum runs as four
+// interleaved chains (a minimum is exact in any order); the weights of four
+// sources are formed as independent chains before being added in order.
 constexpr int kMmseChunk = 1024;
 
 __global__ void __launch_bounds__(128) k_mmse_plain(Geom g, const int64_t* nu,
@@ -306,9 +334,10 @@ __global__ void __launch_bounds__(128) k_mmse_plain(Geom g, const int64_t* nu,
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double yj = __dmul_rn((double)((j < g.n_y ? j : g.n_y - 1) - g.hy),
                                 g.delta);
+    double em[4] = {DBL_MAX, DBL_MAX, DBL_MAX, DBL_MAX};
+    double num = 0.0, den = 0.0;
     double emin = DBL_MAX;
     for (int pass = 0; pass < 2; ++pass) {
-        double num = 0.0, den = 0.0;
         for (int64_t base = 0; base < g.n_x; base += kMmseChunk) {
             const int cnt = (int)min((int64_t)kMmseChunk, g.n_x - base);
             __syncthreads();
@@ -318,42 +347,52 @@ __global__ void __launch_bounds__(128) k_mmse_plain(Geom g, const int64_t* nu,
                 s_f[t] = value_of(g, nu[base + t]);
             }
             __syncthreads();
-            if (pass == 0) {
-                for (int t = 0; t < cnt; ++t) {
-                    const double d = __dsub_rn(yj, s_f[t]);
-                    const double e = __dadd_rn(s_pri[t],
-                                               __ddiv_rn(__dmul_rn(d, d), 2.0));
-                    emin = e < emin ? e : emin;
+            for (int t0 = 0; t0 < cnt; t0 += 4) {
+                double wg[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + q;
+                    wg[q] = 0.0;
+                    if (t < cnt) {
+                        const double d = __dsub_rn(yj, s_f[t]);
+                        const double e = __dadd_rn(s_pri[t],
+                                                   __ddiv_rn(__dmul_rn(d, d), 2.0));
+                        if (pass == 0) em[q] = e < em[q] ? e : em[q];
+                        else wg[q] = exp(-__dsub_rn(e, emin));
+                    }
                 }
-            } else {
-                for (int t = 0; t < cnt; ++t) {
-                    const double d = __dsub_rn(yj, s_f[t]);
-                    const double e = __dadd_rn(s_pri[t],
-                                               __ddiv_rn(__dmul_rn(d, d), 2.0));
-                    const double wgt = exp(-__dsub_rn(e, emin));
-                    num = __dadd_rn(num, __dmul_rn(wgt, s_f[t]));
-                    den = __dadd_rn(den, wgt);
+                if (pass == 1) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (t0 + q < cnt) {
+                            num = __dadd_rn(num, __dmul_rn(wg[q], s_f[t0 + q]));
+                            den = __dadd_rn(den, wg[q]);
+                        }
                 }
             }
         }
-        if (pass == 1 && j < g.n_y) U[j] = __ddiv_rn(num, den);
+        if (pass == 0) emin = fmin(fmin(em[0], em[1]), fmin(em[2], em[3]));
     }
+    if (j < g.n_y) U[j] = __ddiv_rn(num, den);
 }
 
 // Problem 1 (Section V-B): U_j = E[x0 | x1 = y_j] with w uniform on
-// [-W, W]: the x_i with |y_j - f_i| <= W, weighted by the prior alone
-// (exponents x_i^2 / (2 sigma^2) shifted by their minimum over those x_i), or
-// the x_i nearest to y_j when none is within W.  Three passes over the x_i in
-// index order: the nearest distance, the minimum exponent, the sums.
+// [-W, W]: the x_i with |y_j - f_i| <= W weighted by the prior alone, or the
+// x_i nearest to y_j when none is within W.  The weight of x_i is the same
+// for every target, so the block forms exp(-x_i^2 / (2 sigma^2)) once per
+// source (the oracle's per-target shift by the smallest exponent scales
+// numerator and denominator alike and only changes roundings).  Two passes
+// over the x_i: the nearest distance, then the sums in index order.
 __global__ void __launch_bounds__(128) k_mmse_uniform(Geom g, const int64_t* nu,
                                                       double* U) {
-    __shared__ double s_pri[kMmseChunk];
+    __shared__ double s_p[kMmseChunk];
     __shared__ double s_x[kMmseChunk];
     __shared__ double s_f[kMmseChunk];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double yj = __dmul_rn((double)((j < g.n_y ? j : g.n_y - 1) - g.hy), g.delta);
-    double dmin = DBL_MAX, reach = 0.0, emin = DBL_MAX, num = 0.0, den = 0.0;
-    for (int pass = 0; pass < 3; ++pass) {
+    double dmin = DBL_MAX, reach = 0.0, num = 0.0, den = 0.0;
+    double dm[4] = {DBL_MAX, DBL_MAX, DBL_MAX, DBL_MAX};
+    for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) reach = dmin <= g.w_noise ? g.w_noise : dmin;
         for (int64_t base = 0; base < g.n_x; base += kMmseChunk) {
             const int cnt = (int)min((int64_t)kMmseChunk, g.n_x - base);
@@ -361,25 +400,29 @@ __global__ void __launch_bounds__(128) k_mmse_uniform(Geom g, const int64_t* nu,
             for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
                 const double xi = x_of(g, base + t);
                 s_x[t] = xi;
-                s_pri[t] = __ddiv_rn(__dmul_rn(xi, xi), g.two_s2);
+                if (pass == 1) s_p[t] = exp(-__ddiv_rn(__dmul_rn(xi, xi), g.two_s2));
                 s_f[t] = value_of(g, nu[base + t]);
             }
             __syncthreads();
-            for (int t = 0; t < cnt; ++t) {
-                const double d = fabs(__dsub_rn(yj, s_f[t]));
-                if (pass == 0) {
-                    dmin = d < dmin ? d : dmin;
-                } else if (d <= reach) {
-                    if (pass == 1) {
-                        emin = s_pri[t] < emin ? s_pri[t] : emin;
-                    } else {
-                        const double wgt = exp(-__dsub_rn(s_pri[t], emin));
-                        num = __dadd_rn(num, __dmul_rn(wgt, s_x[t]));
-                        den = __dadd_rn(den, wgt);
+            // the nearest distance as four interleaved chains (a minimum is
+            // exact in any order); the sums in index order
+            for (int t0 = 0; t0 < cnt; t0 += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int t = t0 + q;
+                    if (t < cnt) {
+                        const double d = fabs(__dsub_rn(yj, s_f[t]));
+                        if (pass == 0) {
+                            dm[q] = d < dm[q] ? d : dm[q];
+                        } else if (d <= reach) {
+                            num = __dadd_rn(num, __dmul_rn(s_p[t], s_x[t]));
+                            den = __dadd_rn(den, s_p[t]);
+                        }
                     }
                 }
             }
         }
+        if (pass == 0) dmin = fmin(fmin(dm[0], dm[1]), fmin(dm[2], dm[3]));
     }
     if (j < g.n_y) U[j] = __ddiv_rn(num, den);
 }
@@ -468,16 +511,52 @@ __global__ void __launch_bounds__(256) k_search_plain(
 }
 
 // ---- J = sum_i p_i (k^2 (f_i - x_i)^2 + S(f_i)), serial order ------------
-__global__ void k_J_plain(Geom g, const double* px, const int64_t* nu,
-                          const double* Sf, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The block forms the products p_i g_i of a chunk in shared memory, thread 0
+// adds them in index order (the same additions as a serial loop, without a
+// global load in the dependent chain).
+constexpr int kJChunk = 2048;
+__global__ void __launch_bounds__(256) k_J_plain(Geom g, const double* px, const int64_t* nu,
+                                                 const double* Sf, double* out) {
+    __shared__ double v[kJChunk];
     double J = 0.0;
-    for (int64_t i = 0; i < g.n_x; ++i)
-        J = __dadd_rn(J, __dmul_rn(px[i], cost_from_S(g, i, nu[i], Sf[i])));
-    *out = J;
+    for (int64_t base = 0; base < g.n_x; base += kJChunk) {
+        const int cnt = (int)min((int64_t)kJChunk, g.n_x - base);
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int64_t i = base + t;
+            v[t] = __dmul_rn(px[i], cost_from_S(g, i, nu[i], Sf[i]));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int t = 0; t < cnt; ++t) J = __dadd_rn(J, v[t]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = J;
 }
 
 inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// SMs of the current device (cached per device).
+int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 152;
+    }
+    return cache[dev];
+}
+
+// Threads per block for n threads of FP64-heavy work: the largest power of
+// two up to max_bs that still gives every SM a block (at least 32).  The
+// plain path's throughput is the FP64 pipes', so a small problem in large
+// blocks would leave most SMs' FP64 units idle.
+int spread_bs(int64_t n, int max_bs) {
+    int bs = max_bs;
+    while (bs > 32 && (n + bs - 1) / bs < sm_count()) bs /= 2;
+    return bs;
+}
 
 }  // namespace
 
@@ -533,9 +612,11 @@ void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s) {
 
 void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s) {
     if (g.problem == 1)
-        k_mmse_uniform<<<blocks(g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+        k_mmse_uniform<<<blocks(g.n_y, spread_bs(g.n_y, 128)), spread_bs(g.n_y, 128), 0, s>>>(
+            g, d.nu[buf], d.U);
     else
-        k_mmse_plain<<<blocks(g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+        k_mmse_plain<<<blocks(g.n_y, spread_bs(g.n_y, 128)), spread_bs(g.n_y, 128), 0, s>>>(
+            g, d.nu[buf], d.U);
 }
 
 void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {
@@ -545,12 +626,13 @@ void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {
 void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
                    double* out, cudaStream_t s, int at_x) {
     if (n <= 0) return;
-    k_S_list<<<blocks(n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out, at_x);
+    const int bs = spread_bs(n, 128);
+    k_S_list<<<blocks(n, bs), bs, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out, at_x);
 }
 
 void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s) {
     const int64_t threads = g.n_x * (int64_t)g.n_refine;
-    const int bs = 256;
+    const int bs = spread_bs(threads, 256);   // a multiple of the group size (<= 32)
 #define UCP_SEARCH_CASE(G)                                                    \
     case G:                                                                   \
         k_search_plain<G><<<blocks(threads, bs), bs, 0, s>>>(                 \
@@ -570,7 +652,7 @@ void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s)
 
 void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
                     cudaStream_t s) {
-    k_J_plain<<<1, 32, 0, s>>>(g, d.px, d.nu[buf], d.Sf, d.J + slot);
+    k_J_plain<<<1, 256, 0, s>>>(g, d.px, d.nu[buf], d.Sf, d.J + slot);
 }
 
 void launch_f_values(const Geom& g, const int64_t* nu, const double*,
