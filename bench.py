@@ -288,13 +288,18 @@ def batched_work(ps, b, binding, sweeps):
             "mmse_main": (tot["mmse_main"], "fp32")}
 
 
-def measure_batched(args, binding, torch, stream, flush):
+def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
     """c3: 256 uneven instances solved (setup + 10 sweeps + J) as one batch,
     one at a time on the same fast path, and one at a time on the plain FP64
-    path (a sample, extrapolated by grid work)."""
+    path (a sample, extrapolated by grid work).  Under torchrun the instances
+    are partitioned over the ranks by estimated work (no collective on the
+    data path); each rank solves its part as one batch, the time is the
+    slowest rank's, and only the one-GPU comparisons are skipped."""
     from paper_1908_04489_gb300 import workloads as W
-    ps = W.c3()
-    n = len(ps)
+    ps_all = W.c3()
+    n = len(ps_all)
+    parts = W.partition(ps_all, world)
+    ps = [ps_all[k] for k in parts[rank]]
 
     def batch_solve():
         b = binding.Batch(ps, stream=stream)
@@ -306,15 +311,27 @@ def measure_batched(args, binding, torch, stream, flush):
     times = []
     for _ in range(max(1, args.batch_steps)):
         flush.fill_(1)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         b = batch_solve()
         e1.record(stream)
         e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        times.append(max_over_ranks(e0.elapsed_time(e1), world, "cuda"))
         Jb = b.eval_J()
         b.close()
     t_batch = float(np.median(times)) / 1e3
+    if world > 1:
+        est = [sum(W.work_estimate(ps_all[k]) for k in part) for part in parts]
+        return {
+            "workload": "c3: 256 Witsenhausen instances (seed 1908) partitioned over "
+                        f"{world} GPUs by estimated work, one batch per GPU, 10 sweeps",
+            "solves_per_s": n / t_batch, "ms_per_batch": t_batch * 1e3,
+            "scaling": "strong", "instances_per_rank": [len(q) for q in parts],
+            "work_estimate_imbalance": max(est) / (sum(est) / world),
+        }
     # one more batch, untimed, with per-kernel CUDA events around each kernel
     # group of the 10 batched sweeps (kernel by kernel, no graph replay)
     flush.fill_(1)
@@ -618,8 +635,8 @@ def run_gpu(args):
                 "per_kernel": per_kernel}
 
     batched = None
-    if rank == 0 and not args.no_batched:
-        batched = measure_batched(args, binding, torch, stream, flush)
+    if not args.no_batched:   # every rank: the instances are partitioned
+        batched = measure_batched(args, binding, torch, stream, flush, world, rank)
     source_channel = None
     if rank == 0 and not args.no_batched:
         source_channel = measure_source_channel(args, binding, torch, stream, flush)

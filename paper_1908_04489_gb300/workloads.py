@@ -94,6 +94,32 @@ def source_channel(precision: int = 0, **kw):
     return p
 
 
+def work_estimate(p) -> float:
+    """Relative cost of one solve of instance p on the fast path, from its
+    grid sizes alone: the search and the box step grow with the x0 points,
+    the u1 sums with the y points, the correlation tables with both times the
+    taps (used to balance instances across GPUs)."""
+    d = p["delta"]
+    n_x = 2 * round(p["x_half"] / d) + 1
+    n_w = 2 * round(p["w_half"] / d) + 1
+    n_y = 2 * round(p["y_half"] / d) + 1
+    return float(p.get("sweeps", 1)) * (n_x + n_y + (n_x + n_y) * n_w / 256.0)
+
+
+def partition(ps, parts: int):
+    """Split instances over `parts` GPUs by estimated work: longest first to
+    the least loaded part (ties to the lower part and the lower index), each
+    part's indices in increasing order.  Deterministic."""
+    order = sorted(range(len(ps)), key=lambda k: (-work_estimate(ps[k]), k))
+    load = [0.0] * parts
+    out = [[] for _ in range(parts)]
+    for k in order:
+        r = min(range(parts), key=lambda q: (load[q], q))
+        out[r].append(k)
+        load[r] += work_estimate(ps[k])
+    return [sorted(o) for o in out]
+
+
 def c3(n: int = 256, seed: int = 1908, precision: int = 1):
     """Batched: n instances, seed 1908 stream 0, delta in {0.01, 0.02},
     identity init, 10 sweeps."""

@@ -80,3 +80,20 @@ def test_product_path_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(binding, "lib_path", lambda: "/nonexistent/libucp.so")
     with pytest.raises(RuntimeError, match="not built"):
         binding.load()
+
+
+def test_instances_are_partitioned_by_work_for_several_gpus():
+    """The batched workload's split over GPUs: every instance on exactly one
+    rank, deterministic, and no rank above the ideal share by more than the
+    largest instance (longest-first greedy)."""
+    sys.path.insert(0, ROOT)
+    from paper_1908_04489_gb300 import workloads as W
+    ps = W.c3()
+    est = [W.work_estimate(p) for p in ps]
+    for world in (1, 2, 3, 8):
+        parts = W.partition(ps, world)
+        assert sorted(k for part in parts for k in part) == list(range(len(ps)))
+        assert parts == W.partition(ps, world)
+        load = [sum(est[k] for k in part) for part in parts]
+        assert max(load) <= sum(est) / world + max(est) + 1e-9
+        assert all(part == sorted(part) for part in parts)
