@@ -141,18 +141,6 @@ __device__ __forceinline__ bool before(double ga, int32_t pa, double gb,
     return ga < gb || (ga == gb && pa < pb);
 }
 
-template <int G>
-__device__ __forceinline__ void group_argmin(double& gv, int32_t& pos,
-                                             int64_t& nu) {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-        const double go = __shfl_xor_sync(0xffffffffu, gv, off, G);
-        const int32_t po = __shfl_xor_sync(0xffffffffu, pos, off, G);
-        const int64_t no = __shfl_xor_sync(0xffffffffu, nu, off, G);
-        if (before(go, po, gv, pos)) { gv = go; pos = po; nu = no; }
-    }
-}
-
 // ---- setup ------------------------------------------------------------
 
 // Normalised prior weights p_i and quadrature weights phi_l: the
@@ -445,29 +433,135 @@ __global__ void k_S_list(Geom g, const double* __restrict__ phi,
     out[k] = at_x ? quad_plain(g, phi, U, Ud, nus[k], k) : S_plain(g, phi, U, Ud, nus[k]);
 }
 
-// ---- u0 step: candidate search, one group of n_refine lanes per x_i ----
-template <int G>
+// ---- u0 step: candidate search, one warp per x_i ------------------------
+
+// The quadrature of candidate nu at x0 point i over the C sub-lanes of a
+// candidate slot (consecutive lanes from slot_base; every lane of the warp
+// calls this): sub-lane s forms the 32-term chunk sums k = s, s + C, ...,
+// and every sub-lane merges all chunk sums in chunk order through the
+// fixed-order stack of fixed_sum.cuh -- the sum S_plain / Q_plain form, bit
+// for bit (the same term operations: clamped positions use the end values of
+// U, interior ones the interpolant), with C independent chains on the FP64
+// pipe.
+template <int C>
+__device__ double quad_split(const Geom& g, const double* __restrict__ phi,
+                             const double* __restrict__ U, const double* __restrict__ Ud,
+                             int64_t nu, int64_t i, int sub, int slot_base) {
+    const int64_t cell = nu >> g.shift;
+    const double t = __dmul_rn((double)(nu - (cell << g.shift)), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy;
+    const double u = value_of(g, nu);
+    const double x = x_of(g, i);
+    const int64_t ny1 = g.n_y - 1;
+    const bool sc = g.problem == 1;
+    // residuals at the clamped ends
+    const double hL = __dadd_rn(U[0], __dmul_rn(t, 0.0));
+    const double hR = __dadd_rn(U[ny1], __dmul_rn(t, 0.0));
+    const double eL = sc ? __dsub_rn(hL, x) : __dsub_rn(u, hL);
+    const double eR = sc ? __dsub_rn(hR, x) : __dsub_rn(u, hR);
+    const double eL2 = __dmul_rn(eL, eL), eR2 = __dmul_rn(eR, eR);
+    const int64_t nch = sum_chunks(g.n_w);
+    FixedSum acc;
+    for (int64_t k0 = 0; k0 < nch; k0 += C) {
+        const int64_t k = k0 + sub;
+        double cs = 0.0;
+        if (k < nch) {
+            const int64_t b = k * kSumChunk, e = min(b + kSumChunk, g.n_w);
+            const int64_t lL = min(e, max(b, -jb));        // j < 0 below lL
+            const int64_t lI = min(e, max(lL, ny1 - jb));  // interior below lI
+            int64_t l = b;
+            for (; l < lL; ++l) cs = __dadd_rn(cs, __dmul_rn(phi[l], eL2));
+            if (sc) {
+                for (; l + 8 <= lI; l += 8) {
+                    double tm[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int64_t j = jb + l + q;
+                        const double d = __dsub_rn(__dadd_rn(U[j], __dmul_rn(t, Ud[j])), x);
+                        tm[q] = __dmul_rn(phi[l + q], __dmul_rn(d, d));
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cs = __dadd_rn(cs, tm[q]);
+                }
+                for (; l < lI; ++l) {
+                    const int64_t j = jb + l;
+                    const double d = __dsub_rn(__dadd_rn(U[j], __dmul_rn(t, Ud[j])), x);
+                    cs = __dadd_rn(cs, __dmul_rn(phi[l], __dmul_rn(d, d)));
+                }
+            } else {
+                for (; l + 8 <= lI; l += 8) {
+                    double tm[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int64_t j = jb + l + q;
+                        const double d = __dsub_rn(u, __dadd_rn(U[j], __dmul_rn(t, Ud[j])));
+                        tm[q] = __dmul_rn(phi[l + q], __dmul_rn(d, d));
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cs = __dadd_rn(cs, tm[q]);
+                }
+                for (; l < lI; ++l) {
+                    const int64_t j = jb + l;
+                    const double d = __dsub_rn(u, __dadd_rn(U[j], __dmul_rn(t, Ud[j])));
+                    cs = __dadd_rn(cs, __dmul_rn(phi[l], __dmul_rn(d, d)));
+                }
+            }
+            for (; l < e; ++l) cs = __dadd_rn(cs, __dmul_rn(phi[l], eR2));
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < C; ++s2) {
+            const double v = __shfl_sync(0xffffffffu, cs, slot_base + s2);
+            if (k0 + s2 < nch) acc.push_chunk(v);
+        }
+    }
+    return acc.result();
+}
+
+// First minimum over the candidate slots of an x0 point's P lanes (aligned
+// groups within the warp; the C sub-lanes of a slot hold the same values).
+template <int C, int P>
+__device__ __forceinline__ void slot_argmin(double& gv, int32_t& pos, int64_t& nu) {
+#pragma unroll
+    for (int off = P / 2; off >= C; off >>= 1) {
+        const double go = __shfl_xor_sync(0xffffffffu, gv, off);
+        const int32_t po = __shfl_xor_sync(0xffffffffu, pos, off);
+        const int64_t no = __shfl_xor_sync(0xffffffffu, nu, off);
+        if (before(go, po, gv, pos)) { gv = go; pos = po; nu = no; }
+    }
+}
+
+// P = G C lanes per x_i: G = n_refine candidate slots of C lanes each (C = 1
+// on grids that fill the GPU; C = 32 / G, one warp per x_i, on small ones,
+// whose FP64 pipes would otherwise idle).  Stage 0 (incumbent, neighbours,
+// coarse) takes the slots in rounds, each refinement level one candidate per
+// slot; the first minimum in list order wins.  Problem 0 reads the
+// precomputed S of the incumbents, neighbours and coarse values; problem 1's
+// estimation error depends on x_i and is formed here for every candidate.
+template <int G, int C>
 __global__ void __launch_bounds__(256) k_search_plain(
     Geom g, const double* __restrict__ phi, const double* __restrict__ U,
     const double* __restrict__ Ud, const int64_t* __restrict__ nu_pre,
     const double* __restrict__ Sf, const double* __restrict__ Sc,
     const int64_t* __restrict__ coarse, int64_t* __restrict__ nu_out,
     int32_t* __restrict__ idx_out) {
-    const int lane = threadIdx.x & (G - 1);
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    constexpr int P = G * C;
+    const int lane = threadIdx.x & 31;
+    const int lp = lane % P;
+    const int slot = lp / C, sub = lp % C, slot_base = lane - sub;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / P;
     const bool active = i < g.n_x;
     const int64_t ic = active ? i : g.n_x - 1;
 
     double best_g = DBL_MAX;
     int32_t best_p = INT_MAX;
     int64_t best_nu = 0;
-    // stage 0: incumbent, neighbours, coarse (their S is precomputed)
     const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
-    for (int p = lane; p < n0; p += G) {
-        int64_t nu;
-        double S;
-        if (p == 0) {
-            nu = nu_pre[ic];
+    for (int pb = 0; pb < n0; pb += G) {   // the same rounds for every slot
+        const int p = pb + slot;
+        const bool valid = p < n0;
+        int64_t nu = nu_pre[ic];
+        double S = 0.0;
+        if (!valid || p == 0) {
             S = Sf[ic];
         } else if (p <= 2 * g.n_nbr) {
             const int d = p <= g.n_nbr ? p - g.n_nbr - 1 : p - g.n_nbr;
@@ -480,31 +574,30 @@ __global__ void __launch_bounds__(256) k_search_plain(
             nu = coarse[c];
             S = g.problem == 1 ? 0.0 : Sc[c];
         }
-        // problem 1: the estimation error depends on x_i, so only the
-        // incumbent's comes precomputed
-        if (g.problem == 1 && p != 0) S = Q_plain(g, phi, U, Ud, nu, x_of(g, ic));
+        if (g.problem == 1) S = quad_split<C>(g, phi, U, Ud, nu, ic, sub, slot_base);
         const double gv = cost_from_S(g, ic, nu, S);
-        if (before(gv, p, best_g, best_p)) { best_g = gv; best_p = p; best_nu = nu; }
+        if (valid && before(gv, p, best_g, best_p)) { best_g = gv; best_p = p; best_nu = nu; }
     }
-    group_argmin<G>(best_g, best_p, best_nu);
+    slot_argmin<C, P>(best_g, best_p, best_nu);
 
     // refinement levels around the best so far
     const int half = G / 2;
-    const int64_t m = lane < half ? lane - half : lane - half + 1;
+    const int64_t m = slot < half ? slot - half : slot - half + 1;
     int pos = n0;
     for (int lv = 1; lv <= g.n_levels; ++lv) {
         const int64_t h = g.q << (g.bits * (g.n_levels - lv));
         const int64_t nu = best_nu + m * h;
-        const double gv = cost_from_S(g, ic, nu, quad_plain(g, phi, U, Ud, nu, ic));
+        const double gv = cost_from_S(g, ic, nu,
+                                      quad_split<C>(g, phi, U, Ud, nu, ic, sub, slot_base));
         double cg = best_g;
         int32_t cp = best_p;
         int64_t cn = best_nu;
-        if (before(gv, pos + lane, cg, cp)) { cg = gv; cp = pos + lane; cn = nu; }
-        group_argmin<G>(cg, cp, cn);
+        if (before(gv, pos + slot, cg, cp)) { cg = gv; cp = pos + slot; cn = nu; }
+        slot_argmin<C, P>(cg, cp, cn);
         best_g = cg; best_p = cp; best_nu = cn;
         pos += G;
     }
-    if (active && lane == 0) {
+    if (active && lp == 0) {   // the first lane of the point's group
         nu_out[i] = best_nu;
         idx_out[i] = best_p;
     }
@@ -631,14 +724,23 @@ void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
 }
 
 void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s) {
-    const int64_t threads = g.n_x * (int64_t)g.n_refine;
-    const int bs = spread_bs(threads, 256);   // a multiple of the group size (<= 32)
-#define UCP_SEARCH_CASE(G)                                                    \
-    case G:                                                                   \
-        k_search_plain<G><<<blocks(threads, bs), bs, 0, s>>>(                 \
-            g, d.phi, d.U, d.Ud, d.nu[buf_in], d.Sf, d.Sc, d.coarse,          \
-            d.nu[buf_in ^ 1], d.idx);                                         \
-        break;
+    // one warp per x0 point (split quadratures) when that still leaves at
+    // most 16 warps per SM, else n_refine lanes per point
+    const bool split = g.n_x <= 16 * (int64_t)sm_count();
+#define UCP_SEARCH_CASE(G)                                                        \
+    case G: {                                                                     \
+        const int64_t threads = g.n_x * (int64_t)(split ? 32 : G);                \
+        const int bs = spread_bs(threads, 256);                                   \
+        if (split)                                                                \
+            k_search_plain<G, 32 / G><<<blocks(threads, bs), bs, 0, s>>>(         \
+                g, d.phi, d.U, d.Ud, d.nu[buf_in], d.Sf, d.Sc, d.coarse,          \
+                d.nu[buf_in ^ 1], d.idx);                                         \
+        else                                                                      \
+            k_search_plain<G, 1><<<blocks(threads, bs), bs, 0, s>>>(              \
+                g, d.phi, d.U, d.Ud, d.nu[buf_in], d.Sf, d.Sc, d.coarse,          \
+                d.nu[buf_in ^ 1], d.idx);                                         \
+        break;                                                                    \
+    }
     switch (g.n_refine) {
         UCP_SEARCH_CASE(2)
         UCP_SEARCH_CASE(4)

@@ -60,6 +60,22 @@ def test_lockstep_c1(binding, precision, init):
     lockstep(binding, p, nu, o.mmse(nu), sweeps=3)
 
 
+def test_lockstep_plain_path_on_a_grid_that_fills_the_gpu(binding):
+    """The plain search takes n_refine lanes per x0 point on grids of more
+    than 16 warps per SM (small grids get a warp per point with the
+    quadrature split over it); 5001 x0 points take the former."""
+    import os
+    p = dict(W.c1(), delta=0.01, precision=0)
+    o = oracle.Oracle(p)
+    assert o.n_x == 5001
+    nu = o.init(0)
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        lockstep(binding, p, nu, o.mmse(nu), sweeps=1)
+    finally:
+        oracle.set_threads(1)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_trajectory_c1(binding, precision):
     """Independent 10-sweep solves of config c1 (identity init)."""
