@@ -24,6 +24,10 @@
  *      marginal cost C_1 (one Newton step of Section III-D; the closed form
  *      of Section IV-C).
  *   3. J <- sum_i p_i g(f_i; x_i) in FP64.
+ * The same sweep solves zero-delay source-channel coding (Section V-B) when
+ * ucp_params.problem = 1: f is u0 itself, g(u; x_i) = k^2 u^2 +
+ * sum_l phi_l (U^(u + w_l) - x_i)^2 with equal weights phi_l, and the u1 step
+ * is U_j <- E[x0 | x1 = y_j] under uniform noise (plain FP64 path).
  *
  * Conventions for every call:
  *   - Return value: a ucp_status.  No call aborts, traps or exits.  After
@@ -136,7 +140,8 @@ UCP_API ucp_status ucp_ctx_destroy(ucp_ctx* ctx);
 /* ---- one instance ---------------------------------------------------- */
 
 /* Validate params, build the grids and weights on the device, set f from
- * the init, then U <- E[x1 | y1] and J.  Work is enqueued on `stream`. */
+ * the init, then U <- E[x1 | y1] (problem 1: E[x0 | x1]) and J.  Work is
+ * enqueued on `stream`. */
 UCP_API ucp_status ucp_create(ucp_ctx* ctx, const ucp_params* params, void* stream,
                       ucp_inst** out);
 /* Grid sizes, candidate-list length and device bytes held. */
@@ -151,14 +156,16 @@ UCP_API ucp_status ucp_eval_J(ucp_inst* inst, double* J_out);
 UCP_API ucp_status ucp_J_history(ucp_inst* inst, double* out, uint64_t n,
                          uint64_t* n_written);
 /* Synchronise and copy the controllers to host buffers (any may be NULL):
- * f (n_x; u0 = f - x0 if as_paper_u0), U (n_y), idx = list position of the
+ * f (n_x; u0 = f - x0 if as_paper_u0; problem 1 carries u0 itself, so f is
+ * returned as is), U (n_y), idx = list position of the
  * winner of every x_i in the last sweep (n_x, -1 before the first sweep). */
 UCP_API ucp_status ucp_get_controllers(ucp_inst* inst, double* f, uint64_t n_x,
                                double* u1, uint64_t n_y, int32_t as_paper_u0,
                                int32_t* idx);
 /* Replace the state from host buffers: f (n_x values, rounded to the lattice
  * delta 2^-(n_levels log2(n_refine/2)) that all candidates lie on); U (n_y)
- * or NULL to recompute U <- E[x1 | y1].  J is recomputed.  Resume from a
+ * or NULL to recompute U (the u1 step of the instance's problem).  J is
+ * recomputed.  Resume from a
  * checkpoint = ucp_get_controllers + ucp_set_controllers. */
 UCP_API ucp_status ucp_set_controllers(ucp_inst* inst, const double* f, uint64_t n_x,
                                const double* u1, uint64_t n_y);
