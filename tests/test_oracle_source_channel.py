@@ -84,6 +84,49 @@ def test_J_without_transmission_is_the_prior_variance():
         assert abs(o.J(nu, o.mmse(nu)) - s * s) < 1e-9
 
 
+@pytest.mark.parametrize("a", [0.6, 1.0, 1.7])
+def test_search_with_a_linear_u1_finds_the_continuous_minimiser(a):
+    """U = a y (inside the grid): with symmetric equal weights,
+    g(u; x) = k^2 u^2 + a^2 (u^2 + E w^2) - 2 a x u + x^2, minimised at
+    u* = a x / (k^2 + a^2); the search lands within the finest step of it."""
+    p = sc(y_half=9.0, cand_half=6.0)
+    o = oracle.Oracle(p)
+    g = o.grids()
+    U = a * g["y"]
+    nu0 = o.init(0)
+    sel = np.arange(100, 401, 25)
+    out, _ = o.search(nu0, U, sel[0], sel[-1] + 1)
+    k2 = p["k"] ** 2
+    q = 2 * -(-round(p["cand_half"] / p["delta"]) // (p["n_coarse"] - 1))
+    h_fine = q * p["delta"] / (p["n_refine"] // 2) ** p["n_levels"]
+    for i in sel:
+        u_star = a * g["x"][i] / (k2 + a * a)
+        assert abs(o.value(out[i]) - u_star) <= h_fine / 2 + 1e-12, (i, o.value(out[i]), u_star)
+
+
+@pytest.mark.parametrize("c,a", [(0.5, 0.8), (1.2, 0.3)])
+def test_J_closed_form_for_linear_controllers(c, a):
+    """f = c x0 and U = a y (inside the grid): J = sum_i p_i [k^2 f_i^2 +
+    a^2 (f_i^2 + E w^2) - 2 a f_i x_i + x_i^2] = (k^2 c^2 + a^2 c^2 - 2 a c + 1) s2
+    + a^2 E w^2, with s2 = sigma^2 (wide x grid) and E w^2 the second moment of
+    the equal-weight w grid, delta^2 hw (hw + 1) / 3."""
+    p = sc(x_half=8.0, y_half=20.0, cand_half=6.0)
+    o = oracle.Oracle(p)
+    g = o.grids()
+    nu = o.init(2, c * g["x"])
+    U = a * g["y"]
+    hw = round(p["w_half"] / p["delta"])
+    ew2 = p["delta"] ** 2 * hw * (hw + 1) / 3.0
+    k2 = p["k"] ** 2
+    fx = o.value(nu)                      # c x0 rounded to the candidate lattice
+    s_ff = float(np.sum(g["px"] * fx * fx)); s_fx = float(np.sum(g["px"] * fx * g["x"]))
+    ref = k2 * s_ff + a * a * (s_ff + ew2) - 2 * a * s_fx + 1.0
+    assert abs(o.J(nu, U) - ref) < 1e-10
+    # and against the exact moments of the continuous prior (lattice rounding of f)
+    cont = (k2 * c * c + a * a * c * c - 2 * a * c + 1.0) + a * a * ew2
+    assert abs(o.J(nu, U) - cont) < 1e-3
+
+
 def test_cost_against_library_interpolation():
     o = oracle.Oracle(sc())
     g = o.grids()
