@@ -138,6 +138,19 @@ def test_table_init_and_u0_output(binding, precision):
         assert abs(inst.eval_J() - o.J(nu, o.mmse(nu))) <= TOL_J
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_staircase_start_equals_the_oracle(binding, precision):
+    """The odd staircase start of the c2 workload, set up by the GPU
+    (init_kind 1), equals the oracle's start value for value before any
+    sweep, at full c2 size (10001 x0 points)."""
+    p = W.c2(precision=precision)
+    o = oracle.Oracle(p)
+    with binding.Instance(p) as inst:
+        got = inst.get_controllers()
+    np.testing.assert_array_equal(got["f"], o.value(o.init(1)))
+    assert np.all(got["idx"] == -1)
+
+
 def test_full_size_c2_sampled(binding):
     """Config c2 at full size (10001 / 2401 / 14001 points), as the bench runs
     it: after two sweeps, a sampled subset of x_i and y_j is recomputed by the

@@ -26,6 +26,12 @@ MUTANTS = {
         "int64_t h = g->q * ((int64_t)1 << (bits * (p->n_levels - lv)));",
         "int64_t h = g->q * ((int64_t)1 << (bits * (p->n_levels - lv + 1)));"),
     "J without prior weights": ("J = J + px[i] * terms[i];", "J = J + terms[i];"),
+    "staircase steps 3.5 wide": ("if (half_steps(7.0, p->delta, &n7) || n7 < 1) return -1;",
+                                 "if (half_steps(3.5, p->delta, &n7) || n7 < 1) return -1;"),
+    "staircase levels 3.5 (m + 1)": (
+        "double v = 3.5 * (double)(2 * m + 1) / p->delta * (double)g.one;",
+        "double v = 3.5 * (double)(m + 1) / p->delta * (double)g.one;"),
+    "staircase without its cap": ("if (m > 2) m = 2;", ""),
 }
 
 
@@ -79,6 +85,16 @@ def pin_failures(L):
         ref = 0.09 * (u - gs["x"][i]) ** 2 + np_S(s, Us, u)
         if abs(s.cost(Us, i, nu) - ref) > 1e-10 * max(1.0, ref):
             bad.append("cost vs library interpolation")
+            break
+    # the odd staircase start: levels +-3.5, +-10.5, +-17.5 with jumps at 7, 14
+    c1 = oracle.Oracle(W.c1(), library=L)
+    fs = c1.value(c1.init(1))
+    hx = (c1.n_x - 1) // 2
+    for xv, level in ((0.0, 0.0), (6.95, 3.5), (7.0, 10.5), (13.95, 10.5), (14.0, 17.5),
+                      (25.0, 17.5)):
+        i = hx + int(round(xv / 0.05))
+        if abs(fs[i] - level) > 1e-12 or abs(fs[2 * hx - i] + level) > 1e-12:
+            bad.append("staircase start")
             break
     rng = np.random.default_rng(3)
     nu_pre = s.init(2, gs["x"] + rng.normal(0, 0.5, s.n_x))

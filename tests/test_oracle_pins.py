@@ -276,3 +276,39 @@ def test_paper_converged_value_band():
     oracle.set_threads(1)
     assert abs(r["J"][-1] - ref) < 0.006
     assert r["J"][-1] < r["J"][1]
+
+
+def staircase_level(x_units, delta):
+    """The odd three-step staircase start, f(x) = 3.5 sgn(x) (2 min(floor(|x|/7),
+    2) + 1) with f(0) = 0, evaluated in exact rational arithmetic at
+    x = x_units * delta (so that floor(|x|/7) is not at the mercy of a rounded
+    quotient at the jumps)."""
+    from fractions import Fraction
+    x = Fraction(int(x_units)) * Fraction(repr(delta))
+    if x == 0:
+        return 0.0
+    m = min(int(abs(x) / 7), 2)
+    return float((1 if x > 0 else -1) * Fraction(7, 2) * (2 * m + 1))
+
+
+@pytest.mark.parametrize("delta", [0.05, 0.005])
+def test_staircase_start_values(delta):
+    """The odd staircase start (the garbled "3.5 sign-rounded(x0/7)" read as
+    three steps per side: levels +-3.5, +-10.5, +-17.5, jumps at |x0| = 7 and
+    14, f(0) = 0): the oracle's lattice values equal the formula at every x0
+    point, and at the named points on both sides of each jump."""
+    p = W.base(delta=delta)
+    o = oracle.Oracle(p)
+    f = o.value(o.init(1))
+    hx = (o.n_x - 1) // 2
+    ref = np.array([staircase_level(i - hx, delta) for i in range(o.n_x)])
+    assert np.max(np.abs(f - ref)) <= 1e-12
+    named = {0.0: 0.0, 7.0 - delta: 3.5, 7.0: 10.5, 14.0 - delta: 10.5, 14.0: 17.5,
+             25.0: 17.5}
+    for xv, level in named.items():
+        for sgn in (1, -1):
+            i = hx + sgn * int(round(xv / delta))
+            assert abs(f[i] - sgn * level) <= 1e-12, (xv, sgn, f[i])
+    # odd, three levels per side
+    assert np.array_equal(f, -f[::-1])
+    assert sorted(set(np.round(f, 9))) == [-17.5, -10.5, -3.5, 0.0, 3.5, 10.5, 17.5]

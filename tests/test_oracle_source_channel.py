@@ -76,6 +76,37 @@ def test_u1_uses_the_nearest_sources_beyond_the_window():
     assert np.max(np.abs(U)) < 1e-15
 
 
+def three_level(o):
+    """f = 3 for x0 > 0, -5 for x0 < 0, 0.5 at x0 = 0 (lattice values), and
+    the prior-weighted means of x0 over each side."""
+    g = o.grids()
+    x = g["x"]
+    f = np.where(x > 0, 3.0, np.where(x < 0, -5.0, 0.5))
+    nu = o.init(2, f)
+    wgt = np.exp(-x * x / (2 * o.params["sigma"] ** 2))
+    pos, neg = x > 0, x < 0
+    return nu, np.sum(wgt[pos] * x[pos]) / np.sum(wgt[pos]), \
+        np.sum(wgt[neg] * x[neg]) / np.sum(wgt[neg])
+
+
+@pytest.mark.parametrize("yv,which", [(6.5, "pos"), (4.5, "pos"), (2.2, "pos"),
+                                      (1.6, "zero"), (-7.0, "neg"), (-4.2, "neg")])
+def test_u1_takes_the_nearest_group_of_sources(yv, which):
+    """Section V-B's likelihood is flat on |y - f(x0)| <= W.  With three
+    groups of sources (f = 3 on x0 > 0, f = -5 on x0 < 0, f = 0.5 at x0 = 0)
+    and W = 1: y = 2.2 and -4.2 see one group inside the window; y = 6.5, 4.5
+    and -7 see none and take the nearest group (the limit of a slightly
+    wider window); y = 1.6 is 1.1 from the lone source at x0 = 0 and 1.4 from
+    the f = 3 group, so U = 0 there, where averaging all groups, or widening
+    the window by W, would not give 0."""
+    o = oracle.Oracle(sc())
+    nu, mpos, mneg = three_level(o)
+    j = int(round(yv / o.params["delta"])) + (o.n_y - 1) // 2
+    got = o.mmse(nu, j, j + 1)[j]
+    ref = {"pos": mpos, "neg": mneg, "zero": 0.0}[which]
+    assert abs(got - ref) <= 1e-13, (yv, got, ref)
+
+
 def test_J_without_transmission_is_the_prior_variance():
     """u0 = 0: u1 = E[x0] = 0 and J = E[x0^2] = sigma^2."""
     for s in (1.0, 1.7):
@@ -180,6 +211,12 @@ MUTANTS = {
     "control on u - x": ("return g->kk * (u * u) + acc;",
                          "return g->kk * ((u - x) * (u - x)) + acc;"),
     "Gaussian weights": ("if (g->p.problem == 1) phi[l] = 1.0;", ""),
+    "no nearest-source fallback": ("double reach = dmin <= W ? W : dmin;",
+                                   "double reach = W;"),
+    "fallback window widened by W": ("double reach = dmin <= W ? W : dmin;",
+                                     "double reach = dmin <= W ? W : dmin + W;"),
+    "fallback takes every source": ("double reach = dmin <= W ? W : dmin;",
+                                    "double reach = dmin <= W ? W : INFINITY;"),
 }
 
 
@@ -192,6 +229,13 @@ def pin_failures(L):
     t = oracle.Oracle(sc(delta=0.001, x_half=5.0, y_half=7.0, cand_half=6.0), library=L)
     if abs(u1_of_linear(t, 0.5, 0.37) - truncated_normal_mean(-1.26, 2.74, 1.0)) > 2e-3:
         bad.append("u1 truncated mean")
+    nu3, mpos, mneg = three_level(o)
+    for yv, ref in ((6.5, mpos), (1.6, 0.0), (-7.0, mneg)):
+        j = int(round(yv / o.params["delta"])) + (o.n_y - 1) // 2
+        got = o.mmse(nu3, j, j + 1)[j]
+        if not abs(got - ref) <= 1e-13:
+            bad.append("nearest sources")
+            break
     Uc = 0.8 * np.tanh(2 * g["y"]) + 0.05 * g["y"]
     for i, nu in [(10, 5 << o.shift), (250, -(13 << o.shift) + 77)]:
         ref = np_cost(o, Uc, i, float(o.value(nu)))
