@@ -142,6 +142,19 @@ def c4(n: int = 20000, rate: float = 1000.0, seed: int = 1908,
     return reqs, times
 
 
+def c4_sample(n_sample: int = 200, n: int = 20000, seed: int = 1908):
+    """Indices of a seeded sample of the c4 request stream (the parameters of
+    c4 do not depend on the arrival rate): ``n_sample`` distinct request
+    numbers in [0, n), drawn by a partial Fisher-Yates shuffle on seed 1908
+    stream 3, returned in increasing order."""
+    rng = SplitMix64(seed, 3)
+    perm = list(range(n))
+    for k in range(n_sample):
+        r = k + min(int(rng.uniform() * (n - k)), n - k - 1)
+        perm[k], perm[r] = perm[r], perm[k]
+    return sorted(perm[:n_sample])
+
+
 def small(**kw):
     """A small instance for unit tests: delta=0.1 and narrow grids."""
     p = base(delta=0.1, x_half=12.0, w_half=4.0, y_half=20.0, cand_half=15.0,
