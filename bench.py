@@ -6,13 +6,22 @@ delta = 0.005 (10001 x0 / 2401 w / 14001 y points), odd 3-step staircase init,
 solve: setup (grids, weights, init, u1, J) + 50 sweeps, every step of the
 path in the library's kernels.
 
-  value  -- solves/s with the instance set up on the device inside the timed
-            region (CUDA events on the instance stream; L2 flushed between
-            steps by a 512 MiB write outside the events).
-  e2e    -- solves/s through the C ABI from host buffers: the initial
-            controller table goes host->device, f and u1 come back, J is read.
-  cpu_baseline / --impl reference -- the FP64 C oracle timed on the host
-            cores on a bounded sample of the same solve, extrapolated.
+  value        -- solves/s with the instance set up on the device inside the
+                  timed region (CUDA events on the instance stream; L2 flushed
+                  between steps by a 512 MiB write outside the events).
+  e2e          -- solves/s through the C ABI from host buffers: the initial
+                  controller table goes host->device, f and u1 come back, J is
+                  read.
+  parity       -- the FP64 C oracle's own whole solve of the same workload
+                  (all host cores) against the GPU's: J after every sweep,
+                  the final controllers.
+  cpu_baseline -- that oracle solve's time (a whole solve, not a sample).
+  --impl reference -- the oracle on the host cores, each step a bounded
+                  sample of one solve (its share of the solve stated).
+  roofline     -- the dominant kernel's algorithmic work (the method's
+                  arithmetic, not the instructions that emulate its precision)
+                  per CUDA-event-timed launch, against the measured peak of
+                  the pipe it runs on; "issued" gives the emulation count.
 
 Under torchrun every rank solves its own copy (independent problems, no
 collective): weak scaling, value = all solves / max-over-ranks time.
@@ -71,32 +80,46 @@ def init_table(p):
     return np.where(a == 0, 0.0, np.sign(a) * 3.5 * (2 * m + 1))
 
 
-# ---- algorithmic work per kernel launch ----------------------------------
-# Correlation tables: bf16 tensor-core products, counted as issued: per table
-# (3), column group (64 columns of 128 positions), tap chunk (128 taps) and
-# slice product (21 of the six 8-bit slices per operand): one M=128 (phases)
-# x N=64 (columns) x K=128 product, 2 flops per multiply-add.
-TC_PRODUCTS = 21
-# The rest runs in double-float on the FP32 pipe; work is counted in FP32
-# flops of its double-float operations (FADD/FMUL 1, FFMA 2):
-#   df_add 11, df_mul 10, product-and-accumulate 18.
-#   mmse_main: per directly summed (source, target): weight-times-f
-#              accumulate 18, weight accumulate 11, recurrence product 10 = 39;
-#              per (source, run) the anchor exponent (40) and exp (90).  Per
-#              Taylor-expanded (box, run): the anchor (130) and per target the
-#              shift of z (11), the recurrence product (10) and two scaled
-#              accumulates (42); per Taylor term 21 in double-float, 2 in FP32.
-#   search:    per (x_i, candidate): one screened evaluation of the cell
-#              quadratic, S = A0 + t (A1 + t A2) (2 df_mul + 2 df_add), the
-#              control term k^2 (u - x)^2 (3 df_mul), their sum and the bound:
-#              104.
+# ---- work per kernel launch -------------------------------------------------
+# Two counts per kernel.  "algorithmic": the method's own arithmetic as this
+# path formulates it, 2 flops per multiply-add:
+#   search  per (x_i, candidate) 19: S(u) from the three correlation tables at
+#           the candidate's position (1 - t, the two P terms, the three Q/R
+#           products and their weights, the sums: 15) plus k^2 (u - x)^2 and
+#           the sum (4);
+#   tables  per (table, position, tap) 2: P, Q and R are three correlations of
+#           n_pos positions over n_w taps;
+#   u1 sums per Taylor term evaluated 2 (one Horner step), per directly summed
+#           (source, target) pair 8 (the weight's exponent, two accumulations)
+#           plus one exp counted apart; the terms come from device counters.
+# "issued": what the precision emulation costs on the pipe it runs on --
+#   tables  bf16 tensor products as issued: 21 products of the six 8-bit
+#           slices per operand, per table, 64-column group and 128-tap chunk,
+#           M = 128 x N = 64 x K = 128;
+#   double-float kernels in FP32 flops of their double-float operations
+#           (FADD/FMUL 1, FFMA 2; df_add 11, df_mul 10, product-accumulate 18):
+#           search 104 per candidate (the screened evaluation and its bound);
+#           u1 per direct pair 39 and per (source, run) 130, per Taylor
+#           (box, run) 130 + 63 per target, per Taylor term 21 (double-float)
+#           or 2 (FP32).
 # The plain FP64 path counts FP64 flops: 6 per quadrature term.
+TC_PRODUCTS = 21
+ALG_SEARCH_CAND = 19.0
+ALG_TABLE_TAP = 2.0
+ALG_U1_TERM = 2.0
+ALG_U1_PAIR = 8.0
 FLOPS_U1_PAIR = 39.0
 FLOPS_U1_ANCHOR = 130.0
 FLOPS_U1_BOX_TARGET = 63.0
 FLOPS_U1_TERM_DF = 21.0
 FLOPS_U1_TERM_F32 = 2.0
 FLOPS_SEARCH_CAND = 104.0
+
+# DRAM bytes per launch from one-kernel ncu captures of the current kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum; cold cache), keyed by the
+# profiled kernel group; None where the kernel changed since its capture.
+TRAFFIC_BYTES = {"c2": {"search": 0.21e6, "tables": 1.70e6, "mmse_main": 0.07e6}}
+TRAFFIC_SOURCE = "profiles/hot_kernels_c2_ncu_full.md"
 
 # kernels launched per timed group of the library's profiler (the groups not
 # listed launch one kernel), and the instance set-up launches of one solve
@@ -105,24 +128,44 @@ FLOPS_SEARCH_CAND = 104.0
 KERNELS_PER_GROUP = {"search": 2}
 SETUP_LAUNCHES = 15
 
+WORK_MODEL = {
+    "search": "19 flops per (x0 point, candidate): S(u) from the three correlation "
+              "tables (15) + k^2 (u - x)^2 and the sum (4)",
+    "tables": "2 flops per (table, position, tap): 3 n_pos n_w multiply-adds",
+    "mmse_main": "2 flops per Taylor term evaluated + 8 per directly summed "
+                 "(source, target) pair, from device counters",
+}
+DTYPE = {
+    1: ("f32x2", "double-float (pairs of FP32, ~48 bits) on the FP32 pipe for the "
+                 "screened search, the u1 sums and J's terms; exact 8-bit integer "
+                 "slices in bf16 on the tensor cores (FP32 accumulation, exact) for "
+                 "the correlation tables; FP64 for near-tie re-costs, the u1 ratio and "
+                 "J's sum; decisions equal the FP64 oracle's"),
+    0: ("f64", "FP64 throughout (plain path)"),
+}
+
 
 def kernel_work(p, sizes, counters, launches):
+    """{kernel group: (algorithmic flops, issued flops, pipe)} per launch."""
     nx, nw, ny = sizes["n_x"], sizes["n_w"], sizes["n_y"]
-    L, R = p["n_levels"], p["n_refine"]
     if p["precision"] == 0:
-        return {"search": (nx * L * R * nw * 6.0, "fp64"),
-                "mmse": (nx * ny * 8.0, "fp64")}
+        q = nx * sizes["n_cand"] * nw * 6.0
+        return {"search": (q, q, "fp64"), "mmse": (nx * ny * 8.0, nx * ny * 8.0, "fp64")}
     run = sizes.get("run", 16)
     per = 1.0 / max(1, launches.get("mmse_main", 1))
+    terms = counters.get("u1_df_terms", 0) + counters.get("u1_f32_terms", 0)
+    u1_alg = (terms * ALG_U1_TERM + counters.get("u1_pairs", 0) * run * ALG_U1_PAIR) * per
     u1 = (counters.get("u1_pairs", 0) * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR) +
           counters.get("u1_boxes", 0) * (run * FLOPS_U1_BOX_TARGET + FLOPS_U1_ANCHOR) +
           counters.get("u1_df_terms", 0) * FLOPS_U1_TERM_DF +
           counters.get("u1_f32_terms", 0) * FLOPS_U1_TERM_F32) * per
     tab = 3 * sizes["tc_ng"] * sizes["tc_nch"] * TC_PRODUCTS * 2.0 * 128 * 64 * 128
+    tab_alg = 3.0 * sizes["n_pos"] * nw * ALG_TABLE_TAP
     return {
-        "tables": (tab, "bf16"),
-        "mmse_main": (u1, "fp32"),
-        "search": (nx * sizes["n_cand"] * FLOPS_SEARCH_CAND, "fp32"),
+        "tables": (tab_alg, tab, "bf16"),
+        "mmse_main": (u1_alg, u1, "fp32"),
+        "search": (nx * sizes["n_cand"] * ALG_SEARCH_CAND,
+                   nx * sizes["n_cand"] * FLOPS_SEARCH_CAND, "fp32"),
     }
 
 
@@ -190,23 +233,37 @@ class Clocks:
 
 # ---- CPU oracle sample ----------------------------------------------------
 
-def oracle_sample(p, budget_s=12.0, threads=None):
+def oracle_sample(p, budget_s=12.0, threads=None, seed=0):
     """Time the oracle on a bounded sample of one solve and extrapolate:
-    strided x_i for the search, strided y_j for the u1 step, full J."""
+    64-point blocks of x_i for the search and, on grids whose u1 step alone
+    would take long, 64-row blocks of y_j for the u1 step, each spread over
+    the grid; one J.  Returns (solves/s, threads, description, seconds
+    spent); seconds * solves/s is the share of one solve the sample did."""
     import oracle
     threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     o = oracle.Oracle(p)
     nu = o.init(p["init_kind"]) if p["init_kind"] != 2 else o.init(2, init_table(p))
-    t0 = time.perf_counter()
-    U = o.mmse(nu)
-    t_mmse_full = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    if o.n_x * o.n_y <= 4e8:
+        t0 = time.perf_counter()
+        U = o.mmse(nu)
+        t_mmse = time.perf_counter() - t0
+        rows = o.n_y
+    else:
+        U = np.interp(np.linspace(-1, 1, o.n_y), [-1, 1], [-1, 1]) * p["y_half"]
+        rows, t_u = 0, 0.0
+        for j0 in rng.permutation(np.arange(0, max(1, o.n_y - 63), 64)):
+            t0 = time.perf_counter()
+            o.mmse(nu, int(j0), int(min(o.n_y, j0 + 64)))
+            t_u += time.perf_counter() - t0
+            rows += int(min(o.n_y, j0 + 64) - j0)
+            if t_u >= budget_s * 0.2:
+                break
+        t_mmse = t_u / rows * o.n_y
     t0 = time.perf_counter()
     o.J(nu, U)
     t_J = time.perf_counter() - t0
-    # search: blocks of 64 consecutive x_i spread over the grid, added until
-    # the budget is used (OpenMP splits each block over the host cores)
-    rng = np.random.default_rng(0)
     starts = rng.permutation(np.arange(0, max(1, o.n_x - 63), 64))
     done_i, t_search = 0, 0.0
     for s0 in starts:
@@ -216,13 +273,46 @@ def oracle_sample(p, budget_s=12.0, threads=None):
         done_i += int(min(o.n_x, s0 + 64) - s0)
         if t_search >= budget_s * 0.7:
             break
-    per_sweep = t_search / done_i * o.n_x + t_mmse_full + t_J
-    solve_s = t_mmse_full + t_J + p["sweeps"] * per_sweep
+    per_sweep = t_search / done_i * o.n_x + t_mmse + t_J
+    solve_s = t_mmse + t_J + p["sweeps"] * per_sweep
     oracle.set_threads(1)
+    spent = t_search + t_J + (t_mmse if rows == o.n_y else t_mmse * rows / o.n_y)
     sample = (f"{done_i} of {o.n_x} x0 searches (64-point blocks spread over "
-              f"the grid) + one full u1 step "
-              f"({o.n_y} y points) + one J, extrapolated to {p['sweeps']} sweeps")
-    return 1.0 / solve_s, threads, sample, t_search + t_mmse_full + t_J
+              f"the grid), {rows} of {o.n_y} u1 rows, one J; extrapolated to "
+              f"set-up + {p['sweeps']} sweeps")
+    return 1.0 / solve_s, threads, sample, spent
+
+
+def oracle_parity(p, inst, args):
+    """The oracle's own whole solve of the workload on every host core
+    (init, u1, then every sweep) against the GPU's solve held by `inst`: J
+    after every sweep, the final controllers.  Its wall time is the CPU
+    baseline (a whole solve, not a sample)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    o = oracle.Oracle(p)
+    t0 = time.perf_counter()
+    r = o.solve(int(p["init_kind"]), int(p["sweeps"]))
+    secs = time.perf_counter() - t0
+    oracle.set_threads(1)
+    Jh = inst.J_history()
+    st = inst.get_controllers()
+    fo = o.value(r["nu"])
+    ndiff = int(np.sum(st["f"] != fo))
+    dJ = float(np.max(np.abs(Jh - r["J"])))
+    dU = float(np.max(np.abs(st["U"] - r["U"])))
+    parity = {"compared": f"the oracle's own solve (set-up + {p['sweeps']} sweeps) "
+                          "against the GPU's: J after every sweep, final f and u1",
+              "max_abs_dJ": dJ, "tol_J": 1e-9, "J": float(Jh[-1]),
+              "J_oracle": float(r["J"][-1]), "final_f_points_differing": ndiff,
+              "controllers_bit_identical": ndiff == 0, "max_abs_dU": dU, "tol_U": 1e-6,
+              "pass": bool(dJ <= 1e-9 and dU <= 1e-6)}
+    cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one whole solve of the workload (set-up + {p['sweeps']} sweeps) "
+                     f"on {cores} host cores, not extrapolated",
+           "seconds": round(secs, 2)}
+    return parity, cpu
 
 
 # ---- multi-rank aggregation -------------------------------------------------
@@ -270,23 +360,46 @@ def fast_sizes(p, binding):
 
 
 def batched_work(ps, b, binding, sweeps):
-    """Algorithmic work of one batched sweep per modelled kernel group,
-    summed over the members (the single-instance model of kernel_work).  The
-    u1 counters cover the set-up's u1 step and the sweeps; they are scaled
-    to one sweep by 1 / (sweeps + 1)."""
-    tot = {"search": 0.0, "tables": 0.0, "mmse_main": 0.0}
+    """Work of one batched sweep per modelled kernel group, summed over the
+    members (the single-instance model of kernel_work).  The u1 counters
+    cover the set-up's u1 step and the sweeps; they are scaled to one sweep
+    by 1 / (sweeps + 1)."""
+    tot = {}
     for p, m in zip(ps, b.members):
         sz = fast_sizes(p, binding)
-        c = m.work_counters()
-        run = sz["run"]
-        tot["search"] += m.n_x * m.n_cand * FLOPS_SEARCH_CAND
-        tot["tables"] += 3 * sz["tc_ng"] * sz["tc_nch"] * TC_PRODUCTS * 2.0 * 128 * 64 * 128
-        tot["mmse_main"] += (c["u1_pairs"] * (run * FLOPS_U1_PAIR + FLOPS_U1_ANCHOR) +
-                             c["u1_boxes"] * (run * FLOPS_U1_BOX_TARGET + FLOPS_U1_ANCHOR) +
-                             c["u1_df_terms"] * FLOPS_U1_TERM_DF +
-                             c["u1_f32_terms"] * FLOPS_U1_TERM_F32) / (sweeps + 1)
-    return {"search": (tot["search"], "fp32"), "tables": (tot["tables"], "bf16"),
-            "mmse_main": (tot["mmse_main"], "fp32")}
+        c = {k: v / (sweeps + 1) for k, v in m.work_counters().items()}
+        for k, (a, i, pp) in kernel_work(p, sz, c, {"mmse_main": 1}).items():
+            ta, ti, _ = tot.get(k, (0.0, 0.0, pp))
+            tot[k] = (ta + a, ti + i, pp)
+    return tot
+
+
+def roofline_entries(work, kern, pipe_peak):
+    """Per modelled kernel group: ms per launch (CUDA events), algorithmic and
+    issued TFLOP/s and their fractions of the pipe's measured peak."""
+    out = {}
+    for k, (alg, iss, pp) in work.items():
+        if k in kern and kern[k][0]:
+            ms_l = kern[k][1] / kern[k][0]
+            pk, bound, _ = pipe_peak[pp]
+            a_, i_ = alg / (ms_l / 1e3) / 1e12, iss / (ms_l / 1e3) / 1e12
+            out[k] = {"bound": bound, "pipe": pp, "ms_per_launch": ms_l,
+                      "algorithmic_tflops": a_, "frac": a_ / pk,
+                      "issued_tflops": i_, "issued_frac": i_ / pk}
+    return out
+
+
+def pipe_peaks(peaks):
+    mp = load_peaks()
+    return {
+        "fp32": (peaks["fp32_tflops"], "alu",
+                 "of measured FP32 FMA throughput (ucp_probe_alu, this run)"),
+        "fp64": (peaks["fp64_tflops"], "alu",
+                 "of measured FP64 FMA throughput (ucp_probe_alu, this run)"),
+        "bf16": (mp.get("bf16_tflops_sustained", 1700.0), "tensor",
+                 "of measured dense bf16 cuBLAS throughput, sustained (MEASURED_PEAKS.json)"
+                 if "bf16_tflops_sustained" in mp else "of fallback dense bf16 1.7 PFLOP/s"),
+    }
 
 
 def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
@@ -342,16 +455,7 @@ def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
     kern = b.kernel_times()
     work = batched_work(ps, b, binding, sweeps=10)
     b.close()
-    mp = load_peaks()
-    peak = {"fp32": binding.probe_alu(stream)["fp32_tflops"],
-            "bf16": mp.get("bf16_tflops_sustained", 1700.0)}
-    per_kernel = {}
-    for k, (w, pp) in work.items():
-        if k in kern and kern[k][0]:
-            ms_l = kern[k][1] / kern[k][0]
-            a_ = w / (ms_l / 1e3) / 1e12
-            per_kernel[k] = {"pipe": pp, "achieved_tflops": a_, "frac": a_ / peak[pp],
-                             "ms_per_launch": ms_l}
+    per_kernel = roofline_entries(work, kern, pipe_peaks(binding.probe_alu(stream)))
     # one at a time, same fast path
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     flush.fill_(1)
@@ -494,10 +598,68 @@ def measure_serving(args, binding, torch):
                     "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)),
                     "max_batch": st["max_active"], "steps": st["steps"]})
+    cap = max(r["solves_per_s"] for r in out)
+    kept = [r["rate_per_s"] for r in out if r["solves_per_s"] >= 0.95 * r["rate_per_s"]]
     return {"workload": "c4: Poisson stream, 20 sweeps per request, delta in "
                         "{0.05,0.01,0.005}, k log-U[0.05,0.5], sigma U[1,10] "
                         f"({args.serve_requests} requests per rate)",
-            "rates": out}
+            "rates": out, "capacity_solves_per_s": cap,
+            "knee_rate_per_s": max(kept) if kept else None,
+            "knee": "the highest offered rate served at >= 95% of the rate"}
+
+
+def measure_c5(args, binding, torch, stream, flush):
+    """c5, the large single instance (k = 0.2, sigma = 10, delta = 0.001:
+    100001 x0 / 14001 w / 120001 y points, 6 levels, identity start, 20
+    sweeps): whole solves timed with CUDA events, the per-kernel roofline of
+    a profiled solve, the oracle on a sample, and J after every sweep against
+    the oracle's stored 20-sweep solve."""
+    from paper_1908_04489_gb300 import workloads as W
+    p = W.c5()
+    sizes = fast_sizes(p, binding)
+    with binding.Instance(p, stream=stream) as inst:
+        inst.sweep(p["sweeps"])
+        inst.eval_J()
+    times, counters = [], dict.fromkeys(binding.Instance.COUNTERS, 0)
+    for _ in range(max(1, args.c5_steps)):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst = binding.Instance(p, stream=stream)
+        inst.sweep(p["sweeps"])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        Jh = inst.J_history()
+        for k, v in inst.work_counters().items():
+            counters[k] += v / max(1, args.c5_steps)
+        inst.close()
+    with binding.Instance(p, stream=stream) as inst:
+        inst.profile(True)
+        inst.sweep(p["sweeps"])
+        kern = {k: list(v) for k, v in inst.kernel_times().items()}
+    work = kernel_work(p, sizes, counters, {k: v[0] for k, v in kern.items()})
+    per_kernel = roofline_entries(work, kern, pipe_peaks(binding.probe_alu(stream)))
+    t = float(np.median(times)) / 1e3
+    out = {"workload": "c5: k=0.2 sigma=10, delta=0.001 (100001 x0 / 14001 w / 120001 y), "
+                       "6 levels, identity init, 20 sweeps",
+           "solves_per_s": 1.0 / t, "ms_per_solve": t * 1e3, "J": float(Jh[-1]),
+           "kernels_ms_per_solve": {k: v[1] for k, v in kern.items()},
+           "roofline_per_kernel": per_kernel,
+           "work_per_solve": counters}
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_c5.json")
+    if os.path.exists(gold):
+        ref = json.load(open(gold))["solve"]["J"]
+        out["parity"] = {"compared": "J after every sweep against the oracle's own "
+                                     "20-sweep solve (stored by the oracle-only script "
+                                     "tests/golden/make_oracle_trajectories.py)",
+                         "max_abs_dJ": float(np.max(np.abs(Jh - np.asarray(ref)))),
+                         "tol_J": 1e-9}
+    if not args.no_cpu:
+        v, cores, sample, spent = oracle_sample(p, 8.0)
+        out["cpu_oracle"] = {"solves_per_s": v, "cores": cores, "sample": sample,
+                             "seconds": round(spent, 2)}
+    return out
 
 
 def run_gpu(args):
@@ -523,12 +685,6 @@ def run_gpu(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     peaks = binding.probe_alu(stream)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sample, spent = oracle_sample(p, args.cpu_budget)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": sample, "seconds": round(spent, 2)}
 
     for _ in range(args.warmup):
         inst = binding.Instance(p, stream=stream)
@@ -574,18 +730,6 @@ def run_gpu(args):
     total_ms = max_over_ranks(float(np.sum(step_ms)), world, "cuda")
     value = whole_job_rate(world, args.steps, total_ms / 1e3)
 
-    parity = None
-    if rank == 0 and not args.no_cpu:
-        import oracle
-        st = last.get_controllers()
-        o = oracle.Oracle(p)
-        oracle.set_threads(os.cpu_count() or 1)
-        Jo = o.J(o.init(2, st["f"]), st["U"])
-        oracle.set_threads(1)
-        parity = {"J": Js[-1], "J_oracle_from_gpu_state": Jo,
-                  "abs_dJ": abs(Js[-1] - Jo), "tol": 1e-9}
-    last.close()
-
     # ---- end-to-end through the C ABI with host buffers
     table = init_table(p)
     pe = dict(p, init_kind=2)
@@ -609,30 +753,19 @@ def run_gpu(args):
     launches = {k: v[0] for k, v in kern.items()}
     work = kernel_work(p, sizes, {k: v / args.steps for k, v in counters.items()},
                        {k: v / args.steps for k, v in launches.items()})
-    mp = load_peaks()
-    pipe_peak = {
-        "fp32": (peaks["fp32_tflops"], "alu", "measured FP32 FMA throughput (ucp_probe_alu, this run)"),
-        "fp64": (peaks["fp64_tflops"], "alu", "measured FP64 FMA throughput (ucp_probe_alu, this run)"),
-        "bf16": (mp.get("bf16_tflops_sustained", 1700.0), "tensor",
-                 "measured dense bf16 cuBLAS throughput, sustained (MEASURED_PEAKS.json)"
-                 if "bf16_tflops_sustained" in mp else "fallback dense bf16 1.7 PFLOP/s"),
-    }
-    per_kernel = {}
-    for k, (w, pp) in work.items():
-        if k in kern:
-            ms_l = kern[k][1] / kern[k][0]
-            a_ = w / (ms_l / 1e3) / 1e12
-            pk, bound, _ = pipe_peak[pp]
-            per_kernel[k] = {"bound": bound, "pipe": pp, "achieved_tflops": a_,
-                             "frac": a_ / pk, "ms_per_launch": ms_l}
-    dom = max((k for k in kern if k in work), key=lambda k: kern[k][1])
-    nl, ms = kern[dom]
-    flops, pipe = work[dom]
-    peak, bound, src = pipe_peak[pipe]
-    achieved = flops / (ms / nl / 1e3) / 1e12
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": src, "share_of_step": ms / total_ms,
+    pp_ = pipe_peaks(peaks)
+    per_kernel = roofline_entries(work, kern, pp_)
+    dom = max(per_kernel, key=lambda k: kern[k][1])
+    d = per_kernel[dom]
+    peak, bound, src = pp_[d["pipe"]]
+    traffic = TRAFFIC_BYTES.get(args.workload, {}).get(dom)
+    roofline = {"bound": bound, "kernel": dom, "achieved": d["algorithmic_tflops"],
+                "peak": peak, "unit": "TFLOP/s", "frac": d["frac"],
+                "traffic": traffic,
+                "traffic_source": TRAFFIC_SOURCE if traffic is not None else None,
+                "work_model": WORK_MODEL.get(dom, ""),
+                "issued": {"achieved": d["issued_tflops"], "frac": d["issued_frac"]},
+                "peak_source": src, "share_of_step": kern[dom][1] / total_ms,
                 "per_kernel": per_kernel}
 
     batched = None
@@ -644,13 +777,22 @@ def run_gpu(args):
     serving = None
     if rank == 0 and not args.no_serving:
         serving = measure_serving(args, binding, torch)
+    large = None
+    if rank == 0 and not args.no_c5 and args.workload != "c5":
+        large = measure_c5(args, binding, torch, stream, flush)
+    # the oracle's own solve last: no host load while the GPU legs run
+    parity, cpu = None, None
+    if rank == 0 and not args.no_cpu:
+        parity, cpu = oracle_parity(p, last, args)
+    last.close()
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[p["precision"]][0],
+        "dtype_detail": DTYPE[p["precision"]][1],
         "data": "synthetic (analytic Witsenhausen instance, Section V-A)",
         "config": {"workload": desc, "precision": p["precision"],
                    "l2": "flushed between steps (512 MiB write outside the events)",
@@ -670,6 +812,8 @@ def run_gpu(args):
         line["source_channel"] = source_channel
     if serving is not None:
         line["serving"] = serving
+    if large is not None:
+        line["large"] = large
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -709,25 +853,34 @@ def run_profile(args):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores, on the workload of the GPU
+    arm.  A whole c2 oracle solve takes tens of seconds, so each step is a
+    bounded sample of one solve (different blocks of x0 points each step);
+    ms_per_step is the sample's measured time and solves_per_step the share
+    of one solve it did, so value = solves done / time taken."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     p, desc = workload(args.workload, args.precision)
-    vals = []
+    secs, shares = [], []
     for s in range(args.warmup + args.steps):
-        v, cores, sample, spent = oracle_sample(p, args.cpu_budget / 2)
+        v, cores, sample, spent = oracle_sample(p, args.ref_step_s, seed=s)
         if s >= args.warmup:
-            vals.append(v)
-    value = float(np.mean(vals))
+            secs.append(spent)
+            shares.append(spent * v)
+    value = float(np.sum(shares) / np.sum(secs))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "solves_per_step": float(np.mean(shares)),
         "config": {"workload": desc, "precision": "oracle FP64"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle",
+                         "sample": "each step: " + sample + " (a share "
+                                   f"{float(np.mean(shares)):.4f} of one solve)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -742,7 +895,8 @@ def main():
     ap.add_argument("--impl", default="ucp", choices=["ucp", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-step-s", type=float, default=1.5,
+                    help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -750,9 +904,11 @@ def main():
                     help="with --workload c3 --profile-sweeps: batch size")
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--c5-steps", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rates", type=float, nargs="+",
-                    default=[100.0, 1000.0, 5000.0])
+                    default=[100.0, 200.0, 500.0, 1000.0, 2000.0, 5000.0])
     ap.add_argument("--serve-slots", type=int, default=512)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--profile-sweeps", type=int, default=0,

@@ -25,6 +25,8 @@
 #include <float.h>
 #include <limits.h>
 
+#include <algorithm>
+
 #include "df.cuh"
 #include "fixed_sum.cuh"
 #include "ucp_fast.cuh"
@@ -92,6 +94,10 @@ constexpr int kTieBatch = 8;   // candidates re-costed exactly per pass
 // the second tier, the members and results of the exact costs, and the
 // block's scratch (the groups' shared columns, free once screening is done).
 constexpr int kCoopT = 256;   // threads per block of the deferred search
+// additions per thread in one level of the exact costs' chunk tree: a level
+// of mb candidates holds at most mb * nch / 2 <= kCoopT * kTieBatch / 2 pairs
+constexpr int kTreeAdds = kTieBatch / 2;
+static_assert(kTreeAdds * 2 == kTieBatch, "tree additions per thread");
 struct CoopSmem {
     double acc[kCoopT / 2][2];
     float emax[kCoopT / 2][2], demax[kCoopT / 2][2];
@@ -116,46 +122,86 @@ __device__ double exact_costs_coop(const Geom& g, const FastView& f, int64_t i,
     const int64_t cap = (int64_t)kCoopT * kTieBatch;
     double* ch = cs->scratch;
     const int per = (int)max((int64_t)1, min((int64_t)M, cap / nch));
+    // chunk k of candidate m: terms 32k .. 32k + 31 added left to right
+    auto chunk = [&](int64_t cnu, int64_t k) {
+        const int64_t cell = cnu >> g.shift;
+        const double t = __dmul_rn((double)(cnu - cell * g.one), inv_one(g));
+        const int64_t jb = cell - g.hw + g.hy;
+        const double u = value_of(g, cnu);
+        const int64_t e = min((k + 1) * kSumChunk, g.n_w);
+        double a = 0.0;
+        int64_t l = k * kSumChunk;
+        // eight terms as independent chains, then added in order
+        for (; l + 8 <= e; l += 8) {
+            double tm[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                tm[q] = exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l + q);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a = __dadd_rn(a, tm[q]);
+        }
+        for (; l < e; ++l) a = __dadd_rn(a, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
+        return a;
+    };
     for (int m0 = 0; m0 < M; m0 += per) {
         const int mb = min(per, M - m0);
-        const int64_t span = cap / mb;   // chunks per pass and candidate
+        if ((int64_t)mb * nch <= cap) {
+            // every chunk sum of the mb candidates in shared memory, then the
+            // fixed pairwise tree level by level, each level's additions in
+            // parallel: entries (2k, 2k + 1) of a level give entry k of the
+            // next, an unpaired last entry moving up unchanged (the order of
+            // fixed_sum.cuh, so the same double)
+            for (int64_t idx = threadIdx.x; idx < mb * nch; idx += blockDim.x) {
+                const int m = (int)(idx / nch);
+                ch[idx] = chunk(cs->mem_nu[m0 + m], idx % nch);
+            }
+            __syncthreads();
+            for (int64_t n = nch; n > 1;) {
+                const int64_t h = n / 2;    // mb * h <= cap / 2 = kTreeAdds * blockDim.x
+                double v[kTreeAdds];
+                int nv = 0;
+                for (int64_t idx = threadIdx.x; idx < mb * h; idx += blockDim.x) {
+                    const int64_t m = idx / h, k = idx % h;
+                    v[nv++] = __dadd_rn(ch[m * nch + 2 * k], ch[m * nch + 2 * k + 1]);
+                }
+                double mv = 0.0;
+                if ((n & 1) && threadIdx.x < (unsigned)mb) mv = ch[threadIdx.x * nch + n - 1];
+                __syncthreads();
+                nv = 0;
+                for (int64_t idx = threadIdx.x; idx < mb * h; idx += blockDim.x) {
+                    const int64_t m = idx / h, k = idx % h;
+                    ch[m * nch + k] = v[nv++];
+                }
+                if ((n & 1) && threadIdx.x < (unsigned)mb) ch[threadIdx.x * nch + h] = mv;
+                __syncthreads();
+                n = h + (n & 1);
+            }
+            if (threadIdx.x < (unsigned)mb) {
+                const int64_t cnu = cs->mem_nu[m0 + threadIdx.x];
+                const double a = __dsub_rn(value_of(g, cnu), x_of(g, i));
+                cs->res[m0 + threadIdx.x] =
+                    __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), ch[threadIdx.x * nch]);
+            }
+            __syncthreads();
+            continue;
+        }
+        // one candidate with more chunks than the scratch holds: chunks in
+        // passes, each pass's sums streamed into the binary-counter stack
+        const int64_t span = cap;
         FixedSum acc;
         for (int64_t c0 = 0; c0 < nch; c0 += span) {
             const int64_t cn = min(span, nch - c0);
-            for (int64_t idx = threadIdx.x; idx < mb * cn; idx += blockDim.x) {
-                const int m = (int)(idx / cn);
-                const int64_t k = c0 + idx % cn;
-                const int64_t cnu = cs->mem_nu[m0 + m];
-                const int64_t cell = cnu >> g.shift;
-                const double t = __dmul_rn((double)(cnu - cell * g.one), inv_one(g));
-                const int64_t jb = cell - g.hw + g.hy;
-                const double u = value_of(g, cnu);
-                const int64_t e = min((k + 1) * kSumChunk, g.n_w);
-                double a = 0.0;
-                int64_t l = k * kSumChunk;
-                // eight terms as independent chains, then added in order
-                for (; l + 8 <= e; l += 8) {
-                    double tm[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        tm[q] = exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l + q);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) a = __dadd_rn(a, tm[q]);
-                }
-                for (; l < e; ++l)
-                    a = __dadd_rn(a, exact_term(g, f.phi, f.U, f.Ud, jb, t, u, l));
-                ch[m * cn + (k - c0)] = a;
-            }
+            for (int64_t idx = threadIdx.x; idx < cn; idx += blockDim.x)
+                ch[idx] = chunk(cs->mem_nu[m0], c0 + idx);
             __syncthreads();
-            if (threadIdx.x < (unsigned)mb)
-                for (int64_t k = 0; k < cn; ++k) acc.push_chunk(ch[threadIdx.x * cn + k]);
+            if (threadIdx.x == 0)
+                for (int64_t k = 0; k < cn; ++k) acc.push_chunk(ch[k]);
             __syncthreads();
         }
-        if (threadIdx.x < (unsigned)mb) {
-            const int64_t cnu = cs->mem_nu[m0 + threadIdx.x];
+        if (threadIdx.x == 0) {
+            const int64_t cnu = cs->mem_nu[m0];
             const double a = __dsub_rn(value_of(g, cnu), x_of(g, i));
-            cs->res[m0 + threadIdx.x] =
-                __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc.result());
+            cs->res[m0] = __dadd_rn(__dmul_rn(g.kk, __dmul_rn(a, a)), acc.result());
         }
     }
     __syncthreads();
@@ -884,9 +930,15 @@ __global__ void __launch_bounds__(kSearchT, 6) k_search_fast(Geom g, FastView f,
     search_body<kFastG>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
 }
 
-constexpr int kDeferBlocks = 64;        // blocks of the deferred search (one instance)
+// Blocks of the deferred search of one instance: one per 128 x0 points
+// (fine grids defer many points at their last levels), at least 64, at most
+// four per SM.
+static unsigned defer_blocks_of(const Geom& g) {
+    const int64_t b = g.n_x / 128;
+    return (unsigned)std::max<int64_t>(64, std::min<int64_t>(b, 4 * (int64_t)sm_count()));
+}
 
-__global__ void __launch_bounds__(kCoopT) k_search_deferred(Geom g, FastView f,
+__global__ void __launch_bounds__(kCoopT, 2) k_search_deferred(Geom g, FastView f,
                                                            const int64_t* __restrict__ nu_pre,
                                                            int64_t* __restrict__ nu_out,
                                                            int32_t* __restrict__ idx_out,
@@ -1024,7 +1076,7 @@ __global__ void __launch_bounds__(kSearchT, 6) kb_search(const InstDev* insts, c
                         sd.f.n_exact, tie_smem, r.local);
 }
 
-__global__ void __launch_bounds__(kCoopT) kb_search_deferred(const InstDev* insts,
+__global__ void __launch_bounds__(kCoopT, 2) kb_search_deferred(const InstDev* insts,
                                                             const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
@@ -1095,7 +1147,8 @@ void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
     const int64_t threads = g.n_x * (int64_t)kFastG;
     k_search_fast<<<blocks(threads, kSearchT), kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx,
                                                                   f.n_exact);
-    k_search_deferred<<<kDeferBlocks, kCoopT, 0, s>>>(g, f, nu_in, nu_out, idx, f.n_exact);
+    k_search_deferred<<<defer_blocks_of(g), kCoopT, 0, s>>>(g, f, nu_in, nu_out, idx,
+                                                            f.n_exact);
 }
 
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {

@@ -628,6 +628,18 @@ __global__ void __launch_bounds__(256) k_J_plain(Geom g, const double* px, const
 
 inline unsigned blocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Threads per block for n threads of FP64-heavy work: the largest power of
+// two up to max_bs that still gives every SM a block (at least 32).  The
+// plain path's throughput is the FP64 pipes', so a small problem in large
+// blocks would leave most SMs' FP64 units idle.
+int spread_bs(int64_t n, int max_bs) {
+    int bs = max_bs;
+    while (bs > 32 && (n + bs - 1) / bs < sm_count()) bs /= 2;
+    return bs;
+}
+
+}  // namespace
+
 // SMs of the current device (cached per device).
 int sm_count() {
     static int cache[64] = {};
@@ -640,18 +652,6 @@ int sm_count() {
     }
     return cache[dev];
 }
-
-// Threads per block for n threads of FP64-heavy work: the largest power of
-// two up to max_bs that still gives every SM a block (at least 32).  The
-// plain path's throughput is the FP64 pipes', so a small problem in large
-// blocks would leave most SMs' FP64 units idle.
-int spread_bs(int64_t n, int max_bs) {
-    int bs = max_bs;
-    while (bs > 32 && (n + bs - 1) / bs < sm_count()) bs /= 2;
-    return bs;
-}
-
-}  // namespace
 
 // ---- launch wrappers ----------------------------------------------------
 

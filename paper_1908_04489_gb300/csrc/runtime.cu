@@ -459,19 +459,29 @@ static void solo_drop(ucp_inst* in) {
     in->solo_tried = false;
 }
 
+// The one-member batch set that the fast path's sweeps launch the u1 step,
+// the tables and J over (built on first use; false if it cannot be).
+static bool solo_ensure(ucp_inst* in) {
+    if (in->solo) return true;
+    if (in->solo_failed) return false;
+    in->solo = new BatchSet();
+    in->solo->arena = &in->arena;
+    std::vector<ucp_inst*> one{in};
+    if (batchset_build(*in->solo, one, in->stream) != UCP_OK) {
+        cudaGetLastError();
+        delete in->solo;
+        in->solo = nullptr;
+        in->solo_failed = true;
+        return false;
+    }
+    return true;
+}
+
 static bool solo_sweeps(ucp_inst* in, int n) {
     if (!in->stream || in->prof.on) return false;
     if (!in->solo_tried) {
         in->solo_tried = true;
-        if (!in->solo) {
-            in->solo = new BatchSet();
-            in->solo->arena = &in->arena;
-            std::vector<ucp_inst*> one{in};
-            if (batchset_build(*in->solo, one, in->stream) != UCP_OK) {
-                cudaGetLastError();
-                return false;
-            }
-        }
+        if (!solo_ensure(in)) return false;
         for (int c = 0; c < 2; ++c) {
             cudaGraph_t graph = nullptr;
             if (cudaStreamBeginCapture(in->stream, cudaStreamCaptureModeThreadLocal) !=
@@ -499,6 +509,24 @@ static bool solo_sweeps(ucp_inst* in, int n) {
     return true;
 }
 
+// The same launches as the graphs, kernel by kernel (default stream, or the
+// profiler on: each kernel group timed by events).
+static bool solo_launches(ucp_inst* in, int n) {
+    if (!solo_ensure(in)) return false;
+    std::vector<ucp_inst*> one{in};
+    if (batchset_refresh(*in->solo, one, in->stream) != UCP_OK) return false;
+    Prof* prof = in->prof.on ? &in->prof : nullptr;
+    for (int k = 0; k < n; ++k) {
+        UCP_LAUNCH(in, "search", launch_search_fast(in->g, in->fv, in->d.nu[in->cur],
+                                                    in->d.nu[in->cur ^ 1], in->d.idx,
+                                                    in->stream));
+        launch_batch_rest(in->solo->bl, in->stream, prof);
+        in->cur ^= 1;
+    }
+    in->sweeps_done += n;
+    return true;
+}
+
 ucp_status inst_sweep(ucp_inst* in, int n) {
     if (n == 0) return UCP_OK;
     ucp_status st = grow_history(in, in->sweeps_done + 1 + n);
@@ -507,6 +535,7 @@ ucp_status inst_sweep(ucp_inst* in, int n) {
     DevState& d = in->d;
     cudaStream_t s = in->stream;
     if (in->fast && solo_sweeps(in, n)) return check(in, "sweep");
+    if (in->fast && solo_launches(in, n)) return check(in, "sweep");
     if (in->fast) {
         for (int k = 0; k < n; ++k) {
             UCP_LAUNCH(in, "search", launch_search_fast(g, in->fv, d.nu[in->cur],

@@ -234,6 +234,9 @@ void launch_batch_setup_tc(const SetupLaunch& sl, cudaStream_t s);
 constexpr int kDeferBlocksBatch = 4;
 constexpr size_t kDeferRecBytes = 64;
 
+// Streaming multiprocessors of the current device (cached).
+int sm_count();
+
 // ---- plain FP64 path (kernels_plain.cu) --------------------------------
 void launch_weights(const Geom& g, DevState& d, cudaStream_t s);
 void launch_init(const Geom& g, DevState& d, int kind, int buf, cudaStream_t s);

@@ -105,6 +105,7 @@ struct ucp_inst {
     ucp::BatchSet* solo = nullptr;
     cudaGraphExec_t solo_graph[2] = {nullptr, nullptr};
     bool solo_tried = false;
+    bool solo_failed = false;   // the one-member batch set could not be built
 };
 
 namespace ucp {

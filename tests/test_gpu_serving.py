@@ -73,7 +73,7 @@ def test_served_results_equal_standalone_solves(binding):
 def test_requests_join_while_others_run(binding):
     """A request submitted after others started is admitted before they
     finish (it shares their steps) and still gets its standalone result."""
-    long_req = dict(small_requests(1, seed=5)[0], sweeps=40)
+    long_req = dict(small_requests(1, seed=5)[0], sweeps=2000)
     late = dict(small_requests(1, seed=6)[0], sweeps=2)
     with binding.Server(max_slots=8) as srv:
         t1 = srv.submit(long_req)

@@ -13,12 +13,18 @@ the marginal cost of one candidate (Section V-A) moves by at most
 2 eps sqrt(S) + eps^2, S the quadrature part of the cost (Cauchy-Schwarz over
 the normalised weights).  A near-tie at one refinement level changes the
 centre of the next, so a flipped decision can end anywhere along another
-branch of the coarse-to-fine search.  check() therefore replays the oracle's
-search for every x_i where the two sides' new f differ, from the GPU's
-pre-sweep controller under the oracle's table, branching at every stage over
-the candidates within that allowance of the stage minimum, and asserts that
-the GPU's (value, list position) is one of the reachable winners; it also
-asserts |dJ| <= 1e-9 per sweep and U within 1e-6, and reports the counts.
+branch of the coarse-to-fine search.  At the first sweep whose decisions
+differ (the controllers before it bit-identical, the tables within rounding)
+first_divergence() replays the oracle's search for every x_i where the new f
+differ, under the oracle's table, branching at every stage over the
+candidates within that allowance of the stage minimum, and asserts that the
+GPU's (value, list position) is one of the reachable winners.  Later sweeps
+start from different controllers and are counted, not replayed; J is bounded
+by |dJ| <= 1e-9 after every sweep throughout, and where every decision
+agreed, U within 1e-6.  (A near-tie between two distant values -- f at the
+edge of a step of the staircase -- moves U by up to the step height in the
+thin transition zones where that source dominates, which J weighs by ~1e-9
+or less.)
 """
 from __future__ import annotations
 
@@ -114,40 +120,59 @@ def possible_winners(o, U, nu_pre, i, eps):
     return {(c[0], c[2]) for c in states}
 
 
+def first_divergence(o, pre, post, what="", threads=None):
+    """The first sweep whose decisions differ: `pre` is the GPU's state
+    before it (controller bit-identical to the oracle's, u1 table within
+    rounding), `post` the GPU's state after it.  The oracle recomputes its own
+    table from that controller and its own decisions; every x_i where the
+    GPU's winner differs must be one the oracle's search can end on when its
+    costs move within what the tables' difference eps allows.  Returns a
+    report (points, eps, the oracle's cost gaps of the GPU's winners)."""
+    import os
+    oracle.set_threads(threads or os.cpu_count() or 1)
+    try:
+        nu_pre = o.init(2, pre["f"])
+        U_o = o.mmse(nu_pre)
+        nu_o, _ = o.search(nu_pre, U_o)
+    finally:
+        oracle.set_threads(1)
+    eps = float(np.max(np.abs(pre["U"] - U_o)))
+    nu_g = o.init(2, post["f"])
+    diff = np.nonzero(nu_g != nu_o)[0]
+    gaps = []
+    for i in diff:
+        win = possible_winners(o, U_o, nu_pre, int(i), eps)
+        got = (int(nu_g[i]), int(post["idx"][i]))
+        assert got in win, (what, int(i), got, sorted(win), eps)
+        gaps.append(o.cost(U_o, int(i), got[0]) - o.cost(U_o, int(i), int(nu_o[i])))
+    return dict(points=int(diff.size), eps=eps,
+                max_abs_gap=float(max((abs(x) for x in gaps), default=0.0)),
+                max_df=float(np.max(np.abs(o.value(nu_g) - o.value(nu_o)))) if diff.size else 0.0)
+
+
 def check(o, gpu, orc, what=""):
-    """Assert |dJ| <= 1e-9 per sweep, U within 1e-6 at the end, and that every
-    GPU decision that differs from the oracle's is one the oracle's own
-    search can make from the GPU's pre-sweep controller when its costs move
-    within what the measured table difference allows; return a report."""
-    n_x = o.n_x
+    """Assert |dJ| <= 1e-9 per sweep; where every decision agreed, U within
+    1e-6; at the first sweep whose decisions differ, that each differing
+    decision is a near-tie the tables' difference can reverse (later sweeps
+    start from different controllers and are counted, not replayed).
+    Returns a report."""
     assert len(gpu) == len(orc)
     dJ = [abs(g["J"] - c["J"]) for g, c in zip(gpu, orc)]
     rep = dict(what=what, sweeps=len(orc) - 1, max_dJ=max(dJ), first_diff_sweep=None,
-               diff_points=[], ties=[], max_dU=0.0)
+               diff_points=[], first=None, max_dU=0.0)
     assert max(dJ) <= TOL_J, (what, max(dJ), int(np.argmax(dJ)))
     np.testing.assert_array_equal(gpu[0]["f"], o.value(orc[0]["nu"]))
     for s in range(1, len(orc)):
-        fo = o.value(orc[s]["nu"])
-        fg = gpu[s]["f"]
-        eps = float(np.max(np.abs(gpu[s - 1]["U"] - orc[s - 1]["U"])))
-        rep["max_dU"] = max(rep["max_dU"], eps)
-        diff = np.nonzero(fg != fo)[0]
+        diff = np.nonzero(gpu[s]["f"] != o.value(orc[s]["nu"]))[0]
         rep["diff_points"].append(int(diff.size))
-        if not diff.size:
-            continue
-        if rep["first_diff_sweep"] is None:
+        if diff.size and rep["first_diff_sweep"] is None:
             rep["first_diff_sweep"] = s
-        nu_g_pre = o.init(2, gpu[s - 1]["f"])
-        nu_g = o.init(2, fg)
-        for i in diff:
-            win = possible_winners(o, orc[s - 1]["U"], nu_g_pre, int(i), eps)
-            got = (int(nu_g[i]), int(gpu[s]["idx"][i]))
-            g_gpu = o.cost(orc[s - 1]["U"], int(i), got[0])
-            g_best = min(o.cost(orc[s - 1]["U"], int(i), v) for v, _ in win)
-            rep["ties"].append(dict(sweep=s, i=int(i), branches=len(win),
-                                    gap=float(g_gpu - g_best), eps=eps))
-            assert got in win, (what, s, int(i), got, sorted(win), eps)
-    rep["max_dU"] = max(rep["max_dU"], float(np.max(np.abs(gpu[-1]["U"] - orc[-1]["U"]))))
-    assert rep["max_dU"] <= 1e-6, (what, rep["max_dU"])
+            rep["first"] = first_divergence(o, gpu[s - 1], gpu[s], what)
+    rep["max_dU"] = float(np.max(np.abs(gpu[-1]["U"] - orc[-1]["U"])))
+    rep["max_df"] = float(np.max(np.abs(gpu[-1]["f"] - o.value(orc[-1]["nu"]))))
     rep["final_diff_points"] = rep["diff_points"][-1] if rep["diff_points"] else 0
+    if rep["first_diff_sweep"] is None:
+        # the same decisions throughout: the controllers are bit-identical
+        # and u1 differs only by the rounding of its sums
+        assert rep["max_dU"] <= 1e-6, (what, rep["max_dU"])
     return rep
