@@ -47,6 +47,13 @@ class _Params(ctypes.Structure):
                 ("n_nbr", ctypes.c_int32), ("problem", ctypes.c_int32)]
 
 
+class Alg1Report(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("local_iters", ctypes.c_int32), ("exhaustion_iters", ctypes.c_int32),
+                ("N_L", ctypes.c_int32), ("N_P", ctypes.c_int32),
+                ("J", ctypes.c_double), ("I_L", ctypes.c_double), ("I_P", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -100,6 +107,14 @@ def _configure(L):
     L.orc_J.restype = ctypes.c_double
     L.orc_solve.argtypes = [P, ctypes.c_int, dp, ctypes.c_int, i64p, dp,
                             dp, i32p]
+    L.orc_derivs.argtypes = [P, dp, ctypes.c_int64, ctypes.c_int64, dp, dp]
+    L.orc_local_update.argtypes = [P, i64p, dp, ctypes.c_double, i64p, ctypes.c_int64,
+                                   ctypes.c_int64]
+    L.orc_split.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    L.orc_split.restype = ctypes.c_int
+    L.orc_algorithm1.argtypes = [P, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, i64p, dp, dp, i32p,
+                                 ctypes.POINTER(Alg1Report)]
     L.orc_set_threads.argtypes = [ctypes.c_int]
     L.orc_get_threads.restype = ctypes.c_int
     return L
@@ -217,6 +232,48 @@ class Oracle:
         nu = np.ascontiguousarray(nu, np.int64)
         U = np.ascontiguousarray(U, np.float64)
         return float(self._lib().orc_J(ctypes.byref(self._p), _i64p(nu), _dp(U)))
+
+    # -- Algorithm 1 (Sections III-B to III-D) ---------------------------
+    def derivs(self, U, i, nu):
+        """(g'/2, g''/2) of the marginal cost of u0 at x_i, u = value(nu)."""
+        U = np.ascontiguousarray(U, np.float64)
+        a, b = ctypes.c_double(), ctypes.c_double()
+        if self._lib().orc_derivs(ctypes.byref(self._p), _dp(U), int(i), int(nu),
+                                  ctypes.byref(a), ctypes.byref(b)) != 0:
+            raise ValueError("invalid parameters")
+        return a.value, b.value
+
+    def local_update(self, nu_pre, U, tau=0.0, i0=0, i1=None):
+        i1 = self.n_x if i1 is None else i1
+        nu_pre = np.ascontiguousarray(nu_pre, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        out = nu_pre.copy()
+        self._lib().orc_local_update(ctypes.byref(self._p), _i64p(nu_pre), _dp(U),
+                                     float(tau), _i64p(out), int(i0), int(i1))
+        return out
+
+    def split(self, I_L, I_P, N, n_l):
+        return int(self._lib().orc_split(float(I_L), float(I_P), int(N), int(n_l)))
+
+    def algorithm1(self, init_kind=0, N=20, precision=1e-10, tau=0.0, max_rounds=100,
+                   table=None):
+        nu = np.empty(self.n_x, dtype=np.int64)
+        U = np.empty(self.n_y)
+        Jp = np.full(1 + 2 * max_rounds, np.nan)
+        NL = np.full(max_rounds, -1, dtype=np.int32)
+        rep = Alg1Report()
+        tab = None if table is None else np.ascontiguousarray(table, np.float64)
+        rc = self._lib().orc_algorithm1(ctypes.byref(self._p), int(init_kind),
+                                        _dp(tab) if tab is not None else None, int(N),
+                                        float(precision), float(tau), int(max_rounds),
+                                        _i64p(nu), _dp(U), _dp(Jp), _i32p(NL),
+                                        ctypes.byref(rep))
+        if rc != 0:
+            raise ValueError("oracle algorithm1 failed")
+        r = {k: getattr(rep, k) for k, _ in Alg1Report._fields_}
+        n = r["rounds"]
+        r.update(nu=nu, U=U, J_phase=Jp[:1 + 2 * n], N_L_rounds=NL[:n])
+        return r
 
     def solve(self, init_kind: int, n_sweeps: int, table=None, want_idx=False):
         nu = np.empty(self.n_x, dtype=np.int64)

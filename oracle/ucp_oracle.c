@@ -39,6 +39,11 @@
  * f = u0, equal quadrature weights, and u1(y) = E[x0 | x1 = y], a
  * prior-weighted mean over the sources within W of y (see ucp_oracle.h).
  *
+ * Algorithm 1 (Sections III-B to III-D): the local update of u0 (Newton's
+ * step on the marginal cost where its second derivative is positive, else a
+ * gradient step), the adaptive split of each round's N iterations between
+ * local update and partial exhaustion, and the termination at precision p.
+ *
  * Parity status: S, g, the search, the u1 update and J are pinned by the
  * tests in tests/test_oracle_pins.py (closed forms, library interpolation,
  * brute force, invariants).  The converged J printed in Section V-A is a
@@ -527,6 +532,144 @@ int orc_solve(const orc_params* p, int init_kind, const double* table,
                    sizeof(int32_t) * (size_t)g.n_x);
     }
     memcpy(nu_out, a, sizeof(int64_t) * (size_t)g.n_x);
+    free(a); free(b); free(idx);
+    return 0;
+}
+
+/* ---- Algorithm 1: local update, adaptive split, outer loop ------------- */
+
+/* g'/2 and g''/2 at u = value(nu) for x_i (see ucp_oracle.h): the same
+ * positions, interpolation and summation order as S_of / cost_sc, each sum
+ * factored by the cell width delta so that its terms need no division. */
+static void derivs_of(const geom* g, const double* phi, const double* U, int64_t i,
+                      int64_t nu, double* h1, double* h2) {
+    int64_t cell = floor_div(nu, g->one);
+    double t = ldexp((double)(nu - cell * g->one), -g->shift);
+    int64_t jb = cell - g->hw + g->hy;
+    double u = value_of(g, nu), x = x_of(g, i), dl = g->p.delta;
+    double* a = (double*)malloc(sizeof(double) * (size_t)g->n_w);
+    double* b = (double*)malloc(sizeof(double) * (size_t)g->n_w);
+    for (int64_t l = 0; l < g->n_w; ++l) {
+        int64_t j = jb + l;
+        int64_t jl = j < 0 ? 0 : (j > g->n_y - 1 ? g->n_y - 1 : j);
+        int64_t jr = j + 1 < 0 ? 0 : (j + 1 > g->n_y - 1 ? g->n_y - 1 : j + 1);
+        double d = U[jr] - U[jl];
+        double uh = U[jl] + t * d;
+        if (g->p.problem == 1) {
+            a[l] = phi[l] * ((uh - x) * d);
+            b[l] = phi[l] * (d * d);
+        } else {
+            double e = u - uh, c = dl - d;
+            a[l] = phi[l] * (e * c);
+            b[l] = phi[l] * (c * c);
+        }
+    }
+    double s1 = fixed_sum(a, g->n_w), s2 = fixed_sum(b, g->n_w);
+    free(a);
+    free(b);
+    double lin = g->p.problem == 1 ? g->kk * u : g->kk * (u - x);
+    *h1 = lin + s1 / dl;
+    *h2 = g->kk + s2 / (dl * dl);
+}
+
+int orc_derivs(const orc_params* p, const double* U, int64_t i, int64_t nu,
+               double* half_d1, double* half_d2) {
+    geom g;
+    if (make_geom(p, &g)) return -1;
+    double* phi = (double*)malloc(sizeof(double) * (size_t)g.n_w);
+    phi_weights(&g, phi);
+    derivs_of(&g, phi, U, i, nu, half_d1, half_d2);
+    free(phi);
+    return 0;
+}
+
+/* Local update of u0 (Section III-D, "Local Update"), every x_i from the
+ * pre-update controller (Jacobi, as the partial exhaustion): Newton's step
+ * where g'' > 0, else the gradient step with step size tau; the new value
+ * is rounded to the controller lattice (value / delta * 2^shift, nearest,
+ * halves away from zero), so that every later cost is evaluated at exact
+ * positions.  A step to a non-finite or unrepresentable value keeps f_i. */
+void orc_local_update(const orc_params* p, const int64_t* nu_pre, const double* U,
+                      double tau, int64_t* nu_out, int64_t i0, int64_t i1) {
+    geom g;
+    if (make_geom(p, &g)) return;
+    double* phi = (double*)malloc(sizeof(double) * (size_t)g.n_w);
+    phi_weights(&g, phi);
+#pragma omp parallel for schedule(dynamic, 8) num_threads(g_threads)
+    for (int64_t i = i0; i < i1; ++i) {
+        double h1, h2;
+        derivs_of(&g, phi, U, i, nu_pre[i], &h1, &h2);
+        double u = value_of(&g, nu_pre[i]);
+        double un = h2 > 0.0 ? u - h1 / h2 : u - tau * (2.0 * h1);
+        double v = un / p->delta * (double)g.one;
+        nu_out[i] = fabs(v) < 9.0e15 ? (int64_t)llround(v) : nu_pre[i];
+    }
+    free(phi);
+}
+
+int orc_split(double I_L, double I_P, int N, int n_l) {
+    if (!(I_L + I_P > 0.0)) return n_l;
+    double r = floor(I_L * (double)N / (I_L + I_P));
+    int nl = r < 1.0 ? 1 : (r > (double)(N - 1) ? N - 1 : (int)r);
+    return nl;
+}
+
+int orc_algorithm1(const orc_params* p, int init_kind, const double* table, int N,
+                   double precision, double tau, int max_rounds, int64_t* nu_out,
+                   double* U_out, double* J_phase, int32_t* NL_rounds,
+                   orc_alg1_report* rep) {
+    geom g;
+    if (make_geom(p, &g) || N < 2 || max_rounds < 0 || !(precision >= 0.0)) return -1;
+    int64_t* a = (int64_t*)malloc(sizeof(int64_t) * (size_t)g.n_x);
+    int64_t* b = (int64_t*)malloc(sizeof(int64_t) * (size_t)g.n_x);
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)g.n_x);
+    if (orc_init(p, init_kind, table, a)) {
+        free(a); free(b); free(idx);
+        return -1;
+    }
+    orc_mmse(p, a, U_out, 0, g.n_y);
+    double Jc = orc_J(p, a, U_out);
+    if (J_phase) J_phase[0] = Jc;
+    double IL = precision, IP = precision;
+    int NL = N / 2, NP = N - NL, rounds = 0, nloc = 0, nexh = 0;
+    while (IL + IP > precision && rounds < max_rounds) {
+        if (NL_rounds) NL_rounds[rounds] = NL;
+        double J0 = Jc;
+        for (int k = 0; k < NL; ++k) {            /* m = 0, then m = 1 */
+            orc_local_update(p, a, U_out, tau, b, 0, g.n_x);
+            int64_t* t = a; a = b; b = t;
+            orc_mmse(p, a, U_out, 0, g.n_y);
+            ++nloc;
+        }
+        Jc = orc_J(p, a, U_out);
+        IL = fabs(J0 - Jc);
+        if (J_phase) J_phase[1 + 2 * rounds] = Jc;
+        double J1 = Jc;
+        for (int k = 0; k < NP; ++k) {
+            orc_search(p, a, U_out, b, idx, 0, g.n_x);
+            int64_t* t = a; a = b; b = t;
+            orc_mmse(p, a, U_out, 0, g.n_y);
+            ++nexh;
+        }
+        Jc = orc_J(p, a, U_out);
+        IP = fabs(J1 - Jc);
+        if (J_phase) J_phase[2 + 2 * rounds] = Jc;
+        NL = orc_split(IL, IP, N, NL);
+        NP = N - NL;
+        ++rounds;
+    }
+    memcpy(nu_out, a, sizeof(int64_t) * (size_t)g.n_x);
+    if (rep) {
+        rep->rounds = rounds;
+        rep->converged = IL + IP <= precision;
+        rep->local_iters = nloc;
+        rep->exhaustion_iters = nexh;
+        rep->N_L = NL;
+        rep->N_P = NP;
+        rep->J = Jc;
+        rep->I_L = IL;
+        rep->I_P = IP;
+    }
     free(a); free(b); free(idx);
     return 0;
 }

@@ -95,6 +95,53 @@ int orc_solve(const orc_params* p, int init_kind, const double* table,
               int n_sweeps, int64_t* nu_out, double* U_out, double* J_hist,
               int32_t* idx_hist);
 
+/* ---- Algorithm 1's outer loop (Sections III-B to III-D) ----------------
+ *
+ * Local update of u0 at x_i: with the linear interpolant of U the marginal
+ * cost g(u; x_i) is a quadratic in u on each y-cell, and its derivatives
+ * there are, with d_l = U[jr] - U[jl] the table step of the cell holding
+ * u + w_l (0 beyond the table) and uh_l the interpolated value,
+ *   problem 0: g'/2 = k^2 (u - x_i) + (1/delta) sum_l phi_l (u - uh_l)(delta - d_l)
+ *              g''/2 = k^2 + (1/delta^2) sum_l phi_l (delta - d_l)^2
+ *   problem 1: g'/2 = k^2 u + (1/delta) sum_l phi_l (uh_l - x_i) d_l
+ *              g''/2 = k^2 + (1/delta^2) sum_l phi_l d_l^2
+ * (the derivatives from the right at cell boundaries).  The sums are taken
+ * in the fixed order of the w quadrature.  orc_derivs returns g'/2 and
+ * g''/2.  The update is Newton's step u - g'/g'' where g'' > 0, else the
+ * gradient step u - tau g' (never taken on these two problems, where
+ * g'' >= 2 k^2), rounded to the controller lattice like a table start. */
+int orc_derivs(const orc_params* p, const double* U, int64_t i, int64_t nu,
+               double* half_d1, double* half_d2);
+void orc_local_update(const orc_params* p, const int64_t* nu_pre, const double* U,
+                      double tau, int64_t* nu_out, int64_t i0, int64_t i1);
+
+/* Adaptive minimisation: the local-update share of the next round,
+ * N_L = min(max(floor(I_L N / (I_L + I_P)), 1), N - 1) (kept as n_l when
+ * I_L + I_P = 0). */
+int orc_split(double I_L, double I_P, int N, int n_l);
+
+typedef struct {
+    int32_t rounds;            /* rounds run                                  */
+    int32_t converged;         /* 1 if I_L + I_P <= precision at the end      */
+    int32_t local_iters;       /* local-update iterations (Newton + u1 step)  */
+    int32_t exhaustion_iters;  /* partial-exhaustion iterations (sweeps)      */
+    int32_t N_L, N_P;          /* the split the next round would use          */
+    double J, I_L, I_P;        /* final J and the last round's improvements   */
+} orc_alg1_report;
+
+/* Algorithm 1: init -> U = mmse(f) -> J_c; I_L = I_P = precision;
+ * N_L = floor(N/2), N_P = N - N_L; while I_L + I_P > precision (and fewer
+ * than max_rounds rounds): N_L local-update iterations (u0 by the local
+ * update above, then u1 by its exact minimiser), J, I_L = |J before - J
+ * after|; N_P partial-exhaustion iterations (the sweep of orc_search and
+ * orc_mmse), J, I_P likewise; the next split by orc_split.  J_phase (may be
+ * NULL, 1 + 2 max_rounds entries): the initial J, then J after every phase;
+ * NL_rounds (may be NULL, max_rounds entries): N_L of every round run. */
+int orc_algorithm1(const orc_params* p, int init_kind, const double* table, int N,
+                   double precision, double tau, int max_rounds, int64_t* nu_out,
+                   double* U_out, double* J_phase, int32_t* NL_rounds,
+                   orc_alg1_report* rep);
+
 /* Threads used by orc_search / orc_mmse / orc_solve (OpenMP; 1 = serial).
  * Results do not depend on the thread count. */
 void orc_set_threads(int n);
