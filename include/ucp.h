@@ -171,6 +171,52 @@ UCP_API ucp_status ucp_set_controllers(ucp_inst* inst, const double* f, uint64_t
                                const double* u1, uint64_t n_y);
 UCP_API ucp_status ucp_destroy(ucp_inst* inst);
 
+/* ---- Algorithm 1's outer loop (Sections III-B to III-D) ----------------- */
+
+/* Local update (Section III-D, "Local Update"): n iterations, each moving
+ * every f_i (all x0 points in parallel, from the controller before the
+ * iteration) by Newton's step on its marginal cost, u <- u - g'(u)/g''(u)
+ * where g'' > 0, else by the gradient step u <- u - tau g'(u), the new value
+ * rounded to the controller lattice (as ucp_set_controllers rounds a
+ * table); then u1 <- its exact minimiser (the u1 step of ucp_sweep) and J,
+ * recorded in the J history like a sweep.  g' and g'' are the derivatives of
+ * the discretised cost, which is quadratic in u on each y-cell (from the
+ * right at a cell boundary), formed by the w quadrature in FP64 in its fixed
+ * order; g'' >= 2 k^2 > 0 on both problems, so the gradient branch is not
+ * reached there.  The winners' list positions (ucp_get_controllers idx) keep
+ * the last sweep's.  Asynchronous on the instance stream. */
+UCP_API ucp_status ucp_local_update(ucp_inst* inst, int32_t n, double tau);
+
+typedef struct {
+    int32_t N;            /* iterations per round, >= 2 (20 in Section IV)    */
+    int32_t max_rounds;   /* stop after this many rounds, >= 0               */
+    double precision;     /* p >= 0: stop once I_L + I_P <= p (1e-10)        */
+    double tau;           /* gradient step where g'' <= 0                    */
+} ucp_solve_params;
+
+typedef struct {
+    int32_t rounds;            /* rounds run                                 */
+    int32_t converged;         /* 1 if I_L + I_P <= p when the loop ended    */
+    int32_t local_iters;       /* local-update iterations run                */
+    int32_t exhaustion_iters;  /* partial-exhaustion iterations (sweeps) run */
+    int32_t N_L, N_P;          /* the split the next round would take        */
+    double J, I_L, I_P;        /* J at the end; the last round's changes     */
+} ucp_solve_report;
+
+/* Algorithm 1 ("Generic Solver") from the instance's current state: with
+ * I_L = I_P = p and N_L = floor(N/2), N_P = N - N_L, while I_L + I_P > p:
+ * N_L local-update iterations (ucp_local_update), I_L = |J before - J
+ * after|; N_P partial-exhaustion iterations (ucp_sweep), I_P likewise; then
+ * N_L = min(max(floor(I_L N / (I_L + I_P)), 1), N - 1), N_P = N - N_L
+ * (the split kept when I_L + I_P = 0).  Synchronises after every phase to
+ * read J.  J_phase (host, may be NULL, 1 + 2 max_rounds entries) receives
+ * the starting J and J after every phase; NL_rounds (host, may be NULL,
+ * max_rounds entries) N_L of every round run.  UCP_E_ARG for N < 2,
+ * max_rounds < 0 or a negative or non-finite precision or tau. */
+UCP_API ucp_status ucp_solve(ucp_inst* inst, const ucp_solve_params* params,
+                             ucp_solve_report* report, double* J_phase,
+                             int32_t* NL_rounds);
+
 /* Fast path: number of candidate costs re-computed by the serial FP64
  * quadrature because screened table costs left a near-tie open (since
  * creation; 0 on the plain path).  Synchronises. */

@@ -81,6 +81,18 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 
 
+class SolveParams(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("precision", ctypes.c_double), ("tau", ctypes.c_double)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("local_iters", ctypes.c_int32), ("exhaustion_iters", ctypes.c_int32),
+                ("N_L", ctypes.c_int32), ("N_P", ctypes.c_int32),
+                ("J", ctypes.c_double), ("I_L", ctypes.c_double), ("I_P", ctypes.c_double)]
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -143,6 +155,9 @@ def load():
                                          ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
     L.ucp_batch_kernel_times.restype = ctypes.c_int32
+    L.ucp_local_update.argtypes = [_vp, ctypes.c_int32, ctypes.c_double]
+    L.ucp_solve.argtypes = [_vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveReport),
+                            _dp, _i32p]
     _lib = L
     return L
 
@@ -320,6 +335,26 @@ class Instance:
                                 bt.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                 n_cols, sz), "ucp_get_tables")
         return {"P": P, "Q": Q, "R": R, "bound": bt, "c_lo": int(sz[2]), "jlo": int(sz[3])}
+
+    def local_update(self, n: int = 1, tau: float = 0.0):
+        """n local-update iterations of Algorithm 1 (``ucp_local_update``)."""
+        _check(load().ucp_local_update(self.h, int(n), float(tau)), "ucp_local_update")
+
+    def solve(self, N=20, precision=1e-10, tau=0.0, max_rounds=100) -> dict:
+        """Algorithm 1's outer loop from the current state (``ucp_solve``):
+        the report, J after every phase and N_L of every round."""
+        sp = SolveParams(int(N), int(max_rounds), float(precision), float(tau))
+        rep = SolveReport()
+        cap = max(0, int(max_rounds))       # the library rejects a negative count
+        Jp = np.full(1 + 2 * cap, np.nan)
+        NL = np.full(max(1, cap), -1, dtype=np.int32)
+        _check(load().ucp_solve(self.h, ctypes.byref(sp), ctypes.byref(rep),
+                                _ptr(Jp, ctypes.c_double), _ptr(NL, ctypes.c_int32)),
+               "ucp_solve")
+        r = {k: getattr(rep, k) for k, _ in SolveReport._fields_}
+        n = r["rounds"]
+        r.update(J_phase=Jp[:1 + 2 * n], N_L_rounds=NL[:n])
+        return r
 
     def tie_recosts(self) -> int:
         v = ctypes.c_int64()

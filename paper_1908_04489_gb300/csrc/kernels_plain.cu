@@ -638,6 +638,107 @@ int spread_bs(int64_t n, int max_bs) {
     return bs;
 }
 
+// ---- Algorithm 1's local update of u0 (Section III-D) ------------------------
+
+// Sums of two arrays of n chunk sums by the fixed pairwise tree of
+// fixed_sum.cuh, level by level and in place (entries 2k and 2k + 1 of a
+// level give entry k of the next, an unpaired last entry moves up), every
+// level's additions spread over the block; the results land in A[0], B[0].
+__device__ void block_tree2(double* A, double* B, int64_t n) {
+    while (n > 1) {
+        const int64_t h = n / 2;
+        for (int64_t k0 = 0; k0 < h; k0 += blockDim.x) {   // the same for the block
+            const int64_t k = k0 + threadIdx.x;
+            double a = 0.0, b = 0.0;
+            if (k < h) {
+                a = __dadd_rn(A[2 * k], A[2 * k + 1]);
+                b = __dadd_rn(B[2 * k], B[2 * k + 1]);
+            }
+            __syncthreads();   // later passes read only entries >= k0 + blockDim.x
+            if (k < h) {
+                A[k] = a;
+                B[k] = b;
+            }
+            __syncthreads();
+        }
+        if (n & 1) {
+            if (threadIdx.x == 0) {
+                A[h] = A[n - 1];
+                B[h] = B[n - 1];
+            }
+            __syncthreads();
+        }
+        n = h + (n & 1);
+    }
+}
+
+// One block per x0 point i.  With the linear interpolant of U the marginal
+// cost g(u; x_i) is a quadratic in u on each y-cell; its derivatives at
+// u = f_i (from the right at a cell boundary) are, with d_l = U[jr] - U[jl]
+// the table step of the cell holding u + w_l (0 beyond the table) and uh_l
+// the interpolated value,
+//   problem 0: g'/2 = k^2 (u - x_i) + (1/delta) sum_l phi_l (u - uh_l)(delta - d_l),
+//              g''/2 = k^2 + (1/delta^2) sum_l phi_l (delta - d_l)^2;
+//   problem 1: g'/2 = k^2 u + (1/delta) sum_l phi_l (uh_l - x_i) d_l,
+//              g''/2 = k^2 + (1/delta^2) sum_l phi_l d_l^2.
+// Each sum in the fixed order of the w quadrature (32-term chunks in order,
+// then the pairwise tree), every operation rounded once.  The new value is
+// Newton's step u - g'/g'' where g'' > 0, else the gradient step u - tau g',
+// rounded to the controller lattice like a table start (nearest, halves
+// away from zero); a non-finite or unrepresentable step keeps f_i.
+constexpr int kLocalT = 128;
+__global__ void __launch_bounds__(kLocalT) k_local_update(Geom g, const double* __restrict__ phi,
+                                                          const double* __restrict__ U,
+                                                          const int64_t* __restrict__ nu_in,
+                                                          int64_t* __restrict__ nu_out,
+                                                          double tau) {
+    extern __shared__ double loc_sm[];
+    const int64_t i = blockIdx.x;
+    const int64_t nu = nu_in[i];
+    const int64_t cell = nu >> g.shift;
+    const double t = __dmul_rn((double)(nu - (cell << g.shift)), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy;
+    const double u = value_of(g, nu), x = x_of(g, i), dl = g.delta;
+    const int64_t ny1 = g.n_y - 1;
+    const int64_t nch = sum_chunks(g.n_w);
+    double* A = loc_sm;
+    double* B = loc_sm + nch;
+    for (int64_t k = threadIdx.x; k < nch; k += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        const int64_t l1 = min((k + 1) * kSumChunk, g.n_w);
+        for (int64_t l = k * kSumChunk; l < l1; ++l) {
+            const int64_t j = jb + l;
+            const int64_t jl = j < 0 ? 0 : (j > ny1 ? ny1 : j);
+            const int64_t jr = j + 1 < 0 ? 0 : (j + 1 > ny1 ? ny1 : j + 1);
+            const double d = __dsub_rn(U[jr], U[jl]);
+            const double uh = __dadd_rn(U[jl], __dmul_rn(t, d));
+            double ta, tb;
+            if (g.problem == 1) {
+                ta = __dmul_rn(phi[l], __dmul_rn(__dsub_rn(uh, x), d));
+                tb = __dmul_rn(phi[l], __dmul_rn(d, d));
+            } else {
+                const double e = __dsub_rn(u, uh), c = __dsub_rn(dl, d);
+                ta = __dmul_rn(phi[l], __dmul_rn(e, c));
+                tb = __dmul_rn(phi[l], __dmul_rn(c, c));
+            }
+            a = __dadd_rn(a, ta);
+            b = __dadd_rn(b, tb);
+        }
+        A[k] = a;
+        B[k] = b;
+    }
+    __syncthreads();
+    block_tree2(A, B, nch);
+    if (threadIdx.x != 0) return;
+    const double lin = g.problem == 1 ? __dmul_rn(g.kk, u) : __dmul_rn(g.kk, __dsub_rn(u, x));
+    const double h1 = __dadd_rn(lin, __ddiv_rn(A[0], dl));
+    const double h2 = __dadd_rn(g.kk, __ddiv_rn(B[0], __dmul_rn(dl, dl)));
+    const double un = h2 > 0.0 ? __dsub_rn(u, __ddiv_rn(h1, h2))
+                               : __dsub_rn(u, __dmul_rn(tau, __dmul_rn(2.0, h1)));
+    const double v = __dmul_rn(__ddiv_rn(un, g.delta), (double)g.one);
+    nu_out[i] = fabs(v) < 9.0e15 ? (int64_t)llround(v) : nu;
+}
+
 }  // namespace
 
 // SMs of the current device (cached per device).
@@ -710,6 +811,27 @@ void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s) {
     else
         k_mmse_plain<<<blocks(g.n_y, spread_bs(g.n_y, 128)), spread_bs(g.n_y, 128), 0, s>>>(
             g, d.nu[buf], d.U);
+}
+
+// Shared memory of the local update for grids of n_w taps (two chunk-sum
+// arrays); 0 if more than a block can hold.
+size_t local_update_smem(const Geom& g) {
+    const size_t b = 16 * (size_t)sum_chunks(g.n_w);
+    return b <= 200 * 1024 ? b : 0;
+}
+
+cudaError_t launch_local_update(const Geom& g, const double* phi, const double* U,
+                                const int64_t* nu_in, int64_t* nu_out, double tau,
+                                cudaStream_t s) {
+    const size_t smem = local_update_smem(g);
+    if (!smem) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_local_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_local_update<<<(unsigned)g.n_x, kLocalT, smem, s>>>(g, phi, U, nu_in, nu_out, tau);
+    return cudaGetLastError();
 }
 
 void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {

@@ -4,6 +4,7 @@
 // closed-form u1 update, then J; Section IV-A's Jacobi parallelism):
 //   search(f_pre, U) -> f ; U <- E[x1 | y1] ; S at the coarse list and at f
 //   under the new U ; J.
+#include <math.h>
 #include <string.h>
 
 #include "ucp_fast.cuh"
@@ -555,6 +556,87 @@ ucp_status inst_sweep(ucp_inst* in, int n) {
         in->sweeps_done += 1;
         st = refresh_costs(in, (int)in->sweeps_done);
         if (st != UCP_OK) return st;
+    }
+    return UCP_OK;
+}
+
+ucp_status inst_local_update(ucp_inst* in, int n, double tau) {
+    if (n == 0) return UCP_OK;
+    ucp_status st = grow_history(in, in->sweeps_done + 1 + n);
+    if (st != UCP_OK) return st;
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    cudaStream_t s = in->stream;
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = cudaSuccess;
+        UCP_LAUNCH(in, "local_update", e = launch_local_update(g, d.phi, d.U, d.nu[in->cur],
+                                                               d.nu[in->cur ^ 1], tau, s));
+        if (e != cudaSuccess) return check(in, "local update");
+        in->cur ^= 1;
+        in->sweeps_done += 1;
+        if (in->fast) {
+            launch_mmse_fast(g, in->fv, d.nu[in->cur], d.U, s, &in->prof);
+            st = fast_refresh(in, (int)in->sweeps_done);
+        } else {
+            UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, in->cur, s));
+            st = refresh_costs(in, (int)in->sweeps_done);
+        }
+        if (st != UCP_OK) return st;
+    }
+    return check(in, "local update");
+}
+
+int alg1_split(double I_L, double I_P, int N, int n_l) {
+    if (!(I_L + I_P > 0.0)) return n_l;
+    const double r = floor(I_L * (double)N / (I_L + I_P));
+    return r < 1.0 ? 1 : (r > (double)(N - 1) ? N - 1 : (int)r);
+}
+
+// Algorithm 1 (Sections III-B to III-D): rounds of N_L local-update
+// iterations and N_P partial-exhaustion iterations (sweeps), J read after
+// each phase, I_L and I_P the absolute changes of J over the two phases,
+// the next split proportional to them (each phase at least once), until
+// I_L + I_P <= p.  Starts from the instance's current state.
+ucp_status inst_solve(ucp_inst* in, const ucp_solve_params& sp, ucp_solve_report* rep,
+                      double* J_phase, int32_t* NL_rounds) {
+    auto J_now = [&](double* J) {
+        return inst_read(in, in->d.J + in->sweeps_done, J, sizeof(double));
+    };
+    double Jc = 0.0;
+    ucp_status st = J_now(&Jc);
+    if (st != UCP_OK) return st;
+    if (J_phase) J_phase[0] = Jc;
+    const int N = sp.N;
+    double IL = sp.precision, IP = sp.precision;
+    int NL = N / 2, NP = N - NL, rounds = 0, nloc = 0, nexh = 0;
+    while (IL + IP > sp.precision && rounds < sp.max_rounds) {
+        if (NL_rounds) NL_rounds[rounds] = NL;
+        const double J0 = Jc;
+        if ((st = inst_local_update(in, NL, sp.tau)) != UCP_OK) return st;
+        nloc += NL;
+        if ((st = J_now(&Jc)) != UCP_OK) return st;
+        IL = fabs(J0 - Jc);
+        if (J_phase) J_phase[1 + 2 * rounds] = Jc;
+        const double J1 = Jc;
+        if ((st = inst_sweep(in, NP)) != UCP_OK) return st;
+        nexh += NP;
+        if ((st = J_now(&Jc)) != UCP_OK) return st;
+        IP = fabs(J1 - Jc);
+        if (J_phase) J_phase[2 + 2 * rounds] = Jc;
+        NL = alg1_split(IL, IP, N, NL);
+        NP = N - NL;
+        ++rounds;
+    }
+    if (rep) {
+        rep->rounds = rounds;
+        rep->converged = IL + IP <= sp.precision;
+        rep->local_iters = nloc;
+        rep->exhaustion_iters = nexh;
+        rep->N_L = NL;
+        rep->N_P = NP;
+        rep->J = Jc;
+        rep->I_L = IL;
+        rep->I_P = IP;
     }
     return UCP_OK;
 }

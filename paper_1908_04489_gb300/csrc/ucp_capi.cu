@@ -244,6 +244,34 @@ extern "C" ucp_status ucp_sweep(ucp_inst* in, int32_t n_sweeps) {
     return inst_sweep(in, n_sweeps);
 }
 
+static ucp_status arg_error(const char* where, const char* why) {
+    set_error("%s: %s", where, why);
+    return UCP_E_ARG;
+}
+
+extern "C" ucp_status ucp_local_update(ucp_inst* in, int32_t n, double tau) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    if (n < 0 || !std::isfinite(tau))
+        return arg_error("ucp_local_update", "n must be >= 0 and tau finite");
+    if (!local_update_smem(in->g))
+        return arg_error("ucp_local_update", "w grid too long for the local update");
+    return inst_local_update(in, n, tau);
+}
+
+extern "C" ucp_status ucp_solve(ucp_inst* in, const ucp_solve_params* sp,
+                                ucp_solve_report* rep, double* J_phase, int32_t* NL_rounds) {
+    if (!in || !sp) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    if (sp->N < 2 || sp->max_rounds < 0 || !(sp->precision >= 0.0) ||
+        !std::isfinite(sp->precision) || !std::isfinite(sp->tau))
+        return arg_error("ucp_solve", "N >= 2, max_rounds >= 0, finite precision >= 0 "
+                                      "and finite tau required");
+    if (!local_update_smem(in->g))
+        return arg_error("ucp_solve", "w grid too long for the local update");
+    return inst_solve(in, *sp, rep, J_phase, NL_rounds);
+}
+
 extern "C" ucp_status ucp_eval_J(ucp_inst* in, double* J_out) {
     if (!in || !J_out) return UCP_E_ARG;
     if (in->poisoned) return UCP_E_STATE;

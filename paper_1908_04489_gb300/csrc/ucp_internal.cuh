@@ -253,5 +253,12 @@ void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
                     cudaStream_t s);
 void launch_f_values(const Geom& g, const int64_t* nu, const double* x_or_null,
                      double* out, int as_u0, cudaStream_t s);
+// Algorithm 1's local update of u0 (Section III-D): nu_out = Newton's step
+// (gradient step tau where g'' <= 0) from nu_in under the u1 table U, every
+// x0 point in parallel; exact FP64 in the w quadrature's fixed order.
+size_t local_update_smem(const Geom& g);
+cudaError_t launch_local_update(const Geom& g, const double* phi, const double* U,
+                                const int64_t* nu_in, int64_t* nu_out, double tau,
+                                cudaStream_t s);
 
 }  // namespace ucp

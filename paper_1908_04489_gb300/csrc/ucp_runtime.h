@@ -126,6 +126,15 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
 ucp_status inst_create(ucp_ctx* ctx, const ucp_params* params, cudaStream_t stream,
                        bool own_setup, ucp_inst** out, void* slab = nullptr);
 ucp_status inst_sweep(ucp_inst* in, int n);
+// n local-update iterations of Algorithm 1 (u0 by the local update, then u1
+// by its exact minimiser, then J), recorded in the J history like sweeps.
+ucp_status inst_local_update(ucp_inst* in, int n, double tau);
+// Algorithm 1's outer loop on the host around the two kinds of iteration.
+ucp_status inst_solve(ucp_inst* in, const ucp_solve_params& sp, ucp_solve_report* rep,
+                      double* J_phase, int32_t* NL_rounds);
+// N_L of the next round: min(max(floor(I_L N / (I_L + I_P)), 1), N - 1),
+// n_l when I_L + I_P = 0.
+int alg1_split(double I_L, double I_P, int N, int n_l);
 // Make room in the J history for `need` entries (synchronises on growth).
 ucp_status grow_history(ucp_inst* in, long long need);
 ucp_status inst_sync(ucp_inst* in);
