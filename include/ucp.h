@@ -171,6 +171,25 @@ UCP_API ucp_status ucp_set_controllers(ucp_inst* inst, const double* f, uint64_t
                                const double* u1, uint64_t n_y);
 UCP_API ucp_status ucp_destroy(ucp_inst* inst);
 
+/* ---- one sweep split over processes (Section IV-A) ----------------------- */
+
+/* For a fixed controller the u0 step of every x0 point is independent of
+ * the others (Section IV-A), so one instance's sweep can be split over
+ * processes (one per GPU): each holds the same instance, searches its range
+ * of x0 points, the new values are exchanged, and every process finishes
+ * the sweep (u1 step, tables, J) on the whole new controller.
+ *   ucp_sweep_part: the search of x0 points i0 .. i1 - 1 (0 <= i0 <= i1 <=
+ *     n_x) from the current state; f_part (host, i1 - i0 doubles) receives
+ *     their new values.  Synchronises.  The winners' list positions
+ *     (ucp_get_controllers idx) are valid for this range only.
+ *   ucp_sweep_finish: f (host, n_x doubles) is the whole new controller
+ *     (every range's part); it becomes the controller and the rest of the
+ *     sweep runs, J recorded as after ucp_sweep.  Synchronises on the copy.
+ * ucp_sweep_part over [0, n_x) followed by ucp_sweep_finish gives exactly
+ * ucp_sweep(1).  UCP_E_ARG for ranges or buffers out of bounds. */
+UCP_API ucp_status ucp_sweep_part(ucp_inst* inst, int64_t i0, int64_t i1, double* f_part);
+UCP_API ucp_status ucp_sweep_finish(ucp_inst* inst, const double* f, uint64_t n_x);
+
 /* ---- Algorithm 1's outer loop (Sections III-B to III-D) ----------------- */
 
 /* Local update (Section III-D, "Local Update"): n iterations, each moving

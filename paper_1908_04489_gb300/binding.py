@@ -156,6 +156,8 @@ def load():
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
     L.ucp_batch_kernel_times.restype = ctypes.c_int32
     L.ucp_local_update.argtypes = [_vp, ctypes.c_int32, ctypes.c_double]
+    L.ucp_sweep_part.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, _dp]
+    L.ucp_sweep_finish.argtypes = [_vp, _dp, _u64]
     L.ucp_solve.argtypes = [_vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveReport),
                             _dp, _i32p]
     _lib = L
@@ -335,6 +337,19 @@ class Instance:
                                 bt.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                 n_cols, sz), "ucp_get_tables")
         return {"P": P, "Q": Q, "R": R, "bound": bt, "c_lo": int(sz[2]), "jlo": int(sz[3])}
+
+    def sweep_part(self, i0: int, i1: int) -> np.ndarray:
+        """The search of x0 points i0..i1-1; their new f (``ucp_sweep_part``)."""
+        out = np.empty(max(0, int(i1) - int(i0)))
+        _check(load().ucp_sweep_part(self.h, int(i0), int(i1), _ptr(out, ctypes.c_double)),
+               "ucp_sweep_part")
+        return out
+
+    def sweep_finish(self, f):
+        """The whole new f, then the rest of the sweep (``ucp_sweep_finish``)."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check(load().ucp_sweep_finish(self.h, _ptr(f, ctypes.c_double), f.size),
+               "ucp_sweep_finish")
 
     def local_update(self, n: int = 1, tau: float = 0.0):
         """n local-update iterations of Algorithm 1 (``ucp_local_update``)."""

@@ -884,18 +884,20 @@ __device__ __forceinline__ void search_one(const Geom& g, const FastView& f,
 }
 
 // One group of G lanes per x0 point; near-ties are deferred.
+// Points i_lo .. i_hi - 1 (i_hi < 0: every point) are searched.
 template <int G>
 __device__ __forceinline__ void search_body(const Geom& g, const FastView& f,
                                             const int64_t* __restrict__ nu_pre,
                                             int64_t* __restrict__ nu_out,
                                             int32_t* __restrict__ idx_out,
                                             int32_t* n_exact, double* tie_smem,
-                                            int64_t bx) {
-    const int64_t i = (bx * blockDim.x + threadIdx.x) / G;
+                                            int64_t bx, int64_t i_lo = 0, int64_t i_hi = -1) {
+    const int64_t i = i_lo + (bx * blockDim.x + threadIdx.x) / G;
+    const int64_t hi = i_hi < 0 ? g.n_x : i_hi;
     double* tie_terms = tie_smem + (threadIdx.x / G) * (kGroupScratch * G);
     const Best none{{FLT_MAX, 0.f}, 0.f, INT_MAX, 0, false, 0.0};
     search_one<G, kTierDefer>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_terms,
-                              nullptr, i, i < g.n_x, true, 0, none);
+                              nullptr, i, i < hi, true, 0, none);
 }
 
 // The deferred x0 points, one per block at a time (blocks bx, bx + nbx, ...
@@ -925,9 +927,11 @@ __global__ void __launch_bounds__(kSearchT, 6) k_search_fast(Geom g, FastView f,
                                                      const int64_t* __restrict__ nu_pre,
                                                      int64_t* __restrict__ nu_out,
                                                      int32_t* __restrict__ idx_out,
-                                                     int32_t* n_exact) {
+                                                     int32_t* n_exact, int64_t i_lo,
+                                                     int64_t i_hi) {
     __shared__ double tie_smem[kSearchT * kGroupScratch];
-    search_body<kFastG>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x);
+    search_body<kFastG>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x,
+                        i_lo, i_hi);
 }
 
 // Blocks of the deferred search of one instance: one per 128 x0 points
@@ -1143,10 +1147,13 @@ void launch_batch_setup_fast(const SetupLaunch& sl, cudaStream_t s) {
 }
 
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
-                        int64_t* nu_out, int32_t* idx, cudaStream_t s) {
-    const int64_t threads = g.n_x * (int64_t)kFastG;
+                        int64_t* nu_out, int32_t* idx, cudaStream_t s, int64_t i_lo,
+                        int64_t i_hi) {
+    const int64_t hi = i_hi < 0 ? g.n_x : i_hi;
+    const int64_t threads = (hi - i_lo) * (int64_t)kFastG;
+    if (threads <= 0) return;
     k_search_fast<<<blocks(threads, kSearchT), kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx,
-                                                                  f.n_exact);
+                                                                  f.n_exact, i_lo, hi);
     k_search_deferred<<<defer_blocks_of(g), kCoopT, 0, s>>>(g, f, nu_in, nu_out, idx,
                                                             f.n_exact);
 }

@@ -543,13 +543,13 @@ __global__ void __launch_bounds__(256) k_search_plain(
     const double* __restrict__ Ud, const int64_t* __restrict__ nu_pre,
     const double* __restrict__ Sf, const double* __restrict__ Sc,
     const int64_t* __restrict__ coarse, int64_t* __restrict__ nu_out,
-    int32_t* __restrict__ idx_out) {
+    int32_t* __restrict__ idx_out, int64_t i_lo, int64_t i_hi) {
     constexpr int P = G * C;
     const int lane = threadIdx.x & 31;
     const int lp = lane % P;
     const int slot = lp / C, sub = lp % C, slot_base = lane - sub;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / P;
-    const bool active = i < g.n_x;
+    const int64_t i = i_lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / P;
+    const bool active = i < i_hi;
     const int64_t ic = active ? i : g.n_x - 1;
 
     double best_g = DBL_MAX;
@@ -845,22 +845,26 @@ void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
     k_S_list<<<blocks(n, bs), bs, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out, at_x);
 }
 
-void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s) {
+void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s,
+                         int64_t i_lo, int64_t i_hi) {
+    if (i_hi < 0) i_hi = g.n_x;
+    const int64_t n = i_hi - i_lo;
+    if (n <= 0) return;
     // one warp per x0 point (split quadratures) when that still leaves at
     // most 16 warps per SM, else n_refine lanes per point
-    const bool split = g.n_x <= 16 * (int64_t)sm_count();
+    const bool split = n <= 16 * (int64_t)sm_count();
 #define UCP_SEARCH_CASE(G)                                                        \
     case G: {                                                                     \
-        const int64_t threads = g.n_x * (int64_t)(split ? 32 : G);                \
+        const int64_t threads = n * (int64_t)(split ? 32 : G);                    \
         const int bs = spread_bs(threads, 256);                                   \
         if (split)                                                                \
             k_search_plain<G, 32 / G><<<blocks(threads, bs), bs, 0, s>>>(         \
                 g, d.phi, d.U, d.Ud, d.nu[buf_in], d.Sf, d.Sc, d.coarse,          \
-                d.nu[buf_in ^ 1], d.idx);                                         \
+                d.nu[buf_in ^ 1], d.idx, i_lo, i_hi);                             \
         else                                                                      \
             k_search_plain<G, 1><<<blocks(threads, bs), bs, 0, s>>>(              \
                 g, d.phi, d.U, d.Ud, d.nu[buf_in], d.Sf, d.Sc, d.coarse,          \
-                d.nu[buf_in ^ 1], d.idx);                                         \
+                d.nu[buf_in ^ 1], d.idx, i_lo, i_hi);                             \
         break;                                                                    \
     }
     switch (g.n_refine) {

@@ -5,6 +5,8 @@
 //   search(f_pre, U) -> f ; U <- E[x1 | y1] ; S at the coarse list and at f
 //   under the new U ; J.
 #include <math.h>
+
+#include <vector>
 #include <string.h>
 
 #include "ucp_fast.cuh"
@@ -584,6 +586,51 @@ ucp_status inst_local_update(ucp_inst* in, int n, double tau) {
         if (st != UCP_OK) return st;
     }
     return check(in, "local update");
+}
+
+// One sweep split over several processes (Section IV-A: the x0 points are
+// independent for a fixed controller).  Part: the search of points i0..i1-1
+// from the current state into the next buffer, their new values copied to
+// host memory.  Finish: the full new controller (every part) from host
+// memory into the next buffer, then the rest of the sweep (u1 step, tables
+// or costs, J).  Part over every point + finish == one ucp_sweep.
+ucp_status inst_sweep_part(ucp_inst* in, int64_t i0, int64_t i1, double* f_host) {
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    cudaStream_t s = in->stream;
+    if (in->fast) {
+        UCP_LAUNCH(in, "search", launch_search_fast(g, in->fv, d.nu[in->cur],
+                                                    d.nu[in->cur ^ 1], d.idx, s, i0, i1));
+    } else {
+        UCP_LAUNCH(in, "search", launch_search_plain(g, d, in->cur, s, i0, i1));
+    }
+    const size_t n = (size_t)(i1 - i0);
+    if (n == 0) return check(in, "sweep part");
+    std::vector<int64_t> nu(n);
+    ucp_status st = inst_read(in, d.nu[in->cur ^ 1] + i0, nu.data(), 8 * n);
+    if (st != UCP_OK) return st;
+    for (size_t k = 0; k < n; ++k) f_host[k] = ldexp((double)nu[k] * g.delta, -g.shift);
+    return UCP_OK;
+}
+
+ucp_status inst_sweep_finish(ucp_inst* in, const double* f_host) {
+    const Geom& g = in->g;
+    DevState& d = in->d;
+    cudaStream_t s = in->stream;
+    ucp_status st = grow_history(in, in->sweeps_done + 2);
+    if (st != UCP_OK) return st;
+    cudaMemcpyAsync(d.table, f_host, 8 * (size_t)g.n_x, cudaMemcpyHostToDevice, s);
+    UCP_LAUNCH(in, "init", launch_table_to_lattice(g, d.table, d.nu[in->cur ^ 1], s));
+    // the caller's host buffer must not be read after we return
+    if (cudaStreamSynchronize(s) != cudaSuccess) return check(in, "sweep finish copy");
+    in->cur ^= 1;
+    in->sweeps_done += 1;
+    if (in->fast) {
+        launch_mmse_fast(g, in->fv, d.nu[in->cur], d.U, s, &in->prof);
+        return fast_refresh(in, (int)in->sweeps_done);
+    }
+    UCP_LAUNCH(in, "mmse", launch_mmse_plain(g, d, in->cur, s));
+    return refresh_costs(in, (int)in->sweeps_done);
 }
 
 int alg1_split(double I_L, double I_P, int N, int n_l) {

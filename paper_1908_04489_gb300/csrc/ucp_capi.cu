@@ -249,6 +249,25 @@ static ucp_status arg_error(const char* where, const char* why) {
     return UCP_E_ARG;
 }
 
+extern "C" ucp_status ucp_sweep_part(ucp_inst* in, int64_t i0, int64_t i1, double* f_part) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    if (i0 < 0 || i1 < i0 || i1 > in->g.n_x || (i1 > i0 && !f_part))
+        return arg_error("ucp_sweep_part", "need 0 <= i0 <= i1 <= n_x and a host buffer");
+    return inst_sweep_part(in, i0, i1, f_part);
+}
+
+extern "C" ucp_status ucp_sweep_finish(ucp_inst* in, const double* f, uint64_t n_x) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    if (!f || n_x != (uint64_t)in->g.n_x)
+        return arg_error("ucp_sweep_finish", "f must hold n_x values");
+    for (uint64_t k = 0; k < n_x; ++k)
+        if (!(fabs(f[k] / in->g.delta * (double)in->g.one) < 9.0e15))
+            return arg_error("ucp_sweep_finish", "f value not finite or out of range");
+    return inst_sweep_finish(in, f);
+}
+
 extern "C" ucp_status ucp_local_update(ucp_inst* in, int32_t n, double tau) {
     if (!in) return UCP_E_ARG;
     if (in->poisoned) return UCP_E_STATE;

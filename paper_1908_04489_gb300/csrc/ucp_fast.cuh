@@ -49,8 +49,11 @@ void launch_tc_setup(const Geom& g, const FastView& f, cudaStream_t s);
 void launch_tables(const Geom& g, const FastView& f, const double* U, double* Ud,
                    cudaStream_t s, Prof* prof);
 void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
+// The search of x0 points i_lo .. i_hi - 1 (i_hi < 0: all), from nu_in into
+// nu_out (Jacobi).
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
-                        int64_t* nu_out, int32_t* idx, cudaStream_t s);
+                        int64_t* nu_out, int32_t* idx, cudaStream_t s, int64_t i_lo = 0,
+                        int64_t i_hi = -1);
 // Blocks of each batched kernel kind for one instance (fast_plan sizes).
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind);
 int64_t batch_mmse_blocks(const Geom& g, const FastPlan& fp);

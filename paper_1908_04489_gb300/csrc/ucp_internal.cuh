@@ -248,7 +248,9 @@ void launch_udiff(const Geom& g, DevState& d, cudaStream_t s);
 // out[k] = quadrature part of the cost of nus[k] (at_x: for x0 point k).
 void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
                    double* out, cudaStream_t s, int at_x);
-void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s);
+// The search of x0 points i_lo .. i_hi - 1 (i_hi < 0: all), Jacobi.
+void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s,
+                         int64_t i_lo = 0, int64_t i_hi = -1);
 void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
                     cudaStream_t s);
 void launch_f_values(const Geom& g, const int64_t* nu, const double* x_or_null,

@@ -129,6 +129,10 @@ ucp_status inst_sweep(ucp_inst* in, int n);
 // n local-update iterations of Algorithm 1 (u0 by the local update, then u1
 // by its exact minimiser, then J), recorded in the J history like sweeps.
 ucp_status inst_local_update(ucp_inst* in, int n, double tau);
+// One sweep split by x0 ranges: the search of a range (its new f to host
+// memory), then the full new f and the rest of the sweep.
+ucp_status inst_sweep_part(ucp_inst* in, int64_t i0, int64_t i1, double* f_host);
+ucp_status inst_sweep_finish(ucp_inst* in, const double* f_host);
 // Algorithm 1's outer loop on the host around the two kinds of iteration.
 ucp_status inst_solve(ucp_inst* in, const ucp_solve_params& sp, ucp_solve_report* rep,
                       double* J_phase, int32_t* NL_rounds);
