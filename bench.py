@@ -33,6 +33,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -415,6 +416,16 @@ def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
     parts = W.partition(ps_all, world)
     ps = [ps_all[k] for k in parts[rank]]
 
+    # launch shapes tuned on a scratch batch of the same members (untimed;
+    # every shape gives the same results), then every timed batch starts
+    # with them through the context
+    from paper_1908_04489_gb300 import autotune
+    tuned, table = autotune.tuned_batch_config(
+        binding, ps, stream, torch.cuda.get_device_name(), retune=True,
+        path=os.path.join(tempfile.gettempdir(), f"ucp_tune_{os.getpid()}.json"))
+    ctx = binding.default_context()
+    ctx.set_launch_config(tuned)
+
     def batch_solve():
         b = binding.Batch(ps, stream=stream)
         b.sweep(10)
@@ -437,7 +448,15 @@ def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
         Jb = b.eval_J()
         b.close()
     t_batch = float(np.median(times)) / 1e3
+    default_ms = table[0][1] if table else None
+    tuned_ms = min(ms for _, ms in table) if table else None
+    tuning = {"config": tuned, "default_ms_per_sweep": default_ms,
+              "tuned_ms_per_sweep": tuned_ms, "configs_timed": len(table) if table else 0,
+              "how": "coordinate descent over search lanes, u1 threads per run and deferred "
+                     "blocks on a scratch batch (CUDA events over 3 sweeps, median of 3); "
+                     "every shape gives the same results"}
     if world > 1:
+        ctx.set_launch_config(autotune.default_config())
         est = [sum(W.work_estimate(ps_all[k]) for k in part) for part in parts]
         return {
             "workload": "c3: 256 Witsenhausen instances (seed 1908) partitioned over "
@@ -456,6 +475,7 @@ def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
     work = batched_work(ps, b, binding, sweeps=10)
     b.close()
     per_kernel = roofline_entries(work, kern, pipe_peaks(binding.probe_alu(stream)))
+    ctx.set_launch_config(autotune.default_config())   # the rules for every other leg
     # one at a time, same fast path
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     flush.fill_(1)
@@ -497,6 +517,7 @@ def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
         "max_abs_J_batched_vs_one_at_a_time": float(np.max(np.abs(Jb - Js))),
         "kernels_ms_per_batch": {k: v[1] for k, v in kern.items()},
         "roofline_per_kernel": per_kernel,
+        "launch_tuning": tuning,
     }
 
 

@@ -171,6 +171,33 @@ UCP_API ucp_status ucp_set_controllers(ucp_inst* inst, const double* f, uint64_t
                                const double* u1, uint64_t n_y);
 UCP_API ucp_status ucp_destroy(ucp_inst* inst);
 
+/* ---- launch shapes (the autotuner's knobs) -------------------------------- */
+
+/* How the same work is spread over threads; every valid choice gives the
+ * same results, bit for bit (the arithmetic of every candidate cost, u1
+ * target and reduction is fixed; only which thread runs it changes).  0 in
+ * any field keeps the library's rule for it. */
+typedef struct {
+    int32_t search_lanes;   /* lanes per x0 point in the screened search:
+                               4, 8 or 16 (rule: 8)                          */
+    int32_t u1_threads[5];  /* threads sharing a u1 run of 1, 2, 4, 8, 16
+                               targets: 1, 2 or 4, at most the run length
+                               (rule: 4 for launches of at most 4 blocks per
+                               SM and for runs of 16, else 1)                */
+    int32_t defer_blocks;   /* blocks of the deferred near-tie search per
+                               instance, 1..4096 (rule: one instance n_x/128
+                               within [64, 4 per SM]; a batch of 16 or more
+                               4 per instance, fewer 64 / n)                 */
+} ucp_launch_config;
+
+/* Set the launch shapes of later sweeps of an instance or a batch (captured
+ * graphs are rebuilt; a batch synchronises its stream first), or, for a
+ * context, the shapes that instances and batches created on it afterwards
+ * start with.  UCP_E_ARG for a value outside its range. */
+UCP_API ucp_status ucp_ctx_set_launch_config(ucp_ctx* ctx, const ucp_launch_config* cfg);
+UCP_API ucp_status ucp_set_launch_config(ucp_inst* inst, const ucp_launch_config* cfg);
+UCP_API ucp_status ucp_batch_set_launch_config(ucp_batch* b, const ucp_launch_config* cfg);
+
 /* ---- one sweep split over processes (Section IV-A) ----------------------- */
 
 /* For a fixed controller the u0 step of every x0 point is independent of

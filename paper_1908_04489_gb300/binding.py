@@ -93,6 +93,20 @@ class SolveReport(ctypes.Structure):
                 ("J", ctypes.c_double), ("I_L", ctypes.c_double), ("I_P", ctypes.c_double)]
 
 
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("search_lanes", ctypes.c_int32), ("u1_threads", ctypes.c_int32 * 5),
+                ("defer_blocks", ctypes.c_int32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        c = cls()
+        c.search_lanes = int(d.get("search_lanes", 0))
+        for r, v in enumerate(d.get("u1_threads", [0] * 5)):
+            c.u1_threads[r] = int(v)
+        c.defer_blocks = int(d.get("defer_blocks", 0))
+        return c
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -157,6 +171,9 @@ def load():
     L.ucp_batch_kernel_times.restype = ctypes.c_int32
     L.ucp_local_update.argtypes = [_vp, ctypes.c_int32, ctypes.c_double]
     L.ucp_sweep_part.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, _dp]
+    L.ucp_set_launch_config.argtypes = [_vp, ctypes.POINTER(LaunchConfig)]
+    L.ucp_ctx_set_launch_config.argtypes = [_vp, ctypes.POINTER(LaunchConfig)]
+    L.ucp_batch_set_launch_config.argtypes = [_vp, ctypes.POINTER(LaunchConfig)]
     L.ucp_sweep_finish.argtypes = [_vp, _dp, _u64]
     L.ucp_solve.argtypes = [_vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveReport),
                             _dp, _i32p]
@@ -224,6 +241,13 @@ class Context:
         _check(L.ucp_ctx_create(self.device, self._alloc, self._free, None,
                                 ctypes.byref(h)), "ucp_ctx_create")
         self.h = h
+
+    def set_launch_config(self, cfg: dict):
+        """Launch shapes that instances and batches created on this context
+        afterwards start with (``ucp_ctx_set_launch_config``)."""
+        c = LaunchConfig.from_dict(cfg)
+        _check(load().ucp_ctx_set_launch_config(self.h, ctypes.byref(c)),
+               "ucp_ctx_set_launch_config")
 
     def close(self):
         if self.h:
@@ -338,6 +362,12 @@ class Instance:
                                 n_cols, sz), "ucp_get_tables")
         return {"P": P, "Q": Q, "R": R, "bound": bt, "c_lo": int(sz[2]), "jlo": int(sz[3])}
 
+    def set_launch_config(self, cfg: dict):
+        """Launch shapes of later sweeps (``ucp_set_launch_config``): keys
+        search_lanes, u1_threads (5 entries), defer_blocks; 0 = the rule."""
+        c = LaunchConfig.from_dict(cfg)
+        _check(load().ucp_set_launch_config(self.h, ctypes.byref(c)), "ucp_set_launch_config")
+
     def sweep_part(self, i0: int, i1: int) -> np.ndarray:
         """The search of x0 points i0..i1-1; their new f (``ucp_sweep_part``)."""
         out = np.empty(max(0, int(i1) - int(i0)))
@@ -450,6 +480,12 @@ class Batch:
         ms = (ctypes.c_double * cap)()
         n = load().ucp_batch_kernel_times(self.h, names, launches, ms, cap)
         return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+    def set_launch_config(self, cfg: dict):
+        """Launch shapes of later batched sweeps (``ucp_batch_set_launch_config``)."""
+        c = LaunchConfig.from_dict(cfg)
+        _check(load().ucp_batch_set_launch_config(self.h, ctypes.byref(c)),
+               "ucp_batch_set_launch_config")
 
     def eval_J(self) -> np.ndarray:
         out = np.empty(len(self.params))

@@ -52,7 +52,8 @@ static int run_slot(int R) {
     return R >= 16 ? 4 : (R >= 8 ? 3 : (R >= 4 ? 2 : (R >= 2 ? 1 : 0)));
 }
 
-static int defer_blocks_per_inst(size_t n) {
+static int defer_blocks_per_inst(size_t n, const LaunchCfg& cfg) {
+    if (cfg.defer_blocks > 0) return cfg.defer_blocks;
     return n >= 16 ? kDeferBlocksBatch : (int)(64 / n);
 }
 
@@ -62,7 +63,7 @@ ucp_status batchset_refresh(BatchSet& bs, const std::vector<ucp_inst*>& members,
     bs.desc.resize(n);
     for (size_t k = 0; k < n; ++k) {
         bs.desc[k] = describe_inst(members[k]);
-        bs.desc[k].defer_blocks = defer_blocks_per_inst(n);
+        bs.desc[k].defer_blocks = defer_blocks_per_inst(n, bs.cfg);
     }
     if (n) cudaMemcpyAsync(bs.insts, bs.desc.data(), sizeof(InstDev) * n,
                            cudaMemcpyHostToDevice, s);
@@ -73,14 +74,15 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
                           cudaStream_t s) {
     const size_t n = members.size();
     std::vector<BlockRef> maps[kBKinds], smap, mmaps[5], dmap;
-    const int defer_blocks = defer_blocks_per_inst(n);
+    const int defer_blocks = defer_blocks_per_inst(n, bs.cfg);
+    const int lanes = bs.cfg.search_lanes ? bs.cfg.search_lanes : kSearchLanesDefault;
     for (size_t k = 0; k < n; ++k) {
         const ucp_inst* in = members[k];
         for (int kind = 1; kind < kBKinds; ++kind) {
             const int64_t nb = batch_blocks(in->g, in->fv, kind);
             for (int64_t x = 0; x < nb; ++x) maps[kind].push_back({(int32_t)k, (int32_t)x});
         }
-        const int64_t ns = batch_blocks(in->g, in->fv, kBSearch);
+        const int64_t ns = search_blocks(in->g, lanes);
         for (int64_t x = 0; x < ns; ++x) smap.push_back({(int32_t)k, (int32_t)x});
         for (int x = 0; x < defer_blocks; ++x) dmap.push_back({(int32_t)k, x});
         std::vector<BlockRef>& mm = mmaps[run_slot(in->fv.run)];
@@ -133,6 +135,8 @@ ucp_status batchset_build(BatchSet& bs, const std::vector<ucp_inst*>& members,
     bl.search_blocks = (int64_t)smap.size();
     bl.defer_map = bs.maps + doff;
     bl.defer_blocks = (int64_t)dmap.size();
+    bl.search_lanes = lanes;
+    for (int r = 0; r < 5; ++r) bl.u1_threads[r] = bs.cfg.u1_threads[r];
     for (int r = 0; r < 5; ++r) {
         bl.mmse_map[r] = bs.maps + moff[r];
         bl.mmse_blocks[r] = (int64_t)mmaps[r].size();
@@ -291,6 +295,7 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
         b->members.push_back(in);
     }
     b->bs.arena = &b->arena;
+    b->bs.cfg = ctx->cfg;
     b->ss.arena = &b->arena;
     b->J_gather = (double*)b->arena.get(2 * sizeof(double) * (size_t)n);
     ucp_status st = b->J_gather ? batchset_build(b->bs, b->members, b->stream) : UCP_E_NOMEM;
@@ -366,6 +371,26 @@ extern "C" UCP_API ucp_status ucp_batch_eval_J(ucp_batch* b, double* J_out) {
             set_error("%s%s", "ucp_batch_eval_J: a tensor-core wait timed out", "");
             return UCP_E_TIMEOUT;
         }
+    return UCP_OK;
+}
+
+extern "C" UCP_API ucp_status ucp_batch_set_launch_config(ucp_batch* b,
+                                                          const ucp_launch_config* c) {
+    if (!b) return UCP_E_ARG;
+    if (b->poisoned) return UCP_E_STATE;
+    LaunchCfg cfg;
+    if (const char* why = launch_cfg_from(c, &cfg)) {
+        set_error("ucp_batch_set_launch_config: %s%s", why, "");
+        return UCP_E_ARG;
+    }
+    // the captured sweep holds the old block maps: drop it, rebuild them
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(b, "ucp_batch_set_launch_config");
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_tried = false;
+    b->bs.cfg = cfg;
+    if (batchset_build(b->bs, b->members, b->stream) != UCP_OK)
+        return fail(b, "ucp_batch_set_launch_config");
     return UCP_OK;
 }
 

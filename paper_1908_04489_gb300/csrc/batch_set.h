@@ -18,6 +18,7 @@ struct BatchSet {
     std::vector<InstDev> desc;
     std::vector<BlockRef> host_maps;
     BatchLaunch bl{};
+    LaunchCfg cfg;                // launch shapes (results do not depend on them)
 };
 
 // Descriptor of a fast-path instance from its host-side state.

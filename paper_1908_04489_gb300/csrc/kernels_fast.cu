@@ -623,7 +623,7 @@ constexpr int kKeep = 12;   // candidates per lane whose screened costs are kept
 constexpr int kGroupScratch = kKeep * 3 / 2 > kTieBatch ? kKeep * 3 / 2 : kTieBatch;
 // lanes per x0 point: the screening search, and the deferred (block-
 // cooperative) search, whose second tier takes up to kCoopG members at once
-constexpr int kFastG = 8;
+constexpr int kFastG = kSearchLanesDefault;
 constexpr int kCoopG = 16;
 
 // How resolve() settles a stage with several values still in play:
@@ -923,6 +923,7 @@ __device__ __forceinline__ void search_deferred_body(const Geom& g, const FastVi
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kSearchT, 6) k_search_fast(Geom g, FastView f,
                                                      const int64_t* __restrict__ nu_pre,
                                                      int64_t* __restrict__ nu_out,
@@ -930,8 +931,8 @@ __global__ void __launch_bounds__(kSearchT, 6) k_search_fast(Geom g, FastView f,
                                                      int32_t* n_exact, int64_t i_lo,
                                                      int64_t i_hi) {
     __shared__ double tie_smem[kSearchT * kGroupScratch];
-    search_body<kFastG>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x,
-                        i_lo, i_hi);
+    search_body<G>(g, f, nu_pre, nu_out, idx_out, n_exact, tie_smem, blockIdx.x, i_lo,
+                   i_hi);
 }
 
 // Blocks of the deferred search of one instance: one per 128 x0 points
@@ -1072,12 +1073,13 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
     return r;
 }
 
+template <int G>
 __global__ void __launch_bounds__(kSearchT, 6) kb_search(const InstDev* insts, const BlockRef* map) {
     __shared__ InstDev sd;
     const BlockRef r = stage(insts, map, sd);
     __shared__ double tie_smem[kSearchT * kGroupScratch];
-    search_body<kFastG>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx,
-                        sd.f.n_exact, tie_smem, r.local);
+    search_body<G>(sd.g, sd.f, sd.nu[sd.cur], sd.nu[sd.cur ^ 1], sd.idx, sd.f.n_exact,
+                   tie_smem, r.local);
 }
 
 __global__ void __launch_bounds__(kCoopT, 2) kb_search_deferred(const InstDev* insts,
@@ -1148,19 +1150,32 @@ void launch_batch_setup_fast(const SetupLaunch& sl, cudaStream_t s) {
 
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
                         int64_t* nu_out, int32_t* idx, cudaStream_t s, int64_t i_lo,
-                        int64_t i_hi) {
+                        int64_t i_hi, const LaunchCfg* cfg) {
     const int64_t hi = i_hi < 0 ? g.n_x : i_hi;
-    const int64_t threads = (hi - i_lo) * (int64_t)kFastG;
+    const int G = cfg && cfg->search_lanes ? cfg->search_lanes : kFastG;
+    const int64_t threads = (hi - i_lo) * (int64_t)G;
     if (threads <= 0) return;
-    k_search_fast<<<blocks(threads, kSearchT), kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx,
-                                                                  f.n_exact, i_lo, hi);
-    k_search_deferred<<<defer_blocks_of(g), kCoopT, 0, s>>>(g, f, nu_in, nu_out, idx,
-                                                            f.n_exact);
+    const unsigned nb = blocks(threads, kSearchT);
+    switch (G) {
+        case 4: k_search_fast<4><<<nb, kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx, f.n_exact,
+                                                        i_lo, hi); break;
+        case 16: k_search_fast<16><<<nb, kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx,
+                                                          f.n_exact, i_lo, hi); break;
+        default: k_search_fast<8><<<nb, kSearchT, 0, s>>>(g, f, nu_in, nu_out, idx, f.n_exact,
+                                                         i_lo, hi); break;
+    }
+    const unsigned nd = cfg && cfg->defer_blocks ? (unsigned)cfg->defer_blocks
+                                                 : defer_blocks_of(g);
+    k_search_deferred<<<nd, kCoopT, 0, s>>>(g, f, nu_in, nu_out, idx, f.n_exact);
+}
+
+int64_t search_blocks(const Geom& g, int lanes) {
+    return (g.n_x * lanes + kSearchT - 1) / kSearchT;
 }
 
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
-        case kBSearch: return (g.n_x * kFastG + kSearchT - 1) / kSearchT;
+        case kBSearch: return search_blocks(g, kFastG);
         case kBTile:
         case kBRun: return u1_batch_blocks(g, fp, kind);
         case kBPerY: return (g.n_y + 255) / 256;
@@ -1180,8 +1195,14 @@ void launch_batch_sweep(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
 void launch_batch_search(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
     const InstDev* d = bl.insts;
     ProfScope ps(prof, "search");
-    if (bl.search_blocks)
-        kb_search<<<(unsigned)bl.search_blocks, kSearchT, 0, s>>>(d, bl.search_map);
+    if (bl.search_blocks) {
+        const unsigned nb = (unsigned)bl.search_blocks;
+        switch (bl.search_lanes) {
+            case 4: kb_search<4><<<nb, kSearchT, 0, s>>>(d, bl.search_map); break;
+            case 16: kb_search<16><<<nb, kSearchT, 0, s>>>(d, bl.search_map); break;
+            default: kb_search<8><<<nb, kSearchT, 0, s>>>(d, bl.search_map); break;
+        }
+    }
     if (bl.defer_blocks)
         kb_search_deferred<<<(unsigned)bl.defer_blocks, kCoopT, 0, s>>>(d, bl.defer_map);
 }

@@ -697,12 +697,19 @@ __global__ void __launch_bounds__(kU1Runs * P) kb_u1_main(const InstDev* insts,
 // Batched launches split runs of 16 targets whatever their size: one thread
 // per 16-target run needs 168 registers and a large unrolled body (measured
 // on 256 uneven instances: 34.1 ms against 39.7 ms per ten sweeps).
+// P threads per run (0: the rule above).  Every target gets the same
+// operations whichever P, so the results do not depend on it.
 template <int R>
-void launch_kb_u1_main(unsigned nb, const InstDev* d, const BlockRef* m, cudaStream_t s) {
-    if (nb <= kU1SplitMaxBlocks || R == 16)
-        kb_u1_main<R, u1_parts<R>()><<<nb, kU1Runs * u1_parts<R>(), 0, s>>>(d, m);
-    else
+void launch_kb_u1_main(unsigned nb, const InstDev* d, const BlockRef* m, cudaStream_t s,
+                       int P) {
+    if (P == 0) P = (nb <= kU1SplitMaxBlocks || R == 16) ? u1_parts<R>() : 1;
+    if (P >= 4 && R >= 4) {
+        kb_u1_main<R, (R >= 4 ? 4 : 1)><<<nb, kU1Runs * 4, 0, s>>>(d, m);
+    } else if (P >= 2 && R >= 2) {
+        kb_u1_main<R, (R >= 2 ? 2 : 1)><<<nb, kU1Runs * 2, 0, s>>>(d, m);
+    } else {
         kb_u1_main<R, 1><<<nb, kU1Runs, 0, s>>>(d, m);
+    }
 }
 
 template <int R>
@@ -835,12 +842,13 @@ void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
             if (bl.mmse_blocks[r] == 0) continue;
             const unsigned nb = (unsigned)bl.mmse_blocks[r];
             const BlockRef* m = bl.mmse_map[r];
+            const int P = bl.u1_threads[r];
             switch (r) {
-                case 0: launch_kb_u1_main<1>(nb, d, m, s); break;
-                case 1: launch_kb_u1_main<2>(nb, d, m, s); break;
-                case 2: launch_kb_u1_main<4>(nb, d, m, s); break;
-                case 3: launch_kb_u1_main<8>(nb, d, m, s); break;
-                default: launch_kb_u1_main<16>(nb, d, m, s); break;
+                case 0: launch_kb_u1_main<1>(nb, d, m, s, P); break;
+                case 1: launch_kb_u1_main<2>(nb, d, m, s, P); break;
+                case 2: launch_kb_u1_main<4>(nb, d, m, s, P); break;
+                case 3: launch_kb_u1_main<8>(nb, d, m, s, P); break;
+                default: launch_kb_u1_main<16>(nb, d, m, s, P); break;
             }
         }
     }

@@ -355,6 +355,7 @@ static ucp_status fast_refresh(ucp_inst* in, int slot) {
 ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
                      const Geom& g, cudaStream_t stream, bool own_setup, void* slab) {
     in->ctx = ctx;
+    in->cfg = ctx->cfg;
     in->params = p;
     in->params.init_table = nullptr;
     in->g = g;
@@ -469,6 +470,7 @@ static bool solo_ensure(ucp_inst* in) {
     if (in->solo_failed) return false;
     in->solo = new BatchSet();
     in->solo->arena = &in->arena;
+    in->solo->cfg = in->cfg;
     std::vector<ucp_inst*> one{in};
     if (batchset_build(*in->solo, one, in->stream) != UCP_OK) {
         cudaGetLastError();
@@ -491,7 +493,7 @@ static bool solo_sweeps(ucp_inst* in, int n) {
                 cudaSuccess)
                 break;
             launch_search_fast(in->g, in->fv, in->d.nu[c], in->d.nu[c ^ 1], in->d.idx,
-                               in->stream);
+                               in->stream, 0, -1, &in->cfg);
             launch_batch_rest(in->solo->bl, in->stream);
             if (cudaStreamEndCapture(in->stream, &graph) == cudaSuccess && graph) {
                 if (cudaGraphInstantiate(&in->solo_graph[c], graph, 0) != cudaSuccess)
@@ -522,12 +524,23 @@ static bool solo_launches(ucp_inst* in, int n) {
     for (int k = 0; k < n; ++k) {
         UCP_LAUNCH(in, "search", launch_search_fast(in->g, in->fv, in->d.nu[in->cur],
                                                     in->d.nu[in->cur ^ 1], in->d.idx,
-                                                    in->stream));
+                                                    in->stream, 0, -1, &in->cfg));
         launch_batch_rest(in->solo->bl, in->stream, prof);
         in->cur ^= 1;
     }
     in->sweeps_done += n;
     return true;
+}
+
+ucp_status inst_set_launch_cfg(ucp_inst* in, const LaunchCfg& cfg) {
+    in->cfg = cfg;
+    solo_drop(in);
+    if (in->solo) {
+        in->solo->cfg = cfg;
+        std::vector<ucp_inst*> one{in};
+        if (batchset_build(*in->solo, one, in->stream) != UCP_OK) return check(in, "launch config");
+    }
+    return UCP_OK;
 }
 
 ucp_status inst_sweep(ucp_inst* in, int n) {
@@ -542,7 +555,8 @@ ucp_status inst_sweep(ucp_inst* in, int n) {
     if (in->fast) {
         for (int k = 0; k < n; ++k) {
             UCP_LAUNCH(in, "search", launch_search_fast(g, in->fv, d.nu[in->cur],
-                                                        d.nu[in->cur ^ 1], d.idx, s));
+                                                        d.nu[in->cur ^ 1], d.idx, s, 0, -1,
+                                                        &in->cfg));
             in->cur ^= 1;
             launch_mmse_fast(g, in->fv, d.nu[in->cur], d.U, s, &in->prof);
             in->sweeps_done += 1;
@@ -600,7 +614,8 @@ ucp_status inst_sweep_part(ucp_inst* in, int64_t i0, int64_t i1, double* f_host)
     cudaStream_t s = in->stream;
     if (in->fast) {
         UCP_LAUNCH(in, "search", launch_search_fast(g, in->fv, d.nu[in->cur],
-                                                    d.nu[in->cur ^ 1], d.idx, s, i0, i1));
+                                                    d.nu[in->cur ^ 1], d.idx, s, i0, i1,
+                                                    &in->cfg));
     } else {
         UCP_LAUNCH(in, "search", launch_search_plain(g, d, in->cur, s, i0, i1));
     }

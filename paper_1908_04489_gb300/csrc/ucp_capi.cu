@@ -249,6 +249,43 @@ static ucp_status arg_error(const char* where, const char* why) {
     return UCP_E_ARG;
 }
 
+namespace ucp {
+const char* launch_cfg_from(const ucp_launch_config* c, LaunchCfg* out) {
+    if (!c) return "NULL configuration";
+    if (c->search_lanes != 0 && c->search_lanes != 4 && c->search_lanes != 8 &&
+        c->search_lanes != 16)
+        return "search_lanes must be 0, 4, 8 or 16";
+    for (int r = 0; r < 5; ++r) {
+        const int P = c->u1_threads[r];
+        if (P != 0 && P != 1 && P != 2 && P != 4) return "u1_threads must be 0, 1, 2 or 4";
+        if (P > (1 << r)) return "u1_threads above the run length";
+    }
+    if (c->defer_blocks < 0 || c->defer_blocks > 4096)
+        return "defer_blocks must be in 0..4096";
+    out->search_lanes = c->search_lanes;
+    for (int r = 0; r < 5; ++r) out->u1_threads[r] = c->u1_threads[r];
+    out->defer_blocks = c->defer_blocks;
+    return nullptr;
+}
+}  // namespace ucp
+
+extern "C" ucp_status ucp_ctx_set_launch_config(ucp_ctx* ctx, const ucp_launch_config* c) {
+    if (!ctx) return UCP_E_ARG;
+    LaunchCfg cfg;
+    if (const char* why = launch_cfg_from(c, &cfg))
+        return arg_error("ucp_ctx_set_launch_config", why);
+    ctx->cfg = cfg;
+    return UCP_OK;
+}
+
+extern "C" ucp_status ucp_set_launch_config(ucp_inst* in, const ucp_launch_config* c) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    LaunchCfg cfg;
+    if (const char* why = launch_cfg_from(c, &cfg)) return arg_error("ucp_set_launch_config", why);
+    return inst_set_launch_cfg(in, cfg);
+}
+
 extern "C" ucp_status ucp_sweep_part(ucp_inst* in, int64_t i0, int64_t i1, double* f_part) {
     if (!in) return UCP_E_ARG;
     if (in->poisoned) return UCP_E_STATE;

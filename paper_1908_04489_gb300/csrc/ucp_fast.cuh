@@ -53,7 +53,9 @@ void launch_batch_tables(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nul
 // nu_out (Jacobi).
 void launch_search_fast(const Geom& g, const FastView& f, const int64_t* nu_in,
                         int64_t* nu_out, int32_t* idx, cudaStream_t s, int64_t i_lo = 0,
-                        int64_t i_hi = -1);
+                        int64_t i_hi = -1, const LaunchCfg* cfg = nullptr);
+// Blocks of the screened search with `lanes` lanes per x0 point.
+int64_t search_blocks(const Geom& g, int lanes);
 // Blocks of each batched kernel kind for one instance (fast_plan sizes).
 int64_t batch_blocks(const Geom& g, const FastPlan& fp, int kind);
 int64_t batch_mmse_blocks(const Geom& g, const FastPlan& fp);

@@ -165,6 +165,16 @@ struct InstDev {
     int32_t defer_blocks;  // blocks of the deferred search for this instance
 };
 
+// Launch shapes that spread the same work differently over threads: every
+// valid choice gives the same results, bit for bit (the autotuner's knobs).
+constexpr int kSearchLanesDefault = 8;   // lanes per x0 point of the search
+struct LaunchCfg {
+    int search_lanes = 0;                 // lanes per x0 point in the search: 4, 8, 16 (0: 8)
+    int u1_threads[5] = {0, 0, 0, 0, 0};  // threads per u1 run of 1, 2, 4, 8, 16 targets:
+                                          // 1, 2 or 4, at most the run length (0: the rule)
+    int defer_blocks = 0;                 // deferred-search blocks per instance (0: the rule)
+};
+
 // Block of a batched launch: which instance, which block of its own grid.
 struct BlockRef {
     int32_t inst;
@@ -188,6 +198,8 @@ struct BatchLaunch {
     int64_t mmse_blocks[5];
     const BlockRef* defer_map;     // deferred (near-tie) search
     int64_t defer_blocks;
+    int search_lanes;              // lanes per x0 point of the search (4, 8, 16)
+    int u1_threads[5];             // threads per u1 run per run length (0: the rule)
 };
 
 // Set-up of a fast instance done by batched launches (instances created

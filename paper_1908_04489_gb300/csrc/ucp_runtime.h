@@ -13,6 +13,7 @@ struct ucp_ctx {
     ucp_alloc_fn alloc = nullptr;
     ucp_free_fn free_fn = nullptr;
     void* user = nullptr;
+    ucp::LaunchCfg cfg;   // launch shapes that new instances and batches start with
 };
 
 namespace ucp {
@@ -106,6 +107,7 @@ struct ucp_inst {
     cudaGraphExec_t solo_graph[2] = {nullptr, nullptr};
     bool solo_tried = false;
     bool solo_failed = false;   // the one-member batch set could not be built
+    ucp::LaunchCfg cfg;         // launch shapes (results do not depend on them)
 };
 
 namespace ucp {
@@ -129,6 +131,10 @@ ucp_status inst_sweep(ucp_inst* in, int n);
 // n local-update iterations of Algorithm 1 (u0 by the local update, then u1
 // by its exact minimiser, then J), recorded in the J history like sweeps.
 ucp_status inst_local_update(ucp_inst* in, int n, double tau);
+// Checks a public launch configuration; nullptr or the reason it is invalid.
+const char* launch_cfg_from(const ucp_launch_config* c, LaunchCfg* out);
+// New launch shapes for later sweeps (graphs and block maps rebuilt).
+ucp_status inst_set_launch_cfg(ucp_inst* in, const LaunchCfg& cfg);
 // One sweep split by x0 ranges: the search of a range (its new f to host
 // memory), then the full new f and the rest of the sweep.
 ucp_status inst_sweep_part(ucp_inst* in, int64_t i0, int64_t i1, double* f_host);
