@@ -119,7 +119,7 @@ FLOPS_SEARCH_CAND = 104.0
 # DRAM bytes per launch from one-kernel ncu captures of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum; cold cache), keyed by the
 # profiled kernel group; None where the kernel changed since its capture.
-TRAFFIC_BYTES = {"c2": {"search": 0.21e6, "tables": 1.70e6, "mmse_main": 0.07e6}}
+TRAFFIC_BYTES = {"c2": {"search": 0.257e6, "tables": 1.70e6, "mmse_main": 0.074e6}}
 TRAFFIC_SOURCE = "profiles/hot_kernels_c2_ncu_full.md"
 
 # kernels launched per timed group of the library's profiler (the groups not
@@ -848,6 +848,9 @@ def run_profile(args):
     import torch
     from paper_1908_04489_gb300 import binding, build
     build.build()
+    if args.search_lanes:
+        binding.load()
+        binding.default_context().set_launch_config({"search_lanes": args.search_lanes})
     if args.workload == "c3":
         # the first --batch-n instances of the batched workload, swept as one
         # batch (captured-graph sweeps on a non-default stream)
@@ -926,6 +929,11 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--search-lanes", type=int, default=0,
+                    help="with --profile-sweeps: lanes per x0 point of the search")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving leg (with --serve-requests 20000: the c4 "
+                         "workload at its own size), one JSON line")
     ap.add_argument("--c5-steps", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rates", type=float, nargs="+",
@@ -941,6 +949,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving_only:
+        import torch
+        from paper_1908_04489_gb300 import binding, build
+        build.build()
+        binding.load()
+        print(json.dumps(measure_serving(args, binding, torch)))
     elif args.profile_sweeps:
         run_profile(args)
     else:
