@@ -210,12 +210,15 @@ def test_c5_trajectory_against_the_oracle(binding):
             if pair is None and shas[-1] != ref["nu_sha"][s + 1]:
                 pair = (prev, st)
         Jh = inst.J_history()
-    compare_stored(o, ref, st["f"], st["U"], Jh, "c5")
     first = next((s for s in range(len(shas)) if shas[s] != ref["nu_sha"][s]), None)
-    print("c5: max |dJ|", float(np.max(np.abs(Jh - np.asarray(ref["J"])))),
-          "first differing sweep:", first)
+    dJ = np.abs(Jh - np.asarray(ref["J"]))
+    print("c5: first differing sweep:", first, "|dJ| per sweep:", [f"{x:.2e}" for x in dJ])
     if first is None:
+        compare_stored(o, ref, st["f"], st["U"], Jh, "c5")
         return
     assert first >= 1
+    # up to and including the first differing sweep both sides follow the
+    # same controller, so J agrees to rounding there
+    assert np.max(dJ[:first + 1]) <= T.TOL_J, dJ[:first + 1]
     rep = T.first_divergence(o, pair[0], pair[1], "c5")
     print(f"c5: sweep {first}:", json.dumps(rep))
