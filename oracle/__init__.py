@@ -20,19 +20,20 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ucp_oracle.c")
+_SRC2 = os.path.join(_HERE, "ucp_oracle2d.c")
 _OUT = os.path.join(_HERE, "_build", "libucp_oracle.so")
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc: FP64, no fused multiply-add, OpenMP."""
+    srcs = (_SRC, _SRC[:-1] + "h", _SRC2, _SRC2[:-1] + "h")
     if (not force and os.path.exists(_OUT)
-            and os.path.getmtime(_OUT) >= max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(_SRC[:-1] + "h"))):
+            and os.path.getmtime(_OUT) >= max(os.path.getmtime(x) for x in srcs)):
         return _OUT
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     tmp = _OUT + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, _SRC2, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _OUT)
     return _OUT
@@ -64,8 +65,8 @@ def build_variant(src_text: str, out_path: str) -> str:
     with open(src, "w") as fh:
         fh.write(src_text)
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                    "-fno-fast-math", "-fopenmp", "-I", _HERE, "-o", out_path, src, "-lm"],
-                   check=True)
+                    "-fno-fast-math", "-fopenmp", "-I", _HERE, "-o", out_path, src, _SRC2,
+                    "-lm"], check=True)
     return out_path
 
 
@@ -288,3 +289,138 @@ class Oracle:
         if rc != 0:
             raise ValueError("oracle solve failed")
         return dict(nu=nu, U=U, J=Jh, idx=idx)
+
+
+# ---- the 2-dimensional Witsenhausen counterexample (Section V-D) -----------
+
+class _Params2(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("delta", ctypes.c_double), ("x_half", ctypes.c_double),
+                ("w_half", ctypes.c_double), ("y_half", ctypes.c_double),
+                ("cand_half", ctypes.c_double), ("n_coarse", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("n_nbr", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def _configure2(L):
+    P = ctypes.POINTER(_Params2)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.orc2_sizes.argtypes = [P, i64p, i64p, i64p, i64p, i32p]
+    L.orc2_weights.argtypes = [P, dp, dp]
+    L.orc2_init.argtypes = [P, ctypes.c_int, dp, i64p]
+    L.orc2_S.argtypes = [P, dp, ctypes.c_int64, ctypes.c_int64]
+    L.orc2_S.restype = ctypes.c_double
+    L.orc2_cost.argtypes = [P, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+    L.orc2_cost.restype = ctypes.c_double
+    L.orc2_search.argtypes = [P, i64p, dp, i64p, i32p, ctypes.c_int64, ctypes.c_int64]
+    L.orc2_candidates.argtypes = [P, i64p, dp, ctypes.c_int64, i64p, dp]
+    L.orc2_mmse.argtypes = [P, i64p, dp, ctypes.c_int64, ctypes.c_int64]
+    L.orc2_J.argtypes = [P, i64p, dp]
+    L.orc2_J.restype = ctypes.c_double
+    return L
+
+
+class Oracle2D:
+    """One instance of the 2-D Witsenhausen counterexample on the oracle.
+    ``params``: k, sigma, delta, x_half, w_half, y_half, cand_half, n_coarse,
+    n_levels, n_nbr.  Controllers are int64 lattice indices of shape
+    (n_x * n_x, 2); u1 tables are arrays of shape (n_y * n_y, 2)."""
+
+    def __init__(self, params, library=None):
+        self._L = library
+        self.params = dict(params)
+        self._p = _Params2(*(float(params[k]) for k in
+                             ("k", "sigma", "delta", "x_half", "w_half", "y_half",
+                              "cand_half")),
+                           int(params["n_coarse"]), int(params["n_levels"]),
+                           int(params["n_nbr"]), 0)
+        n = [ctypes.c_int64() for _ in range(4)]
+        sh = ctypes.c_int32()
+        if self._lib().orc2_sizes(ctypes.byref(self._p), *(ctypes.byref(v) for v in n),
+                                  ctypes.byref(sh)) != 0:
+            raise ValueError(f"invalid 2-D oracle parameters: {params}")
+        self.n_x, self.n_w, self.n_y, self.n_cand = (v.value for v in n)
+        self.shift = sh.value
+        self.N = self.n_x * self.n_x
+
+    def _lib(self):
+        L = self._L if self._L is not None else lib()
+        if not getattr(L, "_orc2", False):
+            _configure2(L)
+            L._orc2 = True
+        return L
+
+    def value(self, nu):
+        nu = np.asarray(nu, dtype=np.int64)
+        return np.ldexp(nu.astype(np.float64) * self.params["delta"], -self.shift)
+
+    def grid(self, n):
+        return (np.arange(n) - (n - 1) // 2) * self.params["delta"]
+
+    def weights(self):
+        px = np.empty(self.N)
+        phi = np.empty(self.n_w * self.n_w)
+        self._lib().orc2_weights(ctypes.byref(self._p), _dp(px), _dp(phi))
+        return px, phi
+
+    def init(self, kind=0, table=None):
+        nu = np.empty((self.N, 2), dtype=np.int64)
+        tab = None if table is None else np.ascontiguousarray(table, np.float64)
+        if self._lib().orc2_init(ctypes.byref(self._p), int(kind),
+                                 _dp(tab) if tab is not None else None, _i64p(nu)) != 0:
+            raise ValueError("2-D oracle init failed")
+        return nu
+
+    def S(self, U, nu1, nu2):
+        U = np.ascontiguousarray(U, np.float64)
+        return float(self._lib().orc2_S(ctypes.byref(self._p), _dp(U), int(nu1), int(nu2)))
+
+    def cost(self, U, i, nu1, nu2):
+        U = np.ascontiguousarray(U, np.float64)
+        return float(self._lib().orc2_cost(ctypes.byref(self._p), _dp(U), int(i), int(nu1),
+                                           int(nu2)))
+
+    def search(self, nu_pre, U, i0=0, i1=None):
+        i1 = self.N if i1 is None else i1
+        nu_pre = np.ascontiguousarray(nu_pre, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        out = nu_pre.copy()
+        idx = np.full(self.N, -1, dtype=np.int32)
+        self._lib().orc2_search(ctypes.byref(self._p), _i64p(nu_pre), _dp(U), _i64p(out),
+                                _i32p(idx), int(i0), int(i1))
+        return out, idx
+
+    def candidates(self, nu_pre, U, i):
+        nu_pre = np.ascontiguousarray(nu_pre, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        nus = np.empty((self.n_cand, 2), dtype=np.int64)
+        gs = np.empty(self.n_cand)
+        k = self._lib().orc2_candidates(ctypes.byref(self._p), _i64p(nu_pre), _dp(U), int(i),
+                                        _i64p(nus), _dp(gs))
+        return nus, gs, int(k)
+
+    def mmse(self, nu, t0=0, t1=None):
+        t1 = self.n_y * self.n_y if t1 is None else t1
+        nu = np.ascontiguousarray(nu, np.int64)
+        U = np.full((self.n_y * self.n_y, 2), np.nan)
+        self._lib().orc2_mmse(ctypes.byref(self._p), _i64p(nu), _dp(U), int(t0), int(t1))
+        return U
+
+    def J(self, nu, U):
+        nu = np.ascontiguousarray(nu, np.int64)
+        U = np.ascontiguousarray(U, np.float64)
+        return float(self._lib().orc2_J(ctypes.byref(self._p), _i64p(nu), _dp(U)))
+
+    def solve(self, n_sweeps, table=None):
+        """init -> U = mmse(f) -> n_sweeps x {search, mmse, J}."""
+        nu = self.init(0 if table is None else 2, table)
+        U = self.mmse(nu)
+        Jh = [self.J(nu, U)]
+        idx = None
+        for _ in range(n_sweeps):
+            nu, idx = self.search(nu, U)
+            U = self.mmse(nu)
+            Jh.append(self.J(nu, U))
+        return dict(nu=nu, U=U, J=np.array(Jh), idx=idx)
