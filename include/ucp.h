@@ -420,6 +420,72 @@ UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
                                          const double* f_dev, double* u1_dev,
                                          void* stream);
 
+/* ---- the 2-dimensional Witsenhausen counterexample (Section V-D) -------- */
+
+/* The state, both controllers and the observation are vectors in R^2:
+ *   x1 = x0 + u0(x0),  y1 = x1 + w,  x2 = x1 - u1(y1),
+ *   J = (1/2) E[k^2 |u0|^2 + |x2|^2],  x0 ~ N(0, sigma^2 I),  w ~ N(0, I)
+ * (the factor 1/2 makes J per dimension, so that it compares with the
+ * scalar problem's).  The sweep is the scalar one in two dimensions, in FP64
+ * with every sum in a fixed order:
+ *   - u0 step, for every x0 point the first minimiser of
+ *     g(u; x) = k^2 |u - x|^2 + sum_cd phi_c phi_d |u - U^(u + w_cd)|^2
+ *     (U^ the bilinear interpolant of the u1 tables, held constant beyond
+ *     them) over the candidate list: the incumbent; f at the other points of
+ *     the (2 n_nbr + 1)^2 window around the point (the incumbent where the
+ *     window leaves the grid); the n_coarse x n_coarse coarse grid
+ *     c_j = (2j - (n_coarse - 1)) (q/2) delta per axis, q = 2 ceil(cand_half /
+ *     ((n_coarse - 1) delta)); then n_levels levels of the 8 neighbours
+ *     best + (s, t) q delta 2^-level, (s, t) in {-1, 0, 1}^2 \ (0, 0) in
+ *     row-major order, around the best so far;
+ *   - u1 step, U(y) = E[x1 | y1 = y] per component (Section IV-C);
+ *   - J in index order.
+ * Grids: one spacing delta for x0 (n_x x n_x points over [-x_half,
+ * x_half]^2), w (n_w x n_w over [-w_half, w_half]^2) and y (n_y x n_y);
+ * point (a, b) is ((a - h) delta, (b - h) delta) with flat index a n + b.
+ * Controller values lie on the lattice delta 2^-n_levels Z per component. */
+typedef struct {
+    double k, sigma, delta;
+    double x_half, w_half, y_half, cand_half;   /* multiples of delta          */
+    int32_t n_coarse;   /* coarse values per axis, 2..64                       */
+    int32_t n_levels;   /* refinement levels, 0..40                            */
+    int32_t n_nbr;      /* window radius, 0..8                                 */
+    int32_t reserved;   /* must be 0                                           */
+} ucp2_params;
+
+typedef struct ucp_inst2 ucp_inst2;
+
+/* Sizes per axis and the candidate-list length (outputs may be NULL).
+ * UCP_E_ARG when params are invalid or the grids exceed n_x <= 441,
+ * n_y <= 2049, n_w <= 1025. */
+UCP_API ucp_status ucp2_plan(const ucp2_params* params, uint64_t* n_x, uint64_t* n_w,
+                             uint64_t* n_y, uint64_t* n_cand);
+/* New instance on `stream` (cudaStream_t as void*): the weights, the start
+ * (init_f NULL: the identity f(x) = x of Section III-D; else host, n_x^2
+ * pairs f[2 i + k], rounded to the lattice), its u1 step and J as entry 0
+ * of the J history.  Device memory comes from the context's allocator. */
+UCP_API ucp_status ucp2_create(ucp_ctx* ctx, const ucp2_params* params,
+                               const double* init_f, void* stream, ucp_inst2** out);
+/* n sweeps (u0 step, u1 step, J), asynchronous on the instance's stream. */
+UCP_API ucp_status ucp2_sweep(ucp_inst2* inst, int32_t n);
+/* J after 0, 1, ... sweeps into host `out` (at most n entries). */
+UCP_API ucp_status ucp2_J_history(ucp_inst2* inst, double* out, uint64_t n,
+                                  uint64_t* n_written);
+/* Host copies (each may be NULL; lengths in elements): f (2 n_x^2,
+ * f[2 i + k]), the u1 tables (2 n_y^2, U[2 t + k]) and the winners' list
+ * positions of the last sweep (n_x^2; -1 before the first sweep).  UCP_E_ARG
+ * if a buffer is shorter than that. */
+UCP_API ucp_status ucp2_get_controllers(ucp_inst2* inst, double* f, uint64_t f_len,
+                                        double* u1, uint64_t u1_len, int32_t* idx,
+                                        uint64_t idx_len);
+/* Replace f (host, 2 n_x^2 values, rounded to the lattice) and, when u1 is
+ * not NULL, the u1 tables (2 n_y^2); with u1 NULL the u1 step runs.  J is
+ * recomputed into the history's current entry.  UCP_E_ARG for other lengths
+ * or values beyond the lattice's range. */
+UCP_API ucp_status ucp2_set_controllers(ucp_inst2* inst, const double* f, uint64_t f_len,
+                                        const double* u1, uint64_t u1_len);
+UCP_API ucp_status ucp2_destroy(ucp_inst2* inst);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,23 @@ class LaunchConfig(ctypes.Structure):
         return c
 
 
+class Params2(ctypes.Structure):
+    """ucp2_params: the 2-dimensional problem of Section V-D."""
+    _fields_ = [("k", ctypes.c_double), ("sigma", ctypes.c_double), ("delta", ctypes.c_double),
+                ("x_half", ctypes.c_double), ("w_half", ctypes.c_double),
+                ("y_half", ctypes.c_double), ("cand_half", ctypes.c_double),
+                ("n_coarse", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("n_nbr", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        c = cls()
+        for name, _ in cls._fields_:
+            if name != "reserved":
+                setattr(c, name, d[name])
+        return c
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -177,6 +194,14 @@ def load():
     L.ucp_sweep_finish.argtypes = [_vp, _dp, _u64]
     L.ucp_solve.argtypes = [_vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveReport),
                             _dp, _i32p]
+    P2 = ctypes.POINTER(Params2)
+    L.ucp2_plan.argtypes = [P2, _u64p, _u64p, _u64p, _u64p]
+    L.ucp2_create.argtypes = [_vp, P2, _dp, _vp, ctypes.POINTER(_vp)]
+    L.ucp2_sweep.argtypes = [_vp, ctypes.c_int32]
+    L.ucp2_J_history.argtypes = [_vp, _dp, _u64, _u64p]
+    L.ucp2_get_controllers.argtypes = [_vp, _dp, _u64, _dp, _u64, _i32p, _u64]
+    L.ucp2_set_controllers.argtypes = [_vp, _dp, _u64, _dp, _u64]
+    L.ucp2_destroy.argtypes = [_vp]
     _lib = L
     return L
 
@@ -415,6 +440,87 @@ class Instance:
         return self
 
     def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan2(params) -> dict:
+    """Sizes of a 2-dimensional instance (host only)."""
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(load().ucp2_plan(ctypes.byref(Params2.from_dict(params)),
+                            *(ctypes.byref(x) for x in v)), "ucp2_plan")
+    return dict(zip(("n_x", "n_w", "n_y", "n_cand"), (x.value for x in v)))
+
+
+class Instance2D:
+    """One instance of the 2-dimensional counterexample (``ucp2_create`` ...
+    ``ucp2_destroy``).  f has shape (n_x^2, 2), the u1 tables (n_y^2, 2),
+    both over flat grid indices a n + b."""
+
+    def __init__(self, params, init_f=None, stream=None, ctx: Context | None = None):
+        import torch
+        L = load()
+        self.ctx = ctx or default_context()
+        self.params = dict(params)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.ctx.device)
+        self.stream = stream
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        sizes = plan2(params)
+        self.n_x, self.n_w, self.n_y, self.n_cand = (sizes[k] for k in
+                                                      ("n_x", "n_w", "n_y", "n_cand"))
+        f0 = None
+        if init_f is not None:
+            f0 = np.ascontiguousarray(init_f, dtype=np.float64).reshape(-1)
+            if f0.size != 2 * self.n_x ** 2:
+                raise ValueError(f"init_f needs {2 * self.n_x ** 2} values, got {f0.size}")
+        h = _vp()
+        self._p = Params2.from_dict(params)
+        _check(L.ucp2_create(self.ctx.h, ctypes.byref(self._p), _ptr(f0, ctypes.c_double),
+                             _vp(sp), ctypes.byref(h)), "ucp2_create")
+        self.h = h
+
+    def sweep(self, n: int = 1):
+        _check(load().ucp2_sweep(self.h, int(n)), "ucp2_sweep")
+
+    def J_history(self, n: int = 1 << 16) -> np.ndarray:
+        out = np.empty(n)
+        m = ctypes.c_uint64()
+        _check(load().ucp2_J_history(self.h, _ptr(out, ctypes.c_double), n,
+                                     ctypes.byref(m)), "ucp2_J_history")
+        return out[:m.value]
+
+    def get_controllers(self, want=("f", "U", "idx")):
+        nx2, ny2 = self.n_x ** 2, self.n_y ** 2
+        f = np.empty((nx2, 2)) if "f" in want else None
+        U = np.empty((ny2, 2)) if "U" in want else None
+        idx = np.empty(nx2, dtype=np.int32) if "idx" in want else None
+        _check(load().ucp2_get_controllers(
+            self.h, _ptr(f, ctypes.c_double), 2 * nx2, _ptr(U, ctypes.c_double), 2 * ny2,
+            _ptr(idx, ctypes.c_int32), nx2), "ucp2_get_controllers")
+        return dict(f=f, U=U, idx=idx)
+
+    def set_controllers(self, f, U=None):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        U = None if U is None else np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
+        _check(load().ucp2_set_controllers(
+            self.h, _ptr(f, ctypes.c_double), f.size, _ptr(U, ctypes.c_double),
+            0 if U is None else U.size), "ucp2_set_controllers")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ucp2_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
         self.close()
 
     def __del__(self):

@@ -1,0 +1,46 @@
+// ucp_2d.h -- the 2-dimensional Witsenhausen counterexample (Section V-D):
+// geometry of one instance and the device state behind ucp2_* (not part of
+// the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ucp.h"
+
+namespace ucp {
+
+// Integer geometry: half widths in units of delta, sizes per axis, the
+// controller lattice (value nu delta 2^-shift, shift = n_levels), the coarse
+// spacing q (units of delta, even) and the candidate-list length.
+struct G2 {
+    double k, kk, sigma, delta;
+    int64_t hx, hw, hy, hr, n_x, n_w, n_y;
+    int32_t shift;
+    int64_t one, q, n_cand;
+    int32_t n_coarse, n_levels, n_nbr;
+};
+
+// Fills g from p; nullptr or the reason p is invalid.
+const char* make_g2(const ucp2_params& p, G2* g);
+
+struct Dev2 {
+    double* px;      // [n_x^2] prior weights
+    double* phi1;    // [n_w] one-dimensional noise weights
+    double* phi2;    // [n_w^2] phi_c phi_d
+    double* U;       // [2 n_y^2] u1 table
+    int64_t* nu[2];  // [2 n_x^2] controller, double buffered
+    int32_t* idx;    // [n_x^2] winner positions of the last sweep
+    double* terms;   // [n_x^2] J's terms
+    double* scratch; // normalising sums
+    double* table;   // [2 n_x^2] host table staging
+    double* J;       // [J capacity] J history
+};
+
+void launch2_setup(const G2& g, Dev2& d, int from_table, cudaStream_t s);
+void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s);
+void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s);
+void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s);
+void launch2_table(const G2& g, Dev2& d, int buf, cudaStream_t s);
+
+}  // namespace ucp

@@ -21,13 +21,13 @@ def declared_symbols():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"UCP_API\s+[\w\s\*]+?\b(ucp_\w+)\s*\(", src))
+            names |= set(re.findall(r"UCP_API\s+[\w\s\*]+?\b(ucp2?_\w+)\s*\(", src))
     return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_symbols()
-    assert "ucp_create" in names and "ucp_sweep" in names
+    assert "ucp_create" in names and "ucp_sweep" in names and "ucp2_sweep" in names
     for n in names:
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 
@@ -110,3 +110,27 @@ def test_create_validates_before_touching_the_device(lib):
     p = binding.Params.from_dict(dict(workloads.c1(), init_kind=2))
     assert lib.ucp_create(None, ctypes.byref(p), None, ctypes.byref(h)) == -1
     assert b"init_table" in lib.ucp_last_error()
+
+
+def test_plan_of_the_2d_problem_matches_the_oracle(lib):
+    """Section V-D's problem: the library's sizes are the 2-D oracle's, and
+    invalid parameters are refused on the host (no context is created)."""
+    import oracle
+    from paper_1908_04489_gb300 import binding
+    p = dict(k=0.2, sigma=5.0, delta=0.3125, x_half=25.0, w_half=5.0, y_half=35.0,
+             cand_half=30.0, n_coarse=13, n_levels=8, n_nbr=2)
+    s = binding.plan2(p)
+    o = oracle.Oracle2D(p)
+    assert (s["n_x"], s["n_w"], s["n_y"], s["n_cand"]) == (o.n_x, o.n_w, o.n_y, o.n_cand)
+    assert (s["n_x"], s["n_cand"]) == (161, 25 + 169 + 64)
+    for bad, msg in ((dict(p, x_half=25.1), "multiples of delta"),
+                     (dict(p, n_coarse=65), "n_coarse"), (dict(p, n_levels=41), "n_levels"),
+                     (dict(p, n_nbr=9), "n_nbr"), (dict(p, sigma=0.0), "> 0"),
+                     (dict(p, delta=0.05), "too large")):
+        with pytest.raises(binding.UcpError) as e:
+            binding.plan2(bad)
+        assert e.value.status == -1 and msg in str(e.value), (bad, str(e.value))
+    h = ctypes.c_void_p()
+    pp = binding.Params2.from_dict(p)
+    assert lib.ucp2_create(None, ctypes.byref(pp), None, None, ctypes.byref(h)) == -1
+    assert b"context" in lib.ucp_last_error()

@@ -1,0 +1,269 @@
+"""The 2-dimensional Witsenhausen counterexample (Section V-D) on the GPU
+against the FP64 2-D oracle, through the ucp2_* C-ABI.
+
+  - lockstep: before every sweep the GPU's own state (f, U) is handed to the
+    oracle, whose search from that state must reproduce the GPU's decisions
+    (lattice values and list positions) bit for bit except at near-ties,
+    where the GPU's result must be one the oracle's search reaches with the
+    tie broken either way; the GPU's u1 tables must equal the oracle's u1
+    step of the GPU's controllers and the GPU's J the oracle's J of the
+    GPU's state;
+  - whole solves: the GPU's trajectory against the oracle's own solve, J
+    within 1e-9 up to and including the first sweep whose decisions differ;
+  - a start from a table, set_controllers, argument errors;
+  - a grid of several warps' worth of candidates (the list longer than 32)
+    with the window leaving the grid, sampled points against the oracle.
+The only differences between the two sides are the exp() of the weights and
+of the u1 step (ulps); everything else is the same FP64 arithmetic in the
+same order, so decisions agree except where two candidates' costs are equal
+to within ~1e-14 of the cost.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+P2 = dict(k=0.2, sigma=5.0, delta=1.25, x_half=12.5, w_half=5.0, y_half=20.0,
+          cand_half=15.0, n_coarse=7, n_levels=6, n_nbr=2)
+# Finer axis, more coarse values than a warp has lanes, window radius 3.
+P2B = dict(k=0.25, sigma=4.0, delta=0.625, x_half=10.0, w_half=3.75, y_half=17.5,
+           cand_half=13.75, n_coarse=9, n_levels=8, n_nbr=3)
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1908_04489_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def allow(g):
+    """Cost gap two FP64 evaluations of one candidate can differ by when the
+    only difference is the weights' exp() ulps (each of the fixed-order sum's
+    terms moves by a few ulps of itself)."""
+    return 1e-14 * max(g, 1e-300)
+
+
+def q_of(p):
+    hr = round(p["cand_half"] / p["delta"])
+    return 2 * max(1, -(-hr // (p["n_coarse"] - 1)))
+
+
+def first_minima(cands):
+    gmin = min(c[1] for c in cands)
+    out, seen = [], set()
+    for c in cands:
+        if c[1] - gmin <= allow(c[1]) and c[0] not in seen:
+            out.append(c)
+            seen.add(c[0])
+    return out
+
+
+def possible_winners(o, U, nu_pre, i):
+    """Every (value pair, list position) the oracle's search of point i ends
+    on with each near-tie broken either way: stage 0 (incumbent, window,
+    coarse grid) as listed, then each level's 8 neighbours around every
+    surviving best."""
+    p = o.params
+    nus, gs, _ = o.candidates(nu_pre, U, i)
+    side = 2 * p["n_nbr"] + 1
+    n0 = side * side + p["n_coarse"] ** 2
+    states = first_minima([((int(nus[k, 0]), int(nus[k, 1])), float(gs[k]), k)
+                           for k in range(n0)])
+    q, L = q_of(p), p["n_levels"]
+    pos = n0
+    moves = [(s, t) for s in (-1, 0, 1) for t in (-1, 0, 1) if (s, t) != (0, 0)]
+    for lv in range(1, L + 1):
+        h = q << (L - lv)
+        nxt = {}
+        for b in states:
+            cands = [b]
+            for k, (s, t) in enumerate(moves):
+                v = (b[0][0] + s * h, b[0][1] + t * h)
+                cands.append((v, o.cost(U, i, *v), pos + k))
+            for c in first_minima(cands):
+                nxt[(c[0], c[2])] = c
+        states = list(nxt.values())
+        pos += 8
+    return {(c[0], c[2]) for c in states}
+
+
+def lattice(o, f):
+    """Lattice indices of GPU f values (exact: they are lattice values)."""
+    nu = np.rint(np.ldexp(f / o.params["delta"], o.shift)).astype(np.int64)
+    assert np.array_equal(o.value(nu), f)
+    return nu
+
+
+def check_sweep(o, nu_pre, U_pre, f_post, idx_post, points=None):
+    """The oracle's search from the GPU's pre-sweep state against the GPU's
+    decisions; returns the number of near-tie differences."""
+    nu_gpu = lattice(o, f_post)
+    if points is None:
+        nu_o, idx_o = o.search(nu_pre, U_pre)
+        points = np.arange(o.N)
+    else:
+        nu_o = np.empty((o.N, 2), dtype=np.int64)
+        idx_o = np.full(o.N, -1, dtype=np.int32)
+        for i in points:
+            a, b = o.search(nu_pre, U_pre, int(i), int(i) + 1)
+            nu_o[i], idx_o[i] = a[i], b[i]
+    ties = 0
+    for i in points:
+        if np.array_equal(nu_o[i], nu_gpu[i]) and idx_o[i] == idx_post[i]:
+            continue
+        win = possible_winners(o, U_pre, nu_pre, int(i))
+        key = ((int(nu_gpu[i, 0]), int(nu_gpu[i, 1])), int(idx_post[i]))
+        assert key in win, (i, key, nu_o[i], idx_o[i], win)
+        ties += 1
+    return ties
+
+
+def test_start_equals_the_oracle(B, O):
+    o = O.Oracle2D(P2)
+    with B.Instance2D(P2) as g:
+        assert (g.n_x, g.n_w, g.n_y, g.n_cand) == (o.n_x, o.n_w, o.n_y, o.n_cand)
+        st = g.get_controllers()
+        nu0 = o.init(0)
+        assert np.array_equal(st["f"], o.value(nu0))
+        assert np.all(st["idx"] == -1)
+        U0 = o.mmse(nu0)
+        assert np.max(np.abs(st["U"] - U0)) <= 1e-12
+        J = g.J_history()
+        assert len(J) == 1
+        assert abs(J[0] - o.J(nu0, st["U"])) <= 1e-13 * J[0]
+        assert abs(J[0] - o.J(nu0, U0)) <= 1e-12 * J[0]
+
+
+@pytest.mark.parametrize("p,sweeps", [(P2, 8), (P2B, 3)], ids=["P2", "P2B"])
+def test_lockstep(B, O, p, sweeps):
+    o = O.Oracle2D(p)
+    ties = 0
+    with B.Instance2D(p) as g:
+        for s in range(sweeps):
+            pre = g.get_controllers()
+            nu_pre = lattice(o, pre["f"])
+            g.sweep(1)
+            post = g.get_controllers()
+            ties += check_sweep(o, nu_pre, pre["U"], post["f"], post["idx"])
+            nu_post = lattice(o, post["f"])
+            assert np.max(np.abs(post["U"] - o.mmse(nu_post))) <= 1e-11, s
+            J = g.J_history()
+            assert len(J) == s + 2
+            assert abs(J[-1] - o.J(nu_post, post["U"])) <= 1e-13 * J[-1], s
+    # Mirror-image candidates have equal costs up to rounding, and the
+    # weights' exp() ulps decide some of those ties the other way.
+    assert ties <= max(2, o.N * sweeps // 50), ties
+
+
+def test_whole_solve_matches_the_oracle(B, O):
+    o = O.Oracle2D(P2)
+    n = 10
+    ref = o.solve(n)
+    traj = []
+    with B.Instance2D(P2) as g:
+        traj.append(g.get_controllers())
+        for _ in range(n):
+            g.sweep(1)
+            traj.append(g.get_controllers())
+        J = g.J_history()
+    assert len(J) == n + 1
+    # Oracle states one sweep at a time (the same calls solve() makes).
+    nu = o.init(0)
+    U = o.mmse(nu)
+    for s in range(n + 1):
+        if s:
+            nu, _ = o.search(nu, U)
+            U = o.mmse(nu)
+        Jo = o.J(nu, U)
+        assert abs(J[s] - Jo) <= 1e-9, (s, J[s], Jo)
+        nu_gpu = lattice(o, traj[s]["f"])
+        if not np.array_equal(nu_gpu, nu):
+            # The first differing sweep: its differences are near-ties of the
+            # oracle's search from the GPU's previous state.
+            nu_pre = lattice(o, traj[s - 1]["f"])
+            check_sweep(o, nu_pre, traj[s - 1]["U"], traj[s]["f"], traj[s]["idx"])
+            break
+    else:
+        assert abs(J[-1] - ref["J"][-1]) <= 1e-9
+    assert J[-1] < J[0]
+
+
+def test_table_start_and_set_controllers(B, O):
+    o = O.Oracle2D(P2)
+    xs = o.grid(o.n_x)
+    h = np.sign(xs) * np.minimum(np.abs(xs), 7.5) * 1.5   # a saturating affine map
+    tab = np.stack([np.repeat(h, o.n_x), np.tile(h, o.n_x)], axis=1)
+    nu = o.init(2, tab)
+    with B.Instance2D(P2, init_f=tab) as g:
+        st = g.get_controllers()
+        assert np.array_equal(st["f"], o.value(nu))
+        assert np.max(np.abs(st["U"] - o.mmse(nu))) <= 1e-11
+        J0 = g.J_history()[0]
+        assert abs(J0 - o.J(nu, st["U"])) <= 1e-13 * J0
+        # set_controllers without U runs the u1 step; with U keeps it.
+        g.set_controllers(o.value(o.init(0)))
+        st2 = g.get_controllers()
+        assert np.array_equal(st2["f"], o.value(o.init(0)))
+        assert np.max(np.abs(st2["U"] - o.mmse(o.init(0)))) <= 1e-11
+        U_any = np.full((o.n_y ** 2, 2), 0.5)
+        g.set_controllers(st["f"], U_any)
+        st3 = g.get_controllers()
+        assert np.array_equal(st3["U"], U_any)
+        J3 = g.J_history()[-1]
+        assert abs(J3 - o.J(nu, U_any)) <= 1e-13 * J3
+        g.sweep(2)
+        assert len(g.J_history()) == 3
+
+
+def test_argument_errors(B):
+    bad = dict(P2, x_half=12.4)
+    with pytest.raises(B.UcpError):
+        B.Instance2D(bad)
+    with pytest.raises(B.UcpError):
+        B.Instance2D(dict(P2, n_coarse=1))
+    with B.Instance2D(P2) as g:
+        with pytest.raises(B.UcpError):
+            g.set_controllers(np.zeros(5))
+        f = np.zeros((g.n_x ** 2, 2))
+        f[3, 1] = np.inf
+        with pytest.raises(B.UcpError):
+            g.set_controllers(f)
+        with pytest.raises(B.UcpError):
+            g.sweep(-1)
+        g.sweep(1)   # the instance is still usable after rejected calls
+        assert len(g.J_history()) == 2
+
+
+def test_larger_grid_sampled(B, O):
+    """n_x = 41, a list of 25 + 81 + 64 = 170 candidates per point (window
+    radius 3 leaving the grid at the border): sampled points, three sweeps."""
+    p = dict(k=0.2, sigma=5.0, delta=0.625, x_half=12.5, w_half=3.75, y_half=20.0,
+             cand_half=15.0, n_coarse=9, n_levels=8, n_nbr=2)
+    o = O.Oracle2D(p)
+    rng = np.random.default_rng(1908)
+    n = o.N
+    border = [0, o.n_x - 1, n - 1, n - o.n_x, o.n_x * (o.n_x // 2) + o.n_x // 2, 1, o.n_x + 1]
+    with B.Instance2D(p) as g:
+        for s in range(3):
+            pre = g.get_controllers()
+            nu_pre = lattice(o, pre["f"])
+            g.sweep(1)
+            post = g.get_controllers()
+            pts = np.unique(np.concatenate([border, rng.choice(n, 60, replace=False)]))
+            check_sweep(o, nu_pre, pre["U"], post["f"], post["idx"], points=pts)
+            nu_post = lattice(o, post["f"])
+            t = rng.choice(o.n_y ** 2, 40, replace=False)
+            for tt in t:
+                Uo = o.mmse(nu_post, int(tt), int(tt) + 1)
+                assert np.max(np.abs(post["U"][tt] - Uo[tt])) <= 1e-11
