@@ -450,7 +450,13 @@ typedef struct {
     int32_t n_coarse;   /* coarse values per axis, 2..64                       */
     int32_t n_levels;   /* refinement levels, 0..40                            */
     int32_t n_nbr;      /* window radius, 0..8                                 */
-    int32_t reserved;   /* must be 0                                           */
+    int32_t direct;     /* bit 0 clear: screened search (correlation tables of
+                           u1 with a certified error bound, the exact quadrature
+                           only for candidates the bound cannot separate); set:
+                           the exact quadrature for every candidate (same
+                           decisions).  Bit 1 clear: the u1 weights factorised
+                           per axis (GEMM-shaped sums); set: each weight's
+                           exponential formed directly (u1 equal to rounding). */
 } ucp2_params;
 
 typedef struct ucp_inst2 ucp_inst2;

@@ -113,14 +113,13 @@ class Params2(ctypes.Structure):
                 ("x_half", ctypes.c_double), ("w_half", ctypes.c_double),
                 ("y_half", ctypes.c_double), ("cand_half", ctypes.c_double),
                 ("n_coarse", ctypes.c_int32), ("n_levels", ctypes.c_int32),
-                ("n_nbr", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_nbr", ctypes.c_int32), ("direct", ctypes.c_int32)]
 
     @classmethod
     def from_dict(cls, d):
         c = cls()
         for name, _ in cls._fields_:
-            if name != "reserved":
-                setattr(c, name, d[name])
+            setattr(c, name, d.get(name, 0) if name == "direct" else d[name])
         return c
 
 

@@ -115,7 +115,26 @@ extern "C" ucp_status ucp2_create(ucp_ctx* ctx, const ucp2_params* p, const doub
     d.terms = (double*)alloc2(in, 8 * n);
     d.scratch = (double*)alloc2(in, 64);
     d.table = (double*)alloc2(in, 16 * n);
-    if (!d.px || !d.phi1 || !d.phi2 || !d.U || !d.nu[0] || !d.nu[1] || !d.idx || !d.terms ||
+    d.phin = (double*)alloc2(in, 8 * nw);
+    const bool screened = !(g.direct & 1), factorised = !(g.direct & 2);
+    if (screened) {
+        d.H = (double*)alloc2(in, 8 * 7 * (size_t)(g.ext_n * g.tab_n));
+        d.tab = (double*)alloc2(in, 64 * (size_t)(g.tab_n * g.tab_n));
+    }
+    if (factorised) {
+        d.mins = (double*)alloc2(in, 8 * (size_t)(2 * g.n_y + 1));
+        d.fa = (double*)alloc2(in, 8 * n * (size_t)g.n_y);
+        d.fb = (double*)alloc2(in, 8 * n * (size_t)g.n_y);
+        d.part = (double*)alloc2(in, 24 * (size_t)g.u1_splits * (size_t)(g.n_y * g.n_y));
+        d.fa64 = (double*)alloc2(in, 8 * n * (size_t)g.n_y);
+        d.fb64 = (double*)alloc2(in, 8 * n * (size_t)g.n_y);
+        d.fv = (double*)alloc2(in, 16 * n);
+        d.list = (int32_t*)alloc2(in, 4 * (1 + (size_t)(g.n_y * g.n_y)));
+    }
+    if ((screened && (!d.H || !d.tab)) ||
+        (factorised && (!d.mins || !d.fa || !d.fb || !d.part || !d.fa64 || !d.fb64 || !d.fv ||
+                        !d.list)) ||
+        !d.phin || !d.px || !d.phi1 || !d.phi2 || !d.U || !d.nu[0] || !d.nu[1] || !d.idx || !d.terms ||
         !d.scratch || !d.table || ensure_J(in, 64) != UCP_OK) {
         free2(in);
         delete in;

@@ -18,6 +18,7 @@
 #include <float.h>
 #include <limits.h>
 
+#include "df.cuh"
 #include "fixed_sum.cuh"
 #include "ucp_2d.h"
 
@@ -52,32 +53,54 @@ __device__ __forceinline__ double bilerp2(const G2& g, const double* __restrict_
     return __dadd_rn(r0, __dmul_rn(t1, __dsub_rn(r1, r0)));
 }
 
+// Where the taps of S(u) at the lattice pair (nu1, nu2) read the u1 table:
+// the cell of u (floor division), the fractions, the first tap's cell.
+struct TapBase {
+    int64_t jb1, jb2;
+    double t1, t2, u1, u2;
+};
+__device__ __forceinline__ TapBase tap_base(const G2& g, int64_t nu1, int64_t nu2) {
+    TapBase b;
+    const int64_t c1 = nu1 >> g.shift, c2 = nu2 >> g.shift;   // floor division
+    b.t1 = __dmul_rn((double)(nu1 - (c1 << g.shift)), inv_one2(g));
+    b.t2 = __dmul_rn((double)(nu2 - (c2 << g.shift)), inv_one2(g));
+    b.jb1 = c1 - g.hw + g.hy;
+    b.jb2 = c2 - g.hw + g.hy;
+    b.u1 = val2(g, nu1);
+    b.u2 = val2(g, nu2);
+    return b;
+}
+// Term (c, d) of S: phi_c phi_d |u - U^(u + w_cd)|^2.
+__device__ __forceinline__ double tap2(const G2& g, const double* __restrict__ phi2,
+                                       const double* __restrict__ U, const TapBase& b,
+                                       int64_t c, int64_t d) {
+    const double e1 = __dsub_rn(b.u1, bilerp2(g, U, 0, b.jb1 + c, b.jb2 + d, b.t1, b.t2));
+    const double e2 = __dsub_rn(b.u2, bilerp2(g, U, 1, b.jb1 + c, b.jb2 + d, b.t1, b.t2));
+    return __dmul_rn(phi2[c * g.n_w + d], __dadd_rn(__dmul_rn(e1, e1), __dmul_rn(e2, e2)));
+}
+
 // S(u) at the lattice pair (nu1, nu2): taps in row-major order, the fixed sum.
 __device__ double S2d(const G2& g, const double* __restrict__ phi2,
                       const double* __restrict__ U, int64_t nu1, int64_t nu2) {
-    const int64_t c1 = nu1 >> g.shift, c2 = nu2 >> g.shift;   // floor division
-    const double t1 = __dmul_rn((double)(nu1 - (c1 << g.shift)), inv_one2(g));
-    const double t2 = __dmul_rn((double)(nu2 - (c2 << g.shift)), inv_one2(g));
-    const int64_t jb1 = c1 - g.hw + g.hy, jb2 = c2 - g.hw + g.hy;
-    const double u1 = val2(g, nu1), u2 = val2(g, nu2);
+    const TapBase b = tap_base(g, nu1, nu2);
     const int64_t m = g.n_w;
     FixedSum acc;
     for (int64_t c = 0; c < m; ++c)
-        for (int64_t d = 0; d < m; ++d) {
-            const double e1 = __dsub_rn(u1, bilerp2(g, U, 0, jb1 + c, jb2 + d, t1, t2));
-            const double e2 = __dsub_rn(u2, bilerp2(g, U, 1, jb1 + c, jb2 + d, t1, t2));
-            acc.add(__dmul_rn(phi2[c * m + d], __dadd_rn(__dmul_rn(e1, e1), __dmul_rn(e2, e2))));
-        }
+        for (int64_t d = 0; d < m; ++d) acc.add(tap2(g, phi2, U, b, c, d));
     return acc.result();
+}
+
+// k^2 |u - x_i|^2, the first part of the marginal cost.
+__device__ __forceinline__ double kterm2(const G2& g, int64_t i, int64_t nu1, int64_t nu2) {
+    const double d1 = __dsub_rn(val2(g, nu1), grid2(g, i / g.n_x, g.hx));
+    const double d2 = __dsub_rn(val2(g, nu2), grid2(g, i % g.n_x, g.hx));
+    return __dmul_rn(g.kk, __dadd_rn(__dmul_rn(d1, d1), __dmul_rn(d2, d2)));
 }
 
 __device__ __forceinline__ double cost2d(const G2& g, const double* __restrict__ phi2,
                                          const double* __restrict__ U, int64_t i,
                                          int64_t nu1, int64_t nu2) {
-    const double d1 = __dsub_rn(val2(g, nu1), grid2(g, i / g.n_x, g.hx));
-    const double d2 = __dsub_rn(val2(g, nu2), grid2(g, i % g.n_x, g.hx));
-    return __dadd_rn(__dmul_rn(g.kk, __dadd_rn(__dmul_rn(d1, d1), __dmul_rn(d2, d2))),
-                     S2d(g, phi2, U, nu1, nu2));
+    return __dadd_rn(kterm2(g, i, nu1, nu2), S2d(g, phi2, U, nu1, nu2));
 }
 
 __device__ __forceinline__ bool before2(double ga, int32_t pa, double gb, int32_t pb) {
@@ -162,12 +185,10 @@ __global__ void __launch_bounds__(kSearch2T) k2_search(G2 g, const double* __res
     }
 }
 
-// u1 step, one thread per target t: the exponents' minimum over the sources,
+// u1 step at target t directly: the exponents' minimum over the sources,
 // then the two numerators and the denominator in source order.
-__global__ void __launch_bounds__(128) k2_mmse(G2 g, const int64_t* __restrict__ nu,
-                                               double* __restrict__ U) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.n_y * g.n_y) return;
+__device__ void mmse_direct(const G2& g, const int64_t* __restrict__ nu, int64_t t,
+                            double* __restrict__ U) {
     const double two_s2 = __dmul_rn(__dmul_rn(2.0, g.sigma), g.sigma);
     const double y1 = grid2(g, t / g.n_y, g.hy), y2 = grid2(g, t % g.n_y, g.hy);
     const int64_t n = g.n_x * g.n_x;
@@ -197,25 +218,252 @@ __global__ void __launch_bounds__(128) k2_mmse(G2 g, const int64_t* __restrict__
     U[2 * t + 1] = __ddiv_rn(a2, den);
 }
 
-// The marginal cost at every point's own value (J's terms).
-__global__ void __launch_bounds__(128) k2_costs(G2 g, const double* __restrict__ phi2,
-                                                const double* __restrict__ U,
-                                                const int64_t* __restrict__ nu,
-                                                double* __restrict__ terms) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n_x * g.n_x) return;
-    terms[i] = cost2d(g, phi2, U, i, nu[2 * i], nu[2 * i + 1]);
+// u1 step, one thread per target t (the direct form).
+__global__ void __launch_bounds__(128) k2_mmse(G2 g, const int64_t* __restrict__ nu,
+                                               double* __restrict__ U) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < g.n_y * g.n_y) mmse_direct(g, nu, t, U);
 }
 
-// J = (1/2) sum_i p_i g_i in index order (one thread: the order is the
-// definition's).
-__global__ void k2_J(G2 g, const double* __restrict__ px, const double* __restrict__ terms,
-                     double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// ---- factorised u1 step -------------------------------------------------------
+//
+// The exponent of source i at target y splits over the axes,
+//   E_i(y) = P_i + Q_i(y_1) + R_i(y_2),  P_i = |x_i|^2 / (2 sigma^2),
+//   Q_i(y_1) = (y_1 - f_i1)^2 / 2,  R_i(y_2) = (y_2 - f_i2)^2 / 2,
+// so exp(-(E_i - e)) with e = min P + min_i Q_i(y_1) + min_i R_i(y_2) is the
+// product a_i(y_1) b_i(y_2) of per-axis factors (the prior folded into a).
+// The weights differ from exp(-(E_i - min_i E_i)) by one factor per target,
+// which cancels in the ratio; the three sums over sources are then
+// GEMM-shaped (n_y x n_y targets, n_x^2 sources) and run split over source
+// ranges, the partial sums added in split order.  The factors are at most 1
+// and terms below FP32's range are lost, so a target whose denominator (that
+// cancelled factor, at least) falls below 2^-60 is recomputed in the direct
+// form; elsewhere the lost terms are below 2^-50 of the denominator.
+
+// mins[j] = min_i Q_i(y_j), mins[n_y + j] = min_i R_i(y_j), mins[2 n_y] =
+// min_i P_i: one block each.
+__device__ __forceinline__ double half_sq(double y, double f) {
+    const double d = y - f;
+    return 0.5 * (d * d);
+}
+__device__ __forceinline__ double prior_expo(const G2& g, int64_t i) {
+    const double xa = grid2(g, i / g.n_x, g.hx), xb = grid2(g, i % g.n_x, g.hx);
+    return (xa * xa + xb * xb) / (2.0 * g.sigma * g.sigma);
+}
+__global__ void __launch_bounds__(256) k2_u1_mins(G2 g, const int64_t* __restrict__ nu,
+                                                  double* __restrict__ mins) {
+    __shared__ double red[256];
+    const int64_t b = blockIdx.x, n = g.n_x * g.n_x;
+    double m = INFINITY;
+    if (b < 2 * g.n_y) {
+        const int q = b < g.n_y ? 0 : 1;
+        const double y = grid2(g, b - q * g.n_y, g.hy);
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+            m = fmin(m, half_sq(y, val2(g, nu[2 * i + q])));
+    } else {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, prior_expo(g, i));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mins[b] = red[0];
+}
+
+// Factor tables, target-major (entry j N + i, N = n_x^2 sources):
+//   fa = exp(-(P_i - min P)) exp(-(Q_i(y_j) - min Q)),  fb = exp(-(R_i(y_j) - min R)),
+// formed in FP64 and kept both as double-float pairs (hi, lo) for the sums
+// and in FP64 for the targets whose factor leaves FP32's range; fv[2 i + q]
+// = f_iq.
+__global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const int64_t* __restrict__ nu,
+                                                     const double* __restrict__ mins,
+                                                     float2* __restrict__ fa,
+                                                     float2* __restrict__ fb,
+                                                     double* __restrict__ fa64,
+                                                     double* __restrict__ fb64,
+                                                     double* __restrict__ fv) {
     const int64_t n = g.n_x * g.n_x;
-    double J = 0.0;
-    for (int64_t i = 0; i < n; ++i) J = __dadd_rn(J, __dmul_rn(px[i], terms[i]));
-    *out = __dmul_rn(0.5, J);
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n * g.n_y) return;
+    const int64_t j = id / n, i = id % n;
+    const double y = grid2(g, j, g.hy);
+    const double f1 = val2(g, nu[2 * i]), f2 = val2(g, nu[2 * i + 1]);
+    const double pa = exp(-(prior_expo(g, i) - mins[2 * g.n_y]));
+    const double va = pa * exp(-(half_sq(y, f1) - mins[j]));
+    const double vb = exp(-(half_sq(y, f2) - mins[g.n_y + j]));
+    const dfloat a = df_from_double(va), b = df_from_double(vb);
+    fa[id] = make_float2(a.hi, a.lo);
+    fb[id] = make_float2(b.hi, b.lo);
+    fa64[id] = va;
+    fb64[id] = vb;
+    if (j == 0) {
+        fv[2 * i] = f1;
+        fv[2 * i + 1] = f2;
+    }
+}
+
+// Partial sums of one split of the sources for a 32 x 32 tile of targets in
+// double-float arithmetic on the FP32 pipe: 256 threads, each a 2 x 2 block
+// of targets (rows ty + 16 r, columns tx + 16 c), 32 sources per
+// shared-memory stage.  Each stage is summed afresh (products kept as
+// unnormalised pairs, accumulation normalised per term) and then added to
+// the running sums with the accurate double-float addition, so a split of K
+// sources carries a relative error of about (32 + K / 32) 2^-47 of its sum
+// of magnitudes.
+constexpr int kU1Tile = 32, kU1Stage = 32;
+__global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict__ fa,
+                                                  const float2* __restrict__ fb,
+                                                  const double* __restrict__ fv,
+                                                  int64_t split_len, double* __restrict__ part) {
+    __shared__ float2 sa[kU1Stage][kU1Tile + 1], sb[kU1Stage][kU1Tile + 1], sf[kU1Stage][2];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t ny = g.n_y, n = g.n_x * g.n_x;
+    const int64_t j1_0 = (int64_t)blockIdx.y * kU1Tile, j2_0 = (int64_t)blockIdx.x * kU1Tile;
+    const int64_t i_lo = (int64_t)blockIdx.z * split_len;
+    const int64_t i_hi = min(i_lo + split_len, n);
+    dfloat D[2][2], N1[2][2], N2[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) D[r][c] = N1[r][c] = N2[r][c] = dfloat{0.0f, 0.0f};
+    for (int64_t i0 = i_lo; i0 < i_hi; i0 += kU1Stage) {
+        for (int k = threadIdx.x; k < kU1Stage * kU1Tile; k += 256) {
+            const int sj = k / kU1Stage, si = k % kU1Stage;   // consecutive sources
+            const int64_t i = i0 + si;
+            const bool ok = i < i_hi;
+            sa[si][sj] = ok && j1_0 + sj < ny ? fa[(j1_0 + sj) * n + i] : make_float2(0.f, 0.f);
+            sb[si][sj] = ok && j2_0 + sj < ny ? fb[(j2_0 + sj) * n + i] : make_float2(0.f, 0.f);
+        }
+        if (threadIdx.x < 2 * kU1Stage) {
+            const int si = threadIdx.x >> 1, q = threadIdx.x & 1;
+            const int64_t i = i0 + si;
+            const dfloat f = df_from_double(i < i_hi ? fv[2 * i + q] : 0.0);
+            sf[si][q] = make_float2(f.hi, f.lo);
+        }
+        __syncthreads();
+        dfloat d[2][2], m1[2][2], m2[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) d[r][c] = m1[r][c] = m2[r][c] = dfloat{0.0f, 0.0f};
+#pragma unroll 2
+        for (int si = 0; si < kU1Stage; ++si) {
+            dfloat a[2], b[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const float2 v = sa[si][ty + 16 * r];
+                a[r] = dfloat{v.x, v.y};
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float2 v = sb[si][tx + 16 * c];
+                b[c] = dfloat{v.x, v.y};
+            }
+            const float2 f1 = sf[si][0], f2 = sf[si][1];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    float p, e, q, qe;
+                    df_mul_raw(a[r], b[c], p, e);
+                    d[r][c] = df_acc(d[r][c], p, e);
+                    df_mul_raw(dfloat{p, e}, dfloat{f1.x, f1.y}, q, qe);
+                    m1[r][c] = df_acc(m1[r][c], q, qe);
+                    df_mul_raw(dfloat{p, e}, dfloat{f2.x, f2.y}, q, qe);
+                    m2[r][c] = df_acc(m2[r][c], q, qe);
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                D[r][c] = df_add_acc(D[r][c], d[r][c]);
+                N1[r][c] = df_add_acc(N1[r][c], m1[r][c]);
+                N2[r][c] = df_add_acc(N2[r][c], m2[r][c]);
+            }
+        __syncthreads();
+    }
+    const int64_t plane = ny * ny;
+    double* out = part + (int64_t)blockIdx.z * 3 * plane;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int64_t j1 = j1_0 + ty + 16 * r, j2 = j2_0 + tx + 16 * c;
+            if (j1 < ny && j2 < ny) {
+                const int64_t t = j1 * ny + j2;
+                out[t] = df_to_double(D[r][c]);
+                out[plane + t] = df_to_double(N1[r][c]);
+                out[2 * plane + t] = df_to_double(N2[r][c]);
+            }
+        }
+}
+
+// U = numerators / denominator with the splits added in order; targets
+// whose denominator is below 2^-60 are listed for the FP64 pass.
+__global__ void __launch_bounds__(128) k2_u1_finish(G2 g, const double* __restrict__ part,
+                                                    int splits, double* __restrict__ U,
+                                                    int32_t* __restrict__ list) {
+    const int64_t plane = g.n_y * g.n_y;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= plane) return;
+    double den = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        const double* p = part + (int64_t)s * 3 * plane;
+        den += p[t];
+        a1 += p[plane + t];
+        a2 += p[2 * plane + t];
+    }
+    if (den >= 0x1p-60) {
+        U[2 * t] = a1 / den;
+        U[2 * t + 1] = a2 / den;
+    } else {
+        list[1 + atomicAdd(list, 1)] = (int32_t)t;
+    }
+}
+
+// The listed targets in FP64, one warp each: lane l sums sources l, l + 32,
+// ... of the FP64 factor tables, then a fixed reduction tree.  FP64's range
+// keeps every term above 2^-50 of the denominator while that is at least
+// 2^-957; below that (a factor gap beyond ~660) the direct form runs.
+__global__ void __launch_bounds__(128) k2_u1_wide(G2 g, const int64_t* __restrict__ nu,
+                                                  const double* __restrict__ fa64,
+                                                  const double* __restrict__ fb64,
+                                                  const double* __restrict__ fv,
+                                                  const int32_t* __restrict__ list,
+                                                  double* __restrict__ U) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = g.n_x * g.n_x, count = list[0];
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < count;
+         w += warps) {
+        const int64_t t = list[1 + w], j1 = t / g.n_y, j2 = t % g.n_y;
+        const double* a = fa64 + j1 * n;
+        const double* b = fb64 + j2 * n;
+        double den = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int64_t i = lane; i < n; i += 32) {
+            const double v = a[i] * b[i];
+            den += v;
+            s1 += v * fv[2 * i];
+            s2 += v * fv[2 * i + 1];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            den += __shfl_xor_sync(0xffffffffu, den, off);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+        }
+        if (den >= 0x1p-957) {
+            if (lane == 0) {
+                U[2 * t] = s1 / den;
+                U[2 * t + 1] = s2 / den;
+            }
+        } else if (lane == 0) {
+            mmse_direct(g, nu, t, U);
+        }
+    }
 }
 
 // ---- set-up -----------------------------------------------------------------
@@ -236,10 +484,11 @@ __global__ void k2_exps(G2 g, double* __restrict__ pr, double* __restrict__ p1) 
     }
 }
 
-// out = sum of v[0..n) in the fixed order (32-term chunks left to right, then
-// pairwise by levels): one block, chunk sums in shared memory, each level's
-// additions spread over the block.
-__global__ void k2_fixed_sum(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+// out = scale x the sum of v[0..n) in the fixed order (32-term chunks left to
+// right, then pairwise by levels): one block, chunk sums in shared memory,
+// each level's additions spread over the block.
+__global__ void k2_fixed_sum(const double* __restrict__ v, int64_t n, double scale,
+                             double* __restrict__ out) {
     extern __shared__ double ch[];
     const int64_t m = sum_chunks(n);
     for (int64_t k = threadIdx.x; k < m; k += blockDim.x) {
@@ -264,7 +513,7 @@ __global__ void k2_fixed_sum(const double* __restrict__ v, int64_t n, double* __
         }
         w = h + (w & 1);
     }
-    if (threadIdx.x == 0) *out = m ? ch[0] : 0.0;
+    if (threadIdx.x == 0) *out = __dmul_rn(scale, m ? ch[0] : 0.0);
 }
 
 // Normalise both weight sets, form phi2, and set the start (identity or the
@@ -299,6 +548,333 @@ __global__ void k2_table(G2 g, const double* __restrict__ table, int64_t* __rest
     nu[i] = (int64_t)llround(__dmul_rn(__ddiv_rn(table[i], g.delta), (double)g.one));
 }
 
+// ---- screened search --------------------------------------------------------
+//
+// With U^ bilinear, S(u) = W |u|^2 - 2 u . sum_k a_k A(j + o_k)
+//                          + sum_kl a_k a_l C_{o_l - o_k}(j + o_k),
+// j the first tap's cell, o_k in {(0,0), (0,1), (1,0), (1,1)} the cell's
+// corners with bilinear weights a_k, W = sum_cd phi_c phi_d, and
+//   A_q(j) = sum_cd phi_c phi_d U_q(j + (c, d))               (q = 1, 2),
+//   C_e(j) = sum_cd phi_c phi_d <U(j + (c, d)), U(j + (c, d) + e)>,
+// e in {(0,0), (0,1), (1,0), (1,1), (1,-1)}, U clamped beyond its grid.  Every
+// table is constant for j below -n_w - 1 or above n_y on an axis (all its
+// taps read the clamped edge there), so corner indices are clamped to that
+// range.  Slots of a cell: A_1, A_2, C_00, C_01, C_10, C_11, C_1m, unused.
+
+// Umax = max |U| and W = (sum_c phi_c)^2 (one block).
+__global__ void __launch_bounds__(256) k2_tab_consts(G2 g, const double* __restrict__ U,
+                                                     const double* __restrict__ phin,
+                                                     double* __restrict__ out) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int64_t k = threadIdx.x; k < 2 * g.n_y * g.n_y; k += blockDim.x)
+        m = fmax(m, fabs(U[k]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double w = 0.0;
+        for (int64_t c = 0; c < g.n_w; ++c) w += phin[c];
+        out[0] = red[0];
+        out[1] = w * w;
+    }
+}
+
+// Row pass: H_f(r, a2) = sum_d phi_d F_f(J1, J2 + d), J1 = tab_lo + r,
+// J2 = tab_lo + a2, with the fields F = U_1, U_2 and <U(J), U(J + e)>.
+__global__ void __launch_bounds__(256) k2_tab_rows(G2 g, const double* __restrict__ U,
+                                                   const double* __restrict__ phin,
+                                                   double* __restrict__ H) {
+    const int64_t L = g.tab_n, plane = g.ext_n * L;
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= plane) return;
+    const int64_t J1 = g.tab_lo + id / L, J2 = g.tab_lo + id % L, n = g.n_y;
+    const int64_t ra = clampy(g, J1) * n, rb = clampy(g, J1 + 1) * n;
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t d = 0; d < g.n_w; ++d) {
+        const int64_t ca = clampy(g, J2 + d), cb = clampy(g, J2 + d + 1),
+                      cm = clampy(g, J2 + d - 1);
+        const double2 u = *reinterpret_cast<const double2*>(U + 2 * (ra + ca));
+        const double2 r = *reinterpret_cast<const double2*>(U + 2 * (ra + cb));   // e = (0, 1)
+        const double2 v = *reinterpret_cast<const double2*>(U + 2 * (rb + ca));   // e = (1, 0)
+        const double2 q = *reinterpret_cast<const double2*>(U + 2 * (rb + cb));   // e = (1, 1)
+        const double2 m = *reinterpret_cast<const double2*>(U + 2 * (rb + cm));   // e = (1, -1)
+        const double w = phin[d];
+        acc[0] += w * u.x;
+        acc[1] += w * u.y;
+        acc[2] += w * (u.x * u.x + u.y * u.y);
+        acc[3] += w * (u.x * r.x + u.y * r.y);
+        acc[4] += w * (u.x * v.x + u.y * v.y);
+        acc[5] += w * (u.x * q.x + u.y * q.y);
+        acc[6] += w * (u.x * m.x + u.y * m.y);
+    }
+#pragma unroll
+    for (int f = 0; f < 7; ++f) H[f * plane + id] = acc[f];
+}
+
+// Column pass: tab(a1, a2) = sum_c phi_c H(a1 + c, a2), 8 slots per cell.
+__global__ void __launch_bounds__(256) k2_tab_cols(G2 g, const double* __restrict__ H,
+                                                   const double* __restrict__ phin,
+                                                   double* __restrict__ tab) {
+    const int64_t L = g.tab_n, plane = g.ext_n * L;
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= L * L) return;
+    const int64_t a1 = id / L, a2 = id % L;
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t c = 0; c < g.n_w; ++c) {
+        const double w = phin[c];
+        const double* h = H + (a1 + c) * L + a2;
+#pragma unroll
+        for (int f = 0; f < 7; ++f) acc[f] += w * h[f * plane];
+    }
+    double2* o = reinterpret_cast<double2*>(tab + 8 * id);
+    o[0] = make_double2(acc[0], acc[1]);
+    o[1] = make_double2(acc[2], acc[3]);
+    o[2] = make_double2(acc[4], acc[5]);
+    o[3] = make_double2(acc[6], 0.0);
+}
+
+__device__ __forceinline__ int64_t tcell(const G2& g, int64_t j) {
+    const int64_t hi = g.tab_lo + g.tab_n - 1;
+    return (j < g.tab_lo ? g.tab_lo : (j > hi ? hi : j)) - g.tab_lo;
+}
+
+// Table cost of candidate (nu1, nu2) at x0 point i and the bound eb on its
+// distance from the exact fixed-order cost cost2d.
+__device__ __forceinline__ void tab_cost(const G2& g, const double* __restrict__ tab, double um,
+                                         double W, int64_t i, int64_t nu1, int64_t nu2,
+                                         double& gt, double& eb) {
+    const TapBase b = tap_base(g, nu1, nu2);
+    const int64_t L = g.tab_n;
+    const int64_t a1 = tcell(g, b.jb1), a1p = tcell(g, b.jb1 + 1);
+    const int64_t a2 = tcell(g, b.jb2), a2p = tcell(g, b.jb2 + 1);
+    const double* P00 = tab + 8 * (a1 * L + a2);
+    const double* P01 = tab + 8 * (a1 * L + a2p);
+    const double* P10 = tab + 8 * (a1p * L + a2);
+    const double* P11 = tab + 8 * (a1p * L + a2p);
+    const double s1 = 1.0 - b.t1, s2 = 1.0 - b.t2;
+    const double w00 = s1 * s2, w01 = s1 * b.t2, w10 = b.t1 * s2, w11 = b.t1 * b.t2;
+    const double A1 = w00 * P00[0] + w01 * P01[0] + w10 * P10[0] + w11 * P11[0];
+    const double A2 = w00 * P00[1] + w01 * P01[1] + w10 * P10[1] + w11 * P11[1];
+    const double Cd = w00 * w00 * P00[2] + w01 * w01 * P01[2] + w10 * w10 * P10[2] +
+                      w11 * w11 * P11[2];
+    const double Cx = w00 * w01 * P00[3] + w00 * w10 * P00[4] + w00 * w11 * P00[5] +
+                      w01 * w10 * P01[6] + w01 * w11 * P01[4] + w10 * w11 * P10[3];
+    const double uu = b.u1 * b.u1 + b.u2 * b.u2;
+    const double S = W * uu - 2.0 * (b.u1 * A1 + b.u2 * A2) + Cd + 2.0 * Cx;
+    gt = kterm2(g, i, nu1, nu2) + S;
+    const double M = uu + 2.0 * (fabs(b.u1) + fabs(b.u2)) * um + 2.0 * um * um;
+    eb = g.eps_k * (M + fabs(gt));
+}
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kExactCh = 512;   // chunk sums of one exact cost a warp keeps in shared memory
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+// The exact cost cost2d of (nu1, nu2) at point i, by the whole warp: lane l
+// forms chunks l, l + 32, ... (each left to right, as FixedSum), then the
+// chunk sums are paired level by level in shared memory.  Same double as
+// cost2d.  Quadratures of more than kExactCh chunks run on lane 0.
+__device__ double warp_exact(const G2& g, const double* __restrict__ phi2,
+                             const double* __restrict__ U, int64_t i, int64_t nu1, int64_t nu2,
+                             double* ch, int lane) {
+    const int64_t T = g.n_w * g.n_w, m = sum_chunks(T);
+    double S;
+    if (m > kExactCh) {
+        double v = 0.0;
+        if (lane == 0) v = S2d(g, phi2, U, nu1, nu2);
+        S = __shfl_sync(kFull, v, 0);
+    } else {
+        const TapBase b = tap_base(g, nu1, nu2);
+        for (int64_t k = lane; k < m; k += 32) {
+            const int64_t j0 = k * kSumChunk, e = min(j0 + kSumChunk, T);
+            int64_t c = j0 / g.n_w, d = j0 % g.n_w;
+            double a = 0.0;
+            for (int64_t j = j0; j < e; ++j) {
+                a = __dadd_rn(a, tap2(g, phi2, U, b, c, d));
+                if (++d == g.n_w) {
+                    d = 0;
+                    ++c;
+                }
+            }
+            ch[k] = a;
+        }
+        __syncwarp();
+        for (int64_t w = m; w > 1;) {
+            const int64_t h = w / 2;
+            for (int64_t k0 = 0; k0 < h; k0 += 32) {
+                const int64_t k = k0 + lane;
+                const double a = k < h ? __dadd_rn(ch[2 * k], ch[2 * k + 1]) : 0.0;
+                __syncwarp();
+                if (k < h) ch[k] = a;
+                __syncwarp();
+            }
+            if (w & 1) {
+                if (lane == 0) ch[h] = ch[w - 1];
+                __syncwarp();
+            }
+            w = h + (w & 1);
+        }
+        S = ch[0];
+        __syncwarp();   // ch is reused by the next call
+    }
+    return __dadd_rn(kterm2(g, i, nu1, nu2), S);
+}
+
+// Resolution of one stage of the list: its contenders (table cost within the
+// bound of the stage's best bound) offered in list order; the winner is the
+// first with the least exact cost.  A value offered again is skipped (same
+// exact cost, later position).  Exact costs are formed only once a second
+// distinct value appears.  Warp-uniform except the seen list (lane k holds
+// the k-th distinct value).
+struct Stage2 {
+    bool has = false, known = false;
+    int64_t b1 = 0, b2 = 0;
+    int32_t bp = 0;
+    double bgt = 0.0, beb = 0.0, bex = 0.0;
+    int nseen = 0;
+    int64_t s1 = 0, s2 = 0;
+
+    __device__ void offer(const G2& g, const double* __restrict__ phi2,
+                          const double* __restrict__ U, int64_t i, double* ch, int lane,
+                          int64_t v1, int64_t v2, int32_t pos, double vgt, double veb,
+                          bool vknown, double vex) {
+        if (__any_sync(kFull, lane < nseen && s1 == v1 && s2 == v2)) return;
+        if (nseen < 32) {
+            if (lane == nseen) {
+                s1 = v1;
+                s2 = v2;
+            }
+            ++nseen;
+        }
+        if (!has) {
+            has = true;
+            b1 = v1; b2 = v2; bp = pos; bgt = vgt; beb = veb;
+            known = vknown;
+            bex = vex;
+            return;
+        }
+        if (!known) {
+            bex = warp_exact(g, phi2, U, i, b1, b2, ch, lane);
+            known = true;
+        }
+        const double ex = vknown ? vex : warp_exact(g, phi2, U, i, v1, v2, ch, lane);
+        if (ex < bex) {
+            b1 = v1; b2 = v2; bp = pos; bgt = vgt; beb = veb; bex = ex;
+        }
+    }
+};
+
+// One warp per x0 point, the list of k2_search with table costs: per stage
+// the threshold min (gt + eb), then the contenders gt - eb <= threshold in
+// list order (any other candidate's exact cost exceeds the stage minimum's).
+__global__ void __launch_bounds__(kSearch2T) k2_search_scr(
+    G2 g, const double* __restrict__ phi2, const double* __restrict__ U,
+    const double* __restrict__ tab, const double* __restrict__ consts,
+    const int64_t* __restrict__ nu_pre, int64_t* __restrict__ nu_out,
+    int32_t* __restrict__ idx_out) {
+    __shared__ double chs[kSearch2T / 32][kExactCh];
+    const int lane = threadIdx.x & 31;
+    double* ch = chs[threadIdx.x >> 5];
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= g.n_x * g.n_x) return;   // the same for the warp
+    const double um = consts[0], W = consts[1];
+    const int64_t side = 2 * (int64_t)g.n_nbr + 1;
+    const int n0 = (int)(side * side + (int64_t)g.n_coarse * g.n_coarse);
+    double thr = DBL_MAX;
+    for (int p = lane; p < n0; p += 32) {
+        int64_t n1, n2;
+        double gt, eb;
+        stage0_cand(g, nu_pre, i, p, n1, n2);
+        tab_cost(g, tab, um, W, i, n1, n2, gt, eb);
+        thr = fmin(thr, gt + eb);
+    }
+    thr = warp_min(thr);
+    Stage2 st;
+    for (int base = 0; base < n0; base += 32) {
+        const int p = base + lane;
+        int64_t n1 = 0, n2 = 0;
+        double gt = 0.0, eb = 0.0;
+        bool cont = false;
+        if (p < n0) {
+            stage0_cand(g, nu_pre, i, p, n1, n2);
+            tab_cost(g, tab, um, W, i, n1, n2, gt, eb);
+            cont = gt - eb <= thr;
+        }
+        unsigned mask = __ballot_sync(kFull, cont);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            st.offer(g, phi2, U, i, ch, lane, __shfl_sync(kFull, n1, src),
+                     __shfl_sync(kFull, n2, src), base + src, __shfl_sync(kFull, gt, src),
+                     __shfl_sync(kFull, eb, src), false, 0.0);
+        }
+    }
+    int pos = n0;
+    for (int lv = 1; lv <= g.n_levels; ++lv) {
+        const int64_t h = g.q << (g.n_levels - lv);
+        int64_t n1 = 0, n2 = 0;
+        double gt = 0.0, eb = 0.0;
+        if (lane < 8) {
+            const int k9 = lane < 4 ? lane : lane + 1;       // 3 x 3 window, centre skipped
+            n1 = st.b1 + (int64_t)(k9 / 3 - 1) * h;
+            n2 = st.b2 + (int64_t)(k9 % 3 - 1) * h;
+            tab_cost(g, tab, um, W, i, n1, n2, gt, eb);
+        }
+        const double t = fmin(warp_min(lane < 8 ? gt + eb : DBL_MAX), st.bgt + st.beb);
+        Stage2 nx;
+        if (st.bgt - st.beb <= t)
+            nx.offer(g, phi2, U, i, ch, lane, st.b1, st.b2, st.bp, st.bgt, st.beb, st.known,
+                     st.bex);
+        unsigned mask = __ballot_sync(kFull, lane < 8 && gt - eb <= t);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            nx.offer(g, phi2, U, i, ch, lane, __shfl_sync(kFull, n1, src),
+                     __shfl_sync(kFull, n2, src), pos + src, __shfl_sync(kFull, gt, src),
+                     __shfl_sync(kFull, eb, src), false, 0.0);
+        }
+        st = nx;
+        pos += 8;
+    }
+    if (lane == 0) {
+        nu_out[2 * i] = st.b1;
+        nu_out[2 * i + 1] = st.b2;
+        idx_out[i] = st.bp;
+    }
+}
+
+// J's terms p_i g(f_i; x_i), one warp per point (the exact cost, the same
+// double as cost2d).
+__global__ void __launch_bounds__(kSearch2T) k2_J_terms(G2 g, const double* __restrict__ phi2,
+                                                        const double* __restrict__ U,
+                                                        const double* __restrict__ px,
+                                                        const int64_t* __restrict__ nu,
+                                                        double* __restrict__ terms) {
+    __shared__ double chs[kSearch2T / 32][kExactCh];
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= g.n_x * g.n_x) return;   // the same for the warp
+    const double c = warp_exact(g, phi2, U, i, nu[2 * i], nu[2 * i + 1], chs[threadIdx.x >> 5],
+                                lane);
+    if (lane == 0) terms[i] = __dmul_rn(px[i], c);
+}
+
+// Normalised one-dimensional noise weights (the factors of phi2).
+__global__ void k2_phin(G2 g, const double* __restrict__ p1, const double* __restrict__ sums,
+                        double* __restrict__ phin) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < g.n_w) phin[c] = __ddiv_rn(p1[c], sums[1]);
+}
+
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
@@ -318,7 +894,7 @@ const char* make_g2(const ucp2_params& p, G2* g) {
     if (p.n_coarse < 2 || p.n_coarse > 64) return "n_coarse must be in 2..64";
     if (p.n_levels < 0 || p.n_levels > 40) return "n_levels must be in 0..40";
     if (p.n_nbr < 0 || p.n_nbr > 8) return "n_nbr must be in 0..8";
-    if (p.reserved != 0) return "reserved must be 0";
+    if (p.direct < 0 || p.direct > 3) return "direct must be in 0..3";
     g->k = p.k;
     g->kk = p.k * p.k;
     g->sigma = p.sigma;
@@ -337,6 +913,21 @@ const char* make_g2(const ucp2_params& p, G2* g) {
     g->n_coarse = p.n_coarse;
     g->n_levels = p.n_levels;
     g->n_nbr = p.n_nbr;
+    g->direct = p.direct;
+    g->tab_lo = -g->n_w - 1;
+    g->tab_n = g->n_y + g->n_w + 2;
+    g->ext_n = g->tab_n + g->n_w - 1;
+    // Table cost against the exact fixed-order cost: below (2 n_w + 170) u M
+    // by a forward error analysis (M the magnitude bound of the terms); taken
+    // with a margin of two.
+    g->eps_k = (double)(4 * g->n_w + 512) * 0x1p-53;
+    // Source splits of the factorised u1 sums: about four blocks per SM.
+    {
+        const int64_t tiles = (g->n_y + 31) / 32, want = (4 * 152 + tiles * tiles - 1) /
+                                                         (tiles * tiles);
+        const int64_t n = g->n_x * g->n_x;
+        g->u1_splits = (int32_t)(want < 1 ? 1 : (want > 64 ? 64 : (want > n ? n : want)));
+    }
     const double vmax = (double)(g->hr + g->q + g->hx + g->hy + g->hw) * (double)g->one;
     if (!(vmax < 4.0e15)) return "lattice indices would overflow";
     return nullptr;
@@ -345,25 +936,52 @@ const char* make_g2(const ucp2_params& p, G2* g) {
 void launch2_setup(const G2& g, Dev2& d, int from_table, cudaStream_t s) {
     const int64_t n = g.n_x * g.n_x, big = n > g.n_w * g.n_w ? n : g.n_w * g.n_w;
     k2_exps<<<nblk(n > g.n_w ? n : g.n_w, 256), 256, 0, s>>>(g, d.px, d.phi1);
-    k2_fixed_sum<<<1, 1024, 8 * sum_chunks(n), s>>>(d.px, n, d.scratch);
-    k2_fixed_sum<<<1, 1024, 8 * sum_chunks(g.n_w), s>>>(d.phi1, g.n_w, d.scratch + 1);
+    k2_fixed_sum<<<1, 1024, 8 * sum_chunks(n), s>>>(d.px, n, 1.0, d.scratch);
+    k2_fixed_sum<<<1, 1024, 8 * sum_chunks(g.n_w), s>>>(d.phi1, g.n_w, 1.0, d.scratch + 1);
     k2_scale_init<<<nblk(big, 256), 256, 0, s>>>(g, d.px, d.phi1, d.phi2, d.scratch, d.nu[0],
                                                  d.table, from_table);
+    k2_phin<<<nblk(g.n_w, 256), 256, 0, s>>>(g, d.phi1, d.scratch, d.phin);
 }
 
 void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s) {
     const int64_t n = g.n_x * g.n_x;
-    k2_search<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(g, d.phi2, d.U, d.nu[cur],
-                                                            d.nu[cur ^ 1], d.idx);
+    if (g.direct & 1) {
+        k2_search<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(g, d.phi2, d.U, d.nu[cur],
+                                                                d.nu[cur ^ 1], d.idx);
+        return;
+    }
+    k2_tab_consts<<<1, 256, 0, s>>>(g, d.U, d.phin, d.scratch + 2);
+    k2_tab_rows<<<nblk(g.ext_n * g.tab_n, 256), 256, 0, s>>>(g, d.U, d.phin, d.H);
+    k2_tab_cols<<<nblk(g.tab_n * g.tab_n, 256), 256, 0, s>>>(g, d.H, d.phin, d.tab);
+    k2_search_scr<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(
+        g, d.phi2, d.U, d.tab, d.scratch + 2, d.nu[cur], d.nu[cur ^ 1], d.idx);
 }
 
 void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
-    k2_mmse<<<nblk(g.n_y * g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+    if (g.direct & 2) {
+        k2_mmse<<<nblk(g.n_y * g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
+        return;
+    }
+    const int64_t n = g.n_x * g.n_x, tiles = (g.n_y + kU1Tile - 1) / kU1Tile;
+    const int64_t len = (n + g.u1_splits - 1) / g.u1_splits;
+    float2* fa = reinterpret_cast<float2*>(d.fa);
+    float2* fb = reinterpret_cast<float2*>(d.fb);
+    k2_u1_mins<<<(unsigned)(2 * g.n_y + 1), 256, 0, s>>>(g, d.nu[buf], d.mins);
+    k2_u1_factors<<<nblk(n * g.n_y, 256), 256, 0, s>>>(g, d.nu[buf], d.mins, fa, fb, d.fa64,
+                                                       d.fb64, d.fv);
+    k2_u1_sums<<<dim3((unsigned)tiles, (unsigned)tiles, (unsigned)g.u1_splits), 256, 0, s>>>(
+        g, fa, fb, d.fv, len, d.part);
+    cudaMemsetAsync(d.list, 0, sizeof(int32_t), s);
+    k2_u1_finish<<<nblk(g.n_y * g.n_y, 128), 128, 0, s>>>(g, d.part, g.u1_splits, d.U, d.list);
+    k2_u1_wide<<<(unsigned)(4 * 152), 128, 0, s>>>(g, d.nu[buf], d.fa64, d.fb64, d.fv, d.list,
+                                                   d.U);
 }
 
 void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s) {
-    k2_costs<<<nblk(g.n_x * g.n_x, 128), 128, 0, s>>>(g, d.phi2, d.U, d.nu[buf], d.terms);
-    k2_J<<<1, 32, 0, s>>>(g, d.px, d.terms, out);
+    const int64_t n = g.n_x * g.n_x;
+    k2_J_terms<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(g, d.phi2, d.U, d.px, d.nu[buf],
+                                                             d.terms);
+    k2_fixed_sum<<<1, 1024, 8 * sum_chunks(n), s>>>(d.terms, n, 0.5, out);
 }
 
 void launch2_table(const G2& g, Dev2& d, int buf, cudaStream_t s) {

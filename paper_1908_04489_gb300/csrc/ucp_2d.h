@@ -13,12 +13,19 @@ namespace ucp {
 // Integer geometry: half widths in units of delta, sizes per axis, the
 // controller lattice (value nu delta 2^-shift, shift = n_levels), the coarse
 // spacing q (units of delta, even) and the candidate-list length.
+// Screened search: the correlation tables cover first-tap cells
+// [tab_lo, tab_lo + tab_n) per axis (tab_lo = -n_w - 1, tab_n = n_y + n_w + 2),
+// their row pass ext_n = tab_n + n_w - 1 rows; eps_k scales the error bound
+// of a table cost.
 struct G2 {
     double k, kk, sigma, delta;
     int64_t hx, hw, hy, hr, n_x, n_w, n_y;
     int32_t shift;
     int64_t one, q, n_cand;
-    int32_t n_coarse, n_levels, n_nbr;
+    int32_t n_coarse, n_levels, n_nbr, direct;
+    int64_t tab_lo, tab_n, ext_n;
+    double eps_k;
+    int32_t u1_splits;   // source splits of the factorised u1 sums
 };
 
 // Fills g from p; nullptr or the reason p is invalid.
@@ -35,6 +42,17 @@ struct Dev2 {
     double* scratch; // normalising sums
     double* table;   // [2 n_x^2] host table staging
     double* J;       // [J capacity] J history
+    double* phin;    // [n_w] normalised one-dimensional noise weights
+    double* H;       // [7 ext_n tab_n] row pass of the correlation tables
+    double* tab;     // [tab_n^2 x 8] correlation tables, 8 slots per cell
+    double* mins;    // [2 n_y + 1] exponent minima of the factorised u1 step
+    double* fa;      // [n_y x n_x^2] prior x axis-1 factors, double-float pairs
+    double* fb;      // [n_y x n_x^2] axis-2 factors, double-float pairs
+    double* fa64;    // the same in FP64
+    double* fb64;
+    double* fv;      // [2 n_x^2] f values
+    double* part;    // [u1_splits x 3 x n_y^2] partial sums
+    int32_t* list;   // [1 + n_y^2] count, then the targets of the FP64 pass
 };
 
 void launch2_setup(const G2& g, Dev2& d, int from_table, cudaStream_t s);

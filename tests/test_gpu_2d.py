@@ -145,11 +145,12 @@ def test_start_equals_the_oracle(B, O):
         assert abs(J[0] - o.J(nu0, U0)) <= 1e-12 * J[0]
 
 
+@pytest.mark.parametrize("direct", [0, 3], ids=["fast", "direct"])
 @pytest.mark.parametrize("p,sweeps", [(P2, 8), (P2B, 3)], ids=["P2", "P2B"])
-def test_lockstep(B, O, p, sweeps):
+def test_lockstep(B, O, p, sweeps, direct):
     o = O.Oracle2D(p)
     ties = 0
-    with B.Instance2D(p) as g:
+    with B.Instance2D(dict(p, direct=direct)) as g:
         for s in range(sweeps):
             pre = g.get_controllers()
             nu_pre = lattice(o, pre["f"])
@@ -267,3 +268,79 @@ def test_larger_grid_sampled(B, O):
             for tt in t:
                 Uo = o.mmse(nu_post, int(tt), int(tt) + 1)
                 assert np.max(np.abs(post["U"][tt] - Uo[tt])) <= 1e-11
+
+
+# n_w^2 = 16641 taps: the exact quadratures of the screened search run on one
+# lane (more chunk sums than a warp keeps in shared memory).
+P2W = dict(k=0.2, sigma=0.6, delta=0.0625, x_half=1.0, w_half=4.0, y_half=6.0,
+           cand_half=2.0, n_coarse=5, n_levels=3, n_nbr=1)
+
+
+def staircase_table(o, step):
+    """A quantised start (f = step round(x / step) per axis): whole windows of
+    equal values, so the list is full of duplicates and exact ties."""
+    xs = o.grid(o.n_x)
+    h = step * np.round(xs / step)
+    return np.stack([np.repeat(h, o.n_x), np.tile(h, o.n_x)], axis=1)
+
+
+@pytest.mark.parametrize("case", ["P2B", "P2W", "staircase"])
+def test_screened_equals_direct(B, O, case):
+    """The screened search makes the direct search's decisions bit for bit
+    (values and list positions) at every sweep."""
+    p, sweeps, tab = {"P2B": (P2B, 4, None), "P2W": (P2W, 2, None),
+                      "staircase": (P2, 6, "stairs")}[case]
+    o = O.Oracle2D(p)
+    init = staircase_table(o, 5.0) if tab else None
+    with B.Instance2D(dict(p, direct=0), init_f=init) as a, \
+            B.Instance2D(dict(p, direct=1), init_f=init) as b:
+        for s in range(sweeps):
+            a.sweep(1)
+            b.sweep(1)
+            sa, sb = a.get_controllers(), b.get_controllers()
+            assert np.array_equal(sa["f"], sb["f"]), s
+            assert np.array_equal(sa["idx"], sb["idx"]), s
+            assert np.array_equal(sa["U"], sb["U"]), s
+        assert np.array_equal(a.J_history(), b.J_history())
+    if case == "P2W":
+        # and the oracle's decisions from the same state
+        with B.Instance2D(p) as g:
+            pre = g.get_controllers()
+            g.sweep(1)
+            post = g.get_controllers()
+            pts = np.arange(0, o.N, 7)
+            check_sweep(o, lattice(o, pre["f"]), pre["U"], post["f"], post["idx"], points=pts)
+
+
+def two_clusters(o, L):
+    """f = (L, -L) on the left half of the x0 grid, (-L, L) on the right:
+    at the target y = (L, L) each source is near in one component only, so
+    the per-axis minima of the factorised weights sum far below the joint
+    one (every factorised weight underflows there)."""
+    a = np.repeat(np.arange(o.n_x), o.n_x)
+    left = a < o.n_x // 2
+    return np.stack([np.where(left, L, -L), np.where(left, -L, L)], axis=1).astype(float)
+
+
+@pytest.mark.parametrize("case", ["identity", "clusters", "clusters_wide"])
+def test_factorised_u1_matches_direct(B, O, case):
+    """identity: every target on the double-float sums; clusters (L = 20):
+    the corner target's factors underflow even in FP64 (gap 2 L^2 = 800), so
+    the direct form runs there; clusters_wide (L = 6.25, gap ~78): beyond
+    FP32's range, inside FP64's -- the FP64 pass."""
+    p = dict(P2B, y_half=30.0) if case.startswith("clusters") else P2B
+    o = O.Oracle2D(p)
+    init = {"identity": None, "clusters": two_clusters(o, 20.0),
+            "clusters_wide": two_clusters(o, 6.25)}[case]
+    with B.Instance2D(dict(p, direct=0), init_f=init) as a, \
+            B.Instance2D(dict(p, direct=2), init_f=init) as b:
+        Ua, Ub = a.get_controllers()["U"], b.get_controllers()["U"]
+        nu = lattice(o, a.get_controllers()["f"])
+        Uo = o.mmse(nu)
+        assert np.max(np.abs(Ua - Ub)) <= 1e-11
+        assert np.max(np.abs(Ua - Uo)) <= 1e-11
+        if case == "clusters":
+            # the corner target (L, L) itself (where the fallback ran)
+            j = o.n_y // 2 + round(20.0 / p["delta"])
+            t = j * o.n_y + j
+            assert np.array_equal(Ua[t], Ub[t])
