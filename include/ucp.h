@@ -452,9 +452,11 @@ typedef struct {
     int32_t n_nbr;      /* window radius, 0..8                                 */
     int32_t direct;     /* bit 0 clear: screened search (correlation tables of
                            u1 with a certified error bound, the exact quadrature
-                           only for candidates the bound cannot separate); set:
-                           the exact quadrature for every candidate (same
-                           decisions).  Bit 1 clear: the u1 weights factorised
+                           only for candidates the bound cannot separate) and J
+                           from the same tables (within half the prior-weighted
+                           bound, ~1e-10, of the exact J); set: the exact
+                           quadrature for every candidate (same decisions) and
+                           for J.  Bit 1 clear: the u1 weights factorised
                            per axis (GEMM-shaped sums); set: each weight's
                            exponential formed directly (u1 equal to rounding). */
 } ucp2_params;

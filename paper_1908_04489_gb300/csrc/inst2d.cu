@@ -128,7 +128,7 @@ extern "C" ucp_status ucp2_create(ucp_ctx* ctx, const ucp2_params* p, const doub
         d.part = (double*)alloc2(in, 24 * (size_t)g.u1_splits * (size_t)(g.n_y * g.n_y));
         d.fa64 = (double*)alloc2(in, 8 * n * (size_t)g.n_y);
         d.fb64 = (double*)alloc2(in, 8 * n * (size_t)g.n_y);
-        d.fv = (double*)alloc2(in, 16 * n);
+        d.fv = (double*)alloc2(in, 24 * n);
         d.list = (int32_t*)alloc2(in, 4 * (1 + (size_t)(g.n_y * g.n_y)));
     }
     if ((screened && (!d.H || !d.tab)) ||

@@ -90,11 +90,31 @@ __device__ double S2d(const G2& g, const double* __restrict__ phi2,
     return acc.result();
 }
 
-// k^2 |u - x_i|^2, the first part of the marginal cost.
-__device__ __forceinline__ double kterm2(const G2& g, int64_t i, int64_t nu1, int64_t nu2) {
-    const double d1 = __dsub_rn(val2(g, nu1), grid2(g, i / g.n_x, g.hx));
-    const double d2 = __dsub_rn(val2(g, nu2), grid2(g, i % g.n_x, g.hx));
+// k^2 |u - x|^2, the first part of the marginal cost, at x = (xa, xb).
+__device__ __forceinline__ double kterm2x(const G2& g, double xa, double xb, int64_t nu1,
+                                          int64_t nu2) {
+    const double d1 = __dsub_rn(val2(g, nu1), xa);
+    const double d2 = __dsub_rn(val2(g, nu2), xb);
     return __dmul_rn(g.kk, __dadd_rn(__dmul_rn(d1, d1), __dmul_rn(d2, d2)));
+}
+__device__ __forceinline__ double kterm2(const G2& g, int64_t i, int64_t nu1, int64_t nu2) {
+    return kterm2x(g, grid2(g, i / g.n_x, g.hx), grid2(g, i % g.n_x, g.hx), nu1, nu2);
+}
+
+// Per-point constants of the search: grid coordinates and position.
+struct Pt2 {
+    int64_t i;
+    int32_t a, b;
+    double xa, xb;
+};
+__device__ __forceinline__ Pt2 make_pt2(const G2& g, int64_t i) {
+    Pt2 q;
+    q.i = i;
+    q.a = (int32_t)(i / g.n_x);
+    q.b = (int32_t)(i - (int64_t)q.a * g.n_x);
+    q.xa = grid2(g, q.a, g.hx);
+    q.xb = grid2(g, q.b, g.hx);
+    return q;
 }
 
 __device__ __forceinline__ double cost2d(const G2& g, const double* __restrict__ phi2,
@@ -105,6 +125,31 @@ __device__ __forceinline__ double cost2d(const G2& g, const double* __restrict__
 
 __device__ __forceinline__ bool before2(double ga, int32_t pa, double gb, int32_t pb) {
     return ga < gb || (ga == gb && pa < pb);
+}
+
+// Candidate p of stage 0 with the point's constants (32-bit index arithmetic).
+__device__ __forceinline__ void stage0_cand_pt(const G2& g, const int64_t* __restrict__ nu_pre,
+                                               const Pt2& q, int p, int64_t& n1, int64_t& n2) {
+    const int r = g.n_nbr, side = 2 * r + 1, win = side * side;
+    if (p == 0) {
+        n1 = nu_pre[2 * q.i];
+        n2 = nu_pre[2 * q.i + 1];
+        return;
+    }
+    if (p < win) {
+        const int k0 = p - 1, centre = r * side + r;
+        const int k = k0 < centre ? k0 : k0 + 1;          // the window, centre skipped
+        const int a = q.a + k / side - r, b = q.b + k % side - r;
+        const int nx = (int)g.n_x;
+        const int64_t j = (a < 0 || a >= nx || b < 0 || b >= nx) ? q.i : (int64_t)a * nx + b;
+        n1 = nu_pre[2 * j];
+        n2 = nu_pre[2 * j + 1];
+        return;
+    }
+    const int ci = p - win, nc = g.n_coarse;
+    const int64_t hq = g.q / 2;
+    n1 = (int64_t)(2 * (ci / nc) - (nc - 1)) * hq * g.one;
+    n2 = (int64_t)(2 * (ci % nc) - (nc - 1)) * hq * g.one;
 }
 
 // Candidate p of stage 0 (incumbent, window, coarse grid) of point i.
@@ -272,36 +317,40 @@ __global__ void __launch_bounds__(256) k2_u1_mins(G2 g, const int64_t* __restric
     if (threadIdx.x == 0) mins[b] = red[0];
 }
 
+// Per source: fv[2 i + q] = f_iq and fv[2 N + i] = exp(-(P_i - min P)).
+__global__ void __launch_bounds__(256) k2_u1_sources(G2 g, const int64_t* __restrict__ nu,
+                                                     const double* __restrict__ mins,
+                                                     double* __restrict__ fv) {
+    const int64_t n = g.n_x * g.n_x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    fv[2 * i] = val2(g, nu[2 * i]);
+    fv[2 * i + 1] = val2(g, nu[2 * i + 1]);
+    fv[2 * n + i] = exp(-(prior_expo(g, i) - mins[2 * g.n_y]));
+}
+
 // Factor tables, target-major (entry j N + i, N = n_x^2 sources):
 //   fa = exp(-(P_i - min P)) exp(-(Q_i(y_j) - min Q)),  fb = exp(-(R_i(y_j) - min R)),
 // formed in FP64 and kept both as double-float pairs (hi, lo) for the sums
-// and in FP64 for the targets whose factor leaves FP32's range; fv[2 i + q]
-// = f_iq.
-__global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const int64_t* __restrict__ nu,
-                                                     const double* __restrict__ mins,
+// and in FP64 for the targets whose factor leaves FP32's range.
+__global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const double* __restrict__ mins,
+                                                     const double* __restrict__ fv,
                                                      float2* __restrict__ fa,
                                                      float2* __restrict__ fb,
                                                      double* __restrict__ fa64,
-                                                     double* __restrict__ fb64,
-                                                     double* __restrict__ fv) {
+                                                     double* __restrict__ fb64) {
     const int64_t n = g.n_x * g.n_x;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n * g.n_y) return;
     const int64_t j = id / n, i = id % n;
     const double y = grid2(g, j, g.hy);
-    const double f1 = val2(g, nu[2 * i]), f2 = val2(g, nu[2 * i + 1]);
-    const double pa = exp(-(prior_expo(g, i) - mins[2 * g.n_y]));
-    const double va = pa * exp(-(half_sq(y, f1) - mins[j]));
-    const double vb = exp(-(half_sq(y, f2) - mins[g.n_y + j]));
+    const double va = fv[2 * n + i] * exp(-(half_sq(y, fv[2 * i]) - mins[j]));
+    const double vb = exp(-(half_sq(y, fv[2 * i + 1]) - mins[g.n_y + j]));
     const dfloat a = df_from_double(va), b = df_from_double(vb);
     fa[id] = make_float2(a.hi, a.lo);
     fb[id] = make_float2(b.hi, b.lo);
     fa64[id] = va;
     fb64[id] = vb;
-    if (j == 0) {
-        fv[2 * i] = f1;
-        fv[2 * i + 1] = f2;
-    }
 }
 
 // Partial sums of one split of the sources for a 32 x 32 tile of targets in
@@ -311,7 +360,7 @@ __global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const int64_t* __rest
 // unnormalised pairs, accumulation normalised per term) and then added to
 // the running sums with the accurate double-float addition, so a split of K
 // sources carries a relative error of about (32 + K / 32) 2^-47 of its sum
-// of magnitudes.
+// of magnitudes.  Stages that cannot matter on the tile are skipped.
 constexpr int kU1Tile = 32, kU1Stage = 32;
 __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict__ fa,
                                                   const float2* __restrict__ fb,
@@ -329,12 +378,17 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
 #pragma unroll
         for (int c = 0; c < 2; ++c) D[r][c] = N1[r][c] = N2[r][c] = dfloat{0.0f, 0.0f};
     for (int64_t i0 = i_lo; i0 < i_hi; i0 += kU1Stage) {
+        bool big_a = false, big_b = false;
         for (int k = threadIdx.x; k < kU1Stage * kU1Tile; k += 256) {
             const int sj = k / kU1Stage, si = k % kU1Stage;   // consecutive sources
             const int64_t i = i0 + si;
             const bool ok = i < i_hi;
-            sa[si][sj] = ok && j1_0 + sj < ny ? fa[(j1_0 + sj) * n + i] : make_float2(0.f, 0.f);
-            sb[si][sj] = ok && j2_0 + sj < ny ? fb[(j2_0 + sj) * n + i] : make_float2(0.f, 0.f);
+            const float2 va = ok && j1_0 + sj < ny ? fa[(j1_0 + sj) * n + i] : make_float2(0.f, 0.f);
+            const float2 vb = ok && j2_0 + sj < ny ? fb[(j2_0 + sj) * n + i] : make_float2(0.f, 0.f);
+            sa[si][sj] = va;
+            sb[si][sj] = vb;
+            big_a |= va.x >= 0x1p-126f;
+            big_b |= vb.x >= 0x1p-126f;
         }
         if (threadIdx.x < 2 * kU1Stage) {
             const int si = threadIdx.x >> 1, q = threadIdx.x & 1;
@@ -342,7 +396,14 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
             const dfloat f = df_from_double(i < i_hi ? fv[2 * i + q] : 0.0);
             sf[si][q] = make_float2(f.hi, f.lo);
         }
-        __syncthreads();
+        // A stage whose axis-1 or axis-2 factors are all below 2^-126 on this
+        // tile adds less than N 2^-126 to any sum (factors are at most 1): at
+        // most 2^-48 of a denominator that stays on this path (>= 2^-60).
+        const bool live = __syncthreads_or(big_a) && __syncthreads_or(big_b);
+        if (!live) {
+            __syncthreads();
+            continue;
+        }
         dfloat d[2][2], m1[2][2], m2[2][2];
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -645,7 +706,7 @@ __device__ __forceinline__ int64_t tcell(const G2& g, int64_t j) {
 // Table cost of candidate (nu1, nu2) at x0 point i and the bound eb on its
 // distance from the exact fixed-order cost cost2d.
 __device__ __forceinline__ void tab_cost(const G2& g, const double* __restrict__ tab, double um,
-                                         double W, int64_t i, int64_t nu1, int64_t nu2,
+                                         double W, const Pt2& pt, int64_t nu1, int64_t nu2,
                                          double& gt, double& eb) {
     const TapBase b = tap_base(g, nu1, nu2);
     const int64_t L = g.tab_n;
@@ -665,7 +726,7 @@ __device__ __forceinline__ void tab_cost(const G2& g, const double* __restrict__
                       w01 * w10 * P01[6] + w01 * w11 * P01[4] + w10 * w11 * P10[3];
     const double uu = b.u1 * b.u1 + b.u2 * b.u2;
     const double S = W * uu - 2.0 * (b.u1 * A1 + b.u2 * A2) + Cd + 2.0 * Cx;
-    gt = kterm2(g, i, nu1, nu2) + S;
+    gt = kterm2x(g, pt.xa, pt.xb, nu1, nu2) + S;
     const double M = uu + 2.0 * (fabs(b.u1) + fabs(b.u2)) * um + 2.0 * um * um;
     eb = g.eps_k * (M + fabs(gt));
 }
@@ -787,14 +848,15 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (i >= g.n_x * g.n_x) return;   // the same for the warp
     const double um = consts[0], W = consts[1];
+    const Pt2 pt = make_pt2(g, i);
     const int64_t side = 2 * (int64_t)g.n_nbr + 1;
     const int n0 = (int)(side * side + (int64_t)g.n_coarse * g.n_coarse);
     double thr = DBL_MAX;
     for (int p = lane; p < n0; p += 32) {
         int64_t n1, n2;
         double gt, eb;
-        stage0_cand(g, nu_pre, i, p, n1, n2);
-        tab_cost(g, tab, um, W, i, n1, n2, gt, eb);
+        stage0_cand_pt(g, nu_pre, pt, p, n1, n2);
+        tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
         thr = fmin(thr, gt + eb);
     }
     thr = warp_min(thr);
@@ -805,8 +867,8 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
         double gt = 0.0, eb = 0.0;
         bool cont = false;
         if (p < n0) {
-            stage0_cand(g, nu_pre, i, p, n1, n2);
-            tab_cost(g, tab, um, W, i, n1, n2, gt, eb);
+            stage0_cand_pt(g, nu_pre, pt, p, n1, n2);
+            tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
             cont = gt - eb <= thr;
         }
         unsigned mask = __ballot_sync(kFull, cont);
@@ -827,7 +889,7 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
             const int k9 = lane < 4 ? lane : lane + 1;       // 3 x 3 window, centre skipped
             n1 = st.b1 + (int64_t)(k9 / 3 - 1) * h;
             n2 = st.b2 + (int64_t)(k9 % 3 - 1) * h;
-            tab_cost(g, tab, um, W, i, n1, n2, gt, eb);
+            tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
         }
         const double t = fmin(warp_min(lane < 8 ? gt + eb : DBL_MAX), st.bgt + st.beb);
         Stage2 nx;
@@ -866,6 +928,21 @@ __global__ void __launch_bounds__(kSearch2T) k2_J_terms(G2 g, const double* __re
     const double c = warp_exact(g, phi2, U, i, nu[2 * i], nu[2 * i + 1], chs[threadIdx.x >> 5],
                                 lane);
     if (lane == 0) terms[i] = __dmul_rn(px[i], c);
+}
+
+// J's terms p_i g~(f_i; x_i) from the correlation tables (the screened
+// mode): |g~ - g| <= eb_i, so J is within (1/2) sum_i p_i eb_i of the exact
+// fixed-order J.
+__global__ void __launch_bounds__(256) k2_J_terms_tab(G2 g, const double* __restrict__ tab,
+                                                      const double* __restrict__ consts,
+                                                      const double* __restrict__ px,
+                                                      const int64_t* __restrict__ nu,
+                                                      double* __restrict__ terms) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_x * g.n_x) return;
+    double gt, eb;
+    tab_cost(g, tab, consts[0], consts[1], make_pt2(g, i), nu[2 * i], nu[2 * i + 1], gt, eb);
+    terms[i] = px[i] * gt;
 }
 
 // Normalised one-dimensional noise weights (the factors of phi2).
@@ -950,9 +1027,6 @@ void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s) {
                                                                 d.nu[cur ^ 1], d.idx);
         return;
     }
-    k2_tab_consts<<<1, 256, 0, s>>>(g, d.U, d.phin, d.scratch + 2);
-    k2_tab_rows<<<nblk(g.ext_n * g.tab_n, 256), 256, 0, s>>>(g, d.U, d.phin, d.H);
-    k2_tab_cols<<<nblk(g.tab_n * g.tab_n, 256), 256, 0, s>>>(g, d.H, d.phin, d.tab);
     k2_search_scr<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(
         g, d.phi2, d.U, d.tab, d.scratch + 2, d.nu[cur], d.nu[cur ^ 1], d.idx);
 }
@@ -967,8 +1041,8 @@ void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
     float2* fa = reinterpret_cast<float2*>(d.fa);
     float2* fb = reinterpret_cast<float2*>(d.fb);
     k2_u1_mins<<<(unsigned)(2 * g.n_y + 1), 256, 0, s>>>(g, d.nu[buf], d.mins);
-    k2_u1_factors<<<nblk(n * g.n_y, 256), 256, 0, s>>>(g, d.nu[buf], d.mins, fa, fb, d.fa64,
-                                                       d.fb64, d.fv);
+    k2_u1_sources<<<nblk(n, 256), 256, 0, s>>>(g, d.nu[buf], d.mins, d.fv);
+    k2_u1_factors<<<nblk(n * g.n_y, 256), 256, 0, s>>>(g, d.mins, d.fv, fa, fb, d.fa64, d.fb64);
     k2_u1_sums<<<dim3((unsigned)tiles, (unsigned)tiles, (unsigned)g.u1_splits), 256, 0, s>>>(
         g, fa, fb, d.fv, len, d.part);
     cudaMemsetAsync(d.list, 0, sizeof(int32_t), s);
@@ -979,6 +1053,16 @@ void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
 
 void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s) {
     const int64_t n = g.n_x * g.n_x;
+    if (!(g.direct & 1)) {
+        // The tables of the new u1 table: J's terms now, the next search later.
+        k2_tab_consts<<<1, 256, 0, s>>>(g, d.U, d.phin, d.scratch + 2);
+        k2_tab_rows<<<nblk(g.ext_n * g.tab_n, 256), 256, 0, s>>>(g, d.U, d.phin, d.H);
+        k2_tab_cols<<<nblk(g.tab_n * g.tab_n, 256), 256, 0, s>>>(g, d.H, d.phin, d.tab);
+        k2_J_terms_tab<<<nblk(n, 256), 256, 0, s>>>(g, d.tab, d.scratch + 2, d.px, d.nu[buf],
+                                                    d.terms);
+        k2_fixed_sum<<<1, 1024, 8 * sum_chunks(n), s>>>(d.terms, n, 0.5, out);
+        return;
+    }
     k2_J_terms<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(g, d.phi2, d.U, d.px, d.nu[buf],
                                                              d.terms);
     k2_fixed_sum<<<1, 1024, 8 * sum_chunks(n), s>>>(d.terms, n, 0.5, out);

@@ -50,7 +50,7 @@ struct Dev2 {
     double* fb;      // [n_y x n_x^2] axis-2 factors, double-float pairs
     double* fa64;    // the same in FP64
     double* fb64;
-    double* fv;      // [2 n_x^2] f values
+    double* fv;      // [3 n_x^2] f values, then the prior factors
     double* part;    // [u1_splits x 3 x n_y^2] partial sums
     int32_t* list;   // [1 + n_y^2] count, then the targets of the FP64 pass
 };
@@ -58,6 +58,10 @@ struct Dev2 {
 void launch2_setup(const G2& g, Dev2& d, int from_table, cudaStream_t s);
 void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s);
 void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s);
+// J of controller buffer buf under the current u1 table into *out.  In the
+// screened mode it first rebuilds the correlation tables of that u1 table
+// (J's terms come from them, and the next search uses them), so it runs
+// after every change of U.
 void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s);
 void launch2_table(const G2& g, Dev2& d, int buf, cudaStream_t s);
 
