@@ -120,6 +120,7 @@ extern "C" ucp_status ucp2_create(ucp_ctx* ctx, const ucp2_params* p, const doub
     if (screened) {
         d.H = (double*)alloc2(in, 8 * 7 * (size_t)(g.ext_n * g.tab_n));
         d.tab = (double*)alloc2(in, 64 * (size_t)(g.tab_n * g.tab_n));
+        d.tabf = (float2*)alloc2(in, 64 * (size_t)(g.tab_n * g.tab_n));
     }
     if (factorised) {
         d.mins = (double*)alloc2(in, 8 * (size_t)(2 * g.n_y + 1));
@@ -131,7 +132,7 @@ extern "C" ucp_status ucp2_create(ucp_ctx* ctx, const ucp2_params* p, const doub
         d.fv = (double*)alloc2(in, 24 * n);
         d.list = (int32_t*)alloc2(in, 4 * (1 + (size_t)(g.n_y * g.n_y)));
     }
-    if ((screened && (!d.H || !d.tab)) ||
+    if ((screened && (!d.H || !d.tab || !d.tabf)) ||
         (factorised && (!d.mins || !d.fa || !d.fb || !d.part || !d.fa64 || !d.fb64 || !d.fv ||
                         !d.list)) ||
         !d.phin || !d.px || !d.phi1 || !d.phi2 || !d.U || !d.nu[0] || !d.nu[1] || !d.idx || !d.terms ||

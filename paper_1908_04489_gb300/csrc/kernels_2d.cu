@@ -106,6 +106,7 @@ struct Pt2 {
     int64_t i;
     int32_t a, b;
     double xa, xb;
+    dfloat xa_d, xb_d;
 };
 __device__ __forceinline__ Pt2 make_pt2(const G2& g, int64_t i) {
     Pt2 q;
@@ -114,6 +115,8 @@ __device__ __forceinline__ Pt2 make_pt2(const G2& g, int64_t i) {
     q.b = (int32_t)(i - (int64_t)q.a * g.n_x);
     q.xa = grid2(g, q.a, g.hx);
     q.xb = grid2(g, q.b, g.hx);
+    q.xa_d = df_from_double(q.xa);
+    q.xb_d = df_from_double(q.xb);
     return q;
 }
 
@@ -679,7 +682,8 @@ __global__ void __launch_bounds__(256) k2_tab_rows(G2 g, const double* __restric
 // Column pass: tab(a1, a2) = sum_c phi_c H(a1 + c, a2), 8 slots per cell.
 __global__ void __launch_bounds__(256) k2_tab_cols(G2 g, const double* __restrict__ H,
                                                    const double* __restrict__ phin,
-                                                   double* __restrict__ tab) {
+                                                   double* __restrict__ tab,
+                                                   float2* __restrict__ tabf) {
     const int64_t L = g.tab_n, plane = g.ext_n * L;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= L * L) return;
@@ -696,6 +700,14 @@ __global__ void __launch_bounds__(256) k2_tab_cols(G2 g, const double* __restric
     o[1] = make_double2(acc[2], acc[3]);
     o[2] = make_double2(acc[4], acc[5]);
     o[3] = make_double2(acc[6], 0.0);
+    float4* of = reinterpret_cast<float4*>(tabf + 8 * id);
+    dfloat v[8];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) v[f] = df_from_double(acc[f]);
+    v[7] = dfloat{0.0f, 0.0f};
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+        of[f] = make_float4(v[2 * f].hi, v[2 * f].lo, v[2 * f + 1].hi, v[2 * f + 1].lo);
 }
 
 __device__ __forceinline__ int64_t tcell(const G2& g, int64_t j) {
@@ -729,6 +741,78 @@ __device__ __forceinline__ void tab_cost(const G2& g, const double* __restrict__
     gt = kterm2x(g, pt.xa, pt.xb, nu1, nu2) + S;
     const double M = uu + 2.0 * (fabs(b.u1) + fabs(b.u2)) * um + 2.0 * um * um;
     eb = g.eps_k * (M + fabs(gt));
+}
+
+// The table cost in double-float arithmetic on the FP32 pipe, with the
+// bound eps_df (M + |g|).  The bilinear weights are exact pairs (the
+// fractions have at most 24 bits); products are accumulated unnormalised
+// into normalised sums.  False (nothing computed) when a lattice index is
+// beyond 2^44, where the pair conversion is not exact.
+__device__ __forceinline__ dfloat df_dot_add(dfloat acc, dfloat a, dfloat b) {
+    float p, e;
+    df_mul_raw(a, b, p, e);
+    return df_acc(acc, p, e);
+}
+__device__ __forceinline__ bool tab_cost_df(const G2& g, const float2* __restrict__ tabf,
+                                            double um, dfloat W, const Pt2& pt, int64_t nu1,
+                                            int64_t nu2, double& gt, double& eb) {
+    const int64_t lim = (int64_t)1 << 44;
+    if (nu1 >= lim || nu1 <= -lim || nu2 >= lim || nu2 <= -lim) return false;
+    const int64_t c1 = nu1 >> g.shift, c2 = nu2 >> g.shift;
+    const float t1 = __fmul_rn(__int2float_rn((int)(nu1 - (c1 << g.shift))), g.inv_one_f);
+    const float t2 = __fmul_rn(__int2float_rn((int)(nu2 - (c2 << g.shift))), g.inv_one_f);
+    const float s1 = __fsub_rn(1.0f, t1), s2 = __fsub_rn(1.0f, t2);   // exact
+    auto exact_prod = [](float a, float b) {
+        const float p = __fmul_rn(a, b);
+        return dfloat{p, __fmaf_rn(a, b, -p)};
+    };
+    const dfloat w00 = exact_prod(s1, s2), w01 = exact_prod(s1, t2);
+    const dfloat w10 = exact_prod(t1, s2), w11 = exact_prod(t1, t2);
+    const int64_t L = g.tab_n, jb1 = c1 - g.hw + g.hy, jb2 = c2 - g.hw + g.hy;
+    const int64_t a1 = tcell(g, jb1), a1p = tcell(g, jb1 + 1);
+    const int64_t a2 = tcell(g, jb2), a2p = tcell(g, jb2 + 1);
+    const float2* P00 = tabf + 8 * (a1 * L + a2);
+    const float2* P01 = tabf + 8 * (a1 * L + a2p);
+    const float2* P10 = tabf + 8 * (a1p * L + a2);
+    const float2* P11 = tabf + 8 * (a1p * L + a2p);
+    auto T = [](const float2* P, int f) {
+        const float2 v = P[f];
+        return dfloat{v.x, v.y};
+    };
+    const dfloat z{0.0f, 0.0f};
+    dfloat A1 = df_dot_add(z, w00, T(P00, 0));
+    A1 = df_dot_add(A1, w01, T(P01, 0));
+    A1 = df_dot_add(A1, w10, T(P10, 0));
+    A1 = df_dot_add(A1, w11, T(P11, 0));
+    dfloat A2 = df_dot_add(z, w00, T(P00, 1));
+    A2 = df_dot_add(A2, w01, T(P01, 1));
+    A2 = df_dot_add(A2, w10, T(P10, 1));
+    A2 = df_dot_add(A2, w11, T(P11, 1));
+    dfloat C = df_dot_add(z, df_mul(w00, w00), T(P00, 2));
+    C = df_dot_add(C, df_mul(w01, w01), T(P01, 2));
+    C = df_dot_add(C, df_mul(w10, w10), T(P10, 2));
+    C = df_dot_add(C, df_mul(w11, w11), T(P11, 2));
+    dfloat X = df_dot_add(z, df_mul(w00, w01), T(P00, 3));
+    X = df_dot_add(X, df_mul(w00, w10), T(P00, 4));
+    X = df_dot_add(X, df_mul(w00, w11), T(P00, 5));
+    X = df_dot_add(X, df_mul(w01, w10), T(P01, 6));
+    X = df_dot_add(X, df_mul(w01, w11), T(P01, 4));
+    X = df_dot_add(X, df_mul(w10, w11), T(P10, 3));
+    const dfloat us{g.us_hi, g.us_lo};
+    const dfloat u1 = df_mul(df_from_i64(nu1), us), u2 = df_mul(df_from_i64(nu2), us);
+    const dfloat uu = df_dot_add(df_mul(u1, u1), u2, u2);
+    dfloat S = df_mul(W, uu);
+    S = df_dot_add(S, dfloat{-2.0f * u1.hi, -2.0f * u1.lo}, A1);
+    S = df_dot_add(S, dfloat{-2.0f * u2.hi, -2.0f * u2.lo}, A2);
+    S = df_add(S, C);
+    S = df_add(S, dfloat{2.0f * X.hi, 2.0f * X.lo});
+    const dfloat d1 = df_sub(u1, pt.xa_d), d2 = df_sub(u2, pt.xb_d);
+    const dfloat kt = df_mul(df_dot_add(df_mul(d1, d1), d2, d2), dfloat{g.kk_hi, g.kk_lo});
+    gt = df_to_double(df_add(kt, S));
+    const float ua = fabsf(u1.hi) + fabsf(u2.hi), umf = (float)um;
+    const float M = uu.hi + 2.0f * ua * umf + 2.0f * umf * umf;
+    eb = g.eps_df * (1.001 * (double)M + fabs(gt));
+    return true;
 }
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -839,7 +923,8 @@ struct Stage2 {
 // list order (any other candidate's exact cost exceeds the stage minimum's).
 __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
     G2 g, const double* __restrict__ phi2, const double* __restrict__ U,
-    const double* __restrict__ tab, const double* __restrict__ consts,
+    const double* __restrict__ tab, const float2* __restrict__ tabf,
+    const double* __restrict__ consts,
     const int64_t* __restrict__ nu_pre, int64_t* __restrict__ nu_out,
     int32_t* __restrict__ idx_out) {
     __shared__ double chs[kSearch2T / 32][kExactCh];
@@ -848,7 +933,14 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (i >= g.n_x * g.n_x) return;   // the same for the warp
     const double um = consts[0], W = consts[1];
+    const dfloat Wd = df_from_double(W);
     const Pt2 pt = make_pt2(g, i);
+    // The double-float table cost where it applies, else the FP64 one (both
+    // certified, so the two may mix).
+    auto cost = [&](int64_t n1, int64_t n2, double& gt, double& eb) {
+        if (!(g.use_df && tab_cost_df(g, tabf, um, Wd, pt, n1, n2, gt, eb)))
+            tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
+    };
     const int64_t side = 2 * (int64_t)g.n_nbr + 1;
     const int n0 = (int)(side * side + (int64_t)g.n_coarse * g.n_coarse);
     double thr = DBL_MAX;
@@ -856,7 +948,7 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
         int64_t n1, n2;
         double gt, eb;
         stage0_cand_pt(g, nu_pre, pt, p, n1, n2);
-        tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
+        cost(n1, n2, gt, eb);
         thr = fmin(thr, gt + eb);
     }
     thr = warp_min(thr);
@@ -868,7 +960,7 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
         bool cont = false;
         if (p < n0) {
             stage0_cand_pt(g, nu_pre, pt, p, n1, n2);
-            tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
+            cost(n1, n2, gt, eb);
             cont = gt - eb <= thr;
         }
         unsigned mask = __ballot_sync(kFull, cont);
@@ -889,7 +981,7 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
             const int k9 = lane < 4 ? lane : lane + 1;       // 3 x 3 window, centre skipped
             n1 = st.b1 + (int64_t)(k9 / 3 - 1) * h;
             n2 = st.b2 + (int64_t)(k9 % 3 - 1) * h;
-            tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
+            cost(n1, n2, gt, eb);
         }
         const double t = fmin(warp_min(lane < 8 ? gt + eb : DBL_MAX), st.bgt + st.beb);
         Stage2 nx;
@@ -998,6 +1090,19 @@ const char* make_g2(const ucp2_params& p, G2* g) {
     // by a forward error analysis (M the magnitude bound of the terms); taken
     // with a margin of two.
     g->eps_k = (double)(4 * g->n_w + 512) * 0x1p-53;
+    // Double-float assembly of a table cost: about 60 operations, each within
+    // 5 2^-48 of the magnitudes bounded by M, and the tables' own rounding to
+    // pairs (2^-48): below 2^-39.5 M; taken as 2^-37 on top of eps_k.
+    g->use_df = g->shift <= 24;
+    g->eps_df = g->eps_k + 0x1p-37;
+    {
+        const double us = ldexp(p.delta, -g->shift);
+        g->us_hi = (float)us;
+        g->us_lo = (float)(us - (double)g->us_hi);
+        g->inv_one_f = (float)ldexp(1.0, -g->shift);
+        g->kk_hi = (float)g->kk;
+        g->kk_lo = (float)(g->kk - (double)g->kk_hi);
+    }
     // Source splits of the factorised u1 sums: about four blocks per SM.
     {
         const int64_t tiles = (g->n_y + 31) / 32, want = (4 * 152 + tiles * tiles - 1) /
@@ -1028,7 +1133,7 @@ void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s) {
         return;
     }
     k2_search_scr<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(
-        g, d.phi2, d.U, d.tab, d.scratch + 2, d.nu[cur], d.nu[cur ^ 1], d.idx);
+        g, d.phi2, d.U, d.tab, d.tabf, d.scratch + 2, d.nu[cur], d.nu[cur ^ 1], d.idx);
 }
 
 void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
@@ -1057,7 +1162,7 @@ void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s) {
         // The tables of the new u1 table: J's terms now, the next search later.
         k2_tab_consts<<<1, 256, 0, s>>>(g, d.U, d.phin, d.scratch + 2);
         k2_tab_rows<<<nblk(g.ext_n * g.tab_n, 256), 256, 0, s>>>(g, d.U, d.phin, d.H);
-        k2_tab_cols<<<nblk(g.tab_n * g.tab_n, 256), 256, 0, s>>>(g, d.H, d.phin, d.tab);
+        k2_tab_cols<<<nblk(g.tab_n * g.tab_n, 256), 256, 0, s>>>(g, d.H, d.phin, d.tab, d.tabf);
         k2_J_terms_tab<<<nblk(n, 256), 256, 0, s>>>(g, d.tab, d.scratch + 2, d.px, d.nu[buf],
                                                     d.terms);
         k2_fixed_sum<<<1, 1024, 8 * sum_chunks(n), s>>>(d.terms, n, 0.5, out);

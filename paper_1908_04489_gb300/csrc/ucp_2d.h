@@ -26,6 +26,11 @@ struct G2 {
     int64_t tab_lo, tab_n, ext_n;
     double eps_k;
     int32_t u1_splits;   // source splits of the factorised u1 sums
+    // Double-float table costs (n_levels <= 24): their error bound eps_df
+    // (M + |g|), the lattice step delta 2^-shift as a float pair, 2^-shift.
+    int32_t use_df;
+    double eps_df;
+    float us_hi, us_lo, inv_one_f, kk_hi, kk_lo;
 };
 
 // Fills g from p; nullptr or the reason p is invalid.
@@ -45,6 +50,7 @@ struct Dev2 {
     double* phin;    // [n_w] normalised one-dimensional noise weights
     double* H;       // [7 ext_n tab_n] row pass of the correlation tables
     double* tab;     // [tab_n^2 x 8] correlation tables, 8 slots per cell
+    float2* tabf;    // the same as double-float pairs
     double* mins;    // [2 n_y + 1] exponent minima of the factorised u1 step
     double* fa;      // [n_y x n_x^2] prior x axis-1 factors, double-float pairs
     double* fb;      // [n_y x n_x^2] axis-2 factors, double-float pairs

@@ -310,14 +310,24 @@ def staircase_table(o, step):
     return np.stack([np.repeat(h, o.n_x), np.tile(h, o.n_x)], axis=1)
 
 
-@pytest.mark.parametrize("case", ["P2B", "P2W", "staircase"])
+@pytest.mark.parametrize("case", ["P2B", "P2W", "staircase", "levels26", "huge"])
 def test_screened_equals_direct(B, O, case):
     """The screened search makes the direct search's decisions bit for bit
-    (values and list positions) at every sweep."""
+    (values and list positions) at every sweep.  levels26: fractions of more
+    than 24 bits, so the FP64 table costs screen; huge: one incumbent beyond
+    2^44 lattice steps, whose table cost falls back to FP64 inside the
+    double-float screening."""
     p, sweeps, tab = {"P2B": (P2B, 4, None), "P2W": (P2W, 2, None),
-                      "staircase": (P2, 6, "stairs")}[case]
+                      "staircase": (P2, 6, "stairs"),
+                      "levels26": (dict(P2, n_levels=26), 3, None),
+                      "huge": (P2, 2, "huge")}[case]
     o = O.Oracle2D(p)
-    init = staircase_table(o, 5.0) if tab else None
+    init = None
+    if tab == "stairs":
+        init = staircase_table(o, 5.0)
+    elif tab == "huge":
+        init = o.value(o.init(0)).astype(float)
+        init[o.N // 3] = (1.0e13, -1.0e13)
     with B.Instance2D(dict(p, direct=0), init_f=init) as a, \
             B.Instance2D(dict(p, direct=1), init_f=init) as b:
         for s in range(sweeps):
