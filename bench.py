@@ -683,6 +683,96 @@ def measure_c5(args, binding, torch, stream, flush):
     return out
 
 
+P2D = dict(k=0.2, sigma=5.0, delta=0.3125, x_half=25.0, w_half=5.0, y_half=35.0,
+           cand_half=30.0, n_coarse=13, n_levels=8, n_nbr=2)
+P2D_SWEEPS = 40
+P2D_PAPER_J = 0.166719   # Section V-D, 160 x 160 samples (other grids and list)
+
+
+def measure_2d(args, binding, torch, stream, flush):
+    """The 2-dimensional counterexample of Section V-D (k = 0.2, sigma = 5):
+    161 x 161 x0 points over [-25, 25]^2 (delta = 0.3125), 33 x 33 noise
+    points, 225 x 225 y points, 13 x 13 coarse values and 8 levels; a solve is
+    the identity start and 40 sweeps.  Whole solves timed with CUDA events;
+    the last sweep checked against the oracle on sampled points (decisions
+    from the GPU's own pre-sweep state, u1 at sampled targets, J of the
+    state); the oracle's sweep rate estimated from the same samples."""
+    import oracle
+    p = dict(P2D)
+    with binding.Instance2D(p, stream=stream) as g:
+        g.sweep(2)
+    times = []
+    for _ in range(max(1, args.twod_steps)):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = binding.Instance2D(p, stream=stream)
+        g.sweep(P2D_SWEEPS - 1)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if _ + 1 < max(1, args.twod_steps):
+            g.close()
+    pre = g.get_controllers()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.sweep(1)
+    e1.record(stream)
+    e1.synchronize()
+    last_ms = e0.elapsed_time(e1)
+    post = g.get_controllers()
+    Jh = g.J_history()
+    g.close()
+    t = (float(np.median(times)) + last_ms) / 1e3
+    out = {"workload": "2-D Witsenhausen (Section V-D): k=0.2 sigma=5, 161x161 x0 over "
+                       "[-25,25]^2 (delta=0.3125), 33x33 w, 225x225 y, 13x13 coarse + "
+                       "8 levels, window radius 2, identity init, 40 sweeps",
+           "solves_per_s": 1.0 / t, "ms_per_solve": t * 1e3,
+           "ms_per_sweep": t * 1e3 / P2D_SWEEPS, "J": float(Jh[-1]),
+           "J_paper": P2D_PAPER_J,
+           "J_note": "plausibility band only: the paper's 160x160 samples, interpolation "
+                     "and candidate scheme differ"}
+    if args.no_cpu:
+        return out
+    import time as _t
+    o = oracle.Oracle2D(p)
+    d, sh = p["delta"], o.shift
+    lat = lambda f: np.rint(np.ldexp(f / d, sh)).astype(np.int64)
+    nu_pre, nu_post = lat(pre["f"]), lat(post["f"])
+    rng = np.random.default_rng(1908)
+    pts = rng.choice(o.N, 48, replace=False)
+    t0 = _t.perf_counter()
+    differ, gap = 0, 0.0
+    for i in pts:
+        a, b = o.search(nu_pre, pre["U"], int(i), int(i) + 1)
+        if not (np.array_equal(a[i], nu_post[i]) and b[i] == post["idx"][i]):
+            differ += 1
+            gap = max(gap, o.cost(pre["U"], int(i), *nu_post[i]) -
+                      o.cost(pre["U"], int(i), *a[i]))
+    t_search = (_t.perf_counter() - t0) / len(pts)
+    tg = rng.choice(o.n_y ** 2, 48, replace=False)
+    t0 = _t.perf_counter()
+    dU = 0.0
+    for tt in tg:
+        Uo = o.mmse(nu_post, int(tt), int(tt) + 1)
+        dU = max(dU, float(np.max(np.abs(post["U"][tt] - Uo[tt]))))
+    t_u1 = (_t.perf_counter() - t0) / len(tg)
+    t0 = _t.perf_counter()
+    Jo = o.J(nu_post, post["U"])
+    t_J = _t.perf_counter() - t0
+    out["parity"] = {"compared": "last sweep: 48 sampled x0 points' decisions from the "
+                                 "GPU's own pre-sweep state, u1 at 48 sampled targets, "
+                                 "J of the GPU's state (FP64 2-D oracle)",
+                     "decisions_differing": differ, "max_cost_gap_of_differing": gap,
+                     "max_abs_dU": dU, "dJ": float(Jh[-1] - Jo), "tol_U": 1e-11}
+    sweep_s = t_search * o.N + t_u1 * o.n_y ** 2 + t_J
+    out["cpu_oracle"] = {"solves_per_s": 1.0 / (sweep_s * P2D_SWEEPS), "cores": 1,
+                         "sample": "48 points' searches, 48 targets' u1, one J, "
+                                   "scaled to a 40-sweep solve",
+                         "s_per_sweep": sweep_s}
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -801,6 +891,9 @@ def run_gpu(args):
     large = None
     if rank == 0 and not args.no_c5 and args.workload != "c5":
         large = measure_c5(args, binding, torch, stream, flush)
+    twod = None
+    if rank == 0 and not args.no_2d:
+        twod = measure_2d(args, binding, torch, stream, flush)
     # the oracle's own solve last: no host load while the GPU legs run
     parity, cpu = None, None
     if rank == 0 and not args.no_cpu:
@@ -835,6 +928,8 @@ def run_gpu(args):
         line["serving"] = serving
     if large is not None:
         line["large"] = large
+    if twod is not None:
+        line["two_dim"] = twod
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -862,6 +957,14 @@ def run_profile(args):
             J = b.eval_J()
         print(json.dumps({"workload": "c3", "instances": len(ps), "J_mean": float(np.mean(J)),
                           "sweeps": args.profile_sweeps, "graph": bool(args.profile_graph)}))
+        torch.cuda.synchronize()
+        return
+    if args.workload == "2d":
+        # the 2-dimensional instance of Section V-D (the bench's 2-D leg)
+        with binding.Instance2D(P2D) as g:
+            g.sweep(args.profile_sweeps)
+            J = g.J_history()
+        print(json.dumps({"workload": "2d", "J": float(J[-1]), "sweeps": args.profile_sweeps}))
         torch.cuda.synchronize()
         return
     p, _ = workload(args.workload, args.precision)
@@ -935,6 +1038,8 @@ def main():
                     help="only the serving leg (with --serve-requests 20000: the c4 "
                          "workload at its own size), one JSON line")
     ap.add_argument("--c5-steps", type=int, default=2)
+    ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--twod-steps", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rates", type=float, nargs="+",
                     default=[100.0, 200.0, 500.0, 1000.0, 2000.0, 5000.0])

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(128) k2_mmse(G2 g, const int64_t* __restrict__
 // The exponent of source i at target y splits over the axes,
 //   E_i(y) = P_i + Q_i(y_1) + R_i(y_2),  P_i = |x_i|^2 / (2 sigma^2),
 //   Q_i(y_1) = (y_1 - f_i1)^2 / 2,  R_i(y_2) = (y_2 - f_i2)^2 / 2,
-// so exp(-(E_i - e)) with e = min P + min_i Q_i(y_1) + min_i R_i(y_2) is the
+// so exp(-(E_i - e)) with e = min_i (P_i + Q_i(y_1)) + min_i R_i(y_2) is the
 // product a_i(y_1) b_i(y_2) of per-axis factors (the prior folded into a).
 // The weights differ from exp(-(E_i - min_i E_i)) by one factor per target,
 // which cancels in the ratio; the three sums over sources are then
@@ -288,8 +288,7 @@ __global__ void __launch_bounds__(128) k2_mmse(G2 g, const int64_t* __restrict__
 // cancelled factor, at least) falls below 2^-60 is recomputed in the direct
 // form; elsewhere the lost terms are below 2^-50 of the denominator.
 
-// mins[j] = min_i Q_i(y_j), mins[n_y + j] = min_i R_i(y_j), mins[2 n_y] =
-// min_i P_i: one block each.
+// Per source: fv[2 i + q] = f_iq and fv[2 N + i] = P_i.
 __device__ __forceinline__ double half_sq(double y, double f) {
     const double d = y - f;
     return 0.5 * (d * d);
@@ -298,19 +297,28 @@ __device__ __forceinline__ double prior_expo(const G2& g, int64_t i) {
     const double xa = grid2(g, i / g.n_x, g.hx), xb = grid2(g, i % g.n_x, g.hx);
     return (xa * xa + xb * xb) / (2.0 * g.sigma * g.sigma);
 }
-__global__ void __launch_bounds__(256) k2_u1_mins(G2 g, const int64_t* __restrict__ nu,
+__global__ void __launch_bounds__(256) k2_u1_sources(G2 g, const int64_t* __restrict__ nu,
+                                                     double* __restrict__ fv) {
+    const int64_t n = g.n_x * g.n_x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    fv[2 * i] = val2(g, nu[2 * i]);
+    fv[2 * i + 1] = val2(g, nu[2 * i + 1]);
+    fv[2 * n + i] = prior_expo(g, i);
+}
+
+// The axis shifts: mins[j] = min_i (P_i + Q_i(y_j)) (the prior folded into
+// axis 1, which keeps the joint minimum closer to the sum of the shifts) and
+// mins[n_y + j] = min_i R_i(y_j); one block each.
+__global__ void __launch_bounds__(256) k2_u1_mins(G2 g, const double* __restrict__ fv,
                                                   double* __restrict__ mins) {
     __shared__ double red[256];
     const int64_t b = blockIdx.x, n = g.n_x * g.n_x;
+    const int q = b < g.n_y ? 0 : 1;
+    const double y = grid2(g, b - q * g.n_y, g.hy);
     double m = INFINITY;
-    if (b < 2 * g.n_y) {
-        const int q = b < g.n_y ? 0 : 1;
-        const double y = grid2(g, b - q * g.n_y, g.hy);
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-            m = fmin(m, half_sq(y, val2(g, nu[2 * i + q])));
-    } else {
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, prior_expo(g, i));
-    }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        m = fmin(m, (q == 0 ? fv[2 * n + i] : 0.0) + half_sq(y, fv[2 * i + q]));
     red[threadIdx.x] = m;
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
@@ -320,22 +328,10 @@ __global__ void __launch_bounds__(256) k2_u1_mins(G2 g, const int64_t* __restric
     if (threadIdx.x == 0) mins[b] = red[0];
 }
 
-// Per source: fv[2 i + q] = f_iq and fv[2 N + i] = exp(-(P_i - min P)).
-__global__ void __launch_bounds__(256) k2_u1_sources(G2 g, const int64_t* __restrict__ nu,
-                                                     const double* __restrict__ mins,
-                                                     double* __restrict__ fv) {
-    const int64_t n = g.n_x * g.n_x;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    fv[2 * i] = val2(g, nu[2 * i]);
-    fv[2 * i + 1] = val2(g, nu[2 * i + 1]);
-    fv[2 * n + i] = exp(-(prior_expo(g, i) - mins[2 * g.n_y]));
-}
-
 // Factor tables, target-major (entry j N + i, N = n_x^2 sources):
-//   fa = exp(-(P_i - min P)) exp(-(Q_i(y_j) - min Q)),  fb = exp(-(R_i(y_j) - min R)),
-// formed in FP64 and kept both as double-float pairs (hi, lo) for the sums
-// and in FP64 for the targets whose factor leaves FP32's range.
+//   fa = exp(-(P_i + Q_i(y_j) - mins[j])),  fb = exp(-(R_i(y_j) - mins[n_y + j])),
+// both at most 1, formed in FP64 and kept as double-float pairs (hi, lo) for
+// the sums and in FP64 for the targets whose factor leaves FP32's range.
 __global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const double* __restrict__ mins,
                                                      const double* __restrict__ fv,
                                                      float2* __restrict__ fa,
@@ -347,7 +343,7 @@ __global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const double* __restr
     if (id >= n * g.n_y) return;
     const int64_t j = id / n, i = id % n;
     const double y = grid2(g, j, g.hy);
-    const double va = fv[2 * n + i] * exp(-(half_sq(y, fv[2 * i]) - mins[j]));
+    const double va = exp(-((fv[2 * n + i] + half_sq(y, fv[2 * i])) - mins[j]));
     const double vb = exp(-(half_sq(y, fv[2 * i + 1]) - mins[g.n_y + j]));
     const dfloat a = df_from_double(va), b = df_from_double(vb);
     fa[id] = make_float2(a.hi, a.lo);
@@ -1145,8 +1141,8 @@ void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
     const int64_t len = (n + g.u1_splits - 1) / g.u1_splits;
     float2* fa = reinterpret_cast<float2*>(d.fa);
     float2* fb = reinterpret_cast<float2*>(d.fb);
-    k2_u1_mins<<<(unsigned)(2 * g.n_y + 1), 256, 0, s>>>(g, d.nu[buf], d.mins);
-    k2_u1_sources<<<nblk(n, 256), 256, 0, s>>>(g, d.nu[buf], d.mins, d.fv);
+    k2_u1_sources<<<nblk(n, 256), 256, 0, s>>>(g, d.nu[buf], d.fv);
+    k2_u1_mins<<<(unsigned)(2 * g.n_y), 256, 0, s>>>(g, d.fv, d.mins);
     k2_u1_factors<<<nblk(n * g.n_y, 256), 256, 0, s>>>(g, d.mins, d.fv, fa, fb, d.fa64, d.fb64);
     k2_u1_sums<<<dim3((unsigned)tiles, (unsigned)tiles, (unsigned)g.u1_splits), 256, 0, s>>>(
         g, fa, fb, d.fv, len, d.part);
