@@ -412,10 +412,13 @@ UCP_API ucp_status ucp_probe_alu(double* fp64_tflops, double* fp32_tflops,
  *           asynchronous on it.
  * It allocates nothing: its intermediate buffers live in one fixed device
  * array of 5.9 MiB that every GPU loading the library holds until exit.
- * Limits: n_x <= 32768 and n_y <= 32768, else UCP_E_ARG.  The first call on
- * a device looks up that array's address with the device current; make it
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU race, so serialise them.  UCP_E_CUDA on a launch failure. */
+ * Limits: n_x <= 32768 and n_y <= 32768, else UCP_E_ARG.  Each call outside
+ * stream capture looks up that array's address with the device current (so
+ * the call stays valid after cudaDeviceReset); a call while `stream` is
+ * capturing uses the address of the last uncaptured call on the device, and
+ * UCP_E_STATE if there was none -- make one call before capturing.  All
+ * calls share the array: calls that overlap on the GPU race, so serialise
+ * them.  UCP_E_CUDA on a launch failure. */
 UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
                                          const double* f_dev, double* u1_dev,
                                          void* stream);

@@ -621,25 +621,28 @@ __global__ void k2_table(G2 g, const double* __restrict__ table, int64_t* __rest
 // taps read the clamped edge there), so corner indices are clamped to that
 // range.  Slots of a cell: A_1, A_2, C_00, C_01, C_10, C_11, C_1m, unused.
 
-// Umax = max |U| and W = (sum_c phi_c)^2 (one block).
+// Umax = max |U| (every block's maximum folded in by an atomic maximum on
+// the bit patterns, which order like the non-negative doubles; out[0] is
+// zeroed before) and W = (sum_c phi_c)^2 (block 0).
 __global__ void __launch_bounds__(256) k2_tab_consts(G2 g, const double* __restrict__ U,
                                                      const double* __restrict__ phin,
                                                      double* __restrict__ out) {
     __shared__ double red[256];
-    double m = 0.0;
-    for (int64_t k = threadIdx.x; k < 2 * g.n_y * g.n_y; k += blockDim.x)
-        m = fmax(m, fabs(U[k]));
-    red[threadIdx.x] = m;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    red[threadIdx.x] = k < 2 * g.n_y * g.n_y ? fabs(U[k]) : 0.0;
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
         if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double w = 0.0;
-        for (int64_t c = 0; c < g.n_w; ++c) w += phin[c];
-        out[0] = red[0];
-        out[1] = w * w;
+        atomicMax(reinterpret_cast<unsigned long long*>(out),
+                  (unsigned long long)__double_as_longlong(red[0]));
+        if (blockIdx.x == 0) {
+            double w = 0.0;
+            for (int64_t c = 0; c < g.n_w; ++c) w += phin[c];
+            out[1] = w * w;
+        }
     }
 }
 
@@ -1156,7 +1159,8 @@ void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s) {
     const int64_t n = g.n_x * g.n_x;
     if (!(g.direct & 1)) {
         // The tables of the new u1 table: J's terms now, the next search later.
-        k2_tab_consts<<<1, 256, 0, s>>>(g, d.U, d.phin, d.scratch + 2);
+        cudaMemsetAsync(d.scratch + 2, 0, sizeof(double), s);
+        k2_tab_consts<<<nblk(2 * g.n_y * g.n_y, 256), 256, 0, s>>>(g, d.U, d.phin, d.scratch + 2);
         k2_tab_rows<<<nblk(g.ext_n * g.tab_n, 256), 256, 0, s>>>(g, d.U, d.phin, d.H);
         k2_tab_cols<<<nblk(g.tab_n * g.tab_n, 256), 256, 0, s>>>(g, d.H, d.phin, d.tab, d.tabf);
         k2_J_terms_tab<<<nblk(n, 256), 256, 0, s>>>(g, d.tab, d.scratch + 2, d.px, d.nu[buf],

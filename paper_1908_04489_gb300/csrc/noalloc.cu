@@ -84,16 +84,30 @@ __global__ void k_na_prepare(Geom g, const double* __restrict__ f,
     if (k < kConstTab) t64[k] = const_table_entry((int)k);
 }
 
-// Device address of g_scratch on the current device (looked up once).
-static ucp_status scratch_address(double** out) {
+// Device address of g_scratch on the current device.  Outside stream
+// capture it is looked up on every call (a context torn down by
+// cudaDeviceReset reloads the module at another address); while `stream` is
+// capturing, the address of the last uncaptured call on this device is used
+// (a symbol lookup may load the module, which capture forbids).
+static ucp_status scratch_address(cudaStream_t stream, double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         set_error("ucp_u1_update_noalloc: %s%s", "no current CUDA device", "");
         return UCP_E_CUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone && !g_addr[dev]) {
+        set_error("ucp_u1_update_noalloc: %s%s",
+                  "first call on this device made during stream capture", "");
+        return UCP_E_STATE;
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
@@ -134,7 +148,7 @@ extern "C" UCP_API ucp_status ucp_u1_update_noalloc(const ucp_params* params,
         return UCP_E_ARG;
     }
     double* base = nullptr;
-    ucp_status st = scratch_address(&base);
+    ucp_status st = scratch_address((cudaStream_t)stream, &base);
     if (st != UCP_OK) return st;
 
     // plan of the u1 kernels over at most kMaxTiles source tiles
