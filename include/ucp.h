@@ -387,6 +387,15 @@ UCP_API ucp_status ucp_srv_fail_next_step(ucp_srv* s);
  * still pending (they are discarded), else UCP_OK. */
 UCP_API ucp_status ucp_srv_destroy(ucp_srv* s);
 
+/* Test hook of the bounded waits (no paper counterpart): with on = 1 the
+ * tensor-core table kernel of this fast-path instance no longer issues its
+ * filter-slice copy, so the one wait that copy would complete runs out (after
+ * a short bound; nothing is in flight behind it).  The kernel then waits for
+ * its other copies, writes zero partials, frees its tensor memory and sets
+ * the error flag; the next synchronising call returns UCP_E_TIMEOUT and the
+ * instance is poisoned.  UCP_E_STATE on the plain path. */
+UCP_API ucp_status ucp_test_tc_skip_copy(ucp_inst* inst, int32_t on);
+
 /* Measured ALU throughput of the current device (no paper counterpart: the
  * denominators of the roofline fractions of the ALU-bound kernels): FP64
  * FMA and FP32 FMA in TFLOP/s (2 flops per FMA) and FP32 ex2 (SFU) in

@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(256) kb_setup_elem(const SetupDev* descs,
         *d.f.n_tier2 = 0;
         *d.f.defer_cnt = 0;
         *d.f.J_done = 0;
-        *d.f.tc_err = 0;
+        d.f.tc_err[0] = 0;
+        d.f.tc_err[1] = 0;
     }
     if (k < 4) d.f.n_pairs[k] = 0;
 }

@@ -422,7 +422,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
         cudaMemsetAsync(in->fv.n_tier2, 0, 4, s);
         cudaMemsetAsync(in->fv.defer_cnt, 0, 4, s);
         cudaMemsetAsync(in->fv.J_done, 0, 4, s);
-        cudaMemsetAsync(in->fv.tc_err, 0, 4, s);
+        cudaMemsetAsync(in->fv.tc_err, 0, 8, s);   // the error flag and the test hook
         cudaMemsetAsync(in->fv.n_pairs, 0, 32, s);
         if (p.init_kind == 2) {
             double fm = 0.0;

@@ -126,7 +126,8 @@ struct FastView : FastPlan {
     int32_t* tc_xe;      // [3][tc_nblk] signal block scales (exponents)
     float2* tc_part;     // [3][tc_nch][64 tc_ng][128] chunk partials (double-float)
     float* tc_bt;        // [tc_na + 1] per-column bound on the table error of S
-    int32_t* tc_err;     // set when a wait of the tensor-core kernel timed out
+    int32_t* tc_err;     // [0] set when a wait of the tensor-core kernel timed out;
+                         // [1] test hook: the table kernel skips its filter copy
     CUtensorMap tc_map[3];  // TMA maps of tc_x per signal: rows of 128 bf16, 64 x 64 boxes
     int32_t* J_done;     // J blocks finished (reset by the last)
     double* W2_dev;      // sum phi_l w_l^2 (device copy)
