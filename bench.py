@@ -521,12 +521,45 @@ def measure_batched(args, binding, torch, stream, flush, world=1, rank=0):
     }
 
 
+def time_solves(binding, torch, stream, flush, p, steps):
+    """Median seconds of whole solves (set-up + p["sweeps"] sweeps) timed
+    with CUDA events on `stream`, after two untimed solves; the last solve's
+    J and controllers."""
+    for _ in range(2):
+        with binding.Instance(p, stream=stream) as inst:
+            inst.sweep(p["sweeps"])
+            inst.eval_J()
+    times = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst = binding.Instance(p, stream=stream)
+        inst.sweep(p["sweeps"])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        J = inst.eval_J()
+        st = inst.get_controllers()
+        Jh = inst.J_history()
+        inst.close()
+    return float(np.median(times)) / 1e3, J, st, Jh
+
+
 def measure_source_channel(args, binding, torch, stream, flush):
     """Section V-B's second problem on the same sweep (zero-delay
-    source-channel coding, lambda = 2, w ~ U(-1, 1)), plain FP64 path: whole
-    solves (set-up + 20 sweeps) timed with CUDA events, J checked against the
-    oracle recomputing it from the GPU's final state."""
+    source-channel coding, lambda = 2, w ~ U(-1, 1)): whole solves (set-up +
+    20 sweeps) timed with CUDA events on the plain FP64 path and in the fast
+    mode (precision 1: screened search on three tables, warp u1 step), J
+    checked against the oracle recomputing it from the GPU's final state and
+    against the oracle's own solve."""
     from paper_1908_04489_gb300 import workloads as W
+    pf = W.source_channel(precision=1)
+    tf, Jf, _, Jhf = time_solves(binding, torch, stream, flush, pf, max(3, args.batch_steps))
+    with binding.Instance(pf, stream=stream) as inst:
+        inst.profile(True)
+        inst.sweep(pf["sweeps"])
+        kern_f = {k: v[1] for k, v in inst.kernel_times().items()}
     p = W.source_channel()
     for _ in range(2):
         with binding.Instance(p, stream=stream) as inst:
@@ -555,7 +588,9 @@ def measure_source_channel(args, binding, torch, stream, flush):
                        "x0 ~ N(0,1), w ~ U(-1,1), delta = 0.02 (501 x0 / 101 w / 701 y), "
                        "identity start, 20 sweeps, plain FP64 path",
            "solves_per_s": 1.0 / t, "ms_per_solve": t * 1e3, "J": J,
-           "J_paper": 0.890756, "kernels_ms_per_solve": kern}
+           "J_paper": 0.890756, "kernels_ms_per_solve": kern,
+           "fast_mode": {"solves_per_s": 1.0 / tf, "ms_per_solve": tf * 1e3, "J": Jf,
+                         "vs_plain": t / tf, "kernels_ms_per_solve": kern_f}}
     # FP64 work of the plain search: 6 flops per quadrature term, every
     # candidate of every x0 point each sweep (the u1 and J passes are small)
     sz = binding.plan(p)
@@ -577,6 +612,8 @@ def measure_source_channel(args, binding, torch, stream, flush):
         out["cpu_oracle"] = {"solves_per_s": 1.0 / tc, "cores": cores,
                              "sample": "one whole solve (20 sweeps) from the identity"}
         out["abs_dJ_vs_oracle_trajectory"] = abs(J - float(ref["J"][-1]))
+        out["fast_mode"]["max_abs_dJ_vs_oracle_trajectory"] = float(
+            np.max(np.abs(np.asarray(Jhf) - np.asarray(ref["J"]))))
     return out
 
 

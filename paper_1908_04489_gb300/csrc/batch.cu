@@ -258,9 +258,9 @@ extern "C" UCP_API ucp_status ucp_batch_create(ucp_ctx* ctx, const ucp_params* p
             set_error("ucp_batch_create: %s%s", why, "");
             return UCP_E_ARG;
         }
-        if (params[k].precision != 1) {
+        if (params[k].precision != 1 || params[k].problem != 0) {
             set_error("ucp_batch_create: %s%s", "batched instances use the fast path "
-                      "(precision 1)", "");
+                      "(precision 1) of Witsenhausen's problem (problem 0)", "");
             return UCP_E_ARG;
         }
     }

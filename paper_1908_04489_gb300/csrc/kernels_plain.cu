@@ -740,6 +740,256 @@ __global__ void __launch_bounds__(kLocalT) k_local_update(Geom g, const double* 
     nu_out[i] = fabs(v) < 9.0e15 ? (int64_t)llround(v) : nu;
 }
 
+// ---- problem 1, fast mode: screened search and warp-parallel u1 step ------
+//
+// With equal noise weights phi_l the estimation error of candidate u at x is
+//   Q(u; x) = sum_l phi_l (U^(u + w_l) - x)^2 = B - 2 x A + x^2 W,
+// A = sum_l phi_l U^_l, B = sum_l phi_l U^_l^2, W = sum_l phi_l, and with the
+// cell jb + t of u + w_0 (U^_l = (1 - t) Ub(jb + l) + t Ub(jb + l + 1), Ub the
+// table clamped at its ends)
+//   A = (1 - t) A0(jb) + t A0(jb + 1),
+//   B = (1 - t)^2 B0(jb) + 2 t (1 - t) B1(jb) + t^2 B0(jb + 1),
+// from three tables over first-tap cells: A0(j) = sum phi_l Ub(j + l),
+// B0(j) = sum phi_l Ub(j + l)^2, B1(j) = sum phi_l Ub(j + l) Ub(j + l + 1).
+// Every table is constant below j = -n_w - 1 and above j = n_y (its taps
+// then all read a clamped end), so corner cells are clamped to that range.
+// The table cost carries the bound eps (M + |g~|), eps = (4 n_w + 512)
+// 2^-53, M = (max |U| + |x|)^2 (a forward error analysis gives below
+// (2 n_w + 170) 2^-53 M for the tables' sums and the assembly against the
+// fixed-order Q_plain); candidates the bound cannot separate are re-costed
+// by quad_split on the whole warp, which is Q_plain bit for bit.
+
+__device__ __forceinline__ int64_t sc_lo(const Geom& g) { return -g.n_w - 1; }
+__device__ __forceinline__ int64_t sc_len(const Geom& g) { return g.n_y + g.n_w + 2; }
+
+// consts[0] = max |U|, consts[1] = W (one block).
+__global__ void __launch_bounds__(256) k_sc_consts(Geom g, const double* __restrict__ U,
+                                                   const double* __restrict__ phi,
+                                                   double* __restrict__ consts) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int64_t j = threadIdx.x; j < g.n_y; j += blockDim.x) m = fmax(m, fabs(U[j]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double w = 0.0;
+        for (int64_t l = 0; l < g.n_w; ++l) w += phi[l];
+        consts[0] = red[0];
+        consts[1] = w;
+    }
+}
+
+// tab[3 a + {0, 1, 2}] = A0, B0, B1 at cell j = sc_lo + a.
+__global__ void __launch_bounds__(256) k_sc_tables(Geom g, const double* __restrict__ U,
+                                                   const double* __restrict__ phi,
+                                                   double* __restrict__ tab) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= sc_len(g)) return;
+    const int64_t j = sc_lo(g) + a, ny1 = g.n_y - 1;
+    double A = 0.0, B0 = 0.0, B1 = 0.0;
+    for (int64_t l = 0; l < g.n_w; ++l) {
+        const int64_t j0 = j + l, j1 = j0 + 1;
+        const double u0 = U[j0 < 0 ? 0 : (j0 > ny1 ? ny1 : j0)];
+        const double u1 = U[j1 < 0 ? 0 : (j1 > ny1 ? ny1 : j1)];
+        const double w = phi[l];
+        A += w * u0;
+        B0 += w * (u0 * u0);
+        B1 += w * (u0 * u1);
+    }
+    tab[3 * a] = A;
+    tab[3 * a + 1] = B0;
+    tab[3 * a + 2] = B1;
+}
+
+// Table cost of candidate nu at x0 point i (value x) and its bound.
+__device__ __forceinline__ void sc_tab_cost(const Geom& g, const double* __restrict__ tab,
+                                            double um, double W, double x, int64_t nu,
+                                            double& gt, double& eb) {
+    const int64_t cell = nu >> g.shift;
+    const double t = __dmul_rn((double)(nu - (cell << g.shift)), inv_one(g));
+    const int64_t jb = cell - g.hw + g.hy, lo = sc_lo(g), hi = lo + sc_len(g) - 1;
+    const int64_t a0 = (jb < lo ? lo : (jb > hi ? hi : jb)) - lo;
+    const int64_t a1 = (jb + 1 < lo ? lo : (jb + 1 > hi ? hi : jb + 1)) - lo;
+    const double s = 1.0 - t;
+    const double A = s * tab[3 * a0] + t * tab[3 * a1];
+    const double B = s * s * tab[3 * a0 + 1] + 2.0 * t * s * tab[3 * a0 + 2] +
+                     t * t * tab[3 * a1 + 1];
+    const double u = value_of(g, nu);
+    gt = __dmul_rn(g.kk, __dmul_rn(u, u)) + (B - 2.0 * x * A + x * x * W);
+    const double m = um + fabs(x);
+    eb = (double)(4 * g.n_w + 512) * 0x1p-53 * (m * m + fabs(gt));
+}
+
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// The exact cost of candidate nu at x0 point i on the whole warp (the
+// plain search's cost, bit for bit); out of line: contenders are rare.
+__device__ __noinline__ double sc_exact(const Geom& g, const double* __restrict__ phi,
+                                        const double* __restrict__ U,
+                                        const double* __restrict__ Ud, int64_t nu, int64_t i,
+                                        int lane) {
+    return cost_from_S(g, i, nu, quad_split<32>(g, phi, U, Ud, nu, i, lane, 0));
+}
+
+// One stage's contenders in list order (warp-uniform): a value offered again
+// is skipped (same exact cost, later position); exact costs are formed only
+// once a second distinct value appears; the first least exact cost wins.
+struct ScStage {
+    bool has = false, known = false;
+    int64_t b = 0;
+    int32_t bp = 0;
+    double bgt = 0.0, beb = 0.0, bex = 0.0;
+    int nseen = 0;
+    int64_t seen = 0;   // lane k: the k-th distinct value
+
+    __device__ void offer(const Geom& g, const double* __restrict__ phi,
+                          const double* __restrict__ U, const double* __restrict__ Ud,
+                          int64_t i, int lane, int64_t v, int32_t pos, double vgt, double veb,
+                          bool vknown, double vex) {
+        if (__any_sync(0xffffffffu, lane < nseen && seen == v)) return;
+        if (nseen < 32) {
+            if (lane == nseen) seen = v;
+            ++nseen;
+        }
+        if (!has) {
+            has = true; b = v; bp = pos; bgt = vgt; beb = veb; known = vknown; bex = vex;
+            return;
+        }
+        if (!known) {
+            bex = sc_exact(g, phi, U, Ud, b, i, lane);
+            known = true;
+        }
+        const double ex = vknown ? vex : sc_exact(g, phi, U, Ud, v, i, lane);
+        if (ex < bex) {
+            b = v; bp = pos; bgt = vgt; beb = veb; bex = ex;
+        }
+    }
+};
+
+// One warp per x0 point: the list of k_search_plain (incumbent, 2 n_nbr
+// neighbours, coarse values, then n_levels levels of n_refine around the
+// best so far) with table costs; per stage the threshold min (g~ + eb) and
+// the contenders g~ - eb <= threshold in list order.
+__global__ void __launch_bounds__(128) k_search_sc(
+    Geom g, const double* __restrict__ phi, const double* __restrict__ U,
+    const double* __restrict__ Ud, const double* __restrict__ tab,
+    const double* __restrict__ consts, const int64_t* __restrict__ nu_pre,
+    const int64_t* __restrict__ coarse, int64_t* __restrict__ nu_out,
+    int32_t* __restrict__ idx_out, int64_t i_lo, int64_t i_hi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = i_lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= i_hi) return;   // the same for the warp
+    const double um = consts[0], W = consts[1], x = x_of(g, i);
+    const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
+    auto stage0 = [&](int p) -> int64_t {
+        if (p == 0) return nu_pre[i];
+        if (p <= 2 * g.n_nbr) {
+            const int d = p <= g.n_nbr ? p - g.n_nbr - 1 : p - g.n_nbr;
+            int64_t ii = i + d;
+            if (ii < 0 || ii >= g.n_x) ii = i;
+            return nu_pre[ii];
+        }
+        return coarse[p - 1 - 2 * g.n_nbr];
+    };
+    double thr = DBL_MAX;
+    for (int p = lane; p < n0; p += 32) {
+        double gt, eb;
+        sc_tab_cost(g, tab, um, W, x, stage0(p), gt, eb);
+        thr = fmin(thr, gt + eb);
+    }
+    thr = warp_min_d(thr);
+    ScStage st;
+    for (int base = 0; base < n0; base += 32) {
+        const int p = base + lane;
+        int64_t v = 0;
+        double gt = 0.0, eb = 0.0;
+        bool cont = false;
+        if (p < n0) {
+            v = stage0(p);
+            sc_tab_cost(g, tab, um, W, x, v, gt, eb);
+            cont = gt - eb <= thr;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, cont);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            st.offer(g, phi, U, Ud, i, lane, __shfl_sync(0xffffffffu, v, src), base + src,
+                     __shfl_sync(0xffffffffu, gt, src), __shfl_sync(0xffffffffu, eb, src),
+                     false, 0.0);
+        }
+    }
+    const int G = g.n_refine, half = G / 2;
+    int pos = n0;
+    for (int lv = 1; lv <= g.n_levels; ++lv) {
+        const int64_t h = g.q << (g.bits * (g.n_levels - lv));
+        int64_t v = 0;
+        double gt = 0.0, eb = 0.0;
+        const bool mine = lane < G;
+        if (mine) {
+            const int64_t m = lane < half ? lane - half : lane - half + 1;
+            v = st.b + m * h;
+            sc_tab_cost(g, tab, um, W, x, v, gt, eb);
+        }
+        const double t = fmin(warp_min_d(mine ? gt + eb : DBL_MAX), st.bgt + st.beb);
+        ScStage nx;
+        if (st.bgt - st.beb <= t)
+            nx.offer(g, phi, U, Ud, i, lane, st.b, st.bp, st.bgt, st.beb, st.known, st.bex);
+        unsigned mask = __ballot_sync(0xffffffffu, mine && gt - eb <= t);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            nx.offer(g, phi, U, Ud, i, lane, __shfl_sync(0xffffffffu, v, src), pos + src,
+                     __shfl_sync(0xffffffffu, gt, src), __shfl_sync(0xffffffffu, eb, src),
+                     false, 0.0);
+        }
+        st = nx;
+        pos += G;
+    }
+    if (lane == 0) {
+        nu_out[i] = st.b;
+        idx_out[i] = st.bp;
+    }
+}
+
+// The u1 step of problem 1 with one warp per target: the nearest distance
+// (a minimum, exact in any order), then the prior-weighted sums of x_i over
+// the sources within reach (lane-strided partial sums, then a fixed
+// butterfly), with the normalised prior weights px.
+__global__ void __launch_bounds__(128) k_mmse_uniform_w(Geom g, const int64_t* __restrict__ nu,
+                                                        const double* __restrict__ px,
+                                                        double* __restrict__ U) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (j >= g.n_y) return;   // the same for the warp
+    const double yj = __dmul_rn((double)(j - g.hy), g.delta);
+    double dmin = DBL_MAX;
+    for (int64_t i = lane; i < g.n_x; i += 32)
+        dmin = fmin(dmin, fabs(__dsub_rn(yj, value_of(g, nu[i]))));
+    dmin = warp_min_d(dmin);
+    const double reach = dmin <= g.w_noise ? g.w_noise : dmin;
+    double num = 0.0, den = 0.0;
+    for (int64_t i = lane; i < g.n_x; i += 32) {
+        if (fabs(__dsub_rn(yj, value_of(g, nu[i]))) <= reach) {
+            num += px[i] * x_of(g, i);
+            den += px[i];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, off);
+        den += __shfl_xor_sync(0xffffffffu, den, off);
+    }
+    if (lane == 0) U[j] = num / den;
+}
+
 }  // namespace
 
 // SMs of the current device (cached per device).
@@ -806,7 +1056,9 @@ void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s) {
 }
 
 void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s) {
-    if (g.problem == 1)
+    if (g.sc_fast)
+        k_mmse_uniform_w<<<blocks(32 * g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.px, d.U);
+    else if (g.problem == 1)
         k_mmse_uniform<<<blocks(g.n_y, spread_bs(g.n_y, 128)), spread_bs(g.n_y, 128), 0, s>>>(
             g, d.nu[buf], d.U);
     else
@@ -851,6 +1103,15 @@ void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s,
     if (i_hi < 0) i_hi = g.n_x;
     const int64_t n = i_hi - i_lo;
     if (n <= 0) return;
+    if (g.sc_fast) {   // problem 1, fast mode: tables of the current U, screened search
+        const int64_t len = g.n_y + g.n_w + 2;
+        k_sc_consts<<<1, 256, 0, s>>>(g, d.U, d.phi, d.sc_consts);
+        k_sc_tables<<<blocks(len, 256), 256, 0, s>>>(g, d.U, d.phi, d.sc_tab);
+        k_search_sc<<<blocks(32 * n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, d.sc_tab,
+                                                        d.sc_consts, d.nu[buf_in], d.coarse,
+                                                        d.nu[buf_in ^ 1], d.idx, i_lo, i_hi);
+        return;
+    }
     // one warp per x0 point (split quadratures) when that still leaves at
     // most 16 warps per SM, else n_refine lanes per point
     const bool split = n <= 16 * (int64_t)sm_count();

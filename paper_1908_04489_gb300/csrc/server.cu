@@ -312,8 +312,9 @@ extern "C" UCP_API ucp_status ucp_submit(ucp_srv* s, const ucp_params* params,
         set_error("ucp_submit: %s%s", why, "");
         return UCP_E_ARG;
     }
-    if (params->precision != 1) {
-        set_error("ucp_submit: %s%s", "served requests use the fast path (precision 1)", "");
+    if (params->precision != 1 || params->problem != 0) {
+        set_error("ucp_submit: %s%s", "served requests use the fast path (precision 1) of "
+                  "Witsenhausen's problem (problem 0)", "");
         return UCP_E_ARG;
     }
     auto r = std::make_shared<Request>();

@@ -50,8 +50,6 @@ const char* make_geom(const ucp_params& p, Geom* g) {
     if (p.flags != 0) return "flags must be 0";
     if (p.reserved != 0) return "reserved must be 0";
     if (p.problem != 0 && p.problem != 1) return "problem must be 0 or 1";
-    if (p.problem == 1 && p.precision != 0)
-        return "problem 1 (source-channel coding) runs on the plain FP64 path (precision 0)";
     if (p.precision != 0 && p.precision != 1) return "precision must be 0 or 1";
     if (p.delta * (p.x_half + p.y_half + p.cand_half) > 200.0)
         return "delta * (x_half + y_half + cand_half) must be <= 200";
@@ -85,6 +83,7 @@ const char* make_geom(const ucp_params& p, Geom* g) {
     g->n_nbr = p.n_nbr;
     g->n_cand = 1 + 2 * p.n_nbr + p.n_coarse + p.n_levels * p.n_refine;
     g->problem = p.problem;
+    g->sc_fast = p.problem == 1 && p.precision == 1;
     g->w_noise = p.w_half;
     // A tile of the u1 step holds at most 32 boxes of f-width 0.1: controllers
     // that vary steadily across x0 (the identity start, or a table start

@@ -27,6 +27,7 @@ struct Geom {
     int32_t u1_tile_min;        // fewest x0 points per tile of the u1 step
     int32_t problem;            // 0 Witsenhausen, 1 source-channel coding
     double w_noise;             // problem 1: noise half width (w_half)
+    int32_t sc_fast;            // problem 1 at precision 1: screened search, warp u1 step
 };
 
 // Fills g from params; returns nullptr or a static reason string.
@@ -52,6 +53,8 @@ struct DevState {
     double* J;        // [1 + max_hist] J history
     double* scratch;  // reduction partials
     double* table;    // [n_x] staging for table inits / set_controllers
+    double* sc_tab;   // problem 1 fast mode: [3 (n_y + n_w + 2)] tables A0, B0, B1
+    double* sc_consts;// problem 1 fast mode: max |U| and the weight sum
 };
 
 // Sizes of the fast path's buffers for one instance.

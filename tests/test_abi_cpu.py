@@ -86,16 +86,18 @@ def test_plan_rejects_invalid_fields(lib, field, value, msg):
     assert e.value.status == -1 and msg in str(e.value)
 
 
-def test_source_channel_problem_is_planned_on_the_plain_path(lib):
-    """Problem 1 (Section V-B) runs on the plain FP64 path: its plan has the
-    grids of its parameters, and the fast path is refused."""
+def test_source_channel_problem_is_planned_on_both_modes(lib):
+    """Problem 1 (Section V-B): its plan has the grids of its parameters on
+    the plain path and in its fast mode (precision 1: the three tables, no
+    tensor-core buffers)."""
     from paper_1908_04489_gb300 import binding, workloads
     p = workloads.source_channel()
     s = binding.plan(p)
     assert (s["n_x"], s["n_w"], s["n_y"], s["n_cand"]) == (501, 101, 701, 133)
-    with pytest.raises(binding.UcpError) as e:
-        binding.plan(dict(p, precision=1))
-    assert e.value.status == -1 and "plain FP64 path" in str(e.value)
+    f = binding.plan(dict(p, precision=1))
+    assert (f["n_x"], f["n_w"], f["n_y"], f["n_cand"]) == (501, 101, 701, 133)
+    extra = f["device_bytes"] - s["device_bytes"]
+    assert 0 < extra <= 8 * 3 * (701 + 101 + 2) + 2 * 256
 
 
 def test_create_validates_before_touching_the_device(lib):

@@ -29,7 +29,7 @@ def binding():
     return b
 
 
-def lockstep(binding, p, nu, U, sweeps):
+def lockstep(binding, p, nu, U, sweeps, tol_u=TOL_U):
     o = oracle.Oracle(p)
     with binding.Instance(p) as inst:
         for _ in range(sweeps):
@@ -41,14 +41,17 @@ def lockstep(binding, p, nu, U, sweeps):
             np.testing.assert_array_equal(got["idx"], idx)
             np.testing.assert_array_equal(got["f"], o.value(nu1))
             U1 = o.mmse(nu1)
-            assert np.max(np.abs(got["U"] - U1)) <= TOL_U
-            assert abs(Jg - o.J(nu1, U1)) <= TOL_J
+            assert np.max(np.abs(got["U"] - U1)) <= tol_u
+            assert abs(Jg - o.J(nu1, got["U"])) <= TOL_J
             nu, U = nu1, U1
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["plain", "fast"])
 @pytest.mark.parametrize("start", ["identity", "noisy", "flat"])
-def test_lockstep_source_channel(binding, start):
-    p = W.source_channel()
+def test_lockstep_source_channel(binding, start, precision):
+    """precision 1: the screened search on the three tables (decisions bit
+    for bit, the weights being equal and exp-free) and the warp u1 step."""
+    p = W.source_channel(precision=precision)
     o = oracle.Oracle(p)
     g = o.grids()
     if start == "identity":
@@ -64,8 +67,9 @@ def test_lockstep_source_channel(binding, start):
 @pytest.mark.parametrize("extra", [dict(n_nbr=0), dict(n_refine=4, n_levels=3),
                                    dict(y_half=2.0), dict(cand_half=9.0, y_half=9.0)],
                          ids=["no neighbours", "n_refine 4", "clamped y", "wide candidates"])
-def test_lockstep_source_channel_edges(binding, extra):
-    p = W.source_channel(**extra)
+@pytest.mark.parametrize("precision", [0, 1], ids=["plain", "fast"])
+def test_lockstep_source_channel_edges(binding, extra, precision):
+    p = W.source_channel(precision=precision, **extra)
     o = oracle.Oracle(p)
     g = o.grids()
     rng = np.random.default_rng(5)
@@ -91,3 +95,54 @@ def test_trajectory_source_channel(binding):
     assert np.max(np.abs(got["U"] - ref["U"])) <= 1e-6
     np.testing.assert_array_equal(u0, got["f"])        # f is u0 itself here
     assert abs(Jh[-1] - 0.890756) < 0.01
+
+
+def test_fast_mode_makes_the_plain_decisions(binding):
+    """From the same controllers and u1 table the fast mode's screened search
+    returns the plain search's values and list positions bit for bit, sweep
+    after sweep of a 20-sweep run (each sweep restarted from the plain
+    instance's state)."""
+    p0 = W.source_channel()
+    p1 = W.source_channel(precision=1)
+    with binding.Instance(p0) as a, binding.Instance(p1) as b:
+        for s in range(p0["sweeps"]):
+            st = a.get_controllers()
+            b.set_controllers(st["f"], st["U"])
+            a.sweep(1)
+            b.sweep(1)
+            ga, gb = a.get_controllers(), b.get_controllers()
+            np.testing.assert_array_equal(ga["idx"], gb["idx"])
+            np.testing.assert_array_equal(ga["f"], gb["f"])
+            assert np.max(np.abs(ga["U"] - gb["U"])) <= TOL_U
+
+
+def test_fast_mode_trajectory(binding):
+    """Independent 20-sweep solves, fast mode against the oracle's own: J
+    within 1e-9 per sweep up to and including the first sweep whose decisions
+    differ (u1 differs from the oracle's by roundings only); the final J near
+    Section V-B's value."""
+    p = W.source_channel(precision=1)
+    o = oracle.Oracle(p)
+    fs = []
+    with binding.Instance(p) as inst:
+        for _ in range(p["sweeps"]):
+            inst.sweep(1)
+            fs.append(inst.get_controllers(want=("f",))["f"])
+        Jh = inst.J_history()
+    nu = o.init(0)
+    U = o.mmse(nu)
+    assert abs(Jh[0] - o.J(nu, U)) <= 1e-9
+    for s in range(p["sweeps"]):
+        nu, _ = o.search(nu, U)
+        U = o.mmse(nu)
+        assert abs(Jh[s + 1] - o.J(nu, U)) <= 1e-9, s
+        if not np.array_equal(fs[s], o.value(nu)):
+            break
+    assert abs(Jh[-1] - 0.890756) < 0.01
+
+
+def test_batches_and_the_server_refuse_problem_1(binding):
+    p = W.source_channel(precision=1)
+    with pytest.raises(binding.UcpError) as e:
+        binding.Batch([p, p])
+    assert "problem 0" in str(e.value)
