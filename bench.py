@@ -1004,6 +1004,17 @@ def run_profile(args):
         print(json.dumps({"workload": "2d", "J": float(J[-1]), "sweeps": args.profile_sweeps}))
         torch.cuda.synchronize()
         return
+    if args.workload == "sc":
+        # Section V-B's problem (source-channel coding), --precision selects the mode
+        from paper_1908_04489_gb300 import workloads as W
+        p = W.source_channel(precision=args.precision)
+        with binding.Instance(p) as inst:
+            inst.sweep(args.profile_sweeps)
+            J = inst.eval_J()
+        print(json.dumps({"workload": "sc", "precision": args.precision, "J": J,
+                          "sweeps": args.profile_sweeps}))
+        torch.cuda.synchronize()
+        return
     p, _ = workload(args.workload, args.precision)
     # on a non-default stream the sweeps replay captured graphs (the bench's
     # timed path); on the default stream they launch kernel by kernel

@@ -263,9 +263,10 @@ UCP_API ucp_status ucp_solve(ucp_inst* inst, const ucp_solve_params* params,
                              ucp_solve_report* report, double* J_phase,
                              int32_t* NL_rounds);
 
-/* Fast path: number of candidate costs re-computed by the serial FP64
- * quadrature because screened table costs left a near-tie open (since
- * creation; 0 on the plain path).  Synchronises. */
+/* Fast path and problem 1's fast mode: number of candidate costs
+ * re-computed by the fixed-order FP64 quadrature because screened table
+ * costs left a near-tie open (since creation; 0 on the plain path).
+ * Synchronises. */
 UCP_API ucp_status ucp_tie_recosts(ucp_inst* inst, int64_t* out);
 
 /* The fast path's correlation tables of the current u1 table, for tests and

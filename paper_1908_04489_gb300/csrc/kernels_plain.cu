@@ -762,36 +762,21 @@ __global__ void __launch_bounds__(kLocalT) k_local_update(Geom g, const double* 
 __device__ __forceinline__ int64_t sc_lo(const Geom& g) { return -g.n_w - 1; }
 __device__ __forceinline__ int64_t sc_len(const Geom& g) { return g.n_y + g.n_w + 2; }
 
-// consts[0] = max |U|, consts[1] = W (one block).
-__global__ void __launch_bounds__(256) k_sc_consts(Geom g, const double* __restrict__ U,
+// One warp per cell j = sc_lo + a: tab[3 a + {0, 1, 2}] = A0, B0, B1 (lanes
+// take taps l = lane, lane + 32, ..., then a fixed butterfly); consts[0] =
+// max |U| (every warp's maximum over the taps it read -- together every
+// entry -- folded in by an atomic maximum on the bit patterns, which order
+// like the non-negative doubles; zeroed before) and consts[1] = W (warp 0).
+__global__ void __launch_bounds__(128) k_sc_tables(Geom g, const double* __restrict__ U,
                                                    const double* __restrict__ phi,
+                                                   double* __restrict__ tab,
                                                    double* __restrict__ consts) {
-    __shared__ double red[256];
-    double m = 0.0;
-    for (int64_t j = threadIdx.x; j < g.n_y; j += blockDim.x) m = fmax(m, fabs(U[j]));
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double w = 0.0;
-        for (int64_t l = 0; l < g.n_w; ++l) w += phi[l];
-        consts[0] = red[0];
-        consts[1] = w;
-    }
-}
-
-// tab[3 a + {0, 1, 2}] = A0, B0, B1 at cell j = sc_lo + a.
-__global__ void __launch_bounds__(256) k_sc_tables(Geom g, const double* __restrict__ U,
-                                                   const double* __restrict__ phi,
-                                                   double* __restrict__ tab) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= sc_len(g)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (a >= sc_len(g)) return;   // the same for the warp
     const int64_t j = sc_lo(g) + a, ny1 = g.n_y - 1;
-    double A = 0.0, B0 = 0.0, B1 = 0.0;
-    for (int64_t l = 0; l < g.n_w; ++l) {
+    double A = 0.0, B0 = 0.0, B1 = 0.0, m = 0.0, W = 0.0;
+    for (int64_t l = lane; l < g.n_w; l += 32) {
         const int64_t j0 = j + l, j1 = j0 + 1;
         const double u0 = U[j0 < 0 ? 0 : (j0 > ny1 ? ny1 : j0)];
         const double u1 = U[j1 < 0 ? 0 : (j1 > ny1 ? ny1 : j1)];
@@ -799,10 +784,25 @@ __global__ void __launch_bounds__(256) k_sc_tables(Geom g, const double* __restr
         A += w * u0;
         B0 += w * (u0 * u0);
         B1 += w * (u0 * u1);
+        m = fmax(m, fabs(u0));
+        W += w;
     }
-    tab[3 * a] = A;
-    tab[3 * a + 1] = B0;
-    tab[3 * a + 2] = B1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        A += __shfl_xor_sync(0xffffffffu, A, off);
+        B0 += __shfl_xor_sync(0xffffffffu, B0, off);
+        B1 += __shfl_xor_sync(0xffffffffu, B1, off);
+        W += __shfl_xor_sync(0xffffffffu, W, off);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    }
+    if (lane == 0) {
+        tab[3 * a] = A;
+        tab[3 * a + 1] = B0;
+        tab[3 * a + 2] = B1;
+        atomicMax(reinterpret_cast<unsigned long long*>(consts),
+                  (unsigned long long)__double_as_longlong(m));
+        if (a == 0) consts[1] = W;
+    }
 }
 
 // Table cost of candidate nu at x0 point i (value x) and its bound.
@@ -835,7 +835,8 @@ __device__ __forceinline__ double warp_min_d(double v) {
 __device__ __noinline__ double sc_exact(const Geom& g, const double* __restrict__ phi,
                                         const double* __restrict__ U,
                                         const double* __restrict__ Ud, int64_t nu, int64_t i,
-                                        int lane) {
+                                        int lane, unsigned long long* count) {
+    if (lane == 0) atomicAdd(count, 1ull);
     return cost_from_S(g, i, nu, quad_split<32>(g, phi, U, Ud, nu, i, lane, 0));
 }
 
@@ -852,8 +853,8 @@ struct ScStage {
 
     __device__ void offer(const Geom& g, const double* __restrict__ phi,
                           const double* __restrict__ U, const double* __restrict__ Ud,
-                          int64_t i, int lane, int64_t v, int32_t pos, double vgt, double veb,
-                          bool vknown, double vex) {
+                          unsigned long long* count, int64_t i, int lane, int64_t v,
+                          int32_t pos, double vgt, double veb, bool vknown, double vex) {
         if (__any_sync(0xffffffffu, lane < nseen && seen == v)) return;
         if (nseen < 32) {
             if (lane == nseen) seen = v;
@@ -864,10 +865,10 @@ struct ScStage {
             return;
         }
         if (!known) {
-            bex = sc_exact(g, phi, U, Ud, b, i, lane);
+            bex = sc_exact(g, phi, U, Ud, b, i, lane, count);
             known = true;
         }
-        const double ex = vknown ? vex : sc_exact(g, phi, U, Ud, v, i, lane);
+        const double ex = vknown ? vex : sc_exact(g, phi, U, Ud, v, i, lane, count);
         if (ex < bex) {
             b = v; bp = pos; bgt = vgt; beb = veb; bex = ex;
         }
@@ -881,13 +882,15 @@ struct ScStage {
 __global__ void __launch_bounds__(128) k_search_sc(
     Geom g, const double* __restrict__ phi, const double* __restrict__ U,
     const double* __restrict__ Ud, const double* __restrict__ tab,
-    const double* __restrict__ consts, const int64_t* __restrict__ nu_pre,
+    double* __restrict__ consts, const int64_t* __restrict__ nu_pre,
     const int64_t* __restrict__ coarse, int64_t* __restrict__ nu_out,
     int32_t* __restrict__ idx_out, int64_t i_lo, int64_t i_hi) {
     const int lane = threadIdx.x & 31;
     const int64_t i = i_lo + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (i >= i_hi) return;   // the same for the warp
     const double um = consts[0], W = consts[1], x = x_of(g, i);
+    // exact re-costs of this instance (a work counter, zeroed at creation)
+    unsigned long long* count = (unsigned long long*)(consts + 2);
     const int n0 = 1 + 2 * g.n_nbr + g.n_coarse;
     auto stage0 = [&](int p) -> int64_t {
         if (p == 0) return nu_pre[i];
@@ -921,7 +924,7 @@ __global__ void __launch_bounds__(128) k_search_sc(
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            st.offer(g, phi, U, Ud, i, lane, __shfl_sync(0xffffffffu, v, src), base + src,
+            st.offer(g, phi, U, Ud, count, i, lane, __shfl_sync(0xffffffffu, v, src), base + src,
                      __shfl_sync(0xffffffffu, gt, src), __shfl_sync(0xffffffffu, eb, src),
                      false, 0.0);
         }
@@ -941,12 +944,13 @@ __global__ void __launch_bounds__(128) k_search_sc(
         const double t = fmin(warp_min_d(mine ? gt + eb : DBL_MAX), st.bgt + st.beb);
         ScStage nx;
         if (st.bgt - st.beb <= t)
-            nx.offer(g, phi, U, Ud, i, lane, st.b, st.bp, st.bgt, st.beb, st.known, st.bex);
+            nx.offer(g, phi, U, Ud, count, i, lane, st.b, st.bp, st.bgt, st.beb, st.known,
+                     st.bex);
         unsigned mask = __ballot_sync(0xffffffffu, mine && gt - eb <= t);
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            nx.offer(g, phi, U, Ud, i, lane, __shfl_sync(0xffffffffu, v, src), pos + src,
+            nx.offer(g, phi, U, Ud, count, i, lane, __shfl_sync(0xffffffffu, v, src), pos + src,
                      __shfl_sync(0xffffffffu, gt, src), __shfl_sync(0xffffffffu, eb, src),
                      false, 0.0);
         }
@@ -959,11 +963,65 @@ __global__ void __launch_bounds__(128) k_search_sc(
     }
 }
 
+// J's quadrature terms Sf[i] = Q(f_i; x_i), one warp per x0 point through
+// the split quadrature (the same double as Q_plain).
+__global__ void __launch_bounds__(128) k_sc_S_f(Geom g, const double* __restrict__ phi,
+                                                const double* __restrict__ U,
+                                                const double* __restrict__ Ud,
+                                                const int64_t* __restrict__ nu,
+                                                double* __restrict__ Sf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (i >= g.n_x) return;   // the same for the warp
+    const double q = quad_split<32>(g, phi, U, Ud, nu[i], i, lane, 0);
+    if (lane == 0) Sf[i] = q;
+}
+
+// J = sum_i p_i g(f_i; x_i) in the fixed order (32-term chunks left to
+// right, then pairwise by levels): one block; the products are formed in
+// parallel into shared memory, the chunk sums from there (n_x <= kScJTerms).
+constexpr int kScJTerms = 4096;
+__global__ void __launch_bounds__(1024) k_sc_J(Geom g, const double* __restrict__ px,
+                                               const int64_t* __restrict__ nu,
+                                               const double* __restrict__ Sf,
+                                               double* __restrict__ out) {
+    __shared__ double v[kScJTerms];
+    __shared__ double ch[kScJTerms / kSumChunk];
+    const int64_t n = g.n_x, m = sum_chunks(n);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        v[i] = __dmul_rn(px[i], cost_from_S(g, i, nu[i], Sf[i]));
+    __syncthreads();
+    for (int64_t k = threadIdx.x; k < m; k += blockDim.x) {
+        double a = 0.0;
+        const int64_t e = min((k + 1) * kSumChunk, n);
+        for (int64_t i = k * kSumChunk; i < e; ++i) a = __dadd_rn(a, v[i]);
+        ch[k] = a;
+    }
+    __syncthreads();
+    for (int64_t w = m; w > 1;) {
+        const int64_t h = w / 2;
+        for (int64_t k0 = 0; k0 < h; k0 += blockDim.x) {
+            const int64_t k = k0 + threadIdx.x;
+            const double a = k < h ? __dadd_rn(ch[2 * k], ch[2 * k + 1]) : 0.0;
+            __syncthreads();
+            if (k < h) ch[k] = a;
+            __syncthreads();
+        }
+        if (w & 1) {
+            if (threadIdx.x == 0) ch[h] = ch[w - 1];
+            __syncthreads();
+        }
+        w = h + (w & 1);
+    }
+    if (threadIdx.x == 0) *out = m ? ch[0] : 0.0;
+}
+
 // The u1 step of problem 1 with one warp per target: the nearest distance
 // (a minimum, exact in any order), then the prior-weighted sums of x_i over
 // the sources within reach (lane-strided partial sums, then a fixed
-// butterfly), with the normalised prior weights px.
-__global__ void __launch_bounds__(128) k_mmse_uniform_w(Geom g, const int64_t* __restrict__ nu,
+// butterfly), with the normalised prior weights px; fv = f values (the
+// same doubles as value_of).
+__global__ void __launch_bounds__(128) k_mmse_uniform_w(Geom g, const double* __restrict__ fv,
                                                         const double* __restrict__ px,
                                                         double* __restrict__ U) {
     const int lane = threadIdx.x & 31;
@@ -972,12 +1030,12 @@ __global__ void __launch_bounds__(128) k_mmse_uniform_w(Geom g, const int64_t* _
     const double yj = __dmul_rn((double)(j - g.hy), g.delta);
     double dmin = DBL_MAX;
     for (int64_t i = lane; i < g.n_x; i += 32)
-        dmin = fmin(dmin, fabs(__dsub_rn(yj, value_of(g, nu[i]))));
+        dmin = fmin(dmin, fabs(__dsub_rn(yj, fv[i])));
     dmin = warp_min_d(dmin);
     const double reach = dmin <= g.w_noise ? g.w_noise : dmin;
     double num = 0.0, den = 0.0;
     for (int64_t i = lane; i < g.n_x; i += 32) {
-        if (fabs(__dsub_rn(yj, value_of(g, nu[i]))) <= reach) {
+        if (fabs(__dsub_rn(yj, fv[i])) <= reach) {
             num += px[i] * x_of(g, i);
             den += px[i];
         }
@@ -1056,8 +1114,10 @@ void launch_coarse_list(const Geom& g, DevState& d, cudaStream_t s) {
 }
 
 void launch_mmse_plain(const Geom& g, DevState& d, int buf, cudaStream_t s) {
-    if (g.sc_fast)
-        k_mmse_uniform_w<<<blocks(32 * g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.px, d.U);
+    if (g.sc_fast) {
+        k_f_values<<<blocks(g.n_x, 256), 256, 0, s>>>(g, d.nu[buf], d.sc_f, 0);
+        k_mmse_uniform_w<<<blocks(32 * g.n_y, 128), 128, 0, s>>>(g, d.sc_f, d.px, d.U);
+    }
     else if (g.problem == 1)
         k_mmse_uniform<<<blocks(g.n_y, spread_bs(g.n_y, 128)), spread_bs(g.n_y, 128), 0, s>>>(
             g, d.nu[buf], d.U);
@@ -1094,6 +1154,10 @@ void launch_udiff(const Geom& g, DevState& d, cudaStream_t s) {
 void launch_S_list(const Geom& g, DevState& d, const int64_t* nus, int64_t n,
                    double* out, cudaStream_t s, int at_x) {
     if (n <= 0) return;
+    if (g.sc_fast && at_x && n == g.n_x) {   // J's terms of every x0 point
+        k_sc_S_f<<<blocks(32 * n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, nus, out);
+        return;
+    }
     const int bs = spread_bs(n, 128);
     k_S_list<<<blocks(n, bs), bs, 0, s>>>(g, d.phi, d.U, d.Ud, nus, n, out, at_x);
 }
@@ -1105,8 +1169,8 @@ void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s,
     if (n <= 0) return;
     if (g.sc_fast) {   // problem 1, fast mode: tables of the current U, screened search
         const int64_t len = g.n_y + g.n_w + 2;
-        k_sc_consts<<<1, 256, 0, s>>>(g, d.U, d.phi, d.sc_consts);
-        k_sc_tables<<<blocks(len, 256), 256, 0, s>>>(g, d.U, d.phi, d.sc_tab);
+        cudaMemsetAsync(d.sc_consts, 0, sizeof(double), s);
+        k_sc_tables<<<blocks(32 * len, 128), 128, 0, s>>>(g, d.U, d.phi, d.sc_tab, d.sc_consts);
         k_search_sc<<<blocks(32 * n, 128), 128, 0, s>>>(g, d.phi, d.U, d.Ud, d.sc_tab,
                                                         d.sc_consts, d.nu[buf_in], d.coarse,
                                                         d.nu[buf_in ^ 1], d.idx, i_lo, i_hi);
@@ -1142,7 +1206,10 @@ void launch_search_plain(const Geom& g, DevState& d, int buf_in, cudaStream_t s,
 
 void launch_J_plain(const Geom& g, DevState& d, int buf, int slot,
                     cudaStream_t s) {
-    k_J_plain<<<1, 256, 0, s>>>(g, d.px, d.nu[buf], d.Sf, d.J + slot);
+    if (g.sc_fast && g.n_x <= kScJTerms)
+        k_sc_J<<<1, 1024, 0, s>>>(g, d.px, d.nu[buf], d.Sf, d.J + slot);
+    else
+        k_J_plain<<<1, 256, 0, s>>>(g, d.px, d.nu[buf], d.Sf, d.J + slot);
 }
 
 void launch_f_values(const Geom& g, const int64_t* nu, const double*,

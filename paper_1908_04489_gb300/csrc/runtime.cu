@@ -222,7 +222,7 @@ size_t inst_bytes(const Geom& g, int precision) {
     const size_t nc = (size_t)g.n_coarse;
     size_t b = 6 * rnd(8 * nx) + rnd(4 * nx) + 2 * rnd(8 * ny) + rnd(8 * nw) +
                2 * rnd(8 * nc) + rnd(8 * 64) + rnd(8 * 4096);
-    if (g.sc_fast) b += rnd(8 * 3 * (size_t)(g.n_y + g.n_w + 2)) + rnd(8 * 4);
+    if (g.sc_fast) b += rnd(8 * 3 * (size_t)(g.n_y + g.n_w + 2)) + rnd(8 * 4) + rnd(8 * nx);
     if (precision == 1 && g.problem == 0) {
         FastPlan fp;
         fast_plan(g, &fp);
@@ -387,14 +387,16 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     if (g.sc_fast) {
         d.sc_tab = (double*)A.get(8 * 3 * (size_t)(g.n_y + g.n_w + 2));
         d.sc_consts = (double*)A.get(8 * 4);
+        d.sc_f = (double*)A.get(8 * nx);
     }
     if (!d.px || !d.phi || !d.U || !d.Ud || !d.nu[0] || !d.nu[1] || !d.coarse ||
         !d.Sf || !d.Sc || !d.idx || !d.J || !d.scratch || !d.table ||
-        (g.sc_fast && (!d.sc_tab || !d.sc_consts))) {
+        (g.sc_fast && (!d.sc_tab || !d.sc_consts || !d.sc_f))) {
         set_error("%s%s", "ucp_create: out of device memory", "");
         return UCP_E_NOMEM;
     }
     in->fast = p.precision == 1 && p.problem == 0;
+    if (g.sc_fast) cudaMemsetAsync(d.sc_consts, 0, 8 * 4, stream);
     if (in->fast) {
         if (tc_init_attributes() != cudaSuccess) return check(in, "tensor-core kernel attributes");
         ucp_status st = fast_alloc(in);

@@ -54,7 +54,8 @@ struct DevState {
     double* scratch;  // reduction partials
     double* table;    // [n_x] staging for table inits / set_controllers
     double* sc_tab;   // problem 1 fast mode: [3 (n_y + n_w + 2)] tables A0, B0, B1
-    double* sc_consts;// problem 1 fast mode: max |U| and the weight sum
+    double* sc_consts;// problem 1 fast mode: max |U|, the weight sum, exact re-costs
+    double* sc_f;     // problem 1 fast mode: [n_x] f values
 };
 
 // Sizes of the fast path's buffers for one instance.
