@@ -753,8 +753,8 @@ __device__ __forceinline__ dfloat df_dot_add(dfloat acc, dfloat a, dfloat b) {
     return df_acc(acc, p, e);
 }
 __device__ __forceinline__ bool tab_cost_df(const G2& g, const float2* __restrict__ tabf,
-                                            double um, dfloat W, const Pt2& pt, int64_t nu1,
-                                            int64_t nu2, double& gt, double& eb) {
+                                            float um, dfloat W, const Pt2& pt, int64_t nu1,
+                                            int64_t nu2, dfloat& lo, dfloat& hi) {
     const int64_t lim = (int64_t)1 << 44;
     if (nu1 >= lim || nu1 <= -lim || nu2 >= lim || nu2 <= -lim) return false;
     const int64_t c1 = nu1 >> g.shift, c2 = nu2 >> g.shift;
@@ -807,16 +807,29 @@ __device__ __forceinline__ bool tab_cost_df(const G2& g, const float2* __restric
     S = df_add(S, dfloat{2.0f * X.hi, 2.0f * X.lo});
     const dfloat d1 = df_sub(u1, pt.xa_d), d2 = df_sub(u2, pt.xb_d);
     const dfloat kt = df_mul(df_dot_add(df_mul(d1, d1), d2, d2), dfloat{g.kk_hi, g.kk_lo});
-    gt = df_to_double(df_add(kt, S));
-    const float ua = fabsf(u1.hi) + fabsf(u2.hi), umf = (float)um;
-    const float M = uu.hi + 2.0f * ua * umf + 2.0f * umf * umf;
-    eb = g.eps_df * (1.001 * (double)M + fabs(gt));
+    const dfloat gv = df_add(kt, S);
+    // the bound in FP32 (eps_df rounded up, M and |g| to ~2^-21), widened by
+    // 0.1%, which also covers the pair additions forming the interval's ends
+    // (2^-47 |g| against eb >= 2^-37 M)
+    const float ua = fabsf(u1.hi) + fabsf(u2.hi);
+    const float M = uu.hi + 2.0f * ua * um + 2.0f * um * um;
+    const float eb = g.eps_df_f * (M + fabsf(gv.hi)) * 1.001f;
+    lo = df_add_f(gv, -eb);
+    hi = df_add_f(gv, eb);
     return true;
 }
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kExactCh = 512;   // chunk sums of one exact cost a warp keeps in shared memory
 
+__device__ __forceinline__ dfloat warp_min_df(dfloat v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const dfloat o{__shfl_xor_sync(kFull, v.hi, off), __shfl_xor_sync(kFull, v.lo, off)};
+        if (df_lt(o, v)) v = o;
+    }
+    return v;
+}
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, off));
@@ -883,13 +896,14 @@ struct Stage2 {
     bool has = false, known = false;
     int64_t b1 = 0, b2 = 0;
     int32_t bp = 0;
-    double bgt = 0.0, beb = 0.0, bex = 0.0;
+    dfloat blo{0.f, 0.f}, bhi{0.f, 0.f};
+    double bex = 0.0;
     int nseen = 0;
     int64_t s1 = 0, s2 = 0;
 
     __device__ void offer(const G2& g, const double* __restrict__ phi2,
                           const double* __restrict__ U, int64_t i, double* ch, int lane,
-                          int64_t v1, int64_t v2, int32_t pos, double vgt, double veb,
+                          int64_t v1, int64_t v2, int32_t pos, dfloat vlo, dfloat vhi,
                           bool vknown, double vex) {
         if (__any_sync(kFull, lane < nseen && s1 == v1 && s2 == v2)) return;
         if (nseen < 32) {
@@ -901,7 +915,7 @@ struct Stage2 {
         }
         if (!has) {
             has = true;
-            b1 = v1; b2 = v2; bp = pos; bgt = vgt; beb = veb;
+            b1 = v1; b2 = v2; bp = pos; blo = vlo; bhi = vhi;
             known = vknown;
             bex = vex;
             return;
@@ -912,7 +926,7 @@ struct Stage2 {
         }
         const double ex = vknown ? vex : warp_exact(g, phi2, U, i, v1, v2, ch, lane);
         if (ex < bex) {
-            b1 = v1; b2 = v2; bp = pos; bgt = vgt; beb = veb; bex = ex;
+            b1 = v1; b2 = v2; bp = pos; blo = vlo; bhi = vhi; bex = ex;
         }
     }
 };
@@ -933,67 +947,80 @@ __global__ void __launch_bounds__(kSearch2T) k2_search_scr(
     if (i >= g.n_x * g.n_x) return;   // the same for the warp
     const double um = consts[0], W = consts[1];
     const dfloat Wd = df_from_double(W);
+    const float umf = __double2float_ru(um);
     const Pt2 pt = make_pt2(g, i);
-    // The double-float table cost where it applies, else the FP64 one (both
-    // certified, so the two may mix).
-    auto cost = [&](int64_t n1, int64_t n2, double& gt, double& eb) {
-        if (!(g.use_df && tab_cost_df(g, tabf, um, Wd, pt, n1, n2, gt, eb)))
-            tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
+    // The certified interval [g~ - eb, g~ + eb] of a candidate's exact cost as
+    // double-float ends: from the double-float table cost where it applies,
+    // else from the FP64 one (ends widened by 10%, far more than their
+    // rounding to pairs).  Lexicographic comparison of normalised pairs is
+    // exact, so the stage logic below is the FP64 one.
+    auto cost = [&](int64_t n1, int64_t n2, dfloat& lo, dfloat& hi) {
+        if (g.use_df && tab_cost_df(g, tabf, umf, Wd, pt, n1, n2, lo, hi)) return;
+        double gt, eb;
+        tab_cost(g, tab, um, W, pt, n1, n2, gt, eb);
+        lo = df_from_double(gt - 1.1 * eb);
+        hi = df_from_double(gt + 1.1 * eb);
     };
+    const dfloat inf{FLT_MAX, 0.f};
     const int64_t side = 2 * (int64_t)g.n_nbr + 1;
     const int n0 = (int)(side * side + (int64_t)g.n_coarse * g.n_coarse);
-    double thr = DBL_MAX;
+    dfloat thr = inf;
     for (int p = lane; p < n0; p += 32) {
         int64_t n1, n2;
-        double gt, eb;
+        dfloat lo, hi;
         stage0_cand_pt(g, nu_pre, pt, p, n1, n2);
-        cost(n1, n2, gt, eb);
-        thr = fmin(thr, gt + eb);
+        cost(n1, n2, lo, hi);
+        if (df_lt(hi, thr)) thr = hi;
     }
-    thr = warp_min(thr);
+    thr = warp_min_df(thr);
     Stage2 st;
     for (int base = 0; base < n0; base += 32) {
         const int p = base + lane;
         int64_t n1 = 0, n2 = 0;
-        double gt = 0.0, eb = 0.0;
+        dfloat lo = inf, hi = inf;
         bool cont = false;
         if (p < n0) {
             stage0_cand_pt(g, nu_pre, pt, p, n1, n2);
-            cost(n1, n2, gt, eb);
-            cont = gt - eb <= thr;
+            cost(n1, n2, lo, hi);
+            cont = !df_lt(thr, lo);
         }
         unsigned mask = __ballot_sync(kFull, cont);
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
             st.offer(g, phi2, U, i, ch, lane, __shfl_sync(kFull, n1, src),
-                     __shfl_sync(kFull, n2, src), base + src, __shfl_sync(kFull, gt, src),
-                     __shfl_sync(kFull, eb, src), false, 0.0);
+                     __shfl_sync(kFull, n2, src), base + src,
+                     dfloat{__shfl_sync(kFull, lo.hi, src), __shfl_sync(kFull, lo.lo, src)},
+                     dfloat{__shfl_sync(kFull, hi.hi, src), __shfl_sync(kFull, hi.lo, src)},
+                     false, 0.0);
         }
     }
     int pos = n0;
     for (int lv = 1; lv <= g.n_levels; ++lv) {
         const int64_t h = g.q << (g.n_levels - lv);
         int64_t n1 = 0, n2 = 0;
-        double gt = 0.0, eb = 0.0;
+        dfloat lo = inf, hi = inf;
         if (lane < 8) {
             const int k9 = lane < 4 ? lane : lane + 1;       // 3 x 3 window, centre skipped
             n1 = st.b1 + (int64_t)(k9 / 3 - 1) * h;
             n2 = st.b2 + (int64_t)(k9 % 3 - 1) * h;
-            cost(n1, n2, gt, eb);
+            cost(n1, n2, lo, hi);
         }
-        const double t = fmin(warp_min(lane < 8 ? gt + eb : DBL_MAX), st.bgt + st.beb);
+        dfloat t = warp_min_df(hi);
+        if (df_lt(st.bhi, t)) t = st.bhi;
         Stage2 nx;
-        if (st.bgt - st.beb <= t)
-            nx.offer(g, phi2, U, i, ch, lane, st.b1, st.b2, st.bp, st.bgt, st.beb, st.known,
+        if (!df_lt(t, st.blo))
+            nx.offer(g, phi2, U, i, ch, lane, st.b1, st.b2, st.bp, st.blo, st.bhi, st.known,
                      st.bex);
-        unsigned mask = __ballot_sync(kFull, lane < 8 && gt - eb <= t);
+        unsigned mask = __ballot_sync(kFull, lane < 8 && !df_lt(t, lo));
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
             nx.offer(g, phi2, U, i, ch, lane, __shfl_sync(kFull, n1, src),
-                     __shfl_sync(kFull, n2, src), pos + src, __shfl_sync(kFull, gt, src),
-                     __shfl_sync(kFull, eb, src), false, 0.0);
+                     __shfl_sync(kFull, n2, src), pos + src,
+                     dfloat{__shfl_sync(kFull, lo.hi, src), __shfl_sync(kFull, lo.lo, src)},
+                     dfloat{__shfl_sync(kFull, hi.hi, src), __shfl_sync(kFull, hi.lo, src)},
+                     false, 0.0);
         }
         st = nx;
         pos += 8;
@@ -1094,6 +1121,7 @@ const char* make_g2(const ucp2_params& p, G2* g) {
     // pairs (2^-48): below 2^-39.5 M; taken as 2^-37 on top of eps_k.
     g->use_df = g->shift <= 24;
     g->eps_df = g->eps_k + 0x1p-37;
+    g->eps_df_f = (float)g->eps_df * (1.0f + 0x1p-20f);   // rounded up
     {
         const double us = ldexp(p.delta, -g->shift);
         g->us_hi = (float)us;

@@ -30,6 +30,7 @@ struct G2 {
     // (M + |g|), the lattice step delta 2^-shift as a float pair, 2^-shift.
     int32_t use_df;
     double eps_df;
+    float eps_df_f;
     float us_hi, us_lo, inv_one_f, kk_hi, kk_lo;
 };
 
