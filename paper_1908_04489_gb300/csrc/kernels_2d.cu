@@ -361,11 +361,13 @@ __global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const double* __restr
 // sources carries a relative error of about (32 + K / 32) 2^-47 of its sum
 // of magnitudes.  Stages that cannot matter on the tile are skipped.
 constexpr int kU1Tile = 32, kU1Stage = 32;
+constexpr unsigned kFull2 = 0xffffffffu;
 __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict__ fa,
                                                   const float2* __restrict__ fb,
                                                   const double* __restrict__ fv,
                                                   int64_t split_len, double* __restrict__ part) {
     __shared__ float2 sa[kU1Stage][kU1Tile + 1], sb[kU1Stage][kU1Tile + 1], sf[kU1Stage][2];
+    __shared__ unsigned wmax[2][8];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int64_t ny = g.n_y, n = g.n_x * g.n_x;
     const int64_t j1_0 = (int64_t)blockIdx.y * kU1Tile, j2_0 = (int64_t)blockIdx.x * kU1Tile;
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
 #pragma unroll
         for (int c = 0; c < 2; ++c) D[r][c] = N1[r][c] = N2[r][c] = dfloat{0.0f, 0.0f};
     for (int64_t i0 = i_lo; i0 < i_hi; i0 += kU1Stage) {
-        bool big_a = false, big_b = false;
+        unsigned ma = 0u, mb = 0u;   // bit patterns of the largest factors (>= 0)
         for (int k = threadIdx.x; k < kU1Stage * kU1Tile; k += 256) {
             const int sj = k / kU1Stage, si = k % kU1Stage;   // consecutive sources
             const int64_t i = i0 + si;
@@ -386,8 +388,8 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
             const float2 vb = ok && j2_0 + sj < ny ? fb[(j2_0 + sj) * n + i] : make_float2(0.f, 0.f);
             sa[si][sj] = va;
             sb[si][sj] = vb;
-            big_a |= va.x >= 0x1p-126f;
-            big_b |= vb.x >= 0x1p-126f;
+            ma = max(ma, __float_as_uint(va.x));
+            mb = max(mb, __float_as_uint(vb.x));
         }
         if (threadIdx.x < 2 * kU1Stage) {
             const int si = threadIdx.x >> 1, q = threadIdx.x & 1;
@@ -395,10 +397,22 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
             const dfloat f = df_from_double(i < i_hi ? fv[2 * i + q] : 0.0);
             sf[si][q] = make_float2(f.hi, f.lo);
         }
-        // A stage whose axis-1 or axis-2 factors are all below 2^-126 on this
-        // tile adds less than N 2^-126 to any sum (factors are at most 1): at
-        // most 2^-48 of a denominator that stays on this path (>= 2^-60).
-        const bool live = __syncthreads_or(big_a) && __syncthreads_or(big_b);
+        // A stage whose largest axis-1 factor times largest axis-2 factor on
+        // this tile is below 2^-126 adds less than N 2^-126 to any sum: at most
+        // 2^-48 of a denominator that stays on this path (>= 2^-60).
+        ma = __reduce_max_sync(kFull2, ma);
+        mb = __reduce_max_sync(kFull2, mb);
+        if ((threadIdx.x & 31) == 0) {
+            wmax[0][threadIdx.x >> 5] = ma;
+            wmax[1][threadIdx.x >> 5] = mb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            ma = max(ma, wmax[0][w]);
+            mb = max(mb, wmax[1][w]);
+        }
+        const bool live = __uint_as_float(ma) * __uint_as_float(mb) >= 0x1p-126f;
         if (!live) {
             __syncthreads();
             continue;
