@@ -761,6 +761,36 @@ def measure_2d(args, binding, torch, stream, flush):
     Jh = g.J_history()
     g.close()
     t = (float(np.median(times)) + last_ms) / 1e3
+    # one more solve with per-kernel-group events, for the dominant kernel's
+    # roofline: the u1 sums, 6 flops per (target, source) pair of the method
+    # (product, denominator, two numerators); issued as about 45 FP32-pipe
+    # instructions per pair slot of the stages it evaluates (not skipped)
+    with binding.Instance2D(p, stream=stream) as gp:
+        gp.profile(True)
+        gp.sweep(P2D_SWEEPS)
+        kern = gp.kernel_times()
+        live = gp.work_counters()["u1_live_pairs"]
+    peaks = pipe_peaks(binding.probe_alu(stream))
+    n_src = (2 * round(p["x_half"] / p["delta"]) + 1) ** 2
+    n_tgt = (2 * round(p["y_half"] / p["delta"]) + 1) ** 2
+    su = kern.get("u1_sums", (0, 0.0))
+    roof = None
+    if su[0]:
+        sec = su[1] / su[0] / 1e3
+        alg = 6.0 * n_src * n_tgt / sec / 1e12
+        live_per = live / (P2D_SWEEPS + 1)
+        issued = 45.0 * live_per / sec / 1e12
+        roof = {"kernel": "k2_u1_sums", "bound": "alu", "unit": "TFLOP/s",
+                "ms_per_launch": sec * 1e3, "pairs_per_launch": n_src * n_tgt,
+                "evaluated_pair_slots_per_pair": live_per / (n_src * n_tgt),
+                "achieved": alg, "peak": peaks["fp32"][0], "frac": alg / peaks["fp32"][0],
+                "peak_source": peaks["fp32"][2],
+                "work_model": "6 flops per (target, source) pair: the weight product, the "
+                              "denominator and two numerators",
+                "vs_fp64_peak": alg / peaks["fp64"][0],
+                "issued": {"fp32_pipe_instr_per_pair_slot": 45, "achieved_tinstr_per_s": issued,
+                           "frac_of_fp32_issue_peak": issued / (peaks["fp32"][0] / 2.0)}}
+    out_kern = {k: v[1] / P2D_SWEEPS for k, v in kern.items()}
     out = {"workload": "2-D Witsenhausen (Section V-D): k=0.2 sigma=5, 161x161 x0 over "
                        "[-25,25]^2 (delta=0.3125), 33x33 w, 225x225 y, 13x13 coarse + "
                        "8 levels, window radius 2, identity init, 40 sweeps",
@@ -768,7 +798,8 @@ def measure_2d(args, binding, torch, stream, flush):
            "ms_per_sweep": t * 1e3 / P2D_SWEEPS, "J": float(Jh[-1]),
            "J_paper": P2D_PAPER_J,
            "J_note": "plausibility band only: the paper's 160x160 samples, interpolation "
-                     "and candidate scheme differ"}
+                     "and candidate scheme differ",
+           "kernels_ms_per_sweep": out_kern, "roofline": roof}
     if args.no_cpu:
         return out
     import time as _t

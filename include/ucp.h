@@ -505,6 +505,17 @@ UCP_API ucp_status ucp2_get_controllers(ucp_inst2* inst, double* f, uint64_t f_l
  * or values beyond the lattice's range. */
 UCP_API ucp_status ucp2_set_controllers(ucp_inst2* inst, const double* f, uint64_t f_len,
                                         const double* u1, uint64_t u1_len);
+/* Per-kernel-group CUDA-event timing of later sweeps (enable 1; 0 stops
+ * and clears), read by ucp2_kernel_times as for ucp_kernel_times: up to cap
+ * entries of a static group name, its launches and total milliseconds;
+ * returns the number of groups, -1 on error.  Synchronises. */
+UCP_API ucp_status ucp2_profile(ucp_inst2* inst, int32_t enable);
+UCP_API int32_t ucp2_kernel_times(ucp_inst2* inst, const char** names, int64_t* launches,
+                                  double* total_ms, int32_t cap);
+/* Work counter since creation: (target, source) pair slots the factorised
+ * u1 sums evaluated -- 32 sources x 32 x 32 targets per stage not skipped as
+ * negligible, padding at the grid's edges included.  Synchronises. */
+UCP_API ucp_status ucp2_work_counters(ucp_inst2* inst, int64_t* live_pairs);
 UCP_API ucp_status ucp2_destroy(ucp_inst2* inst);
 
 #ifdef __cplusplus

@@ -201,6 +201,11 @@ def load():
     L.ucp2_get_controllers.argtypes = [_vp, _dp, _u64, _dp, _u64, _i32p, _u64]
     L.ucp2_set_controllers.argtypes = [_vp, _dp, _u64, _dp, _u64]
     L.ucp2_destroy.argtypes = [_vp]
+    L.ucp2_profile.argtypes = [_vp, ctypes.c_int32]
+    L.ucp2_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_char_p),
+                                    ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int32]
+    L.ucp2_kernel_times.restype = ctypes.c_int32
+    L.ucp2_work_counters.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     _lib = L
     return L
 
@@ -503,6 +508,24 @@ class Instance2D:
             self.h, _ptr(f, ctypes.c_double), 2 * nx2, _ptr(U, ctypes.c_double), 2 * ny2,
             _ptr(idx, ctypes.c_int32), nx2), "ucp2_get_controllers")
         return dict(f=f, U=U, idx=idx)
+
+    def profile(self, on=True):
+        _check(load().ucp2_profile(self.h, int(bool(on))), "ucp2_profile")
+
+    def kernel_times(self, cap=32) -> dict:
+        """{group: (launches, total ms)} of the profiled sweeps."""
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = load().ucp2_kernel_times(self.h, names, launches, ms, cap)
+        if n < 0:
+            raise UcpError(-4, "ucp2_kernel_times", "")
+        return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+    def work_counters(self) -> dict:
+        v = ctypes.c_int64()
+        _check(load().ucp2_work_counters(self.h, ctypes.byref(v)), "ucp2_work_counters")
+        return {"u1_live_pairs": v.value}
 
     def set_controllers(self, f, U=None):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)

@@ -20,6 +20,7 @@ struct ucp_inst2 {
     int cur = 0;
     long long sweeps = 0, J_cap = 0;
     bool poisoned = false;
+    Prof prof;   // CUDA-event timers per kernel group (ucp2_profile)
 };
 
 static void* alloc2(ucp_inst2* in, size_t bytes) {
@@ -151,6 +152,7 @@ extern "C" ucp_status ucp2_create(ucp_ctx* ctx, const ucp2_params* p, const doub
         }
     }
     cudaMemsetAsync(d.idx, 0xff, 4 * n, s);
+    cudaMemsetAsync(d.scratch, 0, 64, s);   // sums, constants, the live-pair count
     launch2_setup(g, d, init_f != nullptr, s);
     launch2_mmse(g, d, 0, s);
     launch2_J(g, d, 0, d.J, s);
@@ -170,11 +172,12 @@ extern "C" ucp_status ucp2_sweep(ucp_inst2* in, int32_t n) {
     if (in->poisoned) return UCP_E_STATE;
     if (ensure_J(in, in->sweeps + 1 + n) != UCP_OK) return UCP_E_NOMEM;
     for (int k = 0; k < n; ++k) {
-        launch2_sweep(in->g, in->d, in->cur, in->stream);
+        Prof* pr = in->prof.on ? &in->prof : nullptr;
+        launch2_sweep(in->g, in->d, in->cur, in->stream, pr);
         in->cur ^= 1;
         in->sweeps += 1;
-        launch2_mmse(in->g, in->d, in->cur, in->stream);
-        launch2_J(in->g, in->d, in->cur, in->d.J + in->sweeps, in->stream);
+        launch2_mmse(in->g, in->d, in->cur, in->stream, pr);
+        launch2_J(in->g, in->d, in->cur, in->d.J + in->sweeps, in->stream, pr);
     }
     return cuda_check(in, "ucp2_sweep");
 }
@@ -240,6 +243,30 @@ extern "C" ucp_status ucp2_set_controllers(ucp_inst2* in, const double* f, uint6
         return UCP_E_CUDA;
     }
     return cuda_check(in, "ucp2_set_controllers");
+}
+
+extern "C" ucp_status ucp2_profile(ucp_inst2* in, int32_t enable) {
+    if (!in) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    return prof_enable(&in->prof, in->stream, enable != 0);
+}
+
+extern "C" int32_t ucp2_kernel_times(ucp_inst2* in, const char** names, int64_t* launches,
+                                     double* total_ms, int32_t cap) {
+    if (!in || cap < 0) return -1;
+    if (cudaStreamSynchronize(in->stream) != cudaSuccess) return -1;
+    return prof_collect(&in->prof, names, launches, total_ms, cap);
+}
+
+extern "C" ucp_status ucp2_work_counters(ucp_inst2* in, int64_t* live_pairs) {
+    if (!in || !live_pairs) return UCP_E_ARG;
+    if (in->poisoned) return UCP_E_STATE;
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, in->d.scratch + 4, sizeof(v), cudaMemcpyDeviceToHost, in->stream);
+    if (cudaStreamSynchronize(in->stream) != cudaSuccess)
+        return cuda_check(in, "ucp2_work_counters");
+    *live_pairs = (int64_t)v;
+    return UCP_OK;
 }
 
 extern "C" ucp_status ucp2_destroy(ucp_inst2* in) {

@@ -21,6 +21,7 @@
 #include "df.cuh"
 #include "fixed_sum.cuh"
 #include "ucp_2d.h"
+#include "ucp_runtime.h"
 
 namespace ucp {
 
@@ -365,7 +366,8 @@ constexpr unsigned kFull2 = 0xffffffffu;
 __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict__ fa,
                                                   const float2* __restrict__ fb,
                                                   const double* __restrict__ fv,
-                                                  int64_t split_len, double* __restrict__ part) {
+                                                  int64_t split_len, double* __restrict__ part,
+                                                  unsigned long long* __restrict__ live_pairs) {
     __shared__ float2 sa[kU1Stage][kU1Tile + 1], sb[kU1Stage][kU1Tile + 1], sf[kU1Stage][2];
     __shared__ unsigned wmax[2][8];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -417,6 +419,7 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
             __syncthreads();
             continue;
         }
+        if (threadIdx.x == 0) atomicAdd(live_pairs, (unsigned long long)(kU1Stage * kU1Tile * kU1Tile));
         dfloat d[2][2], m1[2][2], m2[2][2];
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -1166,7 +1169,8 @@ void launch2_setup(const G2& g, Dev2& d, int from_table, cudaStream_t s) {
     k2_phin<<<nblk(g.n_w, 256), 256, 0, s>>>(g, d.phi1, d.scratch, d.phin);
 }
 
-void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s) {
+void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s, Prof* prof) {
+    ProfScope ps(prof, "search");
     const int64_t n = g.n_x * g.n_x;
     if (g.direct & 1) {
         k2_search<<<nblk(32 * n, kSearch2T), kSearch2T, 0, s>>>(g, d.phi2, d.U, d.nu[cur],
@@ -1177,8 +1181,9 @@ void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s) {
         g, d.phi2, d.U, d.tab, d.tabf, d.scratch + 2, d.nu[cur], d.nu[cur ^ 1], d.idx);
 }
 
-void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
+void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s, Prof* prof) {
     if (g.direct & 2) {
+        ProfScope ps(prof, "u1_direct");
         k2_mmse<<<nblk(g.n_y * g.n_y, 128), 128, 0, s>>>(g, d.nu[buf], d.U);
         return;
     }
@@ -1186,18 +1191,33 @@ void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s) {
     const int64_t len = (n + g.u1_splits - 1) / g.u1_splits;
     float2* fa = reinterpret_cast<float2*>(d.fa);
     float2* fb = reinterpret_cast<float2*>(d.fb);
-    k2_u1_sources<<<nblk(n, 256), 256, 0, s>>>(g, d.nu[buf], d.fv);
-    k2_u1_mins<<<(unsigned)(2 * g.n_y), 256, 0, s>>>(g, d.fv, d.mins);
-    k2_u1_factors<<<nblk(n * g.n_y, 256), 256, 0, s>>>(g, d.mins, d.fv, fa, fb, d.fa64, d.fb64);
-    k2_u1_sums<<<dim3((unsigned)tiles, (unsigned)tiles, (unsigned)g.u1_splits), 256, 0, s>>>(
-        g, fa, fb, d.fv, len, d.part);
-    cudaMemsetAsync(d.list, 0, sizeof(int32_t), s);
-    k2_u1_finish<<<nblk(g.n_y * g.n_y, 128), 128, 0, s>>>(g, d.part, g.u1_splits, d.U, d.list);
-    k2_u1_wide<<<(unsigned)(4 * 152), 128, 0, s>>>(g, d.nu[buf], d.fa64, d.fb64, d.fv, d.list,
-                                                   d.U);
+    {
+        ProfScope ps(prof, "u1_shifts");
+        k2_u1_sources<<<nblk(n, 256), 256, 0, s>>>(g, d.nu[buf], d.fv);
+        k2_u1_mins<<<(unsigned)(2 * g.n_y), 256, 0, s>>>(g, d.fv, d.mins);
+    }
+    {
+        ProfScope ps(prof, "u1_factors");
+        k2_u1_factors<<<nblk(n * g.n_y, 256), 256, 0, s>>>(g, d.mins, d.fv, fa, fb, d.fa64,
+                                                           d.fb64);
+    }
+    {
+        ProfScope ps(prof, "u1_sums");
+        k2_u1_sums<<<dim3((unsigned)tiles, (unsigned)tiles, (unsigned)g.u1_splits), 256, 0, s>>>(
+            g, fa, fb, d.fv, len, d.part, reinterpret_cast<unsigned long long*>(d.scratch + 4));
+    }
+    {
+        ProfScope ps(prof, "u1_finish");
+        cudaMemsetAsync(d.list, 0, sizeof(int32_t), s);
+        k2_u1_finish<<<nblk(g.n_y * g.n_y, 128), 128, 0, s>>>(g, d.part, g.u1_splits, d.U,
+                                                             d.list);
+        k2_u1_wide<<<(unsigned)(4 * 152), 128, 0, s>>>(g, d.nu[buf], d.fa64, d.fb64, d.fv,
+                                                       d.list, d.U);
+    }
 }
 
-void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s) {
+void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s, Prof* prof) {
+    ProfScope ps(prof, "tables_J");
     const int64_t n = g.n_x * g.n_x;
     if (!(g.direct & 1)) {
         // The tables of the new u1 table: J's terms now, the next search later.

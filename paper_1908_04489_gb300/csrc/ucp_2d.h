@@ -45,7 +45,7 @@ struct Dev2 {
     int64_t* nu[2];  // [2 n_x^2] controller, double buffered
     int32_t* idx;    // [n_x^2] winner positions of the last sweep
     double* terms;   // [n_x^2] J's terms
-    double* scratch; // normalising sums
+    double* scratch; // [8]: normalising sums, table constants, [4] live u1 pairs (count)
     double* table;   // [2 n_x^2] host table staging
     double* J;       // [J capacity] J history
     double* phin;    // [n_w] normalised one-dimensional noise weights
@@ -62,14 +62,17 @@ struct Dev2 {
     int32_t* list;   // [1 + n_y^2] count, then the targets of the FP64 pass
 };
 
+struct Prof;   // ucp_runtime.h: CUDA-event timers (null: none)
+
 void launch2_setup(const G2& g, Dev2& d, int from_table, cudaStream_t s);
-void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s);
-void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s);
+void launch2_sweep(const G2& g, Dev2& d, int cur, cudaStream_t s, Prof* prof = nullptr);
+void launch2_mmse(const G2& g, Dev2& d, int buf, cudaStream_t s, Prof* prof = nullptr);
 // J of controller buffer buf under the current u1 table into *out.  In the
 // screened mode it first rebuilds the correlation tables of that u1 table
 // (J's terms come from them, and the next search uses them), so it runs
 // after every change of U.
-void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s);
+void launch2_J(const G2& g, Dev2& d, int buf, double* out, cudaStream_t s,
+               Prof* prof = nullptr);
 void launch2_table(const G2& g, Dev2& d, int buf, cudaStream_t s);
 
 }  // namespace ucp

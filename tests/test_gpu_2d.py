@@ -382,3 +382,23 @@ def test_factorised_u1_matches_direct(B, O, case):
             j = o.n_y // 2 + round(20.0 / p["delta"])
             t = j * o.n_y + j
             assert np.array_equal(Ua[t], Ub[t])
+
+
+def test_profile_and_work_counters(B, O):
+    """Per-kernel-group timing and the evaluated-pair counter of the u1 sums:
+    every group of a sweep is timed once per sweep, and the counter stays
+    within the stages four u1 steps can evaluate (the first at creation)."""
+    o = O.Oracle2D(P2)
+    with B.Instance2D(P2) as g:
+        g.profile(True)
+        g.sweep(3)
+        kt = g.kernel_times()
+        for name in ("search", "u1_shifts", "u1_factors", "u1_sums", "u1_finish", "tables_J"):
+            assert kt[name][0] == 3 and kt[name][1] > 0.0, (name, kt)
+        live = g.work_counters()["u1_live_pairs"]
+        # a stage is 32 sources x 32 x 32 targets (padding included); over all
+        # source splits a tile has at most ceil(N / 32) + 64 stages per u1 step
+        tiles = -(-o.n_y // 32)
+        assert 0 < live <= 4 * tiles * tiles * (-(-o.N // 32) + 64) * 32 ** 3
+        g.profile(False)
+        assert g.kernel_times() == {}
