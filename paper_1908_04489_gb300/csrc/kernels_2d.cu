@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(256) k2_u1_factors(G2 g, const double* __restr
 
 // Partial sums of one split of the sources for a 32 x 32 tile of targets in
 // double-float arithmetic on the FP32 pipe: 256 threads, each a 2 x 2 block
-// of targets (rows ty + 16 r, columns tx + 16 c), 32 sources per
-// shared-memory stage.  Each stage is summed afresh (products kept as
+// of targets (rows 2 ty + r, columns tx + 16 c; a warp holds four whole
+// rows), 32 sources per shared-memory stage.  Each stage is summed afresh (products kept as
 // unnormalised pairs, accumulation normalised per term) and then added to
 // the running sums with the accurate double-float addition, so a split of K
 // sources carries a relative error of about (32 + K / 32) 2^-47 of its sum
@@ -419,47 +419,62 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
             __syncthreads();
             continue;
         }
-        if (threadIdx.x == 0) atomicAdd(live_pairs, (unsigned long long)(kU1Stage * kU1Tile * kU1Tile));
-        dfloat d[2][2], m1[2][2], m2[2][2];
+        // The same test per warp: its four target rows' largest axis-1 factor
+        // times the tile's largest axis-2 factor.  The flag is warp-uniform and
+        // every warp reaches the stage's closing barrier either way.
+        bool warp_live;
+        {
+            const int lane = threadIdx.x & 31, r0 = 4 * (threadIdx.x >> 5);
+            unsigned wa = 0u;
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 4; ++k) wa = max(wa, __float_as_uint(sa[lane][r0 + k].x));
+            wa = __reduce_max_sync(kFull2, wa);
+            warp_live = __uint_as_float(wa) * __uint_as_float(mb) >= 0x1p-126f;
+            if (warp_live && lane == 0)
+                atomicAdd(live_pairs, (unsigned long long)(kU1Stage * 4 * kU1Tile));
+        }
+        if (warp_live) {
+            dfloat d[2][2], m1[2][2], m2[2][2];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) d[r][c] = m1[r][c] = m2[r][c] = dfloat{0.0f, 0.0f};
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) d[r][c] = m1[r][c] = m2[r][c] = dfloat{0.0f, 0.0f};
 #pragma unroll 2
-        for (int si = 0; si < kU1Stage; ++si) {
-            dfloat a[2], b[2];
+            for (int si = 0; si < kU1Stage; ++si) {
+                dfloat a[2], b[2];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const float2 v = sa[si][ty + 16 * r];
-                a[r] = dfloat{v.x, v.y};
-            }
+                for (int r = 0; r < 2; ++r) {
+                    const float2 v = sa[si][2 * ty + r];
+                    a[r] = dfloat{v.x, v.y};
+                }
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float2 v = sb[si][tx + 16 * c];
-                b[c] = dfloat{v.x, v.y};
+                for (int c = 0; c < 2; ++c) {
+                    const float2 v = sb[si][tx + 16 * c];
+                    b[c] = dfloat{v.x, v.y};
+                }
+                const float2 f1 = sf[si][0], f2 = sf[si][1];
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        float p, e, q, qe;
+                        df_mul_raw(a[r], b[c], p, e);
+                        d[r][c] = df_acc(d[r][c], p, e);
+                        df_mul_raw(dfloat{p, e}, dfloat{f1.x, f1.y}, q, qe);
+                        m1[r][c] = df_acc(m1[r][c], q, qe);
+                        df_mul_raw(dfloat{p, e}, dfloat{f2.x, f2.y}, q, qe);
+                        m2[r][c] = df_acc(m2[r][c], q, qe);
+                    }
             }
-            const float2 f1 = sf[si][0], f2 = sf[si][1];
 #pragma unroll
             for (int r = 0; r < 2; ++r)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    float p, e, q, qe;
-                    df_mul_raw(a[r], b[c], p, e);
-                    d[r][c] = df_acc(d[r][c], p, e);
-                    df_mul_raw(dfloat{p, e}, dfloat{f1.x, f1.y}, q, qe);
-                    m1[r][c] = df_acc(m1[r][c], q, qe);
-                    df_mul_raw(dfloat{p, e}, dfloat{f2.x, f2.y}, q, qe);
-                    m2[r][c] = df_acc(m2[r][c], q, qe);
+                    D[r][c] = df_add_acc(D[r][c], d[r][c]);
+                    N1[r][c] = df_add_acc(N1[r][c], m1[r][c]);
+                    N2[r][c] = df_add_acc(N2[r][c], m2[r][c]);
                 }
-        }
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                D[r][c] = df_add_acc(D[r][c], d[r][c]);
-                N1[r][c] = df_add_acc(N1[r][c], m1[r][c]);
-                N2[r][c] = df_add_acc(N2[r][c], m2[r][c]);
-            }
+        }   // warp_live
         __syncthreads();
     }
     const int64_t plane = ny * ny;
@@ -468,7 +483,7 @@ __global__ void __launch_bounds__(256) k2_u1_sums(G2 g, const float2* __restrict
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int64_t j1 = j1_0 + ty + 16 * r, j2 = j2_0 + tx + 16 * c;
+            const int64_t j1 = j1_0 + 2 * ty + r, j2 = j2_0 + tx + 16 * c;
             if (j1 < ny && j2 < ny) {
                 const int64_t t = j1 * ny + j2;
                 out[t] = df_to_double(D[r][c]);
