@@ -88,8 +88,8 @@ def test_plan_rejects_invalid_fields(lib, field, value, msg):
 
 def test_source_channel_problem_is_planned_on_both_modes(lib):
     """Problem 1 (Section V-B): its plan has the grids of its parameters on
-    the plain path and in its fast mode (precision 1: the three tables, no
-    tensor-core buffers)."""
+    the plain path and in its fast mode (precision 1: the three tables and the
+    f values, no tensor-core buffers)."""
     from paper_1908_04489_gb300 import binding, workloads
     p = workloads.source_channel()
     s = binding.plan(p)
@@ -97,7 +97,7 @@ def test_source_channel_problem_is_planned_on_both_modes(lib):
     f = binding.plan(dict(p, precision=1))
     assert (f["n_x"], f["n_w"], f["n_y"], f["n_cand"]) == (501, 101, 701, 133)
     extra = f["device_bytes"] - s["device_bytes"]
-    assert 0 < extra <= 8 * 3 * (701 + 101 + 2) + 2 * 256
+    assert 0 < extra <= 8 * 3 * (701 + 101 + 2) + 8 * 501 + 3 * 256   # tables, f values
 
 
 def test_create_validates_before_touching_the_device(lib):
