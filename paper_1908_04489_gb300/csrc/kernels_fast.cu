@@ -344,6 +344,136 @@ __device__ void direct_df_cost2(const Geom& g, const FastView& f, int64_t i,
                __shfl_sync(gm, demax[b], 0, G), g2[b], b2[b]);
 }
 
+// ---- certified cost differences (between the second and third tiers) ------
+//
+// For two candidates r and m in one cell (fractions t_r, t_m = t_r + dt) the
+// residuals differ by dt dE_l, so
+//   S(m) - S(r) = sum_l phi_l dt dE_l (2 d_l(r) + dt dE_l),
+// a sum of small terms (no cancellation against S), and the control terms
+// differ by k^2 (u_m - u_r)(u_m + u_r - 2 x).  The block forms this in
+// double-float with a bound e_est far below the FP64 rounding of either cost;
+// the serial FP64 costs (the plain path's arithmetic on the same table) obey
+// |g_o(x) - g(x)| <= err_o(x) = beta_rel S + 2u (B + 3D) sqrt(S) + the
+// control term's and the final addition's roundings, B = max |U| and D =
+// max |U_{j+1} - U_j| over the taps (each residual's rounding is below
+// u (|e| + B + 3D), its square's below 3u e^2 + 2u |e| (B + 3D)).  When the
+// estimated difference exceeds e_est + err_o(m) + err_o(r), m's serial cost
+// is certainly above r's.  `delta` and `thresh` are the same in every thread.
+template <int G>
+__device__ void diff_df_coop(const Geom& g, const FastView& f, int64_t i, int64_t nu_r,
+                             int64_t nu_m, int lane, CoopSmem* cs, double& delta,
+                             double& thresh) {
+    const unsigned gm = group_mask<G>();
+    const int part = (int)(threadIdx.x / G), nparts = (int)(blockDim.x / G);
+    const int64_t cell = nu_r >> g.shift, p = cell - f.c_lo;
+    const dfloat t = df_mul_f(df_from_i64(nu_r - cell * g.one), f.inv_one_f);
+    const dfloat dt = df_mul_f(df_from_i64(nu_m - nu_r), f.inv_one_f);
+    double acc_d = 0.0, acc_s = 0.0;
+    dfloat bd{0.f, 0.f}, bs{0.f, 0.f};
+    float t1 = 0.f, t3 = 0.f, emax = 0.f, demax = 0.f;
+    int cnt = 0;
+#pragma unroll 2
+    for (int64_t l = part * G + lane; l < g.n_w; l += G * nparts) {
+        const dfloat w = f.wdf[l], ph = f.phidf[l];
+        const dfloat E0 = f.E[p + l], E1 = f.E[p + l + 1];
+        const dfloat dE = df_add_acc(E1, df_neg(E0));
+        const dfloat d = df_add_acc(df_add_acc(w, E0), df_mul(t, dE));
+        const dfloat dd = df_mul(dt, dE);
+        const dfloat s2 = df_add(df_add(d, d), dd);
+        const dfloat term = df_mul(ph, df_mul(dd, s2));
+        bd = df_add(bd, term);
+        bs = df_add(bs, df_mul(ph, df_mul(d, d)));
+        t1 = fmaf(ph.hi, fabsf(s2.hi), t1);
+        t3 += fabsf(term.hi);
+        emax = fmaxf(emax, fmaxf(fabsf(E0.hi), fabsf(E1.hi)));
+        demax = fmaxf(demax, fabsf(dE.hi));
+        if (++cnt == 8) {
+            acc_d += df_to_double(bd);
+            acc_s += df_to_double(bs);
+            bd = bs = dfloat{0.f, 0.f};
+            cnt = 0;
+        }
+    }
+    acc_d += df_to_double(bd);
+    acc_s += df_to_double(bs);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        acc_d += __shfl_down_sync(gm, acc_d, off, G);
+        acc_s += __shfl_down_sync(gm, acc_s, off, G);
+        t1 += __shfl_down_sync(gm, t1, off, G);
+        t3 += __shfl_down_sync(gm, t3, off, G);
+        emax = fmaxf(emax, __shfl_down_sync(gm, emax, off, G));
+        demax = fmaxf(demax, __shfl_down_sync(gm, demax, off, G));
+    }
+    __syncthreads();   // cs is free (the previous user has read its results)
+    if (lane == 0) {
+        cs->acc[part][0] = acc_d;
+        cs->acc[part][1] = acc_s;
+        cs->emax[part][0] = emax;
+        cs->emax[part][1] = demax;
+        cs->demax[part][0] = t1;
+        cs->demax[part][1] = t3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int q = threadIdx.x;
+        double dS = q < nparts ? cs->acc[q][0] : 0.0, Sr = q < nparts ? cs->acc[q][1] : 0.0;
+        float em = q < nparts ? cs->emax[q][0] : 0.f, dm = q < nparts ? cs->emax[q][1] : 0.f;
+        float T1 = q < nparts ? cs->demax[q][0] : 0.f, T3 = q < nparts ? cs->demax[q][1] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dS += __shfl_down_sync(0xffffffffu, dS, off);
+            Sr += __shfl_down_sync(0xffffffffu, Sr, off);
+            em = fmaxf(em, __shfl_down_sync(0xffffffffu, em, off));
+            dm = fmaxf(dm, __shfl_down_sync(0xffffffffu, dm, off));
+            T1 += __shfl_down_sync(0xffffffffu, T1, off);
+            T3 += __shfl_down_sync(0xffffffffu, T3, off);
+        }
+        if (q == 0) {
+            const double u = 0x1p-53, uf = 0x1p-48;
+            const dfloat step{f.step_hi, f.step_lo}, kk{f.kk_hi, f.kk_lo};
+            const int64_t base = (i - g.hx) * g.one, dnu = nu_m - nu_r;
+            const int64_t snu = nu_m + nu_r - 2 * base;
+            const int64_t lim = (int64_t)1 << 44;
+            const dfloat dctl = df_mul(kk, df_mul(df_mul(df_from_i64(dnu), step),
+                                                  df_mul(df_from_i64(snu), step)));
+            const double dc = df_to_double(dctl);
+            delta = dS + dc;
+            // magnitudes (FP64, rounded up by the final factor)
+            const double Y = (double)f.y_abs, B = (double)em + Y;
+            const double D = (double)dm + (double)f.delta_hi * 1.0001;
+            const double adt = fabs(df_to_double(dt));
+            const double sr = fmax(Sr, 0.0) * 1.01 + 1e-300, sm = fmax(Sr + dS, 0.0) * 1.01 + 1e-300;
+            auto err_o = [&](int64_t nu, double S) {
+                const double a = fabs(df_to_double(df_mul(df_from_i64(nu - base), step)));
+                const double uv = fabs(df_to_double(df_mul(df_from_i64(nu), step)));
+                const double xv = fabs((double)(i - g.hx)) * (double)f.delta_hi;
+                const double ctl = (double)f.kk_hi * a * a;
+                return (double)f.beta_rel * S + 2.0 * u * (B + 3.0 * D) * sqrt(S) +
+                       2.0 * u * (double)f.kk_hi * a * (uv + xv + 2.0 * a) + 4.0 * u * (ctl + S);
+            };
+            // the estimate's own error: the E table's representation (relative
+            // 2^-48 of |E| + |y|) in dt dE and in the residuals, the
+            // double-float operations and sums (generously 2^-40 of the terms'
+            // magnitudes) and the control difference (8 uf of itself)
+            const double epsE = 1.1 * uf * (B + Y);
+            const double e_est = 1.25 * (2.0 * adt * epsE * (double)T1 +
+                                         2.0 * uf * (f.w_half + 4.0 * B + dm) * adt * dm +
+                                         0x1p-40 * (double)T3) +
+                                 8.0 * uf * fabs(dc);
+            const bool ok = llabs(snu) < lim && llabs(dnu) < lim;
+            thresh = ok ? (e_est + err_o(nu_m, sm) + err_o(nu_r, sr)) * 1.01 + 1e-300
+                        : INFINITY;
+            cs->res2[0][0] = delta;
+            cs->res2[0][1] = thresh;
+        }
+    }
+    __syncthreads();
+    delta = cs->res2[0][0];
+    thresh = cs->res2[0][1];
+    __syncthreads();
+}
+
 // ---- screened table cost ------------------------------------------------
 
 struct Eval {
@@ -801,6 +931,37 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         const double wb = __shfl_sync(gm, b2, wl, G);
         return {df_from_double(wg), (float)(wb + 4.0e-15 * fabs(wg)) * 1.0001f, p2min,
                 v2min, false, 0.0};
+    }
+    // between the tiers (block-cooperative search): r = the first least
+    // second-tier cost in play; when every other member in play lies in r's
+    // cell and its cost difference to r is certified positive (diff_df_coop),
+    // r is the first minimum of the serial costs and no serial cost is formed
+    if (Mode == kTierCoop) {
+        const bool mine = lane < M && in2;
+        double rg = mine ? g2 : DBL_MAX;
+        int32_t rp = mine ? mpos : INT_MAX;
+        int64_t rn = mine ? mnu : 0;
+        glex<G>(rg, rp, rn);
+        const int64_t rcell = rn >> g.shift, rpp = rcell - f.c_lo;
+        const bool other = mine && mnu != rn;
+        const bool far = other && (mnu >> g.shift) != rcell;
+        bool cert = rpp >= 0 && rpp + 1 < f.n_pos && !__any_sync(gm, far);
+        unsigned om = (__ballot_sync(gm, other) >> base) & (0xffffffffu >> (32 - G));
+        while (cert && om) {
+            const int src = __ffs(om) - 1;
+            om &= om - 1;
+            double dlt, thr;
+            diff_df_coop<G>(g, f, i, rn, __shfl_sync(gm, mnu, src, G), lane, cs, dlt, thr);
+            cert = dlt > thr;
+        }
+        if (cert) {
+            const unsigned wmask = (__ballot_sync(gm, mine && mpos == rp) >> base) &
+                                   (0xffffffffu >> (32 - G));
+            const int wl = __ffs(wmask) - 1;
+            const double wb = __shfl_sync(gm, b2, wl, G);
+            return {df_from_double(rg), (float)(wb + 4.0e-15 * fabs(rg)) * 1.0001f, rp, rn,
+                    false, 0.0};
+        }
     }
     // third tier: serial FP64 costs of the members still in play
     double xg = DBL_MAX;

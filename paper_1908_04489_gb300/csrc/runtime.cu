@@ -272,6 +272,7 @@ static void fast_bounds(ucp_inst* in, double B) {
     f.beta2_rel = (float)(1.25 * (ser + 8.0 * u + 40.0 * uf2 +
                                   ((double)g.n_w / 16.0 + 8.0) * u));
     f.w_half = (float)W;
+    f.y_abs = (float)Y * (1.0f + 0x1p-20f);
 }
 
 static ucp_status fast_alloc(ucp_inst* in) {

@@ -151,6 +151,7 @@ struct FastView : FastPlan {
     float beta_ctl;      //   + beta_ctl sqrt(control term) + ...
     float beta2_rel;     // direct double-float quadrature: beta2_rel S + ...
     float w_half;        // W (largest |w_l|)
+    float y_abs;         // largest |y| on the extended grid of E
 };
 
 // Device-resident descriptor of one instance of a batch: everything a batched
