@@ -900,6 +900,43 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
     if (overflow)   // more distinct candidates in play than lanes (rare)
         return resolve_serial<G>(g, f, i, lane, best, have_best, hi, p0, p_end, cand,
                                  n_exact, cs);
+    // before the second tier (block-cooperative search): r = the member with
+    // the least table cost; when every other member lies in r's cell and is
+    // certified above it (diff_df_coop), r wins without the second tier
+    int64_t tried = INT64_MIN;   // the r whose certification failed
+    if (Mode == kTierCoop) {
+        const bool mine = lane < M;
+        double rg = DBL_MAX;
+        float rb = 0.f;
+        if (mine) {
+            const Eval e = eval_table(g, f, i, mnu);
+            rg = mexact ? mval : df_to_double(e.gv);
+            rb = mexact ? 0.f : e.beta;
+        }
+        int32_t rp = mine ? mpos : INT_MAX;
+        int64_t rn = mine ? mnu : 0;
+        glex<G>(rg, rp, rn);
+        const int64_t rcell = rn >> g.shift, rpp = rcell - f.c_lo;
+        const bool other = mine && mnu != rn;
+        const bool far = other && (mnu >> g.shift) != rcell;
+        bool cert = rpp >= 0 && rpp + 1 < f.n_pos && !__any_sync(gm, far);
+        unsigned om = (__ballot_sync(gm, other) >> base) & (0xffffffffu >> (32 - G));
+        const bool attempted = cert && om;
+        while (cert && om) {
+            const int src = __ffs(om) - 1;
+            om &= om - 1;
+            double dlt, thr;
+            diff_df_coop<G>(g, f, i, rn, __shfl_sync(gm, mnu, src, G), lane, cs, dlt, thr);
+            cert = dlt > thr;
+        }
+        if (cert) {
+            const unsigned wmask = (__ballot_sync(gm, mine && mpos == rp) >> base) &
+                                   (0xffffffffu >> (32 - G));
+            const float wb = __shfl_sync(gm, rb, __ffs(wmask) - 1, G);
+            return {df_from_double(rg), wb, rp, rn, false, 0.0};
+        }
+        if (attempted) tried = rn;
+    }
     // second tier
     double g2 = 0.0, b2 = 0.0;
     if (lane == 0 && n_exact && f.n_tier2) atomicAdd(f.n_tier2, M);
@@ -945,7 +982,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         const int64_t rcell = rn >> g.shift, rpp = rcell - f.c_lo;
         const bool other = mine && mnu != rn;
         const bool far = other && (mnu >> g.shift) != rcell;
-        bool cert = rpp >= 0 && rpp + 1 < f.n_pos && !__any_sync(gm, far);
+        bool cert = rn != tried && rpp >= 0 && rpp + 1 < f.n_pos && !__any_sync(gm, far);
         unsigned om = (__ballot_sync(gm, other) >> base) & (0xffffffffu >> (32 - G));
         while (cert && om) {
             const int src = __ffs(om) - 1;
