@@ -368,10 +368,10 @@ __device__ void diff_df_coop(const Geom& g, const FastView& f, int64_t i, int64_
     const int64_t cell = nu_r >> g.shift, p = cell - f.c_lo;
     const dfloat t = df_mul_f(df_from_i64(nu_r - cell * g.one), f.inv_one_f);
     const dfloat dt = df_mul_f(df_from_i64(nu_m - nu_r), f.inv_one_f);
-    double acc_d = 0.0, acc_s = 0.0;
+    // each thread's terms summed in double-float (off the FP64 pipe), then
+    // the threads' sums in FP64
     dfloat bd{0.f, 0.f}, bs{0.f, 0.f};
     float t1 = 0.f, t3 = 0.f, emax = 0.f, demax = 0.f;
-    int cnt = 0;
 #pragma unroll 2
     for (int64_t l = part * G + lane; l < g.n_w; l += G * nparts) {
         const dfloat w = f.wdf[l], ph = f.phidf[l];
@@ -387,15 +387,8 @@ __device__ void diff_df_coop(const Geom& g, const FastView& f, int64_t i, int64_
         t3 += fabsf(term.hi);
         emax = fmaxf(emax, fmaxf(fabsf(E0.hi), fabsf(E1.hi)));
         demax = fmaxf(demax, fabsf(dE.hi));
-        if (++cnt == 8) {
-            acc_d += df_to_double(bd);
-            acc_s += df_to_double(bs);
-            bd = bs = dfloat{0.f, 0.f};
-            cnt = 0;
-        }
     }
-    acc_d += df_to_double(bd);
-    acc_s += df_to_double(bs);
+    double acc_d = df_to_double(bd), acc_s = df_to_double(bs);
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
         acc_d += __shfl_down_sync(gm, acc_d, off, G);
@@ -453,13 +446,16 @@ __device__ void diff_df_coop(const Geom& g, const FastView& f, int64_t i, int64_
                        2.0 * u * (double)f.kk_hi * a * (uv + xv + 2.0 * a) + 4.0 * u * (ctl + S);
             };
             // the estimate's own error: the E table's representation (relative
-            // 2^-48 of |E| + |y|) in dt dE and in the residuals, the
-            // double-float operations and sums (generously 2^-40 of the terms'
-            // magnitudes) and the control difference (8 uf of itself)
+            // 2^-48 of |E| + |y|) in dt dE and in the residuals, each term's
+            // double-float operations (8 uf) and its thread's double-float sum
+            // of K terms (2 uf per addition), the FP64 sums over the threads,
+            // all below (K + 8) 2^-46 of the terms' magnitudes, and the control
+            // difference (8 uf of itself)
+            const double K = (double)((g.n_w + G * nparts - 1) / (G * nparts));
             const double epsE = 1.1 * uf * (B + Y);
             const double e_est = 1.25 * (2.0 * adt * epsE * (double)T1 +
                                          2.0 * uf * (f.w_half + 4.0 * B + dm) * adt * dm +
-                                         0x1p-40 * (double)T3) +
+                                         (K + 8.0) * 0x1p-46 * (double)T3) +
                                  8.0 * uf * fabs(dc);
             const bool ok = llabs(snu) < lim && llabs(dnu) < lim;
             thresh = ok ? (e_est + err_o(nu_m, sm) + err_o(nu_r, sr)) * 1.01 + 1e-300
