@@ -45,7 +45,7 @@ constexpr int kTcT = 512;             // threads of the tensor-core kernel
 constexpr uint32_t kTcATile = 128 * 128 * 2;   // filter tile: 128 phases x 128 taps
 constexpr uint32_t kTcBTile = 64 * 128 * 2;    // signal tile: 64 columns x 128 taps
 constexpr uint32_t kTcHBytes = kSl * 8 * 256 * 2;   // a chunk's filter slices
-constexpr int kTcABuf = 3;   // filter tiles in flight: group s runs while s + 2 is built
+constexpr int kTcABuf = 3;   // filter tiles in the ring, built ahead of the MMAs that read them
 constexpr size_t kTcSmem = kSl * kTcBTile + kTcABuf * kTcATile + kTcHBytes + 1024;
 constexpr uint32_t kTmemCols = 512;   // accumulator k at columns 64 k .. 64 k + 63 (k < 6)
 constexpr int64_t kTcPolls = 4000000; // bound of every mbarrier wait
@@ -191,16 +191,31 @@ __global__ void __launch_bounds__(128) k_build_E_tc(Geom g, FastView f,
 // ---- the slice products on the tensor cores ------------------------------
 
 struct TcShared {
-    uint64_t bar[kTcABuf];   // MMAs of slice group s done: bar[s % kTcABuf]
+    uint64_t full[kTcABuf];    // filter tile of slice group s built: full[s % kTcABuf]
+    uint64_t empty[kTcABuf];   // MMAs of slice group s done: empty[s % kTcABuf]
     uint64_t bar_x[kTcSlices];   // signal tile of slice t landed (TMA)
     uint64_t bar_h;    // filter slices landed (bulk copy)
+    uint64_t drain;    // every MMA issued so far done (error path)
     uint32_t tmem;
 };
+
+// Warp 0 issues the MMAs (one elected thread); warps 1 .. kTcT / 32 - 1 build
+// the filter tiles into the ring.
+constexpr int kTcBuilders = kTcT - 32;
 
 // Table tau (0: P from E and a; 1: Q from E^2 and phi; 2: R from E E_+ and
 // phi), column group grp (columns a = 64 grp .. + 63), tap chunk c: the
 // double-float partial D_c[b][a] of positions 128 a + b into tc_part.
 // `tmap` is the signal's TMA map (kernel parameter or global memory).
+//
+// Pipeline: slice group s (filter slice s against signal slices t < kSl - s,
+// accumulator s + t) reads filter buffer s % kTcABuf.  The builder warps fill
+// a buffer once the group that last read it is done (empty, committed by the
+// MMA thread) and arrive on its full barrier; the MMA thread waits on full,
+// issues the group and commits it to empty.  No block-wide barrier between
+// groups: the tensor core runs while the next tiles are built.  The j-th use
+// of a buffer is its barriers' phase j (parity j & 1); a builder never runs
+// more than one phase ahead of the MMA thread, so parities cannot alias.
 __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensorMap* tmap,
                                                int tau, int grp, int c, char* smem_raw,
                                                TcShared& ts) {
@@ -212,9 +227,13 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     const int flt = tau == 0 ? 0 : 1;
     const bool hook = f.tc_err[1] != 0;   // test hook: the filter copy is not issued
     if (tid == 0) {
-        for (int k = 0; k < kTcABuf; ++k) mbar_init(&ts.bar[k], 1);
+        for (int k = 0; k < kTcABuf; ++k) {
+            mbar_init(&ts.full[k], kTcBuilders / 32);
+            mbar_init(&ts.empty[k], 1);
+        }
         for (int t = 0; t < kSl; ++t) mbar_init(&ts.bar_x[t], 1);
         mbar_init(&ts.bar_h, 1);
+        mbar_init(&ts.drain, 1);
         fence_mbar_init();
         // filter slices of the chunk (contiguous), then the signal tiles: row
         // r of slice t is block 64 grp + r + c, two 64-wide boxes per slice
@@ -235,12 +254,11 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // filter tile of slice s: row b holds G[m - b + 127], m < 128
-    auto build_A = [&](int s, char* dst) {
+    // filter tile of slice s: row b holds G[m - b + 127], m < 128 (builder
+    // thread bt of kTcBuilders)
+    auto build_A = [&](int s, char* dst, int bt) {
         const char* hs = tH + (size_t)s * 8 * 256 * 2;
-#pragma unroll
-        for (int k0 = 0; k0 < 128 * 16; k0 += kTcT) {
-            const int k = k0 + tid;
+        for (int k = bt; k < 128 * 16; k += kTcBuilders) {
             const int b = k >> 4, jc = k & 15;
             const int r = 7 - (b & 7);
             const int q = jc + 15 - (b >> 3);
@@ -250,50 +268,62 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     };
     bool ok = mbar_wait(&ts.bar_h, 0, hook ? kTcHookPolls : kTcPolls);
     ok = __syncthreads_and(ok);
-    if (ok) {
-        build_A(0, tA);
-        build_A(1, tA + kTcATile);
-    }
-    fence_proxy_async_smem();
-    __syncthreads();
     const uint32_t tmem = ts.tmem;
     constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
-    // group s reads filter buffer s % kTcABuf and commits to bar[s % kTcABuf];
-    // its completion is that barrier's use s / kTcABuf (phase parity)
-    for (int s = 0; s < kSl; ++s) {
-        if (tid == 0 && ok) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(tA + (s % kTcABuf) * kTcATile);
-            for (int t = 0; s + t < kSl && ok; ++t) {
-                // the first slice group starts as the signal tiles land
-                if (s == 0) ok = mbar_wait(&ts.bar_x[t], 0, kTcPolls);
+    if (ok && warp == 0) {
+        if (lane == 0) {
+            bool issued = false;
+            for (int s = 0; s < kSl && ok; ++s) {
+                ok = mbar_wait(&ts.full[s % kTcABuf], (s / kTcABuf) & 1, kTcPolls);
                 if (!ok) break;
-                const uint32_t b0 = smem_u32(tB + t * kTcBTile);
-                const uint32_t d = tmem + (uint32_t)((s + t) * 64);
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(tA + (s % kTcABuf) * kTcATile);
+                for (int t = 0; s + t < kSl; ++t) {
+                    // the first slice group starts as the signal tiles land
+                    if (s == 0) ok = mbar_wait(&ts.bar_x[t], 0, kTcPolls);
+                    if (!ok) break;
+                    const uint32_t b0 = smem_u32(tB + t * kTcBTile);
+                    const uint32_t d = tmem + (uint32_t)((s + t) * 64);
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const uint32_t off = (uint32_t)((kk & 3) * 32);
-                    umma_bf16(d, umma_desc_sw128(a0 + (kk >> 2) * (128 * 128) + off),
-                              umma_desc_sw128(b0 + (kk >> 2) * (64 * 128) + off), idesc,
-                              (s > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint32_t off = (uint32_t)((kk & 3) * 32);
+                        umma_bf16(d, umma_desc_sw128(a0 + (kk >> 2) * (128 * 128) + off),
+                                  umma_desc_sw128(b0 + (kk >> 2) * (64 * 128) + off), idesc,
+                                  (s > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    issued = true;
                 }
+                if (!ok) break;
+                umma_commit(&ts.empty[s % kTcABuf]);
             }
-            umma_commit(&ts.bar[s % kTcABuf]);
+            if (!ok && issued) {
+                // drain what was issued before tensor memory is freed
+                umma_commit(&ts.drain);
+                mbar_wait(&ts.drain, 0, kTcPolls);
+            }
         }
-        if (s + 2 < kSl) {
-            // filter tile s + 2 goes into the buffer slice group s - 1 read
-            if (s >= 1 && ok)
-                ok = mbar_wait(&ts.bar[(s - 1) % kTcABuf], ((s - 1) / kTcABuf) & 1, kTcPolls);
-            ok = __syncthreads_and(ok);
-            fence_proxy_async_smem();   // the tensor core's reads before our writes
-            if (ok) build_A(s + 2, tA + ((s + 2) % kTcABuf) * kTcATile);
-            fence_proxy_async_smem();
-            ok = __syncthreads_and(ok);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+    } else if (ok) {
+        const int bt = tid - 32;
+        for (int s = 0; s < kSl && ok; ++s) {
+            char* dst = tA + (s % kTcABuf) * kTcATile;
+            if (s >= kTcABuf) {
+                // the group that read this buffer last is done
+                ok = mbar_wait(&ts.empty[s % kTcABuf], ((s - kTcABuf) / kTcABuf) & 1,
+                               kTcPolls);
+                ok = __all_sync(0xffffffffu, ok);   // the warp stays together
+                if (!ok) break;
+                fence_proxy_async_smem();   // the tensor core's reads before our writes
+            }
+            build_A(s, dst, bt);
+            fence_proxy_async_smem();       // our writes before the tensor core's reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ts.full[s % kTcABuf]);
         }
     }
-    // the last commit covers every MMA of this thread
+    // the last commit covers every MMA
     if (ok)
-        ok = mbar_wait(&ts.bar[(kSl - 1) % kTcABuf], ((kSl - 1) / kTcABuf) & 1, kTcPolls);
+        ok = mbar_wait(&ts.empty[(kSl - 1) % kTcABuf], ((kSl - 1) / kTcABuf) & 1, kTcPolls);
     ok = __syncthreads_and(ok);
     tc_fence_after();
     if (ok) {

@@ -70,6 +70,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// One arrival on `bar` (release at CTA scope: this thread's earlier writes
+// are visible to a thread whose wait sees the phase complete).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+
 // TMA: a 2D box of a tiled tensor map into shared memory (x innermost, in
 // elements; x * element size must be a multiple of 16 bytes), completing
 // bytes on `bar`.
