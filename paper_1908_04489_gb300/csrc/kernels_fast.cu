@@ -782,8 +782,10 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
     if (lane == 0 && have_best) hi = df_pm(best.gv, best.beta);
     dfloat* gv_k = (dfloat*)tie_terms;                 // gv_k[k * G + lane]
     float* be_k = (float*)(gv_k + kKeep * G);          // be_k[k * G + lane]
+    // kept rows holding a candidate of this stage (the same for the group)
+    const int nk = p_end > p0 ? min(kKeep, (p_end - p0 + G - 1) / G) : 0;
 #pragma unroll 2
-    for (int k = 0; k < kKeep; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const int p = p0 + lane + k * G;
         if (p < p_end) {
             const Eval e = eval_table(g, f, i, cand(p));
@@ -807,7 +809,7 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         pmin = best.pos;
     }
 #pragma unroll 1
-    for (int k = 0; k < kKeep; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const int p = p0 + lane + k * G;
         if (p < p_end && !df_lt(hi, df_pm(gv_k[k * G + lane], -be_k[k * G + lane]))) {
             const int64_t nu = cand(p);
@@ -825,20 +827,26 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
             pmin = p < pmin ? p : pmin;
         }
     }
-    vmin = gmin_i64<G>(vmin);
-    vmax = gmax_i64<G>(vmax);
+    // one value in play iff every lane's values in play equal the value at
+    // the first position in play (a vote instead of group minima and maxima)
     pmin = gmin_i32<G>(pmin);
-    if (vmin == vmax) {
+    bool one = false;
+    int64_t v0 = 0;
+    if (pmin != INT_MAX) {
+        v0 = (have_best && pmin == best.pos) ? best.nu : cand(pmin);
+        one = __all_sync(group_mask<G>(), vmin == INT64_MAX || (vmin == v0 && vmax == v0));
+    }
+    if (one) {
         // one value in play: its first occurrence wins, with the cost its
         // lane kept (every candidate of that value has the same cost)
         if (have_best && pmin == best.pos) return best;
         const int kk = (pmin - p0) / G, owner = (pmin - p0) % G;
         if (kk < kKeep) {
             __syncwarp(group_mask<G>());
-            return {gv_k[kk * G + owner], be_k[kk * G + owner], pmin, vmin, false, 0.0};
+            return {gv_k[kk * G + owner], be_k[kk * G + owner], pmin, v0, false, 0.0};
         }
-        const Eval e = eval_table(g, f, i, vmin);
-        return {e.gv, e.beta, pmin, vmin, false, 0.0};
+        const Eval e = eval_table(g, f, i, v0);
+        return {e.gv, e.beta, pmin, v0, false, 0.0};
     }
     if (Mode == kTierDefer) return {{0.f, 0.f}, 0.f, kDeferPos, 0, false, 0.0};
     // 3. several values in play.  Gather them into lanes (member m in lane
@@ -873,9 +881,9 @@ __device__ Best resolve(const Geom& g, const FastView& f, int64_t i, int lane,
         }
     };
 #pragma unroll 1
-    for (int k = 0; k < kKeep; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const int pb = p0 + k * G;
-        if (pb < p_end) {   // the same for the group
+        {
             const int p = pb + lane;
             const bool member = p < p_end &&
                                 !df_lt(hi, df_pm(gv_k[k * G + lane], -be_k[k * G + lane]));
