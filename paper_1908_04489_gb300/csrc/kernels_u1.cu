@@ -48,13 +48,14 @@ constexpr float kHMax = 0.05f;      // box half width aimed at when grouping
 constexpr float kHMoments = 0.25f;  // boxes wider than this get no moments
 constexpr float kZetaMax = 1.0f;    // largest |y - c| h expanded
 constexpr int kU1Runs = 32;         // runs per block of the u1 kernel (1 warp)
-constexpr int kBuildT = 256;        // threads per tile of the box kernel (one warp per box)
+constexpr int kBuildT = 256;        // threads per tile of the single-instance box kernel
+constexpr int kBuildTB = 512;       // threads per tile of the batched box kernel
 constexpr int kBoxDF = 16;          // moments up to this order in double-float
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---- sources and boxes ----------------------------------------------------------
 
-// One block per tile (kBuildT threads).
+// One block per tile (NW warps).
 //  1. Every thread: per source f_i and exp(delta f_i) (double-float).
 //  2. Warp 0: greedy grouping of consecutive sources into boxes whose f
 //     values (leading floats) span at most 2 kHMax; the last box of a tile
@@ -70,17 +71,21 @@ struct BoxTerms {
     dfloat d[kBoxDF + 1];             // orders 0..kBoxDF in double-float
     float f[kBoxTerms - kBoxDF];      // the higher ones in FP32
 };
-struct BuildSmem {
+constexpr int kChunkFast = 256;   // chunks whose f range the grouping reads at once
+template <int NW>
+struct BuildSmemT {
     int32_t s0[kBoxMax], n[kBoxMax];
     float fmin[kBoxMax], fmax[kBoxMax];
     float c[kBoxMax], pm[kBoxMax], sc[kBoxMax];
     int32_t ch0[kBoxMax + 1];          // first chunk of each box (expanded boxes)
     int32_t nch[kBoxMax];              // chunks of each box (0: not expanded)
     int nb;
-    BoxTerms terms[kBuildT / 32][32];   // per warp, per lane (source)
+    float cmin[kChunkFast], cmax[kChunkFast];   // f range of each 32-source chunk
+    BoxTerms terms[NW][32];             // per warp, per lane (source)
 };
 
-__device__ __forceinline__ void box_range(const FastView& f, BuildSmem& sm, int64_t slot,
+template <int NW>
+__device__ __forceinline__ void box_range(const FastView& f, BuildSmemT<NW>& sm, int64_t slot,
                                           int k, int lane) {
     const int64_t s0 = sm.s0[k];
     const int n = sm.n[k];
@@ -115,7 +120,8 @@ __device__ __forceinline__ void box_range(const FastView& f, BuildSmem& sm, int6
 }
 
 // Partial moments of sources b .. b + 31 of box k into part[0 .. kBoxTerms].
-__device__ __forceinline__ void chunk_moments(const FastView& f, BuildSmem& sm, int k, int b,
+template <int NW>
+__device__ __forceinline__ void chunk_moments(const FastView& f, BuildSmemT<NW>& sm, int k, int b,
                                               int warp, int lane, dfloat* part) {
     const int64_t s0 = sm.s0[k];
     const int cn = min(32, sm.n[k] - b);
@@ -158,7 +164,8 @@ __device__ __forceinline__ void chunk_moments(const FastView& f, BuildSmem& sm, 
 
 // Box k's moments from its chunk partials (in chunk order), Taylor
 // coefficients and exp(delta c).
-__device__ __forceinline__ void box_coefs(const Geom& g, const FastView& f, BuildSmem& sm,
+template <int NW>
+__device__ __forceinline__ void box_coefs(const Geom& g, const FastView& f, BuildSmemT<NW>& sm,
                                           int64_t slot, int k, int lane,
                                           const dfloat* part) {
     const int q0 = sm.ch0[k], q1 = sm.ch0[k + 1];
@@ -182,20 +189,38 @@ __device__ __forceinline__ void box_coefs(const Geom& g, const FastView& f, Buil
     if (lane == 31) f.box_C[slot] = df_from_double(exp(g.delta * (double)c));
 }
 
+template <int NW>
 __device__ __forceinline__ void box_build_body(const Geom& g, const FastView& f,
                                                const int64_t* __restrict__ nu,
-                                               BuildSmem& sm, int64_t t) {
+                                               BuildSmemT<NW>& sm, int64_t t) {
     const int64_t t0 = t * f.tile;
     const int64_t t1 = min(t0 + f.tile, g.n_x);
     const dfloat dl = {f.delta_hi, f.delta_lo};
     const dfloat step = {f.step_hi, f.step_lo};
-    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
-        // f_i = nu_i delta 2^-shift in double-float (the lattice index is exact)
-        const dfloat fv = df_mul(df_from_i64(nu[i]), step);
-        f.src_nu[i] = nu[i];
-        f.src_f[i] = fv;
-        // exp(delta f_i) in double-float (|delta f_i| stays below ~0.8)
-        f.src_F[i] = df_exp(df_mul(fv, dl), f.t64);
+    // every warp takes whole 32-source chunks (blockDim is a multiple of 32)
+    for (int64_t b0 = t0 + (threadIdx.x & ~31); b0 < t1; b0 += blockDim.x) {
+        const int64_t i = b0 + (threadIdx.x & 31);
+        float lo = FLT_MAX, hi = -FLT_MAX;
+        if (i < t1) {
+            // f_i = nu_i delta 2^-shift in double-float (the lattice index is exact)
+            const dfloat fv = df_mul(df_from_i64(nu[i]), step);
+            f.src_nu[i] = nu[i];
+            f.src_f[i] = fv;
+            // exp(delta f_i) in double-float (|delta f_i| stays below ~0.8)
+            f.src_F[i] = df_exp(df_mul(fv, dl), f.t64);
+            lo = hi = fv.hi;
+        }
+        // the chunk's f range (leading floats), for the grouping below
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        const int64_t c = (b0 - t0) >> 5;
+        if ((threadIdx.x & 31) == 0 && c < kChunkFast) {
+            sm.cmin[c] = lo;
+            sm.cmax[c] = hi;
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -205,15 +230,21 @@ __device__ __forceinline__ void box_build_body(const Geom& g, const FastView& f,
         int nb = 0;
         int64_t sb = t0;
         float bmin = FLT_MAX, bmax = -FLT_MAX;
-        // f of the next two chunks in flight while a chunk is grouped
-        float fa = t0 + lane < t1 ? f.src_f[t0 + lane].hi : 0.0f;
-        float fb = t0 + 32 + lane < t1 ? f.src_f[t0 + 32 + lane].hi : 0.0f;
         for (int64_t base = t0; base < t1; base += 32) {
+            // a chunk that fits whole in the open box (or once no box may
+            // close) closes nothing: every prefix spans no more than the chunk
+            const int64_t c = (base - t0) >> 5;
+            if (c < kChunkFast) {
+                const float lo = fminf(bmin, sm.cmin[c]), hi = fmaxf(bmax, sm.cmax[c]);
+                if (nb == kBoxMax - 1 || hi - lo <= wmax) {
+                    bmin = lo;
+                    bmax = hi;
+                    continue;
+                }
+            }
             const int64_t i = base + lane;
             const bool valid = i < t1;
-            const float fi = fa;   // 0 beyond the tile
-            fa = fb;
-            fb = base + 64 + lane < t1 ? f.src_f[base + 64 + lane].hi : 0.0f;
+            const float fi = valid ? f.src_f[i].hi : 0.0f;
             int from = 0;
             for (;;) {
                 const bool part = valid && lane >= from;
@@ -266,7 +297,7 @@ __device__ __forceinline__ void box_build_body(const Geom& g, const FastView& f,
         f.box_s0[slot0 + threadIdx.x] = sm.s0[threadIdx.x];
         f.box_n[slot0 + threadIdx.x] = sm.n[threadIdx.x];
     }
-    constexpr int kWarps = kBuildT / 32;
+    constexpr int kWarps = NW;
     for (int k = warp; k < nb; k += kWarps) box_range(f, sm, slot0 + k, k, lane);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -636,8 +667,8 @@ __device__ __forceinline__ void u1_combine_body(const Geom& g, const FastView& f
 
 __global__ void __launch_bounds__(kBuildT) k_box_build(Geom g, FastView f,
                                                       const int64_t* __restrict__ nu) {
-    __shared__ BuildSmem sm;
-    box_build_body(g, f, nu, sm, blockIdx.x);
+    __shared__ BuildSmemT<kBuildT / 32> sm;
+    box_build_body<kBuildT / 32>(g, f, nu, sm, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kRunT) k_run_shift(Geom g, FastView f) {
@@ -669,12 +700,18 @@ __device__ __forceinline__ BlockRef stage(const InstDev* insts, const BlockRef* 
     return r;
 }
 
-__global__ void __launch_bounds__(kBuildT) kb_box_build(const InstDev* insts,
+// NW warps per tile, the per-warp term scratch in dynamic shared memory.  A
+// launch of few tiles (a single instance) takes twice the warps of the
+// single-instance kernel, spreading a tile's boxes and chunks wider; each
+// chunk's and box's sums are the same either way.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) kb_box_build(const InstDev* insts,
                                                        const BlockRef* map) {
     __shared__ InstDev sd;
-    __shared__ BuildSmem sm;
+    extern __shared__ __align__(16) char box_smem[];
+    BuildSmemT<NW>& sm = *reinterpret_cast<BuildSmemT<NW>*>(box_smem);
     const BlockRef r = stage(insts, map, sd);
-    box_build_body(sd.g, sd.f, sd.nu[sd.cur ^ 1], sm, r.local);
+    box_build_body<NW>(sd.g, sd.f, sd.nu[sd.cur ^ 1], sm, r.local);
 }
 
 __global__ void __launch_bounds__(kRunT) kb_run_shift(const InstDev* insts,
@@ -813,6 +850,16 @@ void launch_mmse_fast(const Geom& g, const FastView& f, const int64_t* nu,
     if (prof) prof->end(k, ev);
 }
 
+cudaError_t u1_init_attributes() {
+    const cudaError_t e = cudaFuncSetAttribute(kb_box_build<kBuildTB / 32>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(BuildSmemT<kBuildTB / 32>));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kb_box_build<kBuildT / 32>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(BuildSmemT<kBuildT / 32>));
+}
+
 int64_t u1_batch_blocks(const Geom& g, const FastPlan& fp, int kind) {
     switch (kind) {
         case kBTile: return fp.n_tiles;
@@ -830,7 +877,13 @@ void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s, Prof* prof) {
     const InstDev* d = bl.insts;
     {
         ProfScope ps(prof, "u1_boxes");
-        kb_box_build<<<(unsigned)bl.n_blocks[kBTile], kBuildT, 0, s>>>(d, bl.map[kBTile]);
+        const unsigned nb = (unsigned)bl.n_blocks[kBTile];
+        if (nb <= 2 * (unsigned)sm_count())
+            kb_box_build<kBuildTB / 32><<<nb, kBuildTB, sizeof(BuildSmemT<kBuildTB / 32>), s>>>(
+                d, bl.map[kBTile]);
+        else
+            kb_box_build<kBuildT / 32><<<nb, kBuildT, sizeof(BuildSmemT<kBuildT / 32>), s>>>(
+                d, bl.map[kBTile]);
     }
     {
         ProfScope ps(prof, "u1_shift");

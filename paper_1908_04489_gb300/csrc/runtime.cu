@@ -400,6 +400,7 @@ ucp_status inst_init(ucp_inst* in, ucp_ctx* ctx, const ucp_params& p,
     if (g.sc_fast) cudaMemsetAsync(d.sc_consts, 0, 8 * 4, stream);
     if (in->fast) {
         if (tc_init_attributes() != cudaSuccess) return check(in, "tensor-core kernel attributes");
+        if (u1_init_attributes() != cudaSuccess) return check(in, "u1 kernel attributes");
         ucp_status st = fast_alloc(in);
         if (st != UCP_OK) return st;
     }

@@ -27,6 +27,8 @@ void u1_plan(const Geom& g, int max_tiles, FastPlan* fp);
 // an allocator get(ctx, bytes); false if an allocation failed.
 size_t u1_scratch_bytes(const Geom& g, const FastPlan& fp, size_t align);
 bool u1_carve(const Geom& g, FastView* f, void* (*get)(void*, size_t), void* ctx);
+// One-time attribute of the batched u1 kernels (dynamic shared memory).
+cudaError_t u1_init_attributes();
 int64_t u1_batch_blocks(const Geom& g, const FastPlan& fp, int kind);
 void launch_batch_u1(const BatchLaunch& bl, cudaStream_t s, Prof* prof = nullptr);
 void launch_fast_setup(const Geom& g, const FastView& f, cudaStream_t s);
