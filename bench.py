@@ -119,7 +119,7 @@ FLOPS_SEARCH_CAND = 104.0
 # DRAM bytes per launch from one-kernel ncu captures of the current kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum; cold cache), keyed by the
 # profiled kernel group; None where the kernel changed since its capture.
-TRAFFIC_BYTES = {"c2": {"search": 0.257e6, "tables": 1.70e6, "mmse_main": 0.074e6}}
+TRAFFIC_BYTES = {"c2": {"search": 0.264e6, "tables": 1.70e6, "mmse_main": 0.074e6}}
 TRAFFIC_SOURCE = "profiles/hot_kernels_c2_ncu_full.md"
 
 # kernels launched per timed group of the library's profiler (the groups not
