@@ -121,7 +121,9 @@ def test_batch_against_oracle(binding):
 
 def test_batch_c3_sampled(binding):
     """Config c3 (256 uneven instances, delta in {0.01, 0.02}, 10 sweeps):
-    sampled members equal their single-instance solves bit for bit."""
+    sampled members equal their single-instance solves bit for bit.  The
+    batch's launches have more than two u1 tiles per SM, so its box build
+    runs 8 warps per tile where a single instance's runs 16: the same sums."""
     import torch
     ps = W.c3()
     stream = torch.cuda.Stream()
