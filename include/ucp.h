@@ -391,10 +391,14 @@ UCP_API ucp_status ucp_srv_destroy(ucp_srv* s);
 /* Test hook of the bounded waits (no paper counterpart): with on = 1 the
  * tensor-core table kernel of this fast-path instance no longer issues its
  * filter-slice copy, so the one wait that copy would complete runs out (after
- * a short bound; nothing is in flight behind it).  The kernel then waits for
- * its other copies, writes zero partials, frees its tensor memory and sets
- * the error flag; the next synchronising call returns UCP_E_TIMEOUT and the
- * instance is poisoned.  UCP_E_STATE on the plain path. */
+ * a short bound; nothing is in flight behind it).  With on = 2 its builder
+ * warps stop after the first filter tile, so the MMA thread's wait for the
+ * second runs out (short bound) while the first slice group's MMAs are in
+ * flight; it waits for them to complete.  Either way the kernel then waits
+ * for its copies, writes zero partials, frees its tensor memory and sets the
+ * error flag; the next synchronising call returns UCP_E_TIMEOUT and the
+ * instance is poisoned.  on = 0 restores normal operation; other values get
+ * UCP_E_ARG.  UCP_E_STATE on the plain path. */
 UCP_API ucp_status ucp_test_tc_skip_copy(ucp_inst* inst, int32_t on);
 
 /* Measured ALU throughput of the current device (no paper counterpart: the

@@ -49,9 +49,11 @@ constexpr int kTcABuf = 3;   // filter tiles in the ring, built ahead of the MMA
 constexpr size_t kTcSmem = kSl * kTcBTile + kTcABuf * kTcATile + kTcHBytes + 1024;
 constexpr uint32_t kTmemCols = 512;   // accumulator k at columns 64 k .. 64 k + 63 (k < 6)
 constexpr int64_t kTcPolls = 4000000; // bound of every mbarrier wait
-// Bound of the one wait the test hook (tc_err[1] != 0) leaves without a copy:
-// the filter-slice copy is then not issued, so that wait guards nothing in
-// flight and may end early.
+// Bound of the one wait the test hook (tc_err[1] != 0) leaves without its
+// producer, which guards nothing in flight and may end early: hook 1 issues
+// no filter-slice copy (the wait for it); hook 2 builds only the first filter
+// tile (the MMA thread's wait for the second, after the first slice group is
+// in flight; tc_hook_one_group).
 constexpr int64_t kTcHookPolls = 20000;
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) {   // exact for |v| <= 256 integers
@@ -203,6 +205,50 @@ struct TcShared {
 // the filter tiles into the ring.
 constexpr int kTcBuilders = kTcT - 32;
 
+// Test hook 2 (kept out of the pipeline's code): the builders fill only the
+// first filter buffer; the MMA thread issues slice group 0, its wait for the
+// second tile runs out after the short bound, and it waits for the issued
+// MMAs (drain barrier) before returning.  Leaves nothing in flight.
+__device__ __noinline__ void tc_hook_one_group(char* tA, const char* tB, const char* tH,
+                                               uint32_t tmem, TcShared& ts) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp > 0) {
+        for (int k = tid - 32; k < 128 * 16; k += kTcBuilders) {
+            const int b = k >> 4, jc = k & 15;
+            const int r = 7 - (b & 7);
+            const int q = jc + 15 - (b >> 3);
+            *(uint4*)(tA + sw128_offset(128, b, jc)) = *(const uint4*)(tH + (r * 256 + 8 * q) * 2);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ts.full[0]);
+        return;
+    }
+    if (lane != 0) return;
+    if (!mbar_wait(&ts.full[0], 0, kTcPolls)) return;
+    tc_fence_after();
+    constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
+    const uint32_t a0 = smem_u32(tA);
+    bool issued = false;
+    for (int t = 0; t < kSl; ++t) {
+        if (!mbar_wait(&ts.bar_x[t], 0, kTcPolls)) break;
+        const uint32_t b0 = smem_u32(tB + t * kTcBTile);
+        for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t off = (uint32_t)((kk & 3) * 32);
+            umma_bf16(tmem + (uint32_t)(t * 64),
+                      umma_desc_sw128(a0 + (kk >> 2) * (128 * 128) + off),
+                      umma_desc_sw128(b0 + (kk >> 2) * (64 * 128) + off), idesc,
+                      kk > 0 ? 1u : 0u);
+        }
+        issued = true;
+    }
+    mbar_wait(&ts.full[1], 0, kTcHookPolls);   // never filled: runs out
+    if (issued) {
+        umma_commit(&ts.drain);
+        mbar_wait(&ts.drain, 0, kTcPolls);
+    }
+}
+
 // Table tau (0: P from E and a; 1: Q from E^2 and phi; 2: R from E E_+ and
 // phi), column group grp (columns a = 64 grp .. + 63), tap chunk c: the
 // double-float partial D_c[b][a] of positions 128 a + b into tc_part.
@@ -225,7 +271,8 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     char* tH = tA + kTcABuf * kTcATile;  // the chunk's filter slices, 8 shifts each
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int flt = tau == 0 ? 0 : 1;
-    const bool hook = f.tc_err[1] != 0;   // test hook: the filter copy is not issued
+    const int hook_kind = f.tc_err[1];    // test hook (see kTcHookPolls)
+    const bool hook = hook_kind == 1;     // the filter copy is not issued
     if (tid == 0) {
         for (int k = 0; k < kTcABuf; ++k) {
             mbar_init(&ts.full[k], kTcBuilders / 32);
@@ -270,7 +317,10 @@ __device__ __forceinline__ void tc_tables_body(const FastView& f, const CUtensor
     ok = __syncthreads_and(ok);
     const uint32_t tmem = ts.tmem;
     constexpr uint32_t idesc = umma_idesc_bf16(128, 64);
-    if (ok && warp == 0) {
+    if (ok && hook_kind == 2) {
+        tc_hook_one_group(tA, tB, tH, tmem, ts);
+        ok = false;
+    } else if (ok && warp == 0) {
         if (lane == 0) {
             bool issued = false;
             for (int s = 0; s < kSl && ok; ++s) {

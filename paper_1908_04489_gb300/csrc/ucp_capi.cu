@@ -417,7 +417,7 @@ extern "C" ucp_status ucp_tie_recosts(ucp_inst* in, int64_t* out) {
 }
 
 extern "C" ucp_status ucp_test_tc_skip_copy(ucp_inst* in, int32_t on) {
-    if (!in || (on != 0 && on != 1)) return UCP_E_ARG;
+    if (!in || on < 0 || on > 2) return UCP_E_ARG;
     if (in->poisoned || !in->fast) return UCP_E_STATE;
     const int32_t v = on;
     cudaMemcpyAsync(in->fv.tc_err + 1, &v, sizeof(v), cudaMemcpyHostToDevice, in->stream);

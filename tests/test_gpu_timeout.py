@@ -1,9 +1,12 @@
 """The bounded waits of the tensor-core table kernel turn into a status, not a
-hang: the test hook keeps the kernel from issuing its filter-slice copy, so
-the wait that copy would complete runs out (nothing is in flight behind it;
-the kernel waits for its other copies, writes zero partials and frees its
-tensor memory).  The next synchronising call reports UCP_E_TIMEOUT, the
-instance is poisoned, and the context keeps working: a new instance on it
+hang.  Test hook 1 keeps the kernel from issuing its filter-slice copy, so
+the wait that copy would complete runs out (nothing is in flight behind it);
+hook 2 stops the builder warps after the first filter tile, so the MMA
+thread's wait for the second runs out while the first slice group's MMAs are
+in flight, and the kernel waits for them before freeing tensor memory.
+Either way the kernel waits for its other copies, writes zero partials and
+frees its tensor memory; the next synchronising call reports UCP_E_TIMEOUT,
+the instance is poisoned, and the context keeps working: a new instance on it
 solves exactly as before."""
 import ctypes
 
@@ -16,7 +19,8 @@ pytestmark = pytest.mark.gpu
 UCP_E_TIMEOUT, UCP_E_STATE = -5, -6
 
 
-def test_tensor_core_wait_runs_out_and_reports_a_timeout():
+@pytest.mark.parametrize("hook", [1, 2])
+def test_tensor_core_wait_runs_out_and_reports_a_timeout(hook):
     import torch
     from paper_1908_04489_gb300 import binding
     L = binding.load()
@@ -27,7 +31,7 @@ def test_tensor_core_wait_runs_out_and_reports_a_timeout():
         J_ref = ref.J_history()
     inst = binding.Instance(p)
     inst.sweep(1)
-    assert L.ucp_test_tc_skip_copy(inst.h, 1) == 0
+    assert L.ucp_test_tc_skip_copy(inst.h, hook) == 0
     with pytest.raises(binding.UcpError) as e:
         inst.sweep(1)
         inst.eval_J()
